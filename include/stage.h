@@ -1,0 +1,261 @@
+/*
+ * stage.h -- C ABI of the GB300 fleet-staging engine.
+ *
+ * The engine places K identical vehicles at K of B candidate bases so that as
+ * many round-trip missions as possible are within range R, and among those
+ * placements the total round-trip distance is smallest.  It implements the
+ * base ranking of Alg. 1 and the Tabu search of Alg. 3 of "Algorithms for
+ * Optimizing Fleet Staging of Air Ambulances" (arXiv 2001.05291), read for
+ * identical vehicles:
+ *   - a mission goes base -> pickup -> drop-off -> same base (Sec. 3);
+ *   - each leg costs ceil(Euclidean distance) in integer metres, the planar
+ *     metric that Sec. 3 allows for simulated data in place of Eq. 1;
+ *   - c[b][m] = leg(b, pickup_m) + leg(pickup_m, drop_m) + leg(drop_m, b);
+ *   - f(c) = (1, c) if c <= R else (0, 0);  F(O) = sum_m f(min_{o in O} c[o][m]);
+ *     more covered missions is better, then a smaller distance (Eq. 2 with
+ *     the coverage aim of Sec. 1);
+ *   - the Tabu neighbourhood is every swap (close i in O, open available j
+ *     not in O), evaluated in full each iteration on the GPU.
+ *
+ * Conventions
+ *   - Every function returns a stage_status: STAGE_OK (0), STAGE_PENDING (1)
+ *     or a negative error.  stage_last_error() gives the message of the last
+ *     error on a context.
+ *   - Handles are opaque.  Input arrays are copied in (the caller keeps
+ *     ownership); outputs go to caller-allocated HOST buffers unless a flag
+ *     says otherwise.  Nothing returned points into library memory.
+ *   - Coordinates are int32 metres with |x|, |y| <= STAGE_MAX_COORD, so that
+ *     every squared leg length is below 2^52 and the float64 square root of
+ *     the exact integer is correctly rounded to the right ceiling.
+ *   - Base ids are 0-based indices into the instance's base array.
+ *   - All results are integers and are bit-identical run to run.
+ *   - A context is not thread-safe unless created with STAGE_THREADSAFE.
+ *   - The library never falls back to the CPU: without a CUDA device every
+ *     call that needs one returns STAGE_ERR_CUDA.
+ */
+#ifndef STAGE_H
+#define STAGE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define STAGE_API __attribute__((visibility("default")))
+#else
+#define STAGE_API
+#endif
+
+typedef int32_t stage_status;
+
+#define STAGE_OK                0
+#define STAGE_PENDING           1
+#define STAGE_ERR_INVALID_ARG  (-1)  /* malformed argument (NULL, K > B, duplicate base, ...) */
+#define STAGE_ERR_OUT_OF_RANGE (-2)  /* a size or coordinate beyond the limits below */
+#define STAGE_ERR_NO_MEMORY    (-3)  /* device allocation failed */
+#define STAGE_ERR_ADMISSION    (-4)  /* over the context's HBM budget, or no free slot */
+#define STAGE_ERR_TIMEOUT      (-5)  /* a bounded device-side wait or a poll timed out */
+#define STAGE_ERR_CUDA         (-6)  /* CUDA runtime error, or no device */
+#define STAGE_ERR_INTERNAL     (-7)  /* a device self-check failed */
+#define STAGE_ERR_NOT_FOUND    (-8)  /* unknown instance handle or ticket */
+
+#define STAGE_MAX_COORD    (1 << 24)   /* |x|, |y| <= 16,777,216 m */
+#define STAGE_MAX_BASES    65535
+#define STAGE_MAX_MISSIONS (1 << 24)
+#define STAGE_MAX_K        1024
+
+/* context flags */
+#define STAGE_THREADSAFE   1u   /* serialise calls on the context with a mutex */
+#define STAGE_PROFILE      2u   /* time every kernel launch with CUDA events */
+
+/* instance descriptor flags */
+#define STAGE_DESC_DEVICE  1u   /* base_xy/pick_xy/drop_xy/base_available are device pointers */
+
+/* trajectory flags */
+#define STAGE_MOVE_FALLBACK   1  /* every move was tabu and none beat the best: best of all taken */
+#define STAGE_MOVE_ASPIRATION 2  /* a tabu move admitted because it beats the best so far */
+#define STAGE_MOVE_NEW_BEST   4  /* the move produced a new best placement */
+
+typedef struct stage_ctx stage_ctx;
+typedef uint64_t stage_inst;   /* instance handle; 0 is never a valid handle */
+
+/* Optional device allocator (e.g. PyTorch's caching allocator).  alloc returns
+ * a device pointer aligned to 256 bytes or NULL; free releases it. */
+typedef void *(*stage_alloc_fn)(size_t bytes, void *user);
+typedef void (*stage_free_fn)(void *ptr, size_t bytes, void *user);
+
+typedef struct {
+    int32_t device;            /* CUDA device ordinal */
+    uint32_t flags;            /* STAGE_THREADSAFE | STAGE_PROFILE */
+    uint64_t hbm_budget_bytes; /* cap on the context's device memory; 0 = device limit */
+    int32_t max_slots;         /* batch/serving slots run concurrently; 0 = 8 */
+    int32_t reserved0;
+    int64_t spin_limit;        /* bound on every device-side spin; 0 = 1<<26 polls */
+    stage_alloc_fn alloc;      /* NULL = cudaMalloc */
+    stage_free_fn free;        /* must be set iff alloc is */
+    void *alloc_user;
+    void *stream;              /* cudaStream_t to run on; NULL = a stream the context owns */
+} stage_config;
+
+/* Problem data (Sec. 3): B candidate bases and M missions.  Coordinates are
+ * interleaved (x0, y0, x1, y1, ...) int32 metres.  base_available may be NULL
+ * (all available); an unavailable base is never opened. */
+typedef struct {
+    int32_t B;
+    int32_t M;
+    uint32_t flags;            /* STAGE_DESC_DEVICE */
+    int32_t reserved0;
+    const int32_t *base_xy;    /* [2*B] */
+    const int32_t *pick_xy;    /* [2*M] pickup points */
+    const int32_t *drop_xy;    /* [2*M] drop-off points */
+    const uint8_t *base_available; /* [B] or NULL */
+} stage_instance_desc;
+
+/* One Tabu iteration: the swap applied and the objective after it. */
+typedef struct {
+    int32_t iter;   /* iteration number t */
+    int32_t i;      /* base closed */
+    int32_t j;      /* base opened */
+    int32_t flags;  /* STAGE_MOVE_* */
+    int64_t cov;    /* missions covered after the move */
+    int64_t dist;   /* covered distance after the move (metres) */
+} stage_move;
+
+/* Resumable Tabu state (placement, tabu expiries, best so far).  All arrays
+ * are caller-owned host buffers. */
+typedef struct {
+    int32_t t;              /* iteration number of the next step */
+    int32_t best_iter;      /* iteration that produced the best (-1: the start) */
+    int64_t best_cov;
+    int64_t best_dist;
+    int32_t *open;          /* [K] current placement */
+    int32_t *best_open;     /* [K] best placement so far */
+    int32_t *tabu_expiry;   /* [B] move (i, j) is tabu at t iff t < expiry[i] or t < expiry[j] */
+} stage_tabu_state;
+
+typedef struct {
+    int32_t K;                /* vehicles, 1 <= K <= min(B, STAGE_MAX_K) */
+    int32_t R;                /* range in metres, 0 <= R < INT32_MAX */
+    int32_t iters;            /* iterations (Alg. 3 outer loop), >= 0 */
+    int32_t tenure;           /* iterations a moved base stays tabu, >= 0 */
+    int32_t accept_worsening; /* 1: best admissible move even if worse; 0: stop when no
+                                 move improves (the improving-only rule of Sec. 4.3) */
+    int32_t reserved0;
+    const int32_t *start_open;        /* [K] start placement, or NULL: stage_rank_bases */
+    const stage_tabu_state *resume;   /* continue from this state, or NULL */
+} stage_tabu_params;
+
+typedef struct {
+    int32_t n_moves;        /* moves applied (== iterations unless the search stopped) */
+    int32_t best_iter;
+    int64_t best_cov;
+    int64_t best_dist;
+    int64_t final_cov;
+    int64_t final_dist;
+    int32_t *best_open;     /* [K] caller buffer or NULL; filled sorted ascending */
+    int32_t *final_open;    /* [K] caller buffer or NULL; filled sorted ascending */
+    stage_tabu_state *end_state; /* NULL, or filled (caller's arrays) to resume from */
+} stage_tabu_result;
+
+/* ------------------------------------------------------------------ context */
+
+/* Create a context on cfg->device (cfg may be NULL: device 0, defaults).
+ * Errors: STAGE_ERR_CUDA (no device), STAGE_ERR_INVALID_ARG. */
+STAGE_API stage_status stage_create(const stage_config *cfg, stage_ctx **out);
+
+/* Free every instance, slot and buffer of the context.  NULL is a no-op. */
+STAGE_API stage_status stage_destroy(stage_ctx *ctx);
+
+/* Copy the last error message (NUL-terminated, truncated to n) into buf. */
+STAGE_API stage_status stage_last_error(const stage_ctx *ctx, char *buf, size_t n);
+
+/* Library version as major*10000 + minor*100 + patch. */
+STAGE_API int32_t stage_version(void);
+
+/* Device memory currently held by the context, in bytes. */
+STAGE_API stage_status stage_memory_used(const stage_ctx *ctx, uint64_t *out_bytes);
+
+/* ----------------------------------------------------------------- instance */
+
+/* Copy an instance in and build its B x M round-trip cost table on the device
+ * (Sec. 3 distance matrices; the summed base-pickup-destination distance of
+ * Alg. 1).  The table is int32 row-major, one row per base, missions padded
+ * to a multiple of 64 with INT32_MAX.
+ * Errors: STAGE_ERR_INVALID_ARG (NULL pointers, B < 1, M < 1),
+ * STAGE_ERR_OUT_OF_RANGE (B, M or a coordinate beyond the limits),
+ * STAGE_ERR_ADMISSION (over the HBM budget), STAGE_ERR_NO_MEMORY. */
+STAGE_API stage_status stage_load_instance(stage_ctx *ctx, const stage_instance_desc *desc, stage_inst *out);
+
+/* Release an instance and its device memory. */
+STAGE_API stage_status stage_unload_instance(stage_ctx *ctx, stage_inst inst);
+
+/* Base ranking (Alg. 1): S[b] = sum over missions of c[b][m] (int64), then the
+ * K available bases with the smallest S, ties to the lower index.  out_open
+ * [K] receives them in rank order; out_rowsum [B] (nullable) receives S.
+ * Errors: STAGE_ERR_INVALID_ARG (K < 1, fewer than K available bases). */
+STAGE_API stage_status stage_rank_bases(stage_ctx *ctx, stage_inst inst, int32_t K, int32_t *out_open,
+                              int64_t *out_rowsum);
+
+/* F(O) for the placement open[K] (distinct, available base ids) at range R:
+ * missions covered and their summed distance (Eq. 2 with coverage).
+ * Errors: STAGE_ERR_INVALID_ARG (duplicate, unknown or unavailable base). */
+STAGE_API stage_status stage_evaluate_placement(stage_ctx *ctx, stage_inst inst, const int32_t *open,
+                                      int32_t K, int32_t R, int64_t *out_cov, int64_t *out_dist);
+
+/* The whole swap neighbourhood of the placement open[K] at range R: for every
+ * slot k and every base j, out_cov[k*B + j], out_dist[k*B + j] = F(O - open[k]
+ * + j) when j is closed and available, else -1.  (Alg. 3 evaluates these
+ * moves one by one; here one streaming pass of the table computes all.) */
+STAGE_API stage_status stage_evaluate_swaps(stage_ctx *ctx, stage_inst inst, const int32_t *open,
+                                  int32_t K, int32_t R, int64_t *out_cov, int64_t *out_dist);
+
+/* Tabu search (Alg. 3, read for identical vehicles):
+ *   - start: params->start_open, or the ranking of Alg. 1, or params->resume;
+ *   - each iteration evaluates every swap, takes the best admissible one
+ *     (not tabu, or strictly better than the best so far), ordered by
+ *     (covered desc, distance asc, i asc, j asc); when every move is tabu and
+ *     none beats the best, the best of all moves is taken (STAGE_MOVE_FALLBACK);
+ *   - both bases of the move become tabu for `tenure` iterations;
+ *   - stops early when no closed available base exists, or, with
+ *     accept_worsening = 0, when the chosen move does not improve.
+ * traj (nullable) receives one stage_move per applied move ([iters]).
+ * Errors: STAGE_ERR_INVALID_ARG, STAGE_ERR_OUT_OF_RANGE, STAGE_ERR_INTERNAL
+ * (a device self-check failed: the incremental objective disagreed with the
+ * chosen move's). */
+STAGE_API stage_status stage_tabu_run(stage_ctx *ctx, stage_inst inst, const stage_tabu_params *params,
+                            stage_tabu_result *result, stage_move *traj);
+
+/* ---------------------------------------------------------------- profiling */
+
+/* Kernel timing (contexts created with STAGE_PROFILE): launches and summed
+ * device milliseconds of the named kernel ("swap_eval", "select", "refresh",
+ * "table", "rowsum", "topk", "init", "evaluate") since the last reset. */
+STAGE_API stage_status stage_kernel_stats(stage_ctx *ctx, const char *kernel, int64_t *launches,
+                                double *total_ms);
+STAGE_API stage_status stage_reset_stats(stage_ctx *ctx);
+
+/* ------------------------------------------------------------ test support */
+
+/* Copy rows [b0, b0+nb) x missions [m0, m0+nm) of the cost table into out
+ * (row-major nb x nm). */
+STAGE_API stage_status stage_read_table(stage_ctx *ctx, stage_inst inst, int32_t b0, int32_t nb,
+                              int32_t m0, int32_t nm, int32_t *out);
+
+/* Best and second-best open base of every mission for placement open[K],
+ * ordered by (cost, base id): a, b (INT32_MAX when K = 1), b1, b2 (-1 when
+ * K = 1) -- the per-mission ranking of the chosen bases in Alg. 1.  With
+ * tabu_steps > 0, first runs that many Tabu iterations (params as in
+ * stage_tabu_run, start open) and returns the arrays as the GPU's incremental
+ * refresh left them. */
+STAGE_API stage_status stage_best_two(stage_ctx *ctx, stage_inst inst, const int32_t *open, int32_t K,
+                            int32_t R, int32_t tabu_steps, int32_t tenure, int32_t *a,
+                            int32_t *b, int32_t *b1, int32_t *b2);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* STAGE_H */

@@ -1,0 +1,776 @@
+// Host runtime of the staging engine: contexts, instances, device memory,
+// validation and the Tabu driver loop behind the C ABI of include/stage.h.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <unordered_map>
+#include <utility>
+#include <vector>
+
+#include "stage_internal.h"
+
+using namespace stg;
+
+namespace {
+
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+
+struct KernelStat {
+    int64_t launches = 0;
+    double ms = 0.0;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending;
+};
+
+struct Instance {
+    int B = 0, M = 0, M_pad = 0;
+    int n_avail = 0;
+    std::vector<uint8_t> h_avail;
+    DevBuf mem_coords;   // base, pick, drop, pd, avail
+    DevBuf mem_table;    // B x M_pad int32
+    int2 *base = nullptr, *pick = nullptr, *drop = nullptr;
+    int32_t *pd = nullptr;
+    uint8_t *avail = nullptr;
+    int32_t *cost = nullptr;
+    // Tabu workspace, sized for ws_K / ws_traj
+    DevBuf mem_ws;
+    int ws_K = 0, ws_traj = -1;
+    TabuBuffers tb{};
+    DevBuf mem_scratch;  // rank sums, evaluation outputs, exports
+    size_t scratch_bytes = 0;
+};
+
+}  // namespace
+
+struct stage_ctx {
+    int device = 0;
+    uint32_t flags = 0;
+    uint64_t budget = 0;
+    int max_slots = 8;
+    int64_t spin_limit = 1ll << 26;
+    stage_alloc_fn alloc = nullptr;
+    stage_free_fn free = nullptr;
+    void *alloc_user = nullptr;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    uint64_t used = 0;
+    std::unordered_map<uint64_t, Instance *> insts;
+    uint64_t next_id = 1;
+    std::string err;
+    std::recursive_mutex mu;
+    std::unordered_map<std::string, KernelStat> stats;
+    std::vector<cudaEvent_t> event_pool;
+    void *pinned = nullptr;       // small pinned host buffer for early-stop polls
+};
+
+namespace {
+
+struct Guard {
+    stage_ctx *c;
+    bool locked;
+    explicit Guard(stage_ctx *ctx) : c(ctx), locked(ctx && (ctx->flags & STAGE_THREADSAFE))
+    {
+        if (locked) c->mu.lock();
+    }
+    ~Guard()
+    {
+        if (locked) c->mu.unlock();
+    }
+};
+
+stage_status set_err(stage_ctx *c, stage_status code, const char *fmt, ...)
+{
+    if (c) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        c->err = buf;
+    }
+    return code;
+}
+
+#define CK(call)                                                                         \
+    do {                                                                                 \
+        cudaError_t e_ = (call);                                                         \
+        if (e_ != cudaSuccess)                                                           \
+            return set_err(c, STAGE_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+size_t round_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+stage_status dev_alloc(stage_ctx *c, size_t bytes, DevBuf &out)
+{
+    bytes = round_up(bytes ? bytes : 256, 256);
+    if (c->budget && c->used + bytes > c->budget)
+        return set_err(c, STAGE_ERR_ADMISSION, "allocation of %zu bytes exceeds the HBM budget (%llu of %llu used)",
+                       bytes, (unsigned long long)c->used, (unsigned long long)c->budget);
+    void *p = nullptr;
+    if (c->alloc) {
+        p = c->alloc(bytes, c->alloc_user);
+    } else {
+        cudaError_t e = cudaMalloc(&p, bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            p = nullptr;
+        }
+    }
+    if (!p) return set_err(c, STAGE_ERR_NO_MEMORY, "device allocation of %zu bytes failed", bytes);
+    out.p = p;
+    out.bytes = bytes;
+    c->used += bytes;
+    return STAGE_OK;
+}
+
+void dev_free(stage_ctx *c, DevBuf &b)
+{
+    if (!b.p) return;
+    if (c->free) c->free(b.p, b.bytes, c->alloc_user);
+    else cudaFree(b.p);
+    c->used -= b.bytes;
+    b.p = nullptr;
+    b.bytes = 0;
+}
+
+cudaEvent_t get_event(stage_ctx *c)
+{
+    if (!c->event_pool.empty()) {
+        cudaEvent_t e = c->event_pool.back();
+        c->event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// Launch through `f`, counting launches and (with STAGE_PROFILE) timing them.
+template <class F>
+cudaError_t timed(stage_ctx *c, const char *name, int n_kernels, F &&f)
+{
+    KernelStat &ks = c->stats[name];
+    ks.launches += n_kernels;
+    if (!(c->flags & STAGE_PROFILE)) return f();
+    cudaEvent_t e0 = get_event(c), e1 = get_event(c);
+    cudaEventRecord(e0, c->stream);
+    cudaError_t r = f();
+    cudaEventRecord(e1, c->stream);
+    ks.pending.emplace_back(e0, e1);
+    return r;
+}
+
+void fold_stats(stage_ctx *c)
+{
+    for (auto &kv : c->stats) {
+        for (auto &pr : kv.second.pending) {
+            float ms = 0.f;
+            if (cudaEventSynchronize(pr.second) == cudaSuccess &&
+                cudaEventElapsedTime(&ms, pr.first, pr.second) == cudaSuccess)
+                kv.second.ms += ms;
+            c->event_pool.push_back(pr.first);
+            c->event_pool.push_back(pr.second);
+        }
+        kv.second.pending.clear();
+    }
+}
+
+Instance *find_inst(stage_ctx *c, stage_inst h)
+{
+    auto it = c->insts.find(h);
+    return it == c->insts.end() ? nullptr : it->second;
+}
+
+void free_instance(stage_ctx *c, Instance *in)
+{
+    dev_free(c, in->mem_table);
+    dev_free(c, in->mem_coords);
+    dev_free(c, in->mem_ws);
+    dev_free(c, in->mem_scratch);
+    delete in;
+}
+
+stage_status ensure_scratch(stage_ctx *c, Instance *in, size_t bytes)
+{
+    if (in->mem_scratch.p && in->scratch_bytes >= bytes) return STAGE_OK;
+    dev_free(c, in->mem_scratch);
+    stage_status s = dev_alloc(c, bytes, in->mem_scratch);
+    if (s != STAGE_OK) return s;
+    in->scratch_bytes = in->mem_scratch.bytes;
+    return STAGE_OK;
+}
+
+// Sub-allocation of one workspace chunk (256-byte aligned pieces).
+struct Carver {
+    char *base;
+    size_t off = 0;
+    template <class T>
+    T *take(size_t n)
+    {
+        off = round_up(off, 256);
+        T *p = reinterpret_cast<T *>(base ? base + off : nullptr);
+        off += n * sizeof(T);
+        return p;
+    }
+};
+
+size_t carve_ws(char *base, int K, int B, int M_pad, int traj, TabuBuffers &tb)
+{
+    Carver cv{base};
+    tb.a = cv.take<int32_t>(M_pad);
+    tb.b = cv.take<int32_t>(M_pad);
+    tb.s1 = cv.take<int16_t>(M_pad);
+    tb.s2 = cv.take<int16_t>(M_pad);
+    tb.v0 = cv.take<unsigned long long>(2);
+    tb.loss_c = cv.take<unsigned long long>(K);
+    tb.loss_d = cv.take<unsigned long long>(K);
+    tb.gain_c = cv.take<int>(B);
+    tb.gain_d = cv.take<unsigned long long>(B);
+    tb.extra_c = cv.take<int>((size_t)K * B);
+    tb.extra_d = cv.take<unsigned long long>((size_t)K * B);
+    tb.open = cv.take<int32_t>(K);
+    tb.best_open = cv.take<int32_t>(K);
+    tb.cand = cv.take<int32_t>(B);
+    tb.expiry = cv.take<int32_t>(B);
+    tb.st = cv.take<TabuDevState>(1);
+    tb.partials = cv.take<MoveKey>(2 * kSelectBlocks);
+    tb.traj = cv.take<stage_move>(traj > 0 ? traj : 1);
+    return round_up(cv.off, 256);
+}
+
+stage_status ensure_ws(stage_ctx *c, Instance *in, int K, int traj)
+{
+    if (in->mem_ws.p && in->ws_K == K && in->ws_traj >= traj) return STAGE_OK;
+    dev_free(c, in->mem_ws);
+    TabuBuffers tb{};
+    size_t bytes = carve_ws(nullptr, K, in->B, in->M_pad, traj, tb);
+    stage_status s = dev_alloc(c, bytes, in->mem_ws);
+    if (s != STAGE_OK) return s;
+    carve_ws(static_cast<char *>(in->mem_ws.p), K, in->B, in->M_pad, traj, tb);
+    tb.K = K;
+    tb.B = in->B;
+    tb.M = in->M;
+    tb.M_pad = in->M_pad;
+    in->tb = tb;
+    in->ws_K = K;
+    in->ws_traj = traj;
+    return STAGE_OK;
+}
+
+stage_status check_placement(stage_ctx *c, Instance *in, const int32_t *open, int K)
+{
+    if (!open) return set_err(c, STAGE_ERR_INVALID_ARG, "placement pointer is NULL");
+    if (K < 1 || K > in->B || K > STAGE_MAX_K)
+        return set_err(c, STAGE_ERR_INVALID_ARG, "K=%d outside [1, min(B=%d, %d)]", K, in->B, STAGE_MAX_K);
+    std::vector<uint8_t> seen(in->B, 0);
+    for (int k = 0; k < K; k++) {
+        int o = open[k];
+        if (o < 0 || o >= in->B) return set_err(c, STAGE_ERR_INVALID_ARG, "base id %d out of range", o);
+        if (seen[o]) return set_err(c, STAGE_ERR_INVALID_ARG, "base %d appears twice in the placement", o);
+        if (!in->h_avail[o]) return set_err(c, STAGE_ERR_INVALID_ARG, "base %d is unavailable", o);
+        seen[o] = 1;
+    }
+    return STAGE_OK;
+}
+
+stage_status do_rank(stage_ctx *c, Instance *in, int K, int32_t *out_open, int64_t *out_rowsum)
+{
+    if (K < 1 || K > in->B || K > STAGE_MAX_K)
+        return set_err(c, STAGE_ERR_INVALID_ARG, "K=%d outside [1, min(B=%d, %d)]", K, in->B, STAGE_MAX_K);
+    if (K > in->n_avail)
+        return set_err(c, STAGE_ERR_INVALID_ARG, "K=%d exceeds the %d available bases", K, in->n_avail);
+    size_t need = round_up((size_t)in->B * 8, 256) + round_up((size_t)K * 4, 256);
+    stage_status s = ensure_scratch(c, in, need);
+    if (s != STAGE_OK) return s;
+    auto *S = static_cast<unsigned long long *>(in->mem_scratch.p);
+    auto *d_open = reinterpret_cast<int32_t *>(static_cast<char *>(in->mem_scratch.p) +
+                                               round_up((size_t)in->B * 8, 256));
+    CK(cudaMemsetAsync(S, 0, (size_t)in->B * 8, c->stream));
+    CK(timed(c, "rowsum", 1, [&] { return launch_rowsum(in->cost, in->B, in->M, in->M_pad, S, c->stream); }));
+    CK(timed(c, "topk", 1, [&] { return launch_topk(S, in->avail, in->B, K, d_open, c->stream); }));
+    CK(cudaMemcpyAsync(out_open, d_open, (size_t)K * 4, cudaMemcpyDeviceToHost, c->stream));
+    if (out_rowsum)
+        CK(cudaMemcpyAsync(out_rowsum, S, (size_t)in->B * 8, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return STAGE_OK;
+}
+
+// Set up the workspace for placement `open` (host ids), zero the accumulators,
+// and run the per-mission initialisation.  Returns the number of candidates.
+stage_status setup_search(stage_ctx *c, Instance *in, const int32_t *open, int K, int R,
+                          int traj_cap, int tenure, int accept_worsening, int t0,
+                          const int32_t *expiry_in, int *out_nC)
+{
+    stage_status s = ensure_ws(c, in, K, traj_cap);
+    if (s != STAGE_OK) return s;
+    TabuBuffers &tb = in->tb;
+    tb.R = R;
+    std::vector<uint8_t> is_open(in->B, 0);
+    for (int k = 0; k < K; k++) is_open[open[k]] = 1;
+    std::vector<int32_t> cand;
+    cand.reserve(in->B);
+    for (int b = 0; b < in->B; b++)
+        if (in->h_avail[b] && !is_open[b]) cand.push_back(b);
+    const int nC = (int)cand.size();
+    TabuDevState st{};
+    st.t = t0;
+    st.tenure = tenure;
+    st.accept_worsening = accept_worsening;
+    st.nC = nC;
+    st.traj_cap = traj_cap;
+    st.best_iter = -1;
+    std::vector<int32_t> expiry(in->B, 0);
+    if (expiry_in) std::copy(expiry_in, expiry_in + in->B, expiry.begin());
+    CK(cudaMemcpyAsync(tb.open, open, (size_t)K * 4, cudaMemcpyHostToDevice, c->stream));
+    if (nC) CK(cudaMemcpyAsync(tb.cand, cand.data(), (size_t)nC * 4, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(tb.expiry, expiry.data(), (size_t)in->B * 4, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(tb.st, &st, sizeof st, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemsetAsync(tb.v0, 0, 16, c->stream));
+    CK(cudaMemsetAsync(tb.loss_c, 0, (size_t)K * 8, c->stream));
+    CK(cudaMemsetAsync(tb.loss_d, 0, (size_t)K * 8, c->stream));
+    CK(cudaMemsetAsync(tb.gain_c, 0, (size_t)in->B * 4, c->stream));
+    CK(cudaMemsetAsync(tb.gain_d, 0, (size_t)in->B * 8, c->stream));
+    CK(cudaMemsetAsync(tb.extra_c, 0, (size_t)K * in->B * 4, c->stream));
+    CK(cudaMemsetAsync(tb.extra_d, 0, (size_t)K * in->B * 8, c->stream));
+    CK(timed(c, "init", 1, [&] { return launch_init(tb, in->cost, c->stream); }));
+    // the host copies above read stack vectors: finish them before returning
+    CK(cudaStreamSynchronize(c->stream));
+    *out_nC = nC;
+    return STAGE_OK;
+}
+
+stage_status run_tabu(stage_ctx *c, Instance *in, const stage_tabu_params *p,
+                      stage_tabu_result *res, stage_move *traj, int32_t *exp_a, int32_t *exp_b,
+                      int32_t *exp_b1, int32_t *exp_b2)
+{
+    if (!p) return set_err(c, STAGE_ERR_INVALID_ARG, "params is NULL");
+    const int K = p->K;
+    if (K < 1 || K > in->B || K > STAGE_MAX_K)
+        return set_err(c, STAGE_ERR_INVALID_ARG, "K=%d outside [1, min(B=%d, %d)]", K, in->B, STAGE_MAX_K);
+    if (K > in->n_avail)
+        return set_err(c, STAGE_ERR_INVALID_ARG, "K=%d exceeds the %d available bases", K, in->n_avail);
+    if (p->R < 0 || p->R == INT32_MAX)
+        return set_err(c, STAGE_ERR_OUT_OF_RANGE, "R=%d outside [0, INT32_MAX)", p->R);
+    if (p->iters < 0 || p->tenure < 0)
+        return set_err(c, STAGE_ERR_INVALID_ARG, "iters and tenure must be >= 0");
+    std::vector<int32_t> start(K);
+    const stage_tabu_state *rs = p->resume;
+    if (rs) {
+        if (!rs->open || !rs->best_open || !rs->tabu_expiry || rs->t < 0)
+            return set_err(c, STAGE_ERR_INVALID_ARG, "resume state is incomplete");
+        stage_status s = check_placement(c, in, rs->open, K);
+        if (s != STAGE_OK) return s;
+        s = check_placement(c, in, rs->best_open, K);
+        if (s != STAGE_OK) return s;
+        std::copy(rs->open, rs->open + K, start.begin());
+    } else if (p->start_open) {
+        stage_status s = check_placement(c, in, p->start_open, K);
+        if (s != STAGE_OK) return s;
+        std::copy(p->start_open, p->start_open + K, start.begin());
+    } else {
+        stage_status s = do_rank(c, in, K, start.data(), nullptr);
+        if (s != STAGE_OK) return s;
+    }
+    const int iters = p->iters;
+    const int t0 = rs ? rs->t : 0;
+    int nC = 0;
+    stage_status s = setup_search(c, in, start.data(), K, p->R, iters, p->tenure,
+                                  p->accept_worsening ? 1 : 0, t0, rs ? rs->tabu_expiry : nullptr, &nC);
+    if (s != STAGE_OK) return s;
+    TabuBuffers &tb = in->tb;
+    if (rs) {
+        TabuDevState st{};
+        CK(cudaMemcpy(&st, tb.st, sizeof st, cudaMemcpyDeviceToHost));
+        st.best_cov = rs->best_cov;
+        st.best_dist = rs->best_dist;
+        st.best_iter = rs->best_iter;
+        CK(cudaMemcpyAsync(tb.st, &st, sizeof st, cudaMemcpyHostToDevice, c->stream));
+        CK(cudaMemcpyAsync(tb.best_open, rs->best_open, (size_t)K * 4, cudaMemcpyHostToDevice, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+    }
+    CK(timed(c, "begin", 1, [&] { return launch_begin(tb, rs ? 1 : 0, c->stream); }));
+    volatile int *done_flag = static_cast<volatile int *>(c->pinned);
+    for (int it = 0; it < iters && nC > 0; it++) {
+        CK(timed(c, "swap_eval", 1, [&] { return launch_swap_eval(tb, in->cost, nC, 0, c->stream); }));
+        CK(timed(c, "select", 1, [&] { return launch_select(tb, c->stream); }));
+        CK(timed(c, "refresh", 1, [&] { return launch_refresh(tb, in->cost, c->stream); }));
+        // the improving-only rule usually stops early: poll the device flag now and then
+        if (!p->accept_worsening && (it & 31) == 31) {
+            CK(cudaMemcpyAsync(c->pinned, &tb.st->done, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+            CK(cudaStreamSynchronize(c->stream));
+            if (*done_flag) break;
+        }
+    }
+    if (exp_a) {
+        size_t per = round_up((size_t)in->M * 4, 256);
+        s = ensure_scratch(c, in, 4 * per);
+        if (s != STAGE_OK) return s;
+        char *sc = static_cast<char *>(in->mem_scratch.p);
+        auto *da = reinterpret_cast<int32_t *>(sc);
+        auto *db = reinterpret_cast<int32_t *>(sc + per);
+        auto *db1 = reinterpret_cast<int32_t *>(sc + 2 * per);
+        auto *db2 = reinterpret_cast<int32_t *>(sc + 3 * per);
+        CK(launch_export_best_two(tb, da, db, db1, db2, c->stream));
+        CK(cudaMemcpyAsync(exp_a, da, (size_t)in->M * 4, cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaMemcpyAsync(exp_b, db, (size_t)in->M * 4, cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaMemcpyAsync(exp_b1, db1, (size_t)in->M * 4, cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaMemcpyAsync(exp_b2, db2, (size_t)in->M * 4, cudaMemcpyDeviceToHost, c->stream));
+    }
+    TabuDevState st{};
+    std::vector<int32_t> fin(K), best(K), expiry(in->B);
+    CK(cudaMemcpyAsync(&st, tb.st, sizeof st, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(fin.data(), tb.open, (size_t)K * 4, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(best.data(), tb.best_open, (size_t)K * 4, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(expiry.data(), tb.expiry, (size_t)in->B * 4, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (st.err)
+        return set_err(c, STAGE_ERR_INTERNAL, "device self-check failed (code %d) at iteration %d", st.err, st.t);
+    const int n = std::min(st.n_moves, iters);
+    if (traj && n > 0)
+        CK(cudaMemcpy(traj, tb.traj, (size_t)n * sizeof(stage_move), cudaMemcpyDeviceToHost));
+    if (res) {
+        res->n_moves = st.n_moves;
+        res->best_iter = st.best_iter;
+        res->best_cov = st.best_cov;
+        res->best_dist = st.best_dist;
+        res->final_cov = st.cur_cov;
+        res->final_dist = st.cur_dist;
+        if (res->end_state) {
+            stage_tabu_state *es = res->end_state;
+            es->t = st.t;
+            es->best_iter = st.best_iter;
+            es->best_cov = st.best_cov;
+            es->best_dist = st.best_dist;
+            if (es->open) std::copy(fin.begin(), fin.end(), es->open);
+            if (es->best_open) std::copy(best.begin(), best.end(), es->best_open);
+            if (es->tabu_expiry) std::copy(expiry.begin(), expiry.end(), es->tabu_expiry);
+        }
+        std::sort(fin.begin(), fin.end());
+        std::sort(best.begin(), best.end());
+        if (res->best_open) std::copy(best.begin(), best.end(), res->best_open);
+        if (res->final_open) std::copy(fin.begin(), fin.end(), res->final_open);
+    }
+    return STAGE_OK;
+}
+
+}  // namespace
+
+// ============================================================== C ABI
+
+extern "C" {
+
+int32_t stage_version(void) { return 1 * 10000 + 0 * 100 + 0; }
+
+stage_status stage_create(const stage_config *cfg, stage_ctx **out)
+{
+    if (!out) return STAGE_ERR_INVALID_ARG;
+    *out = nullptr;
+    stage_config d{};
+    if (cfg) d = *cfg;
+    if ((d.alloc == nullptr) != (d.free == nullptr)) return STAGE_ERR_INVALID_ARG;
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || n <= 0) {
+        cudaGetLastError();
+        return STAGE_ERR_CUDA;
+    }
+    if (d.device < 0 || d.device >= n) return STAGE_ERR_INVALID_ARG;
+    if (cudaSetDevice(d.device) != cudaSuccess) return STAGE_ERR_CUDA;
+    if (kernels_init() != cudaSuccess) return STAGE_ERR_CUDA;
+    stage_ctx *c = new stage_ctx();
+    c->device = d.device;
+    c->flags = d.flags;
+    c->budget = d.hbm_budget_bytes;
+    c->max_slots = d.max_slots > 0 ? d.max_slots : 8;
+    c->spin_limit = d.spin_limit > 0 ? d.spin_limit : (1ll << 26);
+    c->alloc = d.alloc;
+    c->free = d.free;
+    c->alloc_user = d.alloc_user;
+    if (d.stream) {
+        c->stream = static_cast<cudaStream_t>(d.stream);
+    } else {
+        if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            delete c;
+            return STAGE_ERR_CUDA;
+        }
+        c->own_stream = true;
+    }
+    if (cudaMallocHost(&c->pinned, 256) != cudaSuccess) {
+        if (c->own_stream) cudaStreamDestroy(c->stream);
+        delete c;
+        return STAGE_ERR_CUDA;
+    }
+    *out = c;
+    return STAGE_OK;
+}
+
+stage_status stage_destroy(stage_ctx *c)
+{
+    if (!c) return STAGE_OK;
+    cudaSetDevice(c->device);
+    cudaStreamSynchronize(c->stream);
+    for (auto &kv : c->insts) free_instance(c, kv.second);
+    c->insts.clear();
+    fold_stats(c);
+    for (cudaEvent_t e : c->event_pool) cudaEventDestroy(e);
+    if (c->pinned) cudaFreeHost(c->pinned);
+    if (c->own_stream) cudaStreamDestroy(c->stream);
+    delete c;
+    return STAGE_OK;
+}
+
+stage_status stage_last_error(const stage_ctx *c, char *buf, size_t n)
+{
+    if (!c || !buf || n == 0) return STAGE_ERR_INVALID_ARG;
+    snprintf(buf, n, "%s", c->err.c_str());
+    return STAGE_OK;
+}
+
+stage_status stage_memory_used(const stage_ctx *c, uint64_t *out)
+{
+    if (!c || !out) return STAGE_ERR_INVALID_ARG;
+    *out = c->used;
+    return STAGE_OK;
+}
+
+stage_status stage_load_instance(stage_ctx *c, const stage_instance_desc *d, stage_inst *out)
+{
+    if (!c) return STAGE_ERR_INVALID_ARG;
+    Guard g(c);
+    if (!d || !out) return set_err(c, STAGE_ERR_INVALID_ARG, "desc or out is NULL");
+    if (!d->base_xy || !d->pick_xy || !d->drop_xy)
+        return set_err(c, STAGE_ERR_INVALID_ARG, "coordinate pointer is NULL");
+    if (d->B < 1 || d->M < 1) return set_err(c, STAGE_ERR_INVALID_ARG, "B and M must be >= 1");
+    if (d->B > STAGE_MAX_BASES) return set_err(c, STAGE_ERR_OUT_OF_RANGE, "B=%d > %d", d->B, STAGE_MAX_BASES);
+    if (d->M > STAGE_MAX_MISSIONS) return set_err(c, STAGE_ERR_OUT_OF_RANGE, "M=%d > %d", d->M, STAGE_MAX_MISSIONS);
+    CK(cudaSetDevice(c->device));
+    const bool on_dev = (d->flags & STAGE_DESC_DEVICE) != 0;
+    const int B = d->B, M = d->M;
+    const int M_pad = (int)round_up((size_t)M, kPadMissions);
+    std::vector<uint8_t> avail(B, 1);
+    if (on_dev) {
+        // device inputs: range check on the device, availability read back
+        if (d->base_available) CK(cudaMemcpy(avail.data(), d->base_available, B, cudaMemcpyDeviceToHost));
+        int *flag = static_cast<int *>(c->pinned) + 16;
+        *flag = 0;
+        DevBuf fb;
+        stage_status s0 = dev_alloc(c, 256, fb);
+        if (s0 != STAGE_OK) return s0;
+        int *dflag = static_cast<int *>(fb.p);
+        cudaError_t e0 = cudaMemsetAsync(dflag, 0, 4, c->stream);
+        if (e0 == cudaSuccess) e0 = launch_check_coords(d->base_xy, 2 * (size_t)B, dflag, c->stream);
+        if (e0 == cudaSuccess) e0 = launch_check_coords(d->pick_xy, 2 * (size_t)M, dflag, c->stream);
+        if (e0 == cudaSuccess) e0 = launch_check_coords(d->drop_xy, 2 * (size_t)M, dflag, c->stream);
+        if (e0 == cudaSuccess) e0 = cudaMemcpyAsync(flag, dflag, 4, cudaMemcpyDeviceToHost, c->stream);
+        if (e0 == cudaSuccess) e0 = cudaStreamSynchronize(c->stream);
+        dev_free(c, fb);
+        if (e0 != cudaSuccess) return set_err(c, STAGE_ERR_CUDA, "input check failed: %s", cudaGetErrorString(e0));
+        if (*flag) return set_err(c, STAGE_ERR_OUT_OF_RANGE, "a coordinate exceeds |%d| m", STAGE_MAX_COORD);
+    } else {
+        if (d->base_available) std::copy(d->base_available, d->base_available + B, avail.begin());
+        auto bad = [](const int32_t *v, size_t n) {
+            for (size_t k = 0; k < n; k++)
+                if (v[k] > STAGE_MAX_COORD || v[k] < -STAGE_MAX_COORD) return true;
+            return false;
+        };
+        if (bad(d->base_xy, 2 * (size_t)B) || bad(d->pick_xy, 2 * (size_t)M) || bad(d->drop_xy, 2 * (size_t)M))
+            return set_err(c, STAGE_ERR_OUT_OF_RANGE, "a coordinate exceeds |%d| m", STAGE_MAX_COORD);
+    }
+    for (auto &a : avail) a = a ? 1 : 0;
+    Instance *in = new Instance();
+    in->B = B; in->M = M; in->M_pad = M_pad;
+    in->h_avail = avail;
+    in->n_avail = (int)std::count(avail.begin(), avail.end(), (uint8_t)1);
+    size_t coords = round_up((size_t)B * 8, 256) + 2 * round_up((size_t)M * 8, 256) +
+                    round_up((size_t)M * 4, 256) + round_up((size_t)B, 256);
+    stage_status s = dev_alloc(c, coords, in->mem_coords);
+    if (s == STAGE_OK) s = dev_alloc(c, (size_t)B * M_pad * 4, in->mem_table);
+    if (s != STAGE_OK) {
+        free_instance(c, in);
+        return s;
+    }
+    Carver cv{static_cast<char *>(in->mem_coords.p)};
+    in->base = cv.take<int2>(B);
+    in->pick = cv.take<int2>(M);
+    in->drop = cv.take<int2>(M);
+    in->pd = cv.take<int32_t>(M);
+    in->avail = cv.take<uint8_t>(B);
+    in->cost = static_cast<int32_t *>(in->mem_table.p);
+    const cudaMemcpyKind kind = on_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    cudaError_t e = cudaMemcpyAsync(in->base, d->base_xy, (size_t)B * 8, kind, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(in->pick, d->pick_xy, (size_t)M * 8, kind, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(in->drop, d->drop_xy, (size_t)M * 8, kind, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(in->avail, in->h_avail.data(), B, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess)
+        e = timed(c, "table", 2, [&] {
+            return launch_table(B, M, M_pad, in->base, in->pick, in->drop, in->pd, in->cost, c->stream);
+        });
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        free_instance(c, in);
+        return set_err(c, STAGE_ERR_CUDA, "building the cost table failed: %s", cudaGetErrorString(e));
+    }
+    uint64_t id = c->next_id++;
+    c->insts[id] = in;
+    *out = id;
+    return STAGE_OK;
+}
+
+stage_status stage_unload_instance(stage_ctx *c, stage_inst h)
+{
+    if (!c) return STAGE_ERR_INVALID_ARG;
+    Guard g(c);
+    Instance *in = find_inst(c, h);
+    if (!in) return set_err(c, STAGE_ERR_NOT_FOUND, "unknown instance %llu", (unsigned long long)h);
+    cudaSetDevice(c->device);
+    cudaStreamSynchronize(c->stream);
+    c->insts.erase(h);
+    free_instance(c, in);
+    return STAGE_OK;
+}
+
+stage_status stage_rank_bases(stage_ctx *c, stage_inst h, int32_t K, int32_t *out_open, int64_t *out_rowsum)
+{
+    if (!c) return STAGE_ERR_INVALID_ARG;
+    Guard g(c);
+    Instance *in = find_inst(c, h);
+    if (!in) return set_err(c, STAGE_ERR_NOT_FOUND, "unknown instance %llu", (unsigned long long)h);
+    if (!out_open) return set_err(c, STAGE_ERR_INVALID_ARG, "out_open is NULL");
+    CK(cudaSetDevice(c->device));
+    return do_rank(c, in, K, out_open, out_rowsum);
+}
+
+stage_status stage_evaluate_placement(stage_ctx *c, stage_inst h, const int32_t *open, int32_t K,
+                                      int32_t R, int64_t *out_cov, int64_t *out_dist)
+{
+    if (!c) return STAGE_ERR_INVALID_ARG;
+    Guard g(c);
+    Instance *in = find_inst(c, h);
+    if (!in) return set_err(c, STAGE_ERR_NOT_FOUND, "unknown instance %llu", (unsigned long long)h);
+    if (!out_cov || !out_dist) return set_err(c, STAGE_ERR_INVALID_ARG, "output pointer is NULL");
+    stage_status s = check_placement(c, in, open, K);
+    if (s != STAGE_OK) return s;
+    if (R < 0 || R == INT32_MAX) return set_err(c, STAGE_ERR_OUT_OF_RANGE, "R=%d outside [0, INT32_MAX)", R);
+    CK(cudaSetDevice(c->device));
+    s = ensure_scratch(c, in, 256 + round_up((size_t)K * 4, 256));
+    if (s != STAGE_OK) return s;
+    auto *acc = static_cast<unsigned long long *>(in->mem_scratch.p);
+    auto *d_open = reinterpret_cast<int32_t *>(static_cast<char *>(in->mem_scratch.p) + 256);
+    unsigned long long h_acc[2];
+    CK(cudaMemcpyAsync(d_open, open, (size_t)K * 4, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemsetAsync(acc, 0, 16, c->stream));
+    CK(timed(c, "evaluate", 1, [&] { return launch_evaluate(in->cost, in->M, in->M_pad, d_open, K, R, acc, c->stream); }));
+    CK(cudaMemcpyAsync(h_acc, acc, 16, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    *out_cov = (int64_t)h_acc[0];
+    *out_dist = (int64_t)h_acc[1];
+    return STAGE_OK;
+}
+
+stage_status stage_evaluate_swaps(stage_ctx *c, stage_inst h, const int32_t *open, int32_t K,
+                                  int32_t R, int64_t *out_cov, int64_t *out_dist)
+{
+    if (!c) return STAGE_ERR_INVALID_ARG;
+    Guard g(c);
+    Instance *in = find_inst(c, h);
+    if (!in) return set_err(c, STAGE_ERR_NOT_FOUND, "unknown instance %llu", (unsigned long long)h);
+    if (!out_cov || !out_dist) return set_err(c, STAGE_ERR_INVALID_ARG, "output pointer is NULL");
+    stage_status s = check_placement(c, in, open, K);
+    if (s != STAGE_OK) return s;
+    if (R < 0 || R == INT32_MAX) return set_err(c, STAGE_ERR_OUT_OF_RANGE, "R=%d outside [0, INT32_MAX)", R);
+    CK(cudaSetDevice(c->device));
+    int nC = 0;
+    s = setup_search(c, in, open, K, R, 0, 0, 1, 0, nullptr, &nC);
+    if (s != STAGE_OK) return s;
+    const size_t n = (size_t)K * in->B;
+    s = ensure_scratch(c, in, 2 * round_up(n * 8, 256));
+    if (s != STAGE_OK) return s;
+    auto *oc = static_cast<long long *>(in->mem_scratch.p);
+    auto *od = reinterpret_cast<long long *>(static_cast<char *>(in->mem_scratch.p) + round_up(n * 8, 256));
+    CK(cudaMemsetAsync(oc, 0xff, n * 8, c->stream));
+    CK(cudaMemsetAsync(od, 0xff, n * 8, c->stream));
+    CK(timed(c, "swap_eval", 1, [&] { return launch_swap_eval(in->tb, in->cost, nC, 1, c->stream); }));
+    CK(launch_swap_table(in->tb, nC, oc, od, c->stream));
+    CK(cudaMemcpyAsync(out_cov, oc, n * 8, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(out_dist, od, n * 8, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return STAGE_OK;
+}
+
+stage_status stage_tabu_run(stage_ctx *c, stage_inst h, const stage_tabu_params *p,
+                            stage_tabu_result *res, stage_move *traj)
+{
+    if (!c) return STAGE_ERR_INVALID_ARG;
+    Guard g(c);
+    Instance *in = find_inst(c, h);
+    if (!in) return set_err(c, STAGE_ERR_NOT_FOUND, "unknown instance %llu", (unsigned long long)h);
+    CK(cudaSetDevice(c->device));
+    return run_tabu(c, in, p, res, traj, nullptr, nullptr, nullptr, nullptr);
+}
+
+stage_status stage_best_two(stage_ctx *c, stage_inst h, const int32_t *open, int32_t K, int32_t R,
+                            int32_t tabu_steps, int32_t tenure, int32_t *a, int32_t *b, int32_t *b1,
+                            int32_t *b2)
+{
+    if (!c) return STAGE_ERR_INVALID_ARG;
+    Guard g(c);
+    Instance *in = find_inst(c, h);
+    if (!in) return set_err(c, STAGE_ERR_NOT_FOUND, "unknown instance %llu", (unsigned long long)h);
+    if (!a || !b || !b1 || !b2) return set_err(c, STAGE_ERR_INVALID_ARG, "output pointer is NULL");
+    CK(cudaSetDevice(c->device));
+    stage_tabu_params p{};
+    p.K = K;
+    p.R = R;
+    p.iters = tabu_steps < 0 ? 0 : tabu_steps;
+    p.tenure = tenure;
+    p.accept_worsening = 1;
+    p.start_open = open;
+    return run_tabu(c, in, &p, nullptr, nullptr, a, b, b1, b2);
+}
+
+stage_status stage_read_table(stage_ctx *c, stage_inst h, int32_t b0, int32_t nb, int32_t m0,
+                              int32_t nm, int32_t *out)
+{
+    if (!c) return STAGE_ERR_INVALID_ARG;
+    Guard g(c);
+    Instance *in = find_inst(c, h);
+    if (!in) return set_err(c, STAGE_ERR_NOT_FOUND, "unknown instance %llu", (unsigned long long)h);
+    if (!out || b0 < 0 || nb < 0 || m0 < 0 || nm < 0 || b0 + nb > in->B || m0 + nm > in->M_pad)
+        return set_err(c, STAGE_ERR_INVALID_ARG, "table window out of range");
+    if (nb == 0 || nm == 0) return STAGE_OK;
+    CK(cudaSetDevice(c->device));
+    CK(cudaMemcpy2DAsync(out, (size_t)nm * 4, in->cost + (size_t)b0 * in->M_pad + m0,
+                         (size_t)in->M_pad * 4, (size_t)nm * 4, nb, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return STAGE_OK;
+}
+
+stage_status stage_kernel_stats(stage_ctx *c, const char *kernel, int64_t *launches, double *total_ms)
+{
+    if (!c || !kernel) return STAGE_ERR_INVALID_ARG;
+    Guard g(c);
+    cudaSetDevice(c->device);
+    fold_stats(c);
+    auto it = c->stats.find(kernel);
+    if (launches) *launches = it == c->stats.end() ? 0 : it->second.launches;
+    if (total_ms) *total_ms = it == c->stats.end() ? 0.0 : it->second.ms;
+    return STAGE_OK;
+}
+
+stage_status stage_reset_stats(stage_ctx *c)
+{
+    if (!c) return STAGE_ERR_INVALID_ARG;
+    Guard g(c);
+    cudaSetDevice(c->device);
+    fold_stats(c);
+    c->stats.clear();
+    return STAGE_OK;
+}
+
+}  // extern "C"

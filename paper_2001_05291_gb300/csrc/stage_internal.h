@@ -1,0 +1,98 @@
+// Internal declarations shared by the kernels and the host runtime of the
+// staging engine.  Nothing here is part of the C ABI (include/stage.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "stage.h"
+
+namespace stg {
+
+constexpr int32_t kInf = INT32_MAX;
+constexpr int kPadMissions = 64;     // table rows are padded to a multiple of 64 missions
+
+// Candidate-move key of the Tabu selection: more covered first, then less
+// distance, then lower closed base i, then lower opened base j.
+struct MoveKey {
+    long long cov;
+    long long dist;
+    int i, j;       // global base ids
+    int s, c;       // slot of i in the placement, position of j in the candidate list
+    int valid;      // 0 = no candidate
+    int tabu;       // the move is tabu (admitted by aspiration when chosen)
+};
+
+// Device-resident state of one Tabu run.  Written by the select kernel,
+// read by the evaluation and refresh kernels; the host reads it at the end.
+struct TabuDevState {
+    int t;                // iteration number of the next step
+    int n_moves;          // moves applied (trajectory length)
+    int done;             // 1 once the search has stopped
+    int err;              // nonzero: a self-check failed (see kErr*)
+    int tenure;
+    int accept_worsening;
+    int nC;               // closed available bases (candidate rows)
+    int traj_cap;         // trajectory capacity (entries)
+    long long cur_cov, cur_dist;     // F of the current placement
+    long long best_cov, best_dist;   // best so far
+    int best_iter;
+    int mv_s, mv_i, mv_j; // last applied move: slot, closed base, opened base
+    unsigned int ticket;  // last-block counter of the select kernel
+    int pad[3];
+};
+
+enum : int { kErrObjectiveMismatch = 1, kErrBadSlot = 2 };
+
+// Device buffers of one Tabu run (or one neighbourhood evaluation).
+struct TabuBuffers {
+    int K, B, M, M_pad, R;
+    // per mission (M_pad): best / second-best cost and their slots
+    int32_t *a, *b;
+    int16_t *s1, *s2;
+    // objective decomposition F(i, j) = V0 + gain[j] + loss[i] + extra[i][j]
+    unsigned long long *v0;      // [2]: covered, distance (two's complement)
+    unsigned long long *loss_c;  // [K]
+    unsigned long long *loss_d;  // [K]
+    int *gain_c;                 // [B]
+    unsigned long long *gain_d;  // [B]
+    int *extra_c;                // [K * B]
+    unsigned long long *extra_d; // [K * B]
+    // placement
+    int32_t *open;               // [K] slot -> base
+    int32_t *best_open;          // [K]
+    int32_t *cand;               // [B] closed available bases (first nC entries)
+    int32_t *expiry;             // [B]
+    TabuDevState *st;
+    MoveKey *partials;           // [2 * kSelectBlocks]
+    stage_move *traj;            // [traj_cap]
+};
+
+constexpr int kSelectBlocks = 148;
+constexpr int kSelectThreads = 256;
+
+// ----------------------------------------------------------------- launchers
+// Every launcher enqueues on `stream` and returns the launch error.
+cudaError_t launch_check_coords(const int32_t *v, size_t n, int *bad, cudaStream_t s);
+cudaError_t launch_table(int B, int M, int M_pad, const int2 *base, const int2 *pick,
+                         const int2 *drop, int32_t *pd_scratch, int32_t *cost, cudaStream_t s);
+cudaError_t launch_rowsum(const int32_t *cost, int B, int M, int M_pad, unsigned long long *S,
+                          cudaStream_t s);
+cudaError_t launch_topk(const unsigned long long *S, const uint8_t *avail, int B, int K,
+                        int32_t *open, cudaStream_t s);
+cudaError_t launch_evaluate(const int32_t *cost, int M, int M_pad, const int32_t *open, int K,
+                            int R, unsigned long long *out2, cudaStream_t s);
+cudaError_t launch_init(const TabuBuffers &w, const int32_t *cost, cudaStream_t s);
+cudaError_t launch_begin(const TabuBuffers &w, int resumed, cudaStream_t s);
+cudaError_t launch_swap_eval(const TabuBuffers &w, const int32_t *cost, int nC, int ignore_done,
+                             cudaStream_t s);
+cudaError_t launch_select(const TabuBuffers &w, cudaStream_t s);
+cudaError_t launch_refresh(const TabuBuffers &w, const int32_t *cost, cudaStream_t s);
+cudaError_t launch_export_best_two(const TabuBuffers &w, int32_t *a, int32_t *b, int32_t *b1,
+                                   int32_t *b2, cudaStream_t s);
+cudaError_t launch_swap_table(const TabuBuffers &w, int nC, long long *out_c, long long *out_d,
+                              cudaStream_t s);
+cudaError_t kernels_init();   // one-time function attributes (dynamic shared memory)
+
+}  // namespace stg

@@ -1,0 +1,373 @@
+"""Python binding of the staging engine's C ABI (include/stage.h), via ctypes.
+
+Argument marshalling only: every step of the method runs in the engine's CUDA
+kernels.  PyTorch supplies device memory (the caching allocator, through the
+engine's allocator hook) and the CUDA stream.  There is no CPU fallback: if the
+shared library is missing or no GPU is present, the calls raise.
+
+The module-level functions carry the C names (stage_create, stage_load_instance,
+stage_rank_bases, stage_evaluate_placement, stage_evaluate_swaps,
+stage_tabu_run, ...); ``Context`` wraps the same calls as methods.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_lib", "libstage.so")
+
+STAGE_OK, STAGE_PENDING = 0, 1
+ERRORS = {-1: "INVALID_ARG", -2: "OUT_OF_RANGE", -3: "NO_MEMORY", -4: "ADMISSION", -5: "TIMEOUT",
+          -6: "CUDA", -7: "INTERNAL", -8: "NOT_FOUND"}
+STAGE_THREADSAFE, STAGE_PROFILE = 1, 2
+STAGE_DESC_DEVICE = 1
+MOVE_FALLBACK, MOVE_ASPIRATION, MOVE_NEW_BEST = 1, 2, 4
+MAX_COORD, MAX_BASES, MAX_MISSIONS, MAX_K = 1 << 24, 65535, 1 << 24, 1024
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p)
+
+
+class StageConfig(C.Structure):
+    _fields_ = [("device", C.c_int32), ("flags", C.c_uint32), ("hbm_budget_bytes", C.c_uint64),
+                ("max_slots", C.c_int32), ("reserved0", C.c_int32), ("spin_limit", C.c_int64),
+                ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_user", C.c_void_p),
+                ("stream", C.c_void_p)]
+
+
+class StageInstanceDesc(C.Structure):
+    _fields_ = [("B", C.c_int32), ("M", C.c_int32), ("flags", C.c_uint32), ("reserved0", C.c_int32),
+                ("base_xy", C.c_void_p), ("pick_xy", C.c_void_p), ("drop_xy", C.c_void_p),
+                ("base_available", C.c_void_p)]
+
+
+class StageMove(C.Structure):
+    _fields_ = [("iter", C.c_int32), ("i", C.c_int32), ("j", C.c_int32), ("flags", C.c_int32),
+                ("cov", C.c_int64), ("dist", C.c_int64)]
+
+
+class StageTabuState(C.Structure):
+    _fields_ = [("t", C.c_int32), ("best_iter", C.c_int32), ("best_cov", C.c_int64),
+                ("best_dist", C.c_int64), ("open", C.c_void_p), ("best_open", C.c_void_p),
+                ("tabu_expiry", C.c_void_p)]
+
+
+class StageTabuParams(C.Structure):
+    _fields_ = [("K", C.c_int32), ("R", C.c_int32), ("iters", C.c_int32), ("tenure", C.c_int32),
+                ("accept_worsening", C.c_int32), ("reserved0", C.c_int32),
+                ("start_open", C.c_void_p), ("resume", C.POINTER(StageTabuState))]
+
+
+class StageTabuResult(C.Structure):
+    _fields_ = [("n_moves", C.c_int32), ("best_iter", C.c_int32), ("best_cov", C.c_int64),
+                ("best_dist", C.c_int64), ("final_cov", C.c_int64), ("final_dist", C.c_int64),
+                ("best_open", C.c_void_p), ("final_open", C.c_void_p),
+                ("end_state", C.POINTER(StageTabuState))]
+
+
+_lib = None
+
+
+def lib():
+    """The loaded engine library; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"the CUDA engine library is missing ({LIB_PATH}); "
+                               "build it with paper_2001_05291_gb300.build.build()")
+        L = C.CDLL(LIB_PATH)
+        i32, i64, p, st = C.c_int32, C.c_int64, C.c_void_p, C.c_int32
+        sig = {
+            "stage_create": ([C.POINTER(StageConfig), C.POINTER(p)], st),
+            "stage_destroy": ([p], st),
+            "stage_last_error": ([p, C.c_char_p, C.c_size_t], st),
+            "stage_version": ([], i32),
+            "stage_memory_used": ([p, C.POINTER(C.c_uint64)], st),
+            "stage_load_instance": ([p, C.POINTER(StageInstanceDesc), C.POINTER(C.c_uint64)], st),
+            "stage_unload_instance": ([p, C.c_uint64], st),
+            "stage_rank_bases": ([p, C.c_uint64, i32, p, p], st),
+            "stage_evaluate_placement": ([p, C.c_uint64, p, i32, i32, C.POINTER(i64), C.POINTER(i64)], st),
+            "stage_evaluate_swaps": ([p, C.c_uint64, p, i32, i32, p, p], st),
+            "stage_tabu_run": ([p, C.c_uint64, C.POINTER(StageTabuParams), C.POINTER(StageTabuResult), p], st),
+            "stage_kernel_stats": ([p, C.c_char_p, C.POINTER(i64), C.POINTER(C.c_double)], st),
+            "stage_reset_stats": ([p], st),
+            "stage_read_table": ([p, C.c_uint64, i32, i32, i32, i32, p], st),
+            "stage_best_two": ([p, C.c_uint64, p, i32, i32, i32, i32, p, p, p, p], st),
+        }
+        for name, (args, res) in sig.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = L
+    return _lib
+
+
+class StageError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{ERRORS.get(status, status)}: {message}")
+        self.status = status
+        self.message = message
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def _host_i32(a, n=None) -> np.ndarray:
+    out = np.ascontiguousarray(np.asarray(a), dtype=np.int32)
+    if n is not None and out.size != n:
+        raise ValueError(f"expected {n} values, got {out.size}")
+    return out
+
+
+@dataclass
+class TabuResult:
+    n_moves: int
+    best_open: np.ndarray
+    best_cov: int
+    best_dist: int
+    best_iter: int
+    final_open: np.ndarray
+    final_cov: int
+    final_dist: int
+    moves: list = field(default_factory=list)   # (iter, i, j, flags, cov, dist)
+    end_state: dict | None = None
+
+
+class _TorchAllocator:
+    """Backs the engine's device allocations with PyTorch's caching allocator."""
+
+    def __init__(self, device: int):
+        import torch
+        self.torch = torch
+        self.device = device
+        self.live = {}
+        self.alloc_cb = ALLOC_FN(self._alloc)
+        self.free_cb = FREE_FN(self._free)
+
+    def _alloc(self, nbytes, user):
+        try:
+            t = self.torch.empty(int(nbytes), dtype=self.torch.uint8, device=f"cuda:{self.device}")
+        except Exception:
+            return None
+        p = t.data_ptr()
+        self.live[p] = t
+        return p
+
+    def _free(self, ptr, nbytes, user):
+        self.live.pop(ptr, None)
+
+
+class Context:
+    """One engine context on one GPU (stage_create / stage_destroy)."""
+
+    def __init__(self, device: int = 0, profile: bool = False, threadsafe: bool = False,
+                 hbm_budget: int = 0, max_slots: int = 0, spin_limit: int = 0,
+                 torch_memory: bool = True, stream=None):
+        L = lib()
+        cfg = StageConfig()
+        cfg.device = device
+        cfg.flags = (STAGE_PROFILE if profile else 0) | (STAGE_THREADSAFE if threadsafe else 0)
+        cfg.hbm_budget_bytes = hbm_budget
+        cfg.max_slots = max_slots
+        cfg.spin_limit = spin_limit
+        self._alloc = None
+        self.torch_stream = None
+        if torch_memory:
+            import torch
+            if not torch.cuda.is_available():
+                raise StageError(-6, "no CUDA device")
+            self._alloc = _TorchAllocator(device)
+            cfg.alloc = self._alloc.alloc_cb
+            cfg.free = self._alloc.free_cb
+            self.torch_stream = stream if stream is not None else torch.cuda.Stream(device=device)
+            cfg.stream = self.torch_stream.cuda_stream
+        elif stream is not None:
+            cfg.stream = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+        h = C.c_void_p()
+        rc = L.stage_create(C.byref(cfg), C.byref(h))
+        if rc != STAGE_OK:
+            raise StageError(rc, "stage_create failed")
+        self._h = h
+        self._cfg = cfg
+        self.device = device
+
+    # ------------------------------------------------------------- plumbing
+    def _check(self, rc: int):
+        if rc < 0:
+            buf = C.create_string_buffer(512)
+            lib().stage_last_error(self._h, buf, 512)
+            raise StageError(rc, buf.value.decode(errors="replace"))
+        return rc
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().stage_destroy(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def memory_used(self) -> int:
+        v = C.c_uint64()
+        self._check(lib().stage_memory_used(self._h, C.byref(v)))
+        return int(v.value)
+
+    # ------------------------------------------------------------- instances
+    def load_instance(self, base_xy, pick_xy, drop_xy, base_available=None) -> int:
+        """stage_load_instance.  numpy arrays are copied from the host; CUDA
+        tensors (int32, contiguous) are read on the device."""
+        d = StageInstanceDesc()
+        keep = []
+        if _is_cuda_tensor(base_xy):
+            for t in (base_xy, pick_xy, drop_xy):
+                if not _is_cuda_tensor(t) or t.dtype.itemsize != 4 or not t.is_contiguous():
+                    raise ValueError("device inputs must all be contiguous int32 CUDA tensors")
+            d.B, d.M = base_xy.numel() // 2, pick_xy.numel() // 2
+            d.flags = STAGE_DESC_DEVICE
+            d.base_xy, d.pick_xy, d.drop_xy = base_xy.data_ptr(), pick_xy.data_ptr(), drop_xy.data_ptr()
+            if base_available is not None:
+                d.base_available = base_available.data_ptr()
+            keep = [base_xy, pick_xy, drop_xy, base_available]
+        else:
+            b, p, q = (_host_i32(x) for x in (base_xy, pick_xy, drop_xy))
+            d.B, d.M = b.size // 2, p.size // 2
+            d.base_xy, d.pick_xy, d.drop_xy = _ptr(b), _ptr(p), _ptr(q)
+            keep = [b, p, q]
+            if base_available is not None:
+                av = np.ascontiguousarray(base_available, dtype=np.uint8)
+                d.base_available = _ptr(av)
+                keep.append(av)
+        h = C.c_uint64()
+        self._check(lib().stage_load_instance(self._h, C.byref(d), C.byref(h)))
+        del keep
+        return int(h.value)
+
+    def unload_instance(self, inst: int):
+        self._check(lib().stage_unload_instance(self._h, inst))
+
+    def rank_bases(self, inst: int, K: int, B: int | None = None, rowsum: bool = True):
+        out = np.empty(K, dtype=np.int32)
+        rs = np.empty(B, dtype=np.int64) if (rowsum and B) else None
+        self._check(lib().stage_rank_bases(self._h, inst, K, _ptr(out), None if rs is None else _ptr(rs)))
+        return out, rs
+
+    def evaluate_placement(self, inst: int, open_, R: int):
+        o = _host_i32(open_)
+        cov, dist = C.c_int64(), C.c_int64()
+        self._check(lib().stage_evaluate_placement(self._h, inst, _ptr(o), o.size, R,
+                                                   C.byref(cov), C.byref(dist)))
+        return int(cov.value), int(dist.value)
+
+    def evaluate_swaps(self, inst: int, open_, R: int, B: int):
+        o = _host_i32(open_)
+        fc = np.empty(o.size * B, dtype=np.int64)
+        fd = np.empty(o.size * B, dtype=np.int64)
+        self._check(lib().stage_evaluate_swaps(self._h, inst, _ptr(o), o.size, R, _ptr(fc), _ptr(fd)))
+        return fc.reshape(o.size, B), fd.reshape(o.size, B)
+
+    def tabu_run(self, inst: int, K: int, R: int, iters: int, tenure: int, start_open=None,
+                 accept_worsening: bool = True, resume: dict | None = None, B: int | None = None,
+                 trajectory: bool = True, end_state: bool = False) -> TabuResult:
+        p = StageTabuParams()
+        p.K, p.R, p.iters, p.tenure = K, R, iters, tenure
+        p.accept_worsening = 1 if accept_worsening else 0
+        keep = []
+        if start_open is not None:
+            so = _host_i32(start_open, K)
+            keep.append(so)
+            p.start_open = _ptr(so)
+        if resume is not None:
+            rs = StageTabuState()
+            ro, rb, re_ = (_host_i32(resume[k]) for k in ("open", "best_open", "tabu_expiry"))
+            keep += [ro, rb, re_]
+            rs.t, rs.best_iter = resume["t"], resume["best_iter"]
+            rs.best_cov, rs.best_dist = resume["best_cov"], resume["best_dist"]
+            rs.open, rs.best_open, rs.tabu_expiry = _ptr(ro), _ptr(rb), _ptr(re_)
+            keep.append(rs)
+            p.resume = C.pointer(rs)
+        r = StageTabuResult()
+        best = np.empty(K, dtype=np.int32)
+        fin = np.empty(K, dtype=np.int32)
+        r.best_open, r.final_open = _ptr(best), _ptr(fin)
+        es = None
+        if end_state:
+            if B is None:
+                raise ValueError("end_state needs B")
+            es_open, es_best, es_exp = (np.empty(K, dtype=np.int32), np.empty(K, dtype=np.int32),
+                                        np.empty(B, dtype=np.int32))
+            es = StageTabuState()
+            es.open, es.best_open, es.tabu_expiry = _ptr(es_open), _ptr(es_best), _ptr(es_exp)
+            r.end_state = C.pointer(es)
+        traj = (StageMove * max(1, iters))() if trajectory else None
+        self._check(lib().stage_tabu_run(self._h, inst, C.byref(p), C.byref(r),
+                                         C.cast(traj, C.c_void_p) if traj is not None else None))
+        moves = []
+        if traj is not None:
+            moves = [(traj[k].iter, traj[k].i, traj[k].j, traj[k].flags, traj[k].cov, traj[k].dist)
+                     for k in range(r.n_moves)]
+        out = TabuResult(r.n_moves, best, r.best_cov, r.best_dist, r.best_iter, fin, r.final_cov,
+                         r.final_dist, moves)
+        if es is not None:
+            out.end_state = dict(t=es.t, best_iter=es.best_iter, best_cov=es.best_cov,
+                                 best_dist=es.best_dist, open=es_open, best_open=es_best,
+                                 tabu_expiry=es_exp)
+        return out
+
+    def best_two(self, inst: int, open_, R: int, M: int, tabu_steps: int = 0, tenure: int = 0):
+        o = _host_i32(open_)
+        a, b, b1, b2 = (np.empty(M, dtype=np.int32) for _ in range(4))
+        self._check(lib().stage_best_two(self._h, inst, _ptr(o), o.size, R, tabu_steps, tenure,
+                                         _ptr(a), _ptr(b), _ptr(b1), _ptr(b2)))
+        return a, b, b1, b2
+
+    def read_table(self, inst: int, b0: int, nb: int, m0: int, nm: int) -> np.ndarray:
+        out = np.empty((nb, nm), dtype=np.int32)
+        self._check(lib().stage_read_table(self._h, inst, b0, nb, m0, nm, _ptr(out)))
+        return out
+
+    def kernel_stats(self, name: str):
+        n, ms = C.c_int64(), C.c_double()
+        self._check(lib().stage_kernel_stats(self._h, name.encode(), C.byref(n), C.byref(ms)))
+        return int(n.value), float(ms.value)
+
+    def reset_stats(self):
+        self._check(lib().stage_reset_stats(self._h))
+
+
+def _is_cuda_tensor(x) -> bool:
+    return hasattr(x, "is_cuda") and bool(getattr(x, "is_cuda"))
+
+
+# C-named entry points (same calls as the Context methods)
+def stage_create(**kw) -> Context:
+    return Context(**kw)
+
+
+def stage_destroy(ctx: Context):
+    ctx.close()
+
+
+stage_load_instance = Context.load_instance
+stage_unload_instance = Context.unload_instance
+stage_rank_bases = Context.rank_bases
+stage_evaluate_placement = Context.evaluate_placement
+stage_evaluate_swaps = Context.evaluate_swaps
+stage_tabu_run = Context.tabu_run
+stage_best_two = Context.best_two
+stage_read_table = Context.read_table
+stage_kernel_stats = Context.kernel_stats
+stage_reset_stats = Context.reset_stats

@@ -1,0 +1,280 @@
+"""GPU path (through the C ABI) against the CPU oracle, element by element.
+
+All quantities are integers: the bar is bit-exact equality.  Sizes span several
+swap-evaluation tiles (16,384 missions per block, 8 candidate rows per block)
+with ragged tails, plus the edge cases of the method: K = 1, K = B - 1, no
+candidate base, unavailable bases, tiny M, M not a multiple of 4, the largest K.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2001_05291_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+INF = 2**31 - 1
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2001_05291_gb300 import build, stage
+    build.build()
+    c = stage.Context(device=0, profile=True)
+    yield c
+    c.close()
+
+
+def load(ctx, inst, avail=None):
+    return ctx.load_instance(inst.base_xy, inst.pick_xy, inst.drop_xy, avail)
+
+
+def small(seed, B, M, K, R=None, clustered=True):
+    lay = synth.Layout(400_000, 300_000, clustered=clustered, sigma_m=25_000.0)
+    R = R if R is not None else 350_000
+    return synth.make_instance(f"s{seed}", seed, B, 2 * B, M, K, R, 40, 4, lay)
+
+
+def oracle_table(inst, threads=8):
+    return oracle.cost_table(inst.base_xy, inst.pick_xy, inst.drop_xy, threads)
+
+
+# ---------------------------------------------------------------- cost table
+@pytest.mark.parametrize("name", ["tiny", "province"])
+def test_cost_table_full(ctx, name):
+    inst = synth.by_name(name)
+    h = load(ctx, inst)
+    M_pad = (inst.M + 63) // 64 * 64
+    got = ctx.read_table(h, 0, inst.B, 0, M_pad)
+    want = oracle_table(inst)
+    assert np.array_equal(got[:, : inst.M], want)
+    assert np.all(got[:, inst.M:] == INF)
+    ctx.unload_instance(h)
+
+
+@pytest.mark.parametrize("M", [1, 3, 63, 64, 65, 1000, 16385])
+def test_cost_table_ragged(ctx, M):
+    inst = small(11, 9, M, 3)
+    h = load(ctx, inst)
+    got = ctx.read_table(h, 0, inst.B, 0, M)
+    assert np.array_equal(got, oracle_table(inst))
+    ctx.unload_instance(h)
+
+
+def test_cost_table_extreme_coordinates(ctx):
+    lim = 2**24
+    base = np.array([[-lim, -lim], [lim, lim], [0, 0], [lim, -lim]], dtype=np.int32)
+    pick = np.array([[lim, lim], [-lim, lim], [3, 4], [-lim, -lim], [12345, -9876]], dtype=np.int32)
+    drop = np.array([[-lim, -lim], [lim, -lim], [6, 8], [lim, lim], [-lim, 0]], dtype=np.int32)
+    h = ctx.load_instance(base, pick, drop)
+    got = ctx.read_table(h, 0, 4, 0, 5)
+    assert np.array_equal(got, oracle.cost_table(base, pick, drop))
+    ctx.unload_instance(h)
+
+
+# ---------------------------------------------------------------- ranking / evaluation
+@pytest.mark.parametrize("name", ["tiny", "province"])
+def test_rank_and_evaluate(ctx, name):
+    inst = synth.by_name(name)
+    h = load(ctx, inst)
+    cost = oracle_table(inst)
+    for K in (1, inst.K, inst.B - 1):
+        got, rs = ctx.rank_bases(h, K, inst.B)
+        want, wrs = oracle.rank(cost, K)
+        assert np.array_equal(got, want) and np.array_equal(rs, wrs)
+    o = want[: inst.K]
+    for R in (0, inst.R // 2, inst.R, INF - 1):
+        assert ctx.evaluate_placement(h, o, R) == oracle.evaluate(cost, o, R)
+    ctx.unload_instance(h)
+
+
+def test_rank_with_unavailable_and_ties(ctx):
+    inst = small(21, 30, 500, 5)
+    # duplicate bases produce equal row sums: ties go to the lower index
+    base = np.concatenate([inst.base_xy, inst.base_xy[[3, 7, 7]]], axis=0)
+    avail = np.ones(base.shape[0], dtype=np.uint8)
+    avail[[0, 5, 31]] = 0
+    h = ctx.load_instance(base, inst.pick_xy, inst.drop_xy, avail)
+    cost = oracle.cost_table(base, inst.pick_xy, inst.drop_xy)
+    for K in (1, 4, 12, int(avail.sum())):
+        got, rs = ctx.rank_bases(h, K, base.shape[0])
+        want, wrs = oracle.rank(cost, K, avail)
+        assert np.array_equal(got, want) and np.array_equal(rs, wrs)
+    ctx.unload_instance(h)
+
+
+# ---------------------------------------------------------------- swap neighbourhood
+def check_swaps(ctx, h, cost, open_, R, avail=None):
+    B = cost.shape[0]
+    gc, gd = ctx.evaluate_swaps(h, open_, R, B)
+    wc, wd = oracle.swap_table(cost, open_, R, avail, nthreads=8)
+    for k, i in enumerate(open_):
+        assert np.array_equal(gc[k], wc[i]), f"covered, slot {k}"
+        assert np.array_equal(gd[k], wd[i]), f"distance, slot {k}"
+
+
+@pytest.mark.parametrize("B,M,K", [(20, 200, 5), (37, 16384 + 20, 7), (12, 33000, 1), (9, 5000, 8),
+                                   (60, 40000, 17)])
+def test_swap_neighbourhood(ctx, B, M, K):
+    inst = small(B * 7 + M, B, M, K)
+    h = load(ctx, inst)
+    cost = oracle_table(inst)
+    open_, _ = oracle.rank(cost, K)
+    for R in (inst.R, 150_000, INF - 1):
+        check_swaps(ctx, h, cost, open_, R)
+    ctx.unload_instance(h)
+
+
+def test_swap_neighbourhood_unavailable(ctx):
+    inst = small(5, 25, 3000, 6)
+    avail = np.ones(inst.B, dtype=np.uint8)
+    avail[[1, 2, 20]] = 0
+    h = load(ctx, inst, avail)
+    cost = oracle_table(inst)
+    open_, _ = oracle.rank(cost, 6, avail)
+    check_swaps(ctx, h, cost, open_, inst.R, avail)
+    ctx.unload_instance(h)
+
+
+def test_swap_neighbourhood_province(ctx):
+    inst = synth.province()
+    h = load(ctx, inst)
+    cost = oracle_table(inst)
+    open_, _ = oracle.rank(cost, inst.K)
+    check_swaps(ctx, h, cost, open_, inst.R)
+    ctx.unload_instance(h)
+
+
+# ---------------------------------------------------------------- incremental refresh
+def test_refresh_equals_full_recompute(ctx):
+    inst = small(77, 40, 9000, 6)
+    h = load(ctx, inst)
+    cost = oracle_table(inst)
+    start, _ = oracle.rank(cost, 6)
+    ref = oracle.tabu(cost, 6, inst.R, 30, 3, start_open=start)
+    O = list(start)
+    for steps in range(0, 31, 3):
+        if steps:
+            for (_, i, j, *_r) in ref.moves[steps - 3: steps]:
+                O = [j if x == i else x for x in O]
+        a, b, b1, b2 = ctx.best_two(h, start, inst.R, inst.M, tabu_steps=steps, tenure=3)
+        wa, wb, wb1, wb2 = oracle.best_two(cost, O)
+        assert np.array_equal(a, wa) and np.array_equal(b, wb)
+        assert np.array_equal(b1, wb1) and np.array_equal(b2, wb2)
+    ctx.unload_instance(h)
+
+
+# ---------------------------------------------------------------- Tabu trajectories
+def check_tabu(ctx, h, cost, K, R, iters, tenure, avail=None, **kw):
+    got = ctx.tabu_run(h, K, R, iters, tenure, **kw)
+    okw = {k: v for k, v in kw.items() if k in ("start_open", "accept_worsening")}
+    want = oracle.tabu(cost, K, R, iters, tenure, avail=avail, nthreads=8, **okw)
+    assert [tuple(m) for m in got.moves] == [tuple(m) for m in want.moves]
+    assert got.n_moves == len(want.moves)
+    assert (got.best_cov, got.best_dist, got.best_iter) == (want.best_cov, want.best_dist, want.best_iter)
+    assert np.array_equal(got.best_open, want.best_open)
+    assert np.array_equal(got.final_open, want.final_open)
+    assert (got.final_cov, got.final_dist) == (want.final_cov, want.final_dist)
+    return got
+
+
+def test_tabu_tiny_workload(ctx):
+    inst = synth.tiny()
+    h = load(ctx, inst)
+    cost = oracle_table(inst)
+    got = check_tabu(ctx, h, cost, inst.K, inst.R, inst.iters, inst.tenure)
+    _, oc, od, _ = oracle.bruteforce(cost, inst.K, inst.R)
+    assert (got.best_cov, got.best_dist) == (oc, od)
+    ctx.unload_instance(h)
+
+
+def test_tabu_province_workload(ctx):
+    inst = synth.province()
+    h = load(ctx, inst)
+    check_tabu(ctx, h, oracle_table(inst), inst.K, inst.R, inst.iters, inst.tenure)
+    ctx.unload_instance(h)
+
+
+@pytest.mark.parametrize("B,M,K,tenure,aw", [
+    (20, 200, 1, 2, True), (15, 777, 14, 3, True), (30, 20000, 5, 0, True), (30, 2051, 5, 6, False),
+    (48, 17000, 9, 4, True), (8, 3, 3, 2, True)])
+def test_tabu_edge_cases(ctx, B, M, K, tenure, aw):
+    inst = small(B + 1000 * K + M, B, M, K)
+    h = load(ctx, inst)
+    check_tabu(ctx, h, oracle_table(inst), K, inst.R, 60, tenure, accept_worsening=aw)
+    ctx.unload_instance(h)
+
+
+def test_tabu_no_candidates(ctx):
+    inst = small(3, 4, 100, 4)
+    h = load(ctx, inst)
+    got = ctx.tabu_run(h, 4, inst.R, 10, 2)
+    assert got.n_moves == 0 and got.moves == []
+    assert (got.best_cov, got.best_dist) == oracle.evaluate(oracle_table(inst), np.arange(4), inst.R)
+    ctx.unload_instance(h)
+
+
+def test_tabu_unavailable_and_start(ctx):
+    inst = small(9, 35, 6000, 6)
+    avail = np.ones(inst.B, dtype=np.uint8)
+    avail[[0, 4, 9, 30]] = 0
+    h = load(ctx, inst, avail)
+    cost = oracle_table(inst)
+    start = np.array([1, 2, 3, 5, 6, 7], dtype=np.int32)
+    check_tabu(ctx, h, cost, 6, inst.R, 50, 3, avail=avail, start_open=start)
+    check_tabu(ctx, h, cost, 6, inst.R, 50, 3, avail=avail)
+    ctx.unload_instance(h)
+
+
+def test_tabu_max_K(ctx):
+    inst = small(4, 1100, 700, 1024, R=200_000)
+    h = load(ctx, inst)
+    check_tabu(ctx, h, oracle_table(inst), 1024, inst.R, 8, 2)
+    ctx.unload_instance(h)
+
+
+def test_tabu_resume_equals_uninterrupted(ctx):
+    inst = small(31, 40, 8000, 7)
+    h = load(ctx, inst)
+    full = ctx.tabu_run(h, 7, inst.R, 40, 5)
+    first = ctx.tabu_run(h, 7, inst.R, 17, 5, end_state=True, B=inst.B)
+    second = ctx.tabu_run(h, 7, inst.R, 23, 5, resume=first.end_state)
+    assert first.moves + second.moves == full.moves
+    assert (second.best_cov, second.best_dist, second.best_iter) == (full.best_cov, full.best_dist, full.best_iter)
+    assert np.array_equal(second.best_open, full.best_open)
+    ctx.unload_instance(h)
+
+
+def test_errors_are_reported(ctx):
+    from paper_2001_05291_gb300 import stage
+    inst = small(1, 10, 50, 3)
+    h = load(ctx, inst)
+    with pytest.raises(stage.StageError) as e:
+        ctx.evaluate_placement(h, [1, 1, 2], inst.R)
+    assert e.value.status == -1 and "twice" in e.value.message
+    with pytest.raises(stage.StageError) as e:
+        ctx.tabu_run(h, 11, inst.R, 5, 1)
+    assert e.value.status == -1
+    with pytest.raises(stage.StageError) as e:
+        ctx.tabu_run(h, 3, INF, 5, 1)
+    assert e.value.status == -2
+    with pytest.raises(stage.StageError) as e:
+        ctx.load_instance(np.array([[2**24 + 1, 0]]), inst.pick_xy, inst.drop_xy)
+    assert e.value.status == -2
+    ctx.unload_instance(h)
+    with pytest.raises(stage.StageError) as e:
+        ctx.rank_bases(h, 3)
+    assert e.value.status == -8
+
+
+def test_device_resident_inputs(ctx):
+    import torch
+    inst = synth.tiny()
+    dev = [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in (inst.base_xy, inst.pick_xy, inst.drop_xy)]
+    h = ctx.load_instance(*dev)
+    got = ctx.read_table(h, 0, inst.B, 0, inst.M)
+    assert np.array_equal(got, oracle_table(inst))
+    ctx.unload_instance(h)
