@@ -254,6 +254,59 @@ STAGE_API stage_status stage_best_two(stage_ctx *ctx, stage_inst inst, const int
                             int32_t R, int32_t tabu_steps, int32_t tenure, int32_t *a,
                             int32_t *b, int32_t *b1, int32_t *b2);
 
+/* ------------------------------------------------------- allocation-free call */
+
+/* Every GPU that loads this library keeps a STAGE_NOALLOC_SCRATCH_MB MiB device
+ * array for stage_evaluate_swaps_noalloc until the process exits. */
+#define STAGE_NOALLOC_SCRATCH_MB 8
+#define STAGE_NOALLOC_MAX_BASES  8192
+
+/* stage_evaluate_swaps for callers that cannot allocate device memory.  The
+ * paper has no counterpart: this is a deployment variant of the swap
+ * neighbourhood evaluation, not a step of the method.
+ *
+ * Who needs it: a re-staging service embedded in a host application that owns
+ * all device memory through its own fixed pool, and dispatch loops that must
+ * not block on cudaMalloc (it can synchronise the device) or meet an
+ * out-of-memory failure halfway through a request.  The call makes no
+ * cudaMalloc, cudaFree, cudaMallocHost or other allocating call; the caller
+ * passes every input and output as DEVICE memory, and the scratch of the
+ * computation (per-mission best / second-best arrays, objective accumulators,
+ * candidate list) lives in a file-scope device array of fixed size.
+ *
+ *   cost             B x M_pad int32, row-major, one row per base (the layout
+ *                    stage_load_instance builds): columns M .. M_pad-1 must hold
+ *                    INT32_MAX, M_pad a multiple of 4, base 16-byte aligned
+ *   base_available   [B] uint8, or NULL for all available
+ *   open             [K] distinct available base ids in [0, B) (not checked on
+ *                    the host: they are device memory; an id outside [0, B)
+ *                    makes the kernels read outside the table)
+ *   R                range in metres, 0 <= R < INT32_MAX
+ *   out_cov/out_dist [K*B] int64: entry k*B + j = F(O - open[k] + j) for a
+ *                    closed available j, else -1, exactly as stage_evaluate_swaps
+ *   stream           cudaStream_t to enqueue on (NULL = the legacy default stream)
+ *   errbuf, errlen   optional host buffer that receives an error message
+ *
+ * Limits: B <= STAGE_NOALLOC_MAX_BASES, K <= STAGE_MAX_K, and the scratch,
+ * about 12 bytes per padded mission plus 12 bytes per (K, B) pair, must fit in
+ * STAGE_NOALLOC_SCRATCH_MB MiB (e.g. M_pad up to about 560,000 with K = 64,
+ * B = 2000).  Larger sizes return STAGE_ERR_OUT_OF_RANGE before any work runs.
+ * Other errors: STAGE_ERR_INVALID_ARG, STAGE_ERR_CUDA.
+ *
+ * The call only enqueues work on `stream`; the results are ready when the
+ * stream reaches that point.  All calls share the one scratch array, which
+ * keeps the last call's contents (each call clears what must start at zero):
+ * calls whose work overlaps on the GPU -- on different streams or from
+ * different threads -- race on it and corrupt each other's results, so
+ * serialise them.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress) with that device current; make that first
+ * call before any stream capture begins. */
+STAGE_API stage_status stage_evaluate_swaps_noalloc(const int32_t *cost, int32_t B, int32_t M,
+                                                    int32_t M_pad, const uint8_t *base_available,
+                                                    const int32_t *open, int32_t K, int32_t R,
+                                                    int64_t *out_cov, int64_t *out_dist,
+                                                    void *stream, char *errbuf, size_t errlen);
+
 #ifdef __cplusplus
 }
 #endif

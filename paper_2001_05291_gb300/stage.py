@@ -97,6 +97,8 @@ def lib():
             "stage_reset_stats": ([p], st),
             "stage_read_table": ([p, C.c_uint64, i32, i32, i32, i32, p], st),
             "stage_best_two": ([p, C.c_uint64, p, i32, i32, i32, i32, p, p, p, p], st),
+            "stage_evaluate_swaps_noalloc": ([p, i32, i32, i32, p, p, i32, i32, p, p, p, C.c_char_p,
+                                              C.c_size_t], st),
         }
         for name, (args, res) in sig.items():
             fn = getattr(L, name)
@@ -346,6 +348,31 @@ class Context:
 
     def reset_stats(self):
         self._check(lib().stage_reset_stats(self._h))
+
+
+def evaluate_swaps_noalloc(cost, M: int, open_, R: int, out_cov, out_dist, base_available=None,
+                           stream=None):
+    """stage_evaluate_swaps_noalloc on CUDA tensors: cost [B, M_pad] int32, open_ [K]
+    int32, out_cov / out_dist [K, B] int64, base_available [B] uint8 or None.  For
+    callers that cannot allocate device memory; see include/stage.h.  Only
+    enqueues on `stream` (a torch stream or raw handle; None = legacy default)."""
+    for t in (cost, open_, out_cov, out_dist):
+        if not _is_cuda_tensor(t) or not t.is_contiguous():
+            raise ValueError("inputs and outputs must be contiguous CUDA tensors")
+    B, M_pad = int(cost.shape[0]), int(cost.shape[1])
+    K = int(open_.numel())
+    if out_cov.numel() != K * B or out_dist.numel() != K * B:
+        raise ValueError("outputs must hold K * B values")
+    s = 0 if stream is None else (stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+    err = C.create_string_buffer(512)
+    rc = lib().stage_evaluate_swaps_noalloc(
+        cost.data_ptr(), B, M, M_pad, None if base_available is None else base_available.data_ptr(),
+        open_.data_ptr(), K, R, out_cov.data_ptr(), out_dist.data_ptr(), s, err, 512)
+    if rc != STAGE_OK:
+        raise StageError(rc, err.value.decode(errors="replace"))
+
+
+stage_evaluate_swaps_noalloc = evaluate_swaps_noalloc
 
 
 def _is_cuda_tensor(x) -> bool:
