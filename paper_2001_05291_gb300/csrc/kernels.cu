@@ -3,6 +3,8 @@
 // selection, incremental refresh).  Integer arithmetic throughout; float64 only
 // for the one square root per leg.
 #include <cuda_runtime.h>
+#include <climits>
+#include <cstdlib>
 #include <stdint.h>
 
 #include "stage_internal.h"
@@ -75,6 +77,218 @@ __device__ __forceinline__ bool key_better(const MoveKey &a, const MoveKey &b)
     if (a.dist != b.dist) return a.dist < b.dist;
     if (a.i != b.i) return a.i < b.i;
     return a.j < b.j;
+}
+
+// --------------------------------------------------------------------------
+// Mission order.  The table's columns are laid out in Morton order of the
+// missions' pickup/drop-off midpoints, so neighbouring columns hold missions
+// with similar cost rows: the rare "closer than the second-best" hits of the
+// swap pass bunch into few warps, and refresh rescans bunch into few blocks.
+// Every quantity the engine returns is an integer sum over missions, so the
+// column order changes no result.  The order is a stable LSD radix sort of a
+// 16-bit key (two 8-bit digits), ties kept in mission-index order.
+// --------------------------------------------------------------------------
+
+__global__ void k_mid_bbox(int M, const int2 *__restrict__ pick, const int2 *__restrict__ drop,
+                           int *__restrict__ bbox /* minx, miny, maxx, maxy */)
+{
+    int mnx = INT_MAX, mny = INT_MAX, mxx = INT_MIN, mxy = INT_MIN;
+    for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < M; m += gridDim.x * blockDim.x) {
+        const int2 p = pick[m], d = drop[m];
+        const int x = (p.x + d.x) >> 1, y = (p.y + d.y) >> 1;   // |sum| < 2^25
+        mnx = min(mnx, x); mny = min(mny, y); mxx = max(mxx, x); mxy = max(mxy, y);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        mnx = min(mnx, __shfl_xor_sync(0xffffffffu, mnx, o));
+        mny = min(mny, __shfl_xor_sync(0xffffffffu, mny, o));
+        mxx = max(mxx, __shfl_xor_sync(0xffffffffu, mxx, o));
+        mxy = max(mxy, __shfl_xor_sync(0xffffffffu, mxy, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMin(&bbox[0], mnx); atomicMin(&bbox[1], mny);
+        atomicMax(&bbox[2], mxx); atomicMax(&bbox[3], mxy);
+    }
+}
+
+__device__ __forceinline__ unsigned spread8(unsigned v)
+{
+    v &= 0xffu;
+    v = (v | (v << 4)) & 0x0f0fu;
+    v = (v | (v << 2)) & 0x3333u;
+    v = (v | (v << 1)) & 0x5555u;
+    return v;
+}
+
+__global__ void k_morton_keys(int M, const int2 *__restrict__ pick, const int2 *__restrict__ drop,
+                              const int *__restrict__ bbox, unsigned *__restrict__ key,
+                              int *__restrict__ val)
+{
+    const long long x0 = bbox[0], y0 = bbox[1];
+    const long long wx = (long long)bbox[2] - x0 + 1, wy = (long long)bbox[3] - y0 + 1;
+    for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < M; m += gridDim.x * blockDim.x) {
+        const int2 p = pick[m], d = drop[m];
+        const long long x = (p.x + d.x) >> 1, y = (p.y + d.y) >> 1;
+        const unsigned qx = (unsigned)(((x - x0) << 8) / wx), qy = (unsigned)(((y - y0) << 8) / wy);
+        key[m] = spread8(qx) | (spread8(qy) << 1);
+        val[m] = m;
+    }
+}
+
+constexpr int kSortThreads = 256;
+constexpr int kSortTile = kSortThreads * 16;
+
+__global__ void __launch_bounds__(kSortThreads) k_radix_hist(int n, const unsigned *__restrict__ key,
+                                                             int shift, int nBlocks, int *__restrict__ counts)
+{
+    __shared__ int h[256];
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    const int t0 = blockIdx.x * kSortTile;
+    for (int e = t0 + threadIdx.x; e < min(n, t0 + kSortTile); e += kSortThreads)
+        atomicAdd(&h[(key[e] >> shift) & 255u], 1);
+    __syncthreads();
+    counts[threadIdx.x * nBlocks + blockIdx.x] = h[threadIdx.x];
+}
+
+// Exclusive scan of `n` ints in place, one block of 1024 threads.
+__global__ void __launch_bounds__(1024) k_scan_exclusive(int n, int *__restrict__ v)
+{
+    __shared__ int part[1024];
+    const int per = (n + 1023) / 1024;
+    const int b = threadIdx.x * per, e = min(n, b + per);
+    int s = 0;
+    for (int k = b; k < e; k++) s += v[k];
+    part[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {
+        const int add = threadIdx.x >= o ? part[threadIdx.x - o] : 0;
+        __syncthreads();
+        part[threadIdx.x] += add;
+        __syncthreads();
+    }
+    int run = part[threadIdx.x] - s;
+    for (int k = b; k < e; k++) {
+        const int x = v[k];
+        v[k] = run;
+        run += x;
+    }
+}
+
+// Stable scatter: rounds of 256 elements in index order; within a round, lower
+// warps first and lower lanes first.
+__global__ void __launch_bounds__(kSortThreads) k_radix_scatter(int n, const unsigned *__restrict__ key_in,
+                                                                const int *__restrict__ val_in, int shift,
+                                                                int nBlocks, const int *__restrict__ offsets,
+                                                                unsigned *__restrict__ key_out,
+                                                                int *__restrict__ val_out)
+{
+    constexpr int W = kSortThreads / 32;
+    __shared__ int s_base[256], s_run[256];
+    __shared__ int s_wc[W][257];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    s_base[threadIdx.x] = offsets[threadIdx.x * nBlocks + blockIdx.x];
+    s_run[threadIdx.x] = 0;
+    for (int w = 0; w < W; w++) s_wc[w][threadIdx.x] = 0;
+    __syncthreads();
+    const int t0 = blockIdx.x * kSortTile;
+    for (int r = 0; r < kSortTile / kSortThreads; r++) {
+        const int e = t0 + r * kSortThreads + threadIdx.x;
+        const bool ok = e < n;
+        const unsigned k = ok ? key_in[e] : 0u;
+        const int d = ok ? (int)((k >> shift) & 255u) : 256;
+        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        const int rank = __popc(peers & ((1u << lane) - 1u));
+        if (ok && rank == 0) s_wc[wid][d] = __popc(peers);
+        __syncthreads();
+        if (ok) {
+            int prior = 0;
+            for (int w = 0; w < wid; w++) prior += s_wc[w][d];
+            const int pos = s_base[d] + s_run[d] + prior + rank;
+            key_out[pos] = k;
+            val_out[pos] = val_in[e];
+        }
+        __syncthreads();
+        int tot = 0;
+        for (int w = 0; w < W; w++) { tot += s_wc[w][threadIdx.x]; s_wc[w][threadIdx.x] = 0; }
+        s_run[threadIdx.x] += tot;
+        __syncthreads();
+    }
+}
+
+__global__ void k_apply_order(int M, const int *__restrict__ perm, const int2 *__restrict__ pick,
+                              const int2 *__restrict__ drop, int2 *__restrict__ pick_s,
+                              int2 *__restrict__ drop_s, int *__restrict__ inv)
+{
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < M; q += gridDim.x * blockDim.x) {
+        const int m = perm[q];
+        pick_s[q] = pick[m];
+        drop_s[q] = drop[m];
+        inv[m] = q;
+    }
+}
+
+size_t order_scratch_bytes(int M)
+{
+    const size_t nB = (size_t)(M + kSortTile - 1) / kSortTile;
+    return 4 * ((size_t)M * 4 + 256) + 256 * nB * 4 + 512;
+}
+
+cudaError_t launch_order(int M, const int2 *pick, const int2 *drop, void *scratch, int *perm,
+                         int *inv, int2 *pick_s, int2 *drop_s, cudaStream_t s)
+{
+    const int nB = (M + kSortTile - 1) / kSortTile;
+    auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    char *p = static_cast<char *>(scratch);
+    int *bbox = reinterpret_cast<int *>(p);                 p += 256;
+    unsigned *k0 = reinterpret_cast<unsigned *>(p);         p += al((size_t)M * 4);
+    unsigned *k1 = reinterpret_cast<unsigned *>(p);         p += al((size_t)M * 4);
+    int *v0 = reinterpret_cast<int *>(p);                   p += al((size_t)M * 4);
+    int *v1 = perm;                                          // second pass lands in perm
+    int *counts = reinterpret_cast<int *>(p);
+    const int init[4] = {INT_MAX, INT_MAX, INT_MIN, INT_MIN};
+    cudaError_t e = cudaMemcpyAsync(bbox, init, sizeof init, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return e;
+    int g = (M + 255) / 256;
+    if (g > 1024) g = 1024;
+    k_mid_bbox<<<g, 256, 0, s>>>(M, pick, drop, bbox);
+    k_morton_keys<<<g, 256, 0, s>>>(M, pick, drop, bbox, k0, v0);
+    // pass 1: low digit  (k0, v0) -> (k1, perm as temporary values)
+    k_radix_hist<<<nB, kSortThreads, 0, s>>>(M, k0, 0, nB, counts);
+    k_scan_exclusive<<<1, 1024, 0, s>>>(256 * nB, counts);
+    k_radix_scatter<<<nB, kSortThreads, 0, s>>>(M, k0, v0, 0, nB, counts, k1, v1);
+    // pass 2: high digit (k1, perm) -> (k0, v0); then v0 is the order
+    k_radix_hist<<<nB, kSortThreads, 0, s>>>(M, k1, 8, nB, counts);
+    k_scan_exclusive<<<1, 1024, 0, s>>>(256 * nB, counts);
+    k_radix_scatter<<<nB, kSortThreads, 0, s>>>(M, k1, v1, 8, nB, counts, k0, v0);
+    e = cudaMemcpyAsync(perm, v0, (size_t)M * 4, cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) return e;
+    k_apply_order<<<g, 256, 0, s>>>(M, perm, pick, drop, pick_s, drop_s, inv);
+    return cudaGetLastError();
+}
+
+// Table window in the caller's mission order: out[r][q] = cost[b0 + r][inv[m0 + q]].
+__global__ void k_gather_window(const int32_t *__restrict__ cost, int M, int M_pad, const int *__restrict__ inv,
+                                int b0, int nb, int m0, int nm, int32_t *__restrict__ out)
+{
+    const size_t n = (size_t)nb * nm;
+    for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n; q += (size_t)gridDim.x * blockDim.x) {
+        const int r = (int)(q / nm), c = (int)(q % nm);
+        const int m = m0 + c;
+        const int col = m < M ? inv[m] : m;    // pads keep their position
+        out[q] = cost[(size_t)(b0 + r) * M_pad + col];
+    }
+}
+
+cudaError_t launch_gather_window(const int32_t *cost, int M, int M_pad, const int *inv, int b0, int nb,
+                                 int m0, int nm, int32_t *out, cudaStream_t s)
+{
+    size_t n = (size_t)nb * nm;
+    size_t g = (n + 255) / 256;
+    if (g > 4096) g = 4096;
+    if (g == 0) return cudaSuccess;
+    k_gather_window<<<(int)g, 256, 0, s>>>(cost, M, M_pad, inv, b0, nb, m0, nm, out);
+    return cudaGetLastError();
 }
 
 // --------------------------------------------------------------------------
@@ -306,14 +520,23 @@ __device__ __forceinline__ void scan_best_two(const int32_t *__restrict__ cost, 
     int c1 = kInf, c2 = kInf, i1 = 0x7fffffff, i2 = 0x7fffffff;
     k1 = -1;
     k2 = -1;
-    for (int k = 0; k < K; k++) {
-        const int o = s_open[k];
-        const int c = __ldg(cost + (size_t)o * M_pad + m);
-        if (k1 < 0 || c < c1 || (c == c1 && o < i1)) {
-            k2 = k1; c2 = c1; i2 = i1;
-            k1 = k; c1 = c; i1 = o;
-        } else if (k2 < 0 || c < c2 || (c == c2 && o < i2)) {
-            k2 = k; c2 = c; i2 = o;
+    for (int k0 = 0; k0 < K; k0 += 8) {
+        int cv[8];
+#pragma unroll
+        for (int u = 0; u < 8; u++)
+            cv[u] = (k0 + u < K) ? __ldg(cost + (size_t)s_open[k0 + u] * M_pad + m) : kInf;
+#pragma unroll
+        for (int u = 0; u < 8; u++) {
+            const int k = k0 + u;
+            if (k >= K) break;
+            const int o = s_open[k];
+            const int c = cv[u];
+            if (k1 < 0 || c < c1 || (c == c1 && o < i1)) {
+                k2 = k1; c2 = c1; i2 = i1;
+                k1 = k; c1 = c; i1 = o;
+            } else if (k2 < 0 || c < c2 || (c == c2 && o < i2)) {
+                k2 = k; c2 = c; i2 = o;
+            }
         }
     }
     a = c1;
@@ -508,10 +731,523 @@ k_swap_eval(TabuBuffers w, const int32_t *__restrict__ cost, int ignore_done)
     }
 }
 
+// --------------------------------------------------------------------------
+// a4, streaming form for K <= kPipeMaxK.  Persistent: one block per SM.  Warp 8
+// (the producer) streams row segments of kPipeT missions (8 KB) of the
+// candidate rows into a kPipeStages-deep shared-memory ring with bulk async
+// copies (cp.async.bulk, completion counted on an mbarrier per stage); warps
+// 0-7 (consumers) read each segment from shared memory, 8 missions per thread,
+// with their missions' thresholds held in registers for the whole tile.
+//
+// Work item = (mission tile, chunk of kPipeJ candidate rows), enumerated
+// tile-major; block g takes a contiguous range of items, so it reloads the
+// thresholds only when its tile changes.  Accumulators for the item's rows
+// live in shared memory and are flushed with one global atomic per nonzero
+// entry after the item.
+//
+// Thresholds are clamped at R + 1: a' = min(a, R+1), b' = min(b, R+1).  This
+// drops exactly the elements whose contribution is zero (both sides of every
+// difference uncovered), and inside a hit x <= R, so f(x) = (1, x) and
+// f(max(x, a')) = (a' <= R) ? (1, max(x, a')) : (0, 0).
+// --------------------------------------------------------------------------
+
+constexpr int kPipeT = 2048;
+constexpr int kPipeJ = 8;
+constexpr int kPipeChunksPerUnit = 4;        // work unit = one tile x 32 candidate rows
+constexpr int kPipeStages = 16;
+constexpr int kPipeConsumerWarps = 8;
+constexpr int kPipeConsumers = kPipeConsumerWarps * 32;
+constexpr int kPipeThreads = kPipeConsumers + 32;
+constexpr int kPipeMaxK = 256;
+constexpr int kPipePerThread = kPipeT / kPipeConsumers;   // 8 missions
+constexpr long long kPipeSpinLimit = 1ll << 22;
+
+__device__ __forceinline__ unsigned smem_u32(const void *p)
+{
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long *bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(unsigned long long *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, unsigned parity)
+{
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait: false after kPipeSpinLimit polls.
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity)
+{
+    for (long long k = 0; k < kPipeSpinLimit; k++)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+// Bulk async copy global -> shared, completion counted on `bar`; the table is
+// streamed once per iteration, so it is marked evict-first in L2 and the
+// per-mission thresholds stay resident.
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, unsigned bytes, unsigned long long *bar,
+                                          unsigned long long policy)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(policy)
+        : "memory");
+}
+
+__device__ __forceinline__ unsigned long long evict_first_policy()
+{
+    unsigned long long p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+
+__device__ __forceinline__ void consumer_sync()
+{
+    asm volatile("bar.sync 1, %0;" ::"n"(kPipeConsumers) : "memory");
+}
+
+// Warp sum of per-lane int64 values that each fit in int32, over the lanes of
+// `mask` (all of which call this with the same mask): biased 16-bit halves,
+// three 32-bit reductions.
+__device__ __forceinline__ long long group_sum_small(unsigned mask, long long v)
+{
+    const unsigned u = (unsigned)(v + 2147483648ll);
+    const unsigned lo = __reduce_add_sync(mask, u & 0xffffu);
+    const unsigned hi = __reduce_add_sync(mask, u >> 16);
+    return ((long long)hi << 16) + (long long)lo - ((long long)__popc(mask) << 31);
+}
+
+// Stage kinds carried through the ring: a candidate row segment, the tile's
+// thresholds (a, b, best slot), or the end of the block's work.
+enum : int { kStageRow = 0, kStageAuxA = 1, kStageAuxB = 2, kStageAuxS = 3, kStageEnd = 4 };
+
+struct StageMeta {
+    int kind, tile, chunk, r;
+};
+
+constexpr int kPipeMaxCand = 8192;   // candidate list staged in shared memory
+
+__global__ void __launch_bounds__(kPipeThreads, 1)
+k_swap_stream(TabuBuffers w, const int32_t *__restrict__ cost, int ignore_done)
+{
+    TabuDevState *st = w.st;
+    if (!ignore_done && st->done) return;
+    extern __shared__ __align__(1024) unsigned char sm_pipe[];
+    int32_t *ring = reinterpret_cast<int32_t *>(sm_pipe);
+    unsigned long long *full = reinterpret_cast<unsigned long long *>(sm_pipe + (size_t)kPipeStages * kPipeT * 4);
+    unsigned long long *empty = full + kPipeStages;
+    StageMeta *meta = reinterpret_cast<StageMeta *>(empty + kPipeStages);
+    int *s_cand = reinterpret_cast<int *>(meta + kPipeStages);                                // [nC]
+    unsigned long long *ex_d = reinterpret_cast<unsigned long long *>(s_cand + kPipeMaxCand);  // [K * J]
+    int *ex_c = reinterpret_cast<int *>(ex_d + w.K * kPipeJ);                                 // [K * J]
+    unsigned long long *g_d = reinterpret_cast<unsigned long long *>(ex_c + w.K * kPipeJ + 2);
+    g_d = reinterpret_cast<unsigned long long *>((reinterpret_cast<uintptr_t>(g_d) + 7) & ~(uintptr_t)7);
+    int *g_c = reinterpret_cast<int *>(g_d + kPipeJ);
+
+    const int nC = st->nC;
+    const int K = w.K, B = w.B, R = w.R, M_pad = w.M_pad;
+    const int nTiles = (M_pad + kPipeT - 1) / kPipeT;
+    const int nChunks = (nC + kPipeJ - 1) / kPipeJ;
+    const int nGroups = (nChunks + kPipeChunksPerUnit - 1) / kPipeChunksPerUnit;
+    const unsigned nUnits = (unsigned)nTiles * (unsigned)nGroups;
+
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < kPipeStages; k++) {
+            mbar_init(&full[k], 1);
+            mbar_init(&empty[k], kPipeConsumerWarps);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    for (int k = threadIdx.x; k < nC; k += blockDim.x) s_cand[k] = w.cand[k];
+    for (int k = threadIdx.x; k < K * kPipeJ; k += blockDim.x) { ex_d[k] = 0; ex_c[k] = 0; }
+    if (threadIdx.x < kPipeJ) { g_c[threadIdx.x] = 0; g_d[threadIdx.x] = 0; }
+    __syncthreads();
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (warp == kPipeConsumerWarps) {
+        // ---------------------------------------------------------- producer
+        // Units (tile, group of 4 row chunks) come from a device counter, so a
+        // block that meets a dense hit region takes fewer units; the next unit
+        // is claimed while the current one is issued.  A tile change first
+        // sends the tile's thresholds through the ring.
+        if (lane != 0) return;
+        const unsigned long long policy = evict_first_policy();
+        long long seq = 0;
+        bool ok = true;
+        auto issue = [&](int kind, int tile, int ch, int r, const void *src, unsigned bytes) {
+            const int stg = (int)(seq % kPipeStages);
+            const unsigned par = (unsigned)(((seq / kPipeStages) + 1) & 1);
+            if (!mbar_wait(&empty[stg], par)) { ok = false; return; }
+            meta[stg] = StageMeta{kind, tile, ch, r};
+            seq++;
+            if (bytes == 0) {
+                mbar_arrive(&full[stg]);
+            } else {
+                mbar_arrive_expect_tx(&full[stg], bytes);
+                bulk_load(ring + (size_t)stg * kPipeT, src, bytes, &full[stg], policy);
+            }
+        };
+        unsigned u = atomicAdd(&st->work, 1u);
+        int prev_tile = -1;
+        while (ok && u < nUnits) {
+            const unsigned nxt = atomicAdd(&st->work, 1u);
+            const int tile = (int)(u / nGroups), g = (int)(u % nGroups);
+            const int m0 = tile * kPipeT;
+            const int nm = min(kPipeT, M_pad - m0);
+            if (tile != prev_tile) {
+                issue(kStageAuxA, tile, 0, 0, w.a + m0, (unsigned)nm * 4);
+                if (ok) issue(kStageAuxB, tile, 0, 0, w.b + m0, (unsigned)nm * 4);
+                if (ok) issue(kStageAuxS, tile, 0, 0, w.s1 + m0, (unsigned)nm * 2);
+                prev_tile = tile;
+            }
+            for (int ch = g * kPipeChunksPerUnit; ok && ch < (g + 1) * kPipeChunksPerUnit; ch++)
+                for (int r = 0; ok && r < kPipeJ; r++) {
+                    const int c = ch * kPipeJ + r;
+                    if (c >= nC) break;
+                    issue(kStageRow, tile, ch, r, cost + (size_t)s_cand[c] * M_pad + m0, (unsigned)nm * 4);
+                }
+            u = nxt;
+        }
+        if (ok) issue(kStageEnd, -1, 0, 0, nullptr, 0);
+        if (!ok) {
+            atomicOr(&st->err, kErrPipelineTimeout);
+            for (long long q = seq > kPipeStages ? seq - kPipeStages : 0; q < seq; q++)
+                mbar_wait(&full[q % kPipeStages], (unsigned)((q / kPipeStages) & 1));
+        }
+        return;
+    }
+
+    // -------------------------------------------------------------- consumers
+    const int ct = threadIdx.x;
+    long long seq = 0;
+    int cur_tile = -1, cur_chunk = -1;
+    int ap[kPipePerThread], bp[kPipePerThread], sl[kPipePerThread];
+#pragma unroll
+    for (int e = 0; e < kPipePerThread; e++) { ap[e] = 0; bp[e] = INT_MIN; sl[e] = 0; }
+    bool uni = false;          // all 8 of this thread's missions share one best slot
+    bool abort_local = false;
+    for (;;) {
+        const int stg = (int)(seq % kPipeStages);
+        const unsigned par = (unsigned)((seq / kPipeStages) & 1);
+        seq++;
+        StageMeta md{kStageEnd, -1, 0, 0};
+        int4 x0 = make_int4(0, 0, 0, 0), x1 = x0;
+        if (!abort_local) {
+            // all lanes wait; the outcome is made warp-uniform so that the
+            // warp-collective calls below always see all 32 lanes
+            const bool got = __all_sync(0xffffffffu, mbar_wait(&full[stg], par));
+            if (got) {
+                md = meta[stg];
+                const int4 *src = reinterpret_cast<const int4 *>(ring + (size_t)stg * kPipeT);
+                if (md.kind == kStageAuxS) {
+                    x0 = src[ct];                          // 8 x int16
+                } else if (md.kind != kStageEnd) {
+                    x0 = src[2 * ct];
+                    x1 = src[2 * ct + 1];
+                }
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&empty[stg]);
+            } else {
+                abort_local = true;
+                atomicOr(&st->err, kErrPipelineTimeout);
+            }
+        }
+        // every consumer warp sees the same stage sequence, so these decisions
+        // (and the barriers of the flush) are uniform across the consumer warps
+        if (abort_local) md.kind = kStageEnd;
+        const bool inside = md.tile * kPipeT + ct * kPipePerThread < M_pad;
+        if (md.kind == kStageAuxA) {
+            const int av[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
+#pragma unroll
+            for (int e = 0; e < 8; e++) ap[e] = min(av[e], R + 1);
+            continue;
+        }
+        if (md.kind == kStageAuxB) {
+            const int bv[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
+#pragma unroll
+            for (int e = 0; e < 8; e++) bp[e] = inside ? min(bv[e], R + 1) : INT_MIN;
+            continue;
+        }
+        if (md.kind == kStageAuxS) {
+            const unsigned sv[4] = {(unsigned)x0.x, (unsigned)x0.y, (unsigned)x0.z, (unsigned)x0.w};
+#pragma unroll
+            for (int e = 0; e < 8; e++) sl[e] = inside ? (int)(int16_t)((sv[e >> 1] >> ((e & 1) * 16)) & 0xffff) : 0;
+            uni = true;
+#pragma unroll
+            for (int e = 1; e < 8; e++) uni = uni && (sl[e] == sl[0]);
+            continue;
+        }
+        const bool new_item = md.kind == kStageEnd || md.tile != cur_tile || md.chunk != cur_chunk;
+        if (new_item && cur_tile >= 0) {
+            // flush the finished item's accumulators
+            consumer_sync();
+            const int jbase = cur_chunk * kPipeJ;
+            for (int k = ct; k < K * kPipeJ; k += kPipeConsumers) {
+                const int c = ex_c[k];
+                const unsigned long long d = ex_d[k];
+                if (c | (d != 0)) {
+                    const int r = k % kPipeJ, sidx = k / kPipeJ;
+                    const int j = s_cand[jbase + r];
+                    atomicAdd(&w.extra_c[(size_t)sidx * B + j], c);
+                    atomicAdd(&w.extra_d[(size_t)sidx * B + j], d);
+                    ex_c[k] = 0;
+                    ex_d[k] = 0;
+                }
+            }
+            if (ct < kPipeJ) {
+                const int c = g_c[ct];
+                const unsigned long long d = g_d[ct];
+                if (c | (d != 0)) {
+                    const int j = s_cand[jbase + ct];
+                    atomicAdd(&w.gain_c[j], c);
+                    atomicAdd(&w.gain_d[j], d);
+                    g_c[ct] = 0;
+                    g_d[ct] = 0;
+                }
+            }
+            consumer_sync();
+        }
+        if (md.kind == kStageEnd) break;
+        cur_tile = md.tile;
+        cur_chunk = md.chunk;
+        const int r = md.r;
+        const int xv[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
+        // per-lane sums of this row's contributions (each term is at most one
+        // cost in magnitude, so 8 of them fit in int32)
+        int ec = 0, gc = 0;
+        long long ed = 0, gd = 0;
+        if (xv[0] < bp[0] || xv[1] < bp[1] || xv[2] < bp[2] || xv[3] < bp[3] || xv[4] < bp[4] ||
+            xv[5] < bp[5] || xv[6] < bp[6] || xv[7] < bp[7]) {
+#pragma unroll
+            for (int e = 0; e < 8; e++) {
+                const int x = xv[e], a = ap[e], b = bp[e];
+                if (x < b) {
+                    const int ca = a <= R, cb = b <= R;
+                    const int dc = ca - cb;
+                    const long long dd = (ca ? (long long)max(x, a) : 0ll) - (cb ? (long long)b : 0ll);
+                    if (uni) {
+                        ec += dc;
+                        ed += dd;
+                    } else if (dc | (dd != 0)) {
+                        atomicAdd(&ex_c[sl[e] * kPipeJ + r], dc);
+                        atomicAdd(&ex_d[sl[e] * kPipeJ + r], (unsigned long long)dd);
+                    }
+                    if (x < a) {
+                        gc += 1 - ca;
+                        gd += (long long)x - (ca ? (long long)a : 0ll);
+                    }
+                }
+            }
+        }
+        // warp aggregation: one shared atomic per (slot, row) group of lanes
+        if (uni && (ec | (ed != 0))) {
+            const unsigned am = __activemask();
+            const unsigned peers = __match_any_sync(am, sl[0]);
+            const int sc = (int)__reduce_add_sync(peers, (unsigned)ec);
+            const long long sd = group_sum_small(peers, ed);
+            if (lane == __ffs(peers) - 1 && (sc | (sd != 0))) {
+                atomicAdd(&ex_c[sl[0] * kPipeJ + r], sc);
+                atomicAdd(&ex_d[sl[0] * kPipeJ + r], (unsigned long long)sd);
+            }
+        }
+        if (__any_sync(0xffffffffu, gc | (gd != 0))) {
+            const int sc = (int)__reduce_add_sync(0xffffffffu, (unsigned)gc);
+            const long long sd = group_sum_small(0xffffffffu, gd);
+            if (lane == 0 && (sc | (sd != 0))) {
+                atomicAdd(&g_c[r], sc);
+                atomicAdd(&g_d[r], (unsigned long long)sd);
+            }
+        }
+    }
+}
+
+// --------------------------------------------------------------------------
+// a4, direct form: non-persistent grid (the block scheduler balances dense and
+// sparse regions), 16 candidate rows per block, one thread per 4 consecutive
+// missions, 8 independent 16-byte table loads in flight per thread.  Same
+// clamped thresholds and warp-aggregated accumulation as the streaming form.
+// --------------------------------------------------------------------------
+constexpr int kDirJ = 16;
+constexpr int kDirThreads = 256;
+constexpr int kDirSegment = 16384;
+
+// Hit path of one row for one warp: called (out of line, so the kernel body
+// stays small enough for the instruction cache) only when some lane of the
+// warp has a hit in the row; every lane of the warp takes part.
+__device__ __noinline__ void dir_row(const int4 x, const int4 ap, const int4 bp, const int s0, const int s1,
+                                     const int s2, const int s3, const bool uni, const int r, const int R,
+                                     int *ex_c, unsigned long long *ex_d, int *g_c, unsigned long long *g_d,
+                                     const int lane)
+{
+    int ec = 0, gc = 0;
+    long long ed = 0, gd = 0;
+    if (x.x < bp.x || x.y < bp.y || x.z < bp.z || x.w < bp.w) {
+        const int xv[4] = {x.x, x.y, x.z, x.w}, av[4] = {ap.x, ap.y, ap.z, ap.w},
+                  bv[4] = {bp.x, bp.y, bp.z, bp.w}, sv[4] = {s0, s1, s2, s3};
+#pragma unroll
+        for (int e = 0; e < 4; e++) {
+            const int xe = xv[e], a = av[e], b = bv[e];
+            if (xe < b) {
+                const int ca = a <= R, cb = b <= R;
+                const int dc = ca - cb;
+                const long long dd = (ca ? (long long)max(xe, a) : 0ll) - (cb ? (long long)b : 0ll);
+                if (uni) {
+                    ec += dc;
+                    ed += dd;
+                } else if (dc | (dd != 0)) {
+                    atomicAdd(&ex_c[sv[e] * kDirJ + r], dc);
+                    atomicAdd(&ex_d[sv[e] * kDirJ + r], (unsigned long long)dd);
+                }
+                if (xe < a) {
+                    gc += 1 - ca;
+                    gd += (long long)xe - (ca ? (long long)a : 0ll);
+                }
+            }
+        }
+    }
+    if (uni && (ec | (ed != 0))) {
+        const unsigned am = __activemask();
+        const unsigned peers = __match_any_sync(am, s0);
+        const int sc = (int)__reduce_add_sync(peers, (unsigned)ec);
+        const long long sd = group_sum_small(peers, ed);
+        if (lane == __ffs(peers) - 1 && (sc | (sd != 0))) {
+            atomicAdd(&ex_c[s0 * kDirJ + r], sc);
+            atomicAdd(&ex_d[s0 * kDirJ + r], (unsigned long long)sd);
+        }
+    }
+    if (__any_sync(0xffffffffu, gc | (gd != 0))) {
+        const int sc = (int)__reduce_add_sync(0xffffffffu, (unsigned)gc);
+        const long long sd = group_sum_small(0xffffffffu, gd);
+        if (lane == 0 && (sc | (sd != 0))) {
+            atomicAdd(&g_c[r], sc);
+            atomicAdd(&g_d[r], (unsigned long long)sd);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kDirThreads, 2)
+k_swap_direct(TabuBuffers w, const int32_t *__restrict__ cost, int ignore_done)
+{
+    if (!ignore_done && w.st->done) return;
+    extern __shared__ unsigned long long sm_dir[];
+    const int K = w.K;
+    unsigned long long *ex_d = sm_dir;                               // [K * J]
+    int *ex_c = reinterpret_cast<int *>(ex_d + K * kDirJ);           // [K * J]
+    __shared__ int rows[kDirJ];
+    __shared__ int g_c[kDirJ];
+    __shared__ unsigned long long g_d[kDirJ];
+    const int nC = w.st->nC;
+    const int c0 = blockIdx.y * kDirJ;
+    for (int k = threadIdx.x; k < K * kDirJ; k += blockDim.x) { ex_d[k] = 0; ex_c[k] = 0; }
+    if (threadIdx.x < kDirJ) {
+        rows[threadIdx.x] = (c0 + threadIdx.x < nC) ? w.cand[c0 + threadIdx.x] : -1;
+        g_c[threadIdx.x] = 0;
+        g_d[threadIdx.x] = 0;
+    }
+    __syncthreads();
+    const int R = w.R, lane = threadIdx.x & 31;
+    const size_t M_pad = w.M_pad;
+    const int nrows = min(kDirJ, nC - c0);
+    const int m_begin = blockIdx.x * kDirSegment;
+    const int m_end = min(m_begin + kDirSegment, w.M_pad);
+    // Warp-uniform trip count: every lane of a warp runs every iteration (the
+    // warp-collective reductions in dir_row need all 32 lanes); lanes past the
+    // segment end see thresholds that nothing can beat.
+    const int wbase = 4 * (threadIdx.x & ~31);
+    for (int mw = m_begin + wbase; mw < m_end; mw += 4 * kDirThreads) {
+        const int m = mw + 4 * lane;
+        const bool act = m < m_end;
+        const int q = act ? (m >> 2) : 0;
+        int4 ap = __ldg(reinterpret_cast<const int4 *>(w.a) + q);
+        int4 bp = __ldg(reinterpret_cast<const int4 *>(w.b) + q);
+        const uint2 sp = __ldg(reinterpret_cast<const uint2 *>(w.s1) + q);
+        ap.x = min(ap.x, R + 1); ap.y = min(ap.y, R + 1); ap.z = min(ap.z, R + 1); ap.w = min(ap.w, R + 1);
+        bp.x = min(bp.x, R + 1); bp.y = min(bp.y, R + 1); bp.z = min(bp.z, R + 1); bp.w = min(bp.w, R + 1);
+        if (!act) bp = make_int4(INT_MIN, INT_MIN, INT_MIN, INT_MIN);
+        const int s0 = (int)(int16_t)(sp.x & 0xffff), s1 = (int)(int16_t)(sp.x >> 16);
+        const int s2 = (int)(int16_t)(sp.y & 0xffff), s3 = (int)(int16_t)(sp.y >> 16);
+        const bool uni = (s0 == s1) && (s1 == s2) && (s2 == s3);
+#pragma unroll 1
+        for (int h = 0; h < kDirJ; h += 8) {
+            int4 x[8];
+#pragma unroll
+            for (int r = 0; r < 8; r++)
+                x[r] = (act && h + r < nrows)
+                           ? __ldcs(reinterpret_cast<const int4 *>(cost + (size_t)rows[h + r] * M_pad) + q)
+                           : make_int4(INT_MAX, INT_MAX, INT_MAX, INT_MAX);
+#pragma unroll
+            for (int r = 0; r < 8; r++) {
+                const bool hit = x[r].x < bp.x || x[r].y < bp.y || x[r].z < bp.z || x[r].w < bp.w;
+                if (__any_sync(0xffffffffu, hit))
+                    dir_row(x[r], ap, bp, s0, s1, s2, s3, uni, h + r, R, ex_c, ex_d, g_c, g_d, lane);
+            }
+        }
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < K * kDirJ; k += blockDim.x) {
+        const int r = k % kDirJ, sidx = k / kDirJ;
+        const int j = rows[r];
+        if (j < 0) continue;
+        const int c = ex_c[k];
+        const unsigned long long d = ex_d[k];
+        if (c | (d != 0)) {
+            atomicAdd(&w.extra_c[(size_t)sidx * w.B + j], c);
+            atomicAdd(&w.extra_d[(size_t)sidx * w.B + j], d);
+        }
+    }
+    if (threadIdx.x < kDirJ && rows[threadIdx.x] >= 0) {
+        const int j = rows[threadIdx.x];
+        if (g_c[threadIdx.x]) atomicAdd(&w.gain_c[j], g_c[threadIdx.x]);
+        if (g_d[threadIdx.x]) atomicAdd(&w.gain_d[j], g_d[threadIdx.x]);
+    }
+}
+
+// Swap-evaluation variant: 0 = direct (default), 1 = streaming pipeline,
+// 2 = the plain per-element form.  STAGE_SWAP_VARIANT overrides (tuning).
+static int g_swap_variant = 0;
+
+static int g_num_sms = 0;
+
+size_t swap_stream_smem(int K)
+{
+    return (size_t)kPipeStages * kPipeT * 4 + 2 * kPipeStages * 8 + kPipeStages * sizeof(StageMeta) +
+           (size_t)kPipeMaxCand * 4 + (size_t)K * kPipeJ * 12 + 16 + kPipeJ * 12 + 64;
+}
+
 cudaError_t launch_swap_eval(const TabuBuffers &w, const int32_t *cost, int nC, int ignore_done,
                              cudaStream_t s)
 {
     if (nC <= 0) return cudaSuccess;
+    if (g_swap_variant == 0 && w.K <= kPipeMaxK) {
+        dim3 grid((w.M_pad + kDirSegment - 1) / kDirSegment, (nC + kDirJ - 1) / kDirJ);
+        k_swap_direct<<<grid, kDirThreads, (size_t)w.K * kDirJ * 12, s>>>(w, cost, ignore_done);
+        return cudaGetLastError();
+    }
+    if (g_swap_variant == 1 && w.K <= kPipeMaxK && nC <= kPipeMaxCand && g_num_sms > 0) {
+        k_swap_stream<<<g_num_sms, kPipeThreads, swap_stream_smem(w.K), s>>>(w, cost, ignore_done);
+        return cudaGetLastError();
+    }
     dim3 grid((w.M_pad + kSwapSegment - 1) / kSwapSegment, (nC + kSwapJ - 1) / kSwapJ);
     size_t sm = (size_t)w.K * kSwapJ * (8 + 4);
     k_swap_eval<kSwapJ><<<grid, kSwapThreads, sm, s>>>(w, cost, ignore_done);
@@ -640,6 +1376,7 @@ __global__ void __launch_bounds__(kSelectThreads) k_select(TabuBuffers w)
     block_best2<kSelectThreads>(adm, all, s_adm, s_all);
     if (threadIdx.x == 0) {
         st->ticket = 0;
+        st->work = 0;
         s_newbest = 0;
         if (!all.valid) {
             st->done = 1;                       // no closed available base
@@ -757,22 +1494,24 @@ cudaError_t launch_refresh(const TabuBuffers &w, const int32_t *cost, cudaStream
     return cudaGetLastError();
 }
 
-__global__ void k_export_best_two(TabuBuffers w, int32_t *__restrict__ a, int32_t *__restrict__ b,
-                                  int32_t *__restrict__ b1, int32_t *__restrict__ b2)
+// Per-mission arrays back in the caller's mission order (perm: column -> mission).
+__global__ void k_export_best_two(TabuBuffers w, const int *__restrict__ perm, int32_t *__restrict__ a,
+                                  int32_t *__restrict__ b, int32_t *__restrict__ b1, int32_t *__restrict__ b2)
 {
-    for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < w.M; m += gridDim.x * blockDim.x) {
-        a[m] = w.a[m];
-        b[m] = w.b[m];
-        const int k1 = w.s1[m], k2 = w.s2[m];
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < w.M; q += gridDim.x * blockDim.x) {
+        const int m = perm ? perm[q] : q;
+        a[m] = w.a[q];
+        b[m] = w.b[q];
+        const int k1 = w.s1[q], k2 = w.s2[q];
         b1[m] = w.open[k1];
         b2[m] = k2 >= 0 ? w.open[k2] : -1;
     }
 }
 
-cudaError_t launch_export_best_two(const TabuBuffers &w, int32_t *a, int32_t *b, int32_t *b1,
-                                   int32_t *b2, cudaStream_t s)
+cudaError_t launch_export_best_two(const TabuBuffers &w, const int *perm, int32_t *a, int32_t *b,
+                                   int32_t *b1, int32_t *b2, cudaStream_t s)
 {
-    k_export_best_two<<<grid_missions(w.M_pad), 256, 0, s>>>(w, a, b, b1, b2);
+    k_export_best_two<<<grid_missions(w.M_pad), 256, 0, s>>>(w, perm, a, b, b1, b2);
     return cudaGetLastError();
 }
 
@@ -781,6 +1520,18 @@ cudaError_t kernels_init()
     cudaError_t e = cudaFuncSetAttribute(k_swap_eval<kSwapJ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)(STAGE_MAX_K * kSwapJ * 12));
     if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_swap_stream, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)swap_stream_smem(kPipeMaxK));
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_swap_direct, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(kPipeMaxK * kDirJ * 12));
+    if (e != cudaSuccess) return e;
+    if (const char *v = getenv("STAGE_SWAP_VARIANT")) g_swap_variant = atoi(v);
+    int dev = 0, n = 0;
+    e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    g_num_sms = n;
     return cudaSuccess;
 }
 

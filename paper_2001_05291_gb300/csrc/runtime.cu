@@ -33,10 +33,13 @@ struct Instance {
     int B = 0, M = 0, M_pad = 0;
     int n_avail = 0;
     std::vector<uint8_t> h_avail;
-    DevBuf mem_coords;   // base, pick, drop, pd, avail
-    DevBuf mem_table;    // B x M_pad int32
-    int2 *base = nullptr, *pick = nullptr, *drop = nullptr;
+    DevBuf mem_coords;   // base, pick, drop (caller order and column order), pd, perm, inv, avail
+    DevBuf mem_table;    // B x M_pad int32, columns in mission order `perm`
+    int2 *base = nullptr, *pick = nullptr, *drop = nullptr;   // column order
+    int2 *pick_in = nullptr, *drop_in = nullptr;              // caller order
     int32_t *pd = nullptr;
+    int32_t *perm = nullptr;   // column -> caller's mission index
+    int32_t *inv = nullptr;    // caller's mission index -> column
     uint8_t *avail = nullptr;
     int32_t *cost = nullptr;
     // Tabu workspace, sized for ws_K / ws_traj
@@ -417,7 +420,7 @@ stage_status run_tabu(stage_ctx *c, Instance *in, const stage_tabu_params *p,
         auto *db = reinterpret_cast<int32_t *>(sc + per);
         auto *db1 = reinterpret_cast<int32_t *>(sc + 2 * per);
         auto *db2 = reinterpret_cast<int32_t *>(sc + 3 * per);
-        CK(launch_export_best_two(tb, da, db, db1, db2, c->stream));
+        CK(launch_export_best_two(tb, in->perm, da, db, db1, db2, c->stream));
         CK(cudaMemcpyAsync(exp_a, da, (size_t)in->M * 4, cudaMemcpyDeviceToHost, c->stream));
         CK(cudaMemcpyAsync(exp_b, db, (size_t)in->M * 4, cudaMemcpyDeviceToHost, c->stream));
         CK(cudaMemcpyAsync(exp_b1, db1, (size_t)in->M * 4, cudaMemcpyDeviceToHost, c->stream));
@@ -587,8 +590,8 @@ stage_status stage_load_instance(stage_ctx *c, const stage_instance_desc *d, sta
     in->B = B; in->M = M; in->M_pad = M_pad;
     in->h_avail = avail;
     in->n_avail = (int)std::count(avail.begin(), avail.end(), (uint8_t)1);
-    size_t coords = round_up((size_t)B * 8, 256) + 2 * round_up((size_t)M * 8, 256) +
-                    round_up((size_t)M * 4, 256) + round_up((size_t)B, 256);
+    size_t coords = round_up((size_t)B * 8, 256) + 4 * round_up((size_t)M * 8, 256) +
+                    3 * round_up((size_t)M * 4, 256) + round_up((size_t)B, 256);
     stage_status s = dev_alloc(c, coords, in->mem_coords);
     if (s == STAGE_OK) s = dev_alloc(c, (size_t)B * M_pad * 4, in->mem_table);
     if (s != STAGE_OK) {
@@ -599,19 +602,35 @@ stage_status stage_load_instance(stage_ctx *c, const stage_instance_desc *d, sta
     in->base = cv.take<int2>(B);
     in->pick = cv.take<int2>(M);
     in->drop = cv.take<int2>(M);
+    in->pick_in = cv.take<int2>(M);
+    in->drop_in = cv.take<int2>(M);
     in->pd = cv.take<int32_t>(M);
+    in->perm = cv.take<int32_t>(M);
+    in->inv = cv.take<int32_t>(M);
     in->avail = cv.take<uint8_t>(B);
     in->cost = static_cast<int32_t *>(in->mem_table.p);
+    DevBuf order_tmp;
+    s = dev_alloc(c, order_scratch_bytes(M), order_tmp);
+    if (s != STAGE_OK) {
+        free_instance(c, in);
+        return s;
+    }
     const cudaMemcpyKind kind = on_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     cudaError_t e = cudaMemcpyAsync(in->base, d->base_xy, (size_t)B * 8, kind, c->stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(in->pick, d->pick_xy, (size_t)M * 8, kind, c->stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(in->drop, d->drop_xy, (size_t)M * 8, kind, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(in->pick_in, d->pick_xy, (size_t)M * 8, kind, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(in->drop_in, d->drop_xy, (size_t)M * 8, kind, c->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(in->avail, in->h_avail.data(), B, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess)
+        e = timed(c, "order", 10, [&] {
+            return launch_order(M, in->pick_in, in->drop_in, order_tmp.p, in->perm, in->inv, in->pick,
+                                in->drop, c->stream);
+        });
     if (e == cudaSuccess)
         e = timed(c, "table", 2, [&] {
             return launch_table(B, M, M_pad, in->base, in->pick, in->drop, in->pd, in->cost, c->stream);
         });
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    dev_free(c, order_tmp);
     if (e != cudaSuccess) {
         free_instance(c, in);
         return set_err(c, STAGE_ERR_CUDA, "building the cost table failed: %s", cudaGetErrorString(e));
@@ -745,9 +764,17 @@ stage_status stage_read_table(stage_ctx *c, stage_inst h, int32_t b0, int32_t nb
         return set_err(c, STAGE_ERR_INVALID_ARG, "table window out of range");
     if (nb == 0 || nm == 0) return STAGE_OK;
     CK(cudaSetDevice(c->device));
-    CK(cudaMemcpy2DAsync(out, (size_t)nm * 4, in->cost + (size_t)b0 * in->M_pad + m0,
-                         (size_t)in->M_pad * 4, (size_t)nm * 4, nb, cudaMemcpyDeviceToHost, c->stream));
-    CK(cudaStreamSynchronize(c->stream));
+    // columns are stored in the engine's mission order: gather the window back
+    DevBuf win;
+    stage_status s = dev_alloc(c, (size_t)nb * nm * 4, win);
+    if (s != STAGE_OK) return s;
+    cudaError_t e = launch_gather_window(in->cost, in->M, in->M_pad, in->inv, b0, nb, m0, nm,
+                                         static_cast<int32_t *>(win.p), c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(out, win.p, (size_t)nb * nm * 4, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    dev_free(c, win);
+    if (e != cudaSuccess) return set_err(c, STAGE_ERR_CUDA, "reading the table failed: %s", cudaGetErrorString(e));
     return STAGE_OK;
 }
 

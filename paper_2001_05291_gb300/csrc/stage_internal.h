@@ -40,10 +40,11 @@ struct TabuDevState {
     int best_iter;
     int mv_s, mv_i, mv_j; // last applied move: slot, closed base, opened base
     unsigned int ticket;  // last-block counter of the select kernel
-    int pad[3];
+    unsigned int work;    // work-unit counter of the streaming swap pass
+    int pad[2];
 };
 
-enum : int { kErrObjectiveMismatch = 1, kErrBadSlot = 2 };
+enum : int { kErrObjectiveMismatch = 1, kErrBadSlot = 2, kErrPipelineTimeout = 4 };
 
 // Device buffers of one Tabu run (or one neighbourhood evaluation).
 struct TabuBuffers {
@@ -89,8 +90,14 @@ cudaError_t launch_swap_eval(const TabuBuffers &w, const int32_t *cost, int nC, 
                              cudaStream_t s);
 cudaError_t launch_select(const TabuBuffers &w, cudaStream_t s);
 cudaError_t launch_refresh(const TabuBuffers &w, const int32_t *cost, cudaStream_t s);
-cudaError_t launch_export_best_two(const TabuBuffers &w, int32_t *a, int32_t *b, int32_t *b1,
-                                   int32_t *b2, cudaStream_t s);
+cudaError_t launch_export_best_two(const TabuBuffers &w, const int *perm, int32_t *a, int32_t *b,
+                                   int32_t *b1, int32_t *b2, cudaStream_t s);
+// mission order (Morton order of pickup/drop-off midpoints) and readback in caller order
+size_t order_scratch_bytes(int M);
+cudaError_t launch_order(int M, const int2 *pick, const int2 *drop, void *scratch, int *perm, int *inv,
+                         int2 *pick_s, int2 *drop_s, cudaStream_t s);
+cudaError_t launch_gather_window(const int32_t *cost, int M, int M_pad, const int *inv, int b0, int nb,
+                                 int m0, int nm, int32_t *out, cudaStream_t s);
 cudaError_t launch_swap_table(const TabuBuffers &w, int nC, long long *out_c, long long *out_d,
                               cudaStream_t s);
 cudaError_t kernels_init();   // one-time function attributes (dynamic shared memory)
