@@ -29,7 +29,9 @@
  *     the exact integer is correctly rounded to the right ceiling.
  *   - Base ids are 0-based indices into the instance's base array.
  *   - All results are integers and are bit-identical run to run.
- *   - A context is not thread-safe unless created with STAGE_THREADSAFE.
+ *   - Calls on one context are serialised internally (the batch engine's
+ *     worker thread shares the context); STAGE_THREADSAFE is accepted for
+ *     compatibility and changes nothing.
  *   - The library never falls back to the CPU: without a CUDA device every
  *     call that needs one returns STAGE_ERR_CUDA.
  */
@@ -68,7 +70,7 @@ typedef int32_t stage_status;
 #define STAGE_MAX_K        1024
 
 /* context flags */
-#define STAGE_THREADSAFE   1u   /* serialise calls on the context with a mutex */
+#define STAGE_THREADSAFE   1u   /* accepted; calls are always serialised */
 #define STAGE_PROFILE      2u   /* time every kernel launch with CUDA events */
 
 /* instance descriptor flags */
@@ -227,6 +229,83 @@ STAGE_API stage_status stage_evaluate_swaps(stage_ctx *ctx, stage_inst inst, con
  * chosen move's). */
 STAGE_API stage_status stage_tabu_run(stage_ctx *ctx, stage_inst inst, const stage_tabu_params *params,
                             stage_tabu_result *result, stage_move *traj);
+
+/* ---------------------------------------------------------- updates, batches */
+
+/* Incremental change to a resident instance (re-staging after new demand,
+ * cancelled missions or closed bases).  All arrays are host memory.
+ *   add:      n_add missions appended; they receive the next mission ids
+ *             (M, M+1, ... in the order given)
+ *   remove:   n_remove mission ids withdrawn; their table columns become
+ *             INT32_MAX, so they are never covered and add nothing to any sum
+ *             or to the ranking; removing an id twice is a no-op
+ *   unavail:  bases that may no longer be opened
+ *   avail:    bases that may be opened again */
+typedef struct {
+    int32_t n_add;
+    int32_t n_remove;
+    int32_t n_unavail;
+    int32_t n_avail;
+    const int32_t *add_pick_xy;   /* [2*n_add] */
+    const int32_t *add_drop_xy;   /* [2*n_add] */
+    const int32_t *remove_ids;    /* [n_remove] */
+    const int32_t *unavail_ids;   /* [n_unavail] */
+    const int32_t *avail_ids;     /* [n_avail] */
+} stage_update;
+
+/* Apply an update to a resident instance (synchronous).  The table grows in
+ * place (with slack) when missions are added.
+ * Errors: STAGE_ERR_NOT_FOUND, STAGE_ERR_INVALID_ARG (id out of range),
+ * STAGE_ERR_OUT_OF_RANGE (coordinates, or more than STAGE_MAX_MISSIONS ids),
+ * STAGE_ERR_ADMISSION (the instance is in use by a batch request). */
+STAGE_API stage_status stage_update_instance(stage_ctx *ctx, stage_inst inst, const stage_update *update);
+
+/* One request of the batch engine: a Tabu search (Alg. 3, as stage_tabu_run)
+ * on a resident instance, or on an instance given by value that is loaded for
+ * this request only.  An optional update is applied to the resident instance
+ * first.  Requests on the same instance run one after the other, in
+ * submission order. */
+typedef struct {
+    stage_inst inst;                  /* resident instance, or 0 to use desc */
+    const stage_instance_desc *desc;  /* host descriptor, copied at submit (inst == 0) */
+    const stage_update *update;       /* applied to inst before the search, or NULL (copied at submit) */
+    stage_tabu_params params;         /* K <= 256; resume is not supported; start_open copied at submit */
+    stage_move *traj;                 /* [params.iters] host buffer or NULL; written before completion */
+    int32_t *best_open;               /* [K] host buffer or NULL; sorted ascending */
+    int32_t *final_open;              /* [K] host buffer or NULL; sorted ascending */
+} stage_request;
+
+typedef struct {
+    stage_status status;
+    int32_t n_moves;
+    int32_t best_iter;
+    int32_t reserved0;
+    int64_t best_cov;
+    int64_t best_dist;
+    int64_t final_cov;
+    int64_t final_dist;
+    int64_t t_submit_ns;   /* steady clock: submission, admission to a slot, completion */
+    int64_t t_start_ns;
+    int64_t t_end_ns;
+} stage_result;
+
+/* Queue n requests; tickets[k] identifies request k.  Returns at once: a
+ * worker thread admits requests into slots (at most cfg->max_slots at a time,
+ * and only while the context's HBM budget allows) and advances all active
+ * searches together, one grouped launch per kernel per step, replayed from a
+ * CUDA graph; finished searches leave and waiting ones join between replays.
+ * Each search computes exactly what stage_tabu_run computes alone.  The caller
+ * keeps traj / best_open / final_open valid until stage_poll reports the
+ * ticket done.  Errors: STAGE_ERR_INVALID_ARG (malformed request). */
+STAGE_API stage_status stage_batch_submit(stage_ctx *ctx, const stage_request *reqs, int32_t n,
+                                          uint64_t *tickets);
+
+/* Wait up to timeout_us microseconds (0: do not wait, < 0: no limit) for a
+ * ticket.  Returns STAGE_PENDING while it runs; otherwise fills *out, forgets
+ * the ticket and returns its status (STAGE_OK, or the request's error, e.g.
+ * STAGE_ERR_ADMISSION when it can never fit the HBM budget).
+ * STAGE_ERR_NOT_FOUND for an unknown or already collected ticket. */
+STAGE_API stage_status stage_poll(stage_ctx *ctx, uint64_t ticket, stage_result *out, int32_t timeout_us);
 
 /* ---------------------------------------------------------------- profiling */
 

@@ -68,7 +68,7 @@ def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
     if errors:
         raise RuntimeError("nvcc failed:\n" + "\n".join(errors))
     tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [nvcc, "-shared", "-o", tmp] + objs + ARCH + ["-Xcompiler", "-fPIC"]
+    cmd = [nvcc, "-shared", "-o", tmp] + objs + ARCH + ["-Xcompiler", "-fPIC", "-Xlinker", "--no-undefined"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, LIB)
     return LIB

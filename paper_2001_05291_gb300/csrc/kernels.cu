@@ -275,8 +275,8 @@ __global__ void k_gather_window(const int32_t *__restrict__ cost, int M, int M_p
     for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n; q += (size_t)gridDim.x * blockDim.x) {
         const int r = (int)(q / nm), c = (int)(q % nm);
         const int m = m0 + c;
-        const int col = m < M ? inv[m] : m;    // pads keep their position
-        out[q] = cost[(size_t)(b0 + r) * M_pad + col];
+        const int col = m < M ? inv[m] : m;    // pads keep their position; removed ids have none
+        out[q] = col >= 0 ? cost[(size_t)(b0 + r) * M_pad + col] : kInf;
     }
 }
 
@@ -362,6 +362,72 @@ cudaError_t launch_check_coords(const int32_t *v, size_t n, int *bad, cudaStream
     return cudaGetLastError();
 }
 
+// Instance updates: appended columns, removed columns, fills.
+__global__ void k_fill_i32(int32_t *__restrict__ p, size_t n, int32_t v)
+{
+    for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n; q += (size_t)gridDim.x * blockDim.x) p[q] = v;
+}
+
+cudaError_t launch_fill_i32(int32_t *p, size_t n, int32_t v, cudaStream_t s)
+{
+    size_t g = (n + 255) / 256;
+    if (g > 4096) g = 4096;
+    if (g == 0) return cudaSuccess;
+    k_fill_i32<<<(int)g, 256, 0, s>>>(p, n, v);
+    return cudaGetLastError();
+}
+
+// Costs of columns [col0, col0 + n) for every base (missions appended at the end).
+__global__ void k_table_columns(int B, int col0, int n, int M_pad, const int2 *__restrict__ base,
+                                const int2 *__restrict__ pick, const int2 *__restrict__ drop,
+                                int32_t *__restrict__ pd, int32_t *__restrict__ cost)
+{
+    const size_t total = (size_t)B * n;
+    for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < total; q += (size_t)gridDim.x * blockDim.x) {
+        const int b = (int)(q / n), col = col0 + (int)(q % n);
+        const int2 p = pick[col], d = drop[col], o = base[b];
+        const int l = leg_ceil(p.x, p.y, d.x, d.y);
+        if (b == 0) pd[col] = l;
+        cost[(size_t)b * M_pad + col] = leg_ceil(o.x, o.y, p.x, p.y) + l + leg_ceil(d.x, d.y, o.x, o.y);
+    }
+}
+
+cudaError_t launch_table_columns(int B, int col0, int n, int M_pad, const int2 *base, const int2 *pick,
+                                 const int2 *drop, int32_t *pd, int32_t *cost, cudaStream_t s)
+{
+    size_t total = (size_t)B * n;
+    size_t g = (total + 255) / 256;
+    if (g > 8192) g = 8192;
+    if (g == 0) return cudaSuccess;
+    k_table_columns<<<(int)g, 256, 0, s>>>(B, col0, n, M_pad, base, pick, drop, pd, cost);
+    return cudaGetLastError();
+}
+
+// Removed missions: their columns become INT32_MAX (one block per id).
+__global__ void k_tombstone(const int32_t *__restrict__ ids, int n, int32_t *__restrict__ inv,
+                            int32_t *__restrict__ perm, int32_t *__restrict__ cost, int B, int M_pad)
+{
+    for (int k = blockIdx.x; k < n; k += gridDim.x) {
+        const int col = inv[ids[k]];
+        __syncthreads();
+        if (col < 0) continue;
+        for (int b = threadIdx.x; b < B; b += blockDim.x) cost[(size_t)b * M_pad + col] = kInf;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            inv[ids[k]] = -1;
+            perm[col] = -1;
+        }
+    }
+}
+
+cudaError_t launch_tombstone(const int32_t *ids, int n, int32_t *inv, int32_t *perm, int32_t *cost, int B,
+                             int M_pad, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    k_tombstone<<<n < 1024 ? n : 1024, 256, 0, s>>>(ids, n, inv, perm, cost, B, M_pad);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_table(int B, int M, int M_pad, const int2 *base, const int2 *pick,
                          const int2 *drop, int32_t *pd, int32_t *cost, cudaStream_t s)
 {
@@ -391,8 +457,9 @@ __global__ void __launch_bounds__(256) k_row_sums(const int32_t *__restrict__ co
     for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n4; q += gridDim.x * blockDim.x) {
         int4 v = __ldcs(row + q);
         int m = q << 2;
-        acc += (m + 0 < M ? (long long)v.x : 0) + (m + 1 < M ? (long long)v.y : 0) +
-               (m + 2 < M ? (long long)v.z : 0) + (m + 3 < M ? (long long)v.w : 0);
+        // columns >= M are pads; INT32_MAX inside [0, M) marks a removed mission
+        acc += (m + 0 < M && v.x != kInf ? (long long)v.x : 0) + (m + 1 < M && v.y != kInf ? (long long)v.y : 0) +
+               (m + 2 < M && v.z != kInf ? (long long)v.z : 0) + (m + 3 < M && v.w != kInf ? (long long)v.w : 0);
     }
     block_sum2<256>(acc, dummy);
     if (threadIdx.x == 0) add_ull(&S[b], acc);
@@ -543,7 +610,9 @@ __device__ __forceinline__ void scan_best_two(const int32_t *__restrict__ cost, 
     b = c2;
 }
 
-__global__ void __launch_bounds__(256) k_init(TabuBuffers w, const int32_t *__restrict__ cost)
+// Body shared by the single-instance and the grouped launch: block `bid` of
+// `nb` blocks working on one instance.
+__device__ __forceinline__ void init_body(const TabuBuffers &w, const int32_t *__restrict__ cost, int bid, int nb)
 {
     extern __shared__ unsigned long long sm_init[];
     unsigned long long *s_ld = sm_init;
@@ -556,7 +625,7 @@ __global__ void __launch_bounds__(256) k_init(TabuBuffers w, const int32_t *__re
     }
     __syncthreads();
     long long v0c = 0, v0d = 0;
-    for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < w.M_pad; m += gridDim.x * blockDim.x) {
+    for (int m = bid * blockDim.x + threadIdx.x; m < w.M_pad; m += nb * blockDim.x) {
         if (m >= w.M) {
             w.a[m] = kInf; w.b[m] = kInf; w.s1[m] = 0; w.s2[m] = -1;
             continue;
@@ -568,6 +637,11 @@ __global__ void __launch_bounds__(256) k_init(TabuBuffers w, const int32_t *__re
     }
     __syncthreads();
     flush_loss_v0(w, s_lc, s_ld, v0c, v0d);
+}
+
+__global__ void __launch_bounds__(256) k_init(TabuBuffers w, const int32_t *__restrict__ cost)
+{
+    init_body(w, cost, blockIdx.x, gridDim.x);
 }
 
 static int grid_missions(int M_pad)
@@ -1085,8 +1159,10 @@ k_swap_stream(TabuBuffers w, const int32_t *__restrict__ cost, int ignore_done)
 // --------------------------------------------------------------------------
 // a4, direct form: non-persistent grid (the block scheduler balances dense and
 // sparse regions), 16 candidate rows per block, one thread per 4 consecutive
-// missions, 8 independent 16-byte table loads in flight per thread.  Same
-// clamped thresholds and warp-aggregated accumulation as the streaming form.
+// missions, 4 independent 16-byte table loads in flight per thread and 4
+// blocks (32 warps) per SM: the hit path's latency is hidden by other warps,
+// not by deeper per-thread batches.  Same clamped thresholds and
+// warp-aggregated accumulation as the streaming form.
 // --------------------------------------------------------------------------
 constexpr int kDirJ = 16;
 constexpr int kDirThreads = 256;
@@ -1146,10 +1222,9 @@ __device__ __noinline__ void dir_row(const int4 x, const int4 ap, const int4 bp,
     }
 }
 
-__global__ void __launch_bounds__(kDirThreads, 2)
-k_swap_direct(TabuBuffers w, const int32_t *__restrict__ cost, int ignore_done)
+__device__ __forceinline__ void swap_direct_body(const TabuBuffers &w, const int32_t *__restrict__ cost,
+                                                 int bx, int by)
 {
-    if (!ignore_done && w.st->done) return;
     extern __shared__ unsigned long long sm_dir[];
     const int K = w.K;
     unsigned long long *ex_d = sm_dir;                               // [K * J]
@@ -1158,7 +1233,7 @@ k_swap_direct(TabuBuffers w, const int32_t *__restrict__ cost, int ignore_done)
     __shared__ int g_c[kDirJ];
     __shared__ unsigned long long g_d[kDirJ];
     const int nC = w.st->nC;
-    const int c0 = blockIdx.y * kDirJ;
+    const int c0 = by * kDirJ;
     for (int k = threadIdx.x; k < K * kDirJ; k += blockDim.x) { ex_d[k] = 0; ex_c[k] = 0; }
     if (threadIdx.x < kDirJ) {
         rows[threadIdx.x] = (c0 + threadIdx.x < nC) ? w.cand[c0 + threadIdx.x] : -1;
@@ -1169,7 +1244,7 @@ k_swap_direct(TabuBuffers w, const int32_t *__restrict__ cost, int ignore_done)
     const int R = w.R, lane = threadIdx.x & 31;
     const size_t M_pad = w.M_pad;
     const int nrows = min(kDirJ, nC - c0);
-    const int m_begin = blockIdx.x * kDirSegment;
+    const int m_begin = bx * kDirSegment;
     const int m_end = min(m_begin + kDirSegment, w.M_pad);
     // Warp-uniform trip count: every lane of a warp runs every iteration (the
     // warp-collective reductions in dir_row need all 32 lanes); lanes past the
@@ -1189,15 +1264,15 @@ k_swap_direct(TabuBuffers w, const int32_t *__restrict__ cost, int ignore_done)
         const int s2 = (int)(int16_t)(sp.y & 0xffff), s3 = (int)(int16_t)(sp.y >> 16);
         const bool uni = (s0 == s1) && (s1 == s2) && (s2 == s3);
 #pragma unroll 1
-        for (int h = 0; h < kDirJ; h += 8) {
-            int4 x[8];
+        for (int h = 0; h < kDirJ; h += 4) {
+            int4 x[4];
 #pragma unroll
-            for (int r = 0; r < 8; r++)
+            for (int r = 0; r < 4; r++)
                 x[r] = (act && h + r < nrows)
                            ? __ldcs(reinterpret_cast<const int4 *>(cost + (size_t)rows[h + r] * M_pad) + q)
                            : make_int4(INT_MAX, INT_MAX, INT_MAX, INT_MAX);
 #pragma unroll
-            for (int r = 0; r < 8; r++) {
+            for (int r = 0; r < 4; r++) {
                 const bool hit = x[r].x < bp.x || x[r].y < bp.y || x[r].z < bp.z || x[r].w < bp.w;
                 if (__any_sync(0xffffffffu, hit))
                     dir_row(x[r], ap, bp, s0, s1, s2, s3, uni, h + r, R, ex_c, ex_d, g_c, g_d, lane);
@@ -1221,6 +1296,13 @@ k_swap_direct(TabuBuffers w, const int32_t *__restrict__ cost, int ignore_done)
         if (g_c[threadIdx.x]) atomicAdd(&w.gain_c[j], g_c[threadIdx.x]);
         if (g_d[threadIdx.x]) atomicAdd(&w.gain_d[j], g_d[threadIdx.x]);
     }
+}
+
+__global__ void __launch_bounds__(kDirThreads, 4)
+k_swap_direct(TabuBuffers w, const int32_t *__restrict__ cost, int ignore_done)
+{
+    if (!ignore_done && w.st->done) return;
+    swap_direct_body(w, cost, blockIdx.x, blockIdx.y);
 }
 
 // Swap-evaluation variant: 0 = direct (default), 1 = streaming pipeline,
@@ -1327,21 +1409,15 @@ __device__ __forceinline__ void block_best2(MoveKey &adm, MoveKey &all, MoveKey 
     all = s_all[0];
 }
 
-__global__ void __launch_bounds__(kSelectThreads) k_select(TabuBuffers w)
+// Scan candidates [q0, total) with stride `step` into the best admissible and
+// the best overall key.
+__device__ __forceinline__ void select_scan(const TabuBuffers &w, int t, int nC, long long v0c, long long v0d,
+                                            long long bc, long long bd, long long q0, long long step,
+                                            MoveKey &adm, MoveKey &all)
 {
-    TabuDevState *st = w.st;
-    if (st->done) return;
-    __shared__ MoveKey s_adm[kSelectThreads], s_all[kSelectThreads];
-    __shared__ int s_last, s_newbest;
-    const int t = st->t;
-    const int nC = st->nC;
     const int B = w.B;
-    const long long v0c = (long long)w.v0[0], v0d = (long long)w.v0[1];
-    const long long bc = st->best_cov, bd = st->best_dist;
-    MoveKey adm = invalid_key(), all = invalid_key();
     const long long total = (long long)w.K * nC;
-    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < total;
-         q += (long long)gridDim.x * blockDim.x) {
+    for (long long q = q0; q < total; q += step) {
         const int s = (int)(q / nC), c = (int)(q % nC);
         const int i = w.open[s], j = w.cand[c];
         const size_t sj = (size_t)s * B + j;
@@ -1353,28 +1429,19 @@ __global__ void __launch_bounds__(kSelectThreads) k_select(TabuBuffers w)
         if (key_better(k, all)) all = k;
         if ((!k.tabu || obj_better(k.cov, k.dist, bc, bd)) && key_better(k, adm)) adm = k;
     }
-    block_best2<kSelectThreads>(adm, all, s_adm, s_all);
+}
+
+// Apply the chosen move (called by every thread of one block, with the block's
+// final keys): tabu expiries, best so far, trajectory, and clearing V0 / loss
+// for the refresh.  Also stops the search when there is no candidate, when the
+// improving-only rule says so, or when the iteration budget is used up.
+__device__ __forceinline__ void select_apply(const TabuBuffers &w, const MoveKey &adm, const MoveKey &all,
+                                             long long v0c, long long v0d)
+{
+    TabuDevState *st = w.st;
+    __shared__ int s_newbest;
     if (threadIdx.x == 0) {
-        w.partials[2 * blockIdx.x] = adm;
-        w.partials[2 * blockIdx.x + 1] = all;
-        __threadfence();
-        const unsigned int ticket = atomicAdd(&st->ticket, 1u);
-        s_last = (ticket == gridDim.x - 1);
-    }
-    __syncthreads();
-    if (!s_last) return;
-    __threadfence();
-    adm = invalid_key();
-    all = invalid_key();
-    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
-        MoveKey pa = load_key_cg(&w.partials[2 * b]);
-        MoveKey px = load_key_cg(&w.partials[2 * b + 1]);
-        if (key_better(pa, adm)) adm = pa;
-        if (key_better(px, all)) all = px;
-    }
-    __syncthreads();
-    block_best2<kSelectThreads>(adm, all, s_adm, s_all);
-    if (threadIdx.x == 0) {
+        const int t = st->t;
         st->ticket = 0;
         st->work = 0;
         s_newbest = 0;
@@ -1425,6 +1492,43 @@ __global__ void __launch_bounds__(kSelectThreads) k_select(TabuBuffers w)
     }
 }
 
+__global__ void __launch_bounds__(kSelectThreads) k_select(TabuBuffers w)
+{
+    TabuDevState *st = w.st;
+    if (st->done || st->t >= st->t_end) return;
+    __shared__ MoveKey s_adm[kSelectThreads], s_all[kSelectThreads];
+    __shared__ int s_last;
+    const int t = st->t;
+    const int nC = st->nC;
+    const long long v0c = (long long)w.v0[0], v0d = (long long)w.v0[1];
+    const long long bc = st->best_cov, bd = st->best_dist;
+    MoveKey adm = invalid_key(), all = invalid_key();
+    select_scan(w, t, nC, v0c, v0d, bc, bd, blockIdx.x * (long long)blockDim.x + threadIdx.x,
+                (long long)gridDim.x * blockDim.x, adm, all);
+    block_best2<kSelectThreads>(adm, all, s_adm, s_all);
+    if (threadIdx.x == 0) {
+        w.partials[2 * blockIdx.x] = adm;
+        w.partials[2 * blockIdx.x + 1] = all;
+        __threadfence();
+        const unsigned int ticket = atomicAdd(&st->ticket, 1u);
+        s_last = (ticket == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    adm = invalid_key();
+    all = invalid_key();
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
+        MoveKey pa = load_key_cg(&w.partials[2 * b]);
+        MoveKey px = load_key_cg(&w.partials[2 * b + 1]);
+        if (key_better(pa, adm)) adm = pa;
+        if (key_better(px, all)) all = px;
+    }
+    __syncthreads();
+    block_best2<kSelectThreads>(adm, all, s_adm, s_all);
+    select_apply(w, adm, all, v0c, v0d);
+}
+
 cudaError_t launch_select(const TabuBuffers &w, cudaStream_t s)
 {
     k_select<<<kSelectBlocks, kSelectThreads, 0, s>>>(w);
@@ -1438,7 +1542,8 @@ cudaError_t launch_select(const TabuBuffers &w, cudaStream_t s)
 // gain / extra are cleared for the next evaluation.
 // --------------------------------------------------------------------------
 
-__global__ void __launch_bounds__(256) k_refresh(TabuBuffers w, const int32_t *__restrict__ cost)
+__device__ __forceinline__ void refresh_body(const TabuBuffers &w, const int32_t *__restrict__ cost, int bid,
+                                             int nb)
 {
     TabuDevState *st = w.st;
     if (st->done) return;
@@ -1456,7 +1561,7 @@ __global__ void __launch_bounds__(256) k_refresh(TabuBuffers w, const int32_t *_
     const size_t M_pad = w.M_pad;
     const int32_t *rowj = cost + (size_t)jj * M_pad;
     long long v0c = 0, v0d = 0;
-    for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < w.M; m += gridDim.x * blockDim.x) {
+    for (int m = bid * blockDim.x + threadIdx.x; m < w.M; m += nb * blockDim.x) {
         int a = w.a[m], b = w.b[m];
         int k1 = w.s1[m], k2 = w.s2[m];
         if (k1 != ss && k2 != ss) {
@@ -1479,12 +1584,17 @@ __global__ void __launch_bounds__(256) k_refresh(TabuBuffers w, const int32_t *_
     }
     // clear the neighbourhood accumulators for the next evaluation
     const size_t nE = (size_t)w.K * w.B;
-    const size_t tid = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-    const size_t nth = (size_t)gridDim.x * blockDim.x;
+    const size_t tid = bid * (size_t)blockDim.x + threadIdx.x;
+    const size_t nth = (size_t)nb * blockDim.x;
     for (size_t q = tid; q < nE; q += nth) { w.extra_c[q] = 0; w.extra_d[q] = 0; }
     for (size_t q = tid; q < (size_t)w.B; q += nth) { w.gain_c[q] = 0; w.gain_d[q] = 0; }
     __syncthreads();
     flush_loss_v0(w, s_lc, s_ld, v0c, v0d);
+}
+
+__global__ void __launch_bounds__(256) k_refresh(TabuBuffers w, const int32_t *__restrict__ cost)
+{
+    refresh_body(w, cost, blockIdx.x, gridDim.x);
 }
 
 cudaError_t launch_refresh(const TabuBuffers &w, const int32_t *cost, cudaStream_t s)
@@ -1500,6 +1610,7 @@ __global__ void k_export_best_two(TabuBuffers w, const int *__restrict__ perm, i
 {
     for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < w.M; q += gridDim.x * blockDim.x) {
         const int m = perm ? perm[q] : q;
+        if (m < 0) continue;   // removed mission
         a[m] = w.a[q];
         b[m] = w.b[q];
         const int k1 = w.s1[q], k2 = w.s2[q];
@@ -1515,6 +1626,8 @@ cudaError_t launch_export_best_two(const TabuBuffers &w, const int *perm, int32_
     return cudaGetLastError();
 }
 
+__global__ void k_group_swap(const GroupSlot *__restrict__ slots, const int *__restrict__ off, int n);
+
 cudaError_t kernels_init()
 {
     cudaError_t e = cudaFuncSetAttribute(k_swap_eval<kSwapJ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1526,6 +1639,9 @@ cudaError_t kernels_init()
     e = cudaFuncSetAttribute(k_swap_direct, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)(kPipeMaxK * kDirJ * 12));
     if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_group_swap, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(kGroupMaxK * kDirJ * 12));
+    if (e != cudaSuccess) return e;
     if (const char *v = getenv("STAGE_SWAP_VARIANT")) g_swap_variant = atoi(v);
     int dev = 0, n = 0;
     e = cudaGetDevice(&dev);
@@ -1535,4 +1651,115 @@ cudaError_t kernels_init()
     return cudaSuccess;
 }
 
+
+// --------------------------------------------------------------------------
+// Grouped launches of the batch engine.  Every active slot is one instance in
+// its own Tabu run; one launch of each kernel advances every slot by one step.
+// A slot whose search has stopped, or whose iteration budget is used up,
+// returns at once.
+// --------------------------------------------------------------------------
+
+int group_swap_blocks(int M_pad, int nC, int *bx)
+{
+    *bx = (M_pad + kDirSegment - 1) / kDirSegment;
+    return nC > 0 ? *bx * ((nC + kDirJ - 1) / kDirJ) : 0;
+}
+
+int group_ref_blocks(int M_pad)
+{
+    const int g = (M_pad + 255) / 256;
+    return g < 64 ? g : 64;
+}
+
+// largest i with off[i] <= b (off[0] = 0, off[n] = total)
+__device__ __forceinline__ int find_slot(const int *__restrict__ off, int n, int b)
+{
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (off[mid] <= b) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ void load_slot(const GroupSlot *slots, int slot, GroupSlot &dst)
+{
+    if (threadIdx.x == 0) dst = slots[slot];
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(kDirThreads, 4)
+k_group_swap(const GroupSlot *__restrict__ slots, const int *__restrict__ off, int n)
+{
+    __shared__ GroupSlot g;
+    __shared__ int s_slot;
+    if (threadIdx.x == 0) s_slot = find_slot(off, n, blockIdx.x);
+    __syncthreads();
+    load_slot(slots, s_slot, g);
+    const TabuDevState *st = g.w.st;
+    if (st->done || st->t >= st->t_end) return;
+    const int local = blockIdx.x - off[s_slot];
+    swap_direct_body(g.w, g.cost, local % g.swap_bx, local / g.swap_bx);
+}
+
+cudaError_t launch_group_swap(const GroupSlot *slots, const int *swap_off, int n, int total_blocks, int maxK,
+                              cudaStream_t s)
+{
+    if (total_blocks <= 0 || n <= 0) return cudaSuccess;
+    k_group_swap<<<total_blocks, kDirThreads, (size_t)maxK * kDirJ * 12, s>>>(slots, swap_off, n);
+    return cudaGetLastError();
+}
+
+__global__ void __launch_bounds__(kSelectThreads) k_group_select(const GroupSlot *__restrict__ slots)
+{
+    __shared__ GroupSlot g;
+    __shared__ MoveKey s_adm[kSelectThreads], s_all[kSelectThreads];
+    load_slot(slots, blockIdx.x, g);
+    TabuDevState *st = g.w.st;
+    if (st->done || st->t >= st->t_end) return;
+    const long long v0c = (long long)g.w.v0[0], v0d = (long long)g.w.v0[1];
+    MoveKey adm = invalid_key(), all = invalid_key();
+    select_scan(g.w, st->t, st->nC, v0c, v0d, st->best_cov, st->best_dist, threadIdx.x, blockDim.x, adm, all);
+    block_best2<kSelectThreads>(adm, all, s_adm, s_all);
+    select_apply(g.w, adm, all, v0c, v0d);
+}
+
+cudaError_t launch_group_select(const GroupSlot *slots, int n, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    k_group_select<<<n, kSelectThreads, 0, s>>>(slots);
+    return cudaGetLastError();
+}
+
+__global__ void __launch_bounds__(256) k_group_refresh(const GroupSlot *__restrict__ slots,
+                                                       const int *__restrict__ off, int n)
+{
+    __shared__ GroupSlot g;
+    __shared__ int s_slot;
+    if (threadIdx.x == 0) s_slot = find_slot(off, n, blockIdx.x);
+    __syncthreads();
+    load_slot(slots, s_slot, g);
+    refresh_body(g.w, g.cost, blockIdx.x - off[s_slot], g.ref_blocks);
+}
+
+cudaError_t launch_group_refresh(const GroupSlot *slots, const int *ref_off, int n, int total_blocks, int maxK,
+                                 cudaStream_t s)
+{
+    if (total_blocks <= 0 || n <= 0) return cudaSuccess;
+    k_group_refresh<<<total_blocks, 256, (size_t)maxK * 16, s>>>(slots, ref_off, n);
+    return cudaGetLastError();
+}
+
+__global__ void k_gather_states(const GroupSlot *__restrict__ slots, int n, TabuDevState *__restrict__ out)
+{
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) out[k] = *slots[k].w.st;
+}
+
+cudaError_t launch_gather_states(const GroupSlot *slots, int n, TabuDevState *out, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    k_gather_states<<<(n + 127) / 128, 128, 0, s>>>(slots, n, out);
+    return cudaGetLastError();
+}
 }  // namespace stg

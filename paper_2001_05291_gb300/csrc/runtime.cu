@@ -16,69 +16,16 @@
 
 using namespace stg;
 
-namespace {
+#include "runtime_internal.h"
 
-struct DevBuf {
-    void *p = nullptr;
-    size_t bytes = 0;
-};
-
-struct KernelStat {
-    int64_t launches = 0;
-    double ms = 0.0;
-    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending;
-};
-
-struct Instance {
-    int B = 0, M = 0, M_pad = 0;
-    int n_avail = 0;
-    std::vector<uint8_t> h_avail;
-    DevBuf mem_coords;   // base, pick, drop (caller order and column order), pd, perm, inv, avail
-    DevBuf mem_table;    // B x M_pad int32, columns in mission order `perm`
-    int2 *base = nullptr, *pick = nullptr, *drop = nullptr;   // column order
-    int2 *pick_in = nullptr, *drop_in = nullptr;              // caller order
-    int32_t *pd = nullptr;
-    int32_t *perm = nullptr;   // column -> caller's mission index
-    int32_t *inv = nullptr;    // caller's mission index -> column
-    uint8_t *avail = nullptr;
-    int32_t *cost = nullptr;
-    // Tabu workspace, sized for ws_K / ws_traj
-    DevBuf mem_ws;
-    int ws_K = 0, ws_traj = -1;
-    TabuBuffers tb{};
-    DevBuf mem_scratch;  // rank sums, evaluation outputs, exports
-    size_t scratch_bytes = 0;
-};
-
-}  // namespace
-
-struct stage_ctx {
-    int device = 0;
-    uint32_t flags = 0;
-    uint64_t budget = 0;
-    int max_slots = 8;
-    int64_t spin_limit = 1ll << 26;
-    stage_alloc_fn alloc = nullptr;
-    stage_free_fn free = nullptr;
-    void *alloc_user = nullptr;
-    cudaStream_t stream = nullptr;
-    bool own_stream = false;
-    uint64_t used = 0;
-    std::unordered_map<uint64_t, Instance *> insts;
-    uint64_t next_id = 1;
-    std::string err;
-    std::recursive_mutex mu;
-    std::unordered_map<std::string, KernelStat> stats;
-    std::vector<cudaEvent_t> event_pool;
-    void *pinned = nullptr;       // small pinned host buffer for early-stop polls
-};
-
-namespace {
+namespace stg_rt {
 
 struct Guard {
     stage_ctx *c;
     bool locked;
-    explicit Guard(stage_ctx *ctx) : c(ctx), locked(ctx && (ctx->flags & STAGE_THREADSAFE))
+    // every call is serialised on the context's mutex: the batch engine's
+    // thread shares the context with the caller's thread
+    explicit Guard(stage_ctx *ctx) : c(ctx), locked(ctx != nullptr)
     {
         if (locked) c->mu.lock();
     }
@@ -250,7 +197,7 @@ size_t carve_ws(char *base, int K, int B, int M_pad, int traj, TabuBuffers &tb)
 
 stage_status ensure_ws(stage_ctx *c, Instance *in, int K, int traj)
 {
-    if (in->mem_ws.p && in->ws_K == K && in->ws_traj >= traj) return STAGE_OK;
+    if (in->mem_ws.p && in->ws_K == K && in->ws_traj >= traj && in->ws_M_pad == in->M_pad) return STAGE_OK;
     dev_free(c, in->mem_ws);
     TabuBuffers tb{};
     size_t bytes = carve_ws(nullptr, K, in->B, in->M_pad, traj, tb);
@@ -264,7 +211,28 @@ stage_status ensure_ws(stage_ctx *c, Instance *in, int K, int traj)
     in->tb = tb;
     in->ws_K = K;
     in->ws_traj = traj;
+    in->ws_M_pad = in->M_pad;
     return STAGE_OK;
+}
+
+// Coordinate block of an instance with room for `cap` missions.
+size_t carve_coords(char *base, int B, int cap, Instance *in)
+{
+    Carver cv{base};
+    int2 *b = cv.take<int2>(B);
+    int2 *p = cv.take<int2>(cap);
+    int2 *d = cv.take<int2>(cap);
+    int2 *pi = cv.take<int2>(cap);
+    int2 *di = cv.take<int2>(cap);
+    int32_t *pd = cv.take<int32_t>(cap);
+    int32_t *perm = cv.take<int32_t>(cap);
+    int32_t *inv = cv.take<int32_t>(cap);
+    uint8_t *av = cv.take<uint8_t>(B);
+    if (base && in) {
+        in->base = b; in->pick = p; in->drop = d; in->pick_in = pi; in->drop_in = di;
+        in->pd = pd; in->perm = perm; in->inv = inv; in->avail = av;
+    }
+    return round_up(cv.off, 256);
 }
 
 stage_status check_placement(stage_ctx *c, Instance *in, const int32_t *open, int K)
@@ -329,6 +297,7 @@ stage_status setup_search(stage_ctx *c, Instance *in, const int32_t *open, int K
     st.nC = nC;
     st.traj_cap = traj_cap;
     st.best_iter = -1;
+    st.t_end = t0 + traj_cap;
     std::vector<int32_t> expiry(in->B, 0);
     if (expiry_in) std::copy(expiry_in, expiry_in + in->B, expiry.begin());
     CK(cudaMemcpyAsync(tb.open, open, (size_t)K * 4, cudaMemcpyHostToDevice, c->stream));
@@ -463,7 +432,9 @@ stage_status run_tabu(stage_ctx *c, Instance *in, const stage_tabu_params *p,
     return STAGE_OK;
 }
 
-}  // namespace
+}  // namespace stg_rt
+
+using namespace stg_rt;
 
 // ============================================================== C ABI
 
@@ -516,6 +487,7 @@ stage_status stage_create(const stage_config *cfg, stage_ctx **out)
 stage_status stage_destroy(stage_ctx *c)
 {
     if (!c) return STAGE_OK;
+    engine_destroy(c);
     cudaSetDevice(c->device);
     cudaStreamSynchronize(c->stream);
     for (auto &kv : c->insts) free_instance(c, kv.second);
@@ -590,24 +562,14 @@ stage_status stage_load_instance(stage_ctx *c, const stage_instance_desc *d, sta
     in->B = B; in->M = M; in->M_pad = M_pad;
     in->h_avail = avail;
     in->n_avail = (int)std::count(avail.begin(), avail.end(), (uint8_t)1);
-    size_t coords = round_up((size_t)B * 8, 256) + 4 * round_up((size_t)M * 8, 256) +
-                    3 * round_up((size_t)M * 4, 256) + round_up((size_t)B, 256);
+    size_t coords = carve_coords(nullptr, B, M_pad, nullptr);
     stage_status s = dev_alloc(c, coords, in->mem_coords);
     if (s == STAGE_OK) s = dev_alloc(c, (size_t)B * M_pad * 4, in->mem_table);
     if (s != STAGE_OK) {
         free_instance(c, in);
         return s;
     }
-    Carver cv{static_cast<char *>(in->mem_coords.p)};
-    in->base = cv.take<int2>(B);
-    in->pick = cv.take<int2>(M);
-    in->drop = cv.take<int2>(M);
-    in->pick_in = cv.take<int2>(M);
-    in->drop_in = cv.take<int2>(M);
-    in->pd = cv.take<int32_t>(M);
-    in->perm = cv.take<int32_t>(M);
-    in->inv = cv.take<int32_t>(M);
-    in->avail = cv.take<uint8_t>(B);
+    carve_coords(static_cast<char *>(in->mem_coords.p), B, M_pad, in);
     in->cost = static_cast<int32_t *>(in->mem_table.p);
     DevBuf order_tmp;
     s = dev_alloc(c, order_scratch_bytes(M), order_tmp);
@@ -647,10 +609,143 @@ stage_status stage_unload_instance(stage_ctx *c, stage_inst h)
     Guard g(c);
     Instance *in = find_inst(c, h);
     if (!in) return set_err(c, STAGE_ERR_NOT_FOUND, "unknown instance %llu", (unsigned long long)h);
+    if (in->busy) return set_err(c, STAGE_ERR_ADMISSION, "instance %llu is in use by a batch request",
+                                 (unsigned long long)h);
     cudaSetDevice(c->device);
     cudaStreamSynchronize(c->stream);
     c->insts.erase(h);
     free_instance(c, in);
+    return STAGE_OK;
+}
+
+// Grow an instance's table and mission arrays to hold at least M_new columns.
+static stage_status grow_instance(stage_ctx *c, Instance *in, int M_new)
+{
+    const int cap = (int)round_up((size_t)M_new + (size_t)M_new / 8 + 64, kPadMissions);
+    DevBuf coords, table;
+    stage_status s = dev_alloc(c, carve_coords(nullptr, in->B, cap, nullptr), coords);
+    if (s == STAGE_OK) s = dev_alloc(c, (size_t)in->B * cap * 4, table);
+    if (s != STAGE_OK) {
+        dev_free(c, coords);
+        return s;
+    }
+    Instance nw;
+    carve_coords(static_cast<char *>(coords.p), in->B, cap, &nw);
+    int32_t *cost = static_cast<int32_t *>(table.p);
+    const int M = in->M, B = in->B;
+    cudaStream_t st = c->stream;
+    cudaError_t e = launch_fill_i32(cost, (size_t)B * cap, kInf, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpy2DAsync(cost, (size_t)cap * 4, in->cost, (size_t)in->M_pad * 4, (size_t)M * 4, B,
+                              cudaMemcpyDeviceToDevice, st);
+    auto cp = [&](void *dst, const void *src, size_t n) {
+        if (e == cudaSuccess && n) e = cudaMemcpyAsync(dst, src, n, cudaMemcpyDeviceToDevice, st);
+    };
+    cp(nw.base, in->base, (size_t)B * 8);
+    cp(nw.pick, in->pick, (size_t)M * 8);
+    cp(nw.drop, in->drop, (size_t)M * 8);
+    cp(nw.pick_in, in->pick_in, (size_t)M * 8);
+    cp(nw.drop_in, in->drop_in, (size_t)M * 8);
+    cp(nw.pd, in->pd, (size_t)M * 4);
+    cp(nw.perm, in->perm, (size_t)M * 4);
+    cp(nw.inv, in->inv, (size_t)M * 4);
+    cp(nw.avail, in->avail, (size_t)B);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        dev_free(c, coords);
+        dev_free(c, table);
+        return set_err(c, STAGE_ERR_CUDA, "growing the table failed: %s", cudaGetErrorString(e));
+    }
+    dev_free(c, in->mem_coords);
+    dev_free(c, in->mem_table);
+    in->mem_coords = coords;
+    in->mem_table = table;
+    in->base = nw.base; in->pick = nw.pick; in->drop = nw.drop; in->pick_in = nw.pick_in;
+    in->drop_in = nw.drop_in; in->pd = nw.pd; in->perm = nw.perm; in->inv = nw.inv; in->avail = nw.avail;
+    in->cost = cost;
+    in->M_pad = cap;
+    return STAGE_OK;
+}
+
+stage_status stage_update_instance(stage_ctx *c, stage_inst h, const stage_update *u)
+{
+    if (!c) return STAGE_ERR_INVALID_ARG;
+    Guard g(c);
+    Instance *in = find_inst(c, h);
+    if (!in) return set_err(c, STAGE_ERR_NOT_FOUND, "unknown instance %llu", (unsigned long long)h);
+    if (!u) return set_err(c, STAGE_ERR_INVALID_ARG, "update is NULL");
+    if (in->busy) return set_err(c, STAGE_ERR_ADMISSION, "instance %llu is in use by a batch request",
+                                 (unsigned long long)h);
+    if (u->n_add < 0 || u->n_remove < 0 || u->n_unavail < 0 || u->n_avail < 0 ||
+        (u->n_add && (!u->add_pick_xy || !u->add_drop_xy)) || (u->n_remove && !u->remove_ids) ||
+        (u->n_unavail && !u->unavail_ids) || (u->n_avail && !u->avail_ids))
+        return set_err(c, STAGE_ERR_INVALID_ARG, "malformed update");
+    for (int k = 0; k < u->n_unavail; k++)
+        if (u->unavail_ids[k] < 0 || u->unavail_ids[k] >= in->B)
+            return set_err(c, STAGE_ERR_INVALID_ARG, "base id %d out of range", u->unavail_ids[k]);
+    for (int k = 0; k < u->n_avail; k++)
+        if (u->avail_ids[k] < 0 || u->avail_ids[k] >= in->B)
+            return set_err(c, STAGE_ERR_INVALID_ARG, "base id %d out of range", u->avail_ids[k]);
+    for (int k = 0; k < u->n_remove; k++)
+        if (u->remove_ids[k] < 0 || u->remove_ids[k] >= in->M)
+            return set_err(c, STAGE_ERR_INVALID_ARG, "mission id %d out of range", u->remove_ids[k]);
+    for (size_t k = 0; k < 2 * (size_t)u->n_add; k++) {
+        const int32_t x = u->add_pick_xy[k], y = u->add_drop_xy[k];
+        if (x > STAGE_MAX_COORD || x < -STAGE_MAX_COORD || y > STAGE_MAX_COORD || y < -STAGE_MAX_COORD)
+            return set_err(c, STAGE_ERR_OUT_OF_RANGE, "a coordinate exceeds |%d| m", STAGE_MAX_COORD);
+    }
+    if ((int64_t)in->M + u->n_add > STAGE_MAX_MISSIONS)
+        return set_err(c, STAGE_ERR_OUT_OF_RANGE, "more than %d mission ids", STAGE_MAX_MISSIONS);
+    CK(cudaSetDevice(c->device));
+    // bases
+    if (u->n_unavail || u->n_avail) {
+        for (int k = 0; k < u->n_unavail; k++) in->h_avail[u->unavail_ids[k]] = 0;
+        for (int k = 0; k < u->n_avail; k++) in->h_avail[u->avail_ids[k]] = 1;
+        in->n_avail = (int)std::count(in->h_avail.begin(), in->h_avail.end(), (uint8_t)1);
+        CK(cudaMemcpyAsync(in->avail, in->h_avail.data(), in->B, cudaMemcpyHostToDevice, c->stream));
+    }
+    // removed missions
+    if (u->n_remove) {
+        DevBuf ids;
+        stage_status s = dev_alloc(c, (size_t)u->n_remove * 4, ids);
+        if (s != STAGE_OK) return s;
+        cudaError_t e = cudaMemcpyAsync(ids.p, u->remove_ids, (size_t)u->n_remove * 4, cudaMemcpyHostToDevice,
+                                        c->stream);
+        if (e == cudaSuccess)
+            e = timed(c, "update", 1, [&] {
+                return launch_tombstone(static_cast<int32_t *>(ids.p), u->n_remove, in->inv, in->perm, in->cost,
+                                        in->B, in->M_pad, c->stream);
+            });
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        dev_free(c, ids);
+        if (e != cudaSuccess) return set_err(c, STAGE_ERR_CUDA, "removing missions failed: %s", cudaGetErrorString(e));
+    }
+    // appended missions: next ids, next columns (id == column for appended missions)
+    if (u->n_add) {
+        const int M0 = in->M, M1 = in->M + u->n_add;
+        if (M1 > in->M_pad) {
+            stage_status s = grow_instance(c, in, M1);
+            if (s != STAGE_OK) return s;
+        }
+        std::vector<int32_t> ident(u->n_add);
+        for (int k = 0; k < u->n_add; k++) ident[k] = M0 + k;
+        const size_t n8 = (size_t)u->n_add * 8, n4 = (size_t)u->n_add * 4;
+        CK(cudaMemcpyAsync(in->pick_in + M0, u->add_pick_xy, n8, cudaMemcpyHostToDevice, c->stream));
+        CK(cudaMemcpyAsync(in->drop_in + M0, u->add_drop_xy, n8, cudaMemcpyHostToDevice, c->stream));
+        CK(cudaMemcpyAsync(in->pick + M0, u->add_pick_xy, n8, cudaMemcpyHostToDevice, c->stream));
+        CK(cudaMemcpyAsync(in->drop + M0, u->add_drop_xy, n8, cudaMemcpyHostToDevice, c->stream));
+        CK(cudaMemcpyAsync(in->perm + M0, ident.data(), n4, cudaMemcpyHostToDevice, c->stream));
+        CK(cudaMemcpyAsync(in->inv + M0, ident.data(), n4, cudaMemcpyHostToDevice, c->stream));
+        CK(timed(c, "update", 1, [&] {
+            return launch_table_columns(in->B, M0, u->n_add, in->M_pad, in->base, in->pick, in->drop, in->pd,
+                                        in->cost, c->stream);
+        }));
+        CK(cudaStreamSynchronize(c->stream));
+        in->M = M1;
+    }
+    // the single-run workspace is sized for the old table
+    dev_free(c, in->mem_ws);
+    in->ws_K = 0;
     return STAGE_OK;
 }
 

@@ -41,7 +41,8 @@ struct TabuDevState {
     int mv_s, mv_i, mv_j; // last applied move: slot, closed base, opened base
     unsigned int ticket;  // last-block counter of the select kernel
     unsigned int work;    // work-unit counter of the streaming swap pass
-    int pad[2];
+    int t_end;            // iteration budget: no step at t >= t_end
+    int pad;
 };
 
 enum : int { kErrObjectiveMismatch = 1, kErrBadSlot = 2, kErrPipelineTimeout = 4 };
@@ -75,6 +76,11 @@ constexpr int kSelectThreads = 256;
 
 // ----------------------------------------------------------------- launchers
 // Every launcher enqueues on `stream` and returns the launch error.
+cudaError_t launch_fill_i32(int32_t *p, size_t n, int32_t v, cudaStream_t s);
+cudaError_t launch_table_columns(int B, int col0, int n, int M_pad, const int2 *base, const int2 *pick,
+                                 const int2 *drop, int32_t *pd, int32_t *cost, cudaStream_t s);
+cudaError_t launch_tombstone(const int32_t *ids, int n, int32_t *inv, int32_t *perm, int32_t *cost, int B,
+                             int M_pad, cudaStream_t s);
 cudaError_t launch_check_coords(const int32_t *v, size_t n, int *bad, cudaStream_t s);
 cudaError_t launch_table(int B, int M, int M_pad, const int2 *base, const int2 *pick,
                          const int2 *drop, int32_t *pd_scratch, int32_t *cost, cudaStream_t s);
@@ -101,5 +107,26 @@ cudaError_t launch_gather_window(const int32_t *cost, int M, int M_pad, const in
 cudaError_t launch_swap_table(const TabuBuffers &w, int nC, long long *out_c, long long *out_d,
                               cudaStream_t s);
 cudaError_t kernels_init();   // one-time function attributes (dynamic shared memory)
+
+// ------------------------------------------------------- grouped (batched) launches
+// One descriptor per active slot of the batch engine; one launch covers all of
+// them.  Blocks map to (slot, local block) through prefix offsets.
+struct GroupSlot {
+    TabuBuffers w;
+    const int32_t *cost;
+    int swap_bx;      // swap blocks along the missions of this slot
+    int swap_blocks;  // swap blocks of this slot (swap_bx x row chunks)
+    int ref_blocks;   // refresh blocks of this slot
+    int pad;
+};
+constexpr int kGroupMaxK = 256;
+int group_swap_blocks(int M_pad, int nC, int *bx);
+int group_ref_blocks(int M_pad);
+cudaError_t launch_group_swap(const GroupSlot *slots, const int *swap_off, int n, int total_blocks, int maxK,
+                              cudaStream_t s);
+cudaError_t launch_group_select(const GroupSlot *slots, int n, cudaStream_t s);
+cudaError_t launch_group_refresh(const GroupSlot *slots, const int *ref_off, int n, int total_blocks, int maxK,
+                                 cudaStream_t s);
+cudaError_t launch_gather_states(const GroupSlot *slots, int n, TabuDevState *out, cudaStream_t s);
 
 }  // namespace stg

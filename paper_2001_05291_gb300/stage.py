@@ -62,6 +62,25 @@ class StageTabuParams(C.Structure):
                 ("start_open", C.c_void_p), ("resume", C.POINTER(StageTabuState))]
 
 
+class StageUpdate(C.Structure):
+    _fields_ = [("n_add", C.c_int32), ("n_remove", C.c_int32), ("n_unavail", C.c_int32),
+                ("n_avail", C.c_int32), ("add_pick_xy", C.c_void_p), ("add_drop_xy", C.c_void_p),
+                ("remove_ids", C.c_void_p), ("unavail_ids", C.c_void_p), ("avail_ids", C.c_void_p)]
+
+
+class StageRequest(C.Structure):
+    _fields_ = [("inst", C.c_uint64), ("desc", C.POINTER(StageInstanceDesc)),
+                ("update", C.POINTER(StageUpdate)), ("params", StageTabuParams),
+                ("traj", C.c_void_p), ("best_open", C.c_void_p), ("final_open", C.c_void_p)]
+
+
+class StageResult(C.Structure):
+    _fields_ = [("status", C.c_int32), ("n_moves", C.c_int32), ("best_iter", C.c_int32),
+                ("reserved0", C.c_int32), ("best_cov", C.c_int64), ("best_dist", C.c_int64),
+                ("final_cov", C.c_int64), ("final_dist", C.c_int64), ("t_submit_ns", C.c_int64),
+                ("t_start_ns", C.c_int64), ("t_end_ns", C.c_int64)]
+
+
 class StageTabuResult(C.Structure):
     _fields_ = [("n_moves", C.c_int32), ("best_iter", C.c_int32), ("best_cov", C.c_int64),
                 ("best_dist", C.c_int64), ("final_cov", C.c_int64), ("final_dist", C.c_int64),
@@ -97,6 +116,9 @@ def lib():
             "stage_reset_stats": ([p], st),
             "stage_read_table": ([p, C.c_uint64, i32, i32, i32, i32, p], st),
             "stage_best_two": ([p, C.c_uint64, p, i32, i32, i32, i32, p, p, p, p], st),
+            "stage_update_instance": ([p, C.c_uint64, C.POINTER(StageUpdate)], st),
+            "stage_batch_submit": ([p, C.POINTER(StageRequest), i32, C.POINTER(C.c_uint64)], st),
+            "stage_poll": ([p, C.c_uint64, C.POINTER(StageResult), i32], st),
             "stage_evaluate_swaps_noalloc": ([p, i32, i32, i32, p, p, i32, i32, p, p, p, C.c_char_p,
                                               C.c_size_t], st),
         }
@@ -341,6 +363,73 @@ class Context:
         self._check(lib().stage_read_table(self._h, inst, b0, nb, m0, nm, _ptr(out)))
         return out
 
+    def update_instance(self, inst: int, add_pick=None, add_drop=None, remove=None, unavailable=None,
+                        available=None):
+        """stage_update_instance: append missions, withdraw mission ids, close or reopen bases."""
+        u, keep = _make_update(add_pick, add_drop, remove, unavailable, available)
+        self._check(lib().stage_update_instance(self._h, inst, C.byref(u)))
+        del keep
+
+    def batch_submit(self, requests):
+        """stage_batch_submit.  Each request is a dict: inst (handle) or base_xy/pick_xy/drop_xy
+        (+ base_available) for an instance given by value; K, R, iters, tenure;
+        optional start_open, accept_worsening, update (dict of update_instance's arguments).
+        Returns a list of BatchTicket; call .wait() (or Context.poll) for results."""
+        n = len(requests)
+        arr = (StageRequest * max(1, n))()
+        tickets = (C.c_uint64 * max(1, n))()
+        keep, outs = [], []
+        for k, rq in enumerate(requests):
+            r = arr[k]
+            if "inst" in rq and rq["inst"]:
+                r.inst = rq["inst"]
+            else:
+                d = StageInstanceDesc()
+                b, p, q = (_host_i32(rq[x]) for x in ("base_xy", "pick_xy", "drop_xy"))
+                d.B, d.M = b.size // 2, p.size // 2
+                d.base_xy, d.pick_xy, d.drop_xy = _ptr(b), _ptr(p), _ptr(q)
+                keep += [b, p, q, d]
+                if rq.get("base_available") is not None:
+                    av = np.ascontiguousarray(rq["base_available"], dtype=np.uint8)
+                    d.base_available = _ptr(av)
+                    keep.append(av)
+                r.desc = C.pointer(d)
+            if rq.get("update"):
+                u, kk = _make_update(**rq["update"])
+                keep += [u, kk]
+                r.update = C.pointer(u)
+            K, iters = rq["K"], rq["iters"]
+            r.params.K, r.params.R, r.params.iters, r.params.tenure = K, rq["R"], iters, rq["tenure"]
+            r.params.accept_worsening = 1 if rq.get("accept_worsening", True) else 0
+            if rq.get("start_open") is not None:
+                so = _host_i32(rq["start_open"], K)
+                keep.append(so)
+                r.params.start_open = _ptr(so)
+            traj = (StageMove * max(1, iters))()
+            best = np.empty(K, dtype=np.int32)
+            fin = np.empty(K, dtype=np.int32)
+            r.traj, r.best_open, r.final_open = C.cast(traj, C.c_void_p), _ptr(best), _ptr(fin)
+            outs.append((traj, best, fin))
+        self._check(lib().stage_batch_submit(self._h, arr, n, tickets))
+        del keep
+        return [BatchTicket(self, int(tickets[k]), *outs[k]) for k in range(n)]
+
+    def poll(self, ticket: "BatchTicket", timeout_us: int = -1):
+        """stage_poll: None while the ticket runs (after waiting up to timeout_us), else its result."""
+        res = StageResult()
+        rc = lib().stage_poll(self._h, ticket.id, C.byref(res), timeout_us)
+        if rc == STAGE_PENDING:
+            return None
+        ticket.done = True
+        if rc < 0:
+            raise StageError(rc, f"batch request failed (ticket {ticket.id})")
+        moves = [(ticket.traj[k].iter, ticket.traj[k].i, ticket.traj[k].j, ticket.traj[k].flags,
+                  ticket.traj[k].cov, ticket.traj[k].dist) for k in range(res.n_moves)]
+        out = TabuResult(res.n_moves, ticket.best, res.best_cov, res.best_dist, res.best_iter, ticket.final,
+                         res.final_cov, res.final_dist, moves)
+        out.timing = dict(submit_ns=res.t_submit_ns, start_ns=res.t_start_ns, end_ns=res.t_end_ns)
+        return out
+
     def kernel_stats(self, name: str):
         n, ms = C.c_int64(), C.c_double()
         self._check(lib().stage_kernel_stats(self._h, name.encode(), C.byref(n), C.byref(ms)))
@@ -348,6 +437,36 @@ class Context:
 
     def reset_stats(self):
         self._check(lib().stage_reset_stats(self._h))
+
+
+class BatchTicket:
+    """A submitted batch request; its output buffers live here until collected."""
+
+    def __init__(self, ctx, tid, traj, best, final):
+        self.ctx, self.id, self.traj, self.best, self.final = ctx, tid, traj, best, final
+        self.done = False
+
+    def wait(self, timeout_us: int = -1):
+        return self.ctx.poll(self, timeout_us)
+
+
+def _make_update(add_pick=None, add_drop=None, remove=None, unavailable=None, available=None):
+    u = StageUpdate()
+    keep = []
+    if add_pick is not None:
+        ap, ad = _host_i32(add_pick), _host_i32(add_drop)
+        if ap.size != ad.size:
+            raise ValueError("add_pick and add_drop differ in size")
+        u.n_add, u.add_pick_xy, u.add_drop_xy = ap.size // 2, _ptr(ap), _ptr(ad)
+        keep += [ap, ad]
+    for name, cnt, ptr in ((remove, "n_remove", "remove_ids"), (unavailable, "n_unavail", "unavail_ids"),
+                           (available, "n_avail", "avail_ids")):
+        if name is not None:
+            a = _host_i32(name)
+            setattr(u, cnt, a.size)
+            setattr(u, ptr, _ptr(a))
+            keep.append(a)
+    return u, keep
 
 
 def evaluate_swaps_noalloc(cost, M: int, open_, R: int, out_cov, out_dist, base_available=None,
@@ -396,5 +515,8 @@ stage_evaluate_swaps = Context.evaluate_swaps
 stage_tabu_run = Context.tabu_run
 stage_best_two = Context.best_two
 stage_read_table = Context.read_table
+stage_update_instance = Context.update_instance
+stage_batch_submit = Context.batch_submit
+stage_poll = Context.poll
 stage_kernel_stats = Context.kernel_stats
 stage_reset_stats = Context.reset_stats

@@ -59,6 +59,9 @@ int main(void) {
   P(stage_tabu_state); O(stage_tabu_state, open); O(stage_tabu_state, tabu_expiry);
   P(stage_tabu_params); O(stage_tabu_params, start_open); O(stage_tabu_params, resume);
   P(stage_tabu_result); O(stage_tabu_result, best_open); O(stage_tabu_result, end_state);
+  P(stage_update); O(stage_update, add_pick_xy); O(stage_update, avail_ids);
+  P(stage_request); O(stage_request, params); O(stage_request, traj); O(stage_request, final_open);
+  P(stage_result); O(stage_result, best_cov); O(stage_result, t_end_ns);
   return 0;
 }
 """
@@ -75,7 +78,9 @@ def test_ctypes_layouts_match_header(tmp_path):
                                                                check=True).stdout.splitlines())
     py = {"stage_config": stage.StageConfig, "stage_instance_desc": stage.StageInstanceDesc,
           "stage_move": stage.StageMove, "stage_tabu_state": stage.StageTabuState,
-          "stage_tabu_params": stage.StageTabuParams, "stage_tabu_result": stage.StageTabuResult}
+          "stage_tabu_params": stage.StageTabuParams, "stage_tabu_result": stage.StageTabuResult,
+          "stage_update": stage.StageUpdate, "stage_request": stage.StageRequest,
+          "stage_result": stage.StageResult}
     for key, val in got.items():
         if "." in key:
             t, f = key.split(".")
