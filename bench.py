@@ -46,7 +46,12 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="large", choices=["tiny", "province", "large"])
+    ap.add_argument("--workload", default="large", choices=["tiny", "province", "large", "batched", "serving"])
+    ap.add_argument("--instances", type=int, default=512, help="batched / serving: instances")
+    ap.add_argument("--slots", type=int, default=512, help="batched / serving: engine slots")
+    ap.add_argument("--duration", type=float, default=20.0, help="serving: seconds of arrivals")
+    ap.add_argument("--rate", type=float, default=200.0, help="serving: arrivals per second")
+    ap.add_argument("--no-plain", action="store_true", help="batched: skip the one-launch-per-instance pass")
     ap.add_argument("--missions", type=int, default=0,
                     help="override M of the large workload (smaller profiling cases)")
     ap.add_argument("--e2e-steps", type=int, default=2)
@@ -334,10 +339,188 @@ def kernel_digest() -> str:
     return h.hexdigest()[:16]
 
 
+def _ctx_for(args, stage, torch, local=0):
+    torch.cuda.set_device(local)
+    return stage.Context(device=local, profile=False, max_slots=args.slots)
+
+
+def run_batched(args):
+    """512 independent instances of uneven B, M, K, R (300 Tabu iterations each):
+    one stage_batch_submit of all of them against one stage_tabu_run per instance."""
+    import numpy as np
+    import torch
+    from paper_2001_05291_gb300 import build, stage, synth
+    rank, world, local = env_rank()
+    build.build()
+    insts = synth.batched(n=args.instances)
+    ctx = _ctx_for(args, stage, torch, local)
+    t0 = time.perf_counter()
+    hs = [ctx.load_instance(i.base_xy, i.pick_xy, i.drop_xy) for i in insts]
+    load_s = time.perf_counter() - t0
+    # tile autotuning per shape bucket, outside the timed region (both paths use it)
+    t0 = time.perf_counter()
+    for h, i in zip(hs, insts):
+        ctx.autotune(h, i.K, i.R)
+    tune_s = time.perf_counter() - t0
+    reqs = [dict(inst=h, K=i.K, R=i.R, iters=i.iters, tenure=i.tenure) for h, i in zip(hs, insts)]
+    evals = sum(i.iters * i.K * (i.B - i.K) * i.M for i in insts)
+    # warm-up: a few of each path
+    for t in ctx.batch_submit(reqs[:8]):
+        t.wait()
+    for h, i in list(zip(hs, insts))[:8]:
+        ctx.tabu_run(h, i.K, i.R, i.iters, i.tenure, trajectory=False)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    t0 = time.perf_counter()
+    res = [t.wait() for t in ctx.batch_submit(reqs)]
+    batched_s = time.perf_counter() - t0
+    clk = clocks.stop()
+    if args.no_plain:
+        plain, plain_s = res, float("nan")
+    else:
+        t0 = time.perf_counter()
+        plain = [ctx.tabu_run(h, i.K, i.R, i.iters, i.tenure) for h, i in zip(hs, insts)]
+        plain_s = time.perf_counter() - t0
+    agree = all(a.moves == b.moves and a.best_dist == b.best_dist for a, b in zip(res, plain))
+    line = {"metric": "batched inst/s", "value": len(insts) / batched_s, "unit": "inst/s", "n_gpus": world,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+            "data": "synthetic",
+            "config": {"workload": f"batched: seed 3, {len(insts)} instances, B log-uniform [50, 800], M "
+                                   f"log-uniform [1e3, 2e5], K uniform [4, 32], R uniform [600, 1200] km, "
+                                   f"300 Tabu iterations, tenure 11", "slots": args.slots},
+            "batched_s": batched_s, "plain_s": plain_s, "plain_inst_s": len(insts) / plain_s,
+            "speedup_vs_plain": plain_s / batched_s, "evals_per_s": evals / batched_s,
+            "plain_evals_per_s": evals / plain_s, "load_s": load_s, "autotune_s": tune_s,
+            "batched_equals_plain": agree,
+            "table_gb": sum(i.B * i.M * 4 for i in insts) / 1e9, "clocks": clk}
+    print(json.dumps(line))
+    ctx.close()
+    return 0
+
+
+def serving_trace(args):
+    """Poisson arrivals; 30 % updates to a resident instance (add or remove 1-5 % of its
+    missions, or close 1-3 bases), 70 % fresh instances of the batched size distribution."""
+    import numpy as np
+    from paper_2001_05291_gb300 import synth
+    key = synth.stream_key(4, synth.CLS_ARRIVALS)
+    n = int(args.rate * args.duration * 1.5) + 16
+    u = synth.u01(synth.draws_u64(key, np.arange(6 * n))).reshape(n, 6)
+    gaps = -np.log1p(-u[:, 0]) / args.rate
+    t = np.cumsum(gaps)
+    n = int(np.searchsorted(t, args.duration))
+    sizes = synth.batched_sizes(4, n)
+    trace = []
+    for k in range(n):
+        B, M, K, R = sizes[k]
+        if u[k, 1] < 0.3:
+            kind = ("add", "remove", "close")[min(2, int(u[k, 2] * 3))]
+            trace.append(dict(t=float(t[k]), kind=kind, target=u[k, 3], frac=0.01 + 0.04 * u[k, 4],
+                              nclose=1 + min(2, int(u[k, 5] * 3)), seed=k))
+        else:
+            trace.append(dict(t=float(t[k]), kind="fresh", size=(B, M, K, R), seed=k))
+    return trace
+
+
+def run_serving(args):
+    import numpy as np
+    import torch
+    from paper_2001_05291_gb300 import build, stage, synth
+    rank, world, local = env_rank()
+    build.build()
+    trace = serving_trace(args)
+    pool = [synth.batched_instance(4, 10_000 + p, *s) for p, s in enumerate(synth.batched_sizes(5, 32))]
+    fresh = {}
+    for r in trace:
+        if r["kind"] == "fresh":
+            fresh[r["seed"]] = synth.batched_instance(4, r["seed"], *r["size"])
+
+    def make_update(r, inst, n_ids, closed):
+        rng = synth.u01(synth.draws_u64(synth.stream_key(r["seed"], 77), np.arange(4096)))
+        if r["kind"] == "add":
+            m = max(1, int(r["frac"] * inst.M))
+            src = synth.batched_instance(6, r["seed"], 1, m, 1, inst.R)
+            return dict(add_pick=src.pick_xy, add_drop=src.drop_xy), m
+        if r["kind"] == "remove":
+            m = max(1, int(r["frac"] * inst.M))
+            ids = np.unique((synth.u01(synth.draws_u64(synth.stream_key(r["seed"], 78), np.arange(m))) * n_ids)
+                            .astype(np.int64))
+            return dict(remove=ids), 0
+        ids = [int(x * inst.B) for x in rng[: r["nclose"]]]
+        ids = [b for b in ids if b not in closed][: max(0, inst.B - inst.K - 1 - len(closed))]
+        return dict(unavailable=ids), 0
+
+    def serve(engine: bool):
+        ctx = _ctx_for(args, stage, torch, local)
+        hs = [ctx.load_instance(i.base_xy, i.pick_xy, i.drop_xy) for i in pool]
+        n_ids = [i.M for i in pool]
+        closed = [set() for _ in pool]
+        lat, done_at = [], []
+        start = time.perf_counter()
+        pending = []
+        for r in trace:
+            now = time.perf_counter() - start
+            if r["t"] > now:
+                time.sleep(r["t"] - now)
+            arrive = start + r["t"]
+            if r["kind"] == "fresh":
+                inst = fresh[r["seed"]]
+                rq = dict(base_xy=inst.base_xy, pick_xy=inst.pick_xy, drop_xy=inst.drop_xy, K=inst.K, R=inst.R,
+                          iters=300, tenure=11)
+            else:
+                p = min(len(pool) - 1, int(r["target"] * len(pool)))
+                inst = pool[p]
+                upd, added = make_update(r, inst, n_ids[p], closed[p])
+                n_ids[p] += added
+                closed[p].update(upd.get("unavailable", []))
+                rq = dict(inst=hs[p], K=inst.K, R=inst.R, iters=300, tenure=11, update=upd)
+            if engine:
+                pending.append((arrive, ctx.batch_submit([rq])[0]))
+            else:
+                if "inst" in rq:
+                    ctx.update_instance(rq["inst"], **rq["update"])
+                    ctx.tabu_run(rq["inst"], rq["K"], rq["R"], rq["iters"], rq["tenure"], trajectory=False)
+                else:
+                    h = ctx.load_instance(rq["base_xy"], rq["pick_xy"], rq["drop_xy"])
+                    ctx.tabu_run(h, rq["K"], rq["R"], rq["iters"], rq["tenure"], trajectory=False)
+                    ctx.unload_instance(h)
+                lat.append(time.perf_counter() - arrive)
+                done_at.append(time.perf_counter())
+        for arrive, tk in pending:
+            r = tk.wait()
+            # the engine stamps submission and completion on the same monotonic
+            # clock as time.perf_counter (CLOCK_MONOTONIC)
+            lat.append((r.timing["end_ns"] - r.timing["submit_ns"]) / 1e9)
+            done_at.append(r.timing["end_ns"] / 1e9)
+        wall = max(done_at) - start if done_at else 0.0
+        ctx.close()
+        lat = np.array(lat) * 1000.0
+        return {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                "mean_ms": float(lat.mean()), "throughput_req_s": len(lat) / wall, "wall_s": wall,
+                "requests": len(lat)}
+
+    eng = serve(True)
+    ser = serve(False)
+    line = {"metric": "serving p50/p99 latency", "value": eng["p99_ms"], "unit": "ms (p99)", "n_gpus": world,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+            "data": "synthetic",
+            "config": {"workload": f"serving: seed 4, Poisson {args.rate:g} req/s for {args.duration:g} s, 30 % "
+                                   f"updates to 32 resident instances, 70 % fresh instances of the batched size "
+                                   f"distribution, 300 Tabu iterations, tenure 11", "slots": args.slots},
+            "engine": eng, "serial_plain": ser}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batched":
+        return run_batched(args)
+    if args.workload == "serving":
+        return run_serving(args)
     return run_ours(args)
 
 

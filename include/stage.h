@@ -72,6 +72,7 @@ typedef int32_t stage_status;
 /* context flags */
 #define STAGE_THREADSAFE   1u   /* accepted; calls are always serialised */
 #define STAGE_PROFILE      2u   /* time every kernel launch with CUDA events */
+#define STAGE_AUTOTUNE     4u   /* tune the swap pass's tile the first time a shape is met */
 
 /* instance descriptor flags */
 #define STAGE_DESC_DEVICE  1u   /* base_xy/pick_xy/drop_xy/base_available are device pointers */
@@ -306,6 +307,17 @@ STAGE_API stage_status stage_batch_submit(stage_ctx *ctx, const stage_request *r
  * STAGE_ERR_ADMISSION when it can never fit the HBM budget).
  * STAGE_ERR_NOT_FOUND for an unknown or already collected ticket. */
 STAGE_API stage_status stage_poll(stage_ctx *ctx, uint64_t ticket, stage_result *out, int32_t timeout_us);
+
+/* ----------------------------------------------------------------- autotuner */
+
+/* Tile autotuner of the swap pass.  Times every candidate number of missions
+ * per block (1024 ... 16384) on this instance with placement open[K] (NULL:
+ * the ranking) and range R, and records the fastest for the instance's shape
+ * bucket (ceil log2 of padded missions, of candidate rows, of K); every later
+ * search of that bucket on this process uses it.  *out_missions_per_block
+ * (nullable) receives the choice.  The choice changes no result. */
+STAGE_API stage_status stage_autotune(stage_ctx *ctx, stage_inst inst, const int32_t *open, int32_t K, int32_t R,
+                                      int32_t *out_missions_per_block);
 
 /* ---------------------------------------------------------------- profiling */
 

@@ -72,10 +72,12 @@ struct Engine {
     int cap = 0;
     TabuDevState *h_states = nullptr;      // pinned
     cudaGraphExec_t graph = nullptr;
-    bool dirty = true;
-    int n_swap_blocks = 0, n_ref_blocks = 0, maxK = 1;
+    bool dirty = true;        // slot set changed: device arrays must be rebuilt
+    int stable = 0;           // rounds since the last change (the graph is captured once stable)
+    int n_swap_blocks = 0, n_sel_blocks = 0, n_ref_blocks = 0, maxK = 1;
 
     void run();
+    cudaError_t launch_steps(int steps);
     bool admit(Ticket *tk, bool &transient);
     void complete(Ticket *tk, stage_status st);
     void retire(size_t k, const TabuDevState &s, stage_status status);
@@ -194,6 +196,13 @@ bool Engine::admit(Ticket *tk, bool &transient)
         s = do_rank(c, in, K, start.data(), nullptr);
         if (s != STAGE_OK) return fail(s);
     }
+    if (c->flags & STAGE_AUTOTUNE) {
+        const int nc0 = in->n_avail - K;
+        if (!swap_segment_known(in->M_pad, nc0, K)) {
+            s = autotune_shape(c, in, start.data(), K, p.R, nullptr);
+            if (s != STAGE_OK) return fail(s);
+        }
+    }
     Slot sl;
     sl.tk = tk;
     sl.in = in;
@@ -228,6 +237,9 @@ bool Engine::admit(Ticket *tk, bool &transient)
     st.best_iter = -1;
     st.t_end = p.iters;
     std::vector<int32_t> zeros(in->B, 0);
+    // set-up runs on the context's stream: the engine's stream may be busy
+    // with the current step, which this slot is not part of
+    cudaStream_t stream = c->stream;
     cudaError_t e = cudaMemcpyAsync(tb.open, start.data(), (size_t)K * 4, cudaMemcpyHostToDevice, stream);
     if (e == cudaSuccess && sl.nC)
         e = cudaMemcpyAsync(tb.cand, cand.data(), (size_t)sl.nC * 4, cudaMemcpyHostToDevice, stream);
@@ -276,52 +288,73 @@ stage_status Engine::rebuild()
         h_states = nullptr;
         cap = std::max(n, std::max(cap * 2, 16));
         stage_status s = dev_alloc(c, sizeof(GroupSlot) * (size_t)cap, d_slots);
-        if (s == STAGE_OK) s = dev_alloc(c, sizeof(int) * 2 * (size_t)(cap + 1), d_off);
+        if (s == STAGE_OK) s = dev_alloc(c, sizeof(int) * 3 * (size_t)(cap + 1), d_off);
         if (s == STAGE_OK) s = dev_alloc(c, sizeof(TabuDevState) * (size_t)cap, d_states);
         if (s != STAGE_OK) return s;
         if (cudaMallocHost(&h_states, sizeof(TabuDevState) * (size_t)cap) != cudaSuccess) return STAGE_ERR_CUDA;
     }
     std::vector<GroupSlot> gs(n);
-    std::vector<int> off(2 * (n + 1), 0);
+    std::vector<int> off(3 * (n + 1), 0);
     maxK = 1;
     for (int k = 0; k < n; k++) {
         const Slot &sl = active[k];
         gs[k].w = sl.tb;
         gs[k].cost = sl.in->cost;
-        gs[k].swap_blocks = group_swap_blocks(sl.tb.M_pad, sl.nC, &gs[k].swap_bx);
+        gs[k].swap_blocks = group_swap_blocks(sl.tb.M_pad, sl.nC, sl.tb.K, &gs[k].swap_bx, &gs[k].swap_seg);
+        gs[k].sel_blocks = select_blocks(sl.tb.K, sl.nC);
         gs[k].ref_blocks = group_ref_blocks(sl.tb.M_pad);
         off[k + 1] = off[k] + gs[k].swap_blocks;
-        off[n + 1 + k + 1] = off[n + 1 + k] + gs[k].ref_blocks;
+        off[(n + 1) + k + 1] = off[(n + 1) + k] + gs[k].sel_blocks;
+        off[2 * (n + 1) + k + 1] = off[2 * (n + 1) + k] + gs[k].ref_blocks;
         maxK = std::max(maxK, sl.tb.K);
     }
     n_swap_blocks = off[n];
-    n_ref_blocks = off[2 * n + 1];
+    n_sel_blocks = off[2 * n + 1];
+    n_ref_blocks = off[3 * n + 2];
     cudaError_t e = cudaMemcpyAsync(d_slots.p, gs.data(), sizeof(GroupSlot) * n, cudaMemcpyHostToDevice, stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(d_off.p, off.data(), sizeof(int) * off.size(), cudaMemcpyHostToDevice, stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
     if (e != cudaSuccess) return STAGE_ERR_CUDA;
-    // capture kStepsPerGraph grouped steps
+    dirty = false;
+    stable = 0;
+    return STAGE_OK;
+}
+
+// kStepsPerGraph grouped steps: launched directly while the slot set keeps
+// changing, replayed from a captured CUDA graph once it has been stable.
+cudaError_t Engine::launch_steps(int steps)
+{
+    const int n = (int)active.size();
     const GroupSlot *ds = static_cast<const GroupSlot *>(d_slots.p);
     const int *swap_off = static_cast<const int *>(d_off.p);
-    const int *ref_off = swap_off + n + 1;
-    cudaGraph_t gr = nullptr;
-    e = cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal);
-    for (int k = 0; e == cudaSuccess && k < kStepsPerGraph; k++) {
-        e = launch_group_swap(ds, swap_off, n, n_swap_blocks, maxK, stream);
-        if (e == cudaSuccess) e = launch_group_select(ds, n, stream);
-        if (e == cudaSuccess) e = launch_group_refresh(ds, ref_off, n, n_ref_blocks, maxK, stream);
+    const int *sel_off = swap_off + (n + 1);
+    const int *ref_off = swap_off + 2 * (n + 1);
+    auto enqueue = [&]() {
+        cudaError_t e = cudaSuccess;
+        for (int k = 0; e == cudaSuccess && k < steps; k++) {
+            e = launch_group_swap(ds, swap_off, n, n_swap_blocks, maxK, stream);
+            if (e == cudaSuccess) e = launch_group_select(ds, sel_off, n, n_sel_blocks, stream);
+            if (e == cudaSuccess) e = launch_group_refresh(ds, ref_off, n, n_ref_blocks, maxK, stream);
+        }
+        return e;
+    };
+    if (stable < 1) return enqueue();
+    if (!graph) {
+        cudaGraph_t gr = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) e = enqueue();
+        cudaError_t e2 = cudaStreamEndCapture(stream, &gr);
+        if (e == cudaSuccess) e = e2;
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&graph, gr, 0);
+        if (gr) cudaGraphDestroy(gr);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            graph = nullptr;
+            return enqueue();
+        }
     }
-    cudaError_t e2 = cudaStreamEndCapture(stream, &gr);
-    if (e == cudaSuccess) e = e2;
-    if (e == cudaSuccess) e = cudaGraphInstantiate(&graph, gr, 0);
-    if (gr) cudaGraphDestroy(gr);
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        return STAGE_ERR_CUDA;
-    }
-    dirty = false;
-    return STAGE_OK;
+    return cudaGraphLaunch(graph, stream);
 }
 
 void Engine::retire(size_t k, const TabuDevState &s, stage_status status)
@@ -372,6 +405,29 @@ void Engine::run()
                 pending.pop_front();
             }
         }
+        // 1. advance the current slots (asynchronous)
+        cudaError_t e = cudaSuccess;
+        const int n = (int)active.size();
+        if (n > 0) {
+            if (dirty && rebuild() != STAGE_OK) e = cudaErrorUnknown;
+            if (e == cudaSuccess) {
+                {
+                    std::lock_guard<std::recursive_mutex> g(c->mu);
+                    for (const char *nm : {"group_swap", "group_select", "group_refresh"})
+                        c->stats[nm].launches += kStepsPerGraph;
+                    c->stats["group_steps"].launches += kStepsPerGraph;
+                }
+                e = launch_steps(kStepsPerGraph);
+                if (e == cudaSuccess)
+                    e = launch_gather_states(static_cast<const GroupSlot *>(d_slots.p), n,
+                                             static_cast<TabuDevState *>(d_states.p), stream);
+                if (e == cudaSuccess)
+                    e = cudaMemcpyAsync(h_states, d_states.p, sizeof(TabuDevState) * n, cudaMemcpyDeviceToHost,
+                                        stream);
+            }
+        }
+        // 2. meanwhile admit waiting requests (their set-up runs on the context's stream)
+        const size_t before = active.size();
         std::vector<Ticket *> retry;
         for (Ticket *tk : take) {
             bool transient = false;
@@ -381,40 +437,22 @@ void Engine::run()
             std::lock_guard<std::mutex> lk(mu);
             for (auto it = retry.rbegin(); it != retry.rend(); ++it) pending.push_front(*it);
         }
-        if (active.empty()) {
-            if (!retry.empty()) std::this_thread::sleep_for(std::chrono::microseconds(200));
-            continue;
-        }
-        if (dirty && rebuild() != STAGE_OK) {
-            for (size_t k = active.size(); k-- > 0;) {
+        // 3. finish the step and retire finished slots (only the first n slots took part)
+        if (n > 0) {
+            if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+            for (size_t k = n; k-- > 0;) {
                 TabuDevState z{};
-                retire(k, z, STAGE_ERR_CUDA);
+                const TabuDevState &s = e == cudaSuccess ? h_states[k] : z;
+                const bool fin = e != cudaSuccess || s.done || s.t >= s.t_end || s.err;
+                if (!fin) continue;
+                retire(k, s, e != cudaSuccess ? STAGE_ERR_CUDA : STAGE_OK);
                 active.erase(active.begin() + k);
+                dirty = true;
             }
-            dirty = true;
-            continue;
         }
-        {
-            std::lock_guard<std::recursive_mutex> g(c->mu);
-            for (const char *nm : {"group_swap", "group_select", "group_refresh"}) c->stats[nm].launches += kStepsPerGraph;
-            c->stats["group_steps"].launches += kStepsPerGraph;
-        }
-        cudaError_t e = cudaGraphLaunch(graph, stream);
-        const int n = (int)active.size();
-        if (e == cudaSuccess)
-            e = launch_gather_states(static_cast<const GroupSlot *>(d_slots.p), n,
-                                     static_cast<TabuDevState *>(d_states.p), stream);
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(h_states, d_states.p, sizeof(TabuDevState) * n, cudaMemcpyDeviceToHost, stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
-        for (size_t k = active.size(); k-- > 0;) {
-            const TabuDevState &s = h_states[k];
-            const bool fin = e != cudaSuccess || s.done || s.t >= s.t_end || s.err;
-            if (!fin) continue;
-            retire(k, s, e != cudaSuccess ? STAGE_ERR_CUDA : STAGE_OK);
-            active.erase(active.begin() + k);
-            dirty = true;
-        }
+        if (active.size() != before) dirty = true;
+        if (!dirty) stable += 1;
+        if (active.empty() && !retry.empty()) std::this_thread::sleep_for(std::chrono::microseconds(200));
     }
     // stopping: release what is still held; unfinished tickets report a timeout
     for (size_t k = active.size(); k-- > 0;) {
@@ -426,7 +464,7 @@ void Engine::run()
 
 void engine_destroy(stage_ctx *c)
 {
-    Engine *E = c->engine;
+    Engine *E = c->engine.load();
     if (!E) return;
     {
         std::lock_guard<std::mutex> lk(E->mu);
@@ -449,7 +487,7 @@ void engine_destroy(stage_ctx *c)
     if (E->h_states) cudaFreeHost(E->h_states);
     if (E->stream) cudaStreamDestroy(E->stream);
     delete E;
-    c->engine = nullptr;
+    c->engine.store(nullptr);
 }
 
 }  // namespace stg_rt
@@ -462,10 +500,10 @@ stage_status stage_batch_submit(stage_ctx *c, const stage_request *reqs, int32_t
 {
     if (!c) return STAGE_ERR_INVALID_ARG;
     if (n < 0 || (n > 0 && (!reqs || !tickets))) return set_err(c, STAGE_ERR_INVALID_ARG, "bad request array");
-    Engine *E = nullptr;
-    {
+    Engine *E = c->engine.load();
+    if (!E) {
         std::lock_guard<std::recursive_mutex> g(c->mu);
-        if (!c->engine) {
+        if (!c->engine.load()) {
             cudaSetDevice(c->device);
             E = new Engine();
             E->c = c;
@@ -473,10 +511,10 @@ stage_status stage_batch_submit(stage_ctx *c, const stage_request *reqs, int32_t
                 delete E;
                 return set_err(c, STAGE_ERR_CUDA, "engine stream creation failed");
             }
-            c->engine = E;
+            c->engine.store(E);
             E->th = std::thread([E] { E->run(); });
         }
-        E = c->engine;
+        E = c->engine.load();
     }
     std::vector<std::unique_ptr<Ticket>> made;
     for (int32_t k = 0; k < n; k++) {
@@ -520,7 +558,7 @@ stage_status stage_batch_submit(stage_ctx *c, const stage_request *reqs, int32_t
 stage_status stage_poll(stage_ctx *c, uint64_t ticket, stage_result *out, int32_t timeout_us)
 {
     if (!c || !out) return STAGE_ERR_INVALID_ARG;
-    Engine *E = c->engine;
+    Engine *E = c->engine.load();
     if (!E) return STAGE_ERR_NOT_FOUND;
     std::unique_lock<std::mutex> lk(E->mu);
     auto it = E->tickets.find(ticket);

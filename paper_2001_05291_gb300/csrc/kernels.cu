@@ -11,6 +11,9 @@
 
 namespace stg {
 
+static int g_num_sms = 0;   // SMs of the current device (kernels_init)
+int swap_segment_for(int M_pad, int nC, int K);
+
 // --------------------------------------------------------------------------
 // helpers
 // --------------------------------------------------------------------------
@@ -1166,7 +1169,6 @@ k_swap_stream(TabuBuffers w, const int32_t *__restrict__ cost, int ignore_done)
 // --------------------------------------------------------------------------
 constexpr int kDirJ = 16;
 constexpr int kDirThreads = 256;
-constexpr int kDirSegment = 16384;
 
 // Hit path of one row for one warp: called (out of line, so the kernel body
 // stays small enough for the instruction cache) only when some lane of the
@@ -1223,7 +1225,7 @@ __device__ __noinline__ void dir_row(const int4 x, const int4 ap, const int4 bp,
 }
 
 __device__ __forceinline__ void swap_direct_body(const TabuBuffers &w, const int32_t *__restrict__ cost,
-                                                 int bx, int by)
+                                                 int bx, int by, int seg)
 {
     extern __shared__ unsigned long long sm_dir[];
     const int K = w.K;
@@ -1244,8 +1246,8 @@ __device__ __forceinline__ void swap_direct_body(const TabuBuffers &w, const int
     const int R = w.R, lane = threadIdx.x & 31;
     const size_t M_pad = w.M_pad;
     const int nrows = min(kDirJ, nC - c0);
-    const int m_begin = bx * kDirSegment;
-    const int m_end = min(m_begin + kDirSegment, w.M_pad);
+    const int m_begin = bx * seg;
+    const int m_end = min(m_begin + seg, w.M_pad);
     // Warp-uniform trip count: every lane of a warp runs every iteration (the
     // warp-collective reductions in dir_row need all 32 lanes); lanes past the
     // segment end see thresholds that nothing can beat.
@@ -1299,17 +1301,68 @@ __device__ __forceinline__ void swap_direct_body(const TabuBuffers &w, const int
 }
 
 __global__ void __launch_bounds__(kDirThreads, 4)
-k_swap_direct(TabuBuffers w, const int32_t *__restrict__ cost, int ignore_done)
+k_swap_direct(TabuBuffers w, const int32_t *__restrict__ cost, int ignore_done, int seg)
 {
     if (!ignore_done && w.st->done) return;
-    swap_direct_body(w, cost, blockIdx.x, blockIdx.y);
+    swap_direct_body(w, cost, blockIdx.x, blockIdx.y, seg);
+}
+
+// Missions per block of the direct swap pass: the largest power of two in
+// [1024, 16384] that still gives at least two waves of blocks (4 per SM), so
+// mid-size instances fill the GPU and large ones keep the per-block flush
+// rare.  A measured choice (stage_autotune) overrides it per shape bucket.
+int swap_segment_heuristic(int M_pad, int nC)
+{
+    const int chunks = (nC + kDirJ - 1) / kDirJ;
+    const long long target = 2ll * 4 * (g_num_sms > 0 ? g_num_sms : 152);
+    int seg = 16384;
+    while (seg > 1024 && (long long)((M_pad + seg - 1) / seg) * chunks < target) seg >>= 1;
+    return seg;
+}
+
+// Tile cache: missions per block chosen by measurement, per shape bucket
+// (ceil log2 of padded missions, of candidate rows, and of K).  0 = unset.
+static int g_seg_cache[26][18][12];
+
+static inline int ilog2_ceil(long long v)
+{
+    int r = 0;
+    while ((1ll << r) < v) r++;
+    return r;
+}
+
+int swap_segment_for(int M_pad, int nC, int K)
+{
+    const int a = min(25, ilog2_ceil(M_pad)), b = min(17, ilog2_ceil(nC > 0 ? nC : 1)), c = min(11, ilog2_ceil(K));
+    const int v = g_seg_cache[a][b][c];
+    return v ? v : swap_segment_heuristic(M_pad, nC);
+}
+
+void swap_segment_record(int M_pad, int nC, int K, int seg)
+{
+    const int a = min(25, ilog2_ceil(M_pad)), b = min(17, ilog2_ceil(nC > 0 ? nC : 1)), c = min(11, ilog2_ceil(K));
+    g_seg_cache[a][b][c] = seg;
+}
+
+bool swap_segment_known(int M_pad, int nC, int K)
+{
+    const int a = min(25, ilog2_ceil(M_pad)), b = min(17, ilog2_ceil(nC > 0 ? nC : 1)), c = min(11, ilog2_ceil(K));
+    return g_seg_cache[a][b][c] != 0;
+}
+
+// Launch the direct swap pass with an explicit segment (autotuning).
+cudaError_t launch_swap_direct_seg(const TabuBuffers &w, const int32_t *cost, int nC, int seg, cudaStream_t s)
+{
+    if (nC <= 0) return cudaSuccess;
+    dim3 grid((w.M_pad + seg - 1) / seg, (nC + kDirJ - 1) / kDirJ);
+    k_swap_direct<<<grid, kDirThreads, (size_t)w.K * kDirJ * 12, s>>>(w, cost, 1, seg);
+    return cudaGetLastError();
 }
 
 // Swap-evaluation variant: 0 = direct (default), 1 = streaming pipeline,
 // 2 = the plain per-element form.  STAGE_SWAP_VARIANT overrides (tuning).
 static int g_swap_variant = 0;
 
-static int g_num_sms = 0;
 
 size_t swap_stream_smem(int K)
 {
@@ -1322,8 +1375,9 @@ cudaError_t launch_swap_eval(const TabuBuffers &w, const int32_t *cost, int nC, 
 {
     if (nC <= 0) return cudaSuccess;
     if (g_swap_variant == 0 && w.K <= kPipeMaxK) {
-        dim3 grid((w.M_pad + kDirSegment - 1) / kDirSegment, (nC + kDirJ - 1) / kDirJ);
-        k_swap_direct<<<grid, kDirThreads, (size_t)w.K * kDirJ * 12, s>>>(w, cost, ignore_done);
+        const int seg = swap_segment_for(w.M_pad, nC, w.K);
+        dim3 grid((w.M_pad + seg - 1) / seg, (nC + kDirJ - 1) / kDirJ);
+        k_swap_direct<<<grid, kDirThreads, (size_t)w.K * kDirJ * 12, s>>>(w, cost, ignore_done, seg);
         return cudaGetLastError();
     }
     if (g_swap_variant == 1 && w.K <= kPipeMaxK && nC <= kPipeMaxCand && g_num_sms > 0) {
@@ -1492,10 +1546,11 @@ __device__ __forceinline__ void select_apply(const TabuBuffers &w, const MoveKey
     }
 }
 
-__global__ void __launch_bounds__(kSelectThreads) k_select(TabuBuffers w)
+// Multi-block selection: block `bid` of `nb` scans its share, the last block
+// of the instance to finish (ticket) reduces the block results and applies.
+__device__ __forceinline__ void select_body(const TabuBuffers &w, int bid, int nb)
 {
     TabuDevState *st = w.st;
-    if (st->done || st->t >= st->t_end) return;
     __shared__ MoveKey s_adm[kSelectThreads], s_all[kSelectThreads];
     __shared__ int s_last;
     const int t = st->t;
@@ -1503,22 +1558,22 @@ __global__ void __launch_bounds__(kSelectThreads) k_select(TabuBuffers w)
     const long long v0c = (long long)w.v0[0], v0d = (long long)w.v0[1];
     const long long bc = st->best_cov, bd = st->best_dist;
     MoveKey adm = invalid_key(), all = invalid_key();
-    select_scan(w, t, nC, v0c, v0d, bc, bd, blockIdx.x * (long long)blockDim.x + threadIdx.x,
-                (long long)gridDim.x * blockDim.x, adm, all);
+    select_scan(w, t, nC, v0c, v0d, bc, bd, bid * (long long)blockDim.x + threadIdx.x, (long long)nb * blockDim.x,
+                adm, all);
     block_best2<kSelectThreads>(adm, all, s_adm, s_all);
     if (threadIdx.x == 0) {
-        w.partials[2 * blockIdx.x] = adm;
-        w.partials[2 * blockIdx.x + 1] = all;
+        w.partials[2 * bid] = adm;
+        w.partials[2 * bid + 1] = all;
         __threadfence();
         const unsigned int ticket = atomicAdd(&st->ticket, 1u);
-        s_last = (ticket == gridDim.x - 1);
+        s_last = (ticket == (unsigned)nb - 1);
     }
     __syncthreads();
     if (!s_last) return;
     __threadfence();
     adm = invalid_key();
     all = invalid_key();
-    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
         MoveKey pa = load_key_cg(&w.partials[2 * b]);
         MoveKey px = load_key_cg(&w.partials[2 * b + 1]);
         if (key_better(pa, adm)) adm = pa;
@@ -1529,9 +1584,26 @@ __global__ void __launch_bounds__(kSelectThreads) k_select(TabuBuffers w)
     select_apply(w, adm, all, v0c, v0d);
 }
 
-cudaError_t launch_select(const TabuBuffers &w, cudaStream_t s)
+__global__ void __launch_bounds__(kSelectThreads) k_select(TabuBuffers w)
 {
-    k_select<<<kSelectBlocks, kSelectThreads, 0, s>>>(w);
+    TabuDevState *st = w.st;
+    if (st->done || st->t >= st->t_end) return;
+    select_body(w, blockIdx.x, gridDim.x);
+}
+
+// Blocks for K x nC candidates: about 8 candidates per thread, at most kSelectBlocks.
+int select_blocks(int K, int nC)
+{
+    const long long n = (long long)K * nC;
+    long long b = (n + kSelectThreads * 8 - 1) / (kSelectThreads * 8);
+    if (b < 1) b = 1;
+    if (b > kSelectBlocks) b = kSelectBlocks;
+    return (int)b;
+}
+
+cudaError_t launch_select(const TabuBuffers &w, int nC, cudaStream_t s)
+{
+    k_select<<<select_blocks(w.K, nC), kSelectThreads, 0, s>>>(w);
     return cudaGetLastError();
 }
 
@@ -1659,9 +1731,10 @@ cudaError_t kernels_init()
 // returns at once.
 // --------------------------------------------------------------------------
 
-int group_swap_blocks(int M_pad, int nC, int *bx)
+int group_swap_blocks(int M_pad, int nC, int K, int *bx, int *seg)
 {
-    *bx = (M_pad + kDirSegment - 1) / kDirSegment;
+    *seg = swap_segment_for(M_pad, nC, K);
+    *bx = (M_pad + *seg - 1) / *seg;
     return nC > 0 ? *bx * ((nC + kDirJ - 1) / kDirJ) : 0;
 }
 
@@ -1700,7 +1773,7 @@ k_group_swap(const GroupSlot *__restrict__ slots, const int *__restrict__ off, i
     const TabuDevState *st = g.w.st;
     if (st->done || st->t >= st->t_end) return;
     const int local = blockIdx.x - off[s_slot];
-    swap_direct_body(g.w, g.cost, local % g.swap_bx, local / g.swap_bx);
+    swap_direct_body(g.w, g.cost, local % g.swap_bx, local / g.swap_bx, g.swap_seg);
 }
 
 cudaError_t launch_group_swap(const GroupSlot *slots, const int *swap_off, int n, int total_blocks, int maxK,
@@ -1711,24 +1784,24 @@ cudaError_t launch_group_swap(const GroupSlot *slots, const int *swap_off, int n
     return cudaGetLastError();
 }
 
-__global__ void __launch_bounds__(kSelectThreads) k_group_select(const GroupSlot *__restrict__ slots)
+__global__ void __launch_bounds__(kSelectThreads) k_group_select(const GroupSlot *__restrict__ slots,
+                                                                const int *__restrict__ off, int n)
 {
     __shared__ GroupSlot g;
-    __shared__ MoveKey s_adm[kSelectThreads], s_all[kSelectThreads];
-    load_slot(slots, blockIdx.x, g);
+    __shared__ int s_slot;
+    if (threadIdx.x == 0) s_slot = find_slot(off, n, blockIdx.x);
+    __syncthreads();
+    load_slot(slots, s_slot, g);
     TabuDevState *st = g.w.st;
     if (st->done || st->t >= st->t_end) return;
-    const long long v0c = (long long)g.w.v0[0], v0d = (long long)g.w.v0[1];
-    MoveKey adm = invalid_key(), all = invalid_key();
-    select_scan(g.w, st->t, st->nC, v0c, v0d, st->best_cov, st->best_dist, threadIdx.x, blockDim.x, adm, all);
-    block_best2<kSelectThreads>(adm, all, s_adm, s_all);
-    select_apply(g.w, adm, all, v0c, v0d);
+    select_body(g.w, blockIdx.x - off[s_slot], g.sel_blocks);
 }
 
-cudaError_t launch_group_select(const GroupSlot *slots, int n, cudaStream_t s)
+cudaError_t launch_group_select(const GroupSlot *slots, const int *sel_off, int n, int total_blocks,
+                                cudaStream_t s)
 {
-    if (n <= 0) return cudaSuccess;
-    k_group_select<<<n, kSelectThreads, 0, s>>>(slots);
+    if (n <= 0 || total_blocks <= 0) return cudaSuccess;
+    k_group_select<<<total_blocks, kSelectThreads, 0, s>>>(slots, sel_off, n);
     return cudaGetLastError();
 }
 

@@ -318,6 +318,52 @@ stage_status setup_search(stage_ctx *c, Instance *in, const int32_t *open, int K
     return STAGE_OK;
 }
 
+// Time the swap pass for each candidate missions-per-block and record the
+// fastest for this shape bucket.  Runs on a scratch search state that is
+// discarded (every search sets its state up afresh).
+stage_status autotune_shape(stage_ctx *c, Instance *in, const int32_t *open, int K, int R, int *out_seg)
+{
+    std::vector<int32_t> start(K);
+    if (open) {
+        stage_status s = check_placement(c, in, open, K);
+        if (s != STAGE_OK) return s;
+        std::copy(open, open + K, start.begin());
+    } else {
+        stage_status s = do_rank(c, in, K, start.data(), nullptr);
+        if (s != STAGE_OK) return s;
+    }
+    int nC = 0;
+    stage_status s = setup_search(c, in, start.data(), K, R, 0, 0, 1, 0, nullptr, &nC);
+    if (s != STAGE_OK) return s;
+    if (nC == 0 || K > 256) {
+        if (out_seg) *out_seg = swap_segment_heuristic(in->M_pad, nC);
+        return STAGE_OK;
+    }
+    cudaEvent_t e0 = get_event(c), e1 = get_event(c);
+    float best_ms = 0.f;
+    int best = 0;
+    for (int seg = 1024; seg <= 16384; seg <<= 1) {
+        if (seg > 1024 && (seg >> 1) >= in->M_pad) break;   // one block already covers every mission
+        CK(launch_swap_direct_seg(in->tb, in->cost, nC, seg, c->stream));
+        CK(cudaEventRecord(e0, c->stream));
+        for (int r = 0; r < 3; r++) CK(launch_swap_direct_seg(in->tb, in->cost, nC, seg, c->stream));
+        CK(cudaEventRecord(e1, c->stream));
+        CK(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, e0, e1));
+        if (!best || ms < best_ms) {
+            best_ms = ms;
+            best = seg;
+        }
+    }
+    c->event_pool.push_back(e0);
+    c->event_pool.push_back(e1);
+    c->stats["autotune"].launches += 1;
+    swap_segment_record(in->M_pad, nC, K, best);
+    if (out_seg) *out_seg = best;
+    return STAGE_OK;
+}
+
 stage_status run_tabu(stage_ctx *c, Instance *in, const stage_tabu_params *p,
                       stage_tabu_result *res, stage_move *traj, int32_t *exp_a, int32_t *exp_b,
                       int32_t *exp_b1, int32_t *exp_b2)
@@ -352,6 +398,15 @@ stage_status run_tabu(stage_ctx *c, Instance *in, const stage_tabu_params *p,
     }
     const int iters = p->iters;
     const int t0 = rs ? rs->t : 0;
+    if (c->flags & STAGE_AUTOTUNE) {
+        int nc0 = 0;
+        for (int b = 0; b < in->B; b++) nc0 += in->h_avail[b];
+        nc0 -= K;
+        if (!swap_segment_known(in->M_pad, nc0, K)) {
+            stage_status s = autotune_shape(c, in, start.data(), K, p->R, nullptr);
+            if (s != STAGE_OK) return s;
+        }
+    }
     int nC = 0;
     stage_status s = setup_search(c, in, start.data(), K, p->R, iters, p->tenure,
                                   p->accept_worsening ? 1 : 0, t0, rs ? rs->tabu_expiry : nullptr, &nC);
@@ -371,7 +426,7 @@ stage_status run_tabu(stage_ctx *c, Instance *in, const stage_tabu_params *p,
     volatile int *done_flag = static_cast<volatile int *>(c->pinned);
     for (int it = 0; it < iters && nC > 0; it++) {
         CK(timed(c, "swap_eval", 1, [&] { return launch_swap_eval(tb, in->cost, nC, 0, c->stream); }));
-        CK(timed(c, "select", 1, [&] { return launch_select(tb, c->stream); }));
+        CK(timed(c, "select", 1, [&] { return launch_select(tb, nC, c->stream); }));
         CK(timed(c, "refresh", 1, [&] { return launch_refresh(tb, in->cost, c->stream); }));
         // the improving-only rule usually stops early: poll the device flag now and then
         if (!p->accept_worsening && (it & 31) == 31) {
@@ -826,6 +881,22 @@ stage_status stage_tabu_run(stage_ctx *c, stage_inst h, const stage_tabu_params 
     if (!in) return set_err(c, STAGE_ERR_NOT_FOUND, "unknown instance %llu", (unsigned long long)h);
     CK(cudaSetDevice(c->device));
     return run_tabu(c, in, p, res, traj, nullptr, nullptr, nullptr, nullptr);
+}
+
+stage_status stage_autotune(stage_ctx *c, stage_inst h, const int32_t *open, int32_t K, int32_t R, int32_t *out)
+{
+    if (!c) return STAGE_ERR_INVALID_ARG;
+    Guard g(c);
+    Instance *in = find_inst(c, h);
+    if (!in) return set_err(c, STAGE_ERR_NOT_FOUND, "unknown instance %llu", (unsigned long long)h);
+    if (K < 1 || K > in->B || K > STAGE_MAX_K || K > in->n_avail)
+        return set_err(c, STAGE_ERR_INVALID_ARG, "K=%d outside [1, min(B, %d, available bases)]", K, STAGE_MAX_K);
+    if (R < 0 || R == INT32_MAX) return set_err(c, STAGE_ERR_OUT_OF_RANGE, "R=%d outside [0, INT32_MAX)", R);
+    CK(cudaSetDevice(c->device));
+    int seg = 0;
+    stage_status s = autotune_shape(c, in, open, K, R, &seg);
+    if (s == STAGE_OK && out) *out = seg;
+    return s;
 }
 
 stage_status stage_best_two(stage_ctx *c, stage_inst h, const int32_t *open, int32_t K, int32_t R,

@@ -4,6 +4,7 @@
 
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <condition_variable>
 #include <deque>
 #include <memory>
@@ -74,7 +75,7 @@ struct stage_ctx {
     std::unordered_map<std::string, stg_rt::KernelStat> stats;
     std::vector<cudaEvent_t> event_pool;
     void *pinned = nullptr;       // small pinned host buffer for early-stop polls
-    stg_rt::Engine *engine = nullptr;
+    std::atomic<stg_rt::Engine *> engine{nullptr};
 };
 
 namespace stg_rt {
@@ -90,6 +91,7 @@ size_t carve_ws(char *base, int K, int B, int M_pad, int traj, stg::TabuBuffers 
 stage_status check_placement(stage_ctx *c, Instance *in, const int32_t *open, int K);
 stage_status do_rank(stage_ctx *c, Instance *in, int K, int32_t *out_open, int64_t *out_rowsum);
 void engine_destroy(stage_ctx *c);
+stage_status autotune_shape(stage_ctx *c, Instance *in, const int32_t *open, int K, int R, int *out_seg);
 
 // Launch through `f`, counting launches and (with STAGE_PROFILE) timing them
 // on `stream`.

@@ -94,7 +94,7 @@ cudaError_t launch_init(const TabuBuffers &w, const int32_t *cost, cudaStream_t 
 cudaError_t launch_begin(const TabuBuffers &w, int resumed, cudaStream_t s);
 cudaError_t launch_swap_eval(const TabuBuffers &w, const int32_t *cost, int nC, int ignore_done,
                              cudaStream_t s);
-cudaError_t launch_select(const TabuBuffers &w, cudaStream_t s);
+cudaError_t launch_select(const TabuBuffers &w, int nC, cudaStream_t s);
 cudaError_t launch_refresh(const TabuBuffers &w, const int32_t *cost, cudaStream_t s);
 cudaError_t launch_export_best_two(const TabuBuffers &w, const int *perm, int32_t *a, int32_t *b,
                                    int32_t *b1, int32_t *b2, cudaStream_t s);
@@ -117,14 +117,24 @@ struct GroupSlot {
     int swap_bx;      // swap blocks along the missions of this slot
     int swap_blocks;  // swap blocks of this slot (swap_bx x row chunks)
     int ref_blocks;   // refresh blocks of this slot
+    int swap_seg;     // missions per swap block
+    int sel_blocks;   // select blocks of this slot
     int pad;
 };
 constexpr int kGroupMaxK = 256;
-int group_swap_blocks(int M_pad, int nC, int *bx);
+int group_swap_blocks(int M_pad, int nC, int K, int *bx, int *seg);
+int select_blocks(int K, int nC);
+// missions per block of the direct swap pass, per shape (measured choice or heuristic)
+int swap_segment_for(int M_pad, int nC, int K);
+int swap_segment_heuristic(int M_pad, int nC);
+void swap_segment_record(int M_pad, int nC, int K, int seg);
+bool swap_segment_known(int M_pad, int nC, int K);
+cudaError_t launch_swap_direct_seg(const TabuBuffers &w, const int32_t *cost, int nC, int seg, cudaStream_t s);
 int group_ref_blocks(int M_pad);
 cudaError_t launch_group_swap(const GroupSlot *slots, const int *swap_off, int n, int total_blocks, int maxK,
                               cudaStream_t s);
-cudaError_t launch_group_select(const GroupSlot *slots, int n, cudaStream_t s);
+cudaError_t launch_group_select(const GroupSlot *slots, const int *sel_off, int n, int total_blocks,
+                                cudaStream_t s);
 cudaError_t launch_group_refresh(const GroupSlot *slots, const int *ref_off, int n, int total_blocks, int maxK,
                                  cudaStream_t s);
 cudaError_t launch_gather_states(const GroupSlot *slots, int n, TabuDevState *out, cudaStream_t s);

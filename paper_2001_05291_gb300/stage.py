@@ -23,7 +23,7 @@ LIB_PATH = os.path.join(_PKG, "_lib", "libstage.so")
 STAGE_OK, STAGE_PENDING = 0, 1
 ERRORS = {-1: "INVALID_ARG", -2: "OUT_OF_RANGE", -3: "NO_MEMORY", -4: "ADMISSION", -5: "TIMEOUT",
           -6: "CUDA", -7: "INTERNAL", -8: "NOT_FOUND"}
-STAGE_THREADSAFE, STAGE_PROFILE = 1, 2
+STAGE_THREADSAFE, STAGE_PROFILE, STAGE_AUTOTUNE = 1, 2, 4
 STAGE_DESC_DEVICE = 1
 MOVE_FALLBACK, MOVE_ASPIRATION, MOVE_NEW_BEST = 1, 2, 4
 MAX_COORD, MAX_BASES, MAX_MISSIONS, MAX_K = 1 << 24, 65535, 1 << 24, 1024
@@ -116,6 +116,7 @@ def lib():
             "stage_reset_stats": ([p], st),
             "stage_read_table": ([p, C.c_uint64, i32, i32, i32, i32, p], st),
             "stage_best_two": ([p, C.c_uint64, p, i32, i32, i32, i32, p, p, p, p], st),
+            "stage_autotune": ([p, C.c_uint64, p, i32, i32, C.POINTER(i32)], st),
             "stage_update_instance": ([p, C.c_uint64, C.POINTER(StageUpdate)], st),
             "stage_batch_submit": ([p, C.POINTER(StageRequest), i32, C.POINTER(C.c_uint64)], st),
             "stage_poll": ([p, C.c_uint64, C.POINTER(StageResult), i32], st),
@@ -191,11 +192,12 @@ class Context:
 
     def __init__(self, device: int = 0, profile: bool = False, threadsafe: bool = False,
                  hbm_budget: int = 0, max_slots: int = 0, spin_limit: int = 0,
-                 torch_memory: bool = True, stream=None):
+                 torch_memory: bool = True, stream=None, autotune: bool = False):
         L = lib()
         cfg = StageConfig()
         cfg.device = device
-        cfg.flags = (STAGE_PROFILE if profile else 0) | (STAGE_THREADSAFE if threadsafe else 0)
+        cfg.flags = ((STAGE_PROFILE if profile else 0) | (STAGE_THREADSAFE if threadsafe else 0) |
+                     (STAGE_AUTOTUNE if autotune else 0))
         cfg.hbm_budget_bytes = hbm_budget
         cfg.max_slots = max_slots
         cfg.spin_limit = spin_limit
@@ -430,6 +432,13 @@ class Context:
         out.timing = dict(submit_ns=res.t_submit_ns, start_ns=res.t_start_ns, end_ns=res.t_end_ns)
         return out
 
+    def autotune(self, inst: int, K: int, R: int, open_=None) -> int:
+        """stage_autotune: measured missions-per-block of the swap pass for this shape."""
+        seg = C.c_int32()
+        o = None if open_ is None else _host_i32(open_, K)
+        self._check(lib().stage_autotune(self._h, inst, None if o is None else _ptr(o), K, R, C.byref(seg)))
+        return int(seg.value)
+
     def kernel_stats(self, name: str):
         n, ms = C.c_int64(), C.c_double()
         self._check(lib().stage_kernel_stats(self._h, name.encode(), C.byref(n), C.byref(ms)))
@@ -518,5 +527,6 @@ stage_read_table = Context.read_table
 stage_update_instance = Context.update_instance
 stage_batch_submit = Context.batch_submit
 stage_poll = Context.poll
+stage_autotune = Context.autotune
 stage_kernel_stats = Context.kernel_stats
 stage_reset_stats = Context.reset_stats

@@ -278,3 +278,21 @@ def test_device_resident_inputs(ctx):
     got = ctx.read_table(h, 0, inst.B, 0, inst.M)
     assert np.array_equal(got, oracle_table(inst))
     ctx.unload_instance(h)
+
+
+def test_autotune_changes_no_result(ctx):
+    from paper_2001_05291_gb300 import stage
+    inst = small(41, 90, 30000, 9)
+    h = load(ctx, inst)
+    before = ctx.tabu_run(h, inst.K, inst.R, 25, 3)
+    seg = ctx.autotune(h, inst.K, inst.R)
+    assert seg in (1024, 2048, 4096, 8192, 16384)
+    after = ctx.tabu_run(h, inst.K, inst.R, 25, 3)
+    assert before.moves == after.moves
+    ctx.unload_instance(h)
+    with stage.Context(device=0, autotune=True) as c2:
+        h2 = load(c2, inst)
+        tuned = c2.tabu_run(h2, inst.K, inst.R, 25, 3)
+        assert tuned.moves == before.moves
+    want = oracle.tabu(oracle_table(inst), inst.K, inst.R, 25, 3, nthreads=8)
+    assert [tuple(m) for m in before.moves] == [tuple(m) for m in want.moves]
