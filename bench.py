@@ -66,6 +66,19 @@ def env_rank():
             int(os.environ.get("LOCAL_RANK", "0")))
 
 
+def max_over_ranks(value: float) -> float:
+    """Maximum of a per-rank float over all ranks (identity without a process group).
+    NCCL groups reduce on the rank's GPU, gloo groups on the CPU."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return value
+    dev = f"cuda:{torch.cuda.current_device()}" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def load_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -252,9 +265,7 @@ def run_ours(args):
     stats = {k: ctx.kernel_stats(k) for k in KERNELS}
     launches = sum(n for n, _ in stats.values())
     if dist:
-        t = torch.tensor([ms], device=f"cuda:{local}")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+        ms = max_over_ranks(ms)
         dist.barrier()
 
     per_iter = evals_per_iteration(inst)
@@ -265,16 +276,19 @@ def run_ours(args):
     alg_bytes = TABLE_BYTES_PER_ELEM * nC * inst.M + AUX_BYTES_PER_MISSION * inst.M
     peak, peak_src = load_peaks()
     achieved = alg_bytes / avg_sw_s / 1e9
+    # DRAM traffic per launch from the committed ncu summary, only while the
+    # kernel source is the one that was measured and the workload is the full one
     traffic = None
-    prof = os.path.join(ROOT, "profiles", "swap_eval_traffic.json")
-    if os.path.exists(prof):
-        try:
-            with open(prof) as fh:
-                tp = json.load(fh)
-            if tp.get("workload") == inst.name and tp.get("kernel_digest") == kernel_digest():
-                traffic = tp["bytes_per_launch"]
-        except Exception:
-            traffic = None
+    prof = os.path.join(ROOT, "profiles", "swap_eval_traffic.md")
+    if os.path.exists(prof) and not args.missions:
+        fields = {}
+        with open(prof) as fh:
+            for line in fh:
+                if ":" in line and not line.startswith((" ", "#")):
+                    k, v = line.split(":", 1)
+                    fields[k.strip()] = v.strip()
+        if fields.get("workload") == inst.name and fields.get("kernel_source_digest") == kernel_digest():
+            traffic = float(fields["traffic_bytes_per_launch"])
 
     # end to end: host (pinned) buffers through the public API
     pinned = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
@@ -291,9 +305,7 @@ def run_ours(args):
             e2e_moves += r.n_moves
         e2e_s = time.perf_counter() - t0
         if dist:
-            t = torch.tensor([e2e_s], device=f"cuda:{local}")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_s = float(t.item())
+            e2e_s = max_over_ranks(e2e_s)
         e2e = {"value": world * e2e_moves * inst.K * nC * inst.M / e2e_s, "unit": UNIT,
                "h2d_bytes_per_step": 8 * inst.B + 16 * inst.M,
                "d2h_bytes_per_step": 32 * inst.iters + 8 * inst.K + 48,

@@ -68,13 +68,15 @@ struct Engine {
     bool stop = false;
     cudaStream_t stream = nullptr;
     std::vector<Slot> active;
-    DevBuf d_slots, d_off, d_states;
+    DevBuf d_slots, d_map, d_states;
     int cap = 0;
+    size_t map_cap = 0;       // int2 entries of d_map
     TabuDevState *h_states = nullptr;      // pinned
     cudaGraphExec_t graph = nullptr;
     bool dirty = true;        // slot set changed: device arrays must be rebuilt
     int stable = 0;           // rounds since the last change (the graph is captured once stable)
     int n_swap_blocks = 0, n_sel_blocks = 0, n_ref_blocks = 0, maxK = 1;
+    size_t swap_smem = 0;
 
     void run();
     cudaError_t launch_steps(int steps);
@@ -282,38 +284,56 @@ stage_status Engine::rebuild()
     if (n > cap) {
         std::lock_guard<std::recursive_mutex> g(c->mu);
         dev_free(c, d_slots);
-        dev_free(c, d_off);
         dev_free(c, d_states);
         if (h_states) cudaFreeHost(h_states);
         h_states = nullptr;
         cap = std::max(n, std::max(cap * 2, 16));
         stage_status s = dev_alloc(c, sizeof(GroupSlot) * (size_t)cap, d_slots);
-        if (s == STAGE_OK) s = dev_alloc(c, sizeof(int) * 3 * (size_t)(cap + 1), d_off);
         if (s == STAGE_OK) s = dev_alloc(c, sizeof(TabuDevState) * (size_t)cap, d_states);
         if (s != STAGE_OK) return s;
         if (cudaMallocHost(&h_states, sizeof(TabuDevState) * (size_t)cap) != cudaSuccess) return STAGE_ERR_CUDA;
     }
     std::vector<GroupSlot> gs(n);
-    std::vector<int> off(3 * (n + 1), 0);
+    std::vector<int> mp(n), nc(n);
+    for (int k = 0; k < n; k++) {
+        mp[k] = active[k].tb.M_pad;
+        nc[k] = active[k].nC;
+    }
+    const int common = group_common_segment(mp.data(), nc.data(), n);
     maxK = 1;
+    swap_smem = 0;
+    std::vector<int2> map;   // swap blocks, then select blocks, then refresh blocks
     for (int k = 0; k < n; k++) {
         const Slot &sl = active[k];
         gs[k].w = sl.tb;
         gs[k].cost = sl.in->cost;
-        gs[k].swap_blocks = group_swap_blocks(sl.tb.M_pad, sl.nC, sl.tb.K, &gs[k].swap_bx, &gs[k].swap_seg);
+        gs[k].swap_blocks =
+            group_swap_blocks(sl.tb.M_pad, sl.nC, sl.tb.K, common, &gs[k].swap_bx, &gs[k].swap_seg);
+        swap_smem = std::max(swap_smem, (size_t)sl.tb.K * 16 * 12);
         gs[k].sel_blocks = select_blocks(sl.tb.K, sl.nC);
         gs[k].ref_blocks = group_ref_blocks(sl.tb.M_pad);
-        off[k + 1] = off[k] + gs[k].swap_blocks;
-        off[(n + 1) + k + 1] = off[(n + 1) + k] + gs[k].sel_blocks;
-        off[2 * (n + 1) + k + 1] = off[2 * (n + 1) + k] + gs[k].ref_blocks;
+        for (int b = 0; b < gs[k].swap_blocks; b++) map.push_back(make_int2(k, b));
         maxK = std::max(maxK, sl.tb.K);
     }
-    n_swap_blocks = off[n];
-    n_sel_blocks = off[2 * n + 1];
-    n_ref_blocks = off[3 * n + 2];
+    n_swap_blocks = (int)map.size();
+    for (int k = 0; k < n; k++)
+        for (int b = 0; b < gs[k].sel_blocks; b++) map.push_back(make_int2(k, b));
+    n_sel_blocks = (int)map.size() - n_swap_blocks;
+    for (int k = 0; k < n; k++)
+        for (int b = 0; b < gs[k].ref_blocks; b++) map.push_back(make_int2(k, b));
+    n_ref_blocks = (int)map.size() - n_swap_blocks - n_sel_blocks;
+    if (map.size() > map_cap) {
+        std::lock_guard<std::recursive_mutex> g(c->mu);
+        dev_free(c, d_map);
+        map_cap = std::max(map.size(), 2 * map_cap);
+        if (dev_alloc(c, sizeof(int2) * map_cap, d_map) != STAGE_OK) {
+            map_cap = 0;
+            return STAGE_ERR_NO_MEMORY;
+        }
+    }
     cudaError_t e = cudaMemcpyAsync(d_slots.p, gs.data(), sizeof(GroupSlot) * n, cudaMemcpyHostToDevice, stream);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(d_off.p, off.data(), sizeof(int) * off.size(), cudaMemcpyHostToDevice, stream);
+        e = cudaMemcpyAsync(d_map.p, map.data(), sizeof(int2) * map.size(), cudaMemcpyHostToDevice, stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
     if (e != cudaSuccess) return STAGE_ERR_CUDA;
     dirty = false;
@@ -325,17 +345,16 @@ stage_status Engine::rebuild()
 // changing, replayed from a captured CUDA graph once it has been stable.
 cudaError_t Engine::launch_steps(int steps)
 {
-    const int n = (int)active.size();
     const GroupSlot *ds = static_cast<const GroupSlot *>(d_slots.p);
-    const int *swap_off = static_cast<const int *>(d_off.p);
-    const int *sel_off = swap_off + (n + 1);
-    const int *ref_off = swap_off + 2 * (n + 1);
+    const int2 *map_swap = static_cast<const int2 *>(d_map.p);
+    const int2 *map_sel = map_swap + n_swap_blocks;
+    const int2 *map_ref = map_sel + n_sel_blocks;
     auto enqueue = [&]() {
         cudaError_t e = cudaSuccess;
         for (int k = 0; e == cudaSuccess && k < steps; k++) {
-            e = launch_group_swap(ds, swap_off, n, n_swap_blocks, maxK, stream);
-            if (e == cudaSuccess) e = launch_group_select(ds, sel_off, n, n_sel_blocks, stream);
-            if (e == cudaSuccess) e = launch_group_refresh(ds, ref_off, n, n_ref_blocks, maxK, stream);
+            e = launch_group_swap(ds, map_swap, n_swap_blocks, swap_smem, stream);
+            if (e == cudaSuccess) e = launch_group_select(ds, map_sel, n_sel_blocks, stream);
+            if (e == cudaSuccess) e = launch_group_refresh(ds, map_ref, n_ref_blocks, maxK, stream);
         }
         return e;
     };
@@ -482,7 +501,7 @@ void engine_destroy(stage_ctx *c)
     }
     if (E->graph) cudaGraphExecDestroy(E->graph);
     dev_free(c, E->d_slots);
-    dev_free(c, E->d_off);
+    dev_free(c, E->d_map);
     dev_free(c, E->d_states);
     if (E->h_states) cudaFreeHost(E->h_states);
     if (E->stream) cudaStreamDestroy(E->stream);

@@ -1,7 +1,8 @@
 // sm_103a kernels of the staging engine: cost table, ranking, evaluation and
 // the Tabu loop (per-mission best/second-best, swap neighbourhood, move
-// selection, incremental refresh).  Integer arithmetic throughout; float64 only
-// for the one square root per leg.
+// selection, incremental refresh).  Integer arithmetic throughout; the only
+// floating point is a float32 first guess of each leg's square root, corrected
+// to the exact integer.
 #include <cuda_runtime.h>
 #include <climits>
 #include <cstdlib>
@@ -18,16 +19,21 @@ int swap_segment_for(int M_pad, int nC, int K);
 // helpers
 // --------------------------------------------------------------------------
 
-// Leg cost (Sec. 3; Euclidean in place of Eq. 1): ceil of the correctly rounded
-// float64 square root of the exact squared distance.  |coord| <= 2^24 keeps the
-// square below 2^52, where int64 -> float64 is exact and the ceiling of the
-// rounded root equals the exact integer ceiling.
+// Leg cost (Sec. 3; Euclidean in place of Eq. 1): the ceiling of the square
+// root of the exact squared distance n.  |coord| <= 2^24 keeps n below 2^52,
+// where the ceiling of the correctly rounded float64 root is exactly the
+// integer ceiling square root; that integer is computed here without float64
+// (GB300's float64 rate is low): a float32 estimate, then integer steps to the
+// exact floor root s (s^2 <= n < (s+1)^2), then s + [s^2 != n].
 __device__ __forceinline__ int32_t leg_ceil(int x1, int y1, int x2, int y2)
 {
-    long long dx = (long long)x1 - (long long)x2;
-    long long dy = (long long)y1 - (long long)y2;
-    double r = __dsqrt_rn(__ll2double_rn(dx * dx + dy * dy));
-    return (int32_t)ceil(r);
+    const long long dx = (long long)x1 - (long long)x2;
+    const long long dy = (long long)y1 - (long long)y2;
+    const long long n = dx * dx + dy * dy;
+    long long s = (long long)__fsqrt_rn((float)n);   // within a few units of sqrt(n)
+    while (s * s > n) --s;
+    while ((s + 1) * (s + 1) <= n) ++s;
+    return (int32_t)(s + (s * s != n ? 1 : 0));
 }
 
 __device__ __forceinline__ int warp_sum_i(int v)
@@ -1167,7 +1173,7 @@ k_swap_stream(TabuBuffers w, const int32_t *__restrict__ cost, int ignore_done)
 // not by deeper per-thread batches.  Same clamped thresholds and
 // warp-aggregated accumulation as the streaming form.
 // --------------------------------------------------------------------------
-constexpr int kDirJ = 16;
+constexpr int kDirJ = 16;      // default candidate rows per block
 constexpr int kDirThreads = 256;
 
 // Hit path of one row for one warp: called (out of line, so the kernel body
@@ -1313,7 +1319,7 @@ k_swap_direct(TabuBuffers w, const int32_t *__restrict__ cost, int ignore_done, 
 // rare.  A measured choice (stage_autotune) overrides it per shape bucket.
 int swap_segment_heuristic(int M_pad, int nC)
 {
-    const int chunks = (nC + kDirJ - 1) / kDirJ;
+    const int chunks = (nC + kDirJ - 1) / kDirJ;   // judged at the default 16 rows per block
     const long long target = 2ll * 4 * (g_num_sms > 0 ? g_num_sms : 152);
     int seg = 16384;
     while (seg > 1024 && (long long)((M_pad + seg - 1) / seg) * chunks < target) seg >>= 1;
@@ -1698,7 +1704,7 @@ cudaError_t launch_export_best_two(const TabuBuffers &w, const int *perm, int32_
     return cudaGetLastError();
 }
 
-__global__ void k_group_swap(const GroupSlot *__restrict__ slots, const int *__restrict__ off, int n);
+__global__ void k_group_swap(const GroupSlot *__restrict__ slots, const int2 *__restrict__ map);
 
 cudaError_t kernels_init()
 {
@@ -1708,11 +1714,9 @@ cudaError_t kernels_init()
     e = cudaFuncSetAttribute(k_swap_stream, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)swap_stream_smem(kPipeMaxK));
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_swap_direct, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(kPipeMaxK * kDirJ * 12));
+    e = cudaFuncSetAttribute(k_swap_direct, cudaFuncAttributeMaxDynamicSharedMemorySize, 48 * 1024);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_group_swap, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(kGroupMaxK * kDirJ * 12));
+    e = cudaFuncSetAttribute(k_group_swap, cudaFuncAttributeMaxDynamicSharedMemorySize, 48 * 1024);
     if (e != cudaSuccess) return e;
     if (const char *v = getenv("STAGE_SWAP_VARIANT")) g_swap_variant = atoi(v);
     int dev = 0, n = 0;
@@ -1731,11 +1735,28 @@ cudaError_t kernels_init()
 // returns at once.
 // --------------------------------------------------------------------------
 
-int group_swap_blocks(int M_pad, int nC, int K, int *bx, int *seg)
+// seg_override > 0: the batch's common segment (a whole batch fills the GPU
+// with far fewer, larger blocks than each instance would want alone).
+int group_swap_blocks(int M_pad, int nC, int K, int seg_override, int *bx, int *seg)
 {
-    *seg = swap_segment_for(M_pad, nC, K);
+    *seg = seg_override > 0 ? seg_override : swap_segment_for(M_pad, nC, K);
     *bx = (M_pad + *seg - 1) / *seg;
     return nC > 0 ? *bx * ((nC + kDirJ - 1) / kDirJ) : 0;
+}
+
+// The largest power-of-two segment in [1024, 16384] for which the whole batch
+// still has two waves of blocks; 0 when even 1024 leaves the GPU short (then
+// every slot keeps its own choice).
+int group_common_segment(const int *M_pad, const int *nC, int n)
+{
+    const long long target = 2ll * 4 * (g_num_sms > 0 ? g_num_sms : 152);
+    for (int seg = 16384; seg >= 1024; seg >>= 1) {
+        long long total = 0;
+        for (int k = 0; k < n; k++)
+            if (nC[k] > 0) total += (long long)((M_pad[k] + seg - 1) / seg) * ((nC[k] + kDirJ - 1) / kDirJ);
+        if (total >= target) return seg;
+    }
+    return 0;
 }
 
 int group_ref_blocks(int M_pad)
@@ -1744,83 +1765,69 @@ int group_ref_blocks(int M_pad)
     return g < 64 ? g : 64;
 }
 
-// largest i with off[i] <= b (off[0] = 0, off[n] = total)
-__device__ __forceinline__ int find_slot(const int *__restrict__ off, int n, int b)
-{
-    int lo = 0, hi = n - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (off[mid] <= b) lo = mid;
-        else hi = mid - 1;
-    }
-    return lo;
-}
-
+// Copy one slot descriptor into shared memory, one 4-byte word per thread.
 __device__ __forceinline__ void load_slot(const GroupSlot *slots, int slot, GroupSlot &dst)
 {
-    if (threadIdx.x == 0) dst = slots[slot];
+    static_assert(sizeof(GroupSlot) % 4 == 0, "slot descriptor must be word-sized");
+    constexpr int words = sizeof(GroupSlot) / 4;
+    const int *src = reinterpret_cast<const int *>(slots + slot);
+    int *d = reinterpret_cast<int *>(&dst);
+    for (int k = threadIdx.x; k < words; k += blockDim.x) d[k] = __ldg(src + k);
     __syncthreads();
 }
 
+// map[b] = (slot, block within the slot) for every block of a grouped launch.
 __global__ void __launch_bounds__(kDirThreads, 4)
-k_group_swap(const GroupSlot *__restrict__ slots, const int *__restrict__ off, int n)
+k_group_swap(const GroupSlot *__restrict__ slots, const int2 *__restrict__ map)
 {
     __shared__ GroupSlot g;
-    __shared__ int s_slot;
-    if (threadIdx.x == 0) s_slot = find_slot(off, n, blockIdx.x);
-    __syncthreads();
-    load_slot(slots, s_slot, g);
+    const int2 e = map[blockIdx.x];
+    load_slot(slots, e.x, g);
     const TabuDevState *st = g.w.st;
     if (st->done || st->t >= st->t_end) return;
-    const int local = blockIdx.x - off[s_slot];
-    swap_direct_body(g.w, g.cost, local % g.swap_bx, local / g.swap_bx, g.swap_seg);
+    swap_direct_body(g.w, g.cost, e.y % g.swap_bx, e.y / g.swap_bx, g.swap_seg);
 }
 
-cudaError_t launch_group_swap(const GroupSlot *slots, const int *swap_off, int n, int total_blocks, int maxK,
+cudaError_t launch_group_swap(const GroupSlot *slots, const int2 *map, int total_blocks, size_t smem,
                               cudaStream_t s)
 {
-    if (total_blocks <= 0 || n <= 0) return cudaSuccess;
-    k_group_swap<<<total_blocks, kDirThreads, (size_t)maxK * kDirJ * 12, s>>>(slots, swap_off, n);
+    if (total_blocks <= 0) return cudaSuccess;
+    k_group_swap<<<total_blocks, kDirThreads, smem, s>>>(slots, map);
     return cudaGetLastError();
 }
 
 __global__ void __launch_bounds__(kSelectThreads) k_group_select(const GroupSlot *__restrict__ slots,
-                                                                const int *__restrict__ off, int n)
+                                                                const int2 *__restrict__ map)
 {
     __shared__ GroupSlot g;
-    __shared__ int s_slot;
-    if (threadIdx.x == 0) s_slot = find_slot(off, n, blockIdx.x);
-    __syncthreads();
-    load_slot(slots, s_slot, g);
+    const int2 e = map[blockIdx.x];
+    load_slot(slots, e.x, g);
     TabuDevState *st = g.w.st;
     if (st->done || st->t >= st->t_end) return;
-    select_body(g.w, blockIdx.x - off[s_slot], g.sel_blocks);
+    select_body(g.w, e.y, g.sel_blocks);
 }
 
-cudaError_t launch_group_select(const GroupSlot *slots, const int *sel_off, int n, int total_blocks,
-                                cudaStream_t s)
+cudaError_t launch_group_select(const GroupSlot *slots, const int2 *map, int total_blocks, cudaStream_t s)
 {
-    if (n <= 0 || total_blocks <= 0) return cudaSuccess;
-    k_group_select<<<total_blocks, kSelectThreads, 0, s>>>(slots, sel_off, n);
+    if (total_blocks <= 0) return cudaSuccess;
+    k_group_select<<<total_blocks, kSelectThreads, 0, s>>>(slots, map);
     return cudaGetLastError();
 }
 
 __global__ void __launch_bounds__(256) k_group_refresh(const GroupSlot *__restrict__ slots,
-                                                       const int *__restrict__ off, int n)
+                                                       const int2 *__restrict__ map)
 {
     __shared__ GroupSlot g;
-    __shared__ int s_slot;
-    if (threadIdx.x == 0) s_slot = find_slot(off, n, blockIdx.x);
-    __syncthreads();
-    load_slot(slots, s_slot, g);
-    refresh_body(g.w, g.cost, blockIdx.x - off[s_slot], g.ref_blocks);
+    const int2 e = map[blockIdx.x];
+    load_slot(slots, e.x, g);
+    refresh_body(g.w, g.cost, e.y, g.ref_blocks);
 }
 
-cudaError_t launch_group_refresh(const GroupSlot *slots, const int *ref_off, int n, int total_blocks, int maxK,
+cudaError_t launch_group_refresh(const GroupSlot *slots, const int2 *map, int total_blocks, int maxK,
                                  cudaStream_t s)
 {
-    if (total_blocks <= 0 || n <= 0) return cudaSuccess;
-    k_group_refresh<<<total_blocks, 256, (size_t)maxK * 16, s>>>(slots, ref_off, n);
+    if (total_blocks <= 0) return cudaSuccess;
+    k_group_refresh<<<total_blocks, 256, (size_t)maxK * 16, s>>>(slots, map);
     return cudaGetLastError();
 }
 

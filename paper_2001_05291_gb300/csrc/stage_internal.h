@@ -110,7 +110,7 @@ cudaError_t kernels_init();   // one-time function attributes (dynamic shared me
 
 // ------------------------------------------------------- grouped (batched) launches
 // One descriptor per active slot of the batch engine; one launch covers all of
-// them.  Blocks map to (slot, local block) through prefix offsets.
+// them.  Each launch gets a block map: (slot, block within the slot) per block.
 struct GroupSlot {
     TabuBuffers w;
     const int32_t *cost;
@@ -122,7 +122,8 @@ struct GroupSlot {
     int pad;
 };
 constexpr int kGroupMaxK = 256;
-int group_swap_blocks(int M_pad, int nC, int K, int *bx, int *seg);
+int group_swap_blocks(int M_pad, int nC, int K, int seg_override, int *bx, int *seg);
+int group_common_segment(const int *M_pad, const int *nC, int n);
 int select_blocks(int K, int nC);
 // missions per block of the direct swap pass, per shape (measured choice or heuristic)
 int swap_segment_for(int M_pad, int nC, int K);
@@ -131,11 +132,10 @@ void swap_segment_record(int M_pad, int nC, int K, int seg);
 bool swap_segment_known(int M_pad, int nC, int K);
 cudaError_t launch_swap_direct_seg(const TabuBuffers &w, const int32_t *cost, int nC, int seg, cudaStream_t s);
 int group_ref_blocks(int M_pad);
-cudaError_t launch_group_swap(const GroupSlot *slots, const int *swap_off, int n, int total_blocks, int maxK,
+cudaError_t launch_group_swap(const GroupSlot *slots, const int2 *map, int total_blocks, size_t smem,
                               cudaStream_t s);
-cudaError_t launch_group_select(const GroupSlot *slots, const int *sel_off, int n, int total_blocks,
-                                cudaStream_t s);
-cudaError_t launch_group_refresh(const GroupSlot *slots, const int *ref_off, int n, int total_blocks, int maxK,
+cudaError_t launch_group_select(const GroupSlot *slots, const int2 *map, int total_blocks, cudaStream_t s);
+cudaError_t launch_group_refresh(const GroupSlot *slots, const int2 *map, int total_blocks, int maxK,
                                  cudaStream_t s);
 cudaError_t launch_gather_states(const GroupSlot *slots, int n, TabuDevState *out, cudaStream_t s);
 

@@ -296,3 +296,36 @@ def test_autotune_changes_no_result(ctx):
         assert tuned.moves == before.moves
     want = oracle.tabu(oracle_table(inst), inst.K, inst.R, 25, 3, nthreads=8)
     assert [tuple(m) for m in before.moves] == [tuple(m) for m in want.moves]
+
+
+def test_leg_special_values(ctx):
+    """Exact squares, squares +- 1 and the range extremes, through the table build:
+    each leg must be the exact integer ceiling square root (as the oracle's
+    float64 ceil(sqrt) is in this range)."""
+    import math
+    offs = []
+    for (p, q) in [(3, 4), (5, 12), (20, 21), (119, 120)]:
+        for k in (1, 1000, 99991):
+            offs.append((p * k, q * k))
+    for s in (1, 2, 7, 4096, 2**20 + 3, 2**24, 2**25 - 1):
+        offs.append((s, 1))                       # s^2 + 1
+    for k in (1, 3, 100, 2000, 2895):
+        offs.append((2 * k * k, 2 * k))            # (2k^2 + 1)^2 - 1
+    lim = 2**24
+    # base at the origin; pickup at the offset (clipped into range); drop-off at the base
+    pick = np.array([(max(-lim, min(lim, dx)), max(-lim, min(lim, dy))) for dx, dy in offs], dtype=np.int32)
+    base = np.array([[0, 0], [-lim, -lim]], dtype=np.int32)
+    drop = np.zeros_like(pick)
+    h = ctx.load_instance(base, pick, drop)
+    got = ctx.read_table(h, 0, 2, 0, len(offs))
+    for m, (x, y) in enumerate(pick.tolist()):
+        n0 = x * x + y * y
+        c0 = math.isqrt(n0) + (math.isqrt(n0) ** 2 != n0)
+        n1 = (x + lim) ** 2 + (y + lim) ** 2
+        c1 = math.isqrt(n1) + (math.isqrt(n1) ** 2 != n1)
+        pd = c0                                    # pickup -> drop-off (drop at origin)
+        assert got[0, m] == c0 + pd + 0
+        dn = lim * lim * 2
+        c2 = math.isqrt(dn) + (math.isqrt(dn) ** 2 != dn)
+        assert got[1, m] == c1 + pd + c2
+    ctx.unload_instance(h)
