@@ -1,0 +1,88 @@
+"""Parity at the benchmark's full sizes, in the launch configuration bench.py times.
+
+The oracle cannot run 1000 iterations on an 8 GB table in a test, so the checks
+are: the first moves against the oracle's own search on the full table (the
+trajectory of a longer run starts with the shorter run's), and sampled later
+moves plus the best placement against the oracle's evaluation of the placements
+the GPU reports.  All quantities are integers: zero tolerance.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2001_05291_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+THREADS = os.cpu_count() or 8
+
+
+@pytest.fixture(scope="module")
+def stage_mod():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2001_05291_gb300 import build, stage
+    build.build()
+    return stage
+
+
+def replay(start, moves):
+    """Placements after each move, from the start placement."""
+    O = [int(x) for x in start]
+    out = []
+    for (_, i, j, *_r) in moves:
+        O = [j if x == i else x for x in O]
+        out.append(list(O))
+    return out
+
+
+def test_large_workload_as_benchmarked(stage_mod):
+    stage = stage_mod
+    inst = synth.large()
+    cost = oracle.cost_table(inst.base_xy, inst.pick_xy, inst.drop_xy, THREADS)
+    with stage.Context(device=0) as ctx:
+        h = ctx.load_instance(inst.base_xy, inst.pick_xy, inst.drop_xy)
+        start, rowsum = ctx.rank_bases(h, inst.K, inst.B)
+        got = ctx.tabu_run(h, inst.K, inst.R, inst.iters, inst.tenure)
+        # sampled table windows (caller's mission order) against the oracle's table
+        key = synth.stream_key(2, 90)
+        u = synth.draws_u64(key, np.arange(64))
+        for k in range(0, 64, 2):
+            b, m = int(u[k] % np.uint64(inst.B - 4)), int(u[k + 1] % np.uint64(inst.M - 512))
+            assert np.array_equal(ctx.read_table(h, b, 4, m, 512), cost[b:b + 4, m:m + 512])
+    assert got.n_moves == inst.iters
+    wo, wrs = oracle.rank(cost, inst.K)
+    assert np.array_equal(start, wo) and np.array_equal(rowsum, wrs)
+    ref = oracle.tabu(cost, inst.K, inst.R, 2, inst.tenure, nthreads=THREADS)
+    assert [tuple(m) for m in got.moves[:2]] == [tuple(m) for m in ref.moves]
+    placements = replay(start, got.moves)
+    for t in (2, 100, 500, inst.iters - 1):
+        assert oracle.evaluate(cost, placements[t], inst.R) == (got.moves[t][4], got.moves[t][5])
+    assert oracle.evaluate(cost, got.best_open, inst.R) == (got.best_cov, got.best_dist)
+    assert sorted(placements[-1]) == got.final_open.tolist()
+
+
+def test_batched_workload_instances_in_one_batch(stage_mod):
+    stage = stage_mod
+    sizes = synth.batched_sizes()
+    # the largest, the smallest and a spread of the 512 instances, at their full sizes
+    order = np.argsort([(B - K) * M for B, M, K, R in sizes])
+    pick = [int(order[-1]), int(order[0]), int(order[128]), int(order[256]), int(order[384]), int(order[500])]
+    insts = [synth.batched_instance(3, k, *sizes[k]) for k in pick]
+    with stage.Context(device=0, max_slots=512) as ctx:
+        hs = [ctx.load_instance(i.base_xy, i.pick_xy, i.drop_xy) for i in insts]
+        res = [t.wait() for t in ctx.batch_submit(
+            [dict(inst=h, K=i.K, R=i.R, iters=i.iters, tenure=i.tenure) for h, i in zip(hs, insts)])]
+        starts = [ctx.rank_bases(h, i.K)[0] for h, i in zip(hs, insts)]
+    for inst, r, start in zip(insts, res, starts):
+        assert r.n_moves == inst.iters
+        cost = oracle.cost_table(inst.base_xy, inst.pick_xy, inst.drop_xy, THREADS)
+        ref = oracle.tabu(cost, inst.K, inst.R, 12, inst.tenure, nthreads=THREADS)
+        assert [tuple(m) for m in r.moves[:12]] == [tuple(m) for m in ref.moves]
+        placements = replay(start, r.moves)
+        for t in (50, inst.iters - 1):
+            assert oracle.evaluate(cost, placements[t], inst.R) == (r.moves[t][4], r.moves[t][5])
+        assert oracle.evaluate(cost, r.best_open, inst.R) == (r.best_cov, r.best_dist)
