@@ -309,7 +309,7 @@ stage_status Engine::rebuild()
         gs[k].cost = sl.in->cost;
         gs[k].swap_blocks =
             group_swap_blocks(sl.tb.M_pad, sl.nC, sl.tb.K, common, &gs[k].swap_bx, &gs[k].swap_seg);
-        swap_smem = std::max(swap_smem, (size_t)sl.tb.K * 16 * 12);
+        swap_smem = std::max(swap_smem, swap_direct_smem(sl.tb.K));
         gs[k].sel_blocks = select_blocks(sl.tb.K, sl.nC);
         gs[k].ref_blocks = group_ref_blocks(sl.tb.M_pad);
         for (int b = 0; b < gs[k].swap_blocks; b++) map.push_back(make_int2(k, b));

@@ -36,6 +36,14 @@ __device__ __forceinline__ int32_t leg_ceil(int x1, int y1, int x2, int y2)
     return (int32_t)(s + (s * s != n ? 1 : 0));
 }
 
+// L2 cache policy for data read once per pass: evict it before other lines.
+__device__ __forceinline__ unsigned long long evict_first_policy()
+{
+    unsigned long long p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+
 __device__ __forceinline__ int warp_sum_i(int v)
 {
 #pragma unroll
@@ -898,12 +906,6 @@ __device__ __forceinline__ void bulk_load(void *dst, const void *src, unsigned b
         : "memory");
 }
 
-__device__ __forceinline__ unsigned long long evict_first_policy()
-{
-    unsigned long long p;
-    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
-    return p;
-}
 
 __device__ __forceinline__ void consumer_sync()
 {
@@ -1173,8 +1175,16 @@ k_swap_stream(TabuBuffers w, const int32_t *__restrict__ cost, int ignore_done)
 // not by deeper per-thread batches.  Same clamped thresholds and
 // warp-aggregated accumulation as the streaming form.
 // --------------------------------------------------------------------------
-constexpr int kDirJ = 16;      // default candidate rows per block
+constexpr int kDirJ = 16;      // candidate rows per block
+constexpr int kStages = 2;     // batches of 4 rows in flight per thread
+
 constexpr int kDirThreads = 256;
+// Dynamic shared memory of the direct swap pass: [K][J] accumulators, then the
+// per-thread staging slots.
+size_t swap_direct_smem(int K)
+{
+    return (size_t)K * kDirJ * 12 + 16 + (size_t)kStages * 4 * kDirThreads * 16;
+}
 
 // Hit path of one row for one warp: called (out of line, so the kernel body
 // stays small enough for the instruction cache) only when some lane of the
@@ -1254,39 +1264,78 @@ __device__ __forceinline__ void swap_direct_body(const TabuBuffers &w, const int
     const int nrows = min(kDirJ, nC - c0);
     const int m_begin = bx * seg;
     const int m_end = min(m_begin + seg, w.M_pad);
-    // Warp-uniform trip count: every lane of a warp runs every iteration (the
-    // warp-collective reductions in dir_row need all 32 lanes); lanes past the
-    // segment end see thresholds that nothing can beat.
+    // Table loads are staged through shared memory with per-thread async
+    // copies (cp.async, L2 only), kStages batches of 4 rows ahead, so they keep
+    // streaming while the warp works on hits.  Each thread reads back only the
+    // slots it copied into, after waiting on its own copy groups.  Every lane of
+    // a warp runs every batch (the warp-collective calls in dir_row need all 32
+    // lanes); lanes past the segment end see thresholds nothing can beat.
+    int4 *stg = reinterpret_cast<int4 *>(ex_c + K * kDirJ + ((K * kDirJ) & 3 ? 4 - ((K * kDirJ) & 3) : 0));
     const int wbase = 4 * (threadIdx.x & ~31);
-    for (int mw = m_begin + wbase; mw < m_end; mw += 4 * kDirThreads) {
-        const int m = mw + 4 * lane;
-        const bool act = m < m_end;
-        const int q = act ? (m >> 2) : 0;
-        int4 ap = __ldg(reinterpret_cast<const int4 *>(w.a) + q);
-        int4 bp = __ldg(reinterpret_cast<const int4 *>(w.b) + q);
-        const uint2 sp = __ldg(reinterpret_cast<const uint2 *>(w.s1) + q);
-        ap.x = min(ap.x, R + 1); ap.y = min(ap.y, R + 1); ap.z = min(ap.z, R + 1); ap.w = min(ap.w, R + 1);
-        bp.x = min(bp.x, R + 1); bp.y = min(bp.y, R + 1); bp.z = min(bp.z, R + 1); bp.w = min(bp.w, R + 1);
-        if (!act) bp = make_int4(INT_MIN, INT_MIN, INT_MIN, INT_MIN);
-        const int s0 = (int)(int16_t)(sp.x & 0xffff), s1 = (int)(int16_t)(sp.x >> 16);
-        const int s2 = (int)(int16_t)(sp.y & 0xffff), s3 = (int)(int16_t)(sp.y >> 16);
-        const bool uni = (s0 == s1) && (s1 == s2) && (s2 == s3);
-#pragma unroll 1
-        for (int h = 0; h < kDirJ; h += 4) {
-            int4 x[4];
+    const int first = m_begin + wbase;
+    const int npass = first < m_end ? (m_end - first + 4 * kDirThreads - 1) / (4 * kDirThreads) : 0;
+    const int nbatch = npass * (kDirJ / 4);
+    // the table streams through once per iteration: evict it first from L2, so
+    // the per-mission thresholds (re-read by every row chunk) stay resident
+    const unsigned long long policy = evict_first_policy();
+    auto issue = [&](int i) {
+        const int p = i / (kDirJ / 4), h = (i % (kDirJ / 4)) * 4;
+        const int m = first + p * 4 * kDirThreads + 4 * lane;
+        if (m < m_end) {
+            const int q = m >> 2;
 #pragma unroll
             for (int r = 0; r < 4; r++)
-                x[r] = (act && h + r < nrows)
-                           ? __ldcs(reinterpret_cast<const int4 *>(cost + (size_t)rows[h + r] * M_pad) + q)
-                           : make_int4(INT_MAX, INT_MAX, INT_MAX, INT_MAX);
+                if (h + r < nrows) {
+                    const int4 *src = reinterpret_cast<const int4 *>(cost + (size_t)rows[h + r] * M_pad) + q;
+                    const unsigned dst = (unsigned)__cvta_generic_to_shared(&stg[((i % kStages) * 4 + r) * kDirThreads + threadIdx.x]);
+                    asm volatile("cp.async.cg.shared.global.L2::cache_hint [%0], [%1], 16, %2;" ::"r"(dst), "l"(src),
+                                 "l"(policy)
+                                 : "memory");
+                }
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+#pragma unroll 1
+    for (int i = 0; i < kStages - 1; i++) {
+        if (i < nbatch) issue(i);
+        else asm volatile("cp.async.commit_group;" ::: "memory");
+    }
+    int4 ap = make_int4(0, 0, 0, 0), bp = make_int4(INT_MIN, INT_MIN, INT_MIN, INT_MIN);
+    int s0 = 0, s1 = 0, s2 = 0, s3 = 0;
+    bool uni = false, act = false;
+#pragma unroll 1
+    for (int b = 0; b < nbatch; b++) {
+        if (b + kStages - 1 < nbatch) issue(b + kStages - 1);
+        else asm volatile("cp.async.commit_group;" ::: "memory");
+        const int hb = b % (kDirJ / 4), h = hb * 4;
+        if (hb == 0) {
+            const int m = first + (b / (kDirJ / 4)) * 4 * kDirThreads + 4 * lane;
+            act = m < m_end;
+            const int q = act ? (m >> 2) : 0;
+            ap = __ldg(reinterpret_cast<const int4 *>(w.a) + q);
+            bp = __ldg(reinterpret_cast<const int4 *>(w.b) + q);
+            const uint2 sp = __ldg(reinterpret_cast<const uint2 *>(w.s1) + q);
+            ap.x = min(ap.x, R + 1); ap.y = min(ap.y, R + 1); ap.z = min(ap.z, R + 1); ap.w = min(ap.w, R + 1);
+            bp.x = min(bp.x, R + 1); bp.y = min(bp.y, R + 1); bp.z = min(bp.z, R + 1); bp.w = min(bp.w, R + 1);
+            if (!act) bp = make_int4(INT_MIN, INT_MIN, INT_MIN, INT_MIN);
+            s0 = (int)(int16_t)(sp.x & 0xffff); s1 = (int)(int16_t)(sp.x >> 16);
+            s2 = (int)(int16_t)(sp.y & 0xffff); s3 = (int)(int16_t)(sp.y >> 16);
+            uni = (s0 == s1) && (s1 == s2) && (s2 == s3);
+        }
+        asm volatile("cp.async.wait_group %0;" ::"n"(kStages - 1) : "memory");
+        int4 x[4];
 #pragma unroll
-            for (int r = 0; r < 4; r++) {
-                const bool hit = x[r].x < bp.x || x[r].y < bp.y || x[r].z < bp.z || x[r].w < bp.w;
-                if (__any_sync(0xffffffffu, hit))
-                    dir_row(x[r], ap, bp, s0, s1, s2, s3, uni, h + r, R, ex_c, ex_d, g_c, g_d, lane);
-            }
+        for (int r = 0; r < 4; r++)
+            x[r] = (act && h + r < nrows) ? stg[((b % kStages) * 4 + r) * kDirThreads + threadIdx.x]
+                                          : make_int4(INT_MAX, INT_MAX, INT_MAX, INT_MAX);
+#pragma unroll
+        for (int r = 0; r < 4; r++) {
+            const bool hit = x[r].x < bp.x || x[r].y < bp.y || x[r].z < bp.z || x[r].w < bp.w;
+            if (__any_sync(0xffffffffu, hit))
+                dir_row(x[r], ap, bp, s0, s1, s2, s3, uni, h + r, R, ex_c, ex_d, g_c, g_d, lane);
         }
     }
+    asm volatile("cp.async.wait_all;" ::: "memory");
     __syncthreads();
     for (int k = threadIdx.x; k < K * kDirJ; k += blockDim.x) {
         const int r = k % kDirJ, sidx = k / kDirJ;
@@ -1361,13 +1410,15 @@ cudaError_t launch_swap_direct_seg(const TabuBuffers &w, const int32_t *cost, in
 {
     if (nC <= 0) return cudaSuccess;
     dim3 grid((w.M_pad + seg - 1) / seg, (nC + kDirJ - 1) / kDirJ);
-    k_swap_direct<<<grid, kDirThreads, (size_t)w.K * kDirJ * 12, s>>>(w, cost, 1, seg);
+    k_swap_direct<<<grid, kDirThreads, swap_direct_smem(w.K), s>>>(w, cost, 1, seg);
     return cudaGetLastError();
 }
 
 // Swap-evaluation variant: 0 = direct (default), 1 = streaming pipeline,
 // 2 = the plain per-element form.  STAGE_SWAP_VARIANT overrides (tuning).
 static int g_swap_variant = 0;
+
+bool swap_variant_default() { return g_swap_variant == 0; }
 
 
 size_t swap_stream_smem(int K)
@@ -1383,7 +1434,7 @@ cudaError_t launch_swap_eval(const TabuBuffers &w, const int32_t *cost, int nC, 
     if (g_swap_variant == 0 && w.K <= kPipeMaxK) {
         const int seg = swap_segment_for(w.M_pad, nC, w.K);
         dim3 grid((w.M_pad + seg - 1) / seg, (nC + kDirJ - 1) / kDirJ);
-        k_swap_direct<<<grid, kDirThreads, (size_t)w.K * kDirJ * 12, s>>>(w, cost, ignore_done, seg);
+        k_swap_direct<<<grid, kDirThreads, swap_direct_smem(w.K), s>>>(w, cost, ignore_done, seg);
         return cudaGetLastError();
     }
     if (g_swap_variant == 1 && w.K <= kPipeMaxK && nC <= kPipeMaxCand && g_num_sms > 0) {
@@ -1697,6 +1748,46 @@ __global__ void k_export_best_two(TabuBuffers w, const int *__restrict__ perm, i
     }
 }
 
+// --------------------------------------------------------------------------
+// Small instances: the whole search in one resident block.  Each iteration
+// runs every swap tile, the selection and the refresh back to back, separated
+// by block barriers, so a search costs one launch instead of three per
+// iteration.  Same bodies, same arithmetic, same results as the multi-kernel
+// path.
+// --------------------------------------------------------------------------
+constexpr long long kSmallElems = 1ll << 18;   // (candidates) x (padded missions)
+
+bool tabu_small_fits(int nC, int M_pad, int K)
+{
+    return (long long)nC * M_pad <= kSmallElems && K <= kPipeMaxK;
+}
+
+__global__ void __launch_bounds__(kDirThreads) k_tabu_small(TabuBuffers w, const int32_t *__restrict__ cost,
+                                                            int iters)
+{
+    TabuDevState *st = w.st;
+    const int seg = ((w.M_pad + 1023) / 1024) * 1024;   // one segment covers every mission
+    for (int it = 0; it < iters; it++) {
+        if (st->done || st->t >= st->t_end) break;
+        const int nC = st->nC;
+        for (int by = 0; by * kDirJ < nC; by++) {
+            swap_direct_body(w, cost, 0, by, seg);
+            __syncthreads();
+        }
+        select_body(w, 0, 1);
+        __syncthreads();
+        refresh_body(w, cost, 0, 1);
+        __syncthreads();
+    }
+}
+
+cudaError_t launch_tabu_small(const TabuBuffers &w, const int32_t *cost, int iters, cudaStream_t s)
+{
+    const size_t sm = swap_direct_smem(w.K) > (size_t)w.K * 16 ? swap_direct_smem(w.K) : (size_t)w.K * 16;
+    k_tabu_small<<<1, kDirThreads, sm, s>>>(w, cost, iters);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_export_best_two(const TabuBuffers &w, const int *perm, int32_t *a, int32_t *b,
                                    int32_t *b1, int32_t *b2, cudaStream_t s)
 {
@@ -1705,6 +1796,7 @@ cudaError_t launch_export_best_two(const TabuBuffers &w, const int *perm, int32_
 }
 
 __global__ void k_group_swap(const GroupSlot *__restrict__ slots, const int2 *__restrict__ map);
+__global__ void k_tabu_small(TabuBuffers w, const int32_t *__restrict__ cost, int iters);
 
 cudaError_t kernels_init()
 {
@@ -1714,9 +1806,14 @@ cudaError_t kernels_init()
     e = cudaFuncSetAttribute(k_swap_stream, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)swap_stream_smem(kPipeMaxK));
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_swap_direct, cudaFuncAttributeMaxDynamicSharedMemorySize, 48 * 1024);
+    e = cudaFuncSetAttribute(k_swap_direct, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)swap_direct_smem(kPipeMaxK));
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_group_swap, cudaFuncAttributeMaxDynamicSharedMemorySize, 48 * 1024);
+    e = cudaFuncSetAttribute(k_tabu_small, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)swap_direct_smem(kPipeMaxK));
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_group_swap, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)swap_direct_smem(kGroupMaxK));
     if (e != cudaSuccess) return e;
     if (const char *v = getenv("STAGE_SWAP_VARIANT")) g_swap_variant = atoi(v);
     int dev = 0, n = 0;

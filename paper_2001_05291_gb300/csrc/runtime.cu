@@ -20,6 +20,8 @@ using namespace stg;
 
 namespace stg_rt {
 
+constexpr int kGraphIters = 16;   // iterations per captured graph of a single search
+
 struct Guard {
     stage_ctx *c;
     bool locked;
@@ -424,15 +426,58 @@ stage_status run_tabu(stage_ctx *c, Instance *in, const stage_tabu_params *p,
     }
     CK(timed(c, "begin", 1, [&] { return launch_begin(tb, rs ? 1 : 0, c->stream); }));
     volatile int *done_flag = static_cast<volatile int *>(c->pinned);
-    for (int it = 0; it < iters && nC > 0; it++) {
-        CK(timed(c, "swap_eval", 1, [&] { return launch_swap_eval(tb, in->cost, nC, 0, c->stream); }));
-        CK(timed(c, "select", 1, [&] { return launch_select(tb, nC, c->stream); }));
-        CK(timed(c, "refresh", 1, [&] { return launch_refresh(tb, in->cost, c->stream); }));
-        // the improving-only rule usually stops early: poll the device flag now and then
-        if (!p->accept_worsening && (it & 31) == 31) {
-            CK(cudaMemcpyAsync(c->pinned, &tb.st->done, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
-            CK(cudaStreamSynchronize(c->stream));
-            if (*done_flag) break;
+    const bool profiling = (c->flags & STAGE_PROFILE) != 0;
+    if (nC > 0 && iters > 0 && tabu_small_fits(nC, in->M_pad, K) && swap_variant_default()) {
+        // small instance: the whole search in one resident block
+        CK(timed(c, "tabu_small", 1, [&] { return launch_tabu_small(tb, in->cost, iters, c->stream); }));
+    } else if (nC > 0 && iters >= kGraphIters && !profiling) {
+        // replay kGraphIters iterations at a time from a CUDA graph
+        cudaGraph_t gr = nullptr;
+        cudaGraphExec_t ge = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
+        for (int k = 0; e == cudaSuccess && k < kGraphIters; k++) {
+            e = launch_swap_eval(tb, in->cost, nC, 0, c->stream);
+            if (e == cudaSuccess) e = launch_select(tb, nC, c->stream);
+            if (e == cudaSuccess) e = launch_refresh(tb, in->cost, c->stream);
+        }
+        cudaError_t e2 = cudaStreamEndCapture(c->stream, &gr);
+        if (e == cudaSuccess) e = e2;
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&ge, gr, 0);
+        if (gr) cudaGraphDestroy(gr);
+        if (e != cudaSuccess) {
+            if (ge) cudaGraphExecDestroy(ge);
+            return set_err(c, STAGE_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(e));
+        }
+        int it = 0;
+        for (; it + kGraphIters <= iters; it += kGraphIters) {
+            for (const char *nm : {"swap_eval", "select", "refresh"}) c->stats[nm].launches += kGraphIters;
+            e = cudaGraphLaunch(ge, c->stream);
+            if (e != cudaSuccess) break;
+            if (!p->accept_worsening && ((it / kGraphIters) & 1)) {
+                e = cudaMemcpyAsync(c->pinned, &tb.st->done, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+                if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+                if (e != cudaSuccess || *done_flag) break;
+            }
+        }
+        cudaGraphExecDestroy(ge);
+        CK(e);
+        // the remaining iterations (iterations past the budget do nothing)
+        for (; it < iters && !(!p->accept_worsening && *done_flag); it++) {
+            CK(timed(c, "swap_eval", 1, [&] { return launch_swap_eval(tb, in->cost, nC, 0, c->stream); }));
+            CK(timed(c, "select", 1, [&] { return launch_select(tb, nC, c->stream); }));
+            CK(timed(c, "refresh", 1, [&] { return launch_refresh(tb, in->cost, c->stream); }));
+        }
+    } else {
+        for (int it = 0; it < iters && nC > 0; it++) {
+            CK(timed(c, "swap_eval", 1, [&] { return launch_swap_eval(tb, in->cost, nC, 0, c->stream); }));
+            CK(timed(c, "select", 1, [&] { return launch_select(tb, nC, c->stream); }));
+            CK(timed(c, "refresh", 1, [&] { return launch_refresh(tb, in->cost, c->stream); }));
+            // the improving-only rule usually stops early: poll the device flag now and then
+            if (!p->accept_worsening && (it & 31) == 31) {
+                CK(cudaMemcpyAsync(c->pinned, &tb.st->done, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+                CK(cudaStreamSynchronize(c->stream));
+                if (*done_flag) break;
+            }
         }
     }
     if (exp_a) {

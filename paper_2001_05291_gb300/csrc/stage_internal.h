@@ -124,6 +124,10 @@ struct GroupSlot {
 constexpr int kGroupMaxK = 256;
 int group_swap_blocks(int M_pad, int nC, int K, int seg_override, int *bx, int *seg);
 int group_common_segment(const int *M_pad, const int *nC, int n);
+size_t swap_direct_smem(int K);   // dynamic shared memory of the direct swap pass
+bool tabu_small_fits(int nC, int M_pad, int K);
+bool swap_variant_default();   // the direct swap pass is selected (STAGE_SWAP_VARIANT unset or 0)
+cudaError_t launch_tabu_small(const TabuBuffers &w, const int32_t *cost, int iters, cudaStream_t s);
 int select_blocks(int K, int nC);
 // missions per block of the direct swap pass, per shape (measured choice or heuristic)
 int swap_segment_for(int M_pad, int nC, int K);

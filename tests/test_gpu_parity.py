@@ -329,3 +329,24 @@ def test_leg_special_values(ctx):
         c2 = math.isqrt(dn) + (math.isqrt(dn) ** 2 != dn)
         assert got[1, m] == c1 + pd + c2
     ctx.unload_instance(h)
+
+
+def test_graph_replay_and_small_block_paths():
+    """Without profiling, single searches replay 16-iteration CUDA graphs (large
+    instances) or run in one resident block (small ones); both equal the oracle,
+    also for an iteration count that is not a multiple of 16 and for the
+    improving-only rule that stops early."""
+    from paper_2001_05291_gb300 import stage
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    with stage.Context(device=0) as c2:
+        for inst, iters, aw in ((small(61, 70, 12000, 8), 45, True), (small(62, 70, 12000, 8), 200, False),
+                                (synth.tiny(), 37, True), (small(63, 12, 900, 3), 50, False)):
+            h = load(c2, inst)
+            got = c2.tabu_run(h, inst.K, inst.R, iters, inst.tenure, accept_worsening=aw)
+            want = oracle.tabu(oracle_table(inst), inst.K, inst.R, iters, inst.tenure, accept_worsening=aw,
+                               nthreads=8)
+            assert [tuple(m) for m in got.moves] == [tuple(m) for m in want.moves]
+            assert (got.best_cov, got.best_dist, got.best_iter) == (want.best_cov, want.best_dist, want.best_iter)
+            c2.unload_instance(h)
