@@ -128,6 +128,26 @@ def test_swap_neighbourhood(ctx, B, M, K):
     ctx.unload_instance(h)
 
 
+def test_swap_large_costs_near_range(ctx):
+    """Costs spread up to about 2.5e7 m with R around 2^24, so that many terms
+    near R (the largest values the per-block sums carry) occur: the
+    neighbourhood table and a Tabu trajectory equal the oracle."""
+    rng = np.random.default_rng(2024)
+    B, M, K = 40, 6000, 6
+    base = rng.integers(0, 6_000_000, size=(B, 2), dtype=np.int64).astype(np.int32)
+    pick = rng.integers(0, 6_000_000, size=(M, 2), dtype=np.int64).astype(np.int32)
+    drop = rng.integers(0, 6_000_000, size=(M, 2), dtype=np.int64).astype(np.int32)
+    h = ctx.load_instance(base, pick, drop)
+    cost = oracle.cost_table(base, pick, drop, 8)
+    open_, _ = oracle.rank(cost, K)
+    for R in ((1 << 24) - 3, (1 << 24) - 2, (1 << 24) - 1, 1 << 24):
+        assert ((cost >= R - 2_000_000) & (cost <= R)).any()
+        check_swaps(ctx, h, cost, open_, R)
+    for R in ((1 << 24) - 2, (1 << 24) - 1):
+        check_tabu(ctx, h, cost, K, R, 25, 4)
+    ctx.unload_instance(h)
+
+
 def test_swap_neighbourhood_unavailable(ctx):
     inst = small(5, 25, 3000, 6)
     avail = np.ones(inst.B, dtype=np.uint8)
