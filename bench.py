@@ -51,7 +51,7 @@ def parse_args():
     ap.add_argument("--slots", type=int, default=512, help="batched / serving: engine slots")
     ap.add_argument("--duration", type=float, default=20.0, help="serving: seconds of arrivals")
     ap.add_argument("--rate", type=float, default=200.0, help="serving: arrivals per second")
-    ap.add_argument("--no-plain", action="store_true", help="batched: skip the one-launch-per-instance pass")
+    ap.add_argument("--no-plain", action="store_true", help="batched / serving: skip the plain-path pass")
     ap.add_argument("--missions", type=int, default=0,
                     help="override M of the large workload (smaller profiling cases)")
     ap.add_argument("--e2e-steps", type=int, default=2)
@@ -408,12 +408,18 @@ def run_batched(args):
     for h, i in list(zip(hs, insts))[:8]:
         ctx.tabu_run(h, i.K, i.R, i.iters, i.tenure, trajectory=False)
     torch.cuda.synchronize()
+    ctx.reset_stats()
     clocks = ClockSampler(local)
     clocks.start()
     t0 = time.perf_counter()
     res = [t.wait() for t in ctx.batch_submit(reqs)]
     batched_s = time.perf_counter() - t0
     clk = clocks.stop()
+    phases = {}
+    for nm in ("engine_round", "engine_gpu_round", "engine_idle", "engine_admit", "engine_wait", "engine_retire",
+               "engine_rebuild", "group_steps"):
+        n, ms = ctx.kernel_stats(nm)
+        phases[nm] = {"calls": n, "ms": ms}
     if args.no_plain:
         plain, plain_s = res, float("nan")
     else:
@@ -430,7 +436,7 @@ def run_batched(args):
             "batched_s": batched_s, "plain_s": plain_s, "plain_inst_s": len(insts) / plain_s,
             "speedup_vs_plain": plain_s / batched_s, "evals_per_s": evals / batched_s,
             "plain_evals_per_s": evals / plain_s, "load_s": load_s, "autotune_s": tune_s,
-            "batched_equals_plain": agree,
+            "batched_equals_plain": agree, "host_phases": phases,
             "table_gb": sum(i.B * i.M * 4 for i in insts) / 1e9, "clocks": clk}
     print(json.dumps(line))
     ctx.close()
@@ -532,14 +538,27 @@ def run_serving(args):
             lat.append((r.timing["end_ns"] - r.timing["submit_ns"]) / 1e9)
             done_at.append(r.timing["end_ns"] / 1e9)
         wall = max(done_at) - start if done_at else 0.0
+        phases = None
+        if engine:
+            phases = {}
+            for nm in ("engine_round", "engine_gpu_round", "engine_idle", "engine_admit", "engine_wait",
+                       "engine_retire", "engine_rebuild", "group_steps"):
+                try:
+                    n, ms = ctx.kernel_stats(nm)
+                except Exception:
+                    continue
+                phases[nm] = {"calls": n, "ms": ms}
         ctx.close()
         lat = np.array(lat) * 1000.0
-        return {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-                "mean_ms": float(lat.mean()), "throughput_req_s": len(lat) / wall, "wall_s": wall,
-                "requests": len(lat)}
+        out = {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+               "mean_ms": float(lat.mean()), "throughput_req_s": len(lat) / wall, "wall_s": wall,
+               "requests": len(lat)}
+        if phases is not None:
+            out["host_phases"] = phases
+        return out
 
     eng = serve(True)
-    ser = serve(False)
+    ser = None if args.no_plain else serve(False)
     line = {"metric": "serving p50/p99 latency", "value": eng["p99_ms"], "unit": "ms (p99)", "n_gpus": world,
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
             "data": "synthetic",

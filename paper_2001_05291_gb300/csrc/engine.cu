@@ -15,6 +15,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cstring>
+#include <unordered_set>
 
 #include "runtime_internal.h"
 
@@ -45,6 +46,7 @@ struct Ticket {
     stage_inst inst = 0;
     stage_result res{};
     int state = 0;                         // 0 pending, 1 running, 2 done
+    bool released = false;                 // came back from waiting on its busy instance: goes first
 };
 
 struct Slot {
@@ -73,16 +75,32 @@ struct Engine {
     size_t map_cap = 0;       // int2 entries of d_map
     TabuDevState *h_states = nullptr;      // pinned
     cudaGraphExec_t graph = nullptr;
+    cudaEvent_t ev_round[2] = {nullptr, nullptr};   // brackets each round on the engine stream
     bool dirty = true;        // slot set changed: device arrays must be rebuilt
     int stable = 0;           // rounds since the last change (the graph is captured once stable)
-    int n_swap_blocks = 0, n_sel_blocks = 0, n_ref_blocks = 0, maxK = 1;
-    size_t swap_smem = 0;
+    // Two lanes: the active slots are split into two sets of about equal swap
+    // work, each advanced by its own launches on its own stream, so one lane's
+    // latency-bound selection and refresh overlap the other's streaming swap
+    // pass instead of leaving SMs idle between kernels.
+    struct Lane {
+        int n_swap = 0, n_sel = 0, n_ref = 0, maxK = 1;
+        size_t swap_smem = 0;
+        size_t map_off = 0;   // first entry of this lane's block maps in d_map
+    };
+    Lane lane[2];
+    cudaStream_t stream2 = nullptr;   // lane 1 (lane 0 runs on `stream`)
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    int n_lane0 = 0;                  // active[0, n_lane0) is lane 0, the rest lane 1
+
+    // requests waiting for their instance's current search to finish, per instance, in order
+    std::unordered_map<stage_inst, std::deque<Ticket *>> parked;
 
     void run();
     cudaError_t launch_steps(int steps);
-    bool admit(Ticket *tk, bool &transient);
+    bool admit(Ticket *tk, bool &transient, stage_inst &busy_on);
     void complete(Ticket *tk, stage_status st);
-    void retire(size_t k, const TabuDevState &s, stage_status status);
+    void retire_copy(struct Retiring &r);
+    void retire_finish(struct Retiring &r, bool copies_ok);
     stage_status rebuild();
 };
 
@@ -115,11 +133,13 @@ void Engine::complete(Ticket *tk, stage_status st)
     cv_done.notify_all();
 }
 
-// Admit one request into a new slot.  On a transient shortage (memory, or its
-// instance busy in another slot) returns false with transient = true.
-bool Engine::admit(Ticket *tk, bool &transient)
+// Admit one request into a new slot.  On a memory shortage returns false with
+// transient = true; when its instance is busy in another slot, returns false
+// with busy_on = that instance (the request then waits on the instance).
+bool Engine::admit(Ticket *tk, bool &transient, stage_inst &busy_on)
 {
     transient = false;
+    busy_on = 0;
     std::lock_guard<std::recursive_mutex> g(c->mu);
     stage_status s = STAGE_OK;
     if (!tk->inst) {
@@ -151,8 +171,8 @@ bool Engine::admit(Ticket *tk, bool &transient)
         complete(tk, STAGE_ERR_NOT_FOUND);
         return false;
     }
-    if (in->busy) {
-        transient = true;   // one request per instance at a time: updates and searches stay ordered
+    if (in->busy || (parked.count(tk->inst) && !tk->released)) {
+        busy_on = tk->inst;   // one request per instance at a time: updates and searches stay ordered
         return false;
     }
     auto fail = [&](stage_status st) {
@@ -291,7 +311,31 @@ stage_status Engine::rebuild()
         stage_status s = dev_alloc(c, sizeof(GroupSlot) * (size_t)cap, d_slots);
         if (s == STAGE_OK) s = dev_alloc(c, sizeof(TabuDevState) * (size_t)cap, d_states);
         if (s != STAGE_OK) return s;
+        if (cudaStreamSynchronize(c->stream) != cudaSuccess) return STAGE_ERR_CUDA;   // allocations ordered there
         if (cudaMallocHost(&h_states, sizeof(TabuDevState) * (size_t)cap) != cudaSuccess) return STAGE_ERR_CUDA;
+    }
+    // split into the two lanes by swap work (largest first, to the lighter
+    // lane), lane 0's slots first in `active`
+    {
+        std::vector<int> order(n);
+        for (int k = 0; k < n; k++) order[k] = k;
+        auto work = [&](int k) { return (double)active[k].nC * active[k].tb.M_pad; };
+        std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return work(x) > work(y); });
+        double load[2] = {0.0, 0.0};
+        std::vector<int> side(n, 0);
+        for (int k : order) {
+            const int l = (n >= 2 && load[1] < load[0]) ? 1 : 0;
+            side[k] = l;
+            load[l] += work(k);
+        }
+        std::vector<Slot> re;
+        re.reserve(n);
+        for (int l = 0; l < 2; l++)
+            for (int k = 0; k < n; k++)
+                if (side[k] == l) re.push_back(active[k]);
+        active.swap(re);
+        n_lane0 = 0;
+        for (int k = 0; k < n; k++) n_lane0 += side[k] == 0;
     }
     std::vector<GroupSlot> gs(n);
     std::vector<int> mp(n), nc(n);
@@ -300,28 +344,34 @@ stage_status Engine::rebuild()
         nc[k] = active[k].nC;
     }
     const int common = group_common_segment(mp.data(), nc.data(), n);
-    maxK = 1;
-    swap_smem = 0;
-    std::vector<int2> map;   // swap blocks, then select blocks, then refresh blocks
     for (int k = 0; k < n; k++) {
         const Slot &sl = active[k];
         gs[k].w = sl.tb;
         gs[k].cost = sl.in->cost;
         gs[k].swap_blocks =
             group_swap_blocks(sl.tb.M_pad, sl.nC, sl.tb.K, common, &gs[k].swap_bx, &gs[k].swap_seg);
-        swap_smem = std::max(swap_smem, swap_direct_smem(sl.tb.K));
         gs[k].sel_blocks = select_blocks(sl.tb.K, sl.nC);
         gs[k].ref_blocks = group_ref_blocks(sl.tb.M_pad);
-        for (int b = 0; b < gs[k].swap_blocks; b++) map.push_back(make_int2(k, b));
-        maxK = std::max(maxK, sl.tb.K);
     }
-    n_swap_blocks = (int)map.size();
-    for (int k = 0; k < n; k++)
-        for (int b = 0; b < gs[k].sel_blocks; b++) map.push_back(make_int2(k, b));
-    n_sel_blocks = (int)map.size() - n_swap_blocks;
-    for (int k = 0; k < n; k++)
-        for (int b = 0; b < gs[k].ref_blocks; b++) map.push_back(make_int2(k, b));
-    n_ref_blocks = (int)map.size() - n_swap_blocks - n_sel_blocks;
+    std::vector<int2> map;   // per lane: swap blocks, then select blocks, then refresh blocks
+    for (int l = 0; l < 2; l++) {
+        Lane &ln = lane[l];
+        const int k0 = l == 0 ? 0 : n_lane0, k1 = l == 0 ? n_lane0 : n;
+        ln = Lane{};
+        ln.map_off = map.size();
+        for (int k = k0; k < k1; k++) {
+            for (int b = 0; b < gs[k].swap_blocks; b++) map.push_back(make_int2(k, b));
+            ln.swap_smem = std::max(ln.swap_smem, swap_direct_smem(active[k].tb.K));
+            ln.maxK = std::max(ln.maxK, active[k].tb.K);
+        }
+        ln.n_swap = (int)(map.size() - ln.map_off);
+        for (int k = k0; k < k1; k++)
+            for (int b = 0; b < gs[k].sel_blocks; b++) map.push_back(make_int2(k, b));
+        ln.n_sel = (int)(map.size() - ln.map_off) - ln.n_swap;
+        for (int k = k0; k < k1; k++)
+            for (int b = 0; b < gs[k].ref_blocks; b++) map.push_back(make_int2(k, b));
+        ln.n_ref = (int)(map.size() - ln.map_off) - ln.n_swap - ln.n_sel;
+    }
     if (map.size() > map_cap) {
         std::lock_guard<std::recursive_mutex> g(c->mu);
         dev_free(c, d_map);
@@ -330,6 +380,7 @@ stage_status Engine::rebuild()
             map_cap = 0;
             return STAGE_ERR_NO_MEMORY;
         }
+        if (cudaStreamSynchronize(c->stream) != cudaSuccess) return STAGE_ERR_CUDA;
     }
     cudaError_t e = cudaMemcpyAsync(d_slots.p, gs.data(), sizeof(GroupSlot) * n, cudaMemcpyHostToDevice, stream);
     if (e == cudaSuccess)
@@ -341,21 +392,33 @@ stage_status Engine::rebuild()
     return STAGE_OK;
 }
 
-// kStepsPerGraph grouped steps: launched directly while the slot set keeps
-// changing, replayed from a captured CUDA graph once it has been stable.
+// kStepsPerGraph grouped steps of both lanes (lane 1 forked onto stream2 and
+// joined back): launched directly while the slot set keeps changing, replayed
+// from a captured CUDA graph once it has been stable.
 cudaError_t Engine::launch_steps(int steps)
 {
     const GroupSlot *ds = static_cast<const GroupSlot *>(d_slots.p);
-    const int2 *map_swap = static_cast<const int2 *>(d_map.p);
-    const int2 *map_sel = map_swap + n_swap_blocks;
-    const int2 *map_ref = map_sel + n_sel_blocks;
-    auto enqueue = [&]() {
+    const bool two = lane[1].n_swap + lane[1].n_sel + lane[1].n_ref > 0;
+    auto enqueue_lane = [&](const Lane &ln, cudaStream_t s) {
+        const int2 *map_swap = static_cast<const int2 *>(d_map.p) + ln.map_off;
+        const int2 *map_sel = map_swap + ln.n_swap;
+        const int2 *map_ref = map_sel + ln.n_sel;
         cudaError_t e = cudaSuccess;
         for (int k = 0; e == cudaSuccess && k < steps; k++) {
-            e = launch_group_swap(ds, map_swap, n_swap_blocks, swap_smem, stream);
-            if (e == cudaSuccess) e = launch_group_select(ds, map_sel, n_sel_blocks, stream);
-            if (e == cudaSuccess) e = launch_group_refresh(ds, map_ref, n_ref_blocks, maxK, stream);
+            e = launch_group_swap(ds, map_swap, ln.n_swap, ln.swap_smem, s);
+            if (e == cudaSuccess) e = launch_group_select(ds, map_sel, ln.n_sel, s);
+            if (e == cudaSuccess) e = launch_group_refresh(ds, map_ref, ln.n_ref, ln.maxK, s);
         }
+        return e;
+    };
+    auto enqueue = [&]() {
+        if (!two) return enqueue_lane(lane[0], stream);
+        cudaError_t e = cudaEventRecord(ev_fork, stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(stream2, ev_fork, 0);
+        if (e == cudaSuccess) e = enqueue_lane(lane[0], stream);
+        if (e == cudaSuccess) e = enqueue_lane(lane[1], stream2);
+        if (e == cudaSuccess) e = cudaEventRecord(ev_join, stream2);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(stream, ev_join, 0);
         return e;
     };
     if (stable < 1) return enqueue();
@@ -376,47 +439,100 @@ cudaError_t Engine::launch_steps(int steps)
     return cudaGraphLaunch(graph, stream);
 }
 
-void Engine::retire(size_t k, const TabuDevState &s, stage_status status)
+// Retiring slots: the read-backs of every slot that finished in a round are
+// queued together and waited for once (retire_copy, then one stream
+// synchronisation, then retire_finish).
+struct Retiring {
+    size_t k;
+    TabuDevState s;
+    stage_status status;
+    std::vector<int32_t> fin, best;
+};
+
+void Engine::retire_copy(Retiring &r)
 {
-    Slot &sl = active[k];
+    Slot &sl = active[r.k];
     Ticket *tk = sl.tk;
     const int K = sl.tb.K;
-    std::vector<int32_t> fin(K), best(K);
-    cudaError_t e = cudaMemcpyAsync(fin.data(), sl.tb.open, (size_t)K * 4, cudaMemcpyDeviceToHost, stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(best.data(), sl.tb.best_open, (size_t)K * 4, cudaMemcpyDeviceToHost, stream);
-    const int n = std::min(s.n_moves, tk->req.params.iters);
+    r.fin.assign(K, 0);
+    r.best.assign(K, 0);
+    cudaError_t e = cudaMemcpyAsync(r.fin.data(), sl.tb.open, (size_t)K * 4, cudaMemcpyDeviceToHost, stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(r.best.data(), sl.tb.best_open, (size_t)K * 4, cudaMemcpyDeviceToHost, stream);
+    const int n = std::min(r.s.n_moves, tk->req.params.iters);
     if (e == cudaSuccess && tk->req.traj && n > 0)
         e = cudaMemcpyAsync(tk->req.traj, sl.tb.traj, (size_t)n * sizeof(stage_move), cudaMemcpyDeviceToHost, stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
-    if (e != cudaSuccess && status == STAGE_OK) status = STAGE_ERR_CUDA;
-    if (s.err && status == STAGE_OK) status = STAGE_ERR_INTERNAL;
-    std::sort(fin.begin(), fin.end());
-    std::sort(best.begin(), best.end());
-    if (tk->req.best_open) std::copy(best.begin(), best.end(), tk->req.best_open);
-    if (tk->req.final_open) std::copy(fin.begin(), fin.end(), tk->req.final_open);
-    tk->res.n_moves = s.n_moves;
-    tk->res.best_iter = s.best_iter;
-    tk->res.best_cov = s.best_cov;
-    tk->res.best_dist = s.best_dist;
-    tk->res.final_cov = s.cur_cov;
-    tk->res.final_dist = s.cur_dist;
+    if (e != cudaSuccess && r.status == STAGE_OK) r.status = STAGE_ERR_CUDA;
+}
+
+void Engine::retire_finish(Retiring &r, bool copies_ok)
+{
+    Slot &sl = active[r.k];
+    Ticket *tk = sl.tk;
+    stage_status status = r.status;
+    if (!copies_ok && status == STAGE_OK) status = STAGE_ERR_CUDA;
+    if (r.s.err && status == STAGE_OK) status = STAGE_ERR_INTERNAL;
+    std::sort(r.fin.begin(), r.fin.end());
+    std::sort(r.best.begin(), r.best.end());
+    if (tk->req.best_open) std::copy(r.best.begin(), r.best.end(), tk->req.best_open);
+    if (tk->req.final_open) std::copy(r.fin.begin(), r.fin.end(), tk->req.final_open);
+    tk->res.n_moves = r.s.n_moves;
+    tk->res.best_iter = r.s.best_iter;
+    tk->res.best_cov = r.s.best_cov;
+    tk->res.best_dist = r.s.best_dist;
+    tk->res.final_cov = r.s.cur_cov;
+    tk->res.final_dist = r.s.cur_dist;
+    const stage_inst inst = tk->inst;
     {
         std::lock_guard<std::recursive_mutex> g(c->mu);
         dev_free(c, sl.ws);
         sl.in->busy -= 1;
         if (tk->inline_inst) stage_unload_instance(c, tk->inst);
     }
+    // the next request waiting on this instance goes to the head of the queue
+    auto it = tk->inline_inst ? parked.end() : parked.find(inst);
+    if (it != parked.end()) {
+        Ticket *nx = it->second.front();
+        it->second.pop_front();
+        if (it->second.empty()) parked.erase(it);
+        nx->released = true;
+        std::lock_guard<std::mutex> lk(mu);
+        pending.push_front(nx);
+    }
     complete(tk, status);
 }
+
+// Host-side phases of the worker loop, reported through stage_kernel_stats
+// under engine_* names (calls, milliseconds): where a round's wall time goes.
+struct PhaseClock {
+    stage_ctx *c;
+    const char *name;
+    int64_t t0;
+    PhaseClock(stage_ctx *c_, const char *n) : c(c_), name(n), t0(now_ns()) {}
+    ~PhaseClock()
+    {
+        const double ms = (now_ns() - t0) / 1e6;
+        std::lock_guard<std::recursive_mutex> g(c->mu);
+        KernelStat &k = c->stats[name];
+        k.launches += 1;
+        k.ms += ms;
+    }
+};
 
 void Engine::run()
 {
     cudaSetDevice(c->device);
     for (;;) {
+        PhaseClock round_clock(c, "engine_round");
         std::vector<Ticket *> take;
+        int64_t idle_ns = 0;   // added after the engine lock is released (lock order: context, then engine)
         {
             std::unique_lock<std::mutex> lk(mu);
-            cv_work.wait(lk, [&] { return stop || !pending.empty() || !active.empty(); });
+            if (!(stop || !pending.empty() || !active.empty())) {
+                const int64_t t0 = now_ns();
+                cv_work.wait(lk, [&] { return stop || !pending.empty() || !active.empty(); });
+                idle_ns = now_ns() - t0;
+            }
             if (stop) break;
             const size_t room = (size_t)c->max_slots > active.size() ? c->max_slots - active.size() : 0;
             while (!pending.empty() && take.size() < room) {
@@ -424,11 +540,20 @@ void Engine::run()
                 pending.pop_front();
             }
         }
+        if (idle_ns) {
+            std::lock_guard<std::recursive_mutex> g(c->mu);
+            KernelStat &k = c->stats["engine_idle"];
+            k.launches += 1;
+            k.ms += idle_ns / 1e6;
+        }
         // 1. advance the current slots (asynchronous)
         cudaError_t e = cudaSuccess;
         const int n = (int)active.size();
         if (n > 0) {
-            if (dirty && rebuild() != STAGE_OK) e = cudaErrorUnknown;
+            if (dirty) {
+                PhaseClock pc(c, "engine_rebuild");
+                if (rebuild() != STAGE_OK) e = cudaErrorUnknown;
+            }
             if (e == cudaSuccess) {
                 {
                     std::lock_guard<std::recursive_mutex> g(c->mu);
@@ -436,6 +561,11 @@ void Engine::run()
                         c->stats[nm].launches += kStepsPerGraph;
                     c->stats["group_steps"].launches += kStepsPerGraph;
                 }
+                if (!ev_round[0]) {
+                    cudaEventCreate(&ev_round[0]);
+                    cudaEventCreate(&ev_round[1]);
+                }
+                cudaEventRecord(ev_round[0], stream);
                 e = launch_steps(kStepsPerGraph);
                 if (e == cudaSuccess)
                     e = launch_gather_states(static_cast<const GroupSlot *>(d_slots.p), n,
@@ -443,14 +573,28 @@ void Engine::run()
                 if (e == cudaSuccess)
                     e = cudaMemcpyAsync(h_states, d_states.p, sizeof(TabuDevState) * n, cudaMemcpyDeviceToHost,
                                         stream);
+                cudaEventRecord(ev_round[1], stream);
             }
         }
         // 2. meanwhile admit waiting requests (their set-up runs on the context's stream)
         const size_t before = active.size();
         std::vector<Ticket *> retry;
+        std::unordered_set<stage_inst> held;   // instances with a request sent back to the queue
         for (Ticket *tk : take) {
+            if (tk->inst && held.count(tk->inst)) {
+                retry.push_back(tk);   // keeps requests on one instance in submission order
+                continue;
+            }
+            PhaseClock pc(c, "engine_admit");
             bool transient = false;
-            if (!admit(tk, transient) && transient) retry.push_back(tk);
+            stage_inst busy_on = 0;
+            if (admit(tk, transient, busy_on)) continue;
+            if (busy_on) {
+                parked[busy_on].push_back(tk);
+            } else if (transient) {
+                retry.push_back(tk);
+                if (tk->inst && !tk->inline_inst) held.insert(tk->inst);
+            }
         }
         if (!retry.empty()) {
             std::lock_guard<std::mutex> lk(mu);
@@ -458,14 +602,30 @@ void Engine::run()
         }
         // 3. finish the step and retire finished slots (only the first n slots took part)
         if (n > 0) {
-            if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+            if (e == cudaSuccess) {
+                PhaseClock pc(c, "engine_wait");
+                e = cudaStreamSynchronize(stream);
+            }
+            float gpu_ms = 0.f;
+            if (e == cudaSuccess && cudaEventElapsedTime(&gpu_ms, ev_round[0], ev_round[1]) == cudaSuccess) {
+                std::lock_guard<std::recursive_mutex> g(c->mu);
+                KernelStat &k = c->stats["engine_gpu_round"];   // device time of the round's launches
+                k.launches += 1;
+                k.ms += gpu_ms;
+            }
+            PhaseClock pc(c, "engine_retire");
+            std::vector<Retiring> fins;
             for (size_t k = n; k-- > 0;) {
                 TabuDevState z{};
                 const TabuDevState &s = e == cudaSuccess ? h_states[k] : z;
                 const bool fin = e != cudaSuccess || s.done || s.t >= s.t_end || s.err;
-                if (!fin) continue;
-                retire(k, s, e != cudaSuccess ? STAGE_ERR_CUDA : STAGE_OK);
-                active.erase(active.begin() + k);
+                if (fin) fins.push_back(Retiring{k, s, e != cudaSuccess ? STAGE_ERR_CUDA : STAGE_OK, {}, {}});
+            }
+            for (Retiring &r : fins) retire_copy(r);
+            const bool copies_ok = fins.empty() || cudaStreamSynchronize(stream) == cudaSuccess;
+            for (Retiring &r : fins) {   // descending slot index: erasing keeps the others' indices
+                retire_finish(r, copies_ok);
+                active.erase(active.begin() + r.k);
                 dirty = true;
             }
         }
@@ -474,11 +634,24 @@ void Engine::run()
         if (active.empty() && !retry.empty()) std::this_thread::sleep_for(std::chrono::microseconds(200));
     }
     // stopping: release what is still held; unfinished tickets report a timeout
-    for (size_t k = active.size(); k-- > 0;) {
-        TabuDevState z{};
-        retire(k, z, STAGE_ERR_TIMEOUT);
+    {
+        std::vector<Retiring> fins;
+        for (size_t k = active.size(); k-- > 0;) fins.push_back(Retiring{k, TabuDevState{}, STAGE_ERR_TIMEOUT, {}, {}});
+        for (Retiring &r : fins) {
+            r.fin.assign(active[r.k].tb.K, 0);
+            r.best.assign(active[r.k].tb.K, 0);
+            retire_finish(r, true);
+        }
     }
     active.clear();
+    {
+        // requests still waiting on an instance go back to the queue, which is
+        // answered with a timeout when the engine is destroyed
+        std::lock_guard<std::mutex> lk(mu);
+        for (auto &kv : parked)
+            for (Ticket *tk : kv.second) pending.push_back(tk);
+        parked.clear();
+    }
 }
 
 void engine_destroy(stage_ctx *c)
@@ -500,11 +673,16 @@ void engine_destroy(stage_ctx *c)
         E->pending.clear();
     }
     if (E->graph) cudaGraphExecDestroy(E->graph);
+    for (cudaEvent_t ev : E->ev_round)
+        if (ev) cudaEventDestroy(ev);
     dev_free(c, E->d_slots);
     dev_free(c, E->d_map);
     dev_free(c, E->d_states);
     if (E->h_states) cudaFreeHost(E->h_states);
     if (E->stream) cudaStreamDestroy(E->stream);
+    if (E->stream2) cudaStreamDestroy(E->stream2);
+    if (E->ev_fork) cudaEventDestroy(E->ev_fork);
+    if (E->ev_join) cudaEventDestroy(E->ev_join);
     delete E;
     c->engine.store(nullptr);
 }
@@ -526,7 +704,16 @@ stage_status stage_batch_submit(stage_ctx *c, const stage_request *reqs, int32_t
             cudaSetDevice(c->device);
             E = new Engine();
             E->c = c;
-            if (cudaStreamCreateWithFlags(&E->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            int least = 0, greatest = 0;
+            cudaDeviceGetStreamPriorityRange(&least, &greatest);
+            if (cudaStreamCreateWithPriority(&E->stream, cudaStreamNonBlocking, least) != cudaSuccess ||
+                cudaStreamCreateWithPriority(&E->stream2, cudaStreamNonBlocking, least) != cudaSuccess ||
+                cudaEventCreateWithFlags(&E->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+                cudaEventCreateWithFlags(&E->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+                if (E->stream) cudaStreamDestroy(E->stream);
+                if (E->stream2) cudaStreamDestroy(E->stream2);
+                if (E->ev_fork) cudaEventDestroy(E->ev_fork);
+                if (E->ev_join) cudaEventDestroy(E->ev_join);
                 delete E;
                 return set_err(c, STAGE_ERR_CUDA, "engine stream creation failed");
             }

@@ -68,6 +68,15 @@ stage_status dev_alloc(stage_ctx *c, size_t bytes, DevBuf &out)
     void *p = nullptr;
     if (c->alloc) {
         p = c->alloc(bytes, c->alloc_user);
+    } else if (c->pool) {
+        // stream-ordered on the context stream: every user of the memory is
+        // ordered after that stream (the callers synchronise it before another
+        // stream touches the buffer)
+        cudaError_t e = cudaMallocFromPoolAsync(&p, bytes, c->pool, c->stream);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            p = nullptr;
+        }
     } else {
         cudaError_t e = cudaMalloc(&p, bytes);
         if (e != cudaSuccess) {
@@ -85,7 +94,10 @@ stage_status dev_alloc(stage_ctx *c, size_t bytes, DevBuf &out)
 void dev_free(stage_ctx *c, DevBuf &b)
 {
     if (!b.p) return;
+    // the pool's free is ordered on the context stream and does not wait for
+    // the device (cudaFree would); callers free only memory no stream still uses
     if (c->free) c->free(b.p, b.bytes, c->alloc_user);
+    else if (c->pool) cudaFreeAsync(b.p, c->stream);
     else cudaFree(b.p);
     c->used -= b.bytes;
     b.p = nullptr;
@@ -569,7 +581,12 @@ stage_status stage_create(const stage_config *cfg, stage_ctx **out)
     if (d.stream) {
         c->stream = static_cast<cudaStream_t>(d.stream);
     } else {
-        if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+        // the context's own stream takes the highest priority: set-up work of
+        // requests joining the batch engine (whose stream has the lowest)
+        // then waits for free SMs, not for the whole running step
+        int least = 0, greatest = 0;
+        cudaDeviceGetStreamPriorityRange(&least, &greatest);
+        if (cudaStreamCreateWithPriority(&c->stream, cudaStreamNonBlocking, greatest) != cudaSuccess) {
             delete c;
             return STAGE_ERR_CUDA;
         }
@@ -579,6 +596,21 @@ stage_status stage_create(const stage_config *cfg, stage_ctx **out)
         if (c->own_stream) cudaStreamDestroy(c->stream);
         delete c;
         return STAGE_ERR_CUDA;
+    }
+    int pools = 0;
+    if (!c->alloc && cudaDeviceGetAttribute(&pools, cudaDevAttrMemoryPoolsSupported, c->device) == cudaSuccess &&
+        pools) {
+        cudaMemPoolProps props{};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = c->device;
+        if (cudaMemPoolCreate(&c->pool, &props) == cudaSuccess) {
+            uint64_t keep = UINT64_MAX;   // freed blocks stay with the pool for reuse
+            cudaMemPoolSetAttribute(c->pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        } else {
+            cudaGetLastError();
+            c->pool = nullptr;
+        }
     }
     *out = c;
     return STAGE_OK;
@@ -593,6 +625,10 @@ stage_status stage_destroy(stage_ctx *c)
     for (auto &kv : c->insts) free_instance(c, kv.second);
     c->insts.clear();
     fold_stats(c);
+    if (c->pool) {
+        cudaStreamSynchronize(c->stream);
+        cudaMemPoolDestroy(c->pool);
+    }
     for (cudaEvent_t e : c->event_pool) cudaEventDestroy(e);
     if (c->pinned) cudaFreeHost(c->pinned);
     if (c->own_stream) cudaStreamDestroy(c->stream);

@@ -67,6 +67,7 @@ struct stage_ctx {
     void *alloc_user = nullptr;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
+    cudaMemPool_t pool = nullptr;   // stream-ordered pool behind dev_alloc when no allocator hook is given
     uint64_t used = 0;
     std::unordered_map<uint64_t, stg_rt::Instance *> insts;
     uint64_t next_id = 1;
