@@ -26,6 +26,7 @@ namespace stg_rt {
 namespace {
 
 constexpr int kStepsPerGraph = 8;
+constexpr int kLanes = 2;   // lanes of slots advanced on their own streams (see Engine::Lane)
 
 int64_t now_ns()
 {
@@ -78,24 +79,36 @@ struct Engine {
     cudaEvent_t ev_round[2] = {nullptr, nullptr};   // brackets each round on the engine stream
     bool dirty = true;        // slot set changed: device arrays must be rebuilt
     int stable = 0;           // rounds since the last change (the graph is captured once stable)
-    // Two lanes: the active slots are split into two sets of about equal swap
+    // Lanes: the active slots are split into kLanes sets of about equal swap
     // work, each advanced by its own launches on its own stream, so one lane's
-    // latency-bound selection and refresh overlap the other's streaming swap
+    // latency-bound selection and refresh overlap another's streaming swap
     // pass instead of leaving SMs idle between kernels.
     struct Lane {
         int n_swap = 0, n_sel = 0, n_ref = 0, maxK = 1;
         size_t swap_smem = 0;
         size_t map_off = 0;   // first entry of this lane's block maps in d_map
     };
-    Lane lane[2];
-    cudaStream_t stream2 = nullptr;   // lane 1 (lane 0 runs on `stream`)
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
-    int n_lane0 = 0;                  // active[0, n_lane0) is lane 0, the rest lane 1
+    Lane lane[kLanes];
+    cudaStream_t lane_stream[kLanes] = {};   // lane_stream[0] is `stream`
+    cudaEvent_t ev_fork = nullptr, ev_join[kLanes] = {};
+    int lane_begin[kLanes + 1] = {};         // active[lane_begin[l], lane_begin[l + 1]) is lane l
 
     // requests waiting for their instance's current search to finish, per instance, in order
     std::unordered_map<stage_inst, std::deque<Ticket *>> parked;
 
     void run();
+    void release_streams()
+    {
+        for (int l = 0; l < kLanes; l++) {
+            if (lane_stream[l]) cudaStreamDestroy(lane_stream[l]);
+            if (ev_join[l]) cudaEventDestroy(ev_join[l]);
+            lane_stream[l] = nullptr;
+            ev_join[l] = nullptr;
+        }
+        if (ev_fork) cudaEventDestroy(ev_fork);
+        ev_fork = nullptr;
+        stream = nullptr;
+    }
     cudaError_t launch_steps(int steps);
     bool admit(Ticket *tk, bool &transient, stage_inst &busy_on);
     void complete(Ticket *tk, stage_status st);
@@ -314,28 +327,31 @@ stage_status Engine::rebuild()
         if (cudaStreamSynchronize(c->stream) != cudaSuccess) return STAGE_ERR_CUDA;   // allocations ordered there
         if (cudaMallocHost(&h_states, sizeof(TabuDevState) * (size_t)cap) != cudaSuccess) return STAGE_ERR_CUDA;
     }
-    // split into the two lanes by swap work (largest first, to the lighter
-    // lane), lane 0's slots first in `active`
+    // split into lanes by swap work (largest first, to the lightest lane);
+    // lane l's slots are contiguous in `active`
     {
         std::vector<int> order(n);
         for (int k = 0; k < n; k++) order[k] = k;
         auto work = [&](int k) { return (double)active[k].nC * active[k].tb.M_pad; };
         std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return work(x) > work(y); });
-        double load[2] = {0.0, 0.0};
+        double load[kLanes] = {};
         std::vector<int> side(n, 0);
         for (int k : order) {
-            const int l = (n >= 2 && load[1] < load[0]) ? 1 : 0;
+            int l = 0;
+            for (int q = 1; q < kLanes; q++)
+                if (load[q] < load[l]) l = q;
             side[k] = l;
             load[l] += work(k);
         }
         std::vector<Slot> re;
         re.reserve(n);
-        for (int l = 0; l < 2; l++)
+        for (int l = 0; l < kLanes; l++) {
+            lane_begin[l] = (int)re.size();
             for (int k = 0; k < n; k++)
                 if (side[k] == l) re.push_back(active[k]);
+        }
+        lane_begin[kLanes] = n;
         active.swap(re);
-        n_lane0 = 0;
-        for (int k = 0; k < n; k++) n_lane0 += side[k] == 0;
     }
     std::vector<GroupSlot> gs(n);
     std::vector<int> mp(n), nc(n);
@@ -354,9 +370,9 @@ stage_status Engine::rebuild()
         gs[k].ref_blocks = group_ref_blocks(sl.tb.M_pad);
     }
     std::vector<int2> map;   // per lane: swap blocks, then select blocks, then refresh blocks
-    for (int l = 0; l < 2; l++) {
+    for (int l = 0; l < kLanes; l++) {
         Lane &ln = lane[l];
-        const int k0 = l == 0 ? 0 : n_lane0, k1 = l == 0 ? n_lane0 : n;
+        const int k0 = lane_begin[l], k1 = lane_begin[l + 1];
         ln = Lane{};
         ln.map_off = map.size();
         for (int k = k0; k < k1; k++) {
@@ -392,13 +408,12 @@ stage_status Engine::rebuild()
     return STAGE_OK;
 }
 
-// kStepsPerGraph grouped steps of both lanes (lane 1 forked onto stream2 and
-// joined back): launched directly while the slot set keeps changing, replayed
-// from a captured CUDA graph once it has been stable.
+// kStepsPerGraph grouped steps of every lane (lanes 1.. forked onto their
+// streams and joined back): launched directly while the slot set keeps
+// changing, replayed from a captured CUDA graph once it has been stable.
 cudaError_t Engine::launch_steps(int steps)
 {
     const GroupSlot *ds = static_cast<const GroupSlot *>(d_slots.p);
-    const bool two = lane[1].n_swap + lane[1].n_sel + lane[1].n_ref > 0;
     auto enqueue_lane = [&](const Lane &ln, cudaStream_t s) {
         const int2 *map_swap = static_cast<const int2 *>(d_map.p) + ln.map_off;
         const int2 *map_sel = map_swap + ln.n_swap;
@@ -411,14 +426,18 @@ cudaError_t Engine::launch_steps(int steps)
         }
         return e;
     };
+    auto used = [&](int l) { return lane[l].n_swap + lane[l].n_sel + lane[l].n_ref > 0; };
     auto enqueue = [&]() {
-        if (!two) return enqueue_lane(lane[0], stream);
         cudaError_t e = cudaEventRecord(ev_fork, stream);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(stream2, ev_fork, 0);
-        if (e == cudaSuccess) e = enqueue_lane(lane[0], stream);
-        if (e == cudaSuccess) e = enqueue_lane(lane[1], stream2);
-        if (e == cudaSuccess) e = cudaEventRecord(ev_join, stream2);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(stream, ev_join, 0);
+        for (int l = 1; e == cudaSuccess && l < kLanes; l++)
+            if (used(l)) e = cudaStreamWaitEvent(lane_stream[l], ev_fork, 0);
+        for (int l = 0; e == cudaSuccess && l < kLanes; l++)
+            if (used(l)) e = enqueue_lane(lane[l], lane_stream[l]);
+        for (int l = 1; e == cudaSuccess && l < kLanes; l++)
+            if (used(l)) {
+                e = cudaEventRecord(ev_join[l], lane_stream[l]);
+                if (e == cudaSuccess) e = cudaStreamWaitEvent(stream, ev_join[l], 0);
+            }
         return e;
     };
     if (stable < 1) return enqueue();
@@ -679,10 +698,7 @@ void engine_destroy(stage_ctx *c)
     dev_free(c, E->d_map);
     dev_free(c, E->d_states);
     if (E->h_states) cudaFreeHost(E->h_states);
-    if (E->stream) cudaStreamDestroy(E->stream);
-    if (E->stream2) cudaStreamDestroy(E->stream2);
-    if (E->ev_fork) cudaEventDestroy(E->ev_fork);
-    if (E->ev_join) cudaEventDestroy(E->ev_join);
+    E->release_streams();
     delete E;
     c->engine.store(nullptr);
 }
@@ -706,14 +722,13 @@ stage_status stage_batch_submit(stage_ctx *c, const stage_request *reqs, int32_t
             E->c = c;
             int least = 0, greatest = 0;
             cudaDeviceGetStreamPriorityRange(&least, &greatest);
-            if (cudaStreamCreateWithPriority(&E->stream, cudaStreamNonBlocking, least) != cudaSuccess ||
-                cudaStreamCreateWithPriority(&E->stream2, cudaStreamNonBlocking, least) != cudaSuccess ||
-                cudaEventCreateWithFlags(&E->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-                cudaEventCreateWithFlags(&E->ev_join, cudaEventDisableTiming) != cudaSuccess) {
-                if (E->stream) cudaStreamDestroy(E->stream);
-                if (E->stream2) cudaStreamDestroy(E->stream2);
-                if (E->ev_fork) cudaEventDestroy(E->ev_fork);
-                if (E->ev_join) cudaEventDestroy(E->ev_join);
+            bool ok = cudaEventCreateWithFlags(&E->ev_fork, cudaEventDisableTiming) == cudaSuccess;
+            for (int l = 0; ok && l < kLanes; l++)
+                ok = cudaStreamCreateWithPriority(&E->lane_stream[l], cudaStreamNonBlocking, least) == cudaSuccess &&
+                     cudaEventCreateWithFlags(&E->ev_join[l], cudaEventDisableTiming) == cudaSuccess;
+            E->stream = E->lane_stream[0];
+            if (!ok) {
+                E->release_streams();
                 delete E;
                 return set_err(c, STAGE_ERR_CUDA, "engine stream creation failed");
             }
