@@ -95,6 +95,8 @@ struct Engine {
 
     // requests waiting for their instance's current search to finish, per instance, in order
     std::unordered_map<stage_inst, std::deque<Ticket *>> parked;
+    std::vector<struct Retiring> retiring;   // finished in the last round, released during the next
+    void retire_pending();
 
     void run();
     void release_streams()
@@ -458,11 +460,12 @@ cudaError_t Engine::launch_steps(int steps)
     return cudaGraphLaunch(graph, stream);
 }
 
-// Retiring slots: the read-backs of every slot that finished in a round are
-// queued together and waited for once (retire_copy, then one stream
-// synchronisation, then retire_finish).
+// Retiring slots: a slot that finished in round N leaves the active set before
+// round N+1 is launched, and its read-backs (retire_copy, on the context
+// stream, all waited for once) and release (retire_finish) run on the host
+// while round N+1 runs on the device.
 struct Retiring {
-    size_t k;
+    Slot sl;
     TabuDevState s;
     stage_status status;
     std::vector<int32_t> fin, best;
@@ -470,23 +473,25 @@ struct Retiring {
 
 void Engine::retire_copy(Retiring &r)
 {
-    Slot &sl = active[r.k];
+    Slot &sl = r.sl;
     Ticket *tk = sl.tk;
     const int K = sl.tb.K;
     r.fin.assign(K, 0);
     r.best.assign(K, 0);
-    cudaError_t e = cudaMemcpyAsync(r.fin.data(), sl.tb.open, (size_t)K * 4, cudaMemcpyDeviceToHost, stream);
+    // on the context stream: the engine's streams already run the next round
+    cudaStream_t cs = c->stream;
+    cudaError_t e = cudaMemcpyAsync(r.fin.data(), sl.tb.open, (size_t)K * 4, cudaMemcpyDeviceToHost, cs);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(r.best.data(), sl.tb.best_open, (size_t)K * 4, cudaMemcpyDeviceToHost, stream);
+        e = cudaMemcpyAsync(r.best.data(), sl.tb.best_open, (size_t)K * 4, cudaMemcpyDeviceToHost, cs);
     const int n = std::min(r.s.n_moves, tk->req.params.iters);
     if (e == cudaSuccess && tk->req.traj && n > 0)
-        e = cudaMemcpyAsync(tk->req.traj, sl.tb.traj, (size_t)n * sizeof(stage_move), cudaMemcpyDeviceToHost, stream);
+        e = cudaMemcpyAsync(tk->req.traj, sl.tb.traj, (size_t)n * sizeof(stage_move), cudaMemcpyDeviceToHost, cs);
     if (e != cudaSuccess && r.status == STAGE_OK) r.status = STAGE_ERR_CUDA;
 }
 
 void Engine::retire_finish(Retiring &r, bool copies_ok)
 {
-    Slot &sl = active[r.k];
+    Slot &sl = r.sl;
     Ticket *tk = sl.tk;
     stage_status status = r.status;
     if (!copies_ok && status == STAGE_OK) status = STAGE_ERR_CUDA;
@@ -519,6 +524,15 @@ void Engine::retire_finish(Retiring &r, bool copies_ok)
         pending.push_front(nx);
     }
     complete(tk, status);
+}
+
+void Engine::retire_pending()
+{
+    if (retiring.empty()) return;
+    for (Retiring &r : retiring) retire_copy(r);
+    const bool copies_ok = cudaStreamSynchronize(c->stream) == cudaSuccess;
+    for (Retiring &r : retiring) retire_finish(r, copies_ok);
+    retiring.clear();
 }
 
 // Host-side phases of the worker loop, reported through stage_kernel_stats
@@ -595,7 +609,12 @@ void Engine::run()
                 cudaEventRecord(ev_round[1], stream);
             }
         }
-        // 2. meanwhile admit waiting requests (their set-up runs on the context's stream)
+        // 2. meanwhile release the slots that finished in the previous round
+        //    and admit waiting requests (their set-up runs on the context's stream)
+        if (!retiring.empty()) {
+            PhaseClock pc(c, "engine_retire");
+            retire_pending();
+        }
         const size_t before = active.size();
         std::vector<Ticket *> retry;
         std::unordered_set<stage_inst> held;   // instances with a request sent back to the queue
@@ -632,20 +651,19 @@ void Engine::run()
                 k.launches += 1;
                 k.ms += gpu_ms;
             }
-            PhaseClock pc(c, "engine_retire");
-            std::vector<Retiring> fins;
-            for (size_t k = n; k-- > 0;) {
+            for (size_t k = n; k-- > 0;) {   // descending: erasing keeps the lower indices
                 TabuDevState z{};
                 const TabuDevState &s = e == cudaSuccess ? h_states[k] : z;
                 const bool fin = e != cudaSuccess || s.done || s.t >= s.t_end || s.err;
-                if (fin) fins.push_back(Retiring{k, s, e != cudaSuccess ? STAGE_ERR_CUDA : STAGE_OK, {}, {}});
-            }
-            for (Retiring &r : fins) retire_copy(r);
-            const bool copies_ok = fins.empty() || cudaStreamSynchronize(stream) == cudaSuccess;
-            for (Retiring &r : fins) {   // descending slot index: erasing keeps the others' indices
-                retire_finish(r, copies_ok);
-                active.erase(active.begin() + r.k);
+                if (!fin) continue;
+                retiring.push_back(Retiring{active[k], s, e != cudaSuccess ? STAGE_ERR_CUDA : STAGE_OK, {}, {}});
+                active.erase(active.begin() + k);
                 dirty = true;
+            }
+            // nothing left to run: release now rather than after a next round
+            if (active.empty() && !retiring.empty()) {
+                PhaseClock pc(c, "engine_retire");
+                retire_pending();
             }
         }
         if (active.size() != before) dirty = true;
@@ -653,14 +671,12 @@ void Engine::run()
         if (active.empty() && !retry.empty()) std::this_thread::sleep_for(std::chrono::microseconds(200));
     }
     // stopping: release what is still held; unfinished tickets report a timeout
-    {
-        std::vector<Retiring> fins;
-        for (size_t k = active.size(); k-- > 0;) fins.push_back(Retiring{k, TabuDevState{}, STAGE_ERR_TIMEOUT, {}, {}});
-        for (Retiring &r : fins) {
-            r.fin.assign(active[r.k].tb.K, 0);
-            r.best.assign(active[r.k].tb.K, 0);
-            retire_finish(r, true);
-        }
+    retire_pending();
+    for (size_t k = active.size(); k-- > 0;) {
+        Retiring r{active[k], TabuDevState{}, STAGE_ERR_TIMEOUT, {}, {}};
+        r.fin.assign(r.sl.tb.K, 0);
+        r.best.assign(r.sl.tb.K, 0);
+        retire_finish(r, true);
     }
     active.clear();
     {

@@ -567,6 +567,8 @@ cudaError_t launch_evaluate(const int32_t *cost, int M, int M_pad, const int32_t
 // --------------------------------------------------------------------------
 
 // Accumulate f(b) - f(a) of one mission into the shared loss of its best slot.
+__device__ __forceinline__ long long group_sum_small(unsigned mask, long long v);
+
 __device__ __forceinline__ void mission_terms(int a, int b, int R, long long &v0c, long long &v0d,
                                               int *s_lc, unsigned long long *s_ld, int s1)
 {
@@ -576,8 +578,16 @@ __device__ __forceinline__ void mission_terms(int a, int b, int R, long long &v0
     v0d += da;
     const int dc = cb - ca;
     const long long dd = db - da;
-    if (dc) atomicAdd(&s_lc[s1], dc);
-    if (dd) atomicAdd(&s_ld[s1], (unsigned long long)dd);
+    // lanes with the same best slot add their terms first (neighbouring
+    // columns share slots often), so a slot takes one shared atomic per warp
+    // instead of one per lane; |dd| <= R < 2^31, as group_sum_small needs
+    const unsigned peers = __match_any_sync(__activemask(), s1);
+    const int sc = (int)__reduce_add_sync(peers, (unsigned)dc);
+    const long long sd = group_sum_small(peers, dd);
+    if ((threadIdx.x & 31) == __ffs(peers) - 1) {
+        if (sc) atomicAdd(&s_lc[s1], sc);
+        if (sd) atomicAdd(&s_ld[s1], (unsigned long long)sd);
+    }
 }
 
 // Shared layout used by init and refresh: open ids [K], loss cov [K], loss dist [K].
