@@ -231,6 +231,56 @@ STAGE_API stage_status stage_evaluate_swaps(stage_ctx *ctx, stage_inst inst, con
 STAGE_API stage_status stage_tabu_run(stage_ctx *ctx, stage_inst inst, const stage_tabu_params *params,
                             stage_tabu_result *result, stage_move *traj);
 
+/* Local search (Alg. 2, read for identical vehicles): a first-improvement
+ * scan of the swap neighbourhood in a randomised order.
+ *   - the moves are the swaps (close the base in slot s, open the closed
+ *     available base at candidate position c); the candidate positions 0 ..
+ *     nC-1 start as the closed available bases in ascending id order, nC =
+ *     (available bases) - K, and a swap puts the closed base at the opened
+ *     base's position;
+ *   - pass p scans the K x nC pairs in the order of its two permutations
+ *     (Alg. 2 draws them at random; here the caller supplies them): outer
+ *     loop over slots perm_slots[p*K + a], inner loop over positions
+ *     perm_cands[p*nC + b];
+ *   - each pair is judged against the current placement; the first strictly
+ *     better one (more covered, then less distance) is applied at once and the
+ *     scan goes on with the next pair;
+ *   - a pass that applied a move is followed by the next pair of
+ *     permutations; a pass without one ends the search at a local optimum of
+ *     the whole swap neighbourhood; the search also ends when the passes or
+ *     max_moves run out.
+ * The GPU evaluates the whole neighbourhood for the current placement in one
+ * streaming pass and picks the first improving pair at or after the scan
+ * position, which is the pair the sequential scan would apply next. */
+typedef struct {
+    int32_t K;                   /* vehicles, 1 <= K <= min(B, STAGE_MAX_K) */
+    int32_t R;                   /* range in metres, 0 <= R < INT32_MAX */
+    int32_t n_passes;            /* permutation pairs supplied, >= 1 */
+    int32_t max_moves;           /* move budget (trajectory capacity), >= 0 */
+    const int32_t *perm_slots;   /* [n_passes * K]: each row a permutation of 0 .. K-1 */
+    const int32_t *perm_cands;   /* [n_passes * nC]: each row a permutation of 0 .. nC-1 */
+    const int32_t *start_open;   /* [K] start placement, or NULL: stage_rank_bases */
+} stage_ls_params;
+
+typedef struct {
+    int32_t n_moves;             /* moves applied */
+    int32_t passes;              /* passes started */
+    int32_t local_optimum;       /* 1: the last pass found no improving swap */
+    int32_t reserved0;
+    int64_t final_cov;
+    int64_t final_dist;
+    int32_t *final_open;         /* [K] caller buffer or NULL; filled sorted ascending */
+} stage_ls_result;
+
+/* Run the local search on a resident instance.  traj (nullable) receives one
+ * stage_move per applied move ([max_moves]; iter = move number, flags =
+ * STAGE_MOVE_NEW_BEST).  All arrays are host memory, copied in.
+ * Errors: STAGE_ERR_INVALID_ARG (bad K, a row that is not a permutation,
+ * n_passes < 1, max_moves < 0), STAGE_ERR_OUT_OF_RANGE (R), STAGE_ERR_INTERNAL
+ * (a device self-check failed). */
+STAGE_API stage_status stage_local_search(stage_ctx *ctx, stage_inst inst, const stage_ls_params *params,
+                                          stage_ls_result *result, stage_move *traj);
+
 /* ---------------------------------------------------------- updates, batches */
 
 /* Incremental change to a resident instance (re-staging after new demand,

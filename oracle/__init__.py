@@ -217,6 +217,85 @@ def tabu(cost, K, R, iters, tenure, start_open=None, avail=None, accept_worsenin
                       np.sort(final_open), io.final_cov, io.final_dist, expiry)
 
 
+@dataclass
+class LocalSearchResult:
+    moves: list             # list of (move number, i, j, MOVE_NEW_BEST, cov, dist)
+    final_open: np.ndarray  # sorted ascending
+    final_cov: int
+    final_dist: int
+    passes: int             # passes started
+    local_optimum: bool     # the last pass found no improving swap
+
+
+def local_search(cost, K, R, perm_slots, perm_cands, start_open=None, avail=None, max_moves: int = 100000,
+                 eval_mode: str = "table", nthreads: int = 1) -> LocalSearchResult:
+    """Local search (Alg. 2, Sec. 4.2) read for identical vehicles.
+
+    The moves are base swaps.  The closed available bases sit at candidate
+    positions 0 .. nC-1 (ascending ids at the start); closing the base of slot
+    s and opening the base at position c puts the closed base at position c.
+    Pass p visits the K x nC (slot, position) pairs with the slot loop outside,
+    in the orders perm_slots[p] and perm_cands[p] (the paper's two random
+    permutations, here supplied); every pair is judged against the current
+    placement and the first strictly better one (more covered, then less
+    distance) is applied on the spot, the scan going on with the next pair.
+    A pass that moved is followed by the next pass; a pass that did not ends
+    the search at a local optimum.  The search also ends when the passes or
+    max_moves run out.
+
+    eval_mode "full" judges each pair by evaluating the swapped placement from
+    scratch (the plain definition); "table" reads the pair from swap_table of
+    the current placement, computed again after every applied move."""
+    cost = _i32(cost)
+    B, M = cost.shape
+    if start_open is None:
+        start_open, _ = rank(cost, K, avail)
+    O = [int(x) for x in start_open]
+    av = np.ones(B, dtype=bool) if avail is None else np.asarray(avail).astype(bool)
+    opened = set(O)
+    cand = [b for b in range(B) if av[b] and b not in opened]
+    nC = len(cand)
+    cur = evaluate(cost, O, R)
+    moves = []
+    if nC == 0:
+        return LocalSearchResult(moves, np.sort(np.array(O, dtype=np.int32)), cur[0], cur[1], 0, True)
+
+    def better(x, y):
+        return x[0] > y[0] or (x[0] == y[0] and x[1] < y[1])
+
+    passes, optimum = 0, False
+    for p in range(len(perm_slots)):
+        passes += 1
+        pa, pb = perm_slots[p], perm_cands[p]
+        moved = False
+        table = None
+        for u in range(K * nC):
+            if len(moves) >= max_moves:
+                break
+            s, c = int(pa[u // nC]), int(pb[u % nC])
+            i, j = O[s], cand[c]
+            if eval_mode == "full":
+                trial = list(O)
+                trial[s] = j
+                F = evaluate(cost, trial, R)
+            else:
+                if table is None:
+                    table = swap_table(cost, O, R, avail, nthreads)
+                F = (int(table[0][i, j]), int(table[1][i, j]))
+            if better(F, cur):
+                O[s], cand[c] = j, i
+                cur = F
+                moves.append((len(moves), i, j, MOVE_NEW_BEST, F[0], F[1]))
+                moved = True
+                table = None
+        if len(moves) >= max_moves:
+            break
+        if not moved:
+            optimum = True
+            break
+    return LocalSearchResult(moves, np.sort(np.array(O, dtype=np.int32)), cur[0], cur[1], passes, optimum)
+
+
 def bruteforce(cost, K, R, avail=None):
     """Exact optimum over all K-subsets: (placement, cov, dist, subsets evaluated)."""
     cost = _i32(cost)

@@ -753,7 +753,7 @@ template <int J>
 __global__ void __launch_bounds__(kSwapThreads, 2)
 k_swap_eval(TabuBuffers w, const int32_t *__restrict__ cost, int ignore_done)
 {
-    if (!ignore_done && w.st->done) return;
+    if (!ignore_done && (w.st->done || w.st->ls_hold)) return;
     extern __shared__ unsigned long long sm_swap[];
     const int K = w.K;
     unsigned long long *ex_d = sm_swap;                         // [K * J]
@@ -947,7 +947,7 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
 k_swap_stream(TabuBuffers w, const int32_t *__restrict__ cost, int ignore_done)
 {
     TabuDevState *st = w.st;
-    if (!ignore_done && st->done) return;
+    if (!ignore_done && (st->done || st->ls_hold)) return;
     extern __shared__ __align__(1024) unsigned char sm_pipe[];
     int32_t *ring = reinterpret_cast<int32_t *>(sm_pipe);
     unsigned long long *full = reinterpret_cast<unsigned long long *>(sm_pipe + (size_t)kPipeStages * kPipeT * 4);
@@ -1368,7 +1368,7 @@ __device__ __forceinline__ void swap_direct_body(const TabuBuffers &w, const int
 __global__ void __launch_bounds__(kDirThreads, 4)
 k_swap_direct(TabuBuffers w, const int32_t *__restrict__ cost, int ignore_done, int seg)
 {
-    if (!ignore_done && w.st->done) return;
+    if (!ignore_done && (w.st->done || w.st->ls_hold)) return;
     swap_direct_body(w, cost, blockIdx.x, blockIdx.y, seg);
 }
 
@@ -1685,7 +1685,7 @@ __device__ __forceinline__ void refresh_body(const TabuBuffers &w, const int32_t
                                              int nb)
 {
     TabuDevState *st = w.st;
-    if (st->done) return;
+    if (st->done || st->ls_hold) return;
     extern __shared__ unsigned long long sm_ref[];
     unsigned long long *s_ld = sm_ref;
     int *s_lc = reinterpret_cast<int *>(s_ld + w.K);
@@ -1740,6 +1740,151 @@ cudaError_t launch_refresh(const TabuBuffers &w, const int32_t *cost, cudaStream
 {
     size_t sm = (size_t)w.K * (8 + 4 + 4);
     k_refresh<<<grid_missions(w.M_pad), 256, sm, s>>>(w, cost);
+    return cudaGetLastError();
+}
+
+// --------------------------------------------------------------------------
+// Local search (Alg. 2 as read for identical vehicles): with the accumulators
+// of the current placement, find the first strictly improving (slot,
+// candidate position) pair at or after the scan position in the current
+// pass's order, u = rank_slot[s] * nC + rank_cand[c].  Each block keeps its
+// smallest improving u; the last block to finish reduces them and applies the
+// move, changes pass (accumulators stay valid: evaluation and refresh skip the
+// next step), or stops.
+// --------------------------------------------------------------------------
+struct LsKey {
+    long long cov, dist;
+    int u, s, c, i, j, valid;
+};
+static_assert(sizeof(LsKey) <= sizeof(MoveKey), "local-search keys reuse the partials buffer");
+
+__device__ __forceinline__ bool ls_first(const LsKey &a, const LsKey &b)
+{
+    return a.valid && (!b.valid || a.u < b.u);
+}
+
+__device__ __forceinline__ void ls_block_first(LsKey &k, LsKey *sh)
+{
+    sh[threadIdx.x] = k;
+    __syncthreads();
+    for (int h = kSelectThreads / 2; h > 0; h >>= 1) {
+        if (threadIdx.x < h && ls_first(sh[threadIdx.x + h], sh[threadIdx.x])) sh[threadIdx.x] = sh[threadIdx.x + h];
+        __syncthreads();
+    }
+    k = sh[0];
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(kSelectThreads) k_ls_select(TabuBuffers w, const int *__restrict__ rank_slot,
+                                                             const int *__restrict__ rank_cand)
+{
+    TabuDevState *st = w.st;
+    if (st->done) return;
+    __shared__ LsKey sh[kSelectThreads];
+    __shared__ int s_last, s_moved;
+    const int nC = st->nC, K = w.K, pass = st->ls_pass, u0 = st->ls_pos;
+    const int *ra = rank_slot + (size_t)pass * K;
+    const int *rb = rank_cand + (size_t)pass * nC;
+    const long long v0c = (long long)w.v0[0], v0d = (long long)w.v0[1];
+    const long long cc = st->cur_cov, cd = st->cur_dist;
+    const bool budget_left = st->n_moves < st->traj_cap;
+    LsKey best;
+    best.valid = 0;
+    best.u = 0x7fffffff;
+    const long long total = (long long)K * nC;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; budget_left && q < total;
+         q += (long long)gridDim.x * blockDim.x) {
+        const int s = (int)(q / nC), c = (int)(q % nC);
+        const int u = ra[s] * nC + rb[c];
+        if (u < u0 || (best.valid && u >= best.u)) continue;
+        const int j = w.cand[c];
+        const size_t sj = (size_t)s * w.B + j;
+        const long long cov = v0c + w.gain_c[j] + (long long)w.loss_c[s] + w.extra_c[sj];
+        const long long dist = v0d + (long long)w.gain_d[j] + (long long)w.loss_d[s] + (long long)w.extra_d[sj];
+        if (obj_better(cov, dist, cc, cd)) {
+            best.cov = cov; best.dist = dist; best.u = u; best.s = s; best.c = c;
+            best.i = w.open[s]; best.j = j; best.valid = 1;
+        }
+    }
+    ls_block_first(best, sh);
+    LsKey *part = reinterpret_cast<LsKey *>(w.partials);
+    if (threadIdx.x == 0) {
+        part[blockIdx.x] = best;
+        __threadfence();
+        const unsigned int ticket = atomicAdd(&st->ticket, 1u);
+        s_last = (ticket == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    best.valid = 0;
+    best.u = 0x7fffffff;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
+        LsKey k;
+        k.cov = __ldcg(&part[b].cov);
+        k.dist = __ldcg(&part[b].dist);
+        k.u = __ldcg(&part[b].u);
+        k.s = __ldcg(&part[b].s);
+        k.c = __ldcg(&part[b].c);
+        k.i = __ldcg(&part[b].i);
+        k.j = __ldcg(&part[b].j);
+        k.valid = __ldcg(&part[b].valid);
+        if (ls_first(k, best)) best = k;
+    }
+    ls_block_first(best, sh);
+    if (threadIdx.x == 0) {
+        st->ticket = 0;
+        s_moved = 0;
+        if (st->cur_cov != v0c || st->cur_dist != v0d) {
+            st->err |= kErrObjectiveMismatch;   // refresh disagreed with the applied move
+            st->done = 1;
+        } else if (!budget_left) {
+            st->done = 1;                        // move budget used up
+        } else if (best.valid) {
+            const int t = st->t;
+            w.open[best.s] = best.j;
+            w.cand[best.c] = best.i;
+            st->cur_cov = best.cov;
+            st->cur_dist = best.dist;
+            st->best_cov = best.cov;             // every applied move is strictly better
+            st->best_dist = best.dist;
+            st->best_iter = t;
+            stage_move mv;
+            mv.iter = t; mv.i = best.i; mv.j = best.j; mv.flags = STAGE_MOVE_NEW_BEST;
+            mv.cov = best.cov; mv.dist = best.dist;
+            w.traj[st->n_moves] = mv;
+            st->n_moves += 1;
+            st->t = t + 1;
+            st->mv_s = best.s; st->mv_i = best.i; st->mv_j = best.j;
+            st->ls_pos = best.u + 1;
+            st->ls_moved = 1;
+            st->ls_hold = 0;
+            w.v0[0] = 0;
+            w.v0[1] = 0;
+            s_moved = 1;
+        } else if (st->ls_moved && st->ls_pass + 1 < st->ls_passes) {
+            st->ls_pass += 1;                    // next pair of permutations, same placement
+            st->ls_pos = 0;
+            st->ls_moved = 0;
+            st->ls_hold = 1;
+        } else {
+            st->ls_optimum = st->ls_moved ? 0 : 1;
+            st->done = 1;
+        }
+    }
+    __syncthreads();
+    if (!s_moved) return;
+    for (int k = threadIdx.x; k < K; k += blockDim.x) {
+        w.loss_c[k] = 0;
+        w.loss_d[k] = 0;
+        w.best_open[k] = w.open[k];
+    }
+}
+
+cudaError_t launch_ls_select(const TabuBuffers &w, int nC, const int *rank_slot, const int *rank_cand,
+                             cudaStream_t s)
+{
+    k_ls_select<<<select_blocks(w.K, nC), kSelectThreads, 0, s>>>(w, rank_slot, rank_cand);
     return cudaGetLastError();
 }
 

@@ -544,6 +544,140 @@ stage_status run_tabu(stage_ctx *c, Instance *in, const stage_tabu_params *p,
     return STAGE_OK;
 }
 
+// Local search (Alg. 2 as read for identical vehicles): iterations of
+// (swap pass, first-improvement selection, refresh) until the device state
+// says done; a pass change skips the swap pass and the refresh of the next step.
+stage_status run_local_search(stage_ctx *c, Instance *in, const stage_ls_params *p, stage_ls_result *res,
+                              stage_move *traj)
+{
+    if (!p) return set_err(c, STAGE_ERR_INVALID_ARG, "params is NULL");
+    const int K = p->K;
+    if (K < 1 || K > in->B || K > STAGE_MAX_K)
+        return set_err(c, STAGE_ERR_INVALID_ARG, "K=%d outside [1, min(B=%d, %d)]", K, in->B, STAGE_MAX_K);
+    if (K > in->n_avail)
+        return set_err(c, STAGE_ERR_INVALID_ARG, "K=%d exceeds the %d available bases", K, in->n_avail);
+    if (p->R < 0 || p->R == INT32_MAX)
+        return set_err(c, STAGE_ERR_OUT_OF_RANGE, "R=%d outside [0, INT32_MAX)", p->R);
+    if (p->n_passes < 1 || p->max_moves < 0 || !p->perm_slots || (!p->perm_cands && in->n_avail > K))
+        return set_err(c, STAGE_ERR_INVALID_ARG, "local search needs n_passes >= 1, max_moves >= 0 and permutations");
+    const int nC0 = in->n_avail - K;
+    const int P = p->n_passes;
+    // positions of every slot and candidate in each pass's scan order
+    std::vector<int32_t> rank((size_t)P * (K + nC0), -1);
+    for (int q = 0; q < P; q++) {
+        int32_t *rs = rank.data() + (size_t)q * K;
+        int32_t *rc = rank.data() + (size_t)P * K + (size_t)q * nC0;
+        for (int a = 0; a < K; a++) {
+            const int v = p->perm_slots[(size_t)q * K + a];
+            if (v < 0 || v >= K || rs[v] >= 0)
+                return set_err(c, STAGE_ERR_INVALID_ARG, "perm_slots row %d is not a permutation of 0..%d", q, K - 1);
+            rs[v] = a;
+        }
+        for (int b = 0; b < nC0; b++) {
+            const int v = p->perm_cands[(size_t)q * nC0 + b];
+            if (v < 0 || v >= nC0 || rc[v] >= 0)
+                return set_err(c, STAGE_ERR_INVALID_ARG, "perm_cands row %d is not a permutation of 0..%d", q,
+                               nC0 - 1);
+            rc[v] = b;
+        }
+    }
+    std::vector<int32_t> start(K);
+    if (p->start_open) {
+        stage_status s = check_placement(c, in, p->start_open, K);
+        if (s != STAGE_OK) return s;
+        std::copy(p->start_open, p->start_open + K, start.begin());
+    } else {
+        stage_status s = do_rank(c, in, K, start.data(), nullptr);
+        if (s != STAGE_OK) return s;
+    }
+    int nC = 0;
+    stage_status s = setup_search(c, in, start.data(), K, p->R, p->max_moves, 0, 1, 0, nullptr, &nC);
+    if (s != STAGE_OK) return s;
+    if (nC != nC0) return set_err(c, STAGE_ERR_INTERNAL, "candidate count %d, expected %d", nC, nC0);
+    TabuBuffers &tb = in->tb;
+    DevBuf dr;
+    s = dev_alloc(c, rank.size() * 4 + 4, dr);
+    if (s != STAGE_OK) return s;
+    const int *d_rank_slot = static_cast<const int *>(dr.p);
+    const int *d_rank_cand = d_rank_slot + (size_t)P * K;
+    cudaError_t e = cudaMemcpyAsync(dr.p, rank.data(), rank.size() * 4, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&tb.st->ls_passes, &P, sizeof(int), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = launch_begin(tb, 0, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);   // host vectors above
+    c->stats["begin"].launches += 1;
+    // every step applies a move, changes pass or stops
+    const long long max_steps = (long long)p->max_moves + P + 1;
+    volatile int *done_flag = static_cast<volatile int *>(c->pinned);
+    *done_flag = 0;
+    const bool profiling = (c->flags & STAGE_PROFILE) != 0;
+    auto step = [&]() {
+        cudaError_t r = launch_swap_eval(tb, in->cost, nC, 0, c->stream);
+        if (r == cudaSuccess) r = launch_ls_select(tb, nC, d_rank_slot, d_rank_cand, c->stream);
+        if (r == cudaSuccess) r = launch_refresh(tb, in->cost, c->stream);
+        return r;
+    };
+    auto poll = [&]() {
+        cudaError_t r = cudaMemcpyAsync(c->pinned, &tb.st->done, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+        if (r == cudaSuccess) r = cudaStreamSynchronize(c->stream);
+        return r;
+    };
+    cudaGraphExec_t ge = nullptr;
+    if (e == cudaSuccess && nC > 0 && !profiling && max_steps >= kGraphIters) {
+        cudaGraph_t gr = nullptr;
+        e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
+        for (int k = 0; e == cudaSuccess && k < kGraphIters; k++) e = step();
+        cudaError_t e2 = cudaStreamEndCapture(c->stream, &gr);
+        if (e == cudaSuccess) e = e2;
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&ge, gr, 0);
+        if (gr) cudaGraphDestroy(gr);
+    }
+    long long it = 0;
+    while (e == cudaSuccess && nC > 0 && it < max_steps) {
+        if (ge) {
+            for (const char *nm : {"swap_eval", "ls_select", "refresh"}) c->stats[nm].launches += kGraphIters;
+            e = cudaGraphLaunch(ge, c->stream);
+            it += kGraphIters;
+        } else {
+            for (int k = 0; e == cudaSuccess && k < kGraphIters && it < max_steps; k++, it++) {
+                e = timed(c, "swap_eval", 1, [&] { return launch_swap_eval(tb, in->cost, nC, 0, c->stream); });
+                if (e == cudaSuccess)
+                    e = timed(c, "ls_select", 1,
+                              [&] { return launch_ls_select(tb, nC, d_rank_slot, d_rank_cand, c->stream); });
+                if (e == cudaSuccess)
+                    e = timed(c, "refresh", 1, [&] { return launch_refresh(tb, in->cost, c->stream); });
+            }
+        }
+        if (e == cudaSuccess) e = poll();
+        if (*done_flag) break;
+    }
+    if (ge) cudaGraphExecDestroy(ge);
+    TabuDevState st{};
+    std::vector<int32_t> fin(K);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&st, tb.st, sizeof st, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(fin.data(), tb.open, (size_t)K * 4, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    const int n = std::min(st.n_moves, p->max_moves);
+    if (e == cudaSuccess && traj && n > 0)
+        e = cudaMemcpy(traj, tb.traj, (size_t)n * sizeof(stage_move), cudaMemcpyDeviceToHost);
+    dev_free(c, dr);
+    if (e != cudaSuccess) return set_err(c, STAGE_ERR_CUDA, "local search failed: %s", cudaGetErrorString(e));
+    if (st.err)
+        return set_err(c, STAGE_ERR_INTERNAL, "device self-check failed (code %d) after %d moves", st.err, st.n_moves);
+    if (nC > 0 && !st.done && st.n_moves < p->max_moves)
+        return set_err(c, STAGE_ERR_INTERNAL, "local search did not finish in %lld steps", max_steps);
+    if (res) {
+        res->n_moves = st.n_moves;
+        res->passes = nC > 0 ? st.ls_pass + 1 : 0;
+        res->local_optimum = nC > 0 ? st.ls_optimum : 1;
+        res->final_cov = st.cur_cov;
+        res->final_dist = st.cur_dist;
+        std::sort(fin.begin(), fin.end());
+        if (res->final_open) std::copy(fin.begin(), fin.end(), res->final_open);
+    }
+    return STAGE_OK;
+}
+
 }  // namespace stg_rt
 
 using namespace stg_rt;
@@ -951,6 +1085,17 @@ stage_status stage_evaluate_swaps(stage_ctx *c, stage_inst h, const int32_t *ope
     CK(cudaMemcpyAsync(out_dist, od, n * 8, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     return STAGE_OK;
+}
+
+stage_status stage_local_search(stage_ctx *c, stage_inst h, const stage_ls_params *p, stage_ls_result *res,
+                                stage_move *traj)
+{
+    if (!c) return STAGE_ERR_INVALID_ARG;
+    Guard g(c);
+    Instance *in = find_inst(c, h);
+    if (!in) return set_err(c, STAGE_ERR_NOT_FOUND, "unknown instance %llu", (unsigned long long)h);
+    CK(cudaSetDevice(c->device));
+    return run_local_search(c, in, p, res, traj);
 }
 
 stage_status stage_tabu_run(stage_ctx *c, stage_inst h, const stage_tabu_params *p,

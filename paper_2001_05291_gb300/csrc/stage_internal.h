@@ -42,7 +42,10 @@ struct TabuDevState {
     unsigned int ticket;  // last-block counter of the select kernel
     unsigned int work;    // work-unit counter of the streaming swap pass
     int t_end;            // iteration budget: no step at t >= t_end
-    int pad;
+    // local search (Alg. 2): scan position in the current pass, pass index,
+    // whether the pass applied a move, passes supplied, "accumulators still
+    // valid, skip evaluation and refresh" (after a pass change), local optimum
+    int ls_pos, ls_pass, ls_moved, ls_passes, ls_hold, ls_optimum;
 };
 
 enum : int { kErrObjectiveMismatch = 1, kErrBadSlot = 2, kErrPipelineTimeout = 4 };
@@ -128,6 +131,10 @@ size_t swap_direct_smem(int K);   // dynamic shared memory of the direct swap pa
 bool tabu_small_fits(int nC, int M_pad, int K);
 bool swap_variant_default();   // the direct swap pass is selected (STAGE_SWAP_VARIANT unset or 0)
 cudaError_t launch_tabu_small(const TabuBuffers &w, const int32_t *cost, int iters, cudaStream_t s);
+// local search: first improving swap at or after the scan position of the
+// current pass (rank_slot / rank_cand: [passes][K] / [passes][nC] positions)
+cudaError_t launch_ls_select(const TabuBuffers &w, int nC, const int *rank_slot, const int *rank_cand,
+                             cudaStream_t s);
 int select_blocks(int K, int nC);
 // missions per block of the direct swap pass, per shape (measured choice or heuristic)
 int swap_segment_for(int M_pad, int nC, int K);

@@ -62,6 +62,17 @@ class StageTabuParams(C.Structure):
                 ("start_open", C.c_void_p), ("resume", C.POINTER(StageTabuState))]
 
 
+class StageLsParams(C.Structure):
+    _fields_ = [("K", C.c_int32), ("R", C.c_int32), ("n_passes", C.c_int32), ("max_moves", C.c_int32),
+                ("perm_slots", C.c_void_p), ("perm_cands", C.c_void_p), ("start_open", C.c_void_p)]
+
+
+class StageLsResult(C.Structure):
+    _fields_ = [("n_moves", C.c_int32), ("passes", C.c_int32), ("local_optimum", C.c_int32),
+                ("reserved0", C.c_int32), ("final_cov", C.c_int64), ("final_dist", C.c_int64),
+                ("final_open", C.c_void_p)]
+
+
 class StageUpdate(C.Structure):
     _fields_ = [("n_add", C.c_int32), ("n_remove", C.c_int32), ("n_unavail", C.c_int32),
                 ("n_avail", C.c_int32), ("add_pick_xy", C.c_void_p), ("add_drop_xy", C.c_void_p),
@@ -112,6 +123,7 @@ def lib():
             "stage_evaluate_placement": ([p, C.c_uint64, p, i32, i32, C.POINTER(i64), C.POINTER(i64)], st),
             "stage_evaluate_swaps": ([p, C.c_uint64, p, i32, i32, p, p], st),
             "stage_tabu_run": ([p, C.c_uint64, C.POINTER(StageTabuParams), C.POINTER(StageTabuResult), p], st),
+            "stage_local_search": ([p, C.c_uint64, C.POINTER(StageLsParams), C.POINTER(StageLsResult), p], st),
             "stage_kernel_stats": ([p, C.c_char_p, C.POINTER(i64), C.POINTER(C.c_double)], st),
             "stage_reset_stats": ([p], st),
             "stage_read_table": ([p, C.c_uint64, i32, i32, i32, i32, p], st),
@@ -161,6 +173,17 @@ class TabuResult:
     final_dist: int
     moves: list = field(default_factory=list)   # (iter, i, j, flags, cov, dist)
     end_state: dict | None = None
+
+
+@dataclass
+class LocalSearchResult:
+    n_moves: int
+    passes: int
+    local_optimum: bool
+    final_open: np.ndarray
+    final_cov: int
+    final_dist: int
+    moves: list = field(default_factory=list)   # (move number, i, j, flags, cov, dist)
 
 
 class _TorchAllocator:
@@ -304,6 +327,35 @@ class Context:
         fd = np.empty(o.size * B, dtype=np.int64)
         self._check(lib().stage_evaluate_swaps(self._h, inst, _ptr(o), o.size, R, _ptr(fc), _ptr(fd)))
         return fc.reshape(o.size, B), fd.reshape(o.size, B)
+
+    def local_search(self, inst: int, K: int, R: int, perm_slots, perm_cands, max_moves: int = 100000,
+                     start_open=None, trajectory: bool = True) -> LocalSearchResult:
+        """stage_local_search (Alg. 2): perm_slots [passes, K], perm_cands [passes, nC] with
+        nC = available bases - K; row p of each is pass p's scan order."""
+        ps = np.ascontiguousarray(np.asarray(perm_slots), dtype=np.int32)
+        pc = np.ascontiguousarray(np.asarray(perm_cands), dtype=np.int32)
+        if ps.ndim != 2 or pc.ndim != 2 or ps.shape[0] != pc.shape[0] or ps.shape[1] != K:
+            raise ValueError("perm_slots must be [passes, K] and perm_cands [passes, nC]")
+        p = StageLsParams()
+        p.K, p.R, p.n_passes, p.max_moves = K, R, ps.shape[0], max_moves
+        p.perm_slots, p.perm_cands = _ptr(ps), (_ptr(pc) if pc.size else None)
+        keep = [ps, pc]
+        if start_open is not None:
+            so = _host_i32(start_open, K)
+            keep.append(so)
+            p.start_open = _ptr(so)
+        r = StageLsResult()
+        fin = np.empty(K, dtype=np.int32)
+        r.final_open = _ptr(fin)
+        traj = (StageMove * max(1, max_moves))() if trajectory else None
+        self._check(lib().stage_local_search(self._h, inst, C.byref(p), C.byref(r),
+                                             C.cast(traj, C.c_void_p) if traj is not None else None))
+        moves = []
+        if traj is not None:
+            moves = [(traj[k].iter, traj[k].i, traj[k].j, traj[k].flags, traj[k].cov, traj[k].dist)
+                     for k in range(min(r.n_moves, max_moves))]
+        return LocalSearchResult(r.n_moves, r.passes, bool(r.local_optimum), fin, r.final_cov, r.final_dist,
+                                 moves)
 
     def tabu_run(self, inst: int, K: int, R: int, iters: int, tenure: int, start_open=None,
                  accept_worsening: bool = True, resume: dict | None = None, B: int | None = None,
@@ -522,6 +574,7 @@ stage_rank_bases = Context.rank_bases
 stage_evaluate_placement = Context.evaluate_placement
 stage_evaluate_swaps = Context.evaluate_swaps
 stage_tabu_run = Context.tabu_run
+stage_local_search = Context.local_search
 stage_best_two = Context.best_two
 stage_read_table = Context.read_table
 stage_update_instance = Context.update_instance

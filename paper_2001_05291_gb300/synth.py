@@ -34,6 +34,7 @@ _MASK = (1 << 64) - 1
 
 # entity classes (stream identifiers)
 CLS_BASES, CLS_FACILITIES, CLS_PICKUPS, CLS_DROPOFF, CLS_SIZES, CLS_ARRIVALS, CLS_UPDATES = 1, 2, 3, 4, 5, 6, 7
+CLS_SCAN = 8   # scan orders of the local search
 
 # Draws consumed per point and attempt: [mixture choice, cluster id, u1, u2].
 _DRAWS_PER_POINT = 4
@@ -55,6 +56,21 @@ def _mix64(z: np.ndarray) -> np.ndarray:
     z *= np.uint64(_M2)
     z ^= z >> np.uint64(31)
     return z
+
+
+def scan_orders(seed: int, n_passes: int, K: int, nC: int):
+    """The local search's random scan orders (Alg. 2 draws two permutations per
+    pass): pass p's slot order and candidate-position order, each the stable
+    argsort of fresh SplitMix64 draws.  Returns int32 arrays [n_passes, K] and
+    [n_passes, nC]."""
+    ps = np.empty((n_passes, K), dtype=np.int32)
+    pc = np.empty((n_passes, nC), dtype=np.int32)
+    for p in range(n_passes):
+        ks = draws_u64(stream_key(seed, CLS_SCAN, 2 * p), np.arange(K))
+        kc = draws_u64(stream_key(seed, CLS_SCAN, 2 * p + 1), np.arange(nC))
+        ps[p] = np.argsort(ks, kind="stable")
+        pc[p] = np.argsort(kc, kind="stable")
+    return ps, pc
 
 
 def stream_key(seed: int, cls: int, sub: int = 0) -> int:

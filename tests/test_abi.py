@@ -62,6 +62,8 @@ int main(void) {
   P(stage_update); O(stage_update, add_pick_xy); O(stage_update, avail_ids);
   P(stage_request); O(stage_request, params); O(stage_request, traj); O(stage_request, final_open);
   P(stage_result); O(stage_result, best_cov); O(stage_result, t_end_ns);
+  P(stage_ls_params); O(stage_ls_params, perm_slots); O(stage_ls_params, start_open);
+  P(stage_ls_result); O(stage_ls_result, final_cov); O(stage_ls_result, final_open);
   return 0;
 }
 """
@@ -80,7 +82,8 @@ def test_ctypes_layouts_match_header(tmp_path):
           "stage_move": stage.StageMove, "stage_tabu_state": stage.StageTabuState,
           "stage_tabu_params": stage.StageTabuParams, "stage_tabu_result": stage.StageTabuResult,
           "stage_update": stage.StageUpdate, "stage_request": stage.StageRequest,
-          "stage_result": stage.StageResult}
+          "stage_result": stage.StageResult, "stage_ls_params": stage.StageLsParams,
+          "stage_ls_result": stage.StageLsResult}
     for key, val in got.items():
         if "." in key:
             t, f = key.split(".")
