@@ -86,3 +86,28 @@ def test_batched_workload_instances_in_one_batch(stage_mod):
         for t in (50, inst.iters - 1):
             assert oracle.evaluate(cost, placements[t], inst.R) == (r.moves[t][4], r.moves[t][5])
         assert oracle.evaluate(cost, r.best_open, inst.R) == (r.best_cov, r.best_dist)
+
+
+def test_local_search_large_workload(stage_mod):
+    """Local search (Alg. 2) on the large workload: the first moves equal the
+    oracle's on the full table; the complete run's sampled placements, final
+    objective and strict improvement are checked against the oracle's
+    evaluation."""
+    stage = stage_mod
+    inst = synth.large()
+    cost = oracle.cost_table(inst.base_xy, inst.pick_xy, inst.drop_xy, THREADS)
+    ps, pc = synth.scan_orders(inst.seed, 16, inst.K, inst.B - inst.K)
+    with stage.Context(device=0) as ctx:
+        h = ctx.load_instance(inst.base_xy, inst.pick_xy, inst.drop_xy)
+        start, _ = ctx.rank_bases(h, inst.K, inst.B)
+        first = ctx.local_search(h, inst.K, inst.R, ps, pc, max_moves=3)
+        full = ctx.local_search(h, inst.K, inst.R, ps, pc)
+    ref = oracle.local_search(cost, inst.K, inst.R, ps, pc, max_moves=3, nthreads=THREADS)
+    assert [tuple(m) for m in first.moves] == [tuple(m) for m in ref.moves]
+    assert [tuple(m) for m in full.moves[:3]] == [tuple(m) for m in ref.moves]
+    placements = replay(start, full.moves)
+    covs = [(m[4], -m[5]) for m in full.moves]
+    assert all(a < b for a, b in zip(covs, covs[1:]))
+    for t in sorted({0, len(placements) // 2, len(placements) - 1}):
+        assert oracle.evaluate(cost, placements[t], inst.R) == (full.moves[t][4], full.moves[t][5])
+    assert oracle.evaluate(cost, full.final_open, inst.R) == (full.final_cov, full.final_dist)
