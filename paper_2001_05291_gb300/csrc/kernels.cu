@@ -1185,7 +1185,7 @@ k_swap_stream(TabuBuffers w, const int32_t *__restrict__ cost, int ignore_done)
 // not by deeper per-thread batches.  Same clamped thresholds and
 // warp-aggregated accumulation as the streaming form.
 // --------------------------------------------------------------------------
-constexpr int kDirJ = 16;      // candidate rows per block
+constexpr int kDirJ = 16;      // candidate rows per block (at most; fewer when the grid is small)
 constexpr int kStages = 2;     // batches of 4 rows in flight per thread
 
 constexpr int kDirThreads = 256;
@@ -1199,6 +1199,7 @@ size_t swap_direct_smem(int K)
 // Hit path of one row for one warp: called (out of line, so the kernel body
 // stays small enough for the instruction cache) only when some lane of the
 // warp has a hit in the row; every lane of the warp takes part.
+template <int J>
 __device__ __noinline__ void dir_row(const int4 x, const int4 ap, const int4 bp, const int s0, const int s1,
                                      const int s2, const int s3, const bool uni, const int r, const int R,
                                      int *ex_c, unsigned long long *ex_d, int *g_c, unsigned long long *g_d,
@@ -1220,8 +1221,8 @@ __device__ __noinline__ void dir_row(const int4 x, const int4 ap, const int4 bp,
                     ec += dc;
                     ed += dd;
                 } else if (dc | (dd != 0)) {
-                    atomicAdd(&ex_c[sv[e] * kDirJ + r], dc);
-                    atomicAdd(&ex_d[sv[e] * kDirJ + r], (unsigned long long)dd);
+                    atomicAdd(&ex_c[sv[e] * J + r], dc);
+                    atomicAdd(&ex_d[sv[e] * J + r], (unsigned long long)dd);
                 }
                 if (xe < a) {
                     gc += 1 - ca;
@@ -1236,8 +1237,8 @@ __device__ __noinline__ void dir_row(const int4 x, const int4 ap, const int4 bp,
         const int sc = (int)__reduce_add_sync(peers, (unsigned)ec);
         const long long sd = group_sum_small(peers, ed);
         if (lane == __ffs(peers) - 1 && (sc | (sd != 0))) {
-            atomicAdd(&ex_c[s0 * kDirJ + r], sc);
-            atomicAdd(&ex_d[s0 * kDirJ + r], (unsigned long long)sd);
+            atomicAdd(&ex_c[s0 * J + r], sc);
+            atomicAdd(&ex_d[s0 * J + r], (unsigned long long)sd);
         }
     }
     if (__any_sync(0xffffffffu, gc | (gd != 0))) {
@@ -1250,20 +1251,21 @@ __device__ __noinline__ void dir_row(const int4 x, const int4 ap, const int4 bp,
     }
 }
 
+template <int J>
 __device__ __forceinline__ void swap_direct_body(const TabuBuffers &w, const int32_t *__restrict__ cost,
                                                  int bx, int by, int seg)
 {
     extern __shared__ unsigned long long sm_dir[];
     const int K = w.K;
     unsigned long long *ex_d = sm_dir;                               // [K * J]
-    int *ex_c = reinterpret_cast<int *>(ex_d + K * kDirJ);           // [K * J]
-    __shared__ int rows[kDirJ];
-    __shared__ int g_c[kDirJ];
-    __shared__ unsigned long long g_d[kDirJ];
+    int *ex_c = reinterpret_cast<int *>(ex_d + K * J);           // [K * J]
+    __shared__ int rows[J];
+    __shared__ int g_c[J];
+    __shared__ unsigned long long g_d[J];
     const int nC = w.st->nC;
-    const int c0 = by * kDirJ;
-    for (int k = threadIdx.x; k < K * kDirJ; k += blockDim.x) { ex_d[k] = 0; ex_c[k] = 0; }
-    if (threadIdx.x < kDirJ) {
+    const int c0 = by * J;
+    for (int k = threadIdx.x; k < K * J; k += blockDim.x) { ex_d[k] = 0; ex_c[k] = 0; }
+    if (threadIdx.x < J) {
         rows[threadIdx.x] = (c0 + threadIdx.x < nC) ? w.cand[c0 + threadIdx.x] : -1;
         g_c[threadIdx.x] = 0;
         g_d[threadIdx.x] = 0;
@@ -1271,7 +1273,7 @@ __device__ __forceinline__ void swap_direct_body(const TabuBuffers &w, const int
     __syncthreads();
     const int R = w.R, lane = threadIdx.x & 31;
     const size_t M_pad = w.M_pad;
-    const int nrows = min(kDirJ, nC - c0);
+    const int nrows = min(J, nC - c0);
     const int m_begin = bx * seg;
     const int m_end = min(m_begin + seg, w.M_pad);
     // Table loads are staged through shared memory with per-thread async
@@ -1280,16 +1282,16 @@ __device__ __forceinline__ void swap_direct_body(const TabuBuffers &w, const int
     // slots it copied into, after waiting on its own copy groups.  Every lane of
     // a warp runs every batch (the warp-collective calls in dir_row need all 32
     // lanes); lanes past the segment end see thresholds nothing can beat.
-    int4 *stg = reinterpret_cast<int4 *>(ex_c + K * kDirJ + ((K * kDirJ) & 3 ? 4 - ((K * kDirJ) & 3) : 0));
+    int4 *stg = reinterpret_cast<int4 *>(ex_c + K * J + ((K * J) & 3 ? 4 - ((K * J) & 3) : 0));
     const int wbase = 4 * (threadIdx.x & ~31);
     const int first = m_begin + wbase;
     const int npass = first < m_end ? (m_end - first + 4 * kDirThreads - 1) / (4 * kDirThreads) : 0;
-    const int nbatch = npass * (kDirJ / 4);
+    const int nbatch = npass * (J / 4);
     // the table streams through once per iteration: evict it first from L2, so
     // the per-mission thresholds (re-read by every row chunk) stay resident
     const unsigned long long policy = evict_first_policy();
     auto issue = [&](int i) {
-        const int p = i / (kDirJ / 4), h = (i % (kDirJ / 4)) * 4;
+        const int p = i / (J / 4), h = (i % (J / 4)) * 4;
         const int m = first + p * 4 * kDirThreads + 4 * lane;
         if (m < m_end) {
             const int q = m >> 2;
@@ -1317,9 +1319,9 @@ __device__ __forceinline__ void swap_direct_body(const TabuBuffers &w, const int
     for (int b = 0; b < nbatch; b++) {
         if (b + kStages - 1 < nbatch) issue(b + kStages - 1);
         else asm volatile("cp.async.commit_group;" ::: "memory");
-        const int hb = b % (kDirJ / 4), h = hb * 4;
+        const int hb = b % (J / 4), h = hb * 4;
         if (hb == 0) {
-            const int m = first + (b / (kDirJ / 4)) * 4 * kDirThreads + 4 * lane;
+            const int m = first + (b / (J / 4)) * 4 * kDirThreads + 4 * lane;
             act = m < m_end;
             const int q = act ? (m >> 2) : 0;
             ap = __ldg(reinterpret_cast<const int4 *>(w.a) + q);
@@ -1342,13 +1344,13 @@ __device__ __forceinline__ void swap_direct_body(const TabuBuffers &w, const int
         for (int r = 0; r < 4; r++) {
             const bool hit = x[r].x < bp.x || x[r].y < bp.y || x[r].z < bp.z || x[r].w < bp.w;
             if (__any_sync(0xffffffffu, hit))
-                dir_row(x[r], ap, bp, s0, s1, s2, s3, uni, h + r, R, ex_c, ex_d, g_c, g_d, lane);
+                dir_row<J>(x[r], ap, bp, s0, s1, s2, s3, uni, h + r, R, ex_c, ex_d, g_c, g_d, lane);
         }
     }
     asm volatile("cp.async.wait_all;" ::: "memory");
     __syncthreads();
-    for (int k = threadIdx.x; k < K * kDirJ; k += blockDim.x) {
-        const int r = k % kDirJ, sidx = k / kDirJ;
+    for (int k = threadIdx.x; k < K * J; k += blockDim.x) {
+        const int r = k % J, sidx = k / J;
         const int j = rows[r];
         if (j < 0) continue;
         const int c = ex_c[k];
@@ -1358,18 +1360,19 @@ __device__ __forceinline__ void swap_direct_body(const TabuBuffers &w, const int
             atomicAdd(&w.extra_d[(size_t)sidx * w.B + j], d);
         }
     }
-    if (threadIdx.x < kDirJ && rows[threadIdx.x] >= 0) {
+    if (threadIdx.x < J && rows[threadIdx.x] >= 0) {
         const int j = rows[threadIdx.x];
         if (g_c[threadIdx.x]) atomicAdd(&w.gain_c[j], g_c[threadIdx.x]);
         if (g_d[threadIdx.x]) atomicAdd(&w.gain_d[j], g_d[threadIdx.x]);
     }
 }
 
+template <int J>
 __global__ void __launch_bounds__(kDirThreads, 4)
 k_swap_direct(TabuBuffers w, const int32_t *__restrict__ cost, int ignore_done, int seg)
 {
     if (!ignore_done && (w.st->done || w.st->ls_hold)) return;
-    swap_direct_body(w, cost, blockIdx.x, blockIdx.y, seg);
+    swap_direct_body<J>(w, cost, blockIdx.x, blockIdx.y, seg);
 }
 
 // Missions per block of the direct swap pass: the largest power of two in
@@ -1420,7 +1423,7 @@ cudaError_t launch_swap_direct_seg(const TabuBuffers &w, const int32_t *cost, in
 {
     if (nC <= 0) return cudaSuccess;
     dim3 grid((w.M_pad + seg - 1) / seg, (nC + kDirJ - 1) / kDirJ);
-    k_swap_direct<<<grid, kDirThreads, swap_direct_smem(w.K), s>>>(w, cost, 1, seg);
+    k_swap_direct<kDirJ><<<grid, kDirThreads, swap_direct_smem(w.K), s>>>(w, cost, 1, seg);
     return cudaGetLastError();
 }
 
@@ -1443,8 +1446,18 @@ cudaError_t launch_swap_eval(const TabuBuffers &w, const int32_t *cost, int nC, 
     if (nC <= 0) return cudaSuccess;
     if (g_swap_variant == 0 && w.K <= kPipeMaxK) {
         const int seg = swap_segment_for(w.M_pad, nC, w.K);
-        dim3 grid((w.M_pad + seg - 1) / seg, (nC + kDirJ - 1) / kDirJ);
-        k_swap_direct<<<grid, kDirThreads, swap_direct_smem(w.K), s>>>(w, cost, ignore_done, seg);
+        const int bx = (w.M_pad + seg - 1) / seg;
+        // latency-bound small grids: fewer rows per block, more blocks and
+        // shorter per-warp chains, until the grid reaches two waves
+        const long long waves2 = 2ll * 4 * (g_num_sms > 0 ? g_num_sms : 152);
+        const size_t sm = swap_direct_smem(w.K);
+        if ((long long)bx * ((nC + 15) / 16) >= waves2) {
+            k_swap_direct<16><<<dim3(bx, (nC + 15) / 16), kDirThreads, sm, s>>>(w, cost, ignore_done, seg);
+        } else if ((long long)bx * ((nC + 7) / 8) >= waves2) {
+            k_swap_direct<8><<<dim3(bx, (nC + 7) / 8), kDirThreads, sm, s>>>(w, cost, ignore_done, seg);
+        } else {
+            k_swap_direct<4><<<dim3(bx, (nC + 3) / 4), kDirThreads, sm, s>>>(w, cost, ignore_done, seg);
+        }
         return cudaGetLastError();
     }
     if (g_swap_variant == 1 && w.K <= kPipeMaxK && nC <= kPipeMaxCand && g_num_sms > 0) {
@@ -1658,11 +1671,12 @@ __global__ void __launch_bounds__(kSelectThreads) k_select(TabuBuffers w)
     select_body(w, blockIdx.x, gridDim.x);
 }
 
-// Blocks for K x nC candidates: about 8 candidates per thread, at most kSelectBlocks.
+// Blocks for K x nC candidates: about 2 candidates per thread (each one is a
+// chain of dependent loads), at most kSelectBlocks.
 int select_blocks(int K, int nC)
 {
     const long long n = (long long)K * nC;
-    long long b = (n + kSelectThreads * 8 - 1) / (kSelectThreads * 8);
+    long long b = (n + kSelectThreads * 2 - 1) / (kSelectThreads * 2);
     if (b < 1) b = 1;
     if (b > kSelectBlocks) b = kSelectBlocks;
     return (int)b;
@@ -1926,7 +1940,7 @@ __global__ void __launch_bounds__(kDirThreads) k_tabu_small(TabuBuffers w, const
         if (st->done || st->t >= st->t_end) break;
         const int nC = st->nC;
         for (int by = 0; by * kDirJ < nC; by++) {
-            swap_direct_body(w, cost, 0, by, seg);
+            swap_direct_body<kDirJ>(w, cost, 0, by, seg);
             __syncthreads();
         }
         select_body(w, 0, 1);
@@ -1961,7 +1975,13 @@ cudaError_t kernels_init()
     e = cudaFuncSetAttribute(k_swap_stream, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)swap_stream_smem(kPipeMaxK));
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_swap_direct, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    e = cudaFuncSetAttribute(k_swap_direct<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)swap_direct_smem(kPipeMaxK));
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_swap_direct<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)swap_direct_smem(kPipeMaxK));
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_swap_direct<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)swap_direct_smem(kPipeMaxK));
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(k_tabu_small, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -2037,7 +2057,7 @@ k_group_swap(const GroupSlot *__restrict__ slots, const int2 *__restrict__ map)
     load_slot(slots, e.x, g);
     const TabuDevState *st = g.w.st;
     if (st->done || st->t >= st->t_end) return;
-    swap_direct_body(g.w, g.cost, e.y % g.swap_bx, e.y / g.swap_bx, g.swap_seg);
+    swap_direct_body<kDirJ>(g.w, g.cost, e.y % g.swap_bx, e.y / g.swap_bx, g.swap_seg);
 }
 
 cudaError_t launch_group_swap(const GroupSlot *slots, const int2 *map, int total_blocks, size_t smem,
