@@ -1526,21 +1526,74 @@ __device__ __forceinline__ MoveKey load_key_cg(const MoveKey *p)
     return k;
 }
 
+// The best key of a warp under key_better's order (valid first; covered desc,
+// distance asc, i asc, j asc), left in every lane: one 32-bit warp reduction per
+// field of the order on the lanes still tied, then the winner's key is read
+// from its lane.  Covered counts fit 31 bits, distances are non-negative and
+// base ids fit 16 bits.
+__device__ __forceinline__ void warp_best_key(MoveKey &k)
+{
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    unsigned tied = __ballot_sync(full, k.valid);
+    if (!tied) return;
+    const bool in1 = (tied >> lane) & 1u;
+    const int cv = in1 ? (int)k.cov : -1;
+    const int bc = __reduce_max_sync(full, cv);
+    tied = __ballot_sync(full, in1 && cv == bc);
+    const bool in2 = (tied >> lane) & 1u;
+    const unsigned dh = in2 ? (unsigned)((unsigned long long)k.dist >> 32) : 0xffffffffu;
+    const unsigned bdh = __reduce_min_sync(full, dh);
+    tied = __ballot_sync(full, in2 && dh == bdh);
+    const bool in3 = (tied >> lane) & 1u;
+    const unsigned dl = in3 ? (unsigned)(unsigned long long)k.dist : 0xffffffffu;
+    const unsigned bdl = __reduce_min_sync(full, dl);
+    tied = __ballot_sync(full, in3 && dl == bdl);
+    const bool in4 = (tied >> lane) & 1u;
+    const unsigned ij = in4 ? (((unsigned)k.i << 16) | (unsigned)k.j) : 0xffffffffu;
+    const unsigned bij = __reduce_min_sync(full, ij);
+    tied = __ballot_sync(full, in4 && ij == bij);
+    const int src = __ffs(tied) - 1;
+    MoveKey o;
+    o.cov = __shfl_sync(full, k.cov, src);
+    o.dist = __shfl_sync(full, k.dist, src);
+    o.i = __shfl_sync(full, k.i, src);
+    o.j = __shfl_sync(full, k.j, src);
+    o.s = __shfl_sync(full, k.s, src);
+    o.c = __shfl_sync(full, k.c, src);
+    o.valid = __shfl_sync(full, k.valid, src);
+    o.tabu = __shfl_sync(full, k.tabu, src);
+    k = o;
+}
+
+// Best admissible and best overall key of a block: warp reductions, then one
+// warp over the warps' winners.  Every thread receives the results.
 template <int NT>
 __device__ __forceinline__ void block_best2(MoveKey &adm, MoveKey &all, MoveKey *s_adm, MoveKey *s_all)
 {
-    s_adm[threadIdx.x] = adm;
-    s_all[threadIdx.x] = all;
-    __syncthreads();
-    for (int h = NT / 2; h > 0; h >>= 1) {
-        if (threadIdx.x < h) {
-            if (key_better(s_adm[threadIdx.x + h], s_adm[threadIdx.x])) s_adm[threadIdx.x] = s_adm[threadIdx.x + h];
-            if (key_better(s_all[threadIdx.x + h], s_all[threadIdx.x])) s_all[threadIdx.x] = s_all[threadIdx.x + h];
-        }
-        __syncthreads();
+    static_assert(NT % 32 == 0 && NT <= 1024, "block of whole warps");
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    warp_best_key(adm);
+    warp_best_key(all);
+    if (lane == 0) {
+        s_adm[wid] = adm;
+        s_all[wid] = all;
     }
+    __syncthreads();
+    if (wid == 0) {
+        adm = lane < NT / 32 ? s_adm[lane] : invalid_key();
+        all = lane < NT / 32 ? s_all[lane] : invalid_key();
+        warp_best_key(adm);
+        warp_best_key(all);
+        if (lane == 0) {
+            s_adm[0] = adm;
+            s_all[0] = all;
+        }
+    }
+    __syncthreads();
     adm = s_adm[0];
     all = s_all[0];
+    __syncthreads();
 }
 
 // Scan candidates [q0, total) with stride `step` into the best admissible and
@@ -1631,7 +1684,7 @@ __device__ __forceinline__ void select_apply(const TabuBuffers &w, const MoveKey
 __device__ __forceinline__ void select_body(const TabuBuffers &w, int bid, int nb)
 {
     TabuDevState *st = w.st;
-    __shared__ MoveKey s_adm[kSelectThreads], s_all[kSelectThreads];
+    __shared__ MoveKey s_adm[kSelectThreads / 32], s_all[kSelectThreads / 32];
     __shared__ int s_last;
     const int t = st->t;
     const int nC = st->nC;
@@ -1957,6 +2010,382 @@ cudaError_t launch_tabu_small(const TabuBuffers &w, const int32_t *cost, int ite
     return cudaGetLastError();
 }
 
+// --------------------------------------------------------------------------
+// Small instances, resident form: the whole Tabu search in one block of 1024
+// threads with every per-iteration array in shared memory -- best / second
+// best per mission, gain and extra per candidate position, loss, the
+// placement, the candidate list and the tabu expiries.  Only the cost table
+// (L2-resident at these sizes) and the trajectory live in global memory.  One
+// iteration: the swap pass (a warp per candidate position, so each gain and
+// extra entry has a single writer), the selection (warp-shuffle then one
+// warp), the move by one thread, the refresh.  Same rules and tie-breaks as
+// the multi-kernel path; the state is written back at the end.
+// --------------------------------------------------------------------------
+constexpr int kResThreads = 1024;
+constexpr int kResWarps = kResThreads / 32;
+
+struct ResLayout {
+    size_t gain_d, extra_d, loss_d, gain_c, extra_c, loss_c, a, b, s1, s2, open, cand, expiry, bytes;
+};
+
+__host__ __device__ inline ResLayout res_layout(int K, int B, int M_pad, int nC)
+{
+    ResLayout L;
+    size_t o = 0;
+    auto take = [&](size_t n, size_t al) {
+        o = (o + al - 1) / al * al;
+        const size_t at = o;
+        o += n;
+        return at;
+    };
+    L.gain_d = take((size_t)nC * 8, 8);
+    L.extra_d = take((size_t)K * nC * 8, 8);
+    L.loss_d = take((size_t)K * 8, 8);
+    L.gain_c = take((size_t)nC * 4, 4);
+    L.extra_c = take((size_t)K * nC * 4, 4);
+    L.loss_c = take((size_t)K * 4, 4);
+    L.a = take((size_t)M_pad * 4, 16);
+    L.b = take((size_t)M_pad * 4, 16);
+    L.s1 = take((size_t)M_pad * 2, 16);
+    L.s2 = take((size_t)M_pad * 2, 16);
+    L.open = take((size_t)K * 4, 4);
+    L.cand = take((size_t)nC * 4, 4);
+    L.expiry = take((size_t)B * 4, 4);
+    L.bytes = (o + 15) / 16 * 16;
+    return L;
+}
+
+// Bytes of the resident kernel's shared memory with the cost table staged in
+// it too (0 when it does not fit: the table is then read from global memory).
+__host__ __device__ inline size_t res_bytes_with_table(int K, int B, int M_pad, int nC)
+{
+    const size_t base = res_layout(K, B, M_pad, nC).bytes;
+    const size_t all = base + (size_t)B * M_pad * 4;
+    return all <= 160 * 1024 ? all : 0;
+}
+
+constexpr size_t kResMaxSmem = 160 * 1024;
+
+bool tabu_resident_fits(int K, int B, int M_pad, int nC)
+{
+    return (long long)nC * M_pad <= kSmallElems && K <= kPipeMaxK &&
+           res_layout(K, B, M_pad, nC).bytes <= kResMaxSmem;
+}
+
+__global__ void __launch_bounds__(kResThreads, 1) k_tabu_resident(TabuBuffers w, const int32_t *__restrict__ cost,
+                                                                 int iters)
+{
+    extern __shared__ __align__(16) unsigned char sm_res[];
+    TabuDevState *gst = w.st;
+    const int K = w.K, B = w.B, M = w.M, R = w.R;
+    const size_t M_pad = w.M_pad;
+    const int nC = gst->nC;
+    const ResLayout L = res_layout(K, B, (int)M_pad, nC);
+    long long *gain_d = reinterpret_cast<long long *>(sm_res + L.gain_d);
+    long long *extra_d = reinterpret_cast<long long *>(sm_res + L.extra_d);
+    long long *loss_d = reinterpret_cast<long long *>(sm_res + L.loss_d);
+    int *gain_c = reinterpret_cast<int *>(sm_res + L.gain_c);
+    int *extra_c = reinterpret_cast<int *>(sm_res + L.extra_c);
+    int *loss_c = reinterpret_cast<int *>(sm_res + L.loss_c);
+    int *sa = reinterpret_cast<int *>(sm_res + L.a);
+    int *sb = reinterpret_cast<int *>(sm_res + L.b);
+    int16_t *ss1 = reinterpret_cast<int16_t *>(sm_res + L.s1);
+    int16_t *ss2 = reinterpret_cast<int16_t *>(sm_res + L.s2);
+    int *open = reinterpret_cast<int *>(sm_res + L.open);
+    int *cand = reinterpret_cast<int *>(sm_res + L.cand);
+    int *expiry = reinterpret_cast<int *>(sm_res + L.expiry);
+    // the cost table: a shared-memory copy when it fits, else global memory
+    // (plain loads below, valid for both)
+    const bool staged = res_bytes_with_table(K, B, (int)M_pad, nC) != 0;
+    const int32_t *tab = cost;
+    if (staged) {
+        int4 *dst = reinterpret_cast<int4 *>(sm_res + L.bytes);
+        const int4 *src = reinterpret_cast<const int4 *>(cost);
+        const size_t n4 = (size_t)B * M_pad / 4;
+        for (size_t q = threadIdx.x; q < n4; q += kResThreads) dst[q] = __ldg(src + q);
+        tab = reinterpret_cast<const int32_t *>(sm_res + L.bytes);
+    }
+    __shared__ MoveKey w_adm[kResWarps], w_all[kResWarps];
+    __shared__ long long s_v0c, s_v0d, s_curc, s_curd, s_bestc, s_bestd;
+    __shared__ long long r_c[kResWarps], r_d[kResWarps];
+    __shared__ int s_t, s_nmoves, s_done, s_err, s_best_iter, s_mv_s, s_mv_j, s_moved, s_newbest;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+
+    // ---- load the state set up by the init / begin kernels
+    for (int m = tid; m < M; m += kResThreads) {
+        sa[m] = w.a[m];
+        sb[m] = w.b[m];
+        ss1[m] = w.s1[m];
+        ss2[m] = w.s2[m];
+    }
+    for (int k = tid; k < K; k += kResThreads) {
+        open[k] = w.open[k];
+        loss_c[k] = (int)(long long)w.loss_c[k];
+        loss_d[k] = (long long)w.loss_d[k];
+    }
+    for (int c = tid; c < nC; c += kResThreads) cand[c] = w.cand[c];
+    for (int b = tid; b < B; b += kResThreads) expiry[b] = w.expiry[b];
+    if (tid == 0) {
+        s_v0c = (long long)w.v0[0];
+        s_v0d = (long long)w.v0[1];
+        s_curc = gst->cur_cov;
+        s_curd = gst->cur_dist;
+        s_bestc = gst->best_cov;
+        s_bestd = gst->best_dist;
+        s_best_iter = gst->best_iter;
+        s_t = gst->t;
+        s_nmoves = gst->n_moves;
+        s_done = gst->done;
+        s_err = 0;
+        s_mv_s = gst->mv_s;
+        s_mv_j = gst->mv_j;
+    }
+    __syncthreads();
+    const int tenure = gst->tenure, accept_worsening = gst->accept_worsening, traj_cap = gst->traj_cap;
+    const int t_end = gst->t_end;
+
+    for (int it = 0; it < iters; it++) {
+        if (s_done || s_t >= t_end) break;
+        // ---- swap pass
+        for (int q = tid; q < K * nC; q += kResThreads) {
+            extra_c[q] = 0;
+            extra_d[q] = 0;
+        }
+        __syncthreads();
+        for (int c = warp; c < nC; c += kResWarps) {
+            const int32_t *row = tab + (size_t)cand[c] * M_pad;
+            int gc = 0;
+            long long gd = 0;
+            for (int m0 = 0; m0 < M; m0 += 32) {
+                const int m = m0 + lane;
+                const bool act = m < M;
+                const int x = act ? row[m] : INT_MAX;
+                const int ap = act ? min(sa[m], R + 1) : 0;
+                const int bp = act ? min(sb[m], R + 1) : INT_MIN;
+                const bool hb = x < bp;
+                if (!__any_sync(0xffffffffu, hb)) continue;
+                const int ca = ap <= R, cb = bp <= R;
+                const int dc = hb ? ca - cb : 0;
+                const long long dd = hb ? (ca ? (long long)max(x, ap) : 0ll) - (cb ? (long long)bp : 0ll) : 0ll;
+                const int key = (dc | (dd != 0)) ? (int)ss1[m] : -1;
+                const unsigned peers = __match_any_sync(0xffffffffu, key);
+                const int sc = (int)__reduce_add_sync(peers, (unsigned)dc);
+                const long long sd = group_sum_small(peers, dd);
+                if (key >= 0 && lane == __ffs(peers) - 1) {
+                    extra_c[key * nC + c] += sc;   // this warp is the only writer of column c
+                    extra_d[key * nC + c] += sd;
+                }
+                if (x < ap) {
+                    gc += 1 - ca;
+                    gd += (long long)x - (ca ? (long long)ap : 0ll);
+                }
+            }
+            gc = (int)__reduce_add_sync(0xffffffffu, (unsigned)gc);
+            gd = warp_sum_ll(gd);
+            if (lane == 0) {
+                gain_c[c] = gc;
+                gain_d[c] = gd;
+            }
+        }
+        __syncthreads();
+        // ---- selection (same keys and rules as k_select)
+        {
+            const int t = s_t;
+            const long long v0c = s_v0c, v0d = s_v0d, bc = s_bestc, bd = s_bestd;
+            MoveKey adm = invalid_key(), all = invalid_key();
+            for (int q = tid; q < K * nC; q += kResThreads) {
+                const int sl = q / nC, c = q % nC;
+                MoveKey k;
+                k.i = open[sl];
+                k.j = cand[c];
+                k.s = sl;
+                k.c = c;
+                k.cov = v0c + gain_c[c] + loss_c[sl] + extra_c[q];
+                k.dist = v0d + gain_d[c] + loss_d[sl] + extra_d[q];
+                k.valid = 1;
+                k.tabu = (t < expiry[k.i]) || (t < expiry[k.j]);
+                if (key_better(k, all)) all = k;
+                if ((!k.tabu || obj_better(k.cov, k.dist, bc, bd)) && key_better(k, adm)) adm = k;
+            }
+            warp_best_key(adm);
+            warp_best_key(all);
+            if (lane == 0) {
+                w_adm[warp] = adm;
+                w_all[warp] = all;
+            }
+            __syncthreads();
+            if (warp == 0) {
+                adm = w_adm[lane];
+                all = w_all[lane];
+                warp_best_key(adm);
+                warp_best_key(all);
+                if (lane == 0) {
+                    s_moved = 0;
+                    s_newbest = 0;
+                    if (!all.valid) {
+                        s_done = 1;
+                    } else if (s_curc != v0c || s_curd != v0d) {
+                        s_err |= kErrObjectiveMismatch;
+                        s_done = 1;
+                    } else {
+                        const MoveKey P = adm.valid ? adm : all;
+                        int flags = adm.valid ? (adm.tabu ? STAGE_MOVE_ASPIRATION : 0) : STAGE_MOVE_FALLBACK;
+                        if (!accept_worsening && !obj_better(P.cov, P.dist, s_curc, s_curd)) {
+                            s_done = 1;
+                        } else {
+                            open[P.s] = P.j;
+                            cand[P.c] = P.i;
+                            expiry[P.i] = t + tenure + 1;
+                            expiry[P.j] = t + tenure + 1;
+                            s_curc = P.cov;
+                            s_curd = P.dist;
+                            if (obj_better(P.cov, P.dist, s_bestc, s_bestd)) {
+                                s_bestc = P.cov;
+                                s_bestd = P.dist;
+                                s_best_iter = t;
+                                flags |= STAGE_MOVE_NEW_BEST;
+                                s_newbest = 1;
+                            }
+                            if (s_nmoves < traj_cap) {
+                                stage_move mv;
+                                mv.iter = t; mv.i = P.i; mv.j = P.j; mv.flags = flags;
+                                mv.cov = P.cov; mv.dist = P.dist;
+                                w.traj[s_nmoves] = mv;
+                            }
+                            s_nmoves += 1;
+                            s_t = t + 1;
+                            s_mv_s = P.s;
+                            s_mv_j = P.j;
+                            s_moved = 1;
+                        }
+                    }
+                }
+            }
+            __syncthreads();
+        }
+        if (!s_moved) continue;   // stopped: the loop condition ends the search
+        if (s_newbest)
+            for (int k = tid; k < K; k += kResThreads) w.best_open[k] = open[k];
+        // ---- refresh (slot s* now holds j*)
+        for (int k = tid; k < K; k += kResThreads) {
+            loss_c[k] = 0;
+            loss_d[k] = 0;
+        }
+        __syncthreads();
+        {
+            const int ssl = s_mv_s, jj = s_mv_j;
+            const int32_t *rowj = tab + (size_t)jj * M_pad;
+            long long v0c = 0, v0d = 0;
+            for (int m0 = 0; m0 < M; m0 += kResThreads) {
+                const int m = m0 + tid;
+                const bool act = m < M;
+                int a = 0, b = 0, k1 = -1, k2 = -1;
+                if (act) {
+                    a = sa[m]; b = sb[m]; k1 = ss1[m]; k2 = ss2[m];
+                    if (k1 != ssl && k2 != ssl) {
+                        const int x = rowj[m];
+                        const int id1 = open[k1];
+                        const int id2 = k2 >= 0 ? open[k2] : 0x7fffffff;
+                        if (x < a || (x == a && jj < id1)) {
+                            k2 = k1; b = a;
+                            k1 = ssl; a = x;
+                        } else if (k2 < 0 || x < b || (x == b && jj < id2)) {
+                            k2 = ssl; b = x;
+                        }
+                    } else {
+                        // best two over the open bases by (cost, base id)
+                        int c1 = kInf, c2 = kInf, i1 = 0x7fffffff, i2 = 0x7fffffff;
+                        k1 = -1;
+                        k2 = -1;
+                        for (int k = 0; k < K; k++) {
+                            const int o = open[k];
+                            const int cv = tab[(size_t)o * M_pad + m];
+                            if (k1 < 0 || cv < c1 || (cv == c1 && o < i1)) {
+                                k2 = k1; c2 = c1; i2 = i1;
+                                k1 = k; c1 = cv; i1 = o;
+                            } else if (k2 < 0 || cv < c2 || (cv == c2 && o < i2)) {
+                                k2 = k; c2 = cv; i2 = o;
+                            }
+                        }
+                        a = c1;
+                        b = c2;
+                    }
+                    sa[m] = a; sb[m] = b; ss1[m] = (int16_t)k1; ss2[m] = (int16_t)k2;
+                }
+                const int ca = act && a <= R, cb = act && b <= R;
+                const long long da = ca ? a : 0, db = cb ? b : 0;
+                v0c += ca;
+                v0d += da;
+                const int dc = cb - ca;
+                const long long dd = db - da;
+                const int key = act && (dc | (dd != 0)) ? k1 : -1;
+                const unsigned peers = __match_any_sync(0xffffffffu, key);
+                const int sc = (int)__reduce_add_sync(peers, (unsigned)dc);
+                const long long sd = group_sum_small(peers, dd);
+                if (key >= 0 && lane == __ffs(peers) - 1) {
+                    atomicAdd(&loss_c[key], sc);
+                    atomicAdd(reinterpret_cast<unsigned long long *>(&loss_d[key]), (unsigned long long)sd);
+                }
+            }
+            v0c = warp_sum_ll(v0c);
+            v0d = warp_sum_ll(v0d);
+            if (lane == 0) {
+                r_c[warp] = v0c;
+                r_d[warp] = v0d;
+            }
+            __syncthreads();
+            if (tid == 0) {
+                long long x = 0, y = 0;
+                for (int k = 0; k < kResWarps; k++) {
+                    x += r_c[k];
+                    y += r_d[k];
+                }
+                s_v0c = x;
+                s_v0d = y;
+            }
+            __syncthreads();
+        }
+    }
+    // ---- write the state back
+    __syncthreads();
+    for (int m = tid; m < M; m += kResThreads) {
+        w.a[m] = sa[m];
+        w.b[m] = sb[m];
+        w.s1[m] = ss1[m];
+        w.s2[m] = ss2[m];
+    }
+    for (int k = tid; k < K; k += kResThreads) {
+        w.open[k] = open[k];
+        w.loss_c[k] = (unsigned long long)(long long)loss_c[k];
+        w.loss_d[k] = (unsigned long long)loss_d[k];
+    }
+    for (int c = tid; c < nC; c += kResThreads) w.cand[c] = cand[c];
+    for (int b = tid; b < B; b += kResThreads) w.expiry[b] = expiry[b];
+    if (tid == 0) {
+        w.v0[0] = (unsigned long long)s_v0c;
+        w.v0[1] = (unsigned long long)s_v0d;
+        gst->t = s_t;
+        gst->n_moves = s_nmoves;
+        gst->done = s_done;
+        gst->err |= s_err;
+        gst->cur_cov = s_curc;
+        gst->cur_dist = s_curd;
+        gst->best_cov = s_bestc;
+        gst->best_dist = s_bestd;
+        gst->best_iter = s_best_iter;
+        gst->mv_s = s_mv_s;
+        gst->mv_j = s_mv_j;
+    }
+}
+
+cudaError_t launch_tabu_resident(const TabuBuffers &w, const int32_t *cost, int nC, int iters, cudaStream_t s)
+{
+    const size_t with_table = res_bytes_with_table(w.K, w.B, w.M_pad, nC);
+    const size_t sm = with_table ? with_table : res_layout(w.K, w.B, w.M_pad, nC).bytes;
+    k_tabu_resident<<<1, kResThreads, sm, s>>>(w, cost, iters);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_export_best_two(const TabuBuffers &w, const int *perm, int32_t *a, int32_t *b,
                                    int32_t *b1, int32_t *b2, cudaStream_t s)
 {
@@ -1966,6 +2395,7 @@ cudaError_t launch_export_best_two(const TabuBuffers &w, const int *perm, int32_
 
 __global__ void k_group_swap(const GroupSlot *__restrict__ slots, const int2 *__restrict__ map);
 __global__ void k_tabu_small(TabuBuffers w, const int32_t *__restrict__ cost, int iters);
+__global__ void k_tabu_resident(TabuBuffers w, const int32_t *__restrict__ cost, int iters);
 
 cudaError_t kernels_init()
 {
@@ -1989,6 +2419,8 @@ cudaError_t kernels_init()
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(k_group_swap, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)swap_direct_smem(kGroupMaxK));
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_tabu_resident, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kResMaxSmem);
     if (e != cudaSuccess) return e;
     if (const char *v = getenv("STAGE_SWAP_VARIANT")) g_swap_variant = atoi(v);
     int dev = 0, n = 0;

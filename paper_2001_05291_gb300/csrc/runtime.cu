@@ -439,7 +439,10 @@ stage_status run_tabu(stage_ctx *c, Instance *in, const stage_tabu_params *p,
     CK(timed(c, "begin", 1, [&] { return launch_begin(tb, rs ? 1 : 0, c->stream); }));
     volatile int *done_flag = static_cast<volatile int *>(c->pinned);
     const bool profiling = (c->flags & STAGE_PROFILE) != 0;
-    if (nC > 0 && iters > 0 && tabu_small_fits(nC, in->M_pad, K) && swap_variant_default()) {
+    if (nC > 0 && iters > 0 && tabu_resident_fits(K, in->B, in->M_pad, nC) && swap_variant_default()) {
+        // small instance: the whole search in one block, its arrays in shared memory
+        CK(timed(c, "tabu_small", 1, [&] { return launch_tabu_resident(tb, in->cost, nC, iters, c->stream); }));
+    } else if (nC > 0 && iters > 0 && tabu_small_fits(nC, in->M_pad, K) && swap_variant_default()) {
         // small instance: the whole search in one resident block
         CK(timed(c, "tabu_small", 1, [&] { return launch_tabu_small(tb, in->cost, iters, c->stream); }));
     } else if (nC > 0 && iters >= kGraphIters && !profiling) {

@@ -131,6 +131,9 @@ size_t swap_direct_smem(int K);   // dynamic shared memory of the direct swap pa
 bool tabu_small_fits(int nC, int M_pad, int K);
 bool swap_variant_default();   // the direct swap pass is selected (STAGE_SWAP_VARIANT unset or 0)
 cudaError_t launch_tabu_small(const TabuBuffers &w, const int32_t *cost, int iters, cudaStream_t s);
+// small instances, every per-iteration array in shared memory (one block)
+bool tabu_resident_fits(int K, int B, int M_pad, int nC);
+cudaError_t launch_tabu_resident(const TabuBuffers &w, const int32_t *cost, int nC, int iters, cudaStream_t s);
 // local search: first improving swap at or after the scan position of the
 // current pass (rank_slot / rank_cand: [passes][K] / [passes][nC] positions)
 cudaError_t launch_ls_select(const TabuBuffers &w, int nC, const int *rank_slot, const int *rank_cand,
