@@ -337,6 +337,17 @@ def run_ours(args):
         per_run = s0.elapsed_time(s1) / reps
         search = {"ms_per_search": per_run, "us_per_iteration": 1000.0 * per_run / max(1, r.n_moves),
                   "iterations": r.n_moves}
+        # the same search with per-kernel CUDA events: device time of the
+        # search kernels alone (no host set-up or read-back)
+        with stage.Context(device=local, profile=True) as pctx:
+            hp = pctx.load_instance(*dev)
+            pctx.tabu_run(hp, inst.K, inst.R, inst.iters, inst.tenure)
+            pctx.reset_stats()
+            pr = pctx.tabu_run(hp, inst.K, inst.R, inst.iters, inst.tenure)
+            dev_ms = sum(pctx.kernel_stats(k)[1] for k in ("tabu_small", "swap_eval", "select", "refresh"))
+            pctx.unload_instance(hp)
+        search["kernel_ms_per_search"] = dev_ms
+        search["kernel_us_per_iteration"] = 1000.0 * dev_ms / max(1, pr.n_moves)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

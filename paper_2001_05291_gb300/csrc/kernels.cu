@@ -1830,14 +1830,28 @@ __device__ __forceinline__ bool ls_first(const LsKey &a, const LsKey &b)
     return a.valid && (!b.valid || a.u < b.u);
 }
 
+// Smallest scan position of a block (every thread receives the key): a warp
+// minimum, then one warp over the warps' winners.  Positions are unique.
 __device__ __forceinline__ void ls_block_first(LsKey &k, LsKey *sh)
 {
-    sh[threadIdx.x] = k;
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    unsigned u = k.valid ? (unsigned)k.u : 0xffffffffu;
+    unsigned bu = __reduce_min_sync(full, u);
+    if (lane == __ffs(__ballot_sync(full, u == bu)) - 1) sh[wid] = k;
     __syncthreads();
-    for (int h = kSelectThreads / 2; h > 0; h >>= 1) {
-        if (threadIdx.x < h && ls_first(sh[threadIdx.x + h], sh[threadIdx.x])) sh[threadIdx.x] = sh[threadIdx.x + h];
-        __syncthreads();
+    if (wid == 0) {
+        LsKey c;
+        c.valid = 0;
+        c.u = 0x7fffffff;
+        if (lane < kSelectThreads / 32) c = sh[lane];
+        u = c.valid ? (unsigned)c.u : 0xffffffffu;
+        bu = __reduce_min_sync(full, u);
+        const int src = __ffs(__ballot_sync(full, u == bu)) - 1;
+        __syncwarp();
+        if (lane == src) sh[0] = c;
     }
+    __syncthreads();
     k = sh[0];
     __syncthreads();
 }
@@ -1847,7 +1861,7 @@ __global__ void __launch_bounds__(kSelectThreads) k_ls_select(TabuBuffers w, con
 {
     TabuDevState *st = w.st;
     if (st->done) return;
-    __shared__ LsKey sh[kSelectThreads];
+    __shared__ LsKey sh[kSelectThreads / 32];
     __shared__ int s_last, s_moved;
     const int nC = st->nC, K = w.K, pass = st->ls_pass, u0 = st->ls_pos;
     const int *ra = rank_slot + (size_t)pass * K;
