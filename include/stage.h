@@ -76,6 +76,12 @@ typedef int32_t stage_status;
 
 /* instance descriptor flags */
 #define STAGE_DESC_DEVICE  1u   /* base_xy/pick_xy/drop_xy/base_available are device pointers */
+#define STAGE_DESC_HAVERSINE 2u /* coordinates are (latitude, longitude) in integer microdegrees and
+                                   every leg is the Haversine distance of Eq. 1 on a sphere of radius
+                                   STAGE_EARTH_RADIUS_M, in metres, rounded up */
+#define STAGE_EARTH_RADIUS_M 6371000.0
+#define STAGE_MAX_LAT_UDEG  90000000    /* |latitude| <= 90 degrees */
+#define STAGE_MAX_LON_UDEG  180000000   /* |longitude| <= 180 degrees */
 
 /* trajectory flags */
 #define STAGE_MOVE_FALLBACK   1  /* every move was tabu and none beat the best: best of all taken */
@@ -104,12 +110,14 @@ typedef struct {
 } stage_config;
 
 /* Problem data (Sec. 3): B candidate bases and M missions.  Coordinates are
- * interleaved (x0, y0, x1, y1, ...) int32 metres.  base_available may be NULL
- * (all available); an unavailable base is never opened. */
+ * interleaved (x0, y0, x1, y1, ...) int32 metres in a plane (Euclidean legs),
+ * or, with STAGE_DESC_HAVERSINE, interleaved (latitude, longitude) pairs in
+ * microdegrees (Haversine legs, Eq. 1).  base_available may be NULL (all
+ * available); an unavailable base is never opened. */
 typedef struct {
     int32_t B;
     int32_t M;
-    uint32_t flags;            /* STAGE_DESC_DEVICE */
+    uint32_t flags;            /* STAGE_DESC_DEVICE | STAGE_DESC_HAVERSINE */
     int32_t reserved0;
     const int32_t *base_xy;    /* [2*B] */
     const int32_t *pick_xy;    /* [2*M] pickup points */

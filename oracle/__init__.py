@@ -69,6 +69,10 @@ def lib():
         L.oracle_mission_cost.argtypes = [p, p, p, i32, i32]
         L.oracle_cost_table.restype = None
         L.oracle_cost_table.argtypes = [i32, i32, p, p, p, p, i32]
+        L.oracle_cost_table_metric.restype = None
+        L.oracle_cost_table_metric.argtypes = [i32, i32, p, p, p, p, i32, i32]
+        L.oracle_leg_haversine.restype = i32
+        L.oracle_leg_haversine.argtypes = [i32, i32, i32, i32]
         L.oracle_evaluate.restype = None
         L.oracle_evaluate.argtypes = [i32, i32, p, i32, p, i32, p, p]
         L.oracle_rank.restype = i32
@@ -101,13 +105,18 @@ def leg(x1: int, y1: int, x2: int, y2: int) -> int:
     return int(lib().oracle_leg(x1, y1, x2, y2))
 
 
-def cost_table(base_xy, pick_xy, drop_xy, nthreads: int = 1) -> np.ndarray:
-    """B x M int32 round-trip cost table."""
+def cost_table(base_xy, pick_xy, drop_xy, nthreads: int = 1, haversine: bool = False) -> np.ndarray:
+    """B x M int32 round-trip cost table; haversine: coordinates are (latitude,
+    longitude) microdegrees and the legs follow Eq. 1."""
     bx, px, dx = _i32(base_xy), _i32(pick_xy), _i32(drop_xy)
     B, M = bx.shape[0], px.shape[0]
     out = np.empty((B, M), dtype=np.int32)
-    lib().oracle_cost_table(B, M, _p(bx), _p(px), _p(dx), _p(out), nthreads)
+    lib().oracle_cost_table_metric(B, M, _p(bx), _p(px), _p(dx), _p(out), nthreads, 1 if haversine else 0)
     return out
+
+
+def leg_haversine(lat1: int, lon1: int, lat2: int, lon2: int) -> int:
+    return int(lib().oracle_leg_haversine(lat1, lon1, lat2, lon2))
 
 
 def evaluate(cost: np.ndarray, open_, R: int):

@@ -49,15 +49,44 @@ int32_t oracle_leg(int32_t x1, int32_t y1, int32_t x2, int32_t y2)
     return (int32_t)ceil(d);
 }
 
+/* Eq. 1 (Haversine) between (latitude, longitude) points given in integer
+ * microdegrees, on a sphere of radius 6,371,000 m, rounded up to metres:
+ *   d = 2 r asin(sqrt(sin^2(dphi / 2) + cos(phi1) cos(phi2) sin^2(dpsi / 2))).
+ * The argument of the square root is capped at 1 (antipodes under rounding). */
+#define ORACLE_EARTH_RADIUS_M 6371000.0
+#define ORACLE_UDEG_TO_RAD (3.14159265358979323846 / 180.0 * 1e-6)
+
+int32_t oracle_leg_haversine(int32_t lat1, int32_t lon1, int32_t lat2, int32_t lon2)
+{
+    double phi1 = (double)lat1 * ORACLE_UDEG_TO_RAD, phi2 = (double)lat2 * ORACLE_UDEG_TO_RAD;
+    double dphi = (double)(lat2 - lat1) * ORACLE_UDEG_TO_RAD;
+    double dpsi = (double)(lon2 - lon1) * ORACLE_UDEG_TO_RAD;
+    double sp = sin(0.5 * dphi), sl = sin(0.5 * dpsi);
+    double h = sp * sp + (cos(phi1) * cos(phi2)) * (sl * sl);
+    if (h > 1.0) h = 1.0;
+    double d = (2.0 * ORACLE_EARTH_RADIUS_M) * asin(sqrt(h));
+    return (int32_t)ceil(d);
+}
+
 /* Round-trip cost of mission m flown from base b: the three legs of the
- * mission of Sec. 3 (base -> pickup, pickup -> drop-off, drop-off -> base). */
-int32_t oracle_mission_cost(const int32_t *base_xy, const int32_t *pick_xy,
-                            const int32_t *drop_xy, int32_t b, int32_t m)
+ * mission of Sec. 3 (base -> pickup, pickup -> drop-off, drop-off -> base),
+ * Euclidean on metres (metric 0) or Eq. 1's Haversine on microdegrees (1). */
+int32_t oracle_mission_cost_metric(const int32_t *base_xy, const int32_t *pick_xy,
+                                   const int32_t *drop_xy, int32_t b, int32_t m, int32_t metric)
 {
     int32_t bx = base_xy[2 * b], by = base_xy[2 * b + 1];
     int32_t px = pick_xy[2 * m], py = pick_xy[2 * m + 1];
     int32_t qx = drop_xy[2 * m], qy = drop_xy[2 * m + 1];
+    if (metric == 1)
+        return oracle_leg_haversine(bx, by, px, py) + oracle_leg_haversine(px, py, qx, qy) +
+               oracle_leg_haversine(qx, qy, bx, by);
     return oracle_leg(bx, by, px, py) + oracle_leg(px, py, qx, qy) + oracle_leg(qx, qy, bx, by);
+}
+
+int32_t oracle_mission_cost(const int32_t *base_xy, const int32_t *pick_xy,
+                            const int32_t *drop_xy, int32_t b, int32_t m)
+{
+    return oracle_mission_cost_metric(base_xy, pick_xy, drop_xy, b, m, 0);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -65,7 +94,7 @@ int32_t oracle_mission_cost(const int32_t *base_xy, const int32_t *pick_xy,
 /* cost is B x M, row-major (row = base).                                    */
 /* ------------------------------------------------------------------------ */
 typedef struct {
-    int32_t B, M, m0, m1;
+    int32_t B, M, m0, m1, metric;
     const int32_t *base_xy, *pick_xy, *drop_xy;
     int32_t *cost;
 } table_job;
@@ -76,12 +105,21 @@ static void *table_worker(void *p)
     for (int32_t b = 0; b < t->B; b++)
         for (int32_t m = t->m0; m < t->m1; m++)
             t->cost[(size_t)b * t->M + m] =
-                oracle_mission_cost(t->base_xy, t->pick_xy, t->drop_xy, b, m);
+                oracle_mission_cost_metric(t->base_xy, t->pick_xy, t->drop_xy, b, m, t->metric);
     return NULL;
 }
 
+void oracle_cost_table_metric(int32_t B, int32_t M, const int32_t *base_xy, const int32_t *pick_xy,
+                              const int32_t *drop_xy, int32_t *cost, int32_t nthreads, int32_t metric);
+
 void oracle_cost_table(int32_t B, int32_t M, const int32_t *base_xy, const int32_t *pick_xy,
                        const int32_t *drop_xy, int32_t *cost, int32_t nthreads)
+{
+    oracle_cost_table_metric(B, M, base_xy, pick_xy, drop_xy, cost, nthreads, 0);
+}
+
+void oracle_cost_table_metric(int32_t B, int32_t M, const int32_t *base_xy, const int32_t *pick_xy,
+                              const int32_t *drop_xy, int32_t *cost, int32_t nthreads, int32_t metric)
 {
     if (nthreads < 1) nthreads = 1;
     pthread_t th[256];
@@ -93,6 +131,7 @@ void oracle_cost_table(int32_t B, int32_t M, const int32_t *base_xy, const int32
         jobs[t].m1 = (int32_t)((int64_t)M * (t + 1) / nthreads);
         jobs[t].base_xy = base_xy; jobs[t].pick_xy = pick_xy; jobs[t].drop_xy = drop_xy;
         jobs[t].cost = cost;
+        jobs[t].metric = metric;
         if (nthreads == 1) table_worker(&jobs[t]);
         else pthread_create(&th[t], NULL, table_worker, &jobs[t]);
     }

@@ -44,6 +44,7 @@ struct Ticket {
     bool inline_inst = false;              // instance given by value: loaded and unloaded here
     std::vector<int32_t> d_base, d_pick, d_drop;
     std::vector<uint8_t> d_avail;
+    uint32_t d_flags = 0;                  // STAGE_DESC_HAVERSINE of the inline instance
     stage_inst inst = 0;
     stage_result res{};
     int state = 0;                         // 0 pending, 1 running, 2 done
@@ -166,6 +167,7 @@ bool Engine::admit(Ticket *tk, bool &transient, stage_inst &busy_on)
             d.pick_xy = tk->d_pick.data();
             d.drop_xy = tk->d_drop.data();
             d.base_available = tk->d_avail.empty() ? nullptr : tk->d_avail.data();
+            d.flags = tk->d_flags;
             stage_inst h = 0;
             s = stage_load_instance(c, &d, &h);
             if (s == STAGE_ERR_ADMISSION || s == STAGE_ERR_NO_MEMORY) {
@@ -771,6 +773,7 @@ stage_status stage_batch_submit(stage_ctx *c, const stage_request *reqs, int32_t
             tk->d_pick.assign(d->pick_xy, d->pick_xy + 2 * (size_t)d->M);
             tk->d_drop.assign(d->drop_xy, d->drop_xy + 2 * (size_t)d->M);
             if (d->base_available) tk->d_avail.assign(d->base_available, d->base_available + d->B);
+            tk->d_flags = d->flags & STAGE_DESC_HAVERSINE;
         }
         if (copy_update(tk.get(), r.update) != STAGE_OK)
             return set_err(c, STAGE_ERR_INVALID_ARG, "request %d: malformed update", k);

@@ -36,6 +36,44 @@ __device__ __forceinline__ int32_t leg_ceil(int x1, int y1, int x2, int y2)
     return (int32_t)(s + (s * s != n ? 1 : 0));
 }
 
+// Leg cost of Eq. 1 (Haversine) for points given as (latitude, longitude) in
+// microdegrees, in metres on a sphere of radius STAGE_EARTH_RADIUS_M, rounded
+// up; c1, c2 are the cosines of the two latitudes (computed once per point).
+// The products and sums use explicit round-to-nearest operations (no fused
+// multiply-add), in the order the CPU oracle uses, so that only the sine,
+// cosine and arcsine implementations can differ between the two.
+constexpr double kMicroDegToRad = 3.14159265358979323846 / 180.0 * 1e-6;
+
+__device__ __forceinline__ double lat_cos(int lat)
+{
+    return cos(__dmul_rn((double)lat, kMicroDegToRad));
+}
+
+__device__ __forceinline__ int32_t leg_haversine(int lat1, int lon1, double c1, int lat2, int lon2, double c2)
+{
+    const double dp = __dmul_rn((double)(lat2 - lat1), kMicroDegToRad);
+    const double dl = __dmul_rn((double)(lon2 - lon1), kMicroDegToRad);
+    const double sp = sin(__dmul_rn(0.5, dp)), sl = sin(__dmul_rn(0.5, dl));
+    double h = __dadd_rn(__dmul_rn(sp, sp), __dmul_rn(__dmul_rn(c1, c2), __dmul_rn(sl, sl)));
+    h = fmin(h, 1.0);
+    const double d = __dmul_rn(2.0 * STAGE_EARTH_RADIUS_M, asin(sqrt(h)));
+    return (int32_t)ceil(d);
+}
+
+// Leg by metric: 0 = Euclidean on integer metres, 1 = Haversine.
+template <int Metric>
+__device__ __forceinline__ int32_t leg_of(int2 u, double cu, int2 v, double cv)
+{
+    if (Metric == 0) return leg_ceil(u.x, u.y, v.x, v.y);
+    return leg_haversine(u.x, u.y, cu, v.x, v.y, cv);
+}
+
+template <int Metric>
+__device__ __forceinline__ double point_cos(int2 u)
+{
+    return Metric == 0 ? 0.0 : lat_cos(u.x);
+}
+
 // L2 cache policy for data read once per pass: evict it before other lines.
 __device__ __forceinline__ unsigned long long evict_first_policy()
 {
@@ -112,7 +150,7 @@ __global__ void k_mid_bbox(int M, const int2 *__restrict__ pick, const int2 *__r
     int mnx = INT_MAX, mny = INT_MAX, mxx = INT_MIN, mxy = INT_MIN;
     for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < M; m += gridDim.x * blockDim.x) {
         const int2 p = pick[m], d = drop[m];
-        const int x = (p.x + d.x) >> 1, y = (p.y + d.y) >> 1;   // |sum| < 2^25
+        const int x = (p.x + d.x) >> 1, y = (p.y + d.y) >> 1;   // |sum| < 2^29 (metres or microdegrees)
         mnx = min(mnx, x); mny = min(mny, y); mxx = max(mxx, x); mxy = max(mxy, y);
     }
 #pragma unroll
@@ -312,12 +350,13 @@ cudaError_t launch_gather_window(const int32_t *cost, int M, int M_pad, const in
 // a1: cost table.  c[b][m] = leg(b, p_m) + leg(p_m, d_m) + leg(d_m, b).
 // --------------------------------------------------------------------------
 
+template <int Metric>
 __global__ void k_pickup_drop_leg(int M, const int2 *__restrict__ pick,
                                   const int2 *__restrict__ drop, int32_t *__restrict__ pd)
 {
     for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < M; m += gridDim.x * blockDim.x) {
-        int2 p = pick[m], d = drop[m];
-        pd[m] = leg_ceil(p.x, p.y, d.x, d.y);
+        const int2 p = pick[m], d = drop[m];
+        pd[m] = leg_of<Metric>(p, point_cos<Metric>(p), d, point_cos<Metric>(d));
     }
 }
 
@@ -325,6 +364,7 @@ constexpr int kTableBasesPerBlock = 8;
 
 // Each thread owns 4 consecutive missions and writes them for 8 bases (one
 // 16-byte store per base row); pads (m >= M) hold INT32_MAX.
+template <int Metric>
 __global__ void __launch_bounds__(256) k_build_table(int B, int M, int M_pad,
                                                      const int2 *__restrict__ base,
                                                      const int2 *__restrict__ pick,
@@ -337,45 +377,50 @@ __global__ void __launch_bounds__(256) k_build_table(int B, int M, int M_pad,
     for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n4; q += gridDim.x * blockDim.x) {
         const int m = q << 2;
         int2 p[4], d[4];
+        double cp[4], cd[4];
         int l[4];
 #pragma unroll
         for (int e = 0; e < 4; e++) {
             if (m + e < M) { p[e] = pick[m + e]; d[e] = drop[m + e]; l[e] = pd[m + e]; }
             else { p[e] = make_int2(0, 0); d[e] = make_int2(0, 0); l[e] = -1; }
+            cp[e] = point_cos<Metric>(p[e]);
+            cd[e] = point_cos<Metric>(d[e]);
         }
 #pragma unroll 1
         for (int bb = 0; bb < kTableBasesPerBlock; bb++) {
             const int b = b0 + bb;
             if (b >= B) break;
             const int2 o = base[b];
+            const double co = point_cos<Metric>(o);
             int v[4];
 #pragma unroll
             for (int e = 0; e < 4; e++)
-                v[e] = (l[e] >= 0) ? leg_ceil(o.x, o.y, p[e].x, p[e].y) + l[e] +
-                                         leg_ceil(d[e].x, d[e].y, o.x, o.y)
+                v[e] = (l[e] >= 0) ? leg_of<Metric>(o, co, p[e], cp[e]) + l[e] + leg_of<Metric>(d[e], cd[e], o, co)
                                    : kInf;
             reinterpret_cast<int4 *>(cost + (size_t)b * M_pad)[q] = make_int4(v[0], v[1], v[2], v[3]);
         }
     }
 }
 
-// Input check: flag |coordinate| > STAGE_MAX_COORD (device-resident inputs).
-__global__ void k_check_coords(const int32_t *__restrict__ v, size_t n, int *__restrict__ bad)
+// Input check (device-resident inputs): flag an interleaved (x, y) value
+// outside [-lim_x, lim_x] x [-lim_y, lim_y].
+__global__ void k_check_coords(const int32_t *__restrict__ v, size_t n, int lim_x, int lim_y,
+                               int *__restrict__ bad)
 {
     int found = 0;
     for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) {
-        const int x = v[k];
-        found |= (x > STAGE_MAX_COORD) | (x < -STAGE_MAX_COORD);
+        const int x = v[k], lim = (k & 1) ? lim_y : lim_x;
+        found |= (x > lim) | (x < -lim);
     }
     if (__syncthreads_or(found) && threadIdx.x == 0) atomicOr(bad, 1);
 }
 
-cudaError_t launch_check_coords(const int32_t *v, size_t n, int *bad, cudaStream_t s)
+cudaError_t launch_check_coords(const int32_t *v, size_t n, int lim_x, int lim_y, int *bad, cudaStream_t s)
 {
     size_t g = (n + 255) / 256;
     if (g > 1024) g = 1024;
     if (g == 0) return cudaSuccess;
-    k_check_coords<<<(int)g, 256, 0, s>>>(v, n, bad);
+    k_check_coords<<<(int)g, 256, 0, s>>>(v, n, lim_x, lim_y, bad);
     return cudaGetLastError();
 }
 
@@ -395,6 +440,7 @@ cudaError_t launch_fill_i32(int32_t *p, size_t n, int32_t v, cudaStream_t s)
 }
 
 // Costs of columns [col0, col0 + n) for every base (missions appended at the end).
+template <int Metric>
 __global__ void k_table_columns(int B, int col0, int n, int M_pad, const int2 *__restrict__ base,
                                 const int2 *__restrict__ pick, const int2 *__restrict__ drop,
                                 int32_t *__restrict__ pd, int32_t *__restrict__ cost)
@@ -403,20 +449,24 @@ __global__ void k_table_columns(int B, int col0, int n, int M_pad, const int2 *_
     for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < total; q += (size_t)gridDim.x * blockDim.x) {
         const int b = (int)(q / n), col = col0 + (int)(q % n);
         const int2 p = pick[col], d = drop[col], o = base[b];
-        const int l = leg_ceil(p.x, p.y, d.x, d.y);
+        const double cp = point_cos<Metric>(p), cd = point_cos<Metric>(d), co = point_cos<Metric>(o);
+        const int l = leg_of<Metric>(p, cp, d, cd);
         if (b == 0) pd[col] = l;
-        cost[(size_t)b * M_pad + col] = leg_ceil(o.x, o.y, p.x, p.y) + l + leg_ceil(d.x, d.y, o.x, o.y);
+        cost[(size_t)b * M_pad + col] = leg_of<Metric>(o, co, p, cp) + l + leg_of<Metric>(d, cd, o, co);
     }
 }
 
 cudaError_t launch_table_columns(int B, int col0, int n, int M_pad, const int2 *base, const int2 *pick,
-                                 const int2 *drop, int32_t *pd, int32_t *cost, cudaStream_t s)
+                                 const int2 *drop, int32_t *pd, int32_t *cost, int metric, cudaStream_t s)
 {
     size_t total = (size_t)B * n;
     size_t g = (total + 255) / 256;
     if (g > 8192) g = 8192;
     if (g == 0) return cudaSuccess;
-    k_table_columns<<<(int)g, 256, 0, s>>>(B, col0, n, M_pad, base, pick, drop, pd, cost);
+    if (metric == 1)
+        k_table_columns<1><<<(int)g, 256, 0, s>>>(B, col0, n, M_pad, base, pick, drop, pd, cost);
+    else
+        k_table_columns<0><<<(int)g, 256, 0, s>>>(B, col0, n, M_pad, base, pick, drop, pd, cost);
     return cudaGetLastError();
 }
 
@@ -446,17 +496,22 @@ cudaError_t launch_tombstone(const int32_t *ids, int n, int32_t *inv, int32_t *p
 }
 
 cudaError_t launch_table(int B, int M, int M_pad, const int2 *base, const int2 *pick,
-                         const int2 *drop, int32_t *pd, int32_t *cost, cudaStream_t s)
+                         const int2 *drop, int32_t *pd, int32_t *cost, int metric, cudaStream_t s)
 {
     int g1 = (M + 255) / 256;
     if (g1 > 4096) g1 = 4096;
-    k_pickup_drop_leg<<<g1, 256, 0, s>>>(M, pick, drop, pd);
     int n4 = M_pad / 4;
     int gx = (n4 + 255) / 256;
     int gy = (B + kTableBasesPerBlock - 1) / kTableBasesPerBlock;
     // enough blocks for every SM even when B is small
     if (gx > 1024) gx = 1024;
-    k_build_table<<<dim3(gx, gy), 256, 0, s>>>(B, M, M_pad, base, pick, drop, pd, cost);
+    if (metric == 1) {
+        k_pickup_drop_leg<1><<<g1, 256, 0, s>>>(M, pick, drop, pd);
+        k_build_table<1><<<dim3(gx, gy), 256, 0, s>>>(B, M, M_pad, base, pick, drop, pd, cost);
+    } else {
+        k_pickup_drop_leg<0><<<g1, 256, 0, s>>>(M, pick, drop, pd);
+        k_build_table<0><<<dim3(gx, gy), 256, 0, s>>>(B, M, M_pad, base, pick, drop, pd, cost);
+    }
     return cudaGetLastError();
 }
 

@@ -799,6 +799,10 @@ stage_status stage_load_instance(stage_ctx *c, const stage_instance_desc *d, sta
     if (d->M > STAGE_MAX_MISSIONS) return set_err(c, STAGE_ERR_OUT_OF_RANGE, "M=%d > %d", d->M, STAGE_MAX_MISSIONS);
     CK(cudaSetDevice(c->device));
     const bool on_dev = (d->flags & STAGE_DESC_DEVICE) != 0;
+    const int metric = (d->flags & STAGE_DESC_HAVERSINE) ? 1 : 0;
+    // coordinate bounds: metres in a plane, or latitude / longitude in microdegrees
+    const int lim_x = metric ? STAGE_MAX_LAT_UDEG : STAGE_MAX_COORD;
+    const int lim_y = metric ? STAGE_MAX_LON_UDEG : STAGE_MAX_COORD;
     const int B = d->B, M = d->M;
     const int M_pad = (int)round_up((size_t)M, kPadMissions);
     std::vector<uint8_t> avail(B, 1);
@@ -812,27 +816,32 @@ stage_status stage_load_instance(stage_ctx *c, const stage_instance_desc *d, sta
         if (s0 != STAGE_OK) return s0;
         int *dflag = static_cast<int *>(fb.p);
         cudaError_t e0 = cudaMemsetAsync(dflag, 0, 4, c->stream);
-        if (e0 == cudaSuccess) e0 = launch_check_coords(d->base_xy, 2 * (size_t)B, dflag, c->stream);
-        if (e0 == cudaSuccess) e0 = launch_check_coords(d->pick_xy, 2 * (size_t)M, dflag, c->stream);
-        if (e0 == cudaSuccess) e0 = launch_check_coords(d->drop_xy, 2 * (size_t)M, dflag, c->stream);
+        if (e0 == cudaSuccess) e0 = launch_check_coords(d->base_xy, 2 * (size_t)B, lim_x, lim_y, dflag, c->stream);
+        if (e0 == cudaSuccess) e0 = launch_check_coords(d->pick_xy, 2 * (size_t)M, lim_x, lim_y, dflag, c->stream);
+        if (e0 == cudaSuccess) e0 = launch_check_coords(d->drop_xy, 2 * (size_t)M, lim_x, lim_y, dflag, c->stream);
         if (e0 == cudaSuccess) e0 = cudaMemcpyAsync(flag, dflag, 4, cudaMemcpyDeviceToHost, c->stream);
         if (e0 == cudaSuccess) e0 = cudaStreamSynchronize(c->stream);
         dev_free(c, fb);
         if (e0 != cudaSuccess) return set_err(c, STAGE_ERR_CUDA, "input check failed: %s", cudaGetErrorString(e0));
-        if (*flag) return set_err(c, STAGE_ERR_OUT_OF_RANGE, "a coordinate exceeds |%d| m", STAGE_MAX_COORD);
+        if (*flag) return set_err(c, STAGE_ERR_OUT_OF_RANGE, "a coordinate is outside [-%d, %d] x [-%d, %d]", lim_x,
+                                  lim_x, lim_y, lim_y);
     } else {
         if (d->base_available) std::copy(d->base_available, d->base_available + B, avail.begin());
-        auto bad = [](const int32_t *v, size_t n) {
-            for (size_t k = 0; k < n; k++)
-                if (v[k] > STAGE_MAX_COORD || v[k] < -STAGE_MAX_COORD) return true;
+        auto bad = [&](const int32_t *v, size_t n) {
+            for (size_t k = 0; k < n; k++) {
+                const int lim = (k & 1) ? lim_y : lim_x;
+                if (v[k] > lim || v[k] < -lim) return true;
+            }
             return false;
         };
         if (bad(d->base_xy, 2 * (size_t)B) || bad(d->pick_xy, 2 * (size_t)M) || bad(d->drop_xy, 2 * (size_t)M))
-            return set_err(c, STAGE_ERR_OUT_OF_RANGE, "a coordinate exceeds |%d| m", STAGE_MAX_COORD);
+            return set_err(c, STAGE_ERR_OUT_OF_RANGE, "a coordinate is outside [-%d, %d] x [-%d, %d]", lim_x, lim_x,
+                           lim_y, lim_y);
     }
     for (auto &a : avail) a = a ? 1 : 0;
     Instance *in = new Instance();
     in->B = B; in->M = M; in->M_pad = M_pad;
+    in->metric = metric;
     in->h_avail = avail;
     in->n_avail = (int)std::count(avail.begin(), avail.end(), (uint8_t)1);
     size_t coords = carve_coords(nullptr, B, M_pad, nullptr);
@@ -862,7 +871,7 @@ stage_status stage_load_instance(stage_ctx *c, const stage_instance_desc *d, sta
         });
     if (e == cudaSuccess)
         e = timed(c, "table", 2, [&] {
-            return launch_table(B, M, M_pad, in->base, in->pick, in->drop, in->pd, in->cost, c->stream);
+            return launch_table(B, M, M_pad, in->base, in->pick, in->drop, in->pd, in->cost, metric, c->stream);
         });
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     dev_free(c, order_tmp);
@@ -964,8 +973,9 @@ stage_status stage_update_instance(stage_ctx *c, stage_inst h, const stage_updat
             return set_err(c, STAGE_ERR_INVALID_ARG, "mission id %d out of range", u->remove_ids[k]);
     for (size_t k = 0; k < 2 * (size_t)u->n_add; k++) {
         const int32_t x = u->add_pick_xy[k], y = u->add_drop_xy[k];
-        if (x > STAGE_MAX_COORD || x < -STAGE_MAX_COORD || y > STAGE_MAX_COORD || y < -STAGE_MAX_COORD)
-            return set_err(c, STAGE_ERR_OUT_OF_RANGE, "a coordinate exceeds |%d| m", STAGE_MAX_COORD);
+        const int lim = in->metric ? ((k & 1) ? STAGE_MAX_LON_UDEG : STAGE_MAX_LAT_UDEG) : STAGE_MAX_COORD;
+        if (x > lim || x < -lim || y > lim || y < -lim)
+            return set_err(c, STAGE_ERR_OUT_OF_RANGE, "an added coordinate is outside [-%d, %d]", lim, lim);
     }
     if ((int64_t)in->M + u->n_add > STAGE_MAX_MISSIONS)
         return set_err(c, STAGE_ERR_OUT_OF_RANGE, "more than %d mission ids", STAGE_MAX_MISSIONS);
@@ -1011,7 +1021,7 @@ stage_status stage_update_instance(stage_ctx *c, stage_inst h, const stage_updat
         CK(cudaMemcpyAsync(in->inv + M0, ident.data(), n4, cudaMemcpyHostToDevice, c->stream));
         CK(timed(c, "update", 1, [&] {
             return launch_table_columns(in->B, M0, u->n_add, in->M_pad, in->base, in->pick, in->drop, in->pd,
-                                        in->cost, c->stream);
+                                        in->cost, in->metric, c->stream);
         }));
         CK(cudaStreamSynchronize(c->stream));
         in->M = M1;

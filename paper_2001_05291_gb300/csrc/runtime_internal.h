@@ -32,6 +32,7 @@ struct KernelStat {
 
 struct Instance {
     int B = 0, M = 0, M_pad = 0;   // M: table columns in use (live + removed); M_pad: allocated columns
+    int metric = 0;                // 0: Euclidean legs on metres, 1: Haversine legs on microdegrees (Eq. 1)
     int n_avail = 0;
     std::vector<uint8_t> h_avail;
     DevBuf mem_coords;   // base, pick, drop (caller order and column order), pd, perm, inv, avail

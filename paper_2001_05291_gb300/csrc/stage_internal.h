@@ -81,12 +81,12 @@ constexpr int kSelectThreads = 256;
 // Every launcher enqueues on `stream` and returns the launch error.
 cudaError_t launch_fill_i32(int32_t *p, size_t n, int32_t v, cudaStream_t s);
 cudaError_t launch_table_columns(int B, int col0, int n, int M_pad, const int2 *base, const int2 *pick,
-                                 const int2 *drop, int32_t *pd, int32_t *cost, cudaStream_t s);
+                                 const int2 *drop, int32_t *pd, int32_t *cost, int metric, cudaStream_t s);
 cudaError_t launch_tombstone(const int32_t *ids, int n, int32_t *inv, int32_t *perm, int32_t *cost, int B,
                              int M_pad, cudaStream_t s);
-cudaError_t launch_check_coords(const int32_t *v, size_t n, int *bad, cudaStream_t s);
+cudaError_t launch_check_coords(const int32_t *v, size_t n, int lim_x, int lim_y, int *bad, cudaStream_t s);
 cudaError_t launch_table(int B, int M, int M_pad, const int2 *base, const int2 *pick,
-                         const int2 *drop, int32_t *pd_scratch, int32_t *cost, cudaStream_t s);
+                         const int2 *drop, int32_t *pd_scratch, int32_t *cost, int metric, cudaStream_t s);
 cudaError_t launch_rowsum(const int32_t *cost, int B, int M, int M_pad, unsigned long long *S,
                           cudaStream_t s);
 cudaError_t launch_topk(const unsigned long long *S, const uint8_t *avail, int B, int K,

@@ -24,7 +24,7 @@ STAGE_OK, STAGE_PENDING = 0, 1
 ERRORS = {-1: "INVALID_ARG", -2: "OUT_OF_RANGE", -3: "NO_MEMORY", -4: "ADMISSION", -5: "TIMEOUT",
           -6: "CUDA", -7: "INTERNAL", -8: "NOT_FOUND"}
 STAGE_THREADSAFE, STAGE_PROFILE, STAGE_AUTOTUNE = 1, 2, 4
-STAGE_DESC_DEVICE = 1
+STAGE_DESC_DEVICE, STAGE_DESC_HAVERSINE = 1, 2
 MOVE_FALLBACK, MOVE_ASPIRATION, MOVE_NEW_BEST = 1, 2, 4
 MAX_COORD, MAX_BASES, MAX_MISSIONS, MAX_K = 1 << 24, 65535, 1 << 24, 1024
 
@@ -276,9 +276,10 @@ class Context:
         return int(v.value)
 
     # ------------------------------------------------------------- instances
-    def load_instance(self, base_xy, pick_xy, drop_xy, base_available=None) -> int:
+    def load_instance(self, base_xy, pick_xy, drop_xy, base_available=None, haversine: bool = False) -> int:
         """stage_load_instance.  numpy arrays are copied from the host; CUDA
-        tensors (int32, contiguous) are read on the device."""
+        tensors (int32, contiguous) are read on the device.  haversine: the
+        coordinates are (latitude, longitude) microdegrees (Eq. 1 legs)."""
         d = StageInstanceDesc()
         keep = []
         if _is_cuda_tensor(base_xy):
@@ -300,6 +301,8 @@ class Context:
                 av = np.ascontiguousarray(base_available, dtype=np.uint8)
                 d.base_available = _ptr(av)
                 keep.append(av)
+        if haversine:
+            d.flags |= STAGE_DESC_HAVERSINE
         h = C.c_uint64()
         self._check(lib().stage_load_instance(self._h, C.byref(d), C.byref(h)))
         del keep
@@ -442,6 +445,8 @@ class Context:
                 b, p, q = (_host_i32(rq[x]) for x in ("base_xy", "pick_xy", "drop_xy"))
                 d.B, d.M = b.size // 2, p.size // 2
                 d.base_xy, d.pick_xy, d.drop_xy = _ptr(b), _ptr(p), _ptr(q)
+                if rq.get("haversine"):
+                    d.flags = STAGE_DESC_HAVERSINE
                 keep += [b, p, q, d]
                 if rq.get("base_available") is not None:
                     av = np.ascontiguousarray(rq["base_available"], dtype=np.uint8)

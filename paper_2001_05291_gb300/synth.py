@@ -219,6 +219,35 @@ def large(seed: int = 2, M: int = 1_000_000, B: int = 2000) -> Instance:
     return make_instance("large", seed, B, 2 * B, M, 64, 1200 * KM, 1000, 25, lay)
 
 
+# Geographic instances (Eq. 1 legs): (latitude, longitude) in microdegrees over
+# a 15 x 21 degree region with its clusters in the southern strip (the layout of
+# the province workload, drawn on a latitude / longitude box).
+GEO_LAT0, GEO_LON0 = 42_000_000, -95_000_000
+GEO_LAT_SPAN, GEO_LON_SPAN = 15_000_000, 21_000_000
+
+
+def geo_instance(name: str, seed: int, B: int, M: int, K: int, R: int, iters: int, tenure: int,
+                 n_facilities: int | None = None) -> Instance:
+    """An instance whose coordinates are (latitude, longitude) microdegree pairs."""
+    lay = Layout(GEO_LON_SPAN, GEO_LAT_SPAN, clustered=True, sigma_m=300_000.0)
+    inst = make_instance(name, seed, B, n_facilities or 2 * B, M, K, R, iters, tenure, lay)
+
+    def to_geo(xy):
+        out = np.empty_like(xy)
+        out[:, 0] = GEO_LAT0 + xy[:, 1]   # the layout's y (strip = south) is latitude
+        out[:, 1] = GEO_LON0 + xy[:, 0]
+        return out.astype(np.int32)
+
+    inst.base_xy, inst.pick_xy, inst.drop_xy = to_geo(inst.base_xy), to_geo(inst.pick_xy), to_geo(inst.drop_xy)
+    inst.meta = dict(inst.meta, coordinates="latitude, longitude (microdegrees)")
+    return inst
+
+
+def geo_paper(seed: int = 5) -> Instance:
+    """The paper's own scale on Eq. 1 legs: B=378 bases, M=180 missions, K=12; R=1500 km, 200 it, tenure 7."""
+    return geo_instance("geo_paper", seed, 378, 180, 12, 1500 * KM, 200, 7)
+
+
 def batched_sizes(seed: int = 3, n: int = 512):
     """Per-instance (B, M, K, R) of the batched workload, drawn log-uniform / uniform."""
     key = stream_key(seed, CLS_SIZES, 0)
