@@ -47,7 +47,7 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="large",
-                    choices=["tiny", "province", "large", "batched", "serving", "local"])
+                    choices=["tiny", "province", "large", "batched", "serving", "local", "geo"])
     ap.add_argument("--passes", type=int, default=16, help="local: permutation pairs (scan orders) supplied")
     ap.add_argument("--instances", type=int, default=512, help="batched / serving: instances")
     ap.add_argument("--slots", type=int, default=512, help="batched / serving: engine slots")
@@ -244,8 +244,10 @@ def run_ours(args):
            for a in (inst.base_xy, inst.pick_xy, inst.drop_xy)]
     torch.cuda.synchronize()
 
+    geo = "coordinates" in inst.meta   # (latitude, longitude) microdegrees: Eq. 1 legs
+
     def step(inputs):
-        h = ctx.load_instance(*inputs)
+        h = ctx.load_instance(*inputs, haversine=geo)
         r = ctx.tabu_run(h, inst.K, inst.R, inst.iters, inst.tenure)
         ctx.unload_instance(h)
         return r
@@ -322,7 +324,7 @@ def run_ours(args):
     # above also pays loading, ordering and ranking)
     search = None
     if not profile:
-        h = ctx.load_instance(*dev)
+        h = ctx.load_instance(*dev, haversine=geo)
         for _ in range(2):
             ctx.tabu_run(h, inst.K, inst.R, inst.iters, inst.tenure)
         torch.cuda.synchronize()
@@ -340,7 +342,7 @@ def run_ours(args):
         # the same search with per-kernel CUDA events: device time of the
         # search kernels alone (no host set-up or read-back)
         with stage.Context(device=local, profile=True) as pctx:
-            hp = pctx.load_instance(*dev)
+            hp = pctx.load_instance(*dev, haversine=geo)
             pctx.tabu_run(hp, inst.K, inst.R, inst.iters, inst.tenure)
             pctx.reset_stats()
             pr = pctx.tabu_run(hp, inst.K, inst.R, inst.iters, inst.tenure)

@@ -276,4 +276,4 @@ def batched(seed: int = 3, n: int = 512, scale_m: float = 1.0):
 
 
 def by_name(name: str) -> Instance:
-    return {"tiny": tiny, "province": province, "large": large}[name]()
+    return {"tiny": tiny, "province": province, "large": large, "geo": geo_paper}[name]()
