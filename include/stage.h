@@ -289,6 +289,57 @@ typedef struct {
 STAGE_API stage_status stage_local_search(stage_ctx *ctx, stage_inst inst, const stage_ls_params *params,
                                           stage_ls_result *result, stage_move *traj);
 
+/* Tabu search with a heterogeneous fleet (the vehicle and base types of
+ * Sec. 3 and Eq. 6-10, read for this model):
+ *   - K_rotary rotary-wing vehicles may stand at any base; K_fixed fixed-wing
+ *     vehicles only at aerodromes (base_helipad[b] = 0); one vehicle per base;
+ *   - a mission with mission_rotary[m] = 1 may be flown by rotary-wing
+ *     vehicles only, any other mission by either type; each mission is flown
+ *     from its nearest compatible open base, and the objective is Eq. 2's with
+ *     coverage (most covered, then least distance);
+ *   - start: start_rotary / start_fixed, or the ranking of Alg. 1 with the
+ *     helipad rule of its lines 14-16: bases by (row sum, id), a helipad taken
+ *     only while fewer than K_rotary are taken, until K_rotary + K_fixed; the
+ *     helipads and then the best-ranked aerodromes get the rotary-wing
+ *     vehicles, the other aerodromes the fixed-wing ones;
+ *   - a move takes one vehicle from its base i to a closed available base j
+ *     (an aerodrome for a fixed-wing vehicle); the tabu, aspiration, fallback,
+ *     tie-break and improving-only rules are stage_tabu_run's.
+ * traj (nullable) receives one stage_move per applied move ([iters]).  Arrays
+ * are host memory, copied in; mission ids are the caller's (load order, then
+ * appended missions).
+ * Errors: STAGE_ERR_INVALID_ARG (counts, a fixed-wing start at a helipad, a
+ * start base repeated or unavailable, missing arrays), STAGE_ERR_OUT_OF_RANGE
+ * (R), STAGE_ERR_INTERNAL (a device self-check failed). */
+typedef struct {
+    int32_t K_rotary;                 /* >= 0 */
+    int32_t K_fixed;                  /* >= 0; 1 <= K_rotary + K_fixed <= min(B, STAGE_MAX_K) */
+    int32_t R;                        /* range in metres, 0 <= R < INT32_MAX */
+    int32_t iters;                    /* >= 0 */
+    int32_t tenure;                   /* >= 0 */
+    int32_t accept_worsening;         /* as stage_tabu_params */
+    const uint8_t *base_helipad;      /* [B]: 1 helipad, 0 aerodrome */
+    const uint8_t *mission_rotary;    /* [M]: 1 rotary-wing only */
+    const int32_t *start_rotary;      /* [K_rotary] or NULL (with start_fixed NULL: the ranking) */
+    const int32_t *start_fixed;       /* [K_fixed] or NULL */
+} stage_fleet_params;
+
+typedef struct {
+    int32_t n_moves;
+    int32_t best_iter;
+    int64_t best_cov;
+    int64_t best_dist;
+    int64_t final_cov;
+    int64_t final_dist;
+    int32_t *best_rotary;             /* [K_rotary] caller buffer or NULL; sorted ascending */
+    int32_t *best_fixed;              /* [K_fixed] */
+    int32_t *final_rotary;            /* [K_rotary] */
+    int32_t *final_fixed;             /* [K_fixed] */
+} stage_fleet_result;
+
+STAGE_API stage_status stage_fleet_tabu(stage_ctx *ctx, stage_inst inst, const stage_fleet_params *params,
+                                        stage_fleet_result *result, stage_move *traj);
+
 /* ---------------------------------------------------------- updates, batches */
 
 /* Incremental change to a resident instance (re-staging after new demand,

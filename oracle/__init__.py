@@ -305,6 +305,135 @@ def local_search(cost, K, R, perm_slots, perm_cands, start_open=None, avail=None
     return LocalSearchResult(moves, np.sort(np.array(O, dtype=np.int32)), cur[0], cur[1], passes, optimum)
 
 
+def fleet_rank(cost, helipad, K_rotary, K_fixed, avail=None):
+    """Alg. 1 with the helipad rule (lines 14-16) and the vehicle assignment of
+    lines 20-21: bases by (row sum over every mission, id); a helipad is taken
+    only while fewer than K_rotary are taken, until K_rotary + K_fixed bases;
+    helipads get rotary-wing vehicles first, then the best-ranked aerodromes;
+    the other aerodromes get the fixed-wing vehicles.  Returns (rotary, fixed)."""
+    cost = _i32(cost)
+    B = cost.shape[0]
+    S = cost.astype(np.int64).sum(axis=1)
+    av = np.ones(B, dtype=bool) if avail is None else np.asarray(avail).astype(bool)
+    order = sorted((b for b in range(B) if av[b]), key=lambda b: (int(S[b]), b))
+    chosen, nh = [], 0
+    for b in order:
+        if len(chosen) == K_rotary + K_fixed:
+            break
+        if helipad[b]:
+            if nh < K_rotary:
+                chosen.append(b)
+                nh += 1
+        else:
+            chosen.append(b)
+    rot = [b for b in chosen if helipad[b]]
+    aer = [b for b in chosen if not helipad[b]]
+    rot += aer[:K_rotary - len(rot)]
+    fix = aer[K_rotary - nh:]
+    if len(rot) != K_rotary or len(fix) != K_fixed:
+        raise ValueError("too few available aerodromes for the fixed-wing vehicles")
+    return rot, fix
+
+
+@dataclass
+class FleetResult:
+    moves: list             # list of (iter, i, j, flags, cov, dist)
+    best_rotary: np.ndarray
+    best_fixed: np.ndarray
+    best_cov: int
+    best_dist: int
+    best_iter: int
+    final_rotary: np.ndarray
+    final_fixed: np.ndarray
+    final_cov: int
+    final_dist: int
+
+
+def fleet_tabu(cost, helipad, mission_rotary, K_rotary, K_fixed, R, iters, tenure, start_rotary=None,
+               start_fixed=None, avail=None, accept_worsening=True, eval_mode: str = "full",
+               nthreads: int = 1) -> FleetResult:
+    """Tabu search (Alg. 3) with a heterogeneous fleet (Sec. 3, Eq. 6-10, as read):
+    rotary-wing vehicles at any base, fixed-wing vehicles at aerodromes only,
+    rotary-only missions flown by rotary-wing vehicles only, every mission from
+    its nearest compatible open base; the objective is Eq. 2 with coverage.  A
+    move takes one vehicle from base i to a closed available base j (an
+    aerodrome for a fixed-wing vehicle); tabu expiries, aspiration, fallback,
+    the (covered desc, distance asc, i asc, j asc) order and the improving-only
+    rule are those of tabu().
+
+    eval_mode "full" evaluates every move's placement from scratch; "table"
+    reads the two fast-interchange tables (missions of either type with every
+    vehicle, rotary-only missions with the rotary-wing vehicles)."""
+    cost = _i32(cost)
+    B, M = cost.shape
+    heli = np.asarray(helipad).astype(bool)
+    rmask = np.asarray(mission_rotary).astype(bool)
+    av = np.ones(B, dtype=bool) if avail is None else np.asarray(avail).astype(bool)
+    c0 = np.ascontiguousarray(cost[:, ~rmask])
+    c1 = np.ascontiguousarray(cost[:, rmask])
+    if start_rotary is None and start_fixed is None:
+        start_rotary, start_fixed = fleet_rank(cost, heli, K_rotary, K_fixed, avail)
+    rot = [int(x) for x in (start_rotary if start_rotary is not None else [])]
+    fix = [int(x) for x in (start_fixed if start_fixed is not None else [])]
+
+    def F(r, f):
+        a = evaluate(c0, r + f, R) if c0.shape[1] else (0, 0)
+        b = evaluate(c1, r, R) if (c1.shape[1] and r) else (0, 0)
+        return a[0] + b[0], a[1] + b[1]
+
+    def better(x, y):
+        return x[0] > y[0] or (x[0] == y[0] and x[1] < y[1])
+
+    cur = F(rot, fix)
+    best, best_iter = cur, -1
+    best_r, best_f = list(rot), list(fix)
+    expiry = np.zeros(B, dtype=np.int64)
+    moves = []
+    for t in range(iters):
+        opened = set(rot) | set(fix)
+        cands = [j for j in range(B) if av[j] and j not in opened]
+        if eval_mode == "table":
+            t0 = swap_table(c0, rot + fix, R, avail, nthreads) if c0.shape[1] else None
+            t1 = swap_table(c1, rot, R, avail, nthreads) if (c1.shape[1] and rot) else None
+            v1 = evaluate(c1, rot, R) if (c1.shape[1] and rot) else (0, 0)
+        keys = []   # (key for sorting, cov, dist, i, j, kind, slot)
+        for kind, group in ((0, rot), (1, fix)):
+            for sl, i in enumerate(group):
+                for j in cands:
+                    if kind == 1 and heli[j]:
+                        continue
+                    if eval_mode == "table":
+                        a = (int(t0[0][i, j]), int(t0[1][i, j])) if t0 is not None else (0, 0)
+                        b = ((int(t1[0][i, j]), int(t1[1][i, j])) if t1 is not None else (0, 0)) if kind == 0 else v1
+                        f = (a[0] + b[0], a[1] + b[1])
+                    else:
+                        r2, f2 = list(rot), list(fix)
+                        (r2 if kind == 0 else f2)[sl] = j
+                        f = F(r2, f2)
+                    tabu = t < expiry[i] or t < expiry[j]
+                    keys.append(((-f[0], f[1], i, j), f, i, j, kind, sl, tabu))
+        if not keys:
+            break
+        keys.sort(key=lambda k: k[0])
+        adm = [k for k in keys if not k[6] or better(k[1], best)]
+        pick = adm[0] if adm else keys[0]
+        flags = (MOVE_ASPIRATION if pick[6] else 0) if adm else MOVE_FALLBACK
+        if not accept_worsening and not better(pick[1], cur):
+            break
+        _, f, i, j, kind, sl, _ = pick
+        (rot if kind == 0 else fix)[sl] = j
+        expiry[i] = expiry[j] = t + tenure + 1
+        cur = f
+        if better(f, best):
+            best, best_iter = f, t
+            best_r, best_f = list(rot), list(fix)
+            flags |= MOVE_NEW_BEST
+        moves.append((t, i, j, flags, f[0], f[1]))
+    return FleetResult(moves, np.sort(np.array(best_r, dtype=np.int32)), np.sort(np.array(best_f, dtype=np.int32)),
+                       best[0], best[1], best_iter, np.sort(np.array(rot, dtype=np.int32)),
+                       np.sort(np.array(fix, dtype=np.int32)), cur[0], cur[1])
+
+
 def bruteforce(cost, K, R, avail=None):
     """Exact optimum over all K-subsets: (placement, cov, dist, subsets evaluated)."""
     cost = _i32(cost)

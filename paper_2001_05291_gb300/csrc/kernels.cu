@@ -712,6 +712,10 @@ __device__ __forceinline__ void init_body(const TabuBuffers &w, const int32_t *_
             w.a[m] = kInf; w.b[m] = kInf; w.s1[m] = 0; w.s2[m] = -1;
             continue;
         }
+        if (w.mask && !w.mask[m]) {   // not a mission of this search: never a hit, no term
+            w.a[m] = INT_MIN; w.b[m] = INT_MIN; w.s1[m] = 0; w.s2[m] = -1;
+            continue;
+        }
         int a, b, k1, k2;
         scan_best_two(cost, w.M_pad, m, s_open, w.K, a, b, k1, k2);
         w.a[m] = a; w.b[m] = b; w.s1[m] = (int16_t)k1; w.s2[m] = (int16_t)k2;
@@ -1823,6 +1827,7 @@ __device__ __forceinline__ void refresh_body(const TabuBuffers &w, const int32_t
     const int32_t *rowj = cost + (size_t)jj * M_pad;
     long long v0c = 0, v0d = 0;
     for (int m = bid * blockDim.x + threadIdx.x; m < w.M; m += nb * blockDim.x) {
+        if (w.mask && !w.mask[m]) continue;
         int a = w.a[m], b = w.b[m];
         int k1 = w.s1[m], k2 = w.s2[m];
         if (k1 != ss && k2 != ss) {
@@ -2021,6 +2026,159 @@ cudaError_t launch_ls_select(const TabuBuffers &w, int nC, const int *rank_slot,
                              cudaStream_t s)
 {
     k_ls_select<<<select_blocks(w.K, nC), kSelectThreads, 0, s>>>(w, rank_slot, rank_cand);
+    return cudaGetLastError();
+}
+
+// --------------------------------------------------------------------------
+// Heterogeneous fleet (the vehicle and base types of Sec. 3, Eq. 6-10, as read
+// for this model): Kr rotary-wing vehicles in slots 0 .. Kr-1 (any base) and
+// fixed-wing vehicles in the other slots (aerodromes only); rotary-only
+// missions may be flown by rotary-wing vehicles only.  Two searches share the
+// table: A (all vehicles, the missions any vehicle may fly) and B (the
+// rotary-wing vehicles, the rotary-only missions).  Moving a rotary-wing
+// vehicle from i to j changes both, F = F_A(s, j) + F_B(s, j); moving a
+// fixed-wing vehicle changes only A, F = F_A(s, j) + V0_B, and then B's
+// accumulators stay valid (B holds: its next swap pass and refresh are
+// skipped).  Same admissibility, aspiration, fallback, tie-break and
+// improving-only rule as k_select, over A's candidate list.
+// --------------------------------------------------------------------------
+__global__ void __launch_bounds__(kSelectThreads) k_fleet_select(TabuBuffers A, TabuBuffers B, int Kr, int hasB,
+                                                                const uint8_t *__restrict__ helipad,
+                                                                int *__restrict__ b_pos)
+{
+    TabuDevState *st = A.st;
+    if (st->done || st->t >= st->t_end) return;
+    __shared__ MoveKey s_adm[kSelectThreads / 32], s_all[kSelectThreads / 32];
+    __shared__ int s_last, s_moved, s_newbest, s_rot;
+    const int t = st->t;
+    const int nC = st->nC, K = A.K, Bn = A.B;
+    const long long v0c = (long long)A.v0[0] + (hasB ? (long long)B.v0[0] : 0ll);
+    const long long v0d = (long long)A.v0[1] + (hasB ? (long long)B.v0[1] : 0ll);
+    const long long bc = st->best_cov, bd = st->best_dist;
+    MoveKey adm = invalid_key(), all = invalid_key();
+    const long long total = (long long)K * nC;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < total;
+         q += (long long)gridDim.x * blockDim.x) {
+        const int sl = (int)(q / nC), c = (int)(q % nC);
+        const int j = A.cand[c];
+        const bool rot = sl < Kr;
+        if (!rot && helipad[j]) continue;   // a fixed-wing vehicle needs an aerodrome
+        const size_t sj = (size_t)sl * Bn + j;
+        MoveKey k;
+        k.cov = v0c + A.gain_c[j] + (long long)A.loss_c[sl] + A.extra_c[sj];
+        k.dist = v0d + (long long)A.gain_d[j] + (long long)A.loss_d[sl] + (long long)A.extra_d[sj];
+        if (rot && hasB) {
+            k.cov += B.gain_c[j] + (long long)B.loss_c[sl] + B.extra_c[sj];
+            k.dist += (long long)B.gain_d[j] + (long long)B.loss_d[sl] + (long long)B.extra_d[sj];
+        }
+        k.i = A.open[sl]; k.j = j; k.s = sl; k.c = c; k.valid = 1;
+        k.tabu = (t < A.expiry[k.i]) || (t < A.expiry[j]);
+        if (key_better(k, all)) all = k;
+        if ((!k.tabu || obj_better(k.cov, k.dist, bc, bd)) && key_better(k, adm)) adm = k;
+    }
+    block_best2<kSelectThreads>(adm, all, s_adm, s_all);
+    if (threadIdx.x == 0) {
+        A.partials[2 * blockIdx.x] = adm;
+        A.partials[2 * blockIdx.x + 1] = all;
+        __threadfence();
+        const unsigned int ticket = atomicAdd(&st->ticket, 1u);
+        s_last = (ticket == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    adm = invalid_key();
+    all = invalid_key();
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
+        MoveKey pa = load_key_cg(&A.partials[2 * b]);
+        MoveKey px = load_key_cg(&A.partials[2 * b + 1]);
+        if (key_better(pa, adm)) adm = pa;
+        if (key_better(px, all)) all = px;
+    }
+    __syncthreads();
+    block_best2<kSelectThreads>(adm, all, s_adm, s_all);
+    if (threadIdx.x == 0) {
+        st->ticket = 0;
+        s_moved = 0;
+        s_newbest = 0;
+        s_rot = 0;
+        if (!all.valid) {
+            st->done = 1;                       // no move at all
+        } else if (st->cur_cov != v0c || st->cur_dist != v0d) {
+            st->err |= kErrObjectiveMismatch;   // the refreshes disagreed with the chosen move
+            st->done = 1;
+        } else {
+            const MoveKey P = adm.valid ? adm : all;
+            int flags = adm.valid ? (adm.tabu ? STAGE_MOVE_ASPIRATION : 0) : STAGE_MOVE_FALLBACK;
+            if (!st->accept_worsening && !obj_better(P.cov, P.dist, st->cur_cov, st->cur_dist)) {
+                st->done = 1;
+            } else {
+                A.open[P.s] = P.j;
+                A.cand[P.c] = P.i;
+                A.expiry[P.i] = t + st->tenure + 1;
+                A.expiry[P.j] = t + st->tenure + 1;
+                st->cur_cov = P.cov;
+                st->cur_dist = P.dist;
+                if (obj_better(P.cov, P.dist, st->best_cov, st->best_dist)) {
+                    st->best_cov = P.cov;
+                    st->best_dist = P.dist;
+                    st->best_iter = t;
+                    flags |= STAGE_MOVE_NEW_BEST;
+                    s_newbest = 1;
+                }
+                if (st->n_moves < st->traj_cap) {
+                    stage_move mv;
+                    mv.iter = t; mv.i = P.i; mv.j = P.j; mv.flags = flags;
+                    mv.cov = P.cov; mv.dist = P.dist;
+                    A.traj[st->n_moves] = mv;
+                }
+                st->n_moves += 1;
+                st->t = t + 1;
+                st->mv_s = P.s; st->mv_i = P.i; st->mv_j = P.j;
+                A.v0[0] = 0;
+                A.v0[1] = 0;
+                s_moved = 1;
+                if (hasB) {
+                    TabuDevState *sb = B.st;
+                    if (P.s < Kr) {
+                        // the rotary-wing vehicle moved: B's placement and candidates follow
+                        const int pos = b_pos[P.j];
+                        B.open[P.s] = P.j;
+                        B.cand[pos] = P.i;
+                        b_pos[P.i] = pos;
+                        b_pos[P.j] = -1;
+                        sb->mv_s = P.s; sb->mv_i = P.i; sb->mv_j = P.j;
+                        sb->ls_hold = 0;
+                        B.v0[0] = 0;
+                        B.v0[1] = 0;
+                        s_rot = 1;
+                    } else {
+                        sb->ls_hold = 1;                // B unchanged: skip its swap pass and refresh
+                    }
+                }
+            }
+        }
+        if (st->done && hasB) B.st->done = 1;
+    }
+    __syncthreads();
+    if (!s_moved) return;
+    for (int k = threadIdx.x; k < K; k += blockDim.x) {
+        A.loss_c[k] = 0;
+        A.loss_d[k] = 0;
+        if (s_newbest) A.best_open[k] = A.open[k];
+    }
+    if (s_rot)
+        for (int k = threadIdx.x; k < B.K; k += blockDim.x) {
+            B.loss_c[k] = 0;
+            B.loss_d[k] = 0;
+        }
+}
+
+cudaError_t launch_fleet_select(const TabuBuffers &A, const TabuBuffers &B, int Kr, int hasB,
+                                const uint8_t *helipad, int *b_pos, cudaStream_t s)
+{
+    // A's state holds the candidate count
+    k_fleet_select<<<kSelectBlocks, kSelectThreads, 0, s>>>(A, B, Kr, hasB, helipad, b_pos);
     return cudaGetLastError();
 }
 

@@ -547,6 +547,240 @@ stage_status run_tabu(stage_ctx *c, Instance *in, const stage_tabu_params *p,
     return STAGE_OK;
 }
 
+// ----------------------------------------------------------- heterogeneous fleet
+// Two searches over the one table (see k_fleet_select): A over every vehicle
+// and the missions any vehicle may fly, B over the rotary-wing vehicles and
+// the rotary-only missions; the other search's missions are masked out.
+namespace {
+
+struct FleetSide {
+    DevBuf ws;
+    TabuBuffers tb{};
+    std::vector<int32_t> cand;
+    int nC = 0;
+};
+
+// Workspace, placement, candidates and per-mission initialisation of one side.
+stage_status fleet_side(stage_ctx *c, Instance *in, FleetSide &f, const std::vector<int32_t> &open, int R,
+                        int traj_cap, const uint8_t *d_mask)
+{
+    const int K = (int)open.size();
+    TabuBuffers tb{};
+    const size_t bytes = carve_ws(nullptr, K, in->B, in->M_pad, traj_cap, tb);
+    stage_status s = dev_alloc(c, bytes, f.ws);
+    if (s != STAGE_OK) return s;
+    carve_ws(static_cast<char *>(f.ws.p), K, in->B, in->M_pad, traj_cap, tb);
+    tb.K = K; tb.B = in->B; tb.M = in->M; tb.M_pad = in->M_pad; tb.R = R;
+    tb.mask = d_mask;
+    std::vector<uint8_t> is_open(in->B, 0);
+    for (int b : open) is_open[b] = 1;
+    f.cand.clear();
+    for (int b = 0; b < in->B; b++)
+        if (in->h_avail[b] && !is_open[b]) f.cand.push_back(b);
+    f.nC = (int)f.cand.size();
+    f.tb = tb;
+    std::vector<int32_t> zeros(in->B, 0);
+    CK(cudaMemcpyAsync(tb.open, open.data(), (size_t)K * 4, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(tb.best_open, open.data(), (size_t)K * 4, cudaMemcpyHostToDevice, c->stream));
+    if (f.nC) CK(cudaMemcpyAsync(tb.cand, f.cand.data(), (size_t)f.nC * 4, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(tb.expiry, zeros.data(), (size_t)in->B * 4, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemsetAsync(tb.st, 0, sizeof(TabuDevState), c->stream));
+    CK(cudaMemsetAsync(tb.v0, 0, 16, c->stream));
+    CK(cudaMemsetAsync(tb.loss_c, 0, (size_t)K * 8, c->stream));
+    CK(cudaMemsetAsync(tb.loss_d, 0, (size_t)K * 8, c->stream));
+    CK(cudaMemsetAsync(tb.gain_c, 0, (size_t)in->B * 4, c->stream));
+    CK(cudaMemsetAsync(tb.gain_d, 0, (size_t)in->B * 8, c->stream));
+    CK(cudaMemsetAsync(tb.extra_c, 0, (size_t)K * in->B * 4, c->stream));
+    CK(cudaMemsetAsync(tb.extra_d, 0, (size_t)K * in->B * 8, c->stream));
+    CK(timed(c, "init", 1, [&] { return launch_init(tb, in->cost, c->stream); }));
+    CK(cudaStreamSynchronize(c->stream));   // host vectors above
+    return STAGE_OK;
+}
+
+}  // namespace
+
+stage_status run_fleet(stage_ctx *c, Instance *in, const stage_fleet_params *p, stage_fleet_result *res,
+                       stage_move *traj)
+{
+    if (!p) return set_err(c, STAGE_ERR_INVALID_ARG, "params is NULL");
+    const int Kr = p->K_rotary, Kf = p->K_fixed, K = Kr + Kf;
+    if (Kr < 0 || Kf < 0 || K < 1 || K > in->B || K > STAGE_MAX_K)
+        return set_err(c, STAGE_ERR_INVALID_ARG, "K_rotary=%d, K_fixed=%d: need 1 <= K <= min(B=%d, %d)", Kr, Kf,
+                       in->B, STAGE_MAX_K);
+    if (K > in->n_avail) return set_err(c, STAGE_ERR_INVALID_ARG, "%d vehicles, %d available bases", K, in->n_avail);
+    if (p->R < 0 || p->R == INT32_MAX) return set_err(c, STAGE_ERR_OUT_OF_RANGE, "R=%d outside [0, INT32_MAX)", p->R);
+    if (p->iters < 0 || p->tenure < 0) return set_err(c, STAGE_ERR_INVALID_ARG, "iters and tenure must be >= 0");
+    if (!p->base_helipad || !p->mission_rotary)
+        return set_err(c, STAGE_ERR_INVALID_ARG, "base_helipad and mission_rotary are required");
+    const int B = in->B;
+    std::vector<uint8_t> heli(p->base_helipad, p->base_helipad + B);
+    for (auto &h : heli) h = h ? 1 : 0;
+    // ---- start: given, or ranking with the helipad rule
+    std::vector<int32_t> rot, fix;
+    if (p->start_rotary || p->start_fixed) {
+        if ((Kr && !p->start_rotary) || (Kf && !p->start_fixed))
+            return set_err(c, STAGE_ERR_INVALID_ARG, "give both start_rotary and start_fixed, or neither");
+        if (Kr) rot.assign(p->start_rotary, p->start_rotary + Kr);
+        if (Kf) fix.assign(p->start_fixed, p->start_fixed + Kf);
+        std::vector<int32_t> all(rot);
+        all.insert(all.end(), fix.begin(), fix.end());
+        stage_status s = check_placement(c, in, all.data(), K);
+        if (s != STAGE_OK) return s;
+        for (int b : fix)
+            if (heli[b]) return set_err(c, STAGE_ERR_INVALID_ARG, "fixed-wing start at helipad %d", b);
+    } else {
+        std::vector<int64_t> S(B);
+        int32_t one = 0;
+        stage_status s = do_rank(c, in, 1, &one, S.data());
+        if (s != STAGE_OK) return s;
+        std::vector<int32_t> order;
+        for (int b = 0; b < B; b++)
+            if (in->h_avail[b]) order.push_back(b);
+        std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return S[x] != S[y] ? S[x] < S[y] : x < y; });
+        std::vector<int32_t> chosen;
+        int nh = 0;
+        for (int b : order) {
+            if ((int)chosen.size() == K) break;
+            if (heli[b]) {
+                if (nh < Kr) {
+                    chosen.push_back(b);
+                    nh++;
+                }
+            } else {
+                chosen.push_back(b);
+            }
+        }
+        int aer_avail = 0;
+        for (int b : chosen) aer_avail += !heli[b];
+        if ((int)chosen.size() < K || aer_avail < Kf)
+            return set_err(c, STAGE_ERR_INVALID_ARG, "too few available aerodromes for %d fixed-wing vehicles", Kf);
+        for (int b : chosen)
+            if (heli[b]) rot.push_back(b);
+        for (int b : chosen)
+            if (!heli[b]) {
+                if ((int)rot.size() < Kr) rot.push_back(b);
+                else fix.push_back(b);
+            }
+    }
+    std::vector<int32_t> open(rot);
+    open.insert(open.end(), fix.begin(), fix.end());
+    // ---- per-column mission masks of the two searches
+    std::vector<int32_t> perm(in->M);
+    CK(cudaMemcpy(perm.data(), in->perm, (size_t)in->M * 4, cudaMemcpyDeviceToHost));
+    std::vector<uint8_t> host(3 * (size_t)in->M_pad + B, 0);
+    uint8_t *mA = host.data(), *mB = host.data() + in->M_pad;
+    bool anyB = false;
+    for (int col = 0; col < in->M; col++) {
+        const int m = perm[col];
+        if (m < 0) continue;   // removed mission
+        const bool r = p->mission_rotary[m] != 0;
+        mA[col] = !r;
+        mB[col] = r;
+        anyB |= r;
+    }
+    std::copy(heli.begin(), heli.end(), host.data() + 2 * (size_t)in->M_pad);
+    const int hasB = (Kr >= 1 && anyB) ? 1 : 0;
+    DevBuf dm, dpos;
+    stage_status s = dev_alloc(c, host.size(), dm);
+    if (s != STAGE_OK) return s;
+    s = dev_alloc(c, (size_t)B * 4, dpos);
+    if (s != STAGE_OK) {
+        dev_free(c, dm);
+        return s;
+    }
+    auto *d_m = static_cast<uint8_t *>(dm.p);
+    int *d_pos = static_cast<int *>(dpos.p);
+    FleetSide A, Bs;
+    auto cleanup = [&]() {
+        dev_free(c, A.ws);
+        dev_free(c, Bs.ws);
+        dev_free(c, dm);
+        dev_free(c, dpos);
+    };
+    cudaError_t e = cudaMemcpyAsync(d_m, host.data(), host.size(), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        cleanup();
+        return set_err(c, STAGE_ERR_CUDA, "fleet set-up failed: %s", cudaGetErrorString(e));
+    }
+    s = fleet_side(c, in, A, open, p->R, p->iters, d_m);
+    if (s == STAGE_OK && hasB) s = fleet_side(c, in, Bs, rot, p->R, 1, d_m + in->M_pad);
+    if (s != STAGE_OK) {
+        cleanup();
+        return s;
+    }
+    // state: A carries the search; B only its hold / done flags and last move
+    unsigned long long v0a[2] = {0, 0}, v0b[2] = {0, 0};
+    std::vector<int32_t> pos(B, -1);
+    for (int q = 0; q < Bs.nC; q++) pos[Bs.cand[q]] = q;
+    e = cudaMemcpy(v0a, A.tb.v0, 16, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && hasB) e = cudaMemcpy(v0b, Bs.tb.v0, 16, cudaMemcpyDeviceToHost);
+    TabuDevState st{}, sb{};
+    st.tenure = p->tenure;
+    st.accept_worsening = p->accept_worsening ? 1 : 0;
+    st.nC = A.nC;
+    st.traj_cap = p->iters;
+    st.t_end = p->iters;
+    st.best_iter = -1;
+    st.cur_cov = st.best_cov = (long long)(v0a[0] + v0b[0]);
+    st.cur_dist = st.best_dist = (long long)(v0a[1] + v0b[1]);
+    sb.nC = Bs.nC;
+    sb.t_end = INT32_MAX;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(A.tb.st, &st, sizeof st, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess && hasB) e = cudaMemcpyAsync(Bs.tb.st, &sb, sizeof sb, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_pos, pos.data(), (size_t)B * 4, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    volatile int *done_flag = static_cast<volatile int *>(c->pinned);
+    *done_flag = 0;
+    const uint8_t *d_heli = d_m + 2 * (size_t)in->M_pad;
+    for (int it = 0; e == cudaSuccess && it < p->iters && A.nC > 0; it++) {
+        e = timed(c, "swap_eval", 1, [&] { return launch_swap_eval(A.tb, in->cost, A.nC, 0, c->stream); });
+        if (e == cudaSuccess && hasB && Bs.nC > 0)
+            e = timed(c, "swap_eval", 1, [&] { return launch_swap_eval(Bs.tb, in->cost, Bs.nC, 0, c->stream); });
+        if (e == cudaSuccess)
+            e = timed(c, "fleet_select", 1,
+                      [&] { return launch_fleet_select(A.tb, Bs.tb, Kr, hasB, d_heli, d_pos, c->stream); });
+        if (e == cudaSuccess) e = timed(c, "refresh", 1, [&] { return launch_refresh(A.tb, in->cost, c->stream); });
+        if (e == cudaSuccess && hasB)
+            e = timed(c, "refresh", 1, [&] { return launch_refresh(Bs.tb, in->cost, c->stream); });
+        if (e == cudaSuccess && (it & 31) == 31) {
+            e = cudaMemcpyAsync(c->pinned, &A.tb.st->done, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+            if (*done_flag) break;
+        }
+    }
+    std::vector<int32_t> fin(K), best(K);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&st, A.tb.st, sizeof st, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(fin.data(), A.tb.open, (size_t)K * 4, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(best.data(), A.tb.best_open, (size_t)K * 4, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    const int n = std::min(st.n_moves, p->iters);
+    if (e == cudaSuccess && traj && n > 0)
+        e = cudaMemcpy(traj, A.tb.traj, (size_t)n * sizeof(stage_move), cudaMemcpyDeviceToHost);
+    cleanup();
+    if (e != cudaSuccess) return set_err(c, STAGE_ERR_CUDA, "fleet search failed: %s", cudaGetErrorString(e));
+    if (st.err)
+        return set_err(c, STAGE_ERR_INTERNAL, "device self-check failed (code %d) at iteration %d", st.err, st.t);
+    if (res) {
+        res->n_moves = st.n_moves;
+        res->best_iter = st.best_iter;
+        res->best_cov = st.best_cov;
+        res->best_dist = st.best_dist;
+        res->final_cov = st.cur_cov;
+        res->final_dist = st.cur_dist;
+        auto put = [](std::vector<int32_t> v, int32_t *dst) {
+            std::sort(v.begin(), v.end());
+            if (dst) std::copy(v.begin(), v.end(), dst);
+        };
+        put(std::vector<int32_t>(best.begin(), best.begin() + Kr), res->best_rotary);
+        put(std::vector<int32_t>(best.begin() + Kr, best.end()), res->best_fixed);
+        put(std::vector<int32_t>(fin.begin(), fin.begin() + Kr), res->final_rotary);
+        put(std::vector<int32_t>(fin.begin() + Kr, fin.end()), res->final_fixed);
+    }
+    return STAGE_OK;
+}
+
 // Local search (Alg. 2 as read for identical vehicles): iterations of
 // (swap pass, first-improvement selection, refresh) until the device state
 // says done; a pass change skips the swap pass and the refresh of the next step.
@@ -1098,6 +1332,17 @@ stage_status stage_evaluate_swaps(stage_ctx *c, stage_inst h, const int32_t *ope
     CK(cudaMemcpyAsync(out_dist, od, n * 8, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     return STAGE_OK;
+}
+
+stage_status stage_fleet_tabu(stage_ctx *c, stage_inst h, const stage_fleet_params *p, stage_fleet_result *res,
+                              stage_move *traj)
+{
+    if (!c) return STAGE_ERR_INVALID_ARG;
+    Guard g(c);
+    Instance *in = find_inst(c, h);
+    if (!in) return set_err(c, STAGE_ERR_NOT_FOUND, "unknown instance %llu", (unsigned long long)h);
+    CK(cudaSetDevice(c->device));
+    return run_fleet(c, in, p, res, traj);
 }
 
 stage_status stage_local_search(stage_ctx *c, stage_inst h, const stage_ls_params *p, stage_ls_result *res,

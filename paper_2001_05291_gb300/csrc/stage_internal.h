@@ -72,6 +72,10 @@ struct TabuBuffers {
     TabuDevState *st;
     MoveKey *partials;           // [2 * kSelectBlocks]
     stage_move *traj;            // [traj_cap]
+    // missions of this search, per column (the heterogeneous fleet splits the
+    // missions into two searches); NULL = every mission.  A mission outside
+    // has thresholds INT_MIN: no hit, no term, untouched by the refresh.
+    const uint8_t *mask;
 };
 
 constexpr int kSelectBlocks = 148;
@@ -134,6 +138,11 @@ cudaError_t launch_tabu_small(const TabuBuffers &w, const int32_t *cost, int ite
 // small instances, every per-iteration array in shared memory (one block)
 bool tabu_resident_fits(int K, int B, int M_pad, int nC);
 cudaError_t launch_tabu_resident(const TabuBuffers &w, const int32_t *cost, int nC, int iters, cudaStream_t s);
+// heterogeneous fleet: the best move over both searches (A: every vehicle,
+// every mission a vehicle of any type may fly; B: the rotary-wing vehicles,
+// the rotary-only missions); B's slots are A's first Kr slots
+cudaError_t launch_fleet_select(const TabuBuffers &A, const TabuBuffers &B, int Kr, int hasB,
+                                const uint8_t *helipad, int *b_pos, cudaStream_t s);
 // local search: first improving swap at or after the scan position of the
 // current pass (rank_slot / rank_cand: [passes][K] / [passes][nC] positions)
 cudaError_t launch_ls_select(const TabuBuffers &w, int nC, const int *rank_slot, const int *rank_cand,

@@ -73,6 +73,19 @@ class StageLsResult(C.Structure):
                 ("final_open", C.c_void_p)]
 
 
+class StageFleetParams(C.Structure):
+    _fields_ = [("K_rotary", C.c_int32), ("K_fixed", C.c_int32), ("R", C.c_int32), ("iters", C.c_int32),
+                ("tenure", C.c_int32), ("accept_worsening", C.c_int32), ("base_helipad", C.c_void_p),
+                ("mission_rotary", C.c_void_p), ("start_rotary", C.c_void_p), ("start_fixed", C.c_void_p)]
+
+
+class StageFleetResult(C.Structure):
+    _fields_ = [("n_moves", C.c_int32), ("best_iter", C.c_int32), ("best_cov", C.c_int64),
+                ("best_dist", C.c_int64), ("final_cov", C.c_int64), ("final_dist", C.c_int64),
+                ("best_rotary", C.c_void_p), ("best_fixed", C.c_void_p), ("final_rotary", C.c_void_p),
+                ("final_fixed", C.c_void_p)]
+
+
 class StageUpdate(C.Structure):
     _fields_ = [("n_add", C.c_int32), ("n_remove", C.c_int32), ("n_unavail", C.c_int32),
                 ("n_avail", C.c_int32), ("add_pick_xy", C.c_void_p), ("add_drop_xy", C.c_void_p),
@@ -124,6 +137,7 @@ def lib():
             "stage_evaluate_swaps": ([p, C.c_uint64, p, i32, i32, p, p], st),
             "stage_tabu_run": ([p, C.c_uint64, C.POINTER(StageTabuParams), C.POINTER(StageTabuResult), p], st),
             "stage_local_search": ([p, C.c_uint64, C.POINTER(StageLsParams), C.POINTER(StageLsResult), p], st),
+            "stage_fleet_tabu": ([p, C.c_uint64, C.POINTER(StageFleetParams), C.POINTER(StageFleetResult), p], st),
             "stage_kernel_stats": ([p, C.c_char_p, C.POINTER(i64), C.POINTER(C.c_double)], st),
             "stage_reset_stats": ([p], st),
             "stage_read_table": ([p, C.c_uint64, i32, i32, i32, i32, p], st),
@@ -173,6 +187,21 @@ class TabuResult:
     final_dist: int
     moves: list = field(default_factory=list)   # (iter, i, j, flags, cov, dist)
     end_state: dict | None = None
+
+
+@dataclass
+class FleetResult:
+    n_moves: int
+    best_rotary: np.ndarray
+    best_fixed: np.ndarray
+    best_cov: int
+    best_dist: int
+    best_iter: int
+    final_rotary: np.ndarray
+    final_fixed: np.ndarray
+    final_cov: int
+    final_dist: int
+    moves: list = field(default_factory=list)   # (iter, i, j, flags, cov, dist)
 
 
 @dataclass
@@ -330,6 +359,42 @@ class Context:
         fd = np.empty(o.size * B, dtype=np.int64)
         self._check(lib().stage_evaluate_swaps(self._h, inst, _ptr(o), o.size, R, _ptr(fc), _ptr(fd)))
         return fc.reshape(o.size, B), fd.reshape(o.size, B)
+
+    def fleet_tabu(self, inst: int, K_rotary: int, K_fixed: int, R: int, iters: int, tenure: int, base_helipad,
+                   mission_rotary, start_rotary=None, start_fixed=None, accept_worsening: bool = True,
+                   trajectory: bool = True) -> FleetResult:
+        """stage_fleet_tabu: rotary- and fixed-wing vehicles, helipads, rotary-only missions."""
+        p = StageFleetParams()
+        p.K_rotary, p.K_fixed, p.R, p.iters, p.tenure = K_rotary, K_fixed, R, iters, tenure
+        p.accept_worsening = 1 if accept_worsening else 0
+        hp = np.ascontiguousarray(base_helipad, dtype=np.uint8)
+        mr = np.ascontiguousarray(mission_rotary, dtype=np.uint8)
+        p.base_helipad, p.mission_rotary = _ptr(hp), _ptr(mr)
+        keep = [hp, mr]
+        if start_rotary is not None or start_fixed is not None:
+            sr = _host_i32(start_rotary if start_rotary is not None else [], K_rotary)
+            sf = _host_i32(start_fixed if start_fixed is not None else [], K_fixed)
+            keep += [sr, sf]
+            p.start_rotary = _ptr(sr) if K_rotary else None
+            p.start_fixed = _ptr(sf) if K_fixed else None
+            if not K_rotary and not K_fixed:
+                raise ValueError("no vehicles")
+            if p.start_rotary is None and p.start_fixed is None:
+                raise ValueError("start given for zero vehicles")
+        r = StageFleetResult()
+        br, bf = np.empty(K_rotary, dtype=np.int32), np.empty(K_fixed, dtype=np.int32)
+        fr, ff = np.empty(K_rotary, dtype=np.int32), np.empty(K_fixed, dtype=np.int32)
+        r.best_rotary, r.best_fixed = _ptr(br), _ptr(bf)
+        r.final_rotary, r.final_fixed = _ptr(fr), _ptr(ff)
+        traj = (StageMove * max(1, iters))() if trajectory else None
+        self._check(lib().stage_fleet_tabu(self._h, inst, C.byref(p), C.byref(r),
+                                           C.cast(traj, C.c_void_p) if traj is not None else None))
+        moves = []
+        if traj is not None:
+            moves = [(traj[k].iter, traj[k].i, traj[k].j, traj[k].flags, traj[k].cov, traj[k].dist)
+                     for k in range(min(r.n_moves, iters))]
+        return FleetResult(r.n_moves, br, bf, r.best_cov, r.best_dist, r.best_iter, fr, ff, r.final_cov,
+                           r.final_dist, moves)
 
     def local_search(self, inst: int, K: int, R: int, perm_slots, perm_cands, max_moves: int = 100000,
                      start_open=None, trajectory: bool = True) -> LocalSearchResult:
@@ -580,6 +645,7 @@ stage_evaluate_placement = Context.evaluate_placement
 stage_evaluate_swaps = Context.evaluate_swaps
 stage_tabu_run = Context.tabu_run
 stage_local_search = Context.local_search
+stage_fleet_tabu = Context.fleet_tabu
 stage_best_two = Context.best_two
 stage_read_table = Context.read_table
 stage_update_instance = Context.update_instance

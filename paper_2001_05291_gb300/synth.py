@@ -35,6 +35,7 @@ _MASK = (1 << 64) - 1
 # entity classes (stream identifiers)
 CLS_BASES, CLS_FACILITIES, CLS_PICKUPS, CLS_DROPOFF, CLS_SIZES, CLS_ARRIVALS, CLS_UPDATES = 1, 2, 3, 4, 5, 6, 7
 CLS_SCAN = 8   # scan orders of the local search
+CLS_TYPES = 9  # base and mission types of the heterogeneous fleet
 
 # Draws consumed per point and attempt: [mixture choice, cluster id, u1, u2].
 _DRAWS_PER_POINT = 4
@@ -246,6 +247,26 @@ def geo_instance(name: str, seed: int, B: int, M: int, K: int, R: int, iters: in
 def geo_paper(seed: int = 5) -> Instance:
     """The paper's own scale on Eq. 1 legs: B=378 bases, M=180 missions, K=12; R=1500 km, 200 it, tenure 7."""
     return geo_instance("geo_paper", seed, 378, 180, 12, 1500 * KM, 200, 7)
+
+
+def fleet_types(seed: int, B: int, M: int, n_helipads: int, rotary_frac: float):
+    """Base and mission types of a heterogeneous fleet: n_helipads of the B bases
+    are helipads (the rest aerodromes) and about rotary_frac of the missions
+    need a rotary-wing vehicle; returns uint8 arrays [B], [M]."""
+    kb = draws_u64(stream_key(seed, CLS_TYPES, 0), np.arange(B))
+    heli = np.zeros(B, dtype=np.uint8)
+    heli[np.argsort(kb, kind="stable")[:n_helipads]] = 1
+    rot = (u01(draws_u64(stream_key(seed, CLS_TYPES, 1), np.arange(M))) < rotary_frac).astype(np.uint8)
+    return heli, rot
+
+
+def fleet_paper(seed: int = 5):
+    """The paper's fleet (Sec. 5): 378 bases of which 104 helipads, 8 rotary-wing
+    and 4 fixed-wing vehicles, 180 missions (30 % rotary-only), Eq. 1 legs.
+    Returns (instance, helipad mask, rotary-only mask, K_rotary, K_fixed)."""
+    inst = geo_paper(seed)
+    heli, rot = fleet_types(seed, inst.B, inst.M, 104, 0.3)
+    return inst, heli, rot, 8, 4
 
 
 def batched_sizes(seed: int = 3, n: int = 512):

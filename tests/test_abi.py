@@ -64,6 +64,8 @@ int main(void) {
   P(stage_result); O(stage_result, best_cov); O(stage_result, t_end_ns);
   P(stage_ls_params); O(stage_ls_params, perm_slots); O(stage_ls_params, start_open);
   P(stage_ls_result); O(stage_ls_result, final_cov); O(stage_ls_result, final_open);
+  P(stage_fleet_params); O(stage_fleet_params, base_helipad); O(stage_fleet_params, start_fixed);
+  P(stage_fleet_result); O(stage_fleet_result, final_dist); O(stage_fleet_result, final_fixed);
   return 0;
 }
 """
@@ -83,7 +85,8 @@ def test_ctypes_layouts_match_header(tmp_path):
           "stage_tabu_params": stage.StageTabuParams, "stage_tabu_result": stage.StageTabuResult,
           "stage_update": stage.StageUpdate, "stage_request": stage.StageRequest,
           "stage_result": stage.StageResult, "stage_ls_params": stage.StageLsParams,
-          "stage_ls_result": stage.StageLsResult}
+          "stage_ls_result": stage.StageLsResult, "stage_fleet_params": stage.StageFleetParams,
+          "stage_fleet_result": stage.StageFleetResult}
     for key, val in got.items():
         if "." in key:
             t, f = key.split(".")
