@@ -47,7 +47,7 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="large",
-                    choices=["tiny", "province", "large", "batched", "serving", "local", "geo"])
+                    choices=["tiny", "province", "large", "batched", "serving", "local", "geo", "fleet"])
     ap.add_argument("--passes", type=int, default=16, help="local: permutation pairs (scan orders) supplied")
     ap.add_argument("--instances", type=int, default=512, help="batched / serving: instances")
     ap.add_argument("--slots", type=int, default=512, help="batched / serving: engine slots")
@@ -654,6 +654,62 @@ def run_local(args):
     return 0
 
 
+def run_fleet(args):
+    """The heterogeneous fleet on the large workload's table (or --missions):
+    2000 bases of which 500 helipads, 48 rotary-wing and 16 fixed-wing vehicles,
+    30 % rotary-only missions, 200 Tabu iterations from the ranking.  Each
+    iteration runs two swap passes over the table (every vehicle with the
+    missions either type may fly; the rotary-wing vehicles with the
+    rotary-only missions), the combined selection and the refreshes."""
+    import numpy as np
+    import torch
+    from paper_2001_05291_gb300 import build, stage, synth
+    rank, world, local = env_rank()
+    torch.cuda.set_device(local)
+    build.build()
+    inst = workload("large", args.missions)
+    heli, rot = synth.fleet_types(inst.seed, inst.B, inst.M, inst.B // 4, 0.3)
+    Kr, Kf, iters, tenure = 48, 16, 200, inst.tenure
+    ctx = stage.Context(device=local, profile=True)
+    stream = ctx.torch_stream
+    dev = [torch.from_numpy(np.ascontiguousarray(a)).to(f"cuda:{local}")
+           for a in (inst.base_xy, inst.pick_xy, inst.drop_xy)]
+    h = ctx.load_instance(*dev)
+    for _ in range(args.warmup):
+        ctx.fleet_tabu(h, Kr, Kf, inst.R, iters, tenure, heli, rot)
+    ctx.reset_stats()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    n = 0
+    for _ in range(args.steps):
+        r = ctx.fleet_tabu(h, Kr, Kf, inst.R, iters, tenure, heli, rot)
+        n += r.n_moves
+    e1.record(stream)
+    e1.synchronize()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    stats = {k: ctx.kernel_stats(k) for k in ("swap_eval", "fleet_select", "refresh", "init", "rowsum", "topk")}
+    ctx.unload_instance(h)
+    line = {"metric": "heterogeneous-fleet Tabu iters/s", "value": n / (ms / 1000.0), "unit": "iters/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+            "data": "synthetic",
+            "config": {"workload": f"heterogeneous fleet on {inst.name}: B={inst.B} ({int(heli.sum())} helipads), "
+                                   f"M={inst.M} ({int(rot.sum())} rotary-only), {Kr} rotary-wing + {Kf} "
+                                   f"fixed-wing vehicles, R={inst.R} m, {iters} iterations, tenure {tenure}"},
+            "best": {"cov": r.best_cov, "dist": r.best_dist, "iter": r.best_iter},
+            # no roofline line here: the second search's swap launches return at
+            # once after a fixed-wing move, so an average per launch means nothing
+            "kernels_ms": {k: {"launches": a, "total_ms": b} for k, (a, b) in stats.items()},
+            "gpu_launches": sum(a for a, _ in stats.values()), "clocks": clk}
+    print(json.dumps(line))
+    ctx.close()
+    return 0
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
@@ -664,6 +720,8 @@ def main():
         return run_serving(args)
     if args.workload == "local":
         return run_local(args)
+    if args.workload == "fleet":
+        return run_fleet(args)
     return run_ours(args)
 
 
