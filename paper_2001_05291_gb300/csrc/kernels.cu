@@ -1807,12 +1807,105 @@ cudaError_t launch_select(const TabuBuffers &w, int nC, cudaStream_t s)
 // gain / extra are cleared for the next evaluation.
 // --------------------------------------------------------------------------
 
+constexpr int kRefQ = 2048;   // missions queued for a cooperative rescan per block
+
+// Best and second-best open base of the missions queued for a rescan (their
+// best or second best was the closed base), G threads per mission with G
+// chosen from the queue length so that a short queue still has every thread
+// loading: a thread scans every G-th slot, 8 independent loads at a time,
+// with keys (cost, base id) ordered as in scan_best_two; the G partial pairs
+// are merged by butterfly shuffles within the group.  The mission's terms (V0,
+// loss of its best slot) are added as mission_terms adds them.
+__device__ __forceinline__ void refresh_rescans(const TabuBuffers &w, const int32_t *__restrict__ cost,
+                                                const int *s_open, const int *s_q, int nq, int *s_lc,
+                                                unsigned long long *s_ld, long long &v0c, long long &v0d)
+{
+    constexpr int L = 8;
+    const unsigned full = 0xffffffffu;
+    const int K = w.K;
+    const size_t M_pad = w.M_pad;
+    const int G = nq <= 32 ? 8 : nq <= 64 ? 4 : nq <= 128 ? 2 : 1;   // the same on every thread
+    const int per = blockDim.x / G;
+    const int sub = threadIdx.x & (G - 1);
+    for (int q0 = 0; q0 < nq; q0 += per) {
+        const int qi = q0 + (int)threadIdx.x / G;
+        const bool has = qi < nq;
+        const int m = has ? s_q[qi] : 0;
+        unsigned long long e1 = ~0ull, e2 = ~0ull;
+        int k1 = -1, k2 = -1;
+        if (has) {
+            for (int k0 = sub; k0 < K; k0 += L * G) {
+                int cv[L];
+#pragma unroll
+                for (int u = 0; u < L; u++) {
+                    const int k = k0 + u * G;
+                    cv[u] = k < K ? __ldg(cost + (size_t)s_open[k] * M_pad + m) : 0;
+                }
+#pragma unroll
+                for (int u = 0; u < L; u++) {
+                    const int k = k0 + u * G;
+                    if (k < K) {
+                        const unsigned long long e = ((unsigned long long)(unsigned)cv[u] << 32) | (unsigned)s_open[k];
+                        if (e < e1) {
+                            e2 = e1; k2 = k1;
+                            e1 = e; k1 = k;
+                        } else if (e < e2) {
+                            e2 = e; k2 = k;
+                        }
+                    }
+                }
+            }
+        }
+        // every lane takes part (lanes without a mission carry empty pairs)
+        for (int off = 1; off < G; off <<= 1) {
+            const unsigned long long f1 = __shfl_xor_sync(full, e1, off), f2 = __shfl_xor_sync(full, e2, off);
+            const int g1 = __shfl_xor_sync(full, k1, off), g2 = __shfl_xor_sync(full, k2, off);
+            if (f1 < e1) {
+                if (f2 < e1) { e2 = f2; k2 = g2; } else { e2 = e1; k2 = k1; }
+                e1 = f1; k1 = g1;
+            } else if (f1 < e2) {
+                e2 = f1; k2 = g1;
+            }
+        }
+        if (has && sub == 0) {
+            const int a = (int)(e1 >> 32);
+            const int b = e2 == ~0ull ? kInf : (int)(e2 >> 32);
+            w.a[m] = a; w.b[m] = b; w.s1[m] = (int16_t)k1; w.s2[m] = (int16_t)k2;
+            mission_terms(a, b, w.R, v0c, v0d, s_lc, s_ld, k1);
+        }
+    }
+}
+
+// One mission's rescan by its own thread, past the queue's capacity (out of
+// line: a rare path kept out of the unrolled loop's registers).  Writes the
+// mission's state; returns (a, b) and the best slot in k1.
+__device__ __noinline__ int2 refresh_scan_one(const TabuBuffers &w, const int32_t *__restrict__ cost, int m,
+                                              const int *s_open, int &k1)
+{
+    int a, b, k2;
+    scan_best_two(cost, w.M_pad, m, s_open, w.K, a, b, k1, k2);
+    w.a[m] = a; w.b[m] = b; w.s1[m] = (int16_t)k1; w.s2[m] = (int16_t)k2;
+    return make_int2(a, b);
+}
+
+// a7: incremental refresh after the move (close slot mv_s, open base mv_j in
+// it).  A thread loads a mission's state and the new base's cost together
+// (one round trip, not two dependent ones).  A mission whose best and second
+// best both stay open compares only the new base's cost.  One that lost either
+// needs a rescan of the K open bases: with one mission per thread its own
+// thread does it at once; with several (large instances, grouped searches) it
+// is queued, and after the loop the whole block rescans the queue
+// (refresh_rescans), so the long scans neither serialise behind a thread's
+// other missions nor hold the block's other warps.  Past the queue's capacity
+// a thread scans the mission itself.
 __device__ __forceinline__ void refresh_body(const TabuBuffers &w, const int32_t *__restrict__ cost, int bid,
                                              int nb)
 {
     TabuDevState *st = w.st;
     if (st->done || st->ls_hold) return;
     extern __shared__ unsigned long long sm_ref[];
+    __shared__ int s_q[kRefQ];
+    __shared__ int s_qn;
     unsigned long long *s_ld = sm_ref;
     int *s_lc = reinterpret_cast<int *>(s_ld + w.K);
     int *s_open = s_lc + w.K;
@@ -1821,17 +1914,29 @@ __device__ __forceinline__ void refresh_body(const TabuBuffers &w, const int32_t
         s_lc[k] = 0;
         s_ld[k] = 0;
     }
+    if (threadIdx.x == 0) s_qn = 0;
     __syncthreads();
     const int ss = st->mv_s, jj = st->mv_j;
     const size_t M_pad = w.M_pad;
     const int32_t *rowj = cost + (size_t)jj * M_pad;
     long long v0c = 0, v0d = 0;
-    for (int m = bid * blockDim.x + threadIdx.x; m < w.M; m += nb * blockDim.x) {
-        if (w.mask && !w.mask[m]) continue;
-        int a = w.a[m], b = w.b[m];
-        int k1 = w.s1[m], k2 = w.s2[m];
-        if (k1 != ss && k2 != ss) {
-            const int x = __ldcs(rowj + m);
+    const int base = bid * (int)blockDim.x, stride = nb * (int)blockDim.x;
+    const int rounds = w.M > base ? (w.M - base + stride - 1) / stride : 0;   // the same on every thread
+    const bool queue = rounds > 1;
+    const int lane = threadIdx.x & 31;
+    for (int rd = 0; rd < rounds; rd++) {
+        const int m = base + rd * stride + (int)threadIdx.x;
+        int a = 0, b = 0, k1 = 0, k2 = 0, x = 0;
+        bool in = m < w.M;
+        if (in) {
+            a = w.a[m]; b = w.b[m];
+            k1 = w.s1[m]; k2 = w.s2[m];
+            x = __ldcs(rowj + m);
+            if (w.mask) in = w.mask[m] != 0;
+        }
+        bool term = false;
+        const bool lost = in && (k1 == ss || k2 == ss);
+        if (in && !lost) {
             const int id1 = s_open[k1];
             const int id2 = k2 >= 0 ? s_open[k2] : 0x7fffffff;
             if (x < a || (x == a && jj < id1)) {
@@ -1842,12 +1947,33 @@ __device__ __forceinline__ void refresh_body(const TabuBuffers &w, const int32_t
                 k2 = ss; b = x;
                 w.b[m] = b; w.s2[m] = (int16_t)k2;
             }
-        } else {
-            scan_best_two(cost, M_pad, m, s_open, w.K, a, b, k1, k2);
-            w.a[m] = a; w.b[m] = b; w.s1[m] = (int16_t)k1; w.s2[m] = (int16_t)k2;
+            term = true;
         }
-        mission_terms(a, b, w.R, v0c, v0d, s_lc, s_ld, k1);
+        // queue the missions that lost their best or second best: one shared
+        // atomic per warp, positions in lane order
+        const unsigned lm = __ballot_sync(0xffffffffu, lost);
+        if (lm) {
+            int q0 = kRefQ;   // not queued: scanned in place
+            if (queue) {
+                if (lane == __ffs(lm) - 1) q0 = atomicAdd(&s_qn, __popc(lm));
+                q0 = __shfl_sync(0xffffffffu, q0, __ffs(lm) - 1);
+            }
+            if (lost) {
+                const int pos = q0 + __popc(lm & ((1u << lane) - 1u));
+                if (pos < kRefQ) {
+                    s_q[pos] = m;
+                } else {
+                    const int2 ab = refresh_scan_one(w, cost, m, s_open, k1);
+                    a = ab.x; b = ab.y;
+                    term = true;
+                }
+            }
+        }
+        if (term) mission_terms(a, b, w.R, v0c, v0d, s_lc, s_ld, k1);
     }
+    __syncthreads();
+    const int nq = min(s_qn, kRefQ);   // no thread changes the count after the barrier
+    if (nq > 0) refresh_rescans(w, cost, s_open, s_q, nq, s_lc, s_ld, v0c, v0d);
     // clear the neighbourhood accumulators for the next evaluation
     const size_t nE = (size_t)w.K * w.B;
     const size_t tid = bid * (size_t)blockDim.x + threadIdx.x;
@@ -1858,7 +1984,7 @@ __device__ __forceinline__ void refresh_body(const TabuBuffers &w, const int32_t
     flush_loss_v0(w, s_lc, s_ld, v0c, v0d);
 }
 
-__global__ void __launch_bounds__(256) k_refresh(TabuBuffers w, const int32_t *__restrict__ cost)
+__global__ void __launch_bounds__(256, 4) k_refresh(TabuBuffers w, const int32_t *__restrict__ cost)
 {
     refresh_body(w, cost, blockIdx.x, gridDim.x);
 }
@@ -2745,8 +2871,8 @@ cudaError_t launch_group_select(const GroupSlot *slots, const int2 *map, int tot
     return cudaGetLastError();
 }
 
-__global__ void __launch_bounds__(256) k_group_refresh(const GroupSlot *__restrict__ slots,
-                                                       const int2 *__restrict__ map)
+__global__ void __launch_bounds__(256, 4) k_group_refresh(const GroupSlot *__restrict__ slots,
+                                                          const int2 *__restrict__ map)
 {
     __shared__ GroupSlot g;
     const int2 e = map[blockIdx.x];
