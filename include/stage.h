@@ -73,6 +73,13 @@ typedef int32_t stage_status;
 #define STAGE_THREADSAFE   1u   /* accepted; calls are always serialised */
 #define STAGE_PROFILE      2u   /* time every kernel launch with CUDA events */
 #define STAGE_AUTOTUNE     4u   /* tune the swap pass's tile the first time a shape is met */
+#define STAGE_FULL_PASS    8u   /* Tabu searches (stage_tabu_run) re-evaluate the whole swap
+                                   neighbourhood by a full pass over the cost table every
+                                   iteration.  By default, for tables well beyond the L2 cache,
+                                   the neighbourhood's terms are kept across iterations and
+                                   updated for the missions whose best or second-best open base
+                                   changed (the same values exactly) */
+#define STAGE_INCREMENTAL 16u   /* that incremental update whatever the table's size */
 
 /* instance descriptor flags */
 #define STAGE_DESC_DEVICE  1u   /* base_xy/pick_xy/drop_xy/base_available are device pointers */

@@ -1724,6 +1724,8 @@ __device__ __forceinline__ void select_apply(const TabuBuffers &w, const MoveKey
                 st->n_moves += 1;
                 st->t = t + 1;
                 st->mv_s = P.s; st->mv_i = P.i; st->mv_j = P.j;
+                st->chg_total += st->chg_n;     // the records the last incremental pass took
+                st->chg_n = 0;
                 w.v0[0] = 0;
                 w.v0[1] = 0;
             }
@@ -1809,6 +1811,35 @@ cudaError_t launch_select(const TabuBuffers &w, int nC, cudaStream_t s)
 
 constexpr int kRefQ = 2048;   // missions queued for a cooperative rescan per block
 
+// Whether a mission's terms in the swap neighbourhood changed: they depend on
+// its clamped best and second-best costs and, while it is covered, on its
+// best slot (an uncovered mission adds no extra term to any slot).
+__device__ __forceinline__ bool terms_changed(int ao, int bo, int so, int an, int bn, int sn, int R)
+{
+    const int ao1 = min(ao, R + 1), bo1 = min(bo, R + 1), an1 = min(an, R + 1), bn1 = min(bn, R + 1);
+    return ao1 != an1 || bo1 != bn1 || (an1 <= R && so != sn);
+}
+
+// Append the lanes' changed missions to the record list, two int4 per
+// record: (column, old a, old b, old best slot), (new a, new b, new best
+// slot, 0).  One global atomic per warp; every lane of the warp calls it.
+__device__ __forceinline__ void record_changes(const TabuBuffers &w, bool ch, int m, int ao, int bo, int so, int an,
+                                               int bn, int sn)
+{
+    const unsigned full = 0xffffffffu;
+    const unsigned cm = __ballot_sync(full, ch);
+    if (!cm) return;
+    const int lane = threadIdx.x & 31, lead = __ffs(cm) - 1;
+    int q0 = 0;
+    if (lane == lead) q0 = atomicAdd(&w.st->chg_n, __popc(cm));
+    q0 = __shfl_sync(full, q0, lead);
+    if (ch) {
+        int4 *r = w.chg + 2 * (size_t)(q0 + __popc(cm & ((1u << lane) - 1u)));
+        r[0] = make_int4(m, ao, bo, so);
+        r[1] = make_int4(an, bn, sn, 0);
+    }
+}
+
 // Best and second-best open base of the missions queued for a rescan (their
 // best or second best was the closed base), G threads per mission with G
 // chosen from the queue length so that a short queue still has every thread
@@ -1833,6 +1864,10 @@ __device__ __forceinline__ void refresh_rescans(const TabuBuffers &w, const int3
         const int m = has ? s_q[qi] : 0;
         unsigned long long e1 = ~0ull, e2 = ~0ull;
         int k1 = -1, k2 = -1;
+        int ao = 0, bo = 0, so = 0;   // the state before the move (recorded if it changes)
+        if (has && sub == 0 && w.chg) {
+            ao = w.a[m]; bo = w.b[m]; so = w.s1[m];
+        }
         if (has) {
             for (int k0 = sub; k0 < K; k0 += L * G) {
                 int cv[L];
@@ -1867,12 +1902,14 @@ __device__ __forceinline__ void refresh_rescans(const TabuBuffers &w, const int3
                 e2 = f1; k2 = g1;
             }
         }
-        if (has && sub == 0) {
-            const int a = (int)(e1 >> 32);
-            const int b = e2 == ~0ull ? kInf : (int)(e2 >> 32);
+        const bool lead = has && sub == 0;
+        const int a = (int)(e1 >> 32);
+        const int b = e2 == ~0ull ? kInf : (int)(e2 >> 32);
+        if (lead) {
             w.a[m] = a; w.b[m] = b; w.s1[m] = (int16_t)k1; w.s2[m] = (int16_t)k2;
             mission_terms(a, b, w.R, v0c, v0d, s_lc, s_ld, k1);
         }
+        if (w.chg) record_changes(w, lead && terms_changed(ao, bo, so, a, b, k1, w.R), m, ao, bo, so, a, b, k1);
     }
 }
 
@@ -1936,6 +1973,7 @@ __device__ __forceinline__ void refresh_body(const TabuBuffers &w, const int32_t
         }
         bool term = false;
         const bool lost = in && (k1 == ss || k2 == ss);
+        const int ao = a, bo = b, so = k1;   // the state before the move
         if (in && !lost) {
             const int id1 = s_open[k1];
             const int id2 = k2 >= 0 ? s_open[k2] : 0x7fffffff;
@@ -1970,16 +2008,30 @@ __device__ __forceinline__ void refresh_body(const TabuBuffers &w, const int32_t
             }
         }
         if (term) mission_terms(a, b, w.R, v0c, v0d, s_lc, s_ld, k1);
+        if (w.chg) record_changes(w, term && terms_changed(ao, bo, so, a, b, k1, w.R), m, ao, bo, so, a, b, k1);
     }
     __syncthreads();
     const int nq = min(s_qn, kRefQ);   // no thread changes the count after the barrier
     if (nq > 0) refresh_rescans(w, cost, s_open, s_q, nq, s_lc, s_ld, v0c, v0d);
-    // clear the neighbourhood accumulators for the next evaluation
-    const size_t nE = (size_t)w.K * w.B;
-    const size_t tid = bid * (size_t)blockDim.x + threadIdx.x;
-    const size_t nth = (size_t)nb * blockDim.x;
-    for (size_t q = tid; q < nE; q += nth) { w.extra_c[q] = 0; w.extra_d[q] = 0; }
-    for (size_t q = tid; q < (size_t)w.B; q += nth) { w.gain_c[q] = 0; w.gain_d[q] = 0; }
+    if (w.chg) {
+        // the terms stay; the closed base is a candidate again and its column
+        // is rebuilt from zero (k_swap_row)
+        if (bid == 0) {
+            const int ic = st->mv_i;
+            for (int k = threadIdx.x; k < w.K; k += blockDim.x) {
+                w.extra_c[(size_t)k * w.B + ic] = 0;
+                w.extra_d[(size_t)k * w.B + ic] = 0;
+            }
+            if (threadIdx.x == 0) { w.gain_c[ic] = 0; w.gain_d[ic] = 0; }
+        }
+    } else {
+        // clear the neighbourhood accumulators for the next full evaluation
+        const size_t nE = (size_t)w.K * w.B;
+        const size_t tid = bid * (size_t)blockDim.x + threadIdx.x;
+        const size_t nth = (size_t)nb * blockDim.x;
+        for (size_t q = tid; q < nE; q += nth) { w.extra_c[q] = 0; w.extra_d[q] = 0; }
+        for (size_t q = tid; q < (size_t)w.B; q += nth) { w.gain_c[q] = 0; w.gain_d[q] = 0; }
+    }
     __syncthreads();
     flush_loss_v0(w, s_lc, s_ld, v0c, v0d);
 }
@@ -1993,6 +2045,200 @@ cudaError_t launch_refresh(const TabuBuffers &w, const int32_t *cost, cudaStream
 {
     size_t sm = (size_t)w.K * (8 + 4 + 4);
     k_refresh<<<grid_missions(w.M_pad), 256, sm, s>>>(w, cost);
+    return cudaGetLastError();
+}
+
+// --------------------------------------------------------------------------
+// a4, incremental form.  With the gain and extra terms kept across
+// iterations, a move changes them only through the missions whose clamped
+// best / second-best cost or best slot changed (recorded by the refresh) and
+// through the closed base, which is a candidate again.  k_swap_delta takes
+// each recorded mission's old terms out of, and its new terms into, every
+// other candidate row; k_swap_row rebuilds the closed base's column over all
+// missions.  Afterwards gain and extra equal what a full pass over the table
+// would give for the new placement (integer sums: exactly), so the
+// selection still scores every swap of the neighbourhood.
+// --------------------------------------------------------------------------
+constexpr int kDeltaRows = 256;    // candidate positions per block, one per thread
+constexpr int kDeltaChunk = 32;    // recorded missions staged per block step
+constexpr int kDeltaBatch = 8;     // cost loads in flight per thread
+
+bool swap_delta_fits(int K) { return K <= kPipeMaxK; }
+
+// One run of extra terms of one row at one slot, added when the slot changes.
+struct DeltaRun {
+    int s, c;
+    long long d;
+};
+
+__device__ __forceinline__ void delta_run_add(DeltaRun &run, int s, int c, int d, const TabuBuffers &w, int j)
+{
+    if (s != run.s) {
+        if (run.s >= 0 && (run.c | (run.d != 0))) {
+            atomicAdd(&w.extra_c[(size_t)run.s * w.B + j], run.c);
+            atomicAdd(&w.extra_d[(size_t)run.s * w.B + j], (unsigned long long)run.d);
+        }
+        run.s = s;
+        run.c = 0;
+        run.d = 0;
+    }
+    run.c += c;
+    run.d += d;
+}
+
+// Thread = one base j (every base but the one the move closed: a column
+// that is not a candidate's is never read, and is rebuilt by k_swap_row
+// when its base closes); the block walks chunks of the record list, staged
+// in shared memory, and reads each recorded mission's costs from the
+// mission-major copy of the table, so a warp reads 32 consecutive bases of
+// one mission (one 128-byte line).  The gain terms of the row add up in
+// registers; the extra terms go out in runs of one slot (the records come in
+// runs of neighbouring missions, which share slots).
+__global__ void __launch_bounds__(kDeltaRows) k_swap_delta(TabuBuffers w)
+{
+    TabuDevState *st = w.st;
+    if (st->done || st->ls_hold) return;
+    __shared__ int4 s_old[kDeltaChunk];   // column, clamped a, clamped b, best slot: before the move
+    __shared__ int4 s_new[kDeltaChunk];   // clamped a, clamped b, best slot: after
+    const int ic = st->mv_i, R = w.R;
+    const int nrec = min(st->chg_n, w.M);
+    const int j = blockIdx.x * kDeltaRows + (int)threadIdx.x;
+    const bool row = j < w.B && j != ic;   // the closed base's column: k_swap_row
+    const int32_t *colp = w.costT + (row ? j : 0);
+    const size_t ld = (size_t)w.ldT;
+    long long gc = 0, gd = 0;
+    DeltaRun rn{-1, 0, 0}, ro{-1, 0, 0};   // the new state's terms, the old state's (taken out)
+    for (int e0 = blockIdx.y * kDeltaChunk; e0 < nrec; e0 += gridDim.y * kDeltaChunk) {   // the same on every thread
+        const int n = min(kDeltaChunk, nrec - e0);
+        __syncthreads();   // the previous chunk is consumed
+        if ((int)threadIdx.x < n) {
+            const int4 ro = w.chg[2 * (size_t)(e0 + threadIdx.x)], rq = w.chg[2 * (size_t)(e0 + threadIdx.x) + 1];
+            s_old[threadIdx.x] = make_int4(ro.x, min(ro.y, R + 1), min(ro.z, R + 1), ro.w);
+            s_new[threadIdx.x] = make_int4(min(rq.x, R + 1), min(rq.y, R + 1), rq.z, 0);
+        }
+        __syncthreads();
+        if (!row) continue;
+        for (int k0 = 0; k0 < n; k0 += kDeltaBatch) {
+            int xv[kDeltaBatch];
+#pragma unroll
+            for (int u = 0; u < kDeltaBatch; u++)
+                xv[u] = k0 + u < n ? __ldg(colp + (size_t)s_old[k0 + u].x * ld) : INT_MAX;
+#pragma unroll
+            for (int u = 0; u < kDeltaBatch; u++) {
+                const int x = xv[u];
+                if (k0 + u >= n) break;
+                const int4 o = s_old[k0 + u], q = s_new[k0 + u];
+                const int ao = o.y, bo = o.z, so = o.w, an = q.x, bn = q.y, sn = q.z;
+                if (x >= bo && x >= bn) continue;   // no term in either state (a <= b)
+                const int cao = ao <= R, cbo = bo <= R, can = an <= R, cbn = bn <= R;
+                if (x < an) { gc += 1 - can; gd += (long long)x - (can ? an : 0); }
+                if (x < ao) { gc -= 1 - cao; gd -= (long long)x - (cao ? ao : 0); }
+                if (x < bn) {
+                    const int nc = can - cbn, nd = (can ? max(x, an) : 0) - (cbn ? bn : 0);
+                    if (nc | nd) delta_run_add(rn, sn, nc, nd, w, j);
+                }
+                if (x < bo) {
+                    const int oc = cao - cbo, od = (cao ? max(x, ao) : 0) - (cbo ? bo : 0);
+                    if (oc | od) delta_run_add(ro, so, -oc, -od, w, j);
+                }
+            }
+        }
+    }
+    if (!row) return;
+    delta_run_add(rn, -1, 0, 0, w, j);   // flush
+    delta_run_add(ro, -1, 0, 0, w, j);
+    if (gc) atomicAdd(&w.gain_c[j], (int)gc);
+    if (gd) atomicAdd(&w.gain_d[j], (unsigned long long)gd);
+}
+
+cudaError_t launch_swap_delta(const TabuBuffers &w, cudaStream_t s)
+{
+    const int gx = (w.B + kDeltaRows - 1) / kDeltaRows;
+    // about two waves of resident blocks over the record chunks (their count
+    // is known only on the device), no more than the missions could fill
+    const int sms = g_num_sms > 0 ? g_num_sms : 152;
+    const int max_y = (w.M + kDeltaChunk - 1) / kDeltaChunk;
+    int gy = (2 * 6 * sms + gx - 1) / gx;
+    if (gy > max_y) gy = max_y;
+    if (gy < 1) gy = 1;
+    k_swap_delta<<<dim3(gx, gy), kDeltaRows, 0, s>>>(w);
+    return cudaGetLastError();
+}
+
+int table_ldT(int B) { return (B + 31) / 32 * 32; }
+
+// Tiled transpose through shared memory: reads and writes both coalesced.
+__global__ void __launch_bounds__(256) k_transpose_table(const int32_t *__restrict__ cost, int B, int M_pad, int ldT,
+                                                         int32_t *__restrict__ costT)
+{
+    __shared__ int32_t tile[32][33];
+    const int m0 = blockIdx.x * 32, b0 = blockIdx.y * 32;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8
+    for (int k = ty; k < 32; k += 8) {
+        const int b = b0 + k, m = m0 + tx;
+        tile[k][tx] = (b < B && m < M_pad) ? cost[(size_t)b * M_pad + m] : INT_MAX;
+    }
+    __syncthreads();
+    for (int k = ty; k < 32; k += 8) {
+        const int m = m0 + k, b = b0 + tx;
+        if (m < M_pad && b < ldT) costT[(size_t)m * ldT + b] = tile[tx][k];
+    }
+}
+
+cudaError_t launch_transpose_table(const int32_t *cost, int B, int M_pad, int32_t *costT, cudaStream_t s)
+{
+    const int ldT = table_ldT(B);
+    k_transpose_table<<<dim3((M_pad + 31) / 32, ldT / 32), 256, 0, s>>>(cost, B, M_pad, ldT, costT);
+    return cudaGetLastError();
+}
+
+// The closed base's column over every mission, for the new placement.  Its
+// entries were zeroed by the refresh.
+__global__ void __launch_bounds__(256) k_swap_row(TabuBuffers w, const int32_t *__restrict__ cost)
+{
+    TabuDevState *st = w.st;
+    if (st->done || st->ls_hold) return;
+    extern __shared__ unsigned long long sm_row[];
+    unsigned long long *s_ed = sm_row;                        // [K]
+    int *s_ec = reinterpret_cast<int *>(s_ed + w.K);          // [K]
+    for (int k = threadIdx.x; k < w.K; k += blockDim.x) { s_ed[k] = 0; s_ec[k] = 0; }
+    __syncthreads();
+    const int ic = st->mv_i, R = w.R;
+    const int32_t *row = cost + (size_t)ic * w.M_pad;
+    long long gc = 0, gd = 0;
+    for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < w.M; m += gridDim.x * blockDim.x) {
+        const int a = min(w.a[m], R + 1), b = min(w.b[m], R + 1);
+        const int x = __ldcs(row + m);
+        if (x < b) {
+            const int ca = a <= R, cb = b <= R;
+            const int dc = ca - cb;
+            const long long dd = (ca ? (long long)max(x, a) : 0ll) - (cb ? (long long)b : 0ll);
+            if (dc | (dd != 0)) {
+                const int sl = w.s1[m];
+                atomicAdd(&s_ec[sl], dc);
+                atomicAdd(&s_ed[sl], (unsigned long long)dd);
+            }
+            if (x < a) {
+                gc += 1 - ca;
+                gd += (long long)x - (ca ? (long long)a : 0ll);
+            }
+        }
+    }
+    block_sum2<256>(gc, gd);
+    if (threadIdx.x == 0) {
+        if (gc) atomicAdd(&w.gain_c[ic], (int)gc);
+        if (gd) atomicAdd(&w.gain_d[ic], (unsigned long long)gd);
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < w.K; k += blockDim.x) {
+        if (s_ec[k]) atomicAdd(&w.extra_c[(size_t)k * w.B + ic], s_ec[k]);
+        if (s_ed[k]) atomicAdd(&w.extra_d[(size_t)k * w.B + ic], s_ed[k]);
+    }
+}
+
+cudaError_t launch_swap_row(const TabuBuffers &w, const int32_t *cost, cudaStream_t s)
+{
+    k_swap_row<<<grid_missions(w.M_pad), 256, (size_t)w.K * 12 + 16, s>>>(w, cost);
     return cudaGetLastError();
 }
 

@@ -158,6 +158,8 @@ void free_instance(stage_ctx *c, Instance *in)
     dev_free(c, in->mem_coords);
     dev_free(c, in->mem_ws);
     dev_free(c, in->mem_scratch);
+    dev_free(c, in->mem_chg);
+    dev_free(c, in->mem_costT);
     delete in;
 }
 
@@ -439,6 +441,72 @@ stage_status run_tabu(stage_ctx *c, Instance *in, const stage_tabu_params *p,
     CK(timed(c, "begin", 1, [&] { return launch_begin(tb, rs ? 1 : 0, c->stream); }));
     volatile int *done_flag = static_cast<volatile int *>(c->pinned);
     const bool profiling = (c->flags & STAGE_PROFILE) != 0;
+    // Incremental neighbourhood (multi-kernel path): one full pass, then each
+    // iteration selects and applies a move, refreshes the per-mission state
+    // (recording the missions whose terms changed) and updates the terms from
+    // those records and the closed base's column.  STAGE_FULL_PASS: a full
+    // pass every iteration instead.
+    // Only for tables well beyond the L2 cache: an L2-resident table is
+    // streamed faster than the scattered columns of the changed missions.
+    bool inc = !(c->flags & STAGE_FULL_PASS) && swap_delta_fits(K) && swap_variant_default() &&
+               ((c->flags & STAGE_INCREMENTAL) ||
+                (size_t)nC * in->M_pad * sizeof(int32_t) >= kIncrementalMinTableBytes);
+    TabuBuffers tw = tb;   // the buffers of this run's multi-kernel launches
+    if (inc) {
+        // the change records and the mission-major copy of the table; with no
+        // room for them (the context's HBM budget) the search takes the full pass
+        const int ldT = table_ldT(in->B);
+        const size_t need = (size_t)in->M_pad * 2 * sizeof(int4);
+        const size_t needT = (size_t)in->M_pad * ldT * sizeof(int32_t);
+        if (!in->mem_chg.p || in->mem_chg.bytes < need) {
+            dev_free(c, in->mem_chg);
+            if (dev_alloc(c, need, in->mem_chg) != STAGE_OK) {
+                inc = false;
+                set_err(c, STAGE_OK, "");   // a refused allocation here is not an error of the search
+            }
+        }
+        if (inc && !in->costT_ok) {
+            if (!in->mem_costT.p || in->mem_costT.bytes < needT) {
+                dev_free(c, in->mem_costT);
+                if (dev_alloc(c, needT, in->mem_costT) != STAGE_OK) {
+                    inc = false;
+                    set_err(c, STAGE_OK, "");
+                }
+            }
+            if (inc) {
+                CK(timed(c, "transpose", 1, [&] {
+                    return launch_transpose_table(in->cost, in->B, in->M_pad,
+                                                  static_cast<int32_t *>(in->mem_costT.p), c->stream);
+                }));
+                in->ldT = ldT;
+                in->costT_ok = true;
+            }
+        }
+        if (inc) {
+            tw.chg = static_cast<int4 *>(in->mem_chg.p);
+            tw.costT = static_cast<const int32_t *>(in->mem_costT.p);
+            tw.ldT = in->ldT;
+        }
+    }
+    // one Tabu iteration of the multi-kernel path
+    auto step = [&](bool time_each) -> cudaError_t {
+        cudaError_t e = cudaSuccess;
+        auto run = [&](const char *nm, auto &&f) {
+            if (e != cudaSuccess) return;
+            e = time_each ? timed(c, nm, 1, f) : f();
+        };
+        if (!inc) run("swap_eval", [&] { return launch_swap_eval(tw, in->cost, nC, 0, c->stream); });
+        run("select", [&] { return launch_select(tw, nC, c->stream); });
+        run("refresh", [&] { return launch_refresh(tw, in->cost, c->stream); });
+        if (inc) {
+            run("swap_delta", [&] { return launch_swap_delta(tw, c->stream); });
+            run("swap_row", [&] { return launch_swap_row(tw, in->cost, c->stream); });
+        }
+        return e;
+    };
+    const bool multi = nC > 0 && iters > 0 && !(tabu_resident_fits(K, in->B, in->M_pad, nC) && swap_variant_default()) &&
+                       !(tabu_small_fits(nC, in->M_pad, K) && swap_variant_default());
+    if (inc && multi) CK(timed(c, "swap_eval", 1, [&] { return launch_swap_eval(tw, in->cost, nC, 0, c->stream); }));
     if (nC > 0 && iters > 0 && tabu_resident_fits(K, in->B, in->M_pad, nC) && swap_variant_default()) {
         // small instance: the whole search in one block, its arrays in shared memory
         CK(timed(c, "tabu_small", 1, [&] { return launch_tabu_resident(tb, in->cost, nC, iters, c->stream); }));
@@ -450,11 +518,7 @@ stage_status run_tabu(stage_ctx *c, Instance *in, const stage_tabu_params *p,
         cudaGraph_t gr = nullptr;
         cudaGraphExec_t ge = nullptr;
         cudaError_t e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
-        for (int k = 0; e == cudaSuccess && k < kGraphIters; k++) {
-            e = launch_swap_eval(tb, in->cost, nC, 0, c->stream);
-            if (e == cudaSuccess) e = launch_select(tb, nC, c->stream);
-            if (e == cudaSuccess) e = launch_refresh(tb, in->cost, c->stream);
-        }
+        for (int k = 0; e == cudaSuccess && k < kGraphIters; k++) e = step(false);
         cudaError_t e2 = cudaStreamEndCapture(c->stream, &gr);
         if (e == cudaSuccess) e = e2;
         if (e == cudaSuccess) e = cudaGraphInstantiate(&ge, gr, 0);
@@ -465,7 +529,12 @@ stage_status run_tabu(stage_ctx *c, Instance *in, const stage_tabu_params *p,
         }
         int it = 0;
         for (; it + kGraphIters <= iters; it += kGraphIters) {
-            for (const char *nm : {"swap_eval", "select", "refresh"}) c->stats[nm].launches += kGraphIters;
+            if (inc) {
+                for (const char *nm : {"select", "refresh", "swap_delta", "swap_row"})
+                    c->stats[nm].launches += kGraphIters;
+            } else {
+                for (const char *nm : {"swap_eval", "select", "refresh"}) c->stats[nm].launches += kGraphIters;
+            }
             e = cudaGraphLaunch(ge, c->stream);
             if (e != cudaSuccess) break;
             if (!p->accept_worsening && ((it / kGraphIters) & 1)) {
@@ -477,16 +546,10 @@ stage_status run_tabu(stage_ctx *c, Instance *in, const stage_tabu_params *p,
         cudaGraphExecDestroy(ge);
         CK(e);
         // the remaining iterations (iterations past the budget do nothing)
-        for (; it < iters && !(!p->accept_worsening && *done_flag); it++) {
-            CK(timed(c, "swap_eval", 1, [&] { return launch_swap_eval(tb, in->cost, nC, 0, c->stream); }));
-            CK(timed(c, "select", 1, [&] { return launch_select(tb, nC, c->stream); }));
-            CK(timed(c, "refresh", 1, [&] { return launch_refresh(tb, in->cost, c->stream); }));
-        }
+        for (; it < iters && !(!p->accept_worsening && *done_flag); it++) CK(step(true));
     } else {
         for (int it = 0; it < iters && nC > 0; it++) {
-            CK(timed(c, "swap_eval", 1, [&] { return launch_swap_eval(tb, in->cost, nC, 0, c->stream); }));
-            CK(timed(c, "select", 1, [&] { return launch_select(tb, nC, c->stream); }));
-            CK(timed(c, "refresh", 1, [&] { return launch_refresh(tb, in->cost, c->stream); }));
+            CK(step(true));
             // the improving-only rule usually stops early: poll the device flag now and then
             if (!p->accept_worsening && (it & 31) == 31) {
                 CK(cudaMemcpyAsync(c->pinned, &tb.st->done, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
@@ -519,6 +582,11 @@ stage_status run_tabu(stage_ctx *c, Instance *in, const stage_tabu_params *p,
     CK(cudaStreamSynchronize(c->stream));
     if (st.err)
         return set_err(c, STAGE_ERR_INTERNAL, "device self-check failed (code %d) at iteration %d", st.err, st.t);
+    if (inc && multi) {
+        // missions the incremental passes took (traffic accounting)
+        std::lock_guard<std::recursive_mutex> g(c->mu);
+        c->stats["swap_delta_records"].launches += st.chg_total + st.chg_n;
+    }
     const int n = std::min(st.n_moves, iters);
     if (traj && n > 0)
         CK(cudaMemcpy(traj, tb.traj, (size_t)n * sizeof(stage_move), cudaMemcpyDeviceToHost));
@@ -1260,9 +1328,11 @@ stage_status stage_update_instance(stage_ctx *c, stage_inst h, const stage_updat
         CK(cudaStreamSynchronize(c->stream));
         in->M = M1;
     }
-    // the single-run workspace is sized for the old table
+    // the single-run workspace is sized for the old table; the mission-major
+    // copy is stale
     dev_free(c, in->mem_ws);
     in->ws_K = 0;
+    in->costT_ok = false;
     return STAGE_OK;
 }
 

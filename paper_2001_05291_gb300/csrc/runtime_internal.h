@@ -49,6 +49,10 @@ struct Instance {
     int ws_K = 0, ws_traj = -1, ws_M_pad = 0;
     stg::TabuBuffers tb{};
     DevBuf mem_scratch;  // rank sums, evaluation outputs, exports
+    DevBuf mem_chg;      // change records of the incremental neighbourhood ([2 * M_pad] int4)
+    DevBuf mem_costT;    // the table mission-major for the incremental neighbourhood (M_pad x ldT)
+    int ldT = 0;
+    bool costT_ok = false;   // mem_costT holds the current table
     size_t scratch_bytes = 0;
     int busy = 0;        // batch requests referring to this instance
 };

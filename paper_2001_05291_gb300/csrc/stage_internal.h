@@ -46,6 +46,10 @@ struct TabuDevState {
     // whether the pass applied a move, passes supplied, "accumulators still
     // valid, skip evaluation and refresh" (after a pass change), local optimum
     int ls_pos, ls_pass, ls_moved, ls_passes, ls_hold, ls_optimum;
+    // incremental neighbourhood: missions the last refresh recorded, and the
+    // running total over the search (for the traffic accounting)
+    int chg_n;
+    long long chg_total;
 };
 
 enum : int { kErrObjectiveMismatch = 1, kErrBadSlot = 2, kErrPipelineTimeout = 4 };
@@ -76,6 +80,15 @@ struct TabuBuffers {
     // missions into two searches); NULL = every mission.  A mission outside
     // has thresholds INT_MIN: no hit, no term, untouched by the refresh.
     const uint8_t *mask;
+    // incremental neighbourhood: [2 * M_pad] records, two int4 per mission
+    // whose terms the last refresh changed: (column, old a, old b, old best
+    // slot), (new a, new b, new best slot, 0); the gain / extra terms are then
+    // kept across iterations and updated from these records.  NULL = the
+    // refresh clears the terms and a full pass rebuilds them every iteration.
+    int4 *chg;
+    // incremental neighbourhood: the cost table mission-major, costT[m * ldT + j]
+    const int32_t *costT;
+    int ldT;
 };
 
 constexpr int kSelectBlocks = 148;
@@ -103,6 +116,15 @@ cudaError_t launch_swap_eval(const TabuBuffers &w, const int32_t *cost, int nC, 
                              cudaStream_t s);
 cudaError_t launch_select(const TabuBuffers &w, int nC, cudaStream_t s);
 cudaError_t launch_refresh(const TabuBuffers &w, const int32_t *cost, cudaStream_t s);
+// Incremental neighbourhood (w.chg set): the candidate rows over the missions
+// the refresh recorded, and the column of the base the move closed.
+bool swap_delta_fits(int K);
+constexpr size_t kIncrementalMinTableBytes = 256ull << 20;   // candidate rows x missions, int32
+cudaError_t launch_swap_delta(const TabuBuffers &w, cudaStream_t s);
+// The B x M_pad table copied mission-major (M_pad x ldT, ldT = B rounded up to 32).
+int table_ldT(int B);
+cudaError_t launch_transpose_table(const int32_t *cost, int B, int M_pad, int32_t *costT, cudaStream_t s);
+cudaError_t launch_swap_row(const TabuBuffers &w, const int32_t *cost, cudaStream_t s);
 cudaError_t launch_export_best_two(const TabuBuffers &w, const int *perm, int32_t *a, int32_t *b,
                                    int32_t *b1, int32_t *b2, cudaStream_t s);
 // mission order (Morton order of pickup/drop-off midpoints) and readback in caller order

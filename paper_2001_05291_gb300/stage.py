@@ -23,7 +23,7 @@ LIB_PATH = os.path.join(_PKG, "_lib", "libstage.so")
 STAGE_OK, STAGE_PENDING = 0, 1
 ERRORS = {-1: "INVALID_ARG", -2: "OUT_OF_RANGE", -3: "NO_MEMORY", -4: "ADMISSION", -5: "TIMEOUT",
           -6: "CUDA", -7: "INTERNAL", -8: "NOT_FOUND"}
-STAGE_THREADSAFE, STAGE_PROFILE, STAGE_AUTOTUNE = 1, 2, 4
+STAGE_THREADSAFE, STAGE_PROFILE, STAGE_AUTOTUNE, STAGE_FULL_PASS, STAGE_INCREMENTAL = 1, 2, 4, 8, 16
 STAGE_DESC_DEVICE, STAGE_DESC_HAVERSINE = 1, 2
 MOVE_FALLBACK, MOVE_ASPIRATION, MOVE_NEW_BEST = 1, 2, 4
 MAX_COORD, MAX_BASES, MAX_MISSIONS, MAX_K = 1 << 24, 65535, 1 << 24, 1024
@@ -244,12 +244,14 @@ class Context:
 
     def __init__(self, device: int = 0, profile: bool = False, threadsafe: bool = False,
                  hbm_budget: int = 0, max_slots: int = 0, spin_limit: int = 0,
-                 torch_memory: bool = True, stream=None, autotune: bool = False):
+                 torch_memory: bool = True, stream=None, autotune: bool = False, full_pass: bool = False,
+                 incremental: bool = False):
         L = lib()
         cfg = StageConfig()
         cfg.device = device
         cfg.flags = ((STAGE_PROFILE if profile else 0) | (STAGE_THREADSAFE if threadsafe else 0) |
-                     (STAGE_AUTOTUNE if autotune else 0))
+                     (STAGE_AUTOTUNE if autotune else 0) | (STAGE_FULL_PASS if full_pass else 0) |
+                     (STAGE_INCREMENTAL if incremental else 0))
         cfg.hbm_budget_bytes = hbm_budget
         cfg.max_slots = max_slots
         cfg.spin_limit = spin_limit

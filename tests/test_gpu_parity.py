@@ -370,3 +370,75 @@ def test_graph_replay_and_small_block_paths():
             assert [tuple(m) for m in got.moves] == [tuple(m) for m in want.moves]
             assert (got.best_cov, got.best_dist, got.best_iter) == (want.best_cov, want.best_dist, want.best_iter)
             c2.unload_instance(h)
+
+
+def test_incremental_equals_full_pass():
+    """STAGE_INCREMENTAL (the default for tables well beyond L2) keeps the
+    neighbourhood's gain and extra terms across iterations and updates them from
+    the missions whose best / second best changed and from the closed base's
+    column; STAGE_FULL_PASS re-evaluates the whole table every iteration.  Graph
+    replay and per-kernel launches of the incremental form, and the full pass,
+    all equal the oracle's trajectory: several K (1 to 64), unavailable bases, a
+    start placement, the improving-only rule, R below most costs and R near
+    INT32_MAX."""
+    from paper_2001_05291_gb300 import stage
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    cases = [(small(71, 70, 12000, 8), 120, True, None, None),
+             (small(72, 110, 24000, 17, R=150_000), 50, True, None, None),
+             (small(73, 45, 20000, 1), 40, True, None, None),
+             (small(74, 60, 9000, 5), 80, False, [3, 7, 20, 41], None),
+             (small(75, 50, 8000, 6, R=2**31 - 2), 30, True, None, None),
+             (small(76, 300, 5000, 64), 25, True, None, np.arange(64, dtype=np.int32) * 4)]
+    with stage.Context(device=0, incremental=True) as ci, stage.Context(device=0, profile=True, incremental=True) as cp, \
+            stage.Context(device=0, full_pass=True) as cf:
+        for inst, iters, aw, unavail, start in cases:
+            avail = None
+            if unavail is not None:
+                avail = np.ones(inst.B, dtype=np.uint8)
+                avail[unavail] = 0
+            cost = oracle_table(inst)
+            okw = {"start_open": start} if start is not None else {}
+            want = oracle.tabu(cost, inst.K, inst.R, iters, inst.tenure, avail=avail, accept_worsening=aw,
+                               nthreads=8, **okw)
+            for c in (ci, cp, cf):
+                h = load(c, inst, avail)
+                got = c.tabu_run(h, inst.K, inst.R, iters, inst.tenure, accept_worsening=aw, **okw)
+                assert [tuple(m) for m in got.moves] == [tuple(m) for m in want.moves]
+                assert (got.best_cov, got.best_dist, got.best_iter) == (want.best_cov, want.best_dist,
+                                                                        want.best_iter)
+                assert (got.final_cov, got.final_dist) == (want.final_cov, want.final_dist)
+                c.unload_instance(h)
+        assert cp.kernel_stats("swap_delta")[0] > 0 and cp.kernel_stats("swap_row")[0] > 0
+        assert cf.kernel_stats("swap_delta")[0] == 0
+
+
+def test_incremental_edge_cases_and_resume():
+    """The incremental form on the edge cases of the Tabu tests (K = 1, K = B - 1,
+    tenure 0, improving-only, M = 3) and across a resume, on its per-kernel and
+    graph-replay paths."""
+    from paper_2001_05291_gb300 import stage
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    with stage.Context(device=0, profile=True, incremental=True) as cp, \
+            stage.Context(device=0, incremental=True) as cg:
+        for B, M, K, tenure, aw in [(20, 200, 1, 2, True), (15, 777, 14, 3, True), (30, 20000, 5, 0, True),
+                                    (30, 2051, 5, 6, False), (48, 17000, 9, 4, True), (8, 3, 3, 2, True)]:
+            inst = small(B + 1000 * K + M, B, M, K)
+            cost = oracle_table(inst)
+            for c in (cp, cg):
+                h = load(c, inst)
+                check_tabu(c, h, cost, K, inst.R, 60, tenure, accept_worsening=aw)
+                c.unload_instance(h)
+        inst = small(31, 40, 8000, 7)
+        for c in (cp, cg):
+            h = load(c, inst)
+            full = c.tabu_run(h, 7, inst.R, 40, 5)
+            first = c.tabu_run(h, 7, inst.R, 17, 5, end_state=True, B=inst.B)
+            second = c.tabu_run(h, 7, inst.R, 23, 5, resume=first.end_state)
+            assert [tuple(m) for m in first.moves + second.moves] == [tuple(m) for m in full.moves]
+            assert (second.best_cov, second.best_dist, second.best_iter) == (full.best_cov, full.best_dist,
+                                                                             full.best_iter)
+            c.unload_instance(h)
