@@ -57,6 +57,8 @@ def parse_args():
     ap.add_argument("--missions", type=int, default=0,
                     help="override M of the large workload (smaller profiling cases)")
     ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--full-pass-iters", type=int, default=200,
+                    help="large: Tabu iterations of the full-pass reference run (0: skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-missions", type=int, default=100_000)
     ap.add_argument("--cpu-budget-s", type=float, default=15.0)
@@ -213,7 +215,8 @@ def config_of(inst):
                         f"K={inst.K}, R={inst.R} m, {inst.iters} Tabu iterations, tenure {inst.tenure}",
             "B": inst.B, "M": inst.M, "K": inst.K, "R": inst.R, "iters": inst.iters,
             "tenure": inst.tenure, "instance_digest": inst.digest(),
-            "l2": "inputs larger than L2 (table streamed every iteration)" if inst.B * inst.M * 4 > 256e6
+            "l2": "inputs larger than L2 (the B x M table and its mission-major copy, 8 GB each at the full "
+                  "size; no flush)" if inst.B * inst.M * 4 > 256e6
                   else "L2-resident table (no flush between iterations)"}
 
 
@@ -223,6 +226,23 @@ def config_of(inst):
 DELTA_BYTES_PER_RECORD = 32
 KERNELS = ("table", "order", "rowsum", "topk", "init", "begin", "transpose", "swap_eval", "select", "refresh",
            "swap_delta", "swap_row", "evaluate", "tabu_small", "autotune", "update")
+
+
+def stored_traffic(fname, inst, args):
+    """DRAM bytes per launch from a committed ncu summary under profiles/, only
+    while the kernel source is the one measured and the workload the full one."""
+    prof = os.path.join(ROOT, "profiles", fname)
+    if not os.path.exists(prof) or args.missions:
+        return None
+    fields = {}
+    with open(prof) as fh:
+        for line in fh:
+            if ":" in line and not line.startswith((" ", "#")):
+                k, v = line.split(":", 1)
+                fields[k.strip()] = v.strip()
+    if fields.get("workload") == inst.name and fields.get("kernel_source_digest") == kernel_digest():
+        return float(fields["traffic_bytes_per_launch"])
+    return None
 
 
 def run_ours(args):
@@ -304,17 +324,9 @@ def run_ours(args):
                  "records_fraction": rec_per_launch / inst.M}
     # DRAM traffic per launch from the committed ncu summary, only while the
     # kernel source is the one that was measured and the workload is the full one
-    traffic = None
-    prof = os.path.join(ROOT, "profiles", "swap_eval_traffic.md")
-    if os.path.exists(prof) and not args.missions:
-        fields = {}
-        with open(prof) as fh:
-            for line in fh:
-                if ":" in line and not line.startswith((" ", "#")):
-                    k, v = line.split(":", 1)
-                    fields[k.strip()] = v.strip()
-        if fields.get("workload") == inst.name and fields.get("kernel_source_digest") == kernel_digest():
-            traffic = float(fields["traffic_bytes_per_launch"])
+    traffic = stored_traffic("swap_eval_traffic.md", inst, args)
+    if delta:
+        delta["traffic"] = stored_traffic("swap_delta_traffic.md", inst, args)
 
     # end to end: host (pinned) buffers through the public API
     pinned = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
@@ -336,6 +348,32 @@ def run_ours(args):
                "h2d_bytes_per_step": 8 * inst.B + 16 * inst.M,
                "d2h_bytes_per_step": 32 * inst.iters + 8 * inst.K + 48,
                "steps": args.e2e_steps, "ms_per_step": 1000 * e2e_s / args.e2e_steps}
+
+    # the same search re-evaluating the whole neighbourhood by a full pass over
+    # the table every iteration (STAGE_FULL_PASS): the streaming kernel's
+    # roofline, and the iteration rate the incremental form is compared with
+    full_pass = None
+    if profile and args.full_pass_iters > 0:
+        with stage.Context(device=local, profile=True, full_pass=True) as fctx:
+            hf = fctx.load_instance(*dev, haversine=geo)
+            fctx.tabu_run(hf, inst.K, inst.R, 20, inst.tenure)
+            fctx.reset_stats()
+            torch.cuda.synchronize()
+            f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            f0.record(fctx.torch_stream)
+            fr = fctx.tabu_run(hf, inst.K, inst.R, args.full_pass_iters, inst.tenure)
+            f1.record(fctx.torch_stream)
+            f1.synchronize()
+            f_ms = f0.elapsed_time(f1)
+            fn, fms = fctx.kernel_stats("swap_eval")
+            fctx.unload_instance(hf)
+        f_avg_s = fms / fn / 1000.0
+        full_pass = {"tabu_iters_per_s": fr.n_moves / (f_ms / 1000.0), "iterations": fr.n_moves,
+                     "roofline": {"bound": "hbm", "kernel": "swap_eval", "achieved": alg_bytes / f_avg_s / 1e9,
+                                  "peak": peak, "peak_source": peak_src, "unit": "GB/s",
+                                  "frac": alg_bytes / f_avg_s / 1e9 / peak, "traffic": traffic,
+                                  "algorithmic_bytes_per_launch": alg_bytes, "avg_launch_ms": f_avg_s * 1000.0,
+                                  "launches": fn}}
 
     # latency-bound workloads: the search alone on a loaded instance (the step
     # above also pays loading, ordering and ranking)
@@ -386,11 +424,7 @@ def run_ours(args):
                            "peak_source": peak_src, "unit": "GB/s", "frac": achieved / peak,
                            "traffic": traffic, "algorithmic_bytes_per_launch": alg_bytes,
                            "avg_launch_ms": avg_sw_s * 1000.0, "launches": n_sw}) if profile else None),
-            "roofline_full_pass": ({"bound": "hbm", "kernel": "swap_eval", "achieved": achieved, "peak": peak,
-                                    "peak_source": peak_src, "unit": "GB/s", "frac": achieved / peak,
-                                    "traffic": traffic, "algorithmic_bytes_per_launch": alg_bytes,
-                                    "avg_launch_ms": avg_sw_s * 1000.0, "launches": n_sw}
-                                   if profile and n_sw else None),
+            "full_pass": full_pass,
             "kernels_ms": {k: {"launches": n, "total_ms": round(t, 3)} for k, (n, t) in stats.items() if n},
             "gpu_launches": launches,
             "e2e": e2e,

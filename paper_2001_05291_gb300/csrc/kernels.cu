@@ -2086,14 +2086,16 @@ __device__ __forceinline__ void delta_run_add(DeltaRun &run, int s, int c, int d
     run.d += d;
 }
 
-// Thread = one base j (every base but the one the move closed: a column
-// that is not a candidate's is never read, and is rebuilt by k_swap_row
-// when its base closes); the block walks chunks of the record list, staged
-// in shared memory, and reads each recorded mission's costs from the
-// mission-major copy of the table, so a warp reads 32 consecutive bases of
-// one mission (one 128-byte line).  The gain terms of the row add up in
-// registers; the extra terms go out in runs of one slot (the records come in
-// runs of neighbouring missions, which share slots).
+// Thread = one position p of the mission-major copy, i.e. base border[p]
+// (every base but the one the move closed: a column that is not a
+// candidate's is never read, and is rebuilt by k_swap_row when its base
+// closes); the block walks chunks of the record list, staged in shared
+// memory, and a warp reads 32 consecutive positions of one mission (one
+// 128-byte line).  The positions follow a spatial order of the bases, so the
+// few bases near enough to a mission to carry a term sit in few warps and
+// the others pass the mission together.  The gain terms of the base add up
+// in registers; the extra terms go out in runs of one slot (the records come
+// in runs of neighbouring missions, which share slots).
 __global__ void __launch_bounds__(kDeltaRows) k_swap_delta(TabuBuffers w)
 {
     TabuDevState *st = w.st;
@@ -2102,9 +2104,10 @@ __global__ void __launch_bounds__(kDeltaRows) k_swap_delta(TabuBuffers w)
     __shared__ int4 s_new[kDeltaChunk];   // clamped a, clamped b, best slot: after
     const int ic = st->mv_i, R = w.R;
     const int nrec = min(st->chg_n, w.M);
-    const int j = blockIdx.x * kDeltaRows + (int)threadIdx.x;
-    const bool row = j < w.B && j != ic;   // the closed base's column: k_swap_row
-    const int32_t *colp = w.costT + (row ? j : 0);
+    const int p = blockIdx.x * kDeltaRows + (int)threadIdx.x;
+    const int j = p < w.ldT ? w.border[p] : -1;
+    const bool row = j >= 0 && j != ic;   // the closed base's column: k_swap_row
+    const int32_t *colp = w.costT + (row ? p : 0);
     const size_t ld = (size_t)w.ldT;
     long long gc = 0, gd = 0;
     DeltaRun rn{-1, 0, 0}, ro{-1, 0, 0};   // the new state's terms, the old state's (taken out)
@@ -2153,7 +2156,7 @@ __global__ void __launch_bounds__(kDeltaRows) k_swap_delta(TabuBuffers w)
 
 cudaError_t launch_swap_delta(const TabuBuffers &w, cudaStream_t s)
 {
-    const int gx = (w.B + kDeltaRows - 1) / kDeltaRows;
+    const int gx = (w.ldT + kDeltaRows - 1) / kDeltaRows;
     // about two waves of resident blocks over the record chunks (their count
     // is known only on the device), no more than the missions could fill
     const int sms = g_num_sms > 0 ? g_num_sms : 152;
@@ -2167,16 +2170,18 @@ cudaError_t launch_swap_delta(const TabuBuffers &w, cudaStream_t s)
 
 int table_ldT(int B) { return (B + 31) / 32 * 32; }
 
-// Tiled transpose through shared memory: reads and writes both coalesced.
-__global__ void __launch_bounds__(256) k_transpose_table(const int32_t *__restrict__ cost, int B, int M_pad, int ldT,
+// Tiled transpose through shared memory: reads and writes both coalesced;
+// position p of a mission's row holds base border[p].
+__global__ void __launch_bounds__(256) k_transpose_table(const int32_t *__restrict__ cost, int M_pad, int ldT,
+                                                         const int32_t *__restrict__ border,
                                                          int32_t *__restrict__ costT)
 {
     __shared__ int32_t tile[32][33];
     const int m0 = blockIdx.x * 32, b0 = blockIdx.y * 32;
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8
     for (int k = ty; k < 32; k += 8) {
-        const int b = b0 + k, m = m0 + tx;
-        tile[k][tx] = (b < B && m < M_pad) ? cost[(size_t)b * M_pad + m] : INT_MAX;
+        const int b = border[b0 + k], m = m0 + tx;
+        tile[k][tx] = (b >= 0 && m < M_pad) ? cost[(size_t)b * M_pad + m] : INT_MAX;
     }
     __syncthreads();
     for (int k = ty; k < 32; k += 8) {
@@ -2185,10 +2190,11 @@ __global__ void __launch_bounds__(256) k_transpose_table(const int32_t *__restri
     }
 }
 
-cudaError_t launch_transpose_table(const int32_t *cost, int B, int M_pad, int32_t *costT, cudaStream_t s)
+cudaError_t launch_transpose_table(const int32_t *cost, int B, int M_pad, const int32_t *border, int32_t *costT,
+                                   cudaStream_t s)
 {
     const int ldT = table_ldT(B);
-    k_transpose_table<<<dim3((M_pad + 31) / 32, ldT / 32), 256, 0, s>>>(cost, B, M_pad, ldT, costT);
+    k_transpose_table<<<dim3((M_pad + 31) / 32, ldT / 32), 256, 0, s>>>(cost, M_pad, ldT, border, costT);
     return cudaGetLastError();
 }
 

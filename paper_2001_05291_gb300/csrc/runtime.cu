@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <climits>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -380,6 +381,37 @@ stage_status autotune_shape(stage_ctx *c, Instance *in, const int32_t *open, int
     return STAGE_OK;
 }
 
+// Positions of the bases in the mission-major table copy: Morton order of
+// their coordinates (16 bits per axis over the bounding box), ties by id;
+// positions past B hold -1.
+std::vector<int32_t> spatial_order(const std::vector<int2> &xy, int ld)
+{
+    const int B = (int)xy.size();
+    long long x0 = LLONG_MAX, y0 = LLONG_MAX, x1 = LLONG_MIN, y1 = LLONG_MIN;
+    for (const int2 &q : xy) {
+        x0 = std::min<long long>(x0, q.x); x1 = std::max<long long>(x1, q.x);
+        y0 = std::min<long long>(y0, q.y); y1 = std::max<long long>(y1, q.y);
+    }
+    auto spread16 = [](uint32_t v) {
+        v &= 0xffffu;
+        v = (v | (v << 8)) & 0x00ff00ffu;
+        v = (v | (v << 4)) & 0x0f0f0f0fu;
+        v = (v | (v << 2)) & 0x33333333u;
+        v = (v | (v << 1)) & 0x55555555u;
+        return v;
+    };
+    std::vector<std::pair<uint32_t, int32_t>> key(B);
+    for (int b = 0; b < B; b++) {
+        const uint32_t qx = (uint32_t)(((long long)xy[b].x - x0) * 65535 / std::max(1ll, x1 - x0));
+        const uint32_t qy = (uint32_t)(((long long)xy[b].y - y0) * 65535 / std::max(1ll, y1 - y0));
+        key[b] = {spread16(qx) | (spread16(qy) << 1), b};
+    }
+    std::sort(key.begin(), key.end());
+    std::vector<int32_t> order(ld, -1);
+    for (int p = 0; p < B; p++) order[p] = key[p].second;
+    return order;
+}
+
 stage_status run_tabu(stage_ctx *c, Instance *in, const stage_tabu_params *p,
                       stage_tabu_result *res, stage_move *traj, int32_t *exp_a, int32_t *exp_b,
                       int32_t *exp_b1, int32_t *exp_b2)
@@ -457,7 +489,7 @@ stage_status run_tabu(stage_ctx *c, Instance *in, const stage_tabu_params *p,
         // room for them (the context's HBM budget) the search takes the full pass
         const int ldT = table_ldT(in->B);
         const size_t need = (size_t)in->M_pad * 2 * sizeof(int4);
-        const size_t needT = (size_t)in->M_pad * ldT * sizeof(int32_t);
+        const size_t needT = (size_t)in->M_pad * ldT * sizeof(int32_t) + (size_t)ldT * sizeof(int32_t);
         if (!in->mem_chg.p || in->mem_chg.bytes < need) {
             dev_free(c, in->mem_chg);
             if (dev_alloc(c, need, in->mem_chg) != STAGE_OK) {
@@ -474,10 +506,22 @@ stage_status run_tabu(stage_ctx *c, Instance *in, const stage_tabu_params *p,
                 }
             }
             if (inc) {
+                // bases in Morton order of their coordinates (either metric:
+                // planar metres or latitude / longitude), so that bases near
+                // one another take neighbouring positions
+                std::vector<int2> bxy(in->B);
+                CK(cudaMemcpyAsync(bxy.data(), in->base, (size_t)in->B * sizeof(int2), cudaMemcpyDeviceToHost,
+                                   c->stream));
+                CK(cudaStreamSynchronize(c->stream));
+                std::vector<int32_t> border = spatial_order(bxy, ldT);
+                int32_t *costT = static_cast<int32_t *>(in->mem_costT.p);
+                int32_t *d_border = costT + (size_t)in->M_pad * ldT;
+                CK(cudaMemcpyAsync(d_border, border.data(), (size_t)ldT * sizeof(int32_t), cudaMemcpyHostToDevice,
+                                   c->stream));
                 CK(timed(c, "transpose", 1, [&] {
-                    return launch_transpose_table(in->cost, in->B, in->M_pad,
-                                                  static_cast<int32_t *>(in->mem_costT.p), c->stream);
+                    return launch_transpose_table(in->cost, in->B, in->M_pad, d_border, costT, c->stream);
                 }));
+                CK(cudaStreamSynchronize(c->stream));   // the host order vector goes out of scope
                 in->ldT = ldT;
                 in->costT_ok = true;
             }
@@ -485,6 +529,7 @@ stage_status run_tabu(stage_ctx *c, Instance *in, const stage_tabu_params *p,
         if (inc) {
             tw.chg = static_cast<int4 *>(in->mem_chg.p);
             tw.costT = static_cast<const int32_t *>(in->mem_costT.p);
+            tw.border = tw.costT + (size_t)in->M_pad * in->ldT;
             tw.ldT = in->ldT;
         }
     }

@@ -86,8 +86,10 @@ struct TabuBuffers {
     // kept across iterations and updated from these records.  NULL = the
     // refresh clears the terms and a full pass rebuilds them every iteration.
     int4 *chg;
-    // incremental neighbourhood: the cost table mission-major, costT[m * ldT + j]
+    // incremental neighbourhood: the cost table mission-major with the bases
+    // in a spatial order, costT[m * ldT + p] = cost of base border[p] for m
     const int32_t *costT;
+    const int32_t *border;   // [ldT] position -> base id (-1 past B)
     int ldT;
 };
 
@@ -121,9 +123,11 @@ cudaError_t launch_refresh(const TabuBuffers &w, const int32_t *cost, cudaStream
 bool swap_delta_fits(int K);
 constexpr size_t kIncrementalMinTableBytes = 256ull << 20;   // candidate rows x missions, int32
 cudaError_t launch_swap_delta(const TabuBuffers &w, cudaStream_t s);
-// The B x M_pad table copied mission-major (M_pad x ldT, ldT = B rounded up to 32).
+// The B x M_pad table copied mission-major (M_pad x ldT, ldT = B rounded up to
+// 32), the bases in the order border (position -> base id, -1 past B).
 int table_ldT(int B);
-cudaError_t launch_transpose_table(const int32_t *cost, int B, int M_pad, int32_t *costT, cudaStream_t s);
+cudaError_t launch_transpose_table(const int32_t *cost, int B, int M_pad, const int32_t *border, int32_t *costT,
+                                   cudaStream_t s);
 cudaError_t launch_swap_row(const TabuBuffers &w, const int32_t *cost, cudaStream_t s);
 cudaError_t launch_export_best_two(const TabuBuffers &w, const int *perm, int32_t *a, int32_t *b,
                                    int32_t *b1, int32_t *b2, cudaStream_t s);
