@@ -225,7 +225,7 @@ def config_of(inst):
 # the mission-major copy of the table
 DELTA_BYTES_PER_RECORD = 32
 KERNELS = ("table", "order", "rowsum", "topk", "init", "begin", "transpose", "swap_eval", "select", "refresh",
-           "swap_delta", "swap_row", "evaluate", "tabu_small", "autotune", "update")
+           "swap_delta", "evaluate", "tabu_small", "autotune", "update")
 
 
 def stored_traffic(fname, inst, args):
@@ -402,7 +402,7 @@ def run_ours(args):
             pctx.reset_stats()
             pr = pctx.tabu_run(hp, inst.K, inst.R, inst.iters, inst.tenure)
             dev_ms = sum(pctx.kernel_stats(k)[1] for k in ("tabu_small", "swap_eval", "select", "refresh",
-                                                             "swap_delta", "swap_row"))
+                                                             "swap_delta"))
             pctx.unload_instance(hp)
         search["kernel_ms_per_search"] = dev_ms
         search["kernel_us_per_iteration"] = 1000.0 * dev_ms / max(1, pr.n_moves)

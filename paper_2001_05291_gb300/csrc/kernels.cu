@@ -1726,6 +1726,12 @@ __device__ __forceinline__ void select_apply(const TabuBuffers &w, const MoveKey
                 st->mv_s = P.s; st->mv_i = P.i; st->mv_j = P.j;
                 st->chg_total += st->chg_n;     // the records the last incremental pass took
                 st->chg_n = 0;
+                if (w.chg) {
+                    // the closed base is a candidate again: its column of the
+                    // terms is rebuilt from zero by the refresh
+                    w.gain_c[P.i] = 0;
+                    w.gain_d[P.i] = 0;
+                }
                 w.v0[0] = 0;
                 w.v0[1] = 0;
             }
@@ -1733,10 +1739,15 @@ __device__ __forceinline__ void select_apply(const TabuBuffers &w, const MoveKey
     }
     __syncthreads();
     if (st->done) return;
+    const int ic = st->mv_i;
     for (int k = threadIdx.x; k < w.K; k += blockDim.x) {
         w.loss_c[k] = 0;
         w.loss_d[k] = 0;
         if (s_newbest) w.best_open[k] = w.open[k];
+        if (w.chg) {
+            w.extra_c[(size_t)k * w.B + ic] = 0;
+            w.extra_d[(size_t)k * w.B + ic] = 0;
+        }
     }
 }
 
@@ -1811,6 +1822,10 @@ cudaError_t launch_select(const TabuBuffers &w, int nC, cudaStream_t s)
 
 constexpr int kRefQ = 2048;   // missions queued for a cooperative rescan per block
 
+// Dynamic shared memory of the refresh: per slot the loss (distance, count),
+// the closed base's column terms (distance, count) and the base id.
+size_t refresh_smem(int K) { return (size_t)K * (8 + 8 + 4 + 4 + 4); }
+
 // Whether a mission's terms in the swap neighbourhood changed: they depend on
 // its clamped best and second-best costs and, while it is covered, on its
 // best slot (an uncovered mission adds no extra term to any slot).
@@ -1840,6 +1855,27 @@ __device__ __forceinline__ void record_changes(const TabuBuffers &w, bool ch, in
     }
 }
 
+// A mission's terms in the column of a base x away (the closed base, a
+// candidate again), for its state after the move: the gain term into
+// (gc, gd), the extra term at its best slot into the block's accumulators.
+__device__ __forceinline__ void closed_column_terms(int x, int a, int b, int s1, int R, long long &gc, long long &gd,
+                                                    int *s_ic, unsigned long long *s_id)
+{
+    const int a1 = min(a, R + 1), b1 = min(b, R + 1);
+    if (x >= b1) return;   // a <= b
+    const int ca = a1 <= R, cb = b1 <= R;
+    const int dc = ca - cb;
+    const long long dd = (ca ? (long long)max(x, a1) : 0ll) - (cb ? (long long)b1 : 0ll);
+    if (dc | (dd != 0)) {
+        atomicAdd(&s_ic[s1], dc);
+        atomicAdd(&s_id[s1], (unsigned long long)dd);
+    }
+    if (x < a1) {
+        gc += 1 - ca;
+        gd += (long long)x - (ca ? (long long)a1 : 0ll);
+    }
+}
+
 // Best and second-best open base of the missions queued for a rescan (their
 // best or second best was the closed base), G threads per mission with G
 // chosen from the queue length so that a short queue still has every thread
@@ -1849,7 +1885,9 @@ __device__ __forceinline__ void record_changes(const TabuBuffers &w, bool ch, in
 // loss of its best slot) are added as mission_terms adds them.
 __device__ __forceinline__ void refresh_rescans(const TabuBuffers &w, const int32_t *__restrict__ cost,
                                                 const int *s_open, const int *s_q, int nq, int *s_lc,
-                                                unsigned long long *s_ld, long long &v0c, long long &v0d)
+                                                unsigned long long *s_ld, long long &v0c, long long &v0d,
+                                                const int32_t *rowi, long long &gic, long long &gid, int *s_ic,
+                                                unsigned long long *s_id)
 {
     constexpr int L = 8;
     const unsigned full = 0xffffffffu;
@@ -1864,9 +1902,10 @@ __device__ __forceinline__ void refresh_rescans(const TabuBuffers &w, const int3
         const int m = has ? s_q[qi] : 0;
         unsigned long long e1 = ~0ull, e2 = ~0ull;
         int k1 = -1, k2 = -1;
-        int ao = 0, bo = 0, so = 0;   // the state before the move (recorded if it changes)
+        int ao = 0, bo = 0, so = 0, xi = 0;   // the state before the move (recorded if it changes)
         if (has && sub == 0 && w.chg) {
             ao = w.a[m]; bo = w.b[m]; so = w.s1[m];
+            xi = __ldcs(rowi + m);
         }
         if (has) {
             for (int k0 = sub; k0 < K; k0 += L * G) {
@@ -1908,6 +1947,7 @@ __device__ __forceinline__ void refresh_rescans(const TabuBuffers &w, const int3
         if (lead) {
             w.a[m] = a; w.b[m] = b; w.s1[m] = (int16_t)k1; w.s2[m] = (int16_t)k2;
             mission_terms(a, b, w.R, v0c, v0d, s_lc, s_ld, k1);
+            if (w.chg) closed_column_terms(xi, a, b, k1, w.R, gic, gid, s_ic, s_id);
         }
         if (w.chg) record_changes(w, lead && terms_changed(ao, bo, so, a, b, k1, w.R), m, ao, bo, so, a, b, k1);
     }
@@ -1944,18 +1984,27 @@ __device__ __forceinline__ void refresh_body(const TabuBuffers &w, const int32_t
     __shared__ int s_q[kRefQ];
     __shared__ int s_qn;
     unsigned long long *s_ld = sm_ref;
-    int *s_lc = reinterpret_cast<int *>(s_ld + w.K);
-    int *s_open = s_lc + w.K;
+    unsigned long long *s_id = s_ld + w.K;                     // closed base's column: extra, distance
+    int *s_lc = reinterpret_cast<int *>(s_id + w.K);
+    int *s_ic = s_lc + w.K;                                    // closed base's column: extra, count
+    int *s_open = s_ic + w.K;
     for (int k = threadIdx.x; k < w.K; k += blockDim.x) {
         s_open[k] = w.open[k];
         s_lc[k] = 0;
         s_ld[k] = 0;
+        s_ic[k] = 0;
+        s_id[k] = 0;
     }
     if (threadIdx.x == 0) s_qn = 0;
     __syncthreads();
-    const int ss = st->mv_s, jj = st->mv_j;
+    const int ss = st->mv_s, jj = st->mv_j, ic = st->mv_i;
     const size_t M_pad = w.M_pad;
     const int32_t *rowj = cost + (size_t)jj * M_pad;
+    // incremental form: the closed base is a candidate again, its column of
+    // the terms (zeroed with the move) is rebuilt here over every mission
+    const bool inc = w.chg != nullptr;
+    const int32_t *rowi = cost + (size_t)ic * M_pad;
+    long long gic = 0, gid = 0;
     long long v0c = 0, v0d = 0;
     const int base = bid * (int)blockDim.x, stride = nb * (int)blockDim.x;
     const int rounds = w.M > base ? (w.M - base + stride - 1) / stride : 0;   // the same on every thread
@@ -1963,12 +2012,13 @@ __device__ __forceinline__ void refresh_body(const TabuBuffers &w, const int32_t
     const int lane = threadIdx.x & 31;
     for (int rd = 0; rd < rounds; rd++) {
         const int m = base + rd * stride + (int)threadIdx.x;
-        int a = 0, b = 0, k1 = 0, k2 = 0, x = 0;
+        int a = 0, b = 0, k1 = 0, k2 = 0, x = 0, xi = 0;
         bool in = m < w.M;
         if (in) {
             a = w.a[m]; b = w.b[m];
             k1 = w.s1[m]; k2 = w.s2[m];
             x = __ldcs(rowj + m);
+            if (inc) xi = __ldcs(rowi + m);
             if (w.mask) in = w.mask[m] != 0;
         }
         bool term = false;
@@ -2007,22 +2057,26 @@ __device__ __forceinline__ void refresh_body(const TabuBuffers &w, const int32_t
                 }
             }
         }
-        if (term) mission_terms(a, b, w.R, v0c, v0d, s_lc, s_ld, k1);
-        if (w.chg) record_changes(w, term && terms_changed(ao, bo, so, a, b, k1, w.R), m, ao, bo, so, a, b, k1);
+        if (term) {
+            mission_terms(a, b, w.R, v0c, v0d, s_lc, s_ld, k1);
+            if (inc) closed_column_terms(xi, a, b, k1, w.R, gic, gid, s_ic, s_id);
+        }
+        if (inc) record_changes(w, term && terms_changed(ao, bo, so, a, b, k1, w.R), m, ao, bo, so, a, b, k1);
     }
     __syncthreads();
     const int nq = min(s_qn, kRefQ);   // no thread changes the count after the barrier
-    if (nq > 0) refresh_rescans(w, cost, s_open, s_q, nq, s_lc, s_ld, v0c, v0d);
-    if (w.chg) {
-        // the terms stay; the closed base is a candidate again and its column
-        // is rebuilt from zero (k_swap_row)
-        if (bid == 0) {
-            const int ic = st->mv_i;
-            for (int k = threadIdx.x; k < w.K; k += blockDim.x) {
-                w.extra_c[(size_t)k * w.B + ic] = 0;
-                w.extra_d[(size_t)k * w.B + ic] = 0;
-            }
-            if (threadIdx.x == 0) { w.gain_c[ic] = 0; w.gain_d[ic] = 0; }
+    if (nq > 0) refresh_rescans(w, cost, s_open, s_q, nq, s_lc, s_ld, v0c, v0d, rowi, gic, gid, s_ic, s_id);
+    if (inc) {
+        // the other terms stay; the closed base's column goes out
+        block_sum2<256>(gic, gid);
+        if (threadIdx.x == 0) {
+            if (gic) atomicAdd(&w.gain_c[ic], (int)gic);
+            if (gid) atomicAdd(&w.gain_d[ic], (unsigned long long)gid);
+        }
+        __syncthreads();
+        for (int k = threadIdx.x; k < w.K; k += blockDim.x) {
+            if (s_ic[k]) atomicAdd(&w.extra_c[(size_t)k * w.B + ic], s_ic[k]);
+            if (s_id[k]) atomicAdd(&w.extra_d[(size_t)k * w.B + ic], s_id[k]);
         }
     } else {
         // clear the neighbourhood accumulators for the next full evaluation
@@ -2043,7 +2097,7 @@ __global__ void __launch_bounds__(256, 4) k_refresh(TabuBuffers w, const int32_t
 
 cudaError_t launch_refresh(const TabuBuffers &w, const int32_t *cost, cudaStream_t s)
 {
-    size_t sm = (size_t)w.K * (8 + 4 + 4);
+    const size_t sm = refresh_smem(w.K);
     k_refresh<<<grid_missions(w.M_pad), 256, sm, s>>>(w, cost);
     return cudaGetLastError();
 }
@@ -2054,8 +2108,8 @@ cudaError_t launch_refresh(const TabuBuffers &w, const int32_t *cost, cudaStream
 // best / second-best cost or best slot changed (recorded by the refresh) and
 // through the closed base, which is a candidate again.  k_swap_delta takes
 // each recorded mission's old terms out of, and its new terms into, every
-// other candidate row; k_swap_row rebuilds the closed base's column over all
-// missions.  Afterwards gain and extra equal what a full pass over the table
+// other base's column; the refresh rebuilds the closed base's column over
+// all missions.  Afterwards gain and extra equal what a full pass over the table
 // would give for the new placement (integer sums: exactly), so the
 // selection still scores every swap of the neighbourhood.
 // --------------------------------------------------------------------------
@@ -2088,7 +2142,7 @@ __device__ __forceinline__ void delta_run_add(DeltaRun &run, int s, int c, int d
 
 // Thread = one position p of the mission-major copy, i.e. base border[p]
 // (every base but the one the move closed: a column that is not a
-// candidate's is never read, and is rebuilt by k_swap_row when its base
+// candidate's is never read, and is rebuilt by the refresh when its base
 // closes); the block walks chunks of the record list, staged in shared
 // memory, and a warp reads 32 consecutive positions of one mission (one
 // 128-byte line).  The positions follow a spatial order of the bases, so the
@@ -2102,11 +2156,13 @@ __global__ void __launch_bounds__(kDeltaRows) k_swap_delta(TabuBuffers w)
     if (st->done || st->ls_hold) return;
     __shared__ int4 s_old[kDeltaChunk];   // column, clamped a, clamped b, best slot: before the move
     __shared__ int4 s_new[kDeltaChunk];   // clamped a, clamped b, best slot: after
+    __shared__ long long s_off[kDeltaChunk];   // the mission's row in the mission-major copy
+    __shared__ int s_hi[kDeltaChunk];          // the larger clamped second best: no term from x >= it
     const int ic = st->mv_i, R = w.R;
     const int nrec = min(st->chg_n, w.M);
     const int p = blockIdx.x * kDeltaRows + (int)threadIdx.x;
     const int j = p < w.ldT ? w.border[p] : -1;
-    const bool row = j >= 0 && j != ic;   // the closed base's column: k_swap_row
+    const bool row = j >= 0 && j != ic;   // the closed base's column: the refresh
     const int32_t *colp = w.costT + (row ? p : 0);
     const size_t ld = (size_t)w.ldT;
     long long gc = 0, gd = 0;
@@ -2116,23 +2172,25 @@ __global__ void __launch_bounds__(kDeltaRows) k_swap_delta(TabuBuffers w)
         __syncthreads();   // the previous chunk is consumed
         if ((int)threadIdx.x < n) {
             const int4 ro = w.chg[2 * (size_t)(e0 + threadIdx.x)], rq = w.chg[2 * (size_t)(e0 + threadIdx.x) + 1];
-            s_old[threadIdx.x] = make_int4(ro.x, min(ro.y, R + 1), min(ro.z, R + 1), ro.w);
-            s_new[threadIdx.x] = make_int4(min(rq.x, R + 1), min(rq.y, R + 1), rq.z, 0);
+            const int bo1 = min(ro.z, R + 1), bn1 = min(rq.y, R + 1);
+            s_old[threadIdx.x] = make_int4(ro.x, min(ro.y, R + 1), bo1, ro.w);
+            s_new[threadIdx.x] = make_int4(min(rq.x, R + 1), bn1, rq.z, 0);
+            s_off[threadIdx.x] = (long long)ro.x * (long long)ld;
+            s_hi[threadIdx.x] = max(bo1, bn1);
         }
         __syncthreads();
         if (!row) continue;
         for (int k0 = 0; k0 < n; k0 += kDeltaBatch) {
             int xv[kDeltaBatch];
 #pragma unroll
-            for (int u = 0; u < kDeltaBatch; u++)
-                xv[u] = k0 + u < n ? __ldg(colp + (size_t)s_old[k0 + u].x * ld) : INT_MAX;
+            for (int u = 0; u < kDeltaBatch; u++) xv[u] = k0 + u < n ? __ldg(colp + s_off[k0 + u]) : INT_MAX;
 #pragma unroll
             for (int u = 0; u < kDeltaBatch; u++) {
                 const int x = xv[u];
                 if (k0 + u >= n) break;
+                if (x >= s_hi[k0 + u]) continue;   // no term in either state (a <= b)
                 const int4 o = s_old[k0 + u], q = s_new[k0 + u];
                 const int ao = o.y, bo = o.z, so = o.w, an = q.x, bn = q.y, sn = q.z;
-                if (x >= bo && x >= bn) continue;   // no term in either state (a <= b)
                 const int cao = ao <= R, cbo = bo <= R, can = an <= R, cbn = bn <= R;
                 if (x < an) { gc += 1 - can; gd += (long long)x - (can ? an : 0); }
                 if (x < ao) { gc -= 1 - cao; gd -= (long long)x - (cao ? ao : 0); }
@@ -2195,56 +2253,6 @@ cudaError_t launch_transpose_table(const int32_t *cost, int B, int M_pad, const 
 {
     const int ldT = table_ldT(B);
     k_transpose_table<<<dim3((M_pad + 31) / 32, ldT / 32), 256, 0, s>>>(cost, M_pad, ldT, border, costT);
-    return cudaGetLastError();
-}
-
-// The closed base's column over every mission, for the new placement.  Its
-// entries were zeroed by the refresh.
-__global__ void __launch_bounds__(256) k_swap_row(TabuBuffers w, const int32_t *__restrict__ cost)
-{
-    TabuDevState *st = w.st;
-    if (st->done || st->ls_hold) return;
-    extern __shared__ unsigned long long sm_row[];
-    unsigned long long *s_ed = sm_row;                        // [K]
-    int *s_ec = reinterpret_cast<int *>(s_ed + w.K);          // [K]
-    for (int k = threadIdx.x; k < w.K; k += blockDim.x) { s_ed[k] = 0; s_ec[k] = 0; }
-    __syncthreads();
-    const int ic = st->mv_i, R = w.R;
-    const int32_t *row = cost + (size_t)ic * w.M_pad;
-    long long gc = 0, gd = 0;
-    for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < w.M; m += gridDim.x * blockDim.x) {
-        const int a = min(w.a[m], R + 1), b = min(w.b[m], R + 1);
-        const int x = __ldcs(row + m);
-        if (x < b) {
-            const int ca = a <= R, cb = b <= R;
-            const int dc = ca - cb;
-            const long long dd = (ca ? (long long)max(x, a) : 0ll) - (cb ? (long long)b : 0ll);
-            if (dc | (dd != 0)) {
-                const int sl = w.s1[m];
-                atomicAdd(&s_ec[sl], dc);
-                atomicAdd(&s_ed[sl], (unsigned long long)dd);
-            }
-            if (x < a) {
-                gc += 1 - ca;
-                gd += (long long)x - (ca ? (long long)a : 0ll);
-            }
-        }
-    }
-    block_sum2<256>(gc, gd);
-    if (threadIdx.x == 0) {
-        if (gc) atomicAdd(&w.gain_c[ic], (int)gc);
-        if (gd) atomicAdd(&w.gain_d[ic], (unsigned long long)gd);
-    }
-    __syncthreads();
-    for (int k = threadIdx.x; k < w.K; k += blockDim.x) {
-        if (s_ec[k]) atomicAdd(&w.extra_c[(size_t)k * w.B + ic], s_ec[k]);
-        if (s_ed[k]) atomicAdd(&w.extra_d[(size_t)k * w.B + ic], s_ed[k]);
-    }
-}
-
-cudaError_t launch_swap_row(const TabuBuffers &w, const int32_t *cost, cudaStream_t s)
-{
-    k_swap_row<<<grid_missions(w.M_pad), 256, (size_t)w.K * 12 + 16, s>>>(w, cost);
     return cudaGetLastError();
 }
 
@@ -2610,7 +2618,7 @@ __global__ void __launch_bounds__(kDirThreads) k_tabu_small(TabuBuffers w, const
 
 cudaError_t launch_tabu_small(const TabuBuffers &w, const int32_t *cost, int iters, cudaStream_t s)
 {
-    const size_t sm = swap_direct_smem(w.K) > (size_t)w.K * 16 ? swap_direct_smem(w.K) : (size_t)w.K * 16;
+    const size_t sm = swap_direct_smem(w.K) > refresh_smem(w.K) ? swap_direct_smem(w.K) : refresh_smem(w.K);
     k_tabu_small<<<1, kDirThreads, sm, s>>>(w, cost, iters);
     return cudaGetLastError();
 }
@@ -3136,7 +3144,7 @@ cudaError_t launch_group_refresh(const GroupSlot *slots, const int2 *map, int to
                                  cudaStream_t s)
 {
     if (total_blocks <= 0) return cudaSuccess;
-    k_group_refresh<<<total_blocks, 256, (size_t)maxK * 16, s>>>(slots, map);
+    k_group_refresh<<<total_blocks, 256, refresh_smem(maxK), s>>>(slots, map);
     return cudaGetLastError();
 }
 

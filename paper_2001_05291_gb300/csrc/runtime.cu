@@ -475,9 +475,9 @@ stage_status run_tabu(stage_ctx *c, Instance *in, const stage_tabu_params *p,
     const bool profiling = (c->flags & STAGE_PROFILE) != 0;
     // Incremental neighbourhood (multi-kernel path): one full pass, then each
     // iteration selects and applies a move, refreshes the per-mission state
-    // (recording the missions whose terms changed) and updates the terms from
-    // those records and the closed base's column.  STAGE_FULL_PASS: a full
-    // pass every iteration instead.
+    // (recording the missions whose terms changed, rebuilding the closed
+    // base's column) and updates the other columns from those records.
+    // STAGE_FULL_PASS: a full pass every iteration instead.
     // Only for tables well beyond the L2 cache: an L2-resident table is
     // streamed faster than the scattered columns of the changed missions.
     bool inc = !(c->flags & STAGE_FULL_PASS) && swap_delta_fits(K) && swap_variant_default() &&
@@ -543,10 +543,7 @@ stage_status run_tabu(stage_ctx *c, Instance *in, const stage_tabu_params *p,
         if (!inc) run("swap_eval", [&] { return launch_swap_eval(tw, in->cost, nC, 0, c->stream); });
         run("select", [&] { return launch_select(tw, nC, c->stream); });
         run("refresh", [&] { return launch_refresh(tw, in->cost, c->stream); });
-        if (inc) {
-            run("swap_delta", [&] { return launch_swap_delta(tw, c->stream); });
-            run("swap_row", [&] { return launch_swap_row(tw, in->cost, c->stream); });
-        }
+        if (inc) run("swap_delta", [&] { return launch_swap_delta(tw, c->stream); });
         return e;
     };
     const bool multi = nC > 0 && iters > 0 && !(tabu_resident_fits(K, in->B, in->M_pad, nC) && swap_variant_default()) &&
@@ -575,7 +572,7 @@ stage_status run_tabu(stage_ctx *c, Instance *in, const stage_tabu_params *p,
         int it = 0;
         for (; it + kGraphIters <= iters; it += kGraphIters) {
             if (inc) {
-                for (const char *nm : {"select", "refresh", "swap_delta", "swap_row"})
+                for (const char *nm : {"select", "refresh", "swap_delta"})
                     c->stats[nm].launches += kGraphIters;
             } else {
                 for (const char *nm : {"swap_eval", "select", "refresh"}) c->stats[nm].launches += kGraphIters;

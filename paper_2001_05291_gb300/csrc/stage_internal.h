@@ -118,8 +118,9 @@ cudaError_t launch_swap_eval(const TabuBuffers &w, const int32_t *cost, int nC, 
                              cudaStream_t s);
 cudaError_t launch_select(const TabuBuffers &w, int nC, cudaStream_t s);
 cudaError_t launch_refresh(const TabuBuffers &w, const int32_t *cost, cudaStream_t s);
-// Incremental neighbourhood (w.chg set): the candidate rows over the missions
-// the refresh recorded, and the column of the base the move closed.
+// Incremental neighbourhood (w.chg set): every base's column over the
+// missions the refresh recorded (the refresh itself rebuilds the column of
+// the base the move closed).
 bool swap_delta_fits(int K);
 constexpr size_t kIncrementalMinTableBytes = 256ull << 20;   // candidate rows x missions, int32
 cudaError_t launch_swap_delta(const TabuBuffers &w, cudaStream_t s);
@@ -128,7 +129,6 @@ cudaError_t launch_swap_delta(const TabuBuffers &w, cudaStream_t s);
 int table_ldT(int B);
 cudaError_t launch_transpose_table(const int32_t *cost, int B, int M_pad, const int32_t *border, int32_t *costT,
                                    cudaStream_t s);
-cudaError_t launch_swap_row(const TabuBuffers &w, const int32_t *cost, cudaStream_t s);
 cudaError_t launch_export_best_two(const TabuBuffers &w, const int *perm, int32_t *a, int32_t *b,
                                    int32_t *b1, int32_t *b2, cudaStream_t s);
 // mission order (Morton order of pickup/drop-off midpoints) and readback in caller order

@@ -375,8 +375,8 @@ def test_graph_replay_and_small_block_paths():
 def test_incremental_equals_full_pass():
     """STAGE_INCREMENTAL (the default for tables well beyond L2) keeps the
     neighbourhood's gain and extra terms across iterations and updates them from
-    the missions whose best / second best changed and from the closed base's
-    column; STAGE_FULL_PASS re-evaluates the whole table every iteration.  Graph
+    the missions whose best / second best changed, and rebuilds the closed
+    base's column in the refresh; STAGE_FULL_PASS re-evaluates the whole table every iteration.  Graph
     replay and per-kernel launches of the incremental form, and the full pass,
     all equal the oracle's trajectory: several K (1 to 64), unavailable bases, a
     start placement, the improving-only rule, R below most costs and R near
@@ -410,7 +410,7 @@ def test_incremental_equals_full_pass():
                                                                         want.best_iter)
                 assert (got.final_cov, got.final_dist) == (want.final_cov, want.final_dist)
                 c.unload_instance(h)
-        assert cp.kernel_stats("swap_delta")[0] > 0 and cp.kernel_stats("swap_row")[0] > 0
+        assert cp.kernel_stats("swap_delta")[0] > 0
         assert cf.kernel_stats("swap_delta")[0] == 0
 
 
