@@ -63,6 +63,15 @@ def test_large_workload_as_benchmarked(stage_mod):
         assert oracle.evaluate(cost, placements[t], inst.R) == (got.moves[t][4], got.moves[t][5])
     assert oracle.evaluate(cost, got.best_open, inst.R) == (got.best_cov, got.best_dist)
     assert sorted(placements[-1]) == got.final_open.tolist()
+    # the search as benchmarked keeps the neighbourhood's terms across
+    # iterations; re-evaluating the whole table every iteration gives the same
+    # 1000 moves
+    with stage.Context(device=0, full_pass=True) as cf:
+        hf = cf.load_instance(inst.base_xy, inst.pick_xy, inst.drop_xy)
+        full = cf.tabu_run(hf, inst.K, inst.R, inst.iters, inst.tenure)
+        cf.unload_instance(hf)
+    assert [tuple(m) for m in full.moves] == [tuple(m) for m in got.moves]
+    assert (full.best_cov, full.best_dist, full.best_iter) == (got.best_cov, got.best_dist, got.best_iter)
 
 
 def test_batched_workload_instances_in_one_batch(stage_mod):
