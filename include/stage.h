@@ -75,10 +75,16 @@ typedef int32_t stage_status;
 #define STAGE_AUTOTUNE     4u   /* tune the swap pass's tile the first time a shape is met */
 #define STAGE_FULL_PASS    8u   /* Tabu searches (stage_tabu_run) re-evaluate the whole swap
                                    neighbourhood by a full pass over the cost table every
-                                   iteration.  By default, for tables well beyond the L2 cache,
-                                   the neighbourhood's terms are kept across iterations and
-                                   updated for the missions whose best or second-best open base
-                                   changed (the same values exactly) */
+                                   iteration.  By default, for tables well beyond the L2 cache
+                                   (candidate rows x missions x 4 B >= 256 MiB), the
+                                   neighbourhood's terms are kept across iterations and updated
+                                   for the missions whose best or second-best open base changed
+                                   (the same values exactly).  That form keeps a mission-major
+                                   copy of the cost table with the instance (the table's size
+                                   again, built on the first such search, dropped by
+                                   stage_update_instance) and 32 bytes per mission; when the
+                                   context's HBM budget has no room for them the search takes
+                                   the full pass */
 #define STAGE_INCREMENTAL 16u   /* that incremental update whatever the table's size */
 
 /* instance descriptor flags */
