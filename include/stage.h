@@ -81,7 +81,7 @@ typedef int32_t stage_status;
                                    for the missions whose best or second-best open base changed
                                    (the same values exactly).  That form keeps a mission-major
                                    copy of the cost table with the instance (the table's size
-                                   again, built on the first such search, dropped by
+                                   again, built on the first such search and again after
                                    stage_update_instance) and 32 bytes per mission; when the
                                    context's HBM budget has no room for them the search takes
                                    the full pass */
