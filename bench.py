@@ -440,14 +440,22 @@ def run_ours(args):
     return 0
 
 
+def kernel_code(text: str) -> str:
+    """The kernel source without its comments and blank space: what the
+    compiler sees of it (stored ncu traffic applies to the same code)."""
+    import re
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", "", text)
+    return "\n".join(" ".join(line.split()) for line in text.splitlines() if line.strip())
+
+
 def kernel_digest() -> str:
-    """Hash of the kernel sources: stored ncu traffic applies only to the same code."""
+    """Hash of the kernel code (comments and spacing aside): stored ncu traffic
+    applies only to the same code."""
     import hashlib
-    h = hashlib.sha256()
     src = os.path.join(ROOT, "paper_2001_05291_gb300", "csrc", "kernels.cu")
-    with open(src, "rb") as fh:
-        h.update(fh.read())
-    return h.hexdigest()[:16]
+    with open(src, encoding="utf-8") as fh:
+        return hashlib.sha256(kernel_code(fh.read()).encode()).hexdigest()[:16]
 
 
 def _ctx_for(args, stage, torch, local=0):

@@ -2113,7 +2113,7 @@ cudaError_t launch_refresh(const TabuBuffers &w, const int32_t *cost, cudaStream
 // would give for the new placement (integer sums: exactly), so the
 // selection still scores every swap of the neighbourhood.
 // --------------------------------------------------------------------------
-constexpr int kDeltaRows = 256;    // candidate positions per block, one per thread
+constexpr int kDeltaRows = 256;    // positions of the mission-major copy (bases) per block, one per thread
 constexpr int kDeltaChunk = 32;    // recorded missions staged per block step
 constexpr int kDeltaBatch = 8;     // cost loads in flight per thread
 
