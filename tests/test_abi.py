@@ -103,3 +103,17 @@ def test_create_without_gpu_fails_loudly(libpath):
     with pytest.raises(stage.StageError) as e:
         stage.Context(device=0, torch_memory=False)
     assert e.value.status == -6   # STAGE_ERR_CUDA: no CPU fallback
+
+
+def test_binding_constants_match_header():
+    """The binding's flag and status values are the header's #defines."""
+    from paper_2001_05291_gb300 import stage
+    with open(HEADER) as fh:
+        defs = dict(re.findall(r"#define\s+(STAGE_[A-Z_0-9]+)\s+\(?(-?\d+)u?\)?", fh.read()))
+    names = ["STAGE_THREADSAFE", "STAGE_PROFILE", "STAGE_AUTOTUNE", "STAGE_FULL_PASS", "STAGE_INCREMENTAL",
+             "STAGE_DESC_HAVERSINE"]
+    for n in names:
+        assert n in defs, n
+        assert getattr(stage, n) == int(defs[n]), n
+    flags = [int(defs[n]) for n in names[:5]]
+    assert len(set(flags)) == 5 and all(f & (f - 1) == 0 for f in flags)   # distinct single bits
