@@ -76,7 +76,11 @@ def test_batch_equals_alone_and_oracle(stage_mod):
         assert got[-1].n_moves < 60   # the improving-only search stopped early inside the batch
 
 
-def test_update_matches_rebuilt_instance(stage_mod):
+@pytest.mark.parametrize("incremental", [False, True])
+def test_update_matches_rebuilt_instance(stage_mod, incremental):
+    """An updated instance searches like the rebuilt one; with the incremental
+    neighbourhood the search before the update builds the mission-major copy,
+    the one after it (more missions, some removed) rebuilds it."""
     stage = stage_mod
     inst = small(7, 45, 12000, 7)
     key = synth.stream_key(7, 50)
@@ -84,8 +88,11 @@ def test_update_matches_rebuilt_instance(stage_mod):
     remove = np.unique((u[:400] * inst.M).astype(np.int64))
     add = synth.make_instance("add", 8, 1, 80, 500, 1, 0, 0, 0, synth.Layout(400_000, 300_000))
     closed = [2, 11, 30]
-    with stage.Context(device=0) as ctx:
+    with stage.Context(device=0, incremental=incremental) as ctx:
         h = ctx.load_instance(inst.base_xy, inst.pick_xy, inst.drop_xy)
+        if incremental:
+            before = ctx.tabu_run(h, inst.K, inst.R, 30, 4)
+            same(before, oracle.tabu(table(inst), inst.K, inst.R, 30, 4, nthreads=8))
         ctx.update_instance(h, add_pick=add.pick_xy, add_drop=add.drop_xy, remove=remove, unavailable=closed)
         keep = np.setdiff1d(np.arange(inst.M), remove)
         pick = np.concatenate([inst.pick_xy[keep], add.pick_xy])
