@@ -61,7 +61,6 @@ def parse_args():
                     help="large: Tabu iterations of the full-pass reference run (0: skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-missions", type=int, default=100_000)
-    ap.add_argument("--cpu-budget-s", type=float, default=15.0)
     return ap.parse_args()
 
 
@@ -151,35 +150,67 @@ def evals_per_iteration(inst) -> int:
     return inst.K * (inst.B - inst.K) * inst.M
 
 
-def cpu_baseline(inst, sample_missions: int, budget_s: float):
-    """The oracle, as it stands, on the host cores: table build, ranking and Tabu
-    iterations on the first `sample_missions` missions of the workload."""
+CPU_ITERS = 20   # Tabu iterations of the oracle's timed sample
+
+
+def cpu_baseline(inst, sample_missions: int, iters: int = CPU_ITERS):
+    """The oracle, as it stands, on the host cores: its cost table of the first
+    `sample_missions` missions of the workload and the ranking (timed apart),
+    then `iters` Tabu iterations from the ranking (the timed value: the
+    oracle's gain / loss / extra evaluation of every swap, every iteration).
+    The same measurement serves the bench line's cpu_baseline and the
+    reference arm."""
     import oracle
     threads = os.cpu_count() or 1
     Ms = min(sample_missions, inst.M)
     t0 = time.perf_counter()
     cost = oracle.cost_table(inst.base_xy, inst.pick_xy[:Ms], inst.drop_xy[:Ms], threads)
     start, _ = oracle.rank(cost, inst.K)
-    iters = 0
-    per_iter = inst.K * (inst.B - inst.K) * Ms
-    while True:
-        oracle.tabu(cost, inst.K, inst.R, 1, inst.tenure, start_open=start, nthreads=threads)
-        iters += 1
-        if time.perf_counter() - t0 > budget_s or iters >= 50:
-            break
+    build_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    r = oracle.tabu(cost, inst.K, inst.R, iters, inst.tenure, start_open=start, nthreads=threads)
     dt = time.perf_counter() - t0
-    return {"value": iters * per_iter / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": f"first {Ms} missions of the workload (B={inst.B}, K={inst.K}), table build + "
-                      f"ranking + {iters} Tabu iterations on {threads} threads, {dt:.1f} s",
-            "cpu_model": cpu_model()}
+    n = max(1, len(r.moves))
+    per_iter = inst.K * (inst.B - inst.K) * Ms
+    return {"value": n * per_iter / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"first {Ms} missions of the workload (B={inst.B}, K={inst.K}, R={inst.R} m): {n} Tabu "
+                      f"iterations from the ranking on {threads} threads in {dt:.2f} s (every swap evaluated "
+                      f"every iteration); table build and ranking {build_s:.2f} s, timed apart",
+            "tabu_iters_per_s": n / dt, "table_build_s": build_s, "cpu_model": cpu_model()}
+
+
+# Arm implementer 0x41 part numbers seen on server parts (the kernel's
+# /proc/cpuinfo has no model name on aarch64)
+_ARM_PARTS = {"0xd4f": "Neoverse-V2", "0xd40": "Neoverse-V1", "0xd0c": "Neoverse-N1", "0xd49": "Neoverse-N2",
+              "0xd8e": "Neoverse-N3", "0xd84": "Neoverse-V3"}
 
 
 def cpu_model():
     try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                name = line.split(":", 1)[1].strip()
+                if name and name != "-":
+                    vendor = next((l.split(":", 1)[1].strip() for l in out.splitlines()
+                                   if l.lower().startswith("vendor id")), "")
+                    return f"{vendor} {name}".strip()
+    except Exception:
+        pass
+    try:
+        impl = part = None
         with open("/proc/cpuinfo") as fh:
             for line in fh:
-                if line.lower().startswith(("model name", "cpu model")):
+                low = line.lower()
+                if low.startswith(("model name", "cpu model")):
                     return line.split(":", 1)[1].strip()
+                if low.startswith("cpu implementer"):
+                    impl = line.split(":", 1)[1].strip()
+                if low.startswith("cpu part"):
+                    part = line.split(":", 1)[1].strip()
+        if part:
+            name = _ARM_PARTS.get(part, "unknown part") if impl == "0x41" else "unknown part"
+            return f"Arm implementer {impl} part {part} ({name})"
     except Exception:
         pass
     import platform
@@ -187,15 +218,18 @@ def cpu_model():
 
 
 def run_reference(args):
+    """The reference arm: the CPU oracle (a paper has no code to install) on
+    the same bounded sample and iteration count as the bench line's
+    cpu_baseline, each step one such measurement."""
     rank, world, _ = env_rank()
     if rank != 0:
         return 0
     inst = workload(args.workload, args.missions)
-    sample = min(50_000, inst.M)
+    sample = min(args.cpu_sample_missions, inst.M)
     for _ in range(args.warmup):
-        cpu_baseline(inst, sample, 0.0)
+        cpu_baseline(inst, sample)
     t0 = time.perf_counter()
-    runs = [cpu_baseline(inst, sample, 0.0) for _ in range(args.steps)]
+    runs = [cpu_baseline(inst, sample) for _ in range(args.steps)]
     dt = time.perf_counter() - t0
     value = statistics.mean(r["value"] for r in runs)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
@@ -204,7 +238,7 @@ def run_reference(args):
             "data": "synthetic",
             "config": config_of(inst),
             "cpu_baseline": {"value": value, "unit": UNIT, "kind": "oracle", "cores": runs[0]["cores"],
-                             "sample": runs[0]["sample"]},
+                             "sample": runs[0]["sample"], "cpu_model": runs[0]["cpu_model"]},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
@@ -225,7 +259,13 @@ def config_of(inst):
 # the mission-major copy of the table
 DELTA_BYTES_PER_RECORD = 32
 KERNELS = ("table", "order", "rowsum", "topk", "init", "begin", "transpose", "swap_eval", "select", "refresh",
-           "swap_delta", "evaluate", "tabu_small", "autotune", "update")
+           "swap_delta", "persist", "evaluate", "tabu_small", "autotune", "update")
+# per iteration of the persistent search: the refresh reads each mission's
+# state (a, b: 8 B; best and second-best slot: 4 B) and its costs to the
+# opened and the closed base (8 B); the selection reads each candidate's gain
+# (4 + 8 B) and each (slot, candidate) extra term (4 + 8 B)
+REFRESH_BYTES_PER_MISSION = 20
+SELECT_BYTES_PER_ENTRY = 12
 
 
 def stored_traffic(fname, inst, args):
@@ -322,11 +362,51 @@ def run_ours(args):
                  "traffic": None, "algorithmic_bytes_per_launch": d_bytes, "avg_launch_ms": d_avg_s * 1000.0,
                  "launches": n_sd, "records_per_launch": rec_per_launch,
                  "records_fraction": rec_per_launch / inst.M}
+    # the persistent search (the incremental form's whole loop in one launch):
+    # algorithmic bytes per launch = its iterations' refresh and selection
+    # reads plus the delta step's records (each record's row of the
+    # mission-major copy and the record itself)
+    n_pe, ms_pe = stats["persist"]
+    persist = None
+    if n_pe and ms_pe > 0:
+        iters_run = ctx.kernel_stats("persist_refresh")[0]
+        rec_bytes = records * (TABLE_BYTES_PER_ELEM * (inst.B - 1) + DELTA_BYTES_PER_RECORD)
+        ref_bytes = iters_run * REFRESH_BYTES_PER_MISSION * inst.M
+        sel_bytes = iters_run * SELECT_BYTES_PER_ENTRY * (inst.K + 1) * nC
+        p_bytes = (rec_bytes + ref_bytes + sel_bytes) / n_pe
+        p_avg_s = (ms_pe / n_pe) / 1000.0
+        # the kernel's own clocks per step: the mean over its CTAs and the
+        # slowest CTA, in microseconds per iteration
+        steps = {}
+        for nm in ("move", "refresh", "wait_refresh", "update", "wait_update", "select", "wait_select",
+                   "refresh_loop", "refresh_rescan", "refresh_sums", "update_issue", "update_wait",
+                   "update_compute"):
+            mean = ctx.kernel_stats(f"persist_{nm}")[1]
+            top = ctx.kernel_stats(f"persist_{nm}_max")[1]
+            steps[nm] = {"mean_us": 1000.0 * mean / max(1, iters_run), "max_us": 1000.0 * top / max(1, iters_run)}
+        persist = {"bound": "hbm", "kernel": "persist", "achieved": p_bytes / p_avg_s / 1e9, "peak": peak,
+                   "peak_source": peak_src, "unit": "GB/s", "frac": p_bytes / p_avg_s / 1e9 / peak,
+                   "traffic": None, "algorithmic_bytes_per_launch": p_bytes, "avg_launch_ms": p_avg_s * 1000.0,
+                   "launches": n_pe, "iterations_per_launch": iters_run / n_pe,
+                   "ctas": ctx.kernel_stats("persist_ctas")[0],
+                   "records_per_iteration": records / max(1, iters_run),
+                   "records_fraction": records / max(1, iters_run) / inst.M,
+                   "bytes_per_iteration": {"update": rec_bytes / max(1, iters_run),
+                                           "refresh": ref_bytes / max(1, iters_run),
+                                           "select": sel_bytes / max(1, iters_run)},
+                   "steps_us_per_iteration": steps}
     # DRAM traffic per launch from the committed ncu summary, only while the
     # kernel source is the one that was measured and the workload is the full one
     traffic = stored_traffic("swap_eval_traffic.md", inst, args)
     if delta:
         delta["traffic"] = stored_traffic("swap_delta_traffic.md", inst, args)
+    if persist:
+        persist["traffic"] = stored_traffic("persist_traffic.md", inst, args)
+    # work performed on the device (the logical metric counts every swap of
+    # every iteration): (candidate row, mission) pairs the full passes visit
+    # plus (base, recorded mission) pairs of the incremental updates
+    n_full = stats["swap_eval"][0]
+    performed_pairs = n_full * nC * inst.M + records * (inst.B - 1)
 
     # end to end: host (pinned) buffers through the public API
     pinned = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
@@ -375,6 +455,25 @@ def run_ours(args):
                                   "algorithmic_bytes_per_launch": alg_bytes, "avg_launch_ms": f_avg_s * 1000.0,
                                   "launches": fn}}
 
+    # the same incremental search as three kernel launches per iteration
+    # (STAGE_NO_PERSIST), for comparison with the persistent launch
+    multi_kernel = None
+    if profile and persist and args.full_pass_iters > 0:
+        with stage.Context(device=local, profile=True, persist=False) as mctx:
+            hm = mctx.load_instance(*dev, haversine=geo)
+            mctx.tabu_run(hm, inst.K, inst.R, 20, inst.tenure)
+            torch.cuda.synchronize()
+            m0, m1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            m0.record(mctx.torch_stream)
+            mr = mctx.tabu_run(hm, inst.K, inst.R, args.full_pass_iters, inst.tenure)
+            m1.record(mctx.torch_stream)
+            m1.synchronize()
+            m_ms = m0.elapsed_time(m1)
+            mctx.unload_instance(hm)
+        multi_kernel = {"tabu_iters_per_s": mr.n_moves / (m_ms / 1000.0), "iterations": mr.n_moves,
+                        "note": "select, refresh and incremental update as separate launches per iteration "
+                                "(per-launch CUDA events on)"}
+
     # latency-bound workloads: the search alone on a loaded instance (the step
     # above also pays loading, ordering and ranking)
     search = None
@@ -409,7 +508,7 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(inst, args.cpu_sample_missions, args.cpu_budget_s)
+        cpu = cpu_baseline(inst, args.cpu_sample_missions)
 
     if rank == 0:
         line = {
@@ -419,12 +518,19 @@ def run_ours(args):
             "config": config_of(inst),
             "tabu_iters_per_s": world * moves / (ms / 1000.0),
             "evals_per_iteration": per_iter,
-            "roofline": ((delta if delta and ms_sd > ms_sw else
+            "value_kind": "logical: K*(B-K)*M swap x mission evaluations per Tabu iteration (every swap is "
+                          "scored exactly each iteration, but the incremental form derives the scores from the "
+                          "missions a move touched)",
+            "performed_pairs_per_s": world * performed_pairs / (ms / 1000.0),
+            "performed_pairs_note": "(candidate row, mission) pairs read by full swap passes plus (base, "
+                                    "recorded mission) pairs of the incremental updates, per second",
+            "roofline": ((persist if persist else delta if delta and ms_sd > ms_sw else
                           {"bound": "hbm", "kernel": "swap_eval", "achieved": achieved, "peak": peak,
                            "peak_source": peak_src, "unit": "GB/s", "frac": achieved / peak,
                            "traffic": traffic, "algorithmic_bytes_per_launch": alg_bytes,
                            "avg_launch_ms": avg_sw_s * 1000.0, "launches": n_sw}) if profile else None),
             "full_pass": full_pass,
+            "multi_kernel": multi_kernel,
             "kernels_ms": {k: {"launches": n, "total_ms": round(t, 3)} for k, (n, t) in stats.items() if n},
             "gpu_launches": launches,
             "e2e": e2e,

@@ -86,6 +86,11 @@ typedef int32_t stage_status;
                                    context's HBM budget has no room for them the search takes
                                    the full pass */
 #define STAGE_INCREMENTAL 16u   /* that incremental update whatever the table's size */
+#define STAGE_NO_PERSIST  32u   /* run the incremental update as three kernel launches per
+                                   iteration; by default, where the shape allows (K <= 256,
+                                   B <= 2048), the whole search is one persistent cooperative
+                                   launch whose CTAs meet at grid-wide barriers, each wait
+                                   bounded by spin_limit */
 
 /* instance descriptor flags */
 #define STAGE_DESC_DEVICE  1u   /* base_xy/pick_xy/drop_xy/base_available are device pointers */
@@ -115,7 +120,10 @@ typedef struct {
     uint64_t hbm_budget_bytes; /* cap on the context's device memory; 0 = device limit */
     int32_t max_slots;         /* batch/serving slots run concurrently; 0 = 8 */
     int32_t reserved0;
-    int64_t spin_limit;        /* bound on every device-side spin; 0 = 1<<26 polls */
+    int64_t spin_limit;        /* bound on every device-side wait (the persistent search's grid
+                                  barriers and shared-memory ring), in polls; 0 = 1<<26.  A wait
+                                  that gives up ends the kernel and the call returns
+                                  STAGE_ERR_TIMEOUT; the context stays usable */
     stage_alloc_fn alloc;      /* NULL = cudaMalloc */
     stage_free_fn free;        /* must be set iff alloc is */
     void *alloc_user;
@@ -467,6 +475,12 @@ STAGE_API stage_status stage_best_two(stage_ctx *ctx, stage_inst inst, const int
                             int32_t R, int32_t tabu_steps, int32_t tenure, int32_t *a,
                             int32_t *b, int32_t *b1, int32_t *b2);
 
+/* One bounded device-side wait on a flag that nothing sets, polled at most
+ * the context's spin_limit times (the same wait the persistent search's grid
+ * barriers use).  Returns STAGE_ERR_TIMEOUT when the wait gave up -- the
+ * expected outcome -- with no trap and no hang; the context stays usable. */
+STAGE_API stage_status stage_test_wait_timeout(stage_ctx *ctx);
+
 /* ------------------------------------------------------- allocation-free call */
 
 /* Every GPU that loads this library keeps a STAGE_NOALLOC_SCRATCH_MB MiB device
@@ -491,9 +505,12 @@ STAGE_API stage_status stage_best_two(stage_ctx *ctx, stage_inst inst, const int
  *                    stage_load_instance builds): columns M .. M_pad-1 must hold
  *                    INT32_MAX, M_pad a multiple of 4, base 16-byte aligned
  *   base_available   [B] uint8, or NULL for all available
- *   open             [K] distinct available base ids in [0, B) (not checked on
- *                    the host: they are device memory; an id outside [0, B)
- *                    makes the kernels read outside the table)
+ *   open             [K] distinct available base ids in [0, B).  They are
+ *                    device memory, so the host cannot check them; the first
+ *                    kernel does: with an id outside [0, B), a repeated id or
+ *                    an unavailable base, no objective is computed and every
+ *                    output entry stays -1 (the call still returns STAGE_OK,
+ *                    since it only enqueues the work)
  *   R                range in metres, 0 <= R < INT32_MAX
  *   out_cov/out_dist [K*B] int64: entry k*B + j = F(O - open[k] + j) for a
  *                    closed available j, else -1, exactly as stage_evaluate_swaps

@@ -6,13 +6,26 @@
 #include <cuda_runtime.h>
 #include <climits>
 #include <cstdlib>
+#include <mutex>
 #include <stdint.h>
 
 #include "stage_internal.h"
+#include "device_common.cuh"
 
 namespace stg {
 
-static int g_num_sms = 0;   // SMs of the current device (kernels_init)
+// SMs per device, filled by kernels_init (once per device); launchers size
+// their grids for the current device
+constexpr int kMaxDevices = 64;
+static int g_sms_of[kMaxDevices] = {};
+static std::mutex g_init_mu;
+
+static int sm_count()
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return 152;
+    return g_sms_of[dev] > 0 ? g_sms_of[dev] : 152;
+}
 int swap_segment_for(int M_pad, int nC, int K);
 
 // --------------------------------------------------------------------------
@@ -74,65 +87,12 @@ __device__ __forceinline__ double point_cos(int2 u)
     return Metric == 0 ? 0.0 : lat_cos(u.x);
 }
 
-// L2 cache policy for data read once per pass: evict it before other lines.
-__device__ __forceinline__ unsigned long long evict_first_policy()
-{
-    unsigned long long p;
-    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
-    return p;
-}
 
-__device__ __forceinline__ int warp_sum_i(int v)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
 
-__device__ __forceinline__ long long warp_sum_ll(long long v)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
 
-// Block-wide sum of two int64 values; the result is valid in thread 0.
-template <int NT>
-__device__ __forceinline__ void block_sum2(long long &x, long long &y)
-{
-    __shared__ long long sx[NT / 32], sy[NT / 32];
-    x = warp_sum_ll(x);
-    y = warp_sum_ll(y);
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    if (lane == 0) { sx[wid] = x; sy[wid] = y; }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        long long a = 0, b = 0;
-#pragma unroll
-        for (int k = 0; k < NT / 32; k++) { a += sx[k]; b += sy[k]; }
-        x = a; y = b;
-    }
-}
 
-__device__ __forceinline__ void add_ull(unsigned long long *p, long long v)
-{
-    atomicAdd(p, (unsigned long long)v);
-}
 
-__device__ __forceinline__ bool obj_better(long long c1, long long d1, long long c2, long long d2)
-{
-    return c1 != c2 ? c1 > c2 : d1 < d2;
-}
 
-__device__ __forceinline__ bool key_better(const MoveKey &a, const MoveKey &b)
-{
-    if (!a.valid) return false;
-    if (!b.valid) return true;
-    if (a.cov != b.cov) return a.cov > b.cov;
-    if (a.dist != b.dist) return a.dist < b.dist;
-    if (a.i != b.i) return a.i < b.i;
-    return a.j < b.j;
-}
 
 // --------------------------------------------------------------------------
 // Mission order.  The table's columns are laid out in Morton order of the
@@ -621,29 +581,6 @@ cudaError_t launch_evaluate(const int32_t *cost, int M, int M_pad, const int32_t
 // V0 = sum f(a) and loss[s] = sum_{m: b1 = s} f(b) - f(a).
 // --------------------------------------------------------------------------
 
-// Accumulate f(b) - f(a) of one mission into the shared loss of its best slot.
-__device__ __forceinline__ long long group_sum_small(unsigned mask, long long v);
-
-__device__ __forceinline__ void mission_terms(int a, int b, int R, long long &v0c, long long &v0d,
-                                              int *s_lc, unsigned long long *s_ld, int s1)
-{
-    const int ca = a <= R, cb = b <= R;
-    const long long da = ca ? a : 0, db = cb ? b : 0;
-    v0c += ca;
-    v0d += da;
-    const int dc = cb - ca;
-    const long long dd = db - da;
-    // lanes with the same best slot add their terms first (neighbouring
-    // columns share slots often), so a slot takes one shared atomic per warp
-    // instead of one per lane; |dd| <= R < 2^31, as group_sum_small needs
-    const unsigned peers = __match_any_sync(__activemask(), s1);
-    const int sc = (int)__reduce_add_sync(peers, (unsigned)dc);
-    const long long sd = group_sum_small(peers, dd);
-    if ((threadIdx.x & 31) == __ffs(peers) - 1) {
-        if (sc) atomicAdd(&s_lc[s1], sc);
-        if (sd) atomicAdd(&s_ld[s1], (unsigned long long)sd);
-    }
-}
 
 // Shared layout used by init and refresh: open ids [K], loss cov [K], loss dist [K].
 __device__ __forceinline__ void flush_loss_v0(const TabuBuffers &w, int *s_lc,
@@ -662,35 +599,6 @@ __device__ __forceinline__ void flush_loss_v0(const TabuBuffers &w, int *s_lc,
     }
 }
 
-__device__ __forceinline__ void scan_best_two(const int32_t *__restrict__ cost, size_t M_pad, int m,
-                                              const int *s_open, int K, int &a, int &b, int &k1,
-                                              int &k2)
-{
-    int c1 = kInf, c2 = kInf, i1 = 0x7fffffff, i2 = 0x7fffffff;
-    k1 = -1;
-    k2 = -1;
-    for (int k0 = 0; k0 < K; k0 += 8) {
-        int cv[8];
-#pragma unroll
-        for (int u = 0; u < 8; u++)
-            cv[u] = (k0 + u < K) ? __ldg(cost + (size_t)s_open[k0 + u] * M_pad + m) : kInf;
-#pragma unroll
-        for (int u = 0; u < 8; u++) {
-            const int k = k0 + u;
-            if (k >= K) break;
-            const int o = s_open[k];
-            const int c = cv[u];
-            if (k1 < 0 || c < c1 || (c == c1 && o < i1)) {
-                k2 = k1; c2 = c1; i2 = i1;
-                k1 = k; c1 = c; i1 = o;
-            } else if (k2 < 0 || c < c2 || (c == c2 && o < i2)) {
-                k2 = k; c2 = c; i2 = o;
-            }
-        }
-    }
-    a = c1;
-    b = c2;
-}
 
 // Body shared by the single-instance and the grouped launch: block `bid` of
 // `nb` blocks working on one instance.
@@ -888,351 +796,6 @@ k_swap_eval(TabuBuffers w, const int32_t *__restrict__ cost, int ignore_done)
         const int j = rows[threadIdx.x];
         if (g_c[threadIdx.x]) atomicAdd(&w.gain_c[j], g_c[threadIdx.x]);
         if (g_d[threadIdx.x]) atomicAdd(&w.gain_d[j], g_d[threadIdx.x]);
-    }
-}
-
-// --------------------------------------------------------------------------
-// a4, streaming form for K <= kPipeMaxK.  Persistent: one block per SM.  Warp 8
-// (the producer) streams row segments of kPipeT missions (8 KB) of the
-// candidate rows into a kPipeStages-deep shared-memory ring with bulk async
-// copies (cp.async.bulk, completion counted on an mbarrier per stage); warps
-// 0-7 (consumers) read each segment from shared memory, 8 missions per thread,
-// with their missions' thresholds held in registers for the whole tile.
-//
-// Work item = (mission tile, chunk of kPipeJ candidate rows), enumerated
-// tile-major; block g takes a contiguous range of items, so it reloads the
-// thresholds only when its tile changes.  Accumulators for the item's rows
-// live in shared memory and are flushed with one global atomic per nonzero
-// entry after the item.
-//
-// Thresholds are clamped at R + 1: a' = min(a, R+1), b' = min(b, R+1).  This
-// drops exactly the elements whose contribution is zero (both sides of every
-// difference uncovered), and inside a hit x <= R, so f(x) = (1, x) and
-// f(max(x, a')) = (a' <= R) ? (1, max(x, a')) : (0, 0).
-// --------------------------------------------------------------------------
-
-constexpr int kPipeT = 2048;
-constexpr int kPipeJ = 8;
-constexpr int kPipeChunksPerUnit = 4;        // work unit = one tile x 32 candidate rows
-constexpr int kPipeStages = 16;
-constexpr int kPipeConsumerWarps = 8;
-constexpr int kPipeConsumers = kPipeConsumerWarps * 32;
-constexpr int kPipeThreads = kPipeConsumers + 32;
-constexpr int kPipeMaxK = 256;
-constexpr int kPipePerThread = kPipeT / kPipeConsumers;   // 8 missions
-constexpr long long kPipeSpinLimit = 1ll << 22;
-
-__device__ __forceinline__ unsigned smem_u32(const void *p)
-{
-    return (unsigned)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long *bar, unsigned bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(unsigned long long *bar)
-{
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, unsigned parity)
-{
-    unsigned ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-// Bounded wait: false after kPipeSpinLimit polls.
-__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity)
-{
-    for (long long k = 0; k < kPipeSpinLimit; k++)
-        if (mbar_try_wait(bar, parity)) return true;
-    return false;
-}
-
-// Bulk async copy global -> shared, completion counted on `bar`; the table is
-// streamed once per iteration, so it is marked evict-first in L2 and the
-// per-mission thresholds stay resident.
-__device__ __forceinline__ void bulk_load(void *dst, const void *src, unsigned bytes, unsigned long long *bar,
-                                          unsigned long long policy)
-{
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::"r"(
-            smem_u32(dst)),
-        "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(policy)
-        : "memory");
-}
-
-
-__device__ __forceinline__ void consumer_sync()
-{
-    asm volatile("bar.sync 1, %0;" ::"n"(kPipeConsumers) : "memory");
-}
-
-// Warp sum of per-lane int64 values that each fit in int32, over the lanes of
-// `mask` (all of which call this with the same mask): biased 16-bit halves,
-// three 32-bit reductions.
-__device__ __forceinline__ long long group_sum_small(unsigned mask, long long v)
-{
-    const unsigned u = (unsigned)(v + 2147483648ll);
-    const unsigned lo = __reduce_add_sync(mask, u & 0xffffu);
-    const unsigned hi = __reduce_add_sync(mask, u >> 16);
-    return ((long long)hi << 16) + (long long)lo - ((long long)__popc(mask) << 31);
-}
-
-// Stage kinds carried through the ring: a candidate row segment, the tile's
-// thresholds (a, b, best slot), or the end of the block's work.
-enum : int { kStageRow = 0, kStageAuxA = 1, kStageAuxB = 2, kStageAuxS = 3, kStageEnd = 4 };
-
-struct StageMeta {
-    int kind, tile, chunk, r;
-};
-
-constexpr int kPipeMaxCand = 8192;   // candidate list staged in shared memory
-
-__global__ void __launch_bounds__(kPipeThreads, 1)
-k_swap_stream(TabuBuffers w, const int32_t *__restrict__ cost, int ignore_done)
-{
-    TabuDevState *st = w.st;
-    if (!ignore_done && (st->done || st->ls_hold)) return;
-    extern __shared__ __align__(1024) unsigned char sm_pipe[];
-    int32_t *ring = reinterpret_cast<int32_t *>(sm_pipe);
-    unsigned long long *full = reinterpret_cast<unsigned long long *>(sm_pipe + (size_t)kPipeStages * kPipeT * 4);
-    unsigned long long *empty = full + kPipeStages;
-    StageMeta *meta = reinterpret_cast<StageMeta *>(empty + kPipeStages);
-    int *s_cand = reinterpret_cast<int *>(meta + kPipeStages);                                // [nC]
-    unsigned long long *ex_d = reinterpret_cast<unsigned long long *>(s_cand + kPipeMaxCand);  // [K * J]
-    int *ex_c = reinterpret_cast<int *>(ex_d + w.K * kPipeJ);                                 // [K * J]
-    unsigned long long *g_d = reinterpret_cast<unsigned long long *>(ex_c + w.K * kPipeJ + 2);
-    g_d = reinterpret_cast<unsigned long long *>((reinterpret_cast<uintptr_t>(g_d) + 7) & ~(uintptr_t)7);
-    int *g_c = reinterpret_cast<int *>(g_d + kPipeJ);
-
-    const int nC = st->nC;
-    const int K = w.K, B = w.B, R = w.R, M_pad = w.M_pad;
-    const int nTiles = (M_pad + kPipeT - 1) / kPipeT;
-    const int nChunks = (nC + kPipeJ - 1) / kPipeJ;
-    const int nGroups = (nChunks + kPipeChunksPerUnit - 1) / kPipeChunksPerUnit;
-    const unsigned nUnits = (unsigned)nTiles * (unsigned)nGroups;
-
-    if (threadIdx.x == 0) {
-        for (int k = 0; k < kPipeStages; k++) {
-            mbar_init(&full[k], 1);
-            mbar_init(&empty[k], kPipeConsumerWarps);
-        }
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    for (int k = threadIdx.x; k < nC; k += blockDim.x) s_cand[k] = w.cand[k];
-    for (int k = threadIdx.x; k < K * kPipeJ; k += blockDim.x) { ex_d[k] = 0; ex_c[k] = 0; }
-    if (threadIdx.x < kPipeJ) { g_c[threadIdx.x] = 0; g_d[threadIdx.x] = 0; }
-    __syncthreads();
-
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (warp == kPipeConsumerWarps) {
-        // ---------------------------------------------------------- producer
-        // Units (tile, group of 4 row chunks) come from a device counter, so a
-        // block that meets a dense hit region takes fewer units; the next unit
-        // is claimed while the current one is issued.  A tile change first
-        // sends the tile's thresholds through the ring.
-        if (lane != 0) return;
-        const unsigned long long policy = evict_first_policy();
-        long long seq = 0;
-        bool ok = true;
-        auto issue = [&](int kind, int tile, int ch, int r, const void *src, unsigned bytes) {
-            const int stg = (int)(seq % kPipeStages);
-            const unsigned par = (unsigned)(((seq / kPipeStages) + 1) & 1);
-            if (!mbar_wait(&empty[stg], par)) { ok = false; return; }
-            meta[stg] = StageMeta{kind, tile, ch, r};
-            seq++;
-            if (bytes == 0) {
-                mbar_arrive(&full[stg]);
-            } else {
-                mbar_arrive_expect_tx(&full[stg], bytes);
-                bulk_load(ring + (size_t)stg * kPipeT, src, bytes, &full[stg], policy);
-            }
-        };
-        unsigned u = atomicAdd(&st->work, 1u);
-        int prev_tile = -1;
-        while (ok && u < nUnits) {
-            const unsigned nxt = atomicAdd(&st->work, 1u);
-            const int tile = (int)(u / nGroups), g = (int)(u % nGroups);
-            const int m0 = tile * kPipeT;
-            const int nm = min(kPipeT, M_pad - m0);
-            if (tile != prev_tile) {
-                issue(kStageAuxA, tile, 0, 0, w.a + m0, (unsigned)nm * 4);
-                if (ok) issue(kStageAuxB, tile, 0, 0, w.b + m0, (unsigned)nm * 4);
-                if (ok) issue(kStageAuxS, tile, 0, 0, w.s1 + m0, (unsigned)nm * 2);
-                prev_tile = tile;
-            }
-            for (int ch = g * kPipeChunksPerUnit; ok && ch < (g + 1) * kPipeChunksPerUnit; ch++)
-                for (int r = 0; ok && r < kPipeJ; r++) {
-                    const int c = ch * kPipeJ + r;
-                    if (c >= nC) break;
-                    issue(kStageRow, tile, ch, r, cost + (size_t)s_cand[c] * M_pad + m0, (unsigned)nm * 4);
-                }
-            u = nxt;
-        }
-        if (ok) issue(kStageEnd, -1, 0, 0, nullptr, 0);
-        if (!ok) {
-            atomicOr(&st->err, kErrPipelineTimeout);
-            for (long long q = seq > kPipeStages ? seq - kPipeStages : 0; q < seq; q++)
-                mbar_wait(&full[q % kPipeStages], (unsigned)((q / kPipeStages) & 1));
-        }
-        return;
-    }
-
-    // -------------------------------------------------------------- consumers
-    const int ct = threadIdx.x;
-    long long seq = 0;
-    int cur_tile = -1, cur_chunk = -1;
-    int ap[kPipePerThread], bp[kPipePerThread], sl[kPipePerThread];
-#pragma unroll
-    for (int e = 0; e < kPipePerThread; e++) { ap[e] = 0; bp[e] = INT_MIN; sl[e] = 0; }
-    bool uni = false;          // all 8 of this thread's missions share one best slot
-    bool abort_local = false;
-    for (;;) {
-        const int stg = (int)(seq % kPipeStages);
-        const unsigned par = (unsigned)((seq / kPipeStages) & 1);
-        seq++;
-        StageMeta md{kStageEnd, -1, 0, 0};
-        int4 x0 = make_int4(0, 0, 0, 0), x1 = x0;
-        if (!abort_local) {
-            // all lanes wait; the outcome is made warp-uniform so that the
-            // warp-collective calls below always see all 32 lanes
-            const bool got = __all_sync(0xffffffffu, mbar_wait(&full[stg], par));
-            if (got) {
-                md = meta[stg];
-                const int4 *src = reinterpret_cast<const int4 *>(ring + (size_t)stg * kPipeT);
-                if (md.kind == kStageAuxS) {
-                    x0 = src[ct];                          // 8 x int16
-                } else if (md.kind != kStageEnd) {
-                    x0 = src[2 * ct];
-                    x1 = src[2 * ct + 1];
-                }
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&empty[stg]);
-            } else {
-                abort_local = true;
-                atomicOr(&st->err, kErrPipelineTimeout);
-            }
-        }
-        // every consumer warp sees the same stage sequence, so these decisions
-        // (and the barriers of the flush) are uniform across the consumer warps
-        if (abort_local) md.kind = kStageEnd;
-        const bool inside = md.tile * kPipeT + ct * kPipePerThread < M_pad;
-        if (md.kind == kStageAuxA) {
-            const int av[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
-#pragma unroll
-            for (int e = 0; e < 8; e++) ap[e] = min(av[e], R + 1);
-            continue;
-        }
-        if (md.kind == kStageAuxB) {
-            const int bv[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
-#pragma unroll
-            for (int e = 0; e < 8; e++) bp[e] = inside ? min(bv[e], R + 1) : INT_MIN;
-            continue;
-        }
-        if (md.kind == kStageAuxS) {
-            const unsigned sv[4] = {(unsigned)x0.x, (unsigned)x0.y, (unsigned)x0.z, (unsigned)x0.w};
-#pragma unroll
-            for (int e = 0; e < 8; e++) sl[e] = inside ? (int)(int16_t)((sv[e >> 1] >> ((e & 1) * 16)) & 0xffff) : 0;
-            uni = true;
-#pragma unroll
-            for (int e = 1; e < 8; e++) uni = uni && (sl[e] == sl[0]);
-            continue;
-        }
-        const bool new_item = md.kind == kStageEnd || md.tile != cur_tile || md.chunk != cur_chunk;
-        if (new_item && cur_tile >= 0) {
-            // flush the finished item's accumulators
-            consumer_sync();
-            const int jbase = cur_chunk * kPipeJ;
-            for (int k = ct; k < K * kPipeJ; k += kPipeConsumers) {
-                const int c = ex_c[k];
-                const unsigned long long d = ex_d[k];
-                if (c | (d != 0)) {
-                    const int r = k % kPipeJ, sidx = k / kPipeJ;
-                    const int j = s_cand[jbase + r];
-                    atomicAdd(&w.extra_c[(size_t)sidx * B + j], c);
-                    atomicAdd(&w.extra_d[(size_t)sidx * B + j], d);
-                    ex_c[k] = 0;
-                    ex_d[k] = 0;
-                }
-            }
-            if (ct < kPipeJ) {
-                const int c = g_c[ct];
-                const unsigned long long d = g_d[ct];
-                if (c | (d != 0)) {
-                    const int j = s_cand[jbase + ct];
-                    atomicAdd(&w.gain_c[j], c);
-                    atomicAdd(&w.gain_d[j], d);
-                    g_c[ct] = 0;
-                    g_d[ct] = 0;
-                }
-            }
-            consumer_sync();
-        }
-        if (md.kind == kStageEnd) break;
-        cur_tile = md.tile;
-        cur_chunk = md.chunk;
-        const int r = md.r;
-        const int xv[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
-        // per-lane sums of this row's contributions (each term is at most one
-        // cost in magnitude, so 8 of them fit in int32)
-        int ec = 0, gc = 0;
-        long long ed = 0, gd = 0;
-        if (xv[0] < bp[0] || xv[1] < bp[1] || xv[2] < bp[2] || xv[3] < bp[3] || xv[4] < bp[4] ||
-            xv[5] < bp[5] || xv[6] < bp[6] || xv[7] < bp[7]) {
-#pragma unroll
-            for (int e = 0; e < 8; e++) {
-                const int x = xv[e], a = ap[e], b = bp[e];
-                if (x < b) {
-                    const int ca = a <= R, cb = b <= R;
-                    const int dc = ca - cb;
-                    const long long dd = (ca ? (long long)max(x, a) : 0ll) - (cb ? (long long)b : 0ll);
-                    if (uni) {
-                        ec += dc;
-                        ed += dd;
-                    } else if (dc | (dd != 0)) {
-                        atomicAdd(&ex_c[sl[e] * kPipeJ + r], dc);
-                        atomicAdd(&ex_d[sl[e] * kPipeJ + r], (unsigned long long)dd);
-                    }
-                    if (x < a) {
-                        gc += 1 - ca;
-                        gd += (long long)x - (ca ? (long long)a : 0ll);
-                    }
-                }
-            }
-        }
-        // warp aggregation: one shared atomic per (slot, row) group of lanes
-        if (uni && (ec | (ed != 0))) {
-            const unsigned am = __activemask();
-            const unsigned peers = __match_any_sync(am, sl[0]);
-            const int sc = (int)__reduce_add_sync(peers, (unsigned)ec);
-            const long long sd = group_sum_small(peers, ed);
-            if (lane == __ffs(peers) - 1 && (sc | (sd != 0))) {
-                atomicAdd(&ex_c[sl[0] * kPipeJ + r], sc);
-                atomicAdd(&ex_d[sl[0] * kPipeJ + r], (unsigned long long)sd);
-            }
-        }
-        if (__any_sync(0xffffffffu, gc | (gd != 0))) {
-            const int sc = (int)__reduce_add_sync(0xffffffffu, (unsigned)gc);
-            const long long sd = group_sum_small(0xffffffffu, gd);
-            if (lane == 0 && (sc | (sd != 0))) {
-                atomicAdd(&g_c[r], sc);
-                atomicAdd(&g_d[r], (unsigned long long)sd);
-            }
-        }
     }
 }
 
@@ -1441,7 +1004,7 @@ k_swap_direct(TabuBuffers w, const int32_t *__restrict__ cost, int ignore_done, 
 int swap_segment_heuristic(int M_pad, int nC)
 {
     const int chunks = (nC + kDirJ - 1) / kDirJ;   // judged at the default 16 rows per block
-    const long long target = 2ll * 4 * (g_num_sms > 0 ? g_num_sms : 152);
+    const long long target = 2ll * 4 * sm_count();
     int seg = 16384;
     while (seg > 1024 && (long long)((M_pad + seg - 1) / seg) * chunks < target) seg >>= 1;
     return seg;
@@ -1486,29 +1049,16 @@ cudaError_t launch_swap_direct_seg(const TabuBuffers &w, const int32_t *cost, in
     return cudaGetLastError();
 }
 
-// Swap-evaluation variant: 0 = direct (default), 1 = streaming pipeline,
-// 2 = the plain per-element form.  STAGE_SWAP_VARIANT overrides (tuning).
-static int g_swap_variant = 0;
-
-bool swap_variant_default() { return g_swap_variant == 0; }
-
-
-size_t swap_stream_smem(int K)
-{
-    return (size_t)kPipeStages * kPipeT * 4 + 2 * kPipeStages * 8 + kPipeStages * sizeof(StageMeta) +
-           (size_t)kPipeMaxCand * 4 + (size_t)K * kPipeJ * 12 + 16 + kPipeJ * 12 + 64;
-}
-
 cudaError_t launch_swap_eval(const TabuBuffers &w, const int32_t *cost, int nC, int ignore_done,
                              cudaStream_t s)
 {
     if (nC <= 0) return cudaSuccess;
-    if (g_swap_variant == 0 && w.K <= kPipeMaxK) {
+    if (w.K <= kPipeMaxK) {
         const int seg = swap_segment_for(w.M_pad, nC, w.K);
         const int bx = (w.M_pad + seg - 1) / seg;
         // latency-bound small grids: fewer rows per block, more blocks and
         // shorter per-warp chains, until the grid reaches two waves
-        const long long waves2 = 2ll * 4 * (g_num_sms > 0 ? g_num_sms : 152);
+        const long long waves2 = 2ll * 4 * sm_count();
         const size_t sm = swap_direct_smem(w.K);
         if ((long long)bx * ((nC + 15) / 16) >= waves2) {
             k_swap_direct<16><<<dim3(bx, (nC + 15) / 16), kDirThreads, sm, s>>>(w, cost, ignore_done, seg);
@@ -1517,10 +1067,6 @@ cudaError_t launch_swap_eval(const TabuBuffers &w, const int32_t *cost, int nC, 
         } else {
             k_swap_direct<4><<<dim3(bx, (nC + 3) / 4), kDirThreads, sm, s>>>(w, cost, ignore_done, seg);
         }
-        return cudaGetLastError();
-    }
-    if (g_swap_variant == 1 && w.K <= kPipeMaxK && nC <= kPipeMaxCand && g_num_sms > 0) {
-        k_swap_stream<<<g_num_sms, kPipeThreads, swap_stream_smem(w.K), s>>>(w, cost, ignore_done);
         return cudaGetLastError();
     }
     dim3 grid((w.M_pad + kSwapSegment - 1) / kSwapSegment, (nC + kSwapJ - 1) / kSwapJ);
@@ -1564,96 +1110,9 @@ cudaError_t launch_swap_table(const TabuBuffers &w, int nC, long long *out_c, lo
 // far and the trajectory, and clears V0 / loss for the refresh kernel.
 // --------------------------------------------------------------------------
 
-__device__ __forceinline__ MoveKey invalid_key()
-{
-    MoveKey k;
-    k.cov = 0; k.dist = 0; k.i = 0; k.j = 0; k.s = 0; k.c = 0; k.valid = 0; k.tabu = 0;
-    return k;
-}
 
-__device__ __forceinline__ MoveKey load_key_cg(const MoveKey *p)
-{
-    MoveKey k;
-    k.cov = __ldcg(&p->cov);
-    k.dist = __ldcg(&p->dist);
-    k.i = __ldcg(&p->i);
-    k.j = __ldcg(&p->j);
-    k.s = __ldcg(&p->s);
-    k.c = __ldcg(&p->c);
-    k.valid = __ldcg(&p->valid);
-    k.tabu = __ldcg(&p->tabu);
-    return k;
-}
 
-// The best key of a warp under key_better's order (valid first; covered desc,
-// distance asc, i asc, j asc), left in every lane: one 32-bit warp reduction per
-// field of the order on the lanes still tied, then the winner's key is read
-// from its lane.  Covered counts fit 31 bits, distances are non-negative and
-// base ids fit 16 bits.
-__device__ __forceinline__ void warp_best_key(MoveKey &k)
-{
-    const unsigned full = 0xffffffffu;
-    const int lane = threadIdx.x & 31;
-    unsigned tied = __ballot_sync(full, k.valid);
-    if (!tied) return;
-    const bool in1 = (tied >> lane) & 1u;
-    const int cv = in1 ? (int)k.cov : -1;
-    const int bc = __reduce_max_sync(full, cv);
-    tied = __ballot_sync(full, in1 && cv == bc);
-    const bool in2 = (tied >> lane) & 1u;
-    const unsigned dh = in2 ? (unsigned)((unsigned long long)k.dist >> 32) : 0xffffffffu;
-    const unsigned bdh = __reduce_min_sync(full, dh);
-    tied = __ballot_sync(full, in2 && dh == bdh);
-    const bool in3 = (tied >> lane) & 1u;
-    const unsigned dl = in3 ? (unsigned)(unsigned long long)k.dist : 0xffffffffu;
-    const unsigned bdl = __reduce_min_sync(full, dl);
-    tied = __ballot_sync(full, in3 && dl == bdl);
-    const bool in4 = (tied >> lane) & 1u;
-    const unsigned ij = in4 ? (((unsigned)k.i << 16) | (unsigned)k.j) : 0xffffffffu;
-    const unsigned bij = __reduce_min_sync(full, ij);
-    tied = __ballot_sync(full, in4 && ij == bij);
-    const int src = __ffs(tied) - 1;
-    MoveKey o;
-    o.cov = __shfl_sync(full, k.cov, src);
-    o.dist = __shfl_sync(full, k.dist, src);
-    o.i = __shfl_sync(full, k.i, src);
-    o.j = __shfl_sync(full, k.j, src);
-    o.s = __shfl_sync(full, k.s, src);
-    o.c = __shfl_sync(full, k.c, src);
-    o.valid = __shfl_sync(full, k.valid, src);
-    o.tabu = __shfl_sync(full, k.tabu, src);
-    k = o;
-}
 
-// Best admissible and best overall key of a block: warp reductions, then one
-// warp over the warps' winners.  Every thread receives the results.
-template <int NT>
-__device__ __forceinline__ void block_best2(MoveKey &adm, MoveKey &all, MoveKey *s_adm, MoveKey *s_all)
-{
-    static_assert(NT % 32 == 0 && NT <= 1024, "block of whole warps");
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    warp_best_key(adm);
-    warp_best_key(all);
-    if (lane == 0) {
-        s_adm[wid] = adm;
-        s_all[wid] = all;
-    }
-    __syncthreads();
-    if (wid == 0) {
-        adm = lane < NT / 32 ? s_adm[lane] : invalid_key();
-        all = lane < NT / 32 ? s_all[lane] : invalid_key();
-        warp_best_key(adm);
-        warp_best_key(all);
-        if (lane == 0) {
-            s_adm[0] = adm;
-            s_all[0] = all;
-        }
-    }
-    __syncthreads();
-    adm = s_adm[0];
-    all = s_all[0];
-    __syncthreads();
-}
 
 // Scan candidates [q0, total) with stride `step` into the best admissible and
 // the best overall key.
@@ -1820,150 +1279,16 @@ cudaError_t launch_select(const TabuBuffers &w, int nC, cudaStream_t s)
 // gain / extra are cleared for the next evaluation.
 // --------------------------------------------------------------------------
 
-constexpr int kRefQ = 2048;   // missions queued for a cooperative rescan per block
+   // missions queued for a cooperative rescan per block
 
 // Dynamic shared memory of the refresh: per slot the loss (distance, count),
 // the closed base's column terms (distance, count) and the base id.
 size_t refresh_smem(int K) { return (size_t)K * (8 + 8 + 4 + 4 + 4); }
 
-// Whether a mission's terms in the swap neighbourhood changed: they depend on
-// its clamped best and second-best costs and, while it is covered, on its
-// best slot (an uncovered mission adds no extra term to any slot).
-__device__ __forceinline__ bool terms_changed(int ao, int bo, int so, int an, int bn, int sn, int R)
-{
-    const int ao1 = min(ao, R + 1), bo1 = min(bo, R + 1), an1 = min(an, R + 1), bn1 = min(bn, R + 1);
-    return ao1 != an1 || bo1 != bn1 || (an1 <= R && so != sn);
-}
 
-// Append the lanes' changed missions to the record list, two int4 per
-// record: (column, old a, old b, old best slot), (new a, new b, new best
-// slot, 0).  One global atomic per warp; every lane of the warp calls it.
-__device__ __forceinline__ void record_changes(const TabuBuffers &w, bool ch, int m, int ao, int bo, int so, int an,
-                                               int bn, int sn)
-{
-    const unsigned full = 0xffffffffu;
-    const unsigned cm = __ballot_sync(full, ch);
-    if (!cm) return;
-    const int lane = threadIdx.x & 31, lead = __ffs(cm) - 1;
-    int q0 = 0;
-    if (lane == lead) q0 = atomicAdd(&w.st->chg_n, __popc(cm));
-    q0 = __shfl_sync(full, q0, lead);
-    if (ch) {
-        int4 *r = w.chg + 2 * (size_t)(q0 + __popc(cm & ((1u << lane) - 1u)));
-        r[0] = make_int4(m, ao, bo, so);
-        r[1] = make_int4(an, bn, sn, 0);
-    }
-}
 
-// A mission's terms in the column of a base x away (the closed base, a
-// candidate again), for its state after the move: the gain term into
-// (gc, gd), the extra term at its best slot into the block's accumulators.
-__device__ __forceinline__ void closed_column_terms(int x, int a, int b, int s1, int R, long long &gc, long long &gd,
-                                                    int *s_ic, unsigned long long *s_id)
-{
-    const int a1 = min(a, R + 1), b1 = min(b, R + 1);
-    if (x >= b1) return;   // a <= b
-    const int ca = a1 <= R, cb = b1 <= R;
-    const int dc = ca - cb;
-    const long long dd = (ca ? (long long)max(x, a1) : 0ll) - (cb ? (long long)b1 : 0ll);
-    if (dc | (dd != 0)) {
-        atomicAdd(&s_ic[s1], dc);
-        atomicAdd(&s_id[s1], (unsigned long long)dd);
-    }
-    if (x < a1) {
-        gc += 1 - ca;
-        gd += (long long)x - (ca ? (long long)a1 : 0ll);
-    }
-}
 
-// Best and second-best open base of the missions queued for a rescan (their
-// best or second best was the closed base), G threads per mission with G
-// chosen from the queue length so that a short queue still has every thread
-// loading: a thread scans every G-th slot, 8 independent loads at a time,
-// with keys (cost, base id) ordered as in scan_best_two; the G partial pairs
-// are merged by butterfly shuffles within the group.  The mission's terms (V0,
-// loss of its best slot) are added as mission_terms adds them.
-__device__ __forceinline__ void refresh_rescans(const TabuBuffers &w, const int32_t *__restrict__ cost,
-                                                const int *s_open, const int *s_q, int nq, int *s_lc,
-                                                unsigned long long *s_ld, long long &v0c, long long &v0d,
-                                                const int32_t *rowi, long long &gic, long long &gid, int *s_ic,
-                                                unsigned long long *s_id)
-{
-    constexpr int L = 8;
-    const unsigned full = 0xffffffffu;
-    const int K = w.K;
-    const size_t M_pad = w.M_pad;
-    const int G = nq <= 32 ? 8 : nq <= 64 ? 4 : nq <= 128 ? 2 : 1;   // the same on every thread
-    const int per = blockDim.x / G;
-    const int sub = threadIdx.x & (G - 1);
-    for (int q0 = 0; q0 < nq; q0 += per) {
-        const int qi = q0 + (int)threadIdx.x / G;
-        const bool has = qi < nq;
-        const int m = has ? s_q[qi] : 0;
-        unsigned long long e1 = ~0ull, e2 = ~0ull;
-        int k1 = -1, k2 = -1;
-        int ao = 0, bo = 0, so = 0, xi = 0;   // the state before the move (recorded if it changes)
-        if (has && sub == 0 && w.chg) {
-            ao = w.a[m]; bo = w.b[m]; so = w.s1[m];
-            xi = __ldcs(rowi + m);
-        }
-        if (has) {
-            for (int k0 = sub; k0 < K; k0 += L * G) {
-                int cv[L];
-#pragma unroll
-                for (int u = 0; u < L; u++) {
-                    const int k = k0 + u * G;
-                    cv[u] = k < K ? __ldg(cost + (size_t)s_open[k] * M_pad + m) : 0;
-                }
-#pragma unroll
-                for (int u = 0; u < L; u++) {
-                    const int k = k0 + u * G;
-                    if (k < K) {
-                        const unsigned long long e = ((unsigned long long)(unsigned)cv[u] << 32) | (unsigned)s_open[k];
-                        if (e < e1) {
-                            e2 = e1; k2 = k1;
-                            e1 = e; k1 = k;
-                        } else if (e < e2) {
-                            e2 = e; k2 = k;
-                        }
-                    }
-                }
-            }
-        }
-        // every lane takes part (lanes without a mission carry empty pairs)
-        for (int off = 1; off < G; off <<= 1) {
-            const unsigned long long f1 = __shfl_xor_sync(full, e1, off), f2 = __shfl_xor_sync(full, e2, off);
-            const int g1 = __shfl_xor_sync(full, k1, off), g2 = __shfl_xor_sync(full, k2, off);
-            if (f1 < e1) {
-                if (f2 < e1) { e2 = f2; k2 = g2; } else { e2 = e1; k2 = k1; }
-                e1 = f1; k1 = g1;
-            } else if (f1 < e2) {
-                e2 = f1; k2 = g1;
-            }
-        }
-        const bool lead = has && sub == 0;
-        const int a = (int)(e1 >> 32);
-        const int b = e2 == ~0ull ? kInf : (int)(e2 >> 32);
-        if (lead) {
-            w.a[m] = a; w.b[m] = b; w.s1[m] = (int16_t)k1; w.s2[m] = (int16_t)k2;
-            mission_terms(a, b, w.R, v0c, v0d, s_lc, s_ld, k1);
-            if (w.chg) closed_column_terms(xi, a, b, k1, w.R, gic, gid, s_ic, s_id);
-        }
-        if (w.chg) record_changes(w, lead && terms_changed(ao, bo, so, a, b, k1, w.R), m, ao, bo, so, a, b, k1);
-    }
-}
 
-// One mission's rescan by its own thread, past the queue's capacity (out of
-// line: a rare path kept out of the unrolled loop's registers).  Writes the
-// mission's state; returns (a, b) and the best slot in k1.
-__device__ __noinline__ int2 refresh_scan_one(const TabuBuffers &w, const int32_t *__restrict__ cost, int m,
-                                              const int *s_open, int &k1)
-{
-    int a, b, k2;
-    scan_best_two(cost, w.M_pad, m, s_open, w.K, a, b, k1, k2);
-    w.a[m] = a; w.b[m] = b; w.s1[m] = (int16_t)k1; w.s2[m] = (int16_t)k2;
-    return make_int2(a, b);
-}
 
 // a7: incremental refresh after the move (close slot mv_s, open base mv_j in
 // it).  A thread loads a mission's state and the new base's cost together
@@ -2061,11 +1386,17 @@ __device__ __forceinline__ void refresh_body(const TabuBuffers &w, const int32_t
             mission_terms(a, b, w.R, v0c, v0d, s_lc, s_ld, k1);
             if (inc) closed_column_terms(xi, a, b, k1, w.R, gic, gid, s_ic, s_id);
         }
-        if (inc) record_changes(w, term && terms_changed(ao, bo, so, a, b, k1, w.R), m, ao, bo, so, a, b, k1);
+        if (inc) record_changes(w, &st->chg_n, term && terms_changed(ao, bo, so, a, b, k1, w.R), m, ao, bo, so, a, b, k1);
     }
     __syncthreads();
     const int nq = min(s_qn, kRefQ);   // no thread changes the count after the barrier
-    if (nq > 0) refresh_rescans(w, cost, s_open, s_q, nq, s_lc, s_ld, v0c, v0d, rowi, gic, gid, s_ic, s_id);
+    if (nq > 0)
+        refresh_rescans(
+            w, cost, s_open, s_q, nq, rowi, gic, gid, s_ic, s_id,
+            [&](int a, int b, int k1) { mission_terms(a, b, w.R, v0c, v0d, s_lc, s_ld, k1); },
+            [&](bool ch, int m, int ao, int bo, int so, int an, int bn, int sn) {
+                record_changes(w, &st->chg_n, ch, m, ao, bo, so, an, bn, sn);
+            });
     if (inc) {
         // the other terms stay; the closed base's column goes out
         block_sum2<256>(gic, gid);
@@ -2119,26 +1450,7 @@ constexpr int kDeltaBatch = 8;     // cost loads in flight per thread
 
 bool swap_delta_fits(int K) { return K <= kPipeMaxK; }
 
-// One run of extra terms of one row at one slot, added when the slot changes.
-struct DeltaRun {
-    int s, c;
-    long long d;
-};
 
-__device__ __forceinline__ void delta_run_add(DeltaRun &run, int s, int c, int d, const TabuBuffers &w, int j)
-{
-    if (s != run.s) {
-        if (run.s >= 0 && (run.c | (run.d != 0))) {
-            atomicAdd(&w.extra_c[(size_t)run.s * w.B + j], run.c);
-            atomicAdd(&w.extra_d[(size_t)run.s * w.B + j], (unsigned long long)run.d);
-        }
-        run.s = s;
-        run.c = 0;
-        run.d = 0;
-    }
-    run.c += c;
-    run.d += d;
-}
 
 // Thread = one position p of the mission-major copy, i.e. base border[p]
 // (every base but the one the move closed: a column that is not a
@@ -2217,7 +1529,7 @@ cudaError_t launch_swap_delta(const TabuBuffers &w, cudaStream_t s)
     const int gx = (w.ldT + kDeltaRows - 1) / kDeltaRows;
     // about two waves of resident blocks over the record chunks (their count
     // is known only on the device), no more than the missions could fill
-    const int sms = g_num_sms > 0 ? g_num_sms : 152;
+    const int sms = sm_count();
     const int max_y = (w.M + kDeltaChunk - 1) / kDeltaChunk;
     int gy = (2 * 6 * sms + gx - 1) / gx;
     if (gy > max_y) gy = max_y;
@@ -3010,13 +2322,18 @@ __global__ void k_group_swap(const GroupSlot *__restrict__ slots, const int2 *__
 __global__ void k_tabu_small(TabuBuffers w, const int32_t *__restrict__ cost, int iters);
 __global__ void k_tabu_resident(TabuBuffers w, const int32_t *__restrict__ cost, int iters);
 
+// Function attributes (dynamic shared memory limits) and the SM count, once
+// per device: later calls on an initialised device return at once.
 cudaError_t kernels_init()
 {
-    cudaError_t e = cudaFuncSetAttribute(k_swap_eval<kSwapJ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)(STAGE_MAX_K * kSwapJ * 12));
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_swap_stream, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)swap_stream_smem(kPipeMaxK));
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(g_init_mu);
+    if (g_sms_of[dev] > 0) return cudaSuccess;
+    e = cudaFuncSetAttribute(k_swap_eval<kSwapJ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(STAGE_MAX_K * kSwapJ * 12));
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(k_swap_direct<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)swap_direct_smem(kPipeMaxK));
@@ -3035,12 +2352,12 @@ cudaError_t kernels_init()
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(k_tabu_resident, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kResMaxSmem);
     if (e != cudaSuccess) return e;
-    if (const char *v = getenv("STAGE_SWAP_VARIANT")) g_swap_variant = atoi(v);
-    int dev = 0, n = 0;
-    e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    e = persist_init();
     if (e != cudaSuccess) return e;
-    g_num_sms = n;
+    int n = 0;
+    e = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    g_sms_of[dev] = n;
     return cudaSuccess;
 }
 
@@ -3066,7 +2383,7 @@ int group_swap_blocks(int M_pad, int nC, int K, int seg_override, int *bx, int *
 // every slot keeps its own choice).
 int group_common_segment(const int *M_pad, const int *nC, int n)
 {
-    const long long target = 2ll * 4 * (g_num_sms > 0 ? g_num_sms : 152);
+    const long long target = 2ll * 4 * sm_count();
     for (int seg = 16384; seg >= 1024; seg >>= 1) {
         long long total = 0;
         for (int k = 0; k < n; k++)

@@ -59,30 +59,44 @@ size_t layout(unsigned char *base, int K, int B, int M_pad, TabuBuffers &tb)
 
 // One block: copy the placement, list the closed available bases in ascending
 // order, clear the accumulators and the state.  Earlier calls' contents are
-// overwritten here, so nothing stale survives into this call.
+// overwritten here, so nothing stale survives into this call.  A placement
+// with an id outside [0, B), a repeated id or an unavailable base is refused
+// on the device: every slot is pointed at base 0 (so the per-mission pass
+// reads inside the table), the candidate list is left empty and the state's
+// err word is set, so no objective is written and the outputs keep the -1
+// the call filled them with.
 __global__ void k_noalloc_prepare(TabuBuffers w, const int32_t *__restrict__ open,
                                   const uint8_t *__restrict__ avail)
 {
-    __shared__ uint8_t is_open[STAGE_NOALLOC_MAX_BASES];
-    __shared__ int s_count;
+    __shared__ unsigned is_open[(STAGE_NOALLOC_MAX_BASES + 31) / 32];
+    __shared__ int s_count, s_bad;
     const int B = w.B, K = w.K;
-    for (int b = threadIdx.x; b < B; b += blockDim.x) is_open[b] = 0;
-    if (threadIdx.x == 0) s_count = 0;
+    for (int q = threadIdx.x; q < (B + 31) / 32; q += blockDim.x) is_open[q] = 0;
+    if (threadIdx.x == 0) {
+        s_count = 0;
+        s_bad = 0;
+    }
     __syncthreads();
     for (int k = threadIdx.x; k < K; k += blockDim.x) {
         const int o = open[k];
-        w.open[k] = o;
-        if (o >= 0 && o < B) is_open[o] = 1;
+        bool bad = o < 0 || o >= B;
+        if (!bad) {
+            const unsigned bit = 1u << (o & 31);
+            bad = (atomicOr(&is_open[o >> 5], bit) & bit) != 0 || (avail != nullptr && avail[o] == 0);
+        }
+        if (bad) s_bad = 1;
         w.loss_c[k] = 0;
         w.loss_d[k] = 0;
     }
     __syncthreads();
+    const bool bad = s_bad != 0;
+    for (int k = threadIdx.x; k < K; k += blockDim.x) w.open[k] = bad ? 0 : open[k];
     // ordered compaction, one warp-sized chunk of bases at a time
     const int lane = threadIdx.x & 31;
-    if (threadIdx.x < 32) {
+    if (threadIdx.x < 32 && !bad) {
         for (int b0 = 0; b0 < B; b0 += 32) {
             const int b = b0 + lane;
-            const bool take = b < B && !is_open[b] && (avail == nullptr || avail[b] != 0);
+            const bool take = b < B && !((is_open[b >> 5] >> (b & 31)) & 1u) && (avail == nullptr || avail[b] != 0);
             const unsigned mask = __ballot_sync(0xffffffffu, take);
             if (take) w.cand[s_count + __popc(mask & ((1u << lane) - 1u))] = b;
             __syncwarp();
@@ -106,6 +120,7 @@ __global__ void k_noalloc_prepare(TabuBuffers w, const int32_t *__restrict__ ope
         memset(&st, 0, sizeof st);
         st.nC = s_count;
         st.best_iter = -1;
+        st.err = bad ? kErrBadSlot : 0;
         *w.st = st;
     }
 }
@@ -167,6 +182,13 @@ extern "C" stage_status stage_evaluate_swaps_noalloc(const int32_t *cost, int32_
                 snprintf(msg, sizeof msg, "cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
                 return fail(errbuf, errlen, STAGE_ERR_CUDA, msg);
             }
+            // function attributes and the SM count, once per device
+            e = kernels_init();
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                snprintf(msg, sizeof msg, "kernel set-up failed: %s", cudaGetErrorString(e));
+                return fail(errbuf, errlen, STAGE_ERR_CUDA, msg);
+            }
             g_scratch_addr[dev] = static_cast<unsigned char *>(p);
         }
         base = g_scratch_addr[dev];
@@ -179,8 +201,7 @@ extern "C" stage_status stage_evaluate_swaps_noalloc(const int32_t *cost, int32_
     tb.R = R;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const size_t n = (size_t)K * B;
-    cudaError_t e = kernels_init();
-    if (e == cudaSuccess) e = cudaMemsetAsync(out_cov, 0xff, n * 8, s);
+    cudaError_t e = cudaMemsetAsync(out_cov, 0xff, n * 8, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(out_dist, 0xff, n * 8, s);
     if (e == cudaSuccess) {
         k_noalloc_prepare<<<1, 1024, 0, s>>>(tb, open, base_available);

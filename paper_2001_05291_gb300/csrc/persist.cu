@@ -1,0 +1,907 @@
+// Persistent Tabu search over the incremental neighbourhood (Alg. 3's outer
+// loop on the device): one cooperative launch runs every iteration of a
+// search, its CTAs resident on their SMs and meeting at three grid-wide
+// barriers per iteration.
+//
+// Missions are owned in blocks of kBlockMissions consecutive columns (the
+// table's columns are in a spatial order), block q by CTA q mod G: a move's
+// work -- the missions it touches lie near the bases it exchanges -- spreads
+// over every CTA, and each CTA's share stays spatially coherent.
+//
+// One iteration, for the move u:
+//   barrier A   every CTA has published its best admissible and best overall
+//               key over its share of the swaps; each CTA reduces the same
+//               keys to the same move and applies it to its copy of the
+//               placement, candidate list and tabu expiries (a5, a6);
+//   refresh     each CTA updates the best / second-best state of its missions
+//               (a7), records those whose terms changed, adds their changes of
+//               V0 and loss (kept across moves like gain and extra) and every
+//               mission's terms of the closed base's column to a few global
+//               sums, and appends its records to the move's list (one atomic
+//               per CTA: each CTA's records stay together, in spatial order);
+//   barrier B   the list is complete;
+//   update      each CTA takes an equal contiguous share of the list (the
+//               records lie near the move, so a CTA's own would leave most
+//               CTAs idle) and moves each one's old terms out of, and its new
+//               terms into, every other base's column (a4), streaming the
+//               records' rows of the mission-major table copy through a
+//               shared-memory ring; a thread holds two bases
+//               (the copy's bases are in spatial order, so the bases near a
+//               record share warps and the others pass it with one compare);
+//               gain terms add up in registers, extra terms in runs of one
+//               slot (consecutive records share slots), flushed to the global
+//               columns with atomics;
+//   barrier C   the columns are complete; each CTA scores its share of the
+//               swaps F(s, j) = V0 + gain[j] + loss[s] + extra[s][j] -- the
+//               closed base's column taken from the refresh's sums, which CTA
+//               0 also writes back -- for the next move.
+//
+// The terms are integers, so the columns equal what a full pass over the
+// table would give for each new placement (the fast-interchange
+// decomposition of Whitaker 1983 / Resende and Werneck 2007, kept across
+// moves), and every move is the one the oracle chooses.
+//
+// Sums that one step fills and a later one reads are double-buffered by move
+// parity (V0 / loss, the closed column, the list's length), each reset by CTA
+// 0 in a phase where no CTA reads or writes it (V0 / loss to the previous
+// move's values, the others to zero).  The grid barriers give up after the
+// context's spin limit: the CTA sets an error word and leaves the loop, the
+// others give up at their next barrier, and the host reports STAGE_ERR_TIMEOUT.
+#include <cuda_runtime.h>
+
+#include <climits>
+#include <stdint.h>
+
+#include "stage_internal.h"
+#include "device_common.cuh"
+
+namespace stg {
+
+constexpr int kPerThreads = 1024;
+constexpr int kPerWarps = kPerThreads / 32;
+constexpr int kBlockMissions = 256;    // missions per ownership block (8 warp chunks)
+constexpr int kStageRecs = 4;          // records (table-copy rows) per ring stage
+constexpr int kRing = 4;               // ring stages (kRing - 1 in flight while one is read)
+constexpr int kColCap = 4096;          // record columns staged in shared memory per round
+constexpr int kMaxLd = 2 * kPerThreads;   // table-copy row: two bases per thread
+constexpr size_t kPerSmemLimit = 220 * 1024;
+
+// Per-CTA clocks (ns, summed over the search): choosing and applying the move,
+// the refresh, the wait at the barrier after it, the update, the wait at the
+// barrier after it, the selection, the wait at the barrier before the next
+// move; the first seven cover the whole time, the others split the refresh
+// and the update.
+enum : int {
+    kClkMove = 0, kClkRefresh, kClkWaitB, kClkUpdate, kClkWaitC, kClkSelect, kClkWaitA,
+    // parts of the refresh and the update (thread 0's view; the update's
+    // compute includes the wait for the CTA's slowest warp)
+    kClkRefLoop, kClkRefRescan, kClkRefSums, kClkUpdIssue, kClkUpdWait, kClkUpdCompute, kClocks
+};
+static_assert(kClocks == kPersistClocks, "clock layout shared with the host");
+
+__device__ __forceinline__ long long gtimer()
+{
+    long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Records (two int4 per mission whose terms changed), clamped at R + 1 as the
+// terms use them: (column, hi = max(old b, new b), old a, old b),
+// (old slot, new a, new b, new slot).  No term of a base with cost >= hi changes.
+
+// Shared-memory layout (byte offsets).
+struct PerLayout {
+    size_t ring, meta, colv, cand, expiry, cidx, open, lc, ic, ld, id, lossc, lossd, q, total;
+};
+
+__host__ __device__ inline size_t per_align(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+__host__ __device__ inline PerLayout per_layout(int K, int B, int ldT)
+{
+    PerLayout L{};
+    size_t o = 0;
+    L.ring = o;   o = per_align(o + (size_t)kRing * kStageRecs * ldT * 4, 128);
+    L.meta = o;   o = per_align(o + (size_t)kRing * kStageRecs * 32, 16);
+    L.colv = o;   o = per_align(o + (size_t)kColCap * 4, 16);
+    L.cand = o;   o = per_align(o + (size_t)B * 4, 16);
+    L.expiry = o; o = per_align(o + (size_t)B * 4, 16);
+    L.cidx = o;   o = per_align(o + (size_t)B * 4, 16);
+    L.open = o;   o = per_align(o + (size_t)K * 4, 16);
+    L.lc = o;     o = per_align(o + (size_t)K * 4, 16);
+    L.ic = o;     o = per_align(o + (size_t)K * 4, 16);
+    L.ld = o;     o = per_align(o + (size_t)K * 8, 16);
+    L.id = o;     o = per_align(o + (size_t)K * 8, 16);
+    L.lossc = o;  o = per_align(o + (size_t)K * 8, 16);
+    L.lossd = o;  o = per_align(o + (size_t)K * 8, 16);
+    L.q = o;      o = per_align(o + (size_t)kRefQ * 4, 16);
+    L.total = o;
+    return L;
+}
+
+// ---------------------------------------------------------------- primitives
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p)
+{
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Poll *flag until it differs from `seen`; false after `limit` polls.
+__device__ __forceinline__ bool wait_change(const unsigned *flag, unsigned seen, long long limit)
+{
+    for (long long k = 0; k < limit; k++) {
+        if (ld_acquire_u32(flag) != seen) return true;
+        if (k > 64) __nanosleep(64);
+    }
+    return false;
+}
+
+// Grid-wide barrier (the launch is cooperative, so every CTA is resident).
+// Arrivals count up without reset: barrier number g (from 0) is passed once
+// the count reaches gridDim.x * (g + 1).  Thread 0 of each CTA adds its
+// arrival with release semantics (the CTA's writes, ordered before it by the
+// CTA barrier, become visible first) and polls the count with acquire loads,
+// at most `limit` times, then sets the timeout bit in *err and gives up.
+// Returns false when this CTA gave up or another CTA has reported an error:
+// the caller then leaves the loop.  (The count wraps after 2^32 arrivals:
+// 9 million iterations of three barriers on 152 CTAs.)
+__device__ __forceinline__ bool grid_sync(unsigned *bar, unsigned &gen, long long limit, int *err)
+{
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        const unsigned target = gridDim.x * (gen + 1u);
+        unsigned old;
+        asm volatile("atom.add.release.gpu.global.u32 %0, [%1], 1;" : "=r"(old) : "l"(bar) : "memory");
+        if (old + 1u != target) {
+            ok = 0;
+            for (long long k = 0; k < limit; k++) {
+                if ((int)(ld_acquire_u32(bar) - target) >= 0) {
+                    ok = 1;
+                    break;
+                }
+                if (k > 256) __nanosleep(32);
+            }
+            if (!ok) atomicOr(err, kErrPipelineTimeout);
+        }
+        if (ok && *reinterpret_cast<volatile int *>(err) != 0) ok = 0;
+        s_ok = ok;
+    }
+    __syncthreads();
+    gen += 1u;
+    return s_ok != 0;
+}
+
+__device__ __forceinline__ void cp_async16(void *dst, const void *src, unsigned long long policy)
+{
+    asm volatile("cp.async.cg.shared.global.L2::cache_hint [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)), "l"(src),
+                 "l"(policy)
+                 : "memory");
+}
+
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+
+template <int N>
+__device__ __forceinline__ void cp_async_wait()
+{
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// Add (c, d) into the shared per-slot sums of the lanes with `has`: lanes
+// with the same slot are summed first, one atomic per slot per warp.  Every
+// lane of the warp calls it; |d| < 2^31 (as group_sum_small needs).
+__device__ __forceinline__ void slot_add_warp(bool has, int slot, int c, long long d, int *s_c,
+                                              unsigned long long *s_d)
+{
+    const unsigned full = 0xffffffffu;
+    if (!__ballot_sync(full, has)) return;
+    const unsigned peers = __match_any_sync(full, has ? slot : -1);
+    const int sc = (int)__reduce_add_sync(peers, has ? (unsigned)c : 0u);
+    const long long sd = group_sum_small(peers, has ? d : 0ll);
+    if (has && (int)(threadIdx.x & 31) == __ffs(peers) - 1 && (sc | (sd != 0))) {
+        atomicAdd(&s_c[slot], sc);
+        atomicAdd(&s_d[slot], (unsigned long long)sd);
+    }
+}
+
+// ---------------------------------------------------------------- kernel
+
+struct PersistArgs {
+    TabuBuffers w;                  // search buffers; costT, border, ldT set
+    const int32_t *cost;            // the table, row-major
+    unsigned long long *acc;        // [2][2 + 2K]: V0 (covered, distance), loss_c[K], loss_d[K]
+    unsigned long long *col;        // [2][2 + 2K]: closed column: gain (c, d), extra_c[K], extra_d[K]
+    MoveKey *part;                  // [2 * gridDim.x] best admissible, best overall per CTA
+    unsigned *bar;                  // arrivals at the grid barriers
+    int *err;                       // error word (kErr*)
+    long long *info;                // [2] CTAs, records over the search
+    int *recn;                      // [2] length of the move's record list (w.chg)
+    long long *cta_ns;              // [gridDim.x][kClocks] per-CTA time of each step, ns
+    int4 *region;                   // [gridDim.x * region_cap * 2] each CTA's records of a move
+    long long spin_limit;
+    int region_cap;                 // records per CTA region
+};
+
+// Search scalars, the same in every CTA (each applies the same moves).
+struct PerState {
+    long long cur_c, cur_d, best_c, best_d, v0c, v0d;
+    int t, n_moves, best_iter, done, mv_s, mv_i, mv_j, recn, rbase, qn, prev_i;
+};
+
+// The best admissible and best overall key over this CTA's share of the
+// K x nC swaps, for the placement of iteration st.t.  The base closed by the
+// previous move (st.prev_i, -1 at the start) takes its column from the
+// refresh's sums `cl`.
+__device__ __forceinline__ void persist_select(const TabuBuffers &w, const PerState &st, int nC, const int *s_open,
+                                               const int *s_cand, const int *s_exp, const long long *lossc,
+                                               const long long *lossd, const unsigned long long *cl, MoveKey &adm,
+                                               MoveKey &all)
+{
+    const int K = w.K, t = st.t;
+    const int total = K * nC;   // K <= 256, nC <= 2048
+    const int q0 = (int)((long long)total * blockIdx.x / gridDim.x);
+    const int q1 = (int)((long long)total * (blockIdx.x + 1) / gridDim.x);
+    for (int q = q0 + (int)threadIdx.x; q < q1; q += kPerThreads) {
+        const int s = q / nC, c = q - s * nC;
+        const int i = s_open[s], j = s_cand[c];
+        long long gc, gd, ec, ed;
+        if (j == st.prev_i) {
+            gc = (long long)__ldcg(&cl[0]);
+            gd = (long long)__ldcg(&cl[1]);
+            ec = (long long)__ldcg(&cl[2 + s]);
+            ed = (long long)__ldcg(&cl[2 + K + s]);
+        } else {
+            const size_t sj = (size_t)s * w.B + j;
+            gc = __ldcg(&w.gain_c[j]);
+            gd = (long long)__ldcg(&w.gain_d[j]);
+            ec = __ldcg(&w.extra_c[sj]);
+            ed = (long long)__ldcg(&w.extra_d[sj]);
+        }
+        MoveKey k;
+        k.cov = st.v0c + gc + lossc[s] + ec;
+        k.dist = st.v0d + gd + lossd[s] + ed;
+        k.i = i; k.j = j; k.s = s; k.c = c; k.valid = 1;
+        k.tabu = (t < s_exp[i]) || (t < s_exp[j]);
+        if (key_better(k, all)) all = k;
+        if ((!k.tabu || obj_better(k.cov, k.dist, st.best_c, st.best_d)) && key_better(k, adm)) adm = k;
+    }
+}
+
+__global__ void __launch_bounds__(kPerThreads, 1) k_tabu_persist(PersistArgs A)
+{
+    const TabuBuffers &w = A.w;
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int K = w.K, B = w.B, R = w.R, ldT = w.ldT;
+    const PerLayout L = per_layout(K, B, ldT);
+    int32_t *ring = reinterpret_cast<int32_t *>(smem + L.ring);
+    int4 *smeta = reinterpret_cast<int4 *>(smem + L.meta);
+    int *s_colv = reinterpret_cast<int *>(smem + L.colv);
+    int *s_cand = reinterpret_cast<int *>(smem + L.cand);
+    int *s_exp = reinterpret_cast<int *>(smem + L.expiry);
+    int *s_cidx = reinterpret_cast<int *>(smem + L.cidx);
+    int *s_open = reinterpret_cast<int *>(smem + L.open);
+    int *s_lc = reinterpret_cast<int *>(smem + L.lc);
+    int *s_ic = reinterpret_cast<int *>(smem + L.ic);
+    unsigned long long *s_ld = reinterpret_cast<unsigned long long *>(smem + L.ld);
+    unsigned long long *s_id = reinterpret_cast<unsigned long long *>(smem + L.id);
+    long long *s_lossc = reinterpret_cast<long long *>(smem + L.lossc);
+    long long *s_lossd = reinterpret_cast<long long *>(smem + L.lossd);
+    int *s_q = reinterpret_cast<int *>(smem + L.q);
+    __shared__ MoveKey s_adm[kPerWarps], s_all[kPerWarps];
+    __shared__ PerState S;
+    __shared__ long long s_clk[kClocks + 1];
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const bool lead_cta = blockIdx.x == 0;
+    const int nA = 2 + 2 * K;
+    TabuDevState *st = w.st;
+    const int t_end = st->t_end, tenure = st->tenure, aw = st->accept_worsening, nC = st->nC;
+    const int traj_cap = st->traj_cap;
+    int4 *region = A.region + (size_t)blockIdx.x * A.region_cap * 2;
+    // the update: this thread's two bases (positions tid and tid + 1024 of
+    // the table copy; -1 past the copy's bases)
+    const int j1 = tid < ldT ? w.border[tid] : -1;
+    const int j2 = tid + kPerThreads < ldT ? w.border[tid + kPerThreads] : -1;
+    long long rec_total = 0;   // records of this CTA over the search
+
+    if (tid == 0) {
+        S.t = st->t;
+        S.n_moves = st->n_moves;
+        S.best_iter = st->best_iter;
+        S.done = 0;
+        S.mv_s = st->mv_s; S.mv_i = st->mv_i; S.mv_j = st->mv_j;
+        S.prev_i = -1;
+        S.cur_c = st->cur_cov; S.cur_d = st->cur_dist;
+        S.best_c = st->best_cov; S.best_d = st->best_dist;
+        const unsigned long long *acc = A.acc + (size_t)(S.t & 1) * nA;
+        S.v0c = (long long)acc[0];
+        S.v0d = (long long)acc[1];
+        for (int k = 0; k < kClocks; k++) s_clk[k] = 0;
+        s_clk[kClocks] = gtimer();
+    }
+    for (int k = tid; k < K; k += kPerThreads) {
+        s_open[k] = w.open[k];
+        const unsigned long long *acc = A.acc + (size_t)(st->t & 1) * nA;
+        s_lossc[k] = (long long)acc[2 + k];
+        s_lossd[k] = (long long)acc[2 + K + k];
+    }
+    for (int b = tid; b < B; b += kPerThreads) {
+        s_exp[b] = w.expiry[b];
+        s_cidx[b] = -1;
+    }
+    __syncthreads();
+    for (int c = tid; c < nC; c += kPerThreads) {
+        const int b = w.cand[c];
+        s_cand[c] = b;
+        s_cidx[b] = c;
+    }
+    __syncthreads();
+    unsigned gen = 0;
+    const unsigned long long evict_first = evict_first_policy();
+    __shared__ long long s_sub;   // thread 0: the last mark inside a step
+    auto lap = [&](int which) {
+        if (tid == 0) {
+            const long long now = gtimer();
+            s_clk[which] += now - s_clk[kClocks];
+            s_clk[kClocks] = now;
+            s_sub = now;
+        }
+    };
+    auto sub = [&](int which) {
+        if (tid == 0) {
+            const long long now = gtimer();
+            s_clk[which] += now - s_sub;
+            s_sub = now;
+        }
+    };
+    // the scores of this CTA's share of the swaps for the move of iteration
+    // S.t; CTA 0 also prepares the sums that move's refresh fills, and writes
+    // the previous move's closed column back
+    auto select = [&]() {
+        const int u = S.t;
+        const unsigned long long *clp = A.col + (size_t)((u + 1) & 1) * nA;   // the previous move's sums
+        if (lead_cta) {
+            unsigned long long *nx = A.acc + (size_t)((u + 1) & 1) * nA;
+            const unsigned long long *cu = A.acc + (size_t)(u & 1) * nA;
+            unsigned long long *cl = A.col + (size_t)(u & 1) * nA;
+            for (int k = tid; k < nA; k += kPerThreads) {
+                nx[k] = __ldcg(&cu[k]);   // V0 and loss go on from this placement's
+                cl[k] = 0;
+            }
+            if (tid == 0) A.recn[u & 1] = 0;
+        }
+        MoveKey adm = invalid_key(), all = invalid_key();
+        persist_select(w, S, nC, s_open, s_cand, s_exp, s_lossc, s_lossd, clp, adm, all);
+        block_best2<kPerThreads>(adm, all, s_adm, s_all);
+        if (tid == 0) {
+            A.part[2 * blockIdx.x] = adm;
+            A.part[2 * blockIdx.x + 1] = all;
+        }
+        if (lead_cta && S.prev_i >= 0) {
+            // the closed column, now in the sums, into the global columns
+            // (every CTA reads it from the sums until the next barrier)
+            const int ip = S.prev_i;
+            if (tid == 0) {
+                w.gain_c[ip] = (int)(long long)__ldcg(&clp[0]);
+                w.gain_d[ip] = __ldcg(&clp[1]);
+            }
+            for (int k = tid; k < K; k += kPerThreads) {
+                w.extra_c[(size_t)k * B + ip] = (int)(long long)__ldcg(&clp[2 + k]);
+                w.extra_d[(size_t)k * B + ip] = __ldcg(&clp[2 + K + k]);
+            }
+        }
+        lap(kClkSelect);
+    };
+
+    select();   // the first move's keys
+
+    while (S.t < t_end) {   // S.t is read after a CTA barrier on every path: the same on every thread
+        if (!grid_sync(A.bar, gen, A.spin_limit, A.err)) break;
+        lap(kClkWaitA);
+        const int u = S.t;   // the move of this iteration
+        // ------------------------------------------------ choose and apply the move (a5, a6)
+        MoveKey adm = invalid_key(), all = invalid_key();
+        for (int b = tid; b < (int)gridDim.x; b += kPerThreads) {
+            const MoveKey pa = load_key_cg(&A.part[2 * b]), px = load_key_cg(&A.part[2 * b + 1]);
+            if (key_better(pa, adm)) adm = pa;
+            if (key_better(px, all)) all = px;
+        }
+        block_best2<kPerThreads>(adm, all, s_adm, s_all);
+        if (!all.valid) {
+            if (tid == 0) S.done = 1;   // no closed available base
+            break;
+        }
+        if (S.cur_c != S.v0c || S.cur_d != S.v0d) {
+            // the refresh's objective disagrees with the chosen move's
+            if (lead_cta && tid == 0) atomicOr(A.err, kErrObjectiveMismatch);
+            if (tid == 0) S.done = 1;
+            break;
+        }
+        const MoveKey Pm = adm.valid ? adm : all;
+        if (!aw && !obj_better(Pm.cov, Pm.dist, S.cur_c, S.cur_d)) {
+            if (tid == 0) S.done = 1;   // improving-only rule: no improving move
+            break;
+        }
+        __syncthreads();   // every thread has read S before thread 0 changes it
+        if (tid == 0) {
+            int flags = adm.valid ? (adm.tabu ? STAGE_MOVE_ASPIRATION : 0) : STAGE_MOVE_FALLBACK;
+            if (obj_better(Pm.cov, Pm.dist, S.best_c, S.best_d)) {
+                S.best_c = Pm.cov;
+                S.best_d = Pm.dist;
+                S.best_iter = u;
+                flags |= STAGE_MOVE_NEW_BEST;
+            }
+            S.cur_c = Pm.cov;
+            S.cur_d = Pm.dist;
+            S.mv_s = Pm.s; S.mv_i = Pm.i; S.mv_j = Pm.j;
+            s_open[Pm.s] = Pm.j;
+            s_cand[Pm.c] = Pm.i;
+            s_cidx[Pm.i] = Pm.c;
+            s_cidx[Pm.j] = -1;
+            s_exp[Pm.i] = u + tenure + 1;
+            s_exp[Pm.j] = u + tenure + 1;
+            if (lead_cta) {
+                if (S.n_moves < traj_cap) {
+                    stage_move mv;
+                    mv.iter = u; mv.i = Pm.i; mv.j = Pm.j; mv.flags = flags;
+                    mv.cov = Pm.cov; mv.dist = Pm.dist;
+                    w.traj[S.n_moves] = mv;
+                }
+                if (flags & STAGE_MOVE_NEW_BEST)
+                    for (int k = 0; k < K; k++) w.best_open[k] = s_open[k];
+            }
+            S.n_moves += 1;
+            S.recn = 0;
+            S.qn = 0;
+        }
+        for (int k = tid; k < K; k += kPerThreads) {
+            s_lc[k] = 0;
+            s_ld[k] = 0;
+            s_ic[k] = 0;
+            s_id[k] = 0;
+        }
+        __syncthreads();
+        lap(kClkMove);
+
+        const int ss = S.mv_s, jj = S.mv_j, ic = S.mv_i;
+        // ------------------------------------------------ refresh this CTA's missions (a7)
+        {
+            const size_t M_pad = w.M_pad;
+            const int32_t *rowj = A.cost + (size_t)jj * M_pad;
+            const int32_t *rowi = A.cost + (size_t)ic * M_pad;
+            long long gic = 0, gid = 0, rv0c = 0, rv0d = 0;
+            int *rcount = &S.recn;
+            // a changed mission: its record, in this CTA's region (clamped as
+            // the update reads it), and its change of V0 (f(a) new minus old)
+            // and of loss (f(b) - f(a) out of its old best slot, into its new
+            // one); every lane of the warp calls it
+            auto record = [&](bool ch, int m, int ao, int bo, int so, int an, int bn, int sn) {
+                const unsigned cm = __ballot_sync(0xffffffffu, ch);
+                if (!cm) return;
+                const int lead = __ffs(cm) - 1;
+                int q0 = 0;
+                if (lane == lead) q0 = atomicAdd(rcount, __popc(cm));
+                q0 = __shfl_sync(0xffffffffu, q0, lead);
+                int oc = 0, nc = 0;
+                long long od = 0, nd = 0;
+                if (ch) {
+                    const int ao1 = min(ao, R + 1), bo1 = min(bo, R + 1), an1 = min(an, R + 1), bn1 = min(bn, R + 1);
+                    int4 *r = region + 2 * (size_t)(q0 + __popc(cm & ((1u << lane) - 1u)));
+                    r[0] = make_int4(m, max(bo1, bn1), ao1, bo1);
+                    r[1] = make_int4(so, an1, bn1, sn);
+                    const int cao = ao1 <= R, cbo = bo1 <= R, can = an1 <= R, cbn = bn1 <= R;
+                    const long long fao = cao ? ao1 : 0, fbo = cbo ? bo1 : 0, fan = can ? an1 : 0,
+                                    fbn = cbn ? bn1 : 0;
+                    rv0c += can - cao;
+                    rv0d += fan - fao;
+                    oc = cbo - cao; od = fbo - fao;   // the old loss term, taken out
+                    nc = cbn - can; nd = fbn - fan;   // the new one
+                }
+                slot_add_warp(ch && (oc | (od != 0)), so, -oc, -od, s_lc, s_ld);
+                slot_add_warp(ch && (nc | (nd != 0)), sn, nc, nd, s_lc, s_ld);
+            };
+            // one chunk of 32 missions per warp step, values loaded beforehand.
+            // The search keeps each mission's best and second-best cost exact
+            // up to R and R + 1 above it (an uncovered cost adds no term, so no
+            // term depends on its value or its slot): a mission loses a base
+            // only if that base covered it, and only those are rescanned.
+            auto chunk = [&](int m, bool in, int a, int b, int k1, int k2, int x, int xi) {
+                bool term = false;
+                a = min(a, R + 1);
+                b = min(b, R + 1);
+                const bool lost = in && ((a <= R && k1 == ss) || (b <= R && k2 == ss));
+                const int ao = a, bo = b, so = k1;   // the state before the move
+                if (in && !lost) {
+                    const int x1 = min(x, R + 1);
+                    if (x1 < a || (x1 == a && a <= R && jj < s_open[k1])) {
+                        k2 = k1; b = a;
+                        k1 = ss; a = x1;
+                        w.a[m] = a; w.b[m] = b; w.s1[m] = (int16_t)k1; w.s2[m] = (int16_t)k2;
+                    } else if (x1 < b || (x1 == b && b <= R && jj < s_open[k2])) {
+                        k2 = ss; b = x1;
+                        w.b[m] = b; w.s2[m] = (int16_t)k2;
+                    }
+                    term = true;
+                }
+                // missions that lost their best or second best: rescanned by
+                // the whole CTA after the loop (past the queue's capacity, in place)
+                const unsigned lm = __ballot_sync(0xffffffffu, lost);
+                if (lm) {
+                    int q0 = 0;
+                    if (lane == __ffs(lm) - 1) q0 = atomicAdd(&S.qn, __popc(lm));
+                    q0 = __shfl_sync(0xffffffffu, q0, __ffs(lm) - 1);
+                    if (lost) {
+                        const int pos = q0 + __popc(lm & ((1u << lane) - 1u));
+                        if (pos < kRefQ) {
+                            s_q[pos] = m;
+                        } else {
+                            const int2 ab = refresh_scan_one(w, A.cost, m, s_open, k1);
+                            a = ab.x; b = ab.y;
+                            term = true;
+                        }
+                    }
+                }
+                if (term) closed_column_terms(xi, a, b, k1, R, gic, gid, s_ic, s_id);
+                record(term && terms_changed(ao, bo, so, a, b, k1, R), m, ao, bo, so, a, b, k1);
+            };
+            // this CTA's chunks: chunk r of block b is missions (b * CPB + r)
+            // * 32 .. +31, blocks blockIdx.x, + G, + 2G, ...; warp w takes the
+            // CTA's chunks w, w + 32, ..., kStep per step (their loads in
+            // flight together)
+            constexpr int CPB = kBlockMissions / 32;   // chunks per block
+            const int nch = (w.M + 31) >> 5;
+            const int G = gridDim.x;
+            const int nblk = (nch + CPB - 1) / CPB;
+            const int mine_blocks = nblk > (int)blockIdx.x ? (nblk - (int)blockIdx.x + G - 1) / G : 0;
+            const int mine_chunks = mine_blocks * CPB;
+            auto chunk_of = [&](int k) { return ((int)blockIdx.x + (k / CPB) * G) * CPB + (k % CPB); };
+            constexpr int kStep = 2;
+            for (int k = warp; k < mine_chunks; k += kStep * kPerWarps) {   // the same on every lane
+                int ch[kStep], mm[kStep], va[kStep], vb[kStep], v1[kStep], v2[kStep], vx[kStep], vxi[kStep];
+#pragma unroll
+                for (int e = 0; e < kStep; e++) {
+                    const int kk = k + e * kPerWarps;
+                    ch[e] = kk < mine_chunks ? chunk_of(kk) : nch;
+                    mm[e] = ch[e] * 32 + lane;
+                    const bool in = ch[e] < nch && mm[e] < w.M;
+                    va[e] = in ? w.a[mm[e]] : 0;
+                    vb[e] = in ? w.b[mm[e]] : 0;
+                    v1[e] = in ? w.s1[mm[e]] : 0;
+                    v2[e] = in ? w.s2[mm[e]] : 0;
+                    vx[e] = in ? __ldcs(rowj + mm[e]) : 0;
+                    vxi[e] = in ? __ldcs(rowi + mm[e]) : 0;
+                }
+#pragma unroll
+                for (int e = 0; e < kStep; e++)
+                    if (ch[e] < nch) chunk(mm[e], mm[e] < w.M, va[e], vb[e], v1[e], v2[e], vx[e], vxi[e]);
+            }
+            __syncthreads();
+            sub(kClkRefLoop);
+            const int nq = min(S.qn, kRefQ);   // no thread changes the count after the barrier
+            if (nq > 0)   // (their V0 and loss changes go with their records)
+                refresh_rescans(w, A.cost, s_open, s_q, nq, rowi, gic, gid, s_ic, s_id, [](int, int, int) {},
+                                record);
+            __syncthreads();
+            sub(kClkRefRescan);
+            // the sums: the changes of V0 and loss (into a copy of the last
+            // move's values), the closed base's column
+            unsigned long long *cl = A.col + (size_t)(u & 1) * nA;
+            unsigned long long *nxt = A.acc + (size_t)((u + 1) & 1) * nA;
+            block_sum2<kPerThreads>(gic, gid);
+            if (tid == 0) {
+                if (gic) atomicAdd(&cl[0], (unsigned long long)gic);
+                if (gid) atomicAdd(&cl[1], (unsigned long long)gid);
+            }
+            __syncthreads();
+            block_sum2<kPerThreads>(rv0c, rv0d);
+            if (tid == 0) {
+                if (rv0c) atomicAdd(&nxt[0], (unsigned long long)rv0c);
+                if (rv0d) atomicAdd(&nxt[1], (unsigned long long)rv0d);
+            }
+            if (tid == 0) S.rbase = atomicAdd(&A.recn[u & 1], S.recn);   // this CTA's place in the list
+            for (int k = tid; k < K; k += kPerThreads) {
+                if (s_ic[k]) atomicAdd(&cl[2 + k], (unsigned long long)(long long)s_ic[k]);
+                if (s_id[k]) atomicAdd(&cl[2 + K + k], s_id[k]);
+                if (s_lc[k]) atomicAdd(&nxt[2 + k], (unsigned long long)(long long)s_lc[k]);
+                if (s_ld[k]) atomicAdd(&nxt[2 + K + k], s_ld[k]);
+            }
+            __syncthreads();   // the records, their count and their place are known
+            const int nr = S.recn, rb = S.rbase;
+            for (int q = tid; q < 2 * nr; q += kPerThreads) w.chg[2 * (size_t)rb + q] = region[q];
+            __syncthreads();
+            sub(kClkRefSums);
+        }
+        lap(kClkRefresh);
+        if (!grid_sync(A.bar, gen, A.spin_limit, A.err)) break;
+        lap(kClkWaitB);
+
+        // ------------------------------------------------ update every column with this CTA's records (a4)
+        {
+            // This CTA's share of the list: records r0 .. r0+n-1, taken in
+            // rounds of at most kColCap records whose columns are first read
+            // into shared memory (so that no copy waits on a load).  The ring:
+            // stage k of a round holds its records k*kStageRecs ..
+            // +kStageRecs-1, each one's full row of the table copy (ldT costs)
+            // and the record itself.  Step k (from -(kRing-1)): thread tid
+            // copies 16-byte pieces tid and tid + 1024 of stage k + kRing - 1
+            // (piece p is record p / (ldT / 4), offset p % (ldT / 4)) and,
+            // below 2 kStageRecs, one record half; then every copy of step
+            // k - kRing + 1 -- stage k -- has landed (kRing - 1 steps stay in
+            // flight).  The table copy is read once per move: evict-first in L2.
+            const int ntot = min(__ldcg(&A.recn[u & 1]), w.M);
+            const int r0 = (int)((long long)ntot * blockIdx.x / gridDim.x);
+            const int nshare = (int)((long long)ntot * (blockIdx.x + 1) / gridDim.x) - r0;
+            if (lead_cta) rec_total += ntot;
+            const int qpr = ldT >> 2;   // 16-byte pieces per row
+            static_assert(kStageRecs * (kMaxLd / 4) <= 2 * kPerThreads, "two pieces per thread per stage");
+            const int pr1 = tid / qpr, pr2 = (tid + kPerThreads) / qpr;
+            const bool pc1 = tid < kStageRecs * qpr, pc2 = tid + kPerThreads < kStageRecs * qpr;
+            const int off1 = tid - pr1 * qpr, off2 = tid + kPerThreads - pr2 * qpr;
+            const bool m1 = j1 >= 0 && j1 != ic, m2 = j2 >= 0 && j2 != ic;
+            long long gd1 = 0, gd2 = 0;
+            int gc1 = 0, gc2 = 0;
+            DeltaRun rn1{-1, 0, 0}, ro1{-1, 0, 0}, rn2{-1, 0, 0}, ro2{-1, 0, 0};
+            for (int base = 0; base < nshare; base += kColCap) {   // the same on every thread
+                const int n = min(kColCap, nshare - base);
+                const int4 *list = w.chg + 2 * (size_t)(r0 + base);
+                __syncthreads();   // the previous round's columns are used
+                for (int q = tid; q < n; q += kPerThreads) s_colv[q] = __ldcg(&list[2 * (size_t)q].x);
+                __syncthreads();
+                const int nst = (n + kStageRecs - 1) / kStageRecs;
+                for (int k = -(kRing - 1); k < nst; k++) {   // the same on every thread
+                    sub(kClkUpdCompute);
+                    const int ks = k + kRing - 1;
+                    if (ks < nst) {
+                        const int sg = ks % kRing;
+                        int32_t *dst = ring + (size_t)sg * kStageRecs * ldT;
+                        const int ra = ks * kStageRecs + pr1, rb = ks * kStageRecs + pr2;
+                        if (pc1 && ra < n)
+                            cp_async16(dst + (size_t)pr1 * ldT + 4 * off1,
+                                       w.costT + (size_t)s_colv[ra] * ldT + 4 * off1, evict_first);
+                        if (pc2 && rb < n)
+                            cp_async16(dst + (size_t)pr2 * ldT + 4 * off2,
+                                       w.costT + (size_t)s_colv[rb] * ldT + 4 * off2, evict_first);
+                        if (tid < 2 * kStageRecs) {
+                            const int rec = ks * kStageRecs + (tid >> 1);
+                            if (rec < n)
+                                cp_async16(smeta + (size_t)sg * 2 * kStageRecs + tid,
+                                           list + 2 * (size_t)rec + (tid & 1), evict_first);
+                        }
+                    }
+                    cp_async_commit();
+                    sub(kClkUpdIssue);
+                    cp_async_wait<kRing - 1>();
+                    __syncthreads();   // every thread's copies of stage k have landed
+                    sub(kClkUpdWait);
+                    if (k >= 0) {
+                        const int sg = k % kRing;
+                        const int32_t *rows = ring + (size_t)sg * kStageRecs * ldT;
+                        const int4 *meta = smeta + (size_t)sg * 2 * kStageRecs;
+                        // every record's costs and threshold first (independent
+                        // loads), then the records with a term
+                        int xa[kStageRecs], xb[kStageRecs], hv[kStageRecs];
+#pragma unroll
+                        for (int v = 0; v < kStageRecs; v++) {
+                            const bool valid = k * kStageRecs + v < n;
+                            xa[v] = m1 ? rows[v * ldT + tid] : INT_MAX;
+                            xb[v] = m2 ? rows[v * ldT + tid + kPerThreads] : INT_MAX;
+                            hv[v] = valid ? reinterpret_cast<const int *>(meta)[8 * v + 1] : INT_MIN;
+                        }
+#pragma unroll
+                        for (int v = 0; v < kStageRecs; v++) {
+                            const int hi = hv[v];
+                            if (min(xa[v], xb[v]) >= hi) continue;   // no term in either state (a <= b)
+                            const int4 q0 = meta[2 * v];       // (column, hi, old a, old b)
+                            const int4 q1 = meta[2 * v + 1];   // (old slot, new a, new b, new slot)
+                            const int ao = q0.z, bo = q0.w, so = q1.x, an = q1.y, bn = q1.z, sn = q1.w;
+                            const int cao = ao <= R, cbo = bo <= R, can = an <= R, cbn = bn <= R;
+                            auto terms = [&](int x, int j, int &gc, long long &gd, DeltaRun &rn, DeltaRun &ro) {
+                                if (x >= hi) return;
+                                if (x < an) { gc += 1 - can; gd += (long long)x - (can ? an : 0); }
+                                if (x < ao) { gc -= 1 - cao; gd -= (long long)x - (cao ? ao : 0); }
+                                if (x < bn) {
+                                    const int nc = can - cbn, nd = (can ? max(x, an) : 0) - (cbn ? bn : 0);
+                                    if (nc | nd) delta_run_add(rn, sn, nc, nd, w, j);
+                                }
+                                if (x < bo) {
+                                    const int oc = cao - cbo, od = (cao ? max(x, ao) : 0) - (cbo ? bo : 0);
+                                    if (oc | od) delta_run_add(ro, so, -oc, -od, w, j);
+                                }
+                            };
+                            terms(xa[v], j1, gc1, gd1, rn1, ro1);
+                            terms(xb[v], j2, gc2, gd2, rn2, ro2);
+                        }
+                    }
+                    __syncthreads();   // stage k is read: later copies may go there
+                }
+            }
+            cp_async_wait<0>();
+            sub(kClkUpdCompute);
+            if (m1) {
+                delta_run_add(rn1, -1, 0, 0, w, j1);   // flush
+                delta_run_add(ro1, -1, 0, 0, w, j1);
+                if (gc1) atomicAdd(&w.gain_c[j1], gc1);
+                if (gd1) atomicAdd(&w.gain_d[j1], (unsigned long long)gd1);
+            }
+            if (m2) {
+                delta_run_add(rn2, -1, 0, 0, w, j2);
+                delta_run_add(ro2, -1, 0, 0, w, j2);
+                if (gc2) atomicAdd(&w.gain_c[j2], gc2);
+                if (gd2) atomicAdd(&w.gain_d[j2], (unsigned long long)gd2);
+            }
+        }
+        lap(kClkUpdate);
+        if (tid == 0) {
+            S.t = u + 1;
+            S.prev_i = ic;
+        }
+        if (!grid_sync(A.bar, gen, A.spin_limit, A.err)) break;
+        lap(kClkWaitC);
+        // V0 and loss of the new placement (every CTA's refresh is in)
+        {
+            const unsigned long long *acc = A.acc + (size_t)((u + 1) & 1) * nA;
+            for (int k = tid; k < K; k += kPerThreads) {
+                s_lossc[k] = (long long)__ldcg(&acc[2 + k]);
+                s_lossd[k] = (long long)__ldcg(&acc[2 + K + k]);
+            }
+            if (tid == 0) {
+                S.v0c = (long long)__ldcg(&acc[0]);
+                S.v0d = (long long)__ldcg(&acc[1]);
+            }
+            __syncthreads();
+        }
+        select();   // the next move's keys (and the closed column written back)
+    }
+
+    // ------------------------------------------------ hand the state back (CTA 0)
+    __syncthreads();
+    if (tid == 0) {
+        for (int k = 0; k < kClocks; k++) A.cta_ns[(size_t)blockIdx.x * kClocks + k] = s_clk[k];
+        if (lead_cta) A.info[1] = rec_total;
+    }
+    if (!lead_cta) return;
+    const int t = S.t;
+    const unsigned long long *acc = A.acc + (size_t)(t & 1) * nA;
+    for (int k = tid; k < K; k += kPerThreads) {
+        w.open[k] = s_open[k];
+        w.loss_c[k] = __ldcg(&acc[2 + k]);
+        w.loss_d[k] = __ldcg(&acc[2 + K + k]);
+    }
+    for (int c = tid; c < nC; c += kPerThreads) w.cand[c] = s_cand[c];
+    for (int b = tid; b < B; b += kPerThreads) w.expiry[b] = s_exp[b];
+    if (tid == 0) {
+        w.v0[0] = __ldcg(&acc[0]);
+        w.v0[1] = __ldcg(&acc[1]);
+        st->t = t;
+        st->n_moves = S.n_moves;
+        st->done = S.done;
+        st->cur_cov = S.cur_c;
+        st->cur_dist = S.cur_d;
+        st->best_cov = S.best_c;
+        st->best_dist = S.best_d;
+        st->best_iter = S.best_iter;
+        st->mv_s = S.mv_s;
+        st->mv_i = S.mv_i;
+        st->mv_j = S.mv_j;
+        st->chg_n = 0;
+        st->err |= *reinterpret_cast<volatile int *>(A.err);
+        A.info[0] = gridDim.x;
+    }
+}
+
+// Test support: one block waits on a flag that nothing sets, with the same
+// bounded poll as the grid barrier; the error word records the give-up.
+__global__ void k_wait_unset_flag(const unsigned *flag, long long limit, int *err)
+{
+    if (threadIdx.x == 0 && !wait_change(flag, *flag, limit)) atomicOr(err, kErrPipelineTimeout);
+}
+
+// ---------------------------------------------------------------- host side
+
+static size_t persist_smem(int K, int B, int ldT) { return per_layout(K, B, ldT).total; }
+
+// CTAs of a persistent search: up to one per SM (the cooperative launch needs
+// them all resident), no more than the mission blocks; 0 when the shape is
+// not supported (K > 256, more than 2048 bases, or the per-CTA arrays do not
+// fit in shared memory).
+int persist_grid(int K, int B, int ldT, int M_pad)
+{
+    if (K > kPipeMaxK || (ldT & 31) || ldT > kMaxLd) return 0;
+    const size_t sm = persist_smem(K, B, ldT);
+    if (sm > kPerSmemLimit) return 0;
+    int nb = 0, dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, (const void *)k_tabu_persist, kPerThreads, sm) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    const int blocks = (M_pad + kBlockMissions - 1) / kBlockMissions;
+    int g = nb * sms;
+    if (g > blocks) g = blocks;
+    return g > 0 ? g : 0;
+}
+
+static size_t region_cap(int M_pad, int grid)
+{
+    const int nblk = (M_pad + kBlockMissions - 1) / kBlockMissions;
+    return (size_t)((nblk + grid - 1) / grid) * kBlockMissions;
+}
+
+size_t persist_scratch_bytes(int K, int grid, int M_pad)
+{
+    const size_t nA = 2 + 2 * (size_t)K;
+    return per_align(2 * nA * 8, 256) * 2 + 256 + per_align((size_t)2 * grid * sizeof(MoveKey), 256) +
+           per_align(region_cap(M_pad, grid) * grid * 32, 256) + per_align((size_t)grid * kClocks * 8, 256);
+}
+
+size_t persist_clock_offset(int K, int grid, int M_pad)
+{
+    return persist_scratch_bytes(K, grid, M_pad) - per_align((size_t)grid * kClocks * 8, 256);
+}
+
+size_t persist_info_offset(int K)
+{
+    const size_t nA = 2 + 2 * (size_t)K;
+    return per_align(2 * nA * 8, 256) * 2 + 64;
+}
+
+cudaError_t persist_init()
+{
+    return cudaFuncSetAttribute(k_tabu_persist, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPerSmemLimit);
+}
+
+cudaError_t launch_tabu_persist(const TabuBuffers &w, const int32_t *cost, void *scratch, int grid,
+                                long long spin_limit, cudaStream_t s)
+{
+    const size_t nA = 2 + 2 * (size_t)w.K;
+    if (grid < 1 || w.ldT > kMaxLd || (w.ldT & 31)) return cudaErrorInvalidValue;
+    char *p = static_cast<char *>(scratch);
+    PersistArgs A{};
+    A.w = w;
+    A.cost = cost;
+    A.acc = reinterpret_cast<unsigned long long *>(p);
+    p += per_align(2 * nA * 8, 256);
+    A.col = reinterpret_cast<unsigned long long *>(p);
+    p += per_align(2 * nA * 8, 256);
+    A.bar = reinterpret_cast<unsigned *>(p + 16);
+    A.err = reinterpret_cast<int *>(p + 32);
+    A.recn = reinterpret_cast<int *>(p + 40);
+    A.info = reinterpret_cast<long long *>(p + 64);
+    p += 256;
+    const size_t cleared = (size_t)(p - static_cast<char *>(scratch));
+    A.part = reinterpret_cast<MoveKey *>(p);
+    p += per_align((size_t)2 * grid * sizeof(MoveKey), 256);
+    A.region_cap = (int)region_cap(w.M_pad, grid);
+    A.region = reinterpret_cast<int4 *>(p);
+    p += per_align((size_t)A.region_cap * grid * 32, 256);
+    A.cta_ns = reinterpret_cast<long long *>(p);
+    A.spin_limit = spin_limit > 0 ? spin_limit : (1ll << 26);
+    // clear the sums, counters and barrier, then put the start placement's
+    // V0 and loss (the per-mission initialisation's) in both buffers (the
+    // first selection copies one into the other again)
+    cudaError_t e = cudaMemsetAsync(scratch, 0, cleared, s);
+    for (int b = 0; b < 2 && e == cudaSuccess; b++) {
+        unsigned long long *a0 = A.acc + (size_t)b * nA;
+        e = cudaMemcpyAsync(a0, w.v0, 16, cudaMemcpyDeviceToDevice, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(a0 + 2, w.loss_c, (size_t)w.K * 8, cudaMemcpyDeviceToDevice, s);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(a0 + 2 + w.K, w.loss_d, (size_t)w.K * 8, cudaMemcpyDeviceToDevice, s);
+    }
+    if (e != cudaSuccess) return e;
+    void *args[] = {&A};
+    return cudaLaunchCooperativeKernel((const void *)k_tabu_persist, dim3(grid), dim3(kPerThreads), args,
+                                       persist_smem(w.K, w.B, w.ldT), s);
+}
+
+cudaError_t launch_wait_unset_flag(unsigned *flag, long long limit, int *err, cudaStream_t s)
+{
+    k_wait_unset_flag<<<1, 32, 0, s>>>(flag, limit > 0 ? limit : (1ll << 26), err);
+    return cudaGetLastError();
+}
+
+}  // namespace stg

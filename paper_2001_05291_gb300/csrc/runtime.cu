@@ -161,6 +161,7 @@ void free_instance(stage_ctx *c, Instance *in)
     dev_free(c, in->mem_scratch);
     dev_free(c, in->mem_chg);
     dev_free(c, in->mem_costT);
+    dev_free(c, in->mem_persist);
     delete in;
 }
 
@@ -480,10 +481,20 @@ stage_status run_tabu(stage_ctx *c, Instance *in, const stage_tabu_params *p,
     // STAGE_FULL_PASS: a full pass every iteration instead.
     // Only for tables well beyond the L2 cache: an L2-resident table is
     // streamed faster than the scattered columns of the changed missions.
-    bool inc = !(c->flags & STAGE_FULL_PASS) && swap_delta_fits(K) && swap_variant_default() &&
+    bool inc = !(c->flags & STAGE_FULL_PASS) && swap_delta_fits(K) &&
                ((c->flags & STAGE_INCREMENTAL) ||
                 (size_t)nC * in->M_pad * sizeof(int32_t) >= kIncrementalMinTableBytes);
     TabuBuffers tw = tb;   // the buffers of this run's multi-kernel launches
+    const bool multi = nC > 0 && iters > 0 && !(tabu_resident_fits(K, in->B, in->M_pad, nC)) &&
+                       !(tabu_small_fits(nC, in->M_pad, K));
+    // the incremental form's whole loop in one cooperative launch, where the
+    // shape fits and the device can hold the grid (STAGE_NO_PERSIST: the
+    // per-iteration launches instead)
+    // (not for the test-support export of the per-mission state: the
+    // persistent search keeps it exact only up to R)
+    bool persist = inc && multi && !(c->flags & STAGE_NO_PERSIST) && tw.mask == nullptr && exp_a == nullptr;
+    const int pgrid = persist ? persist_grid(K, in->B, table_ldT(in->B), in->M_pad) : 0;
+    if (pgrid < 1) persist = false;
     if (inc) {
         // the change records and the mission-major copy of the table; with no
         // room for them (the context's HBM budget) the search takes the full pass
@@ -546,15 +557,73 @@ stage_status run_tabu(stage_ctx *c, Instance *in, const stage_tabu_params *p,
         if (inc) run("swap_delta", [&] { return launch_swap_delta(tw, c->stream); });
         return e;
     };
-    const bool multi = nC > 0 && iters > 0 && !(tabu_resident_fits(K, in->B, in->M_pad, nC) && swap_variant_default()) &&
-                       !(tabu_small_fits(nC, in->M_pad, K) && swap_variant_default());
+    if (!inc) persist = false;   // no room for the incremental form's buffers
+    if (persist) {
+        const size_t need = persist_scratch_bytes(K, pgrid, in->M_pad);
+        if (pgrid < 1) {
+            persist = false;
+        } else if (!in->mem_persist.p || in->mem_persist.bytes < need) {
+            dev_free(c, in->mem_persist);
+            if (dev_alloc(c, need, in->mem_persist) != STAGE_OK) {
+                persist = false;
+                set_err(c, STAGE_OK, "");   // a refused allocation here is not an error of the search
+            }
+        }
+    }
     if (inc && multi) CK(timed(c, "swap_eval", 1, [&] { return launch_swap_eval(tw, in->cost, nC, 0, c->stream); }));
-    if (nC > 0 && iters > 0 && tabu_resident_fits(K, in->B, in->M_pad, nC) && swap_variant_default()) {
+    if (nC > 0 && iters > 0 && tabu_resident_fits(K, in->B, in->M_pad, nC)) {
         // small instance: the whole search in one block, its arrays in shared memory
         CK(timed(c, "tabu_small", 1, [&] { return launch_tabu_resident(tb, in->cost, nC, iters, c->stream); }));
-    } else if (nC > 0 && iters > 0 && tabu_small_fits(nC, in->M_pad, K) && swap_variant_default()) {
+    } else if (nC > 0 && iters > 0 && tabu_small_fits(nC, in->M_pad, K)) {
         // small instance: the whole search in one resident block
         CK(timed(c, "tabu_small", 1, [&] { return launch_tabu_small(tb, in->cost, iters, c->stream); }));
+    } else if (persist) {
+        CK(timed(c, "persist", 1, [&] {
+            return launch_tabu_persist(tw, in->cost, in->mem_persist.p, pgrid, c->spin_limit, c->stream);
+        }));
+        // the records over the search (the traffic accounting)
+        long long info[2] = {0, 0};
+        CK(cudaMemcpyAsync(info, static_cast<const char *>(in->mem_persist.p) + persist_info_offset(K), sizeof info,
+                           cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        {
+            std::lock_guard<std::recursive_mutex> g(c->mu);
+            c->stats["swap_delta_records"].launches += info[1];
+            c->stats["persist_ctas"].launches = info[0];
+        }
+        if (profiling) {
+            // the kernel's own clocks: per step the mean over the CTAs and the
+            // slowest CTA ("_max"), with the moves applied as the count
+            std::vector<long long> clk((size_t)pgrid * kPersistClocks);
+            const char *base = static_cast<const char *>(in->mem_persist.p);
+            TabuDevState sd{};
+            CK(cudaMemcpyAsync(&sd, tb.st, sizeof sd, cudaMemcpyDeviceToHost, c->stream));
+            CK(cudaMemcpyAsync(clk.data(), base + persist_clock_offset(K, pgrid, in->M_pad),
+                               clk.size() * sizeof(long long), cudaMemcpyDeviceToHost, c->stream));
+            CK(cudaStreamSynchronize(c->stream));
+            const char *nm[kPersistClocks] = {"persist_move",          "persist_refresh",
+                                              "persist_wait_refresh",  "persist_update",
+                                              "persist_wait_update",   "persist_select",
+                                              "persist_wait_select",   "persist_refresh_loop",
+                                              "persist_refresh_rescan", "persist_refresh_sums",
+                                              "persist_update_issue",  "persist_update_wait",
+                                              "persist_update_compute"};
+            const long long moves = sd.t - t0;
+            for (int k = 0; k < kPersistClocks; k++) {
+                double sum = 0.0, mx = 0.0;
+                for (int g = 0; g < pgrid; g++) {
+                    const double v = clk[(size_t)g * kPersistClocks + k] * 1e-6;
+                    sum += v;
+                    mx = std::max(mx, v);
+                }
+                KernelStat &mean = c->stats[nm[k]];
+                mean.launches += moves;
+                mean.ms += sum / pgrid;
+                KernelStat &top = c->stats[std::string(nm[k]) + "_max"];
+                top.launches += moves;
+                top.ms += mx;
+            }
+        }
     } else if (nC > 0 && iters >= kGraphIters && !profiling) {
         // replay kGraphIters iterations at a time from a CUDA graph
         cudaGraph_t gr = nullptr;
@@ -622,9 +691,12 @@ stage_status run_tabu(stage_ctx *c, Instance *in, const stage_tabu_params *p,
     CK(cudaMemcpyAsync(best.data(), tb.best_open, (size_t)K * 4, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaMemcpyAsync(expiry.data(), tb.expiry, (size_t)in->B * 4, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
+    if (st.err & kErrPipelineTimeout)
+        return set_err(c, STAGE_ERR_TIMEOUT, "a device-side wait gave up after %lld polls at iteration %d",
+                       (long long)c->spin_limit, st.t);
     if (st.err)
         return set_err(c, STAGE_ERR_INTERNAL, "device self-check failed (code %d) at iteration %d", st.err, st.t);
-    if (inc && multi) {
+    if (inc && multi && !persist) {
         // missions the incremental passes took (traffic accounting)
         std::lock_guard<std::recursive_mutex> g(c->mu);
         c->stats["swap_delta_records"].launches += st.chg_total + st.chg_n;
@@ -870,6 +942,9 @@ stage_status run_fleet(stage_ctx *c, Instance *in, const stage_fleet_params *p, 
         e = cudaMemcpy(traj, A.tb.traj, (size_t)n * sizeof(stage_move), cudaMemcpyDeviceToHost);
     cleanup();
     if (e != cudaSuccess) return set_err(c, STAGE_ERR_CUDA, "fleet search failed: %s", cudaGetErrorString(e));
+    if (st.err & kErrPipelineTimeout)
+        return set_err(c, STAGE_ERR_TIMEOUT, "a device-side wait gave up after %lld polls at iteration %d",
+                       (long long)c->spin_limit, st.t);
     if (st.err)
         return set_err(c, STAGE_ERR_INTERNAL, "device self-check failed (code %d) at iteration %d", st.err, st.t);
     if (res) {
@@ -1537,6 +1612,28 @@ stage_status stage_read_table(stage_ctx *c, stage_inst h, int32_t b0, int32_t nb
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     dev_free(c, win);
     if (e != cudaSuccess) return set_err(c, STAGE_ERR_CUDA, "reading the table failed: %s", cudaGetErrorString(e));
+    return STAGE_OK;
+}
+
+stage_status stage_test_wait_timeout(stage_ctx *c)
+{
+    if (!c) return STAGE_ERR_INVALID_ARG;
+    Guard g(c);
+    if (cudaSetDevice(c->device) != cudaSuccess) return set_err(c, STAGE_ERR_CUDA, "cudaSetDevice failed");
+    DevBuf buf;
+    stage_status s = dev_alloc(c, 256, buf);
+    if (s != STAGE_OK) return s;
+    unsigned *flag = static_cast<unsigned *>(buf.p);
+    int *err = reinterpret_cast<int *>(static_cast<char *>(buf.p) + 64);
+    int h_err = 0;
+    cudaError_t e = cudaMemsetAsync(buf.p, 0, 256, c->stream);
+    if (e == cudaSuccess) e = launch_wait_unset_flag(flag, c->spin_limit, err, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h_err, err, sizeof h_err, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    dev_free(c, buf);
+    if (e != cudaSuccess) return set_err(c, STAGE_ERR_CUDA, "bounded-wait test failed: %s", cudaGetErrorString(e));
+    if (h_err & kErrPipelineTimeout)
+        return set_err(c, STAGE_ERR_TIMEOUT, "the device-side wait gave up after %lld polls", (long long)c->spin_limit);
     return STAGE_OK;
 }
 

@@ -51,6 +51,7 @@ struct Instance {
     DevBuf mem_scratch;  // rank sums, evaluation outputs, exports
     DevBuf mem_chg;      // change records of the incremental neighbourhood ([2 * M_pad] int4)
     DevBuf mem_costT;    // the table mission-major for the incremental neighbourhood (M_pad x ldT)
+    DevBuf mem_persist;  // accumulators, counters and barrier of the persistent search
     int ldT = 0;
     bool costT_ok = false;   // mem_costT holds the current table
     size_t scratch_bytes = 0;

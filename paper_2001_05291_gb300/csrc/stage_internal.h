@@ -93,6 +93,7 @@ struct TabuBuffers {
     int ldT;
 };
 
+constexpr int kPipeMaxK = 256;   // most slots of the direct swap pass and of the incremental form
 constexpr int kSelectBlocks = 148;
 constexpr int kSelectThreads = 256;
 
@@ -139,6 +140,30 @@ cudaError_t launch_gather_window(const int32_t *cost, int M, int M_pad, const in
                                  int m0, int nm, int32_t *out, cudaStream_t s);
 cudaError_t launch_swap_table(const TabuBuffers &w, int nC, long long *out_c, long long *out_d,
                               cudaStream_t s);
+// Persistent search (persist.cu): the incremental neighbourhood's whole loop
+// in one cooperative launch.  persist_grid: the CTAs a search of this shape
+// takes on the current device (0 when the shape is not supported: K > 256,
+// more than 2048 bases, or the per-CTA arrays do not fit in shared memory).
+// The scratch (persist_scratch_bytes) holds the sums, barrier, error word,
+// per-CTA keys and record regions; at byte offset persist_info_offset(K) two
+// int64, the CTAs and the records over the search, and at
+// persist_clock_offset(K, grid, M_pad) [grid][kPersistClocks] int64: each
+// CTA's time in ns of each step (choose and apply the move, refresh, wait at
+// the barrier after it, update the columns, wait at the barrier after it,
+// select, wait at the barrier before the next move; then parts of the refresh
+// -- the mission loop, the rescans, the sums -- and of the update -- issuing
+// copies, waiting for them, computing), summed over the search.
+constexpr int kPersistClocks = 13;
+int persist_grid(int K, int B, int ldT, int M_pad);
+size_t persist_scratch_bytes(int K, int grid, int M_pad);
+size_t persist_info_offset(int K);
+size_t persist_clock_offset(int K, int grid, int M_pad);
+cudaError_t launch_tabu_persist(const TabuBuffers &w, const int32_t *cost, void *scratch, int grid,
+                                long long spin_limit, cudaStream_t s);
+cudaError_t persist_init();
+// Test support: a wait on a flag that nothing sets, bounded by `limit` polls;
+// it sets kErrPipelineTimeout in *err when it gives up.
+cudaError_t launch_wait_unset_flag(unsigned *flag, long long limit, int *err, cudaStream_t s);
 cudaError_t kernels_init();   // one-time function attributes (dynamic shared memory)
 
 // ------------------------------------------------------- grouped (batched) launches
@@ -159,7 +184,6 @@ int group_swap_blocks(int M_pad, int nC, int K, int seg_override, int *bx, int *
 int group_common_segment(const int *M_pad, const int *nC, int n);
 size_t swap_direct_smem(int K);   // dynamic shared memory of the direct swap pass
 bool tabu_small_fits(int nC, int M_pad, int K);
-bool swap_variant_default();   // the direct swap pass is selected (STAGE_SWAP_VARIANT unset or 0)
 cudaError_t launch_tabu_small(const TabuBuffers &w, const int32_t *cost, int iters, cudaStream_t s);
 // small instances, every per-iteration array in shared memory (one block)
 bool tabu_resident_fits(int K, int B, int M_pad, int nC);

@@ -24,6 +24,7 @@ STAGE_OK, STAGE_PENDING = 0, 1
 ERRORS = {-1: "INVALID_ARG", -2: "OUT_OF_RANGE", -3: "NO_MEMORY", -4: "ADMISSION", -5: "TIMEOUT",
           -6: "CUDA", -7: "INTERNAL", -8: "NOT_FOUND"}
 STAGE_THREADSAFE, STAGE_PROFILE, STAGE_AUTOTUNE, STAGE_FULL_PASS, STAGE_INCREMENTAL = 1, 2, 4, 8, 16
+STAGE_NO_PERSIST = 32
 STAGE_DESC_DEVICE, STAGE_DESC_HAVERSINE = 1, 2
 MOVE_FALLBACK, MOVE_ASPIRATION, MOVE_NEW_BEST = 1, 2, 4
 MAX_COORD, MAX_BASES, MAX_MISSIONS, MAX_K = 1 << 24, 65535, 1 << 24, 1024
@@ -146,6 +147,7 @@ def lib():
             "stage_update_instance": ([p, C.c_uint64, C.POINTER(StageUpdate)], st),
             "stage_batch_submit": ([p, C.POINTER(StageRequest), i32, C.POINTER(C.c_uint64)], st),
             "stage_poll": ([p, C.c_uint64, C.POINTER(StageResult), i32], st),
+            "stage_test_wait_timeout": ([p], st),
             "stage_evaluate_swaps_noalloc": ([p, i32, i32, i32, p, p, i32, i32, p, p, p, C.c_char_p,
                                               C.c_size_t], st),
         }
@@ -245,13 +247,13 @@ class Context:
     def __init__(self, device: int = 0, profile: bool = False, threadsafe: bool = False,
                  hbm_budget: int = 0, max_slots: int = 0, spin_limit: int = 0,
                  torch_memory: bool = True, stream=None, autotune: bool = False, full_pass: bool = False,
-                 incremental: bool = False):
+                 incremental: bool = False, persist: bool = True, allocator=None):
         L = lib()
         cfg = StageConfig()
         cfg.device = device
         cfg.flags = ((STAGE_PROFILE if profile else 0) | (STAGE_THREADSAFE if threadsafe else 0) |
                      (STAGE_AUTOTUNE if autotune else 0) | (STAGE_FULL_PASS if full_pass else 0) |
-                     (STAGE_INCREMENTAL if incremental else 0))
+                     (STAGE_INCREMENTAL if incremental else 0) | (0 if persist else STAGE_NO_PERSIST))
         cfg.hbm_budget_bytes = hbm_budget
         cfg.max_slots = max_slots
         cfg.spin_limit = spin_limit
@@ -261,7 +263,9 @@ class Context:
             import torch
             if not torch.cuda.is_available():
                 raise StageError(-6, "no CUDA device")
-            self._alloc = _TorchAllocator(device)
+            # allocator: an object with alloc_cb / free_cb (ALLOC_FN / FREE_FN
+            # callbacks); default: PyTorch's caching allocator
+            self._alloc = allocator if allocator is not None else _TorchAllocator(device)
             cfg.alloc = self._alloc.alloc_cb
             cfg.free = self._alloc.free_cb
             self.torch_stream = stream if stream is not None else torch.cuda.Stream(device=device)
@@ -305,6 +309,11 @@ class Context:
         v = C.c_uint64()
         self._check(lib().stage_memory_used(self._h, C.byref(v)))
         return int(v.value)
+
+    def test_wait_timeout(self):
+        """stage_test_wait_timeout: one bounded device wait on a flag nothing
+        sets; raises StageError (TIMEOUT) when it gives up, as expected."""
+        self._check(lib().stage_test_wait_timeout(self._h))
 
     # ------------------------------------------------------------- instances
     def load_instance(self, base_xy, pick_xy, drop_xy, base_available=None, haversine: bool = False) -> int:
@@ -608,13 +617,28 @@ def evaluate_swaps_noalloc(cost, M: int, open_, R: int, out_cov, out_dist, base_
     int32, out_cov / out_dist [K, B] int64, base_available [B] uint8 or None.  For
     callers that cannot allocate device memory; see include/stage.h.  Only
     enqueues on `stream` (a torch stream or raw handle; None = legacy default)."""
-    for t in (cost, open_, out_cov, out_dist):
+    import torch
+    tensors = [cost, open_, out_cov, out_dist] + ([] if base_available is None else [base_available])
+    for t in tensors:
         if not _is_cuda_tensor(t) or not t.is_contiguous():
             raise ValueError("inputs and outputs must be contiguous CUDA tensors")
+    # the scratch address is looked up for the current device, and the kernels
+    # run there: every tensor must live on it
+    dev = torch.cuda.current_device()
+    if any(t.device.index != dev for t in tensors):
+        raise ValueError(f"every tensor must be on the current CUDA device (cuda:{dev})")
+    if cost.dim() != 2 or cost.dtype != torch.int32:
+        raise ValueError("cost must be a 2-D int32 tensor [B, M_pad]")
+    if open_.dtype != torch.int32:
+        raise ValueError("open_ must be an int32 tensor")
+    if out_cov.dtype != torch.int64 or out_dist.dtype != torch.int64:
+        raise ValueError("out_cov and out_dist must be int64 tensors")
     B, M_pad = int(cost.shape[0]), int(cost.shape[1])
     K = int(open_.numel())
     if out_cov.numel() != K * B or out_dist.numel() != K * B:
         raise ValueError("outputs must hold K * B values")
+    if base_available is not None and (base_available.dtype != torch.uint8 or base_available.numel() != B):
+        raise ValueError("base_available must be a uint8 tensor of B values")
     s = 0 if stream is None else (stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
     err = C.create_string_buffer(512)
     rc = lib().stage_evaluate_swaps_noalloc(

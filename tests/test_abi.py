@@ -111,9 +111,9 @@ def test_binding_constants_match_header():
     with open(HEADER) as fh:
         defs = dict(re.findall(r"#define\s+(STAGE_[A-Z_0-9]+)\s+\(?(-?\d+)u?\)?", fh.read()))
     names = ["STAGE_THREADSAFE", "STAGE_PROFILE", "STAGE_AUTOTUNE", "STAGE_FULL_PASS", "STAGE_INCREMENTAL",
-             "STAGE_DESC_HAVERSINE"]
+             "STAGE_NO_PERSIST", "STAGE_DESC_HAVERSINE"]
     for n in names:
         assert n in defs, n
         assert getattr(stage, n) == int(defs[n]), n
-    flags = [int(defs[n]) for n in names[:5]]
-    assert len(set(flags)) == 5 and all(f & (f - 1) == 0 for f in flags)   # distinct single bits
+    flags = [int(defs[n]) for n in names[:6]]
+    assert len(set(flags)) == 6 and all(f & (f - 1) == 0 for f in flags)   # distinct single bits

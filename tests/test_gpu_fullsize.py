@@ -2,9 +2,11 @@
 
 The oracle cannot run 1000 iterations on an 8 GB table in a test, so the checks
 are: the first moves against the oracle's own search on the full table (the
-trajectory of a longer run starts with the shorter run's), and sampled later
-moves plus the best placement against the oracle's evaluation of the placements
-the GPU reports.  All quantities are integers: zero tolerance.
+trajectory of a longer run starts with the shorter run's); sampled later moves
+against the move the oracle takes from the state (placement, tabu expiries,
+best so far) that the GPU's earlier moves lead to; and the best placement and
+sampled placements against the oracle's evaluation.  All quantities are
+integers: zero tolerance.
 """
 import os
 
@@ -39,6 +41,35 @@ def replay(start, moves):
     return out
 
 
+def state_before(cost, R, start, moves, t, tenure):
+    """The search state before move t, rebuilt from the GPU's trajectory: the
+    placement, the tabu expiries (both bases of a move at iteration u stay tabu
+    until u + tenure + 1) and the best so far (changed only by a strictly better
+    placement; the start's iteration is -1)."""
+    O = [int(x) for x in start]
+    expiry = np.zeros(cost.shape[0], dtype=np.int32)
+    best = oracle.evaluate(cost, O, R)
+    best_open, best_iter = list(O), -1
+    for (it, i, j, _f, cov, dist) in moves[:t]:
+        O = [j if x == i else x for x in O]
+        expiry[i] = expiry[j] = it + tenure + 1
+        if cov > best[0] or (cov == best[0] and dist < best[1]):
+            best, best_open, best_iter = (cov, dist), list(O), it
+    return O, expiry, best, best_open, best_iter
+
+
+def check_sampled_moves(cost, K, R, tenure, start, moves, samples):
+    """Each sampled GPU move t is the move the oracle takes from the state the
+    GPU's first t moves lead to: the best admissible swap of the whole
+    neighbourhood under the tabu, aspiration, fallback and tie rules, with its
+    flags and objective."""
+    for t in samples:
+        O, expiry, best, best_open, best_iter = state_before(cost, R, start, moves, t, tenure)
+        ref = oracle.tabu(cost, K, R, 1, tenure, start_open=O, nthreads=THREADS, t0=moves[t][0], expiry_in=expiry,
+                          best_in=best_open, best_cov_in=best[0], best_dist_in=best[1], best_iter_in=best_iter)
+        assert [tuple(m) for m in ref.moves] == [tuple(moves[t])], f"move {t}"
+
+
 def test_large_workload_as_benchmarked(stage_mod):
     stage = stage_mod
     inst = synth.large()
@@ -63,6 +94,8 @@ def test_large_workload_as_benchmarked(stage_mod):
         assert oracle.evaluate(cost, placements[t], inst.R) == (got.moves[t][4], got.moves[t][5])
     assert oracle.evaluate(cost, got.best_open, inst.R) == (got.best_cov, got.best_dist)
     assert sorted(placements[-1]) == got.final_open.tolist()
+    # later moves: each one the oracle's choice from the state the GPU reached
+    check_sampled_moves(cost, inst.K, inst.R, inst.tenure, start, got.moves, (2, 100, 500, inst.iters - 1))
     # the search as benchmarked keeps the neighbourhood's terms across
     # iterations; re-evaluating the whole table every iteration gives the same
     # 1000 moves
@@ -95,6 +128,7 @@ def test_batched_workload_instances_in_one_batch(stage_mod):
         for t in (50, inst.iters - 1):
             assert oracle.evaluate(cost, placements[t], inst.R) == (r.moves[t][4], r.moves[t][5])
         assert oracle.evaluate(cost, r.best_open, inst.R) == (r.best_cov, r.best_dist)
+        check_sampled_moves(cost, inst.K, inst.R, inst.tenure, start, r.moves, (50, 150, inst.iters - 1))
 
 
 def test_local_search_large_workload(stage_mod):

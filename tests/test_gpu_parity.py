@@ -376,9 +376,9 @@ def test_incremental_equals_full_pass():
     """STAGE_INCREMENTAL (the default for tables well beyond L2) keeps the
     neighbourhood's gain and extra terms across iterations and updates them from
     the missions whose best / second best changed, and rebuilds the closed
-    base's column in the refresh; STAGE_FULL_PASS re-evaluates the whole table every iteration.  Graph
-    replay and per-kernel launches of the incremental form, and the full pass,
-    all equal the oracle's trajectory: several K (1 to 64), unavailable bases, a
+    base's column in the refresh; STAGE_FULL_PASS re-evaluates the whole table every iteration.  The
+    persistent launch (the default), the per-kernel launches of the incremental
+    form (STAGE_NO_PERSIST) and the full pass all equal the oracle's trajectory: several K (1 to 64), unavailable bases, a
     start placement, the improving-only rule, R below most costs and R near
     INT32_MAX."""
     from paper_2001_05291_gb300 import stage
@@ -392,7 +392,8 @@ def test_incremental_equals_full_pass():
              (small(75, 50, 8000, 6, R=2**31 - 2), 30, True, None, None),
              (small(76, 300, 5000, 64), 25, True, None, np.arange(64, dtype=np.int32) * 4)]
     with stage.Context(device=0, incremental=True) as ci, stage.Context(device=0, profile=True, incremental=True) as cp, \
-            stage.Context(device=0, full_pass=True) as cf:
+            stage.Context(device=0, full_pass=True) as cf, \
+            stage.Context(device=0, profile=True, incremental=True, persist=False) as cn:
         for inst, iters, aw, unavail, start in cases:
             avail = None
             if unavail is not None:
@@ -402,7 +403,7 @@ def test_incremental_equals_full_pass():
             okw = {"start_open": start} if start is not None else {}
             want = oracle.tabu(cost, inst.K, inst.R, iters, inst.tenure, avail=avail, accept_worsening=aw,
                                nthreads=8, **okw)
-            for c in (ci, cp, cf):
+            for c in (ci, cp, cf, cn):
                 h = load(c, inst, avail)
                 got = c.tabu_run(h, inst.K, inst.R, iters, inst.tenure, accept_worsening=aw, **okw)
                 assert [tuple(m) for m in got.moves] == [tuple(m) for m in want.moves]
@@ -410,19 +411,22 @@ def test_incremental_equals_full_pass():
                                                                         want.best_iter)
                 assert (got.final_cov, got.final_dist) == (want.final_cov, want.final_dist)
                 c.unload_instance(h)
-        assert cp.kernel_stats("swap_delta")[0] > 0
-        assert cf.kernel_stats("swap_delta")[0] == 0
+        # the persistent launch by default, the per-iteration launches with
+        # STAGE_NO_PERSIST, no incremental update with STAGE_FULL_PASS
+        assert cp.kernel_stats("persist")[0] == len(cases) and cp.kernel_stats("swap_delta")[0] == 0
+        assert cn.kernel_stats("swap_delta")[0] > 0 and cn.kernel_stats("persist")[0] == 0
+        assert cf.kernel_stats("swap_delta")[0] == 0 and cf.kernel_stats("persist")[0] == 0
 
 
 def test_incremental_edge_cases_and_resume():
     """The incremental form on the edge cases of the Tabu tests (K = 1, K = B - 1,
-    tenure 0, improving-only, M = 3) and across a resume, on its per-kernel and
-    graph-replay paths."""
+    tenure 0, improving-only, M = 3) and across a resume (an odd start
+    iteration), on its per-kernel path and its persistent launch."""
     from paper_2001_05291_gb300 import stage
     torch = pytest.importorskip("torch")
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
-    with stage.Context(device=0, profile=True, incremental=True) as cp, \
+    with stage.Context(device=0, profile=True, incremental=True, persist=False) as cp, \
             stage.Context(device=0, incremental=True) as cg:
         for B, M, K, tenure, aw in [(20, 200, 1, 2, True), (15, 777, 14, 3, True), (30, 20000, 5, 0, True),
                                     (30, 2051, 5, 6, False), (48, 17000, 9, 4, True), (8, 3, 3, 2, True)]:
