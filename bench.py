@@ -391,6 +391,11 @@ def run_ours(args):
                    "ctas": ctx.kernel_stats("persist_ctas")[0],
                    "records_per_iteration": records / max(1, iters_run),
                    "records_fraction": records / max(1, iters_run) / inst.M,
+                   "terms_per_record": ctx.kernel_stats("swap_delta_term_pairs")[0] / max(1, records),
+                   "term_lanes_per_warp_pass": (ctx.kernel_stats("swap_delta_term_pairs")[0]
+                                                / max(1, ctx.kernel_stats("swap_delta_warp_passes")[0])),
+                   "warp_passes_per_record": ctx.kernel_stats("swap_delta_warp_passes")[0] / max(1, records),
+                   "column_run_writes_per_record": ctx.kernel_stats("swap_delta_run_writes")[0] / max(1, records),
                    "bytes_per_iteration": {"update": rec_bytes / max(1, iters_run),
                                            "refresh": ref_bytes / max(1, iters_run),
                                            "select": sel_bytes / max(1, iters_run)},

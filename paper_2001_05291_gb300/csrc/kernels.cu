@@ -1541,10 +1541,13 @@ cudaError_t launch_swap_delta(const TabuBuffers &w, cudaStream_t s)
 int table_ldT(int B) { return (B + 31) / 32 * 32; }
 
 // Tiled transpose through shared memory: reads and writes both coalesced;
-// position p of a mission's row holds base border[p].
+// position p of a mission's row holds base border[p] (INT32_MAX past B).  Each
+// tile also gives, per mission, the least cost of its 32 positions (the cell
+// minimum, cellmin[m * (ldT / 32) + cell]): exact, and enough to skip a cell
+// with no cost below a threshold.
 __global__ void __launch_bounds__(256) k_transpose_table(const int32_t *__restrict__ cost, int M_pad, int ldT,
                                                          const int32_t *__restrict__ border,
-                                                         int32_t *__restrict__ costT)
+                                                         int32_t *__restrict__ costT, int32_t *__restrict__ cellmin)
 {
     __shared__ int32_t tile[32][33];
     const int m0 = blockIdx.x * 32, b0 = blockIdx.y * 32;
@@ -1554,17 +1557,21 @@ __global__ void __launch_bounds__(256) k_transpose_table(const int32_t *__restri
         tile[k][tx] = (b >= 0 && m < M_pad) ? cost[(size_t)b * M_pad + m] : INT_MAX;
     }
     __syncthreads();
-    for (int k = ty; k < 32; k += 8) {
+    for (int k = ty; k < 32; k += 8) {   // a warp: one mission's 32 positions of the cell
         const int m = m0 + k, b = b0 + tx;
-        if (m < M_pad && b < ldT) costT[(size_t)m * ldT + b] = tile[tx][k];
+        const int32_t v = tile[tx][k];
+        if (m < M_pad && b < ldT) costT[(size_t)m * ldT + b] = v;
+        const int32_t mn = __reduce_min_sync(0xffffffffu, v);
+        if (tx == 0 && m < M_pad) cellmin[(size_t)m * (ldT / 32) + blockIdx.y] = mn;
     }
 }
 
 cudaError_t launch_transpose_table(const int32_t *cost, int B, int M_pad, const int32_t *border, int32_t *costT,
-                                   cudaStream_t s)
+                                   int32_t *cellmin, cudaStream_t s)
 {
     const int ldT = table_ldT(B);
-    k_transpose_table<<<dim3((M_pad + 31) / 32, ldT / 32), 256, 0, s>>>(cost, M_pad, ldT, border, costT);
+    k_transpose_table<<<dim3((M_pad + 31) / 32, ldT / 32), 256, 0, s>>>(cost, M_pad, ldT, border, costT,
+                                                                           cellmin);
     return cudaGetLastError();
 }
 

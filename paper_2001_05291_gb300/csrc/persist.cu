@@ -23,14 +23,16 @@
 //   update      each CTA takes an equal contiguous share of the list (the
 //               records lie near the move, so a CTA's own would leave most
 //               CTAs idle) and moves each one's old terms out of, and its new
-//               terms into, every other base's column (a4), streaming the
-//               records' rows of the mission-major table copy through a
-//               shared-memory ring; a thread holds two bases
-//               (the copy's bases are in spatial order, so the bases near a
-//               record share warps and the others pass it with one compare);
-//               gain terms add up in registers, extra terms in runs of one
-//               slot (consecutive records share slots), flushed to the global
-//               columns with atomics;
+//               terms into, every other base's column (a4).  The copy's bases
+//               are in spatial order, so a record's terms fall in few cells of
+//               32 positions; the exact minimum of each cell of each row
+//               (built with the copy) shows which cells of a record have any
+//               term, and only those pieces of its row (128 bytes) are read.
+//               The (cell, records) work is cut into items dealt to the warps
+//               in turn (the cells near the move carry most of it); the
+//               records are ordered by slot, so gain terms add up in
+//               registers and extra terms in runs of one slot, flushed to the
+//               global columns with atomics;
 //   barrier C   the columns are complete; each CTA scores its share of the
 //               swaps F(s, j) = V0 + gain[j] + loss[s] + extra[s][j] -- the
 //               closed base's column taken from the refresh's sums, which CTA
@@ -60,10 +62,10 @@ namespace stg {
 constexpr int kPerThreads = 1024;
 constexpr int kPerWarps = kPerThreads / 32;
 constexpr int kBlockMissions = 256;    // missions per ownership block (8 warp chunks)
-constexpr int kStageRecs = 4;          // records (table-copy rows) per ring stage
-constexpr int kRing = 4;               // ring stages (kRing - 1 in flight while one is read)
-constexpr int kColCap = 4096;          // record columns staged in shared memory per round
-constexpr int kMaxLd = 2 * kPerThreads;   // table-copy row: two bases per thread
+constexpr int kRecCap = 256;           // records staged in shared memory per round of the update
+constexpr int kUpdBatch = 8;           // listed records whose costs a warp loads at once
+constexpr int kUpdItem = 24;           // listed records of one cell per work item of a warp
+constexpr int kMaxLd = 2048;           // longest table-copy row (its 64 cells fit the item scan)
 constexpr size_t kPerSmemLimit = 220 * 1024;
 
 // Per-CTA clocks (ns, summed over the search): choosing and applying the move,
@@ -73,8 +75,9 @@ constexpr size_t kPerSmemLimit = 220 * 1024;
 // and the update.
 enum : int {
     kClkMove = 0, kClkRefresh, kClkWaitB, kClkUpdate, kClkWaitC, kClkSelect, kClkWaitA,
-    // parts of the refresh and the update (thread 0's view; the update's
-    // compute includes the wait for the CTA's slowest warp)
+    // parts of the refresh and the update (thread 0's view): the update's
+    // record staging, its wait for the CTA's slowest warp, and warp 0's walk
+    // over the records
     kClkRefLoop, kClkRefRescan, kClkRefSums, kClkUpdIssue, kClkUpdWait, kClkUpdCompute, kClocks
 };
 static_assert(kClocks == kPersistClocks, "clock layout shared with the host");
@@ -92,7 +95,7 @@ __device__ __forceinline__ long long gtimer()
 
 // Shared-memory layout (byte offsets).
 struct PerLayout {
-    size_t ring, meta, colv, cand, expiry, cidx, open, lc, ic, ld, id, lossc, lossd, q, total;
+    size_t recs, raw, cnt, cells, wlist, cand, expiry, cidx, open, lc, ic, ld, id, lossc, lossd, q, total;
 };
 
 __host__ __device__ inline size_t per_align(size_t x, size_t a) { return (x + a - 1) / a * a; }
@@ -101,9 +104,11 @@ __host__ __device__ inline PerLayout per_layout(int K, int B, int ldT)
 {
     PerLayout L{};
     size_t o = 0;
-    L.ring = o;   o = per_align(o + (size_t)kRing * kStageRecs * ldT * 4, 128);
-    L.meta = o;   o = per_align(o + (size_t)kRing * kStageRecs * 32, 16);
-    L.colv = o;   o = per_align(o + (size_t)kColCap * 4, 16);
+    L.recs = o;   o = per_align(o + (size_t)kRecCap * 32, 16);
+    L.raw = o;    o = per_align(o + (size_t)kRecCap * 32, 16);
+    L.cnt = o;    o = per_align(o + (size_t)kPipeMaxK * 4, 16);
+    L.cells = o;  o = per_align(o + (size_t)kRecCap * (ldT / 32) * 4, 16);
+    L.wlist = o;  o = per_align(o + (size_t)(ldT / 32) * kRecCap * 2, 16);
     L.cand = o;   o = per_align(o + (size_t)B * 4, 16);
     L.expiry = o; o = per_align(o + (size_t)B * 4, 16);
     L.cidx = o;   o = per_align(o + (size_t)B * 4, 16);
@@ -175,19 +180,13 @@ __device__ __forceinline__ bool grid_sync(unsigned *bar, unsigned &gen, long lon
     return s_ok != 0;
 }
 
-__device__ __forceinline__ void cp_async16(void *dst, const void *src, unsigned long long policy)
+// A read-only cost of the table copy (unchanged during the search), not
+// kept in L1 and first to leave L2: each row is read once per move.
+__device__ __forceinline__ int ld_stream(const int32_t *p, unsigned long long policy)
 {
-    asm volatile("cp.async.cg.shared.global.L2::cache_hint [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)), "l"(src),
-                 "l"(policy)
-                 : "memory");
-}
-
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-
-template <int N>
-__device__ __forceinline__ void cp_async_wait()
-{
-    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+    int v;
+    asm("ld.global.nc.L1::no_allocate.L2::cache_hint.b32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(policy));
+    return v;
 }
 
 // Add (c, d) into the shared per-slot sums of the lanes with `has`: lanes
@@ -276,9 +275,12 @@ __global__ void __launch_bounds__(kPerThreads, 1) k_tabu_persist(PersistArgs A)
     extern __shared__ __align__(128) unsigned char smem[];
     const int K = w.K, B = w.B, R = w.R, ldT = w.ldT;
     const PerLayout L = per_layout(K, B, ldT);
-    int32_t *ring = reinterpret_cast<int32_t *>(smem + L.ring);
-    int4 *smeta = reinterpret_cast<int4 *>(smem + L.meta);
-    int *s_colv = reinterpret_cast<int *>(smem + L.colv);
+    int4 *s_recs = reinterpret_cast<int4 *>(smem + L.recs);
+    int32_t *s_cells = reinterpret_cast<int32_t *>(smem + L.cells);
+    int4 *s_raw = reinterpret_cast<int4 *>(smem + L.raw);
+    int *s_cnt = reinterpret_cast<int *>(smem + L.cnt);
+    uint16_t *s_clist = reinterpret_cast<uint16_t *>(smem + L.wlist);   // [cell][kRecCap]
+    __shared__ int s_ccnt[kMaxLd / 32], s_ipre[kMaxLd / 32 + 1];
     int *s_cand = reinterpret_cast<int *>(smem + L.cand);
     int *s_exp = reinterpret_cast<int *>(smem + L.expiry);
     int *s_cidx = reinterpret_cast<int *>(smem + L.cidx);
@@ -301,11 +303,12 @@ __global__ void __launch_bounds__(kPerThreads, 1) k_tabu_persist(PersistArgs A)
     const int t_end = st->t_end, tenure = st->tenure, aw = st->accept_worsening, nC = st->nC;
     const int traj_cap = st->traj_cap;
     int4 *region = A.region + (size_t)blockIdx.x * A.region_cap * 2;
-    // the update: this thread's two bases (positions tid and tid + 1024 of
-    // the table copy; -1 past the copy's bases)
-    const int j1 = tid < ldT ? w.border[tid] : -1;
-    const int j2 = tid + kPerThreads < ldT ? w.border[tid + kPerThreads] : -1;
     long long rec_total = 0;   // records of this CTA over the search
+    // the update's (record, base) pairs with a term, and the (record, warp
+    // cell) passes with at least one: the update's work and how densely it
+    // fills the warps
+    __shared__ unsigned long long s_terms[3];
+    if (tid < 3) s_terms[tid] = 0;
 
     if (tid == 0) {
         S.t = st->t;
@@ -620,118 +623,204 @@ __global__ void __launch_bounds__(kPerThreads, 1) k_tabu_persist(PersistArgs A)
 
         // ------------------------------------------------ update every column with this CTA's records (a4)
         {
-            // This CTA's share of the list: records r0 .. r0+n-1, taken in
-            // rounds of at most kColCap records whose columns are first read
-            // into shared memory (so that no copy waits on a load).  The ring:
-            // stage k of a round holds its records k*kStageRecs ..
-            // +kStageRecs-1, each one's full row of the table copy (ldT costs)
-            // and the record itself.  Step k (from -(kRing-1)): thread tid
-            // copies 16-byte pieces tid and tid + 1024 of stage k + kRing - 1
-            // (piece p is record p / (ldT / 4), offset p % (ldT / 4)) and,
-            // below 2 kStageRecs, one record half; then every copy of step
-            // k - kRing + 1 -- stage k -- has landed (kRing - 1 steps stay in
-            // flight).  The table copy is read once per move: evict-first in L2.
+            // This CTA's share of the list: records r0 .. r0+nshare-1 (the
+            // list is in spatial order, so a share is spatially compact),
+            // staged in shared memory in rounds of at most kRecCap, ordered by
+            // their new slot (a base's terms in a row then mostly go to one
+            // slot's column and add up in one run), with the cell minima of
+            // each record's row.  Per cell of the row (32 positions, one per
+            // lane) the records whose minimum over the cell is below their
+            // threshold are listed (a cell at or above it has no term); the
+            // lists, cut into items of at most kUpdItem records, are dealt to
+            // the warps in turn, and a warp loads an item's costs in the cell
+            // (32 costs, 128 bytes per record) kUpdBatch records at a time and
+            // compares each lane's cost with the threshold.  Each item adds
+            // its sums to the columns by itself.
             const int ntot = min(__ldcg(&A.recn[u & 1]), w.M);
             const int r0 = (int)((long long)ntot * blockIdx.x / gridDim.x);
             const int nshare = (int)((long long)ntot * (blockIdx.x + 1) / gridDim.x) - r0;
             if (lead_cta) rec_total += ntot;
-            const int qpr = ldT >> 2;   // 16-byte pieces per row
-            static_assert(kStageRecs * (kMaxLd / 4) <= 2 * kPerThreads, "two pieces per thread per stage");
-            const int pr1 = tid / qpr, pr2 = (tid + kPerThreads) / qpr;
-            const bool pc1 = tid < kStageRecs * qpr, pc2 = tid + kPerThreads < kStageRecs * qpr;
-            const int off1 = tid - pr1 * qpr, off2 = tid + kPerThreads - pr2 * qpr;
-            const bool m1 = j1 >= 0 && j1 != ic, m2 = j2 >= 0 && j2 != ic;
-            long long gd1 = 0, gd2 = 0;
-            int gc1 = 0, gc2 = 0;
-            DeltaRun rn1{-1, 0, 0}, ro1{-1, 0, 0}, rn2{-1, 0, 0}, ro2{-1, 0, 0};
-            for (int base = 0; base < nshare; base += kColCap) {   // the same on every thread
-                const int n = min(kColCap, nshare - base);
+            const int nCell = ldT >> 5;
+            const int *srec = reinterpret_cast<const int *>(s_recs);
+            unsigned lanes = 0, passes = 0;   // this warp's pairs with a term, (record, cell) passes
+            unsigned flushes = 0;             // this thread's runs written to the columns
+            for (int base = 0; base < nshare; base += kRecCap) {   // the same on every thread
+                const int n = min(kRecCap, nshare - base);
                 const int4 *list = w.chg + 2 * (size_t)(r0 + base);
-                __syncthreads();   // the previous round's columns are used
-                for (int q = tid; q < n; q += kPerThreads) s_colv[q] = __ldcg(&list[2 * (size_t)q].x);
+                __syncthreads();   // the previous round's records are used
+                for (int q = tid; q < 2 * n; q += kPerThreads) s_raw[q] = __ldcg(&list[q]);
+                for (int k = tid; k < K; k += kPerThreads) s_cnt[k] = 0;
                 __syncthreads();
-                const int nst = (n + kStageRecs - 1) / kStageRecs;
-                for (int k = -(kRing - 1); k < nst; k++) {   // the same on every thread
-                    sub(kClkUpdCompute);
-                    const int ks = k + kRing - 1;
-                    if (ks < nst) {
-                        const int sg = ks % kRing;
-                        int32_t *dst = ring + (size_t)sg * kStageRecs * ldT;
-                        const int ra = ks * kStageRecs + pr1, rb = ks * kStageRecs + pr2;
-                        if (pc1 && ra < n)
-                            cp_async16(dst + (size_t)pr1 * ldT + 4 * off1,
-                                       w.costT + (size_t)s_colv[ra] * ldT + 4 * off1, evict_first);
-                        if (pc2 && rb < n)
-                            cp_async16(dst + (size_t)pr2 * ldT + 4 * off2,
-                                       w.costT + (size_t)s_colv[rb] * ldT + 4 * off2, evict_first);
-                        if (tid < 2 * kStageRecs) {
-                            const int rec = ks * kStageRecs + (tid >> 1);
-                            if (rec < n)
-                                cp_async16(smeta + (size_t)sg * 2 * kStageRecs + tid,
-                                           list + 2 * (size_t)rec + (tid & 1), evict_first);
-                        }
-                    }
-                    cp_async_commit();
-                    sub(kClkUpdIssue);
-                    cp_async_wait<kRing - 1>();
-                    __syncthreads();   // every thread's copies of stage k have landed
-                    sub(kClkUpdWait);
-                    if (k >= 0) {
-                        const int sg = k % kRing;
-                        const int32_t *rows = ring + (size_t)sg * kStageRecs * ldT;
-                        const int4 *meta = smeta + (size_t)sg * 2 * kStageRecs;
-                        // every record's costs and threshold first (independent
-                        // loads), then the records with a term
-                        int xa[kStageRecs], xb[kStageRecs], hv[kStageRecs];
+                // counting sort by new slot (the order within a slot is free:
+                // the sums are integers)
+                static_assert(kRecCap <= kPerThreads, "one record per thread");
+                int key = tid < n ? s_raw[2 * tid + 1].w : 0;
+                key = (unsigned)key < (unsigned)K ? key : 0;   // an index; only the order depends on it
+                const int pos = tid < n ? atomicAdd(&s_cnt[key], 1) : 0;
+                __syncthreads();
+                if (tid < 32) {   // exclusive scan of the K counts (K <= 256: 8 per lane)
+                    int v[8], sum = 0;
 #pragma unroll
-                        for (int v = 0; v < kStageRecs; v++) {
-                            const bool valid = k * kStageRecs + v < n;
-                            xa[v] = m1 ? rows[v * ldT + tid] : INT_MAX;
-                            xb[v] = m2 ? rows[v * ldT + tid + kPerThreads] : INT_MAX;
-                            hv[v] = valid ? reinterpret_cast<const int *>(meta)[8 * v + 1] : INT_MIN;
-                        }
-#pragma unroll
-                        for (int v = 0; v < kStageRecs; v++) {
-                            const int hi = hv[v];
-                            if (min(xa[v], xb[v]) >= hi) continue;   // no term in either state (a <= b)
-                            const int4 q0 = meta[2 * v];       // (column, hi, old a, old b)
-                            const int4 q1 = meta[2 * v + 1];   // (old slot, new a, new b, new slot)
-                            const int ao = q0.z, bo = q0.w, so = q1.x, an = q1.y, bn = q1.z, sn = q1.w;
-                            const int cao = ao <= R, cbo = bo <= R, can = an <= R, cbn = bn <= R;
-                            auto terms = [&](int x, int j, int &gc, long long &gd, DeltaRun &rn, DeltaRun &ro) {
-                                if (x >= hi) return;
-                                if (x < an) { gc += 1 - can; gd += (long long)x - (can ? an : 0); }
-                                if (x < ao) { gc -= 1 - cao; gd -= (long long)x - (cao ? ao : 0); }
-                                if (x < bn) {
-                                    const int nc = can - cbn, nd = (can ? max(x, an) : 0) - (cbn ? bn : 0);
-                                    if (nc | nd) delta_run_add(rn, sn, nc, nd, w, j);
-                                }
-                                if (x < bo) {
-                                    const int oc = cao - cbo, od = (cao ? max(x, ao) : 0) - (cbo ? bo : 0);
-                                    if (oc | od) delta_run_add(ro, so, -oc, -od, w, j);
-                                }
-                            };
-                            terms(xa[v], j1, gc1, gd1, rn1, ro1);
-                            terms(xb[v], j2, gc2, gd2, rn2, ro2);
-                        }
+                    for (int e = 0; e < 8; e++) {
+                        const int k = tid * 8 + e;
+                        v[e] = k < K ? s_cnt[k] : 0;
+                        sum += v[e];
                     }
-                    __syncthreads();   // stage k is read: later copies may go there
+                    int incl = sum;
+#pragma unroll
+                    for (int d = 1; d < 32; d <<= 1) {
+                        const int y = __shfl_up_sync(0xffffffffu, incl, d);
+                        if (tid >= d) incl += y;
+                    }
+                    int run = incl - sum;
+#pragma unroll
+                    for (int e = 0; e < 8; e++) {
+                        const int k = tid * 8 + e;
+                        if (k < K) s_cnt[k] = run;
+                        run += v[e];
+                    }
                 }
+                __syncthreads();
+                if (tid < n) {
+                    const int dst = s_cnt[key] + pos;
+                    s_recs[2 * dst] = s_raw[2 * tid];
+                    s_recs[2 * dst + 1] = s_raw[2 * tid + 1];
+                }
+                __syncthreads();
+                {
+                    const int lane = tid & 31;
+#pragma unroll 4
+                    for (int r = tid >> 5; r < n; r += kPerWarps) {   // a warp per record
+                        const size_t row = (size_t)srec[8 * r] * nCell;
+                        for (int c = lane; c < nCell; c += 32) s_cells[r * nCell + c] = __ldcg(&w.cellmin[row + c]);
+                    }
+                }
+                __syncthreads();
+                sub(kClkUpdIssue);
+                // per cell (32 positions of the row): the records whose minimum
+                // over the cell is below their threshold, in order (a cell at
+                // or above it has no term)
+                const int lane = tid & 31, warp = tid >> 5;
+                for (int cell = warp; cell < nCell; cell += kPerWarps) {   // the same on the warp
+                    uint16_t *cl = s_clist + cell * kRecCap;
+                    int cnt = 0;
+                    for (int rb = 0; rb < n; rb += 32) {   // the same on the warp
+                        const int r = rb + lane;
+                        const bool need = r < n && s_cells[r * nCell + cell] < srec[8 * r + 1];
+                        const unsigned bm = __ballot_sync(0xffffffffu, need);
+                        if (need) cl[cnt + __popc(bm & ((1u << lane) - 1u))] = (uint16_t)r;
+                        cnt += __popc(bm);
+                    }
+                    if (lane == 0) s_ccnt[cell] = cnt;
+                }
+                __syncthreads();
+                // work items: each cell's list in pieces of at most kUpdItem
+                // records, dealt to the warps in turn (the cells near the move
+                // have the longest lists); s_ipre = first item of each cell
+                static_assert(kMaxLd / 32 <= 64, "two cells per lane");
+                if (tid < 32) {
+                    const int c0 = 2 * tid, c1 = c0 + 1;
+                    const int n0 = c0 < nCell ? (s_ccnt[c0] + kUpdItem - 1) / kUpdItem : 0;
+                    const int n1 = c1 < nCell ? (s_ccnt[c1] + kUpdItem - 1) / kUpdItem : 0;
+                    int incl = n0 + n1;
+#pragma unroll
+                    for (int d = 1; d < 32; d <<= 1) {
+                        const int y = __shfl_up_sync(0xffffffffu, incl, d);
+                        if (tid >= d) incl += y;
+                    }
+                    const int ex = incl - n0 - n1;
+                    if (c0 < nCell) s_ipre[c0] = ex;
+                    if (c1 < nCell) s_ipre[c1] = ex + n0;
+                    if (tid == 31) s_ipre[kMaxLd / 32] = incl;
+                }
+                __syncthreads();
+                const int nitems = s_ipre[kMaxLd / 32];
+                for (int it = warp; it < nitems; it += kPerWarps) {   // the same on the warp
+                    int lo = 0, hc = nCell - 1;   // the item's cell: the last with s_ipre <= it
+                    while (lo < hc) {
+                        const int mid = (lo + hc + 1) >> 1;
+                        if (s_ipre[mid] <= it) lo = mid;
+                        else hc = mid - 1;
+                    }
+                    const int cell = lo;
+                    const int e0 = (it - s_ipre[cell]) * kUpdItem, e1 = min(e0 + kUpdItem, s_ccnt[cell]);
+                    const uint16_t *cl = s_clist + cell * kRecCap;
+                    const int pos = cell * 32 + lane;   // < ldT
+                    const int j = w.border[pos];
+                    const bool mine = j >= 0 && j != ic;
+                    // the listed records' costs in this cell (the warp's 32
+                    // consecutive entries of each row, 128 bytes), kUpdBatch
+                    // records' at a time, every load of a batch in flight together
+                    const int32_t *Tp = w.costT + pos;
+                    long long gd = 0;
+                    int gc = 0;
+                    DeltaRun rn{-1, 0, 0}, ro{-1, 0, 0};
+                    for (int q0 = e0; q0 < e1; q0 += kUpdBatch) {   // the same on the warp
+                        int xs[kUpdBatch];
+#pragma unroll
+                        for (int v = 0; v < kUpdBatch; v++) {
+                            const int q = q0 + v;
+                            xs[v] = (q < e1 && mine) ? ld_stream(Tp + (size_t)srec[8 * cl[q]] * ldT, evict_first)
+                                                     : INT_MAX;
+                        }
+#pragma unroll
+                        for (int v = 0; v < kUpdBatch; v++) {
+                            const int q = q0 + v;
+                            if (q >= e1) break;   // the same on the warp
+                            const int r = cl[q];
+                            const int x = xs[v];
+                            const int hi = srec[8 * r + 1];
+                            const unsigned bm = __ballot_sync(0xffffffffu, x < hi);
+                            lanes += __popc(bm);
+                            passes += bm != 0u;
+                            if (x >= hi) continue;
+                            const int4 q0r = s_recs[2 * r];       // (column, hi, old a, old b)
+                            const int4 q1r = s_recs[2 * r + 1];   // (old slot, new a, new b, new slot)
+                            const int ao = q0r.z, bo = q0r.w, so = q1r.x, an = q1r.y, bn = q1r.z, sn = q1r.w;
+                            const int cao = ao <= R, cbo = bo <= R, can = an <= R, cbn = bn <= R;
+                            if (x < an) { gc += 1 - can; gd += (long long)x - (can ? an : 0); }
+                            if (x < ao) { gc -= 1 - cao; gd -= (long long)x - (cao ? ao : 0); }
+                            // extra: the new state's term into the new slot's
+                            // column, the old one's out of the old slot's (one
+                            // run when the slot is kept)
+                            int nc = 0, nd = 0, oc = 0, od = 0;
+                            if (x < bn) { nc = can - cbn; nd = (can ? max(x, an) : 0) - (cbn ? bn : 0); }
+                            if (x < bo) { oc = cao - cbo; od = (cao ? max(x, ao) : 0) - (cbo ? bo : 0); }
+                            if (sn == so) {
+                                nc -= oc;
+                                nd -= od;
+                                oc = od = 0;
+                            }
+                            if (nc | nd) {
+                                flushes += sn != rn.s && rn.s >= 0 && (rn.c | (rn.d != 0));
+                                delta_run_add(rn, sn, nc, nd, w, j);
+                            }
+                            if (oc | od) {
+                                flushes += so != ro.s && ro.s >= 0 && (ro.c | (ro.d != 0));
+                                delta_run_add(ro, so, -oc, -od, w, j);
+                            }
+                        }
+                    }
+                    if (mine) {
+                        flushes += (rn.s >= 0 && (rn.c | (rn.d != 0))) + (ro.s >= 0 && (ro.c | (ro.d != 0)));
+                        delta_run_add(rn, -1, 0, 0, w, j);   // flush
+                        delta_run_add(ro, -1, 0, 0, w, j);
+                        if (gc) atomicAdd(&w.gain_c[j], gc);
+                        if (gd) atomicAdd(&w.gain_d[j], (unsigned long long)gd);
+                    }
+                }
+                sub(kClkUpdCompute);
             }
-            cp_async_wait<0>();
-            sub(kClkUpdCompute);
-            if (m1) {
-                delta_run_add(rn1, -1, 0, 0, w, j1);   // flush
-                delta_run_add(ro1, -1, 0, 0, w, j1);
-                if (gc1) atomicAdd(&w.gain_c[j1], gc1);
-                if (gd1) atomicAdd(&w.gain_d[j1], (unsigned long long)gd1);
+            if ((tid & 31) == 0 && passes) {
+                atomicAdd(&s_terms[0], (unsigned long long)lanes);
+                atomicAdd(&s_terms[1], (unsigned long long)passes);
             }
-            if (m2) {
-                delta_run_add(rn2, -1, 0, 0, w, j2);
-                delta_run_add(ro2, -1, 0, 0, w, j2);
-                if (gc2) atomicAdd(&w.gain_c[j2], gc2);
-                if (gd2) atomicAdd(&w.gain_d[j2], (unsigned long long)gd2);
+            {
+                const unsigned f = __reduce_add_sync(0xffffffffu, flushes);
+                if ((tid & 31) == 0 && f) atomicAdd(&s_terms[2], (unsigned long long)f);
             }
+            __syncthreads();   // the CTA's slowest warp
+            sub(kClkUpdWait);
         }
         lap(kClkUpdate);
         if (tid == 0) {
@@ -758,6 +847,7 @@ __global__ void __launch_bounds__(kPerThreads, 1) k_tabu_persist(PersistArgs A)
 
     // ------------------------------------------------ hand the state back (CTA 0)
     __syncthreads();
+    if (tid < 3) atomicAdd(reinterpret_cast<unsigned long long *>(&A.info[2 + tid]), s_terms[tid]);
     if (tid == 0) {
         for (int k = 0; k < kClocks; k++) A.cta_ns[(size_t)blockIdx.x * kClocks + k] = s_clk[k];
         if (lead_cta) A.info[1] = rec_total;

@@ -500,7 +500,9 @@ stage_status run_tabu(stage_ctx *c, Instance *in, const stage_tabu_params *p,
         // room for them (the context's HBM budget) the search takes the full pass
         const int ldT = table_ldT(in->B);
         const size_t need = (size_t)in->M_pad * 2 * sizeof(int4);
-        const size_t needT = (size_t)in->M_pad * ldT * sizeof(int32_t) + (size_t)ldT * sizeof(int32_t);
+        // the copy, its position order, its cell minima
+        const size_t needT = (size_t)in->M_pad * ldT * sizeof(int32_t) + (size_t)ldT * sizeof(int32_t) +
+                             (size_t)in->M_pad * (ldT / 32) * sizeof(int32_t);
         if (!in->mem_chg.p || in->mem_chg.bytes < need) {
             dev_free(c, in->mem_chg);
             if (dev_alloc(c, need, in->mem_chg) != STAGE_OK) {
@@ -527,10 +529,12 @@ stage_status run_tabu(stage_ctx *c, Instance *in, const stage_tabu_params *p,
                 std::vector<int32_t> border = spatial_order(bxy, ldT);
                 int32_t *costT = static_cast<int32_t *>(in->mem_costT.p);
                 int32_t *d_border = costT + (size_t)in->M_pad * ldT;
+                int32_t *d_cellmin = d_border + ldT;
                 CK(cudaMemcpyAsync(d_border, border.data(), (size_t)ldT * sizeof(int32_t), cudaMemcpyHostToDevice,
                                    c->stream));
                 CK(timed(c, "transpose", 1, [&] {
-                    return launch_transpose_table(in->cost, in->B, in->M_pad, d_border, costT, c->stream);
+                    return launch_transpose_table(in->cost, in->B, in->M_pad, d_border, costT, d_cellmin,
+                                                  c->stream);
                 }));
                 CK(cudaStreamSynchronize(c->stream));   // the host order vector goes out of scope
                 in->ldT = ldT;
@@ -541,6 +545,7 @@ stage_status run_tabu(stage_ctx *c, Instance *in, const stage_tabu_params *p,
             tw.chg = static_cast<int4 *>(in->mem_chg.p);
             tw.costT = static_cast<const int32_t *>(in->mem_costT.p);
             tw.border = tw.costT + (size_t)in->M_pad * in->ldT;
+            tw.cellmin = tw.border + in->ldT;
             tw.ldT = in->ldT;
         }
     }
@@ -581,8 +586,9 @@ stage_status run_tabu(stage_ctx *c, Instance *in, const stage_tabu_params *p,
         CK(timed(c, "persist", 1, [&] {
             return launch_tabu_persist(tw, in->cost, in->mem_persist.p, pgrid, c->spin_limit, c->stream);
         }));
-        // the records over the search (the traffic accounting)
-        long long info[2] = {0, 0};
+        // the records over the search (the traffic accounting), the
+        // (record, base) pairs with a term and the warps' passes over them
+        long long info[5] = {0, 0, 0, 0, 0};
         CK(cudaMemcpyAsync(info, static_cast<const char *>(in->mem_persist.p) + persist_info_offset(K), sizeof info,
                            cudaMemcpyDeviceToHost, c->stream));
         CK(cudaStreamSynchronize(c->stream));
@@ -590,6 +596,9 @@ stage_status run_tabu(stage_ctx *c, Instance *in, const stage_tabu_params *p,
             std::lock_guard<std::recursive_mutex> g(c->mu);
             c->stats["swap_delta_records"].launches += info[1];
             c->stats["persist_ctas"].launches = info[0];
+            c->stats["swap_delta_term_pairs"].launches += info[2];
+            c->stats["swap_delta_warp_passes"].launches += info[3];
+            c->stats["swap_delta_run_writes"].launches += info[4];
         }
         if (profiling) {
             // the kernel's own clocks: per step the mean over the CTAs and the

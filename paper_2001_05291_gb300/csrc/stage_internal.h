@@ -90,6 +90,9 @@ struct TabuBuffers {
     // in a spatial order, costT[m * ldT + p] = cost of base border[p] for m
     const int32_t *costT;
     const int32_t *border;   // [ldT] position -> base id (-1 past B)
+    // [M_pad][ldT / 32]: each mission's least cost over each 32 consecutive
+    // positions of its costT row
+    const int32_t *cellmin;
     int ldT;
 };
 
@@ -129,6 +132,7 @@ cudaError_t launch_swap_delta(const TabuBuffers &w, cudaStream_t s);
 // 32), the bases in the order border (position -> base id, -1 past B).
 int table_ldT(int B);
 cudaError_t launch_transpose_table(const int32_t *cost, int B, int M_pad, const int32_t *border, int32_t *costT,
+                                   int32_t *cellmin,
                                    cudaStream_t s);
 cudaError_t launch_export_best_two(const TabuBuffers &w, const int *perm, int32_t *a, int32_t *b,
                                    int32_t *b1, int32_t *b2, cudaStream_t s);
@@ -145,14 +149,16 @@ cudaError_t launch_swap_table(const TabuBuffers &w, int nC, long long *out_c, lo
 // takes on the current device (0 when the shape is not supported: K > 256,
 // more than 2048 bases, or the per-CTA arrays do not fit in shared memory).
 // The scratch (persist_scratch_bytes) holds the sums, barrier, error word,
-// per-CTA keys and record regions; at byte offset persist_info_offset(K) two
-// int64, the CTAs and the records over the search, and at
-// persist_clock_offset(K, grid, M_pad) [grid][kPersistClocks] int64: each
-// CTA's time in ns of each step (choose and apply the move, refresh, wait at
-// the barrier after it, update the columns, wait at the barrier after it,
+// per-CTA keys and record regions; at byte offset persist_info_offset(K) four
+// int64 -- the CTAs, the records over the search, the update's (record, base)
+// pairs with a term, and the warps' passes (a record with a term in the warp)
+// -- and at persist_clock_offset(K, grid, M_pad) [grid][kPersistClocks] int64:
+// each CTA's time in ns of each step (choose and apply the move, refresh, wait
+// at the barrier after it, update the columns, wait at the barrier after it,
 // select, wait at the barrier before the next move; then parts of the refresh
-// -- the mission loop, the rescans, the sums -- and of the update -- issuing
-// copies, waiting for them, computing), summed over the search.
+// -- the mission loop, the rescans, the sums -- and of the update -- staging
+// the records, waiting for the CTA's slowest warp, warp 0's walk over the
+// records), summed over the search.
 constexpr int kPersistClocks = 13;
 int persist_grid(int K, int B, int ldT, int M_pad);
 size_t persist_scratch_bytes(int K, int grid, int M_pad);

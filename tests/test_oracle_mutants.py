@@ -1,6 +1,7 @@
 """Planted mistakes in a copy of the oracle, on the CPU: each plausible slip
 (a dropped term, a flipped sign or comparison, an off-by-one) must make at least
-one pin of tests/test_oracle_pins.py fail."""
+one pin fail -- of tests/test_oracle_pins.py for the C part (oracle.c), of
+tests/test_oracle_fleet.py for the heterogeneous-fleet part (Python)."""
 import os
 import subprocess
 import sys
@@ -9,6 +10,7 @@ import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle", "oracle.c")
+PY_SRC = os.path.join(ROOT, "oracle", "__init__.py")
 
 MUTANTS = {
     "dropped_pickup_to_dropoff_leg": ("oracle_leg(px, py, qx, qy) + ", ""),
@@ -43,3 +45,51 @@ def test_pins_catch_mutant(name, tmp_path):
                         os.path.join(ROOT, "tests", "test_oracle_pins.py")],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     assert r.returncode != 0, f"mutant {name} survived the pins:\n{r.stdout[-2000:]}"
+
+
+# the fleet ranking (Alg. 1, lines 14-16 and 20-21) and the fleet move rule (Sec. 3)
+PY_MUTANTS = {
+    "fleet_rank_reversed_order": ("key=lambda b: (int(S[b]), b))", "key=lambda b: (-int(S[b]), b))"),
+    "fleet_rank_tie_high_index": ("key=lambda b: (int(S[b]), b))", "key=lambda b: (int(S[b]), -b))"),
+    "fleet_rank_no_helipad_quota": ("            if nh < K_rotary:\n", "            if True:\n"),
+    "fleet_rotary_takes_worst_aerodromes": (
+        "rot += aer[:K_rotary - len(rot)]\n    fix = aer[K_rotary - nh:]",
+        "rot += aer[len(aer) - (K_rotary - nh):]\n    fix = aer[:len(aer) - (K_rotary - nh)]"),
+    "fleet_rotary_moves_first_on_ties": ("keys.append(((-f[0], f[1], i, j),", "keys.append(((-f[0], f[1], kind, i, j),"),
+    "fleet_fixed_wing_on_helipad": ("if kind == 1 and heli[j]:", "if kind == 1 and heli[j] and False:"),
+    "fleet_rotary_only_missions_by_any": ("b = evaluate(c1, r, R) if (c1.shape[1] and r)",
+                                          "b = evaluate(c1, r + f, R) if (c1.shape[1] and r)"),
+    "fleet_tenure_off_by_one": ("expiry[i] = expiry[j] = t + tenure + 1", "expiry[i] = expiry[j] = t + tenure"),
+    "fleet_no_aspiration": ("adm = [k for k in keys if not k[6] or better(k[1], best)]",
+                            "adm = [k for k in keys if not k[6]]"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(PY_MUTANTS))
+def test_fleet_pins_catch_mutant(name, tmp_path, orc):
+    old, new = PY_MUTANTS[name]
+    src = open(PY_SRC).read()
+    assert src.count(old) == 1, f"mutation site of {name} not found once"
+    pkg = tmp_path / "oracle"
+    pkg.mkdir()
+    (pkg / "__init__.py").write_text(src.replace(old, new))
+    env = dict(os.environ, ORACLE_PY_OVERRIDE=str(tmp_path), ORACLE_LIB_OVERRIDE=orc.build())
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                        os.path.join(ROOT, "tests", "test_oracle_fleet.py")],
+                       cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode != 0, f"mutant {name} survived the pins:\n{r.stdout[-2000:]}"
+
+
+def test_fleet_mutant_harness_runs_the_copy(tmp_path, orc):
+    """The unmutated copy passes (so a failing mutant fails for its mutation)."""
+    pkg = tmp_path / "oracle"
+    pkg.mkdir()
+    (pkg / "__init__.py").write_text(open(PY_SRC).read() + "\nCOPY_MARK = 1\n")
+    env = dict(os.environ, ORACLE_PY_OVERRIDE=str(tmp_path), ORACLE_LIB_OVERRIDE=orc.build())
+    r = subprocess.run([sys.executable, "-c", "import sys; sys.path.insert(0, 'tests'); import conftest, oracle; "
+                        "print(oracle.COPY_MARK)"], cwd=ROOT, env=env, capture_output=True, text=True, timeout=120)
+    assert r.stdout.strip() == "1", r.stderr
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                        os.path.join(ROOT, "tests", "test_oracle_fleet.py")],
+                       cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stdout[-2000:]
