@@ -36,17 +36,19 @@ int swap_segment_for(int M_pad, int nC, int K);
 // root of the exact squared distance n.  |coord| <= 2^24 keeps n below 2^52,
 // where the ceiling of the correctly rounded float64 root is exactly the
 // integer ceiling square root; that integer is computed here without float64
-// (GB300's float64 rate is low): a float32 estimate, then integer steps to the
+// (GB300's float64 rate is low): a float32 estimate from the 32-bit
+// differences, then integer steps (one 32 x 32 -> 64-bit product each) to the
 // exact floor root s (s^2 <= n < (s+1)^2), then s + [s^2 != n].
 __device__ __forceinline__ int32_t leg_ceil(int x1, int y1, int x2, int y2)
 {
-    const long long dx = (long long)x1 - (long long)x2;
-    const long long dy = (long long)y1 - (long long)y2;
-    const long long n = dx * dx + dy * dy;
-    long long s = (long long)__fsqrt_rn((float)n);   // within a few units of sqrt(n)
-    while (s * s > n) --s;
-    while ((s + 1) * (s + 1) <= n) ++s;
-    return (int32_t)(s + (s * s != n ? 1 : 0));
+    const int dx = x1 - x2, dy = y1 - y2;   // |.| <= 2^25
+    const long long n = (long long)dx * dx + (long long)dy * dy;
+    const float fx = (float)dx, fy = (float)dy;
+    const float fn = __fmaf_rn(fx, fx, __fmul_rn(fy, fy));   // n to a few parts in 2^24
+    int s = fn > 0.0f ? (int)__fmul_rn(fn, rsqrtf(fn)) : 0;   // within a few units of sqrt(n)
+    while ((long long)s * s > n) --s;
+    while ((long long)(s + 1) * (s + 1) <= n) ++s;
+    return s + ((long long)s * s != n ? 1 : 0);
 }
 
 // Leg cost of Eq. 1 (Haversine) for points given as (latitude, longitude) in
@@ -471,6 +473,118 @@ cudaError_t launch_table(int B, int M, int M_pad, const int2 *base, const int2 *
     } else {
         k_pickup_drop_leg<0><<<g1, 256, 0, s>>>(M, pick, drop, pd);
         k_build_table<0><<<dim3(gx, gy), 256, 0, s>>>(B, M, M_pad, base, pick, drop, pd, cost);
+    }
+    return cudaGetLastError();
+}
+
+// The table, its row sums, its mission-major copy and the copy's cell minima
+// in one pass (no second read of the table).  A block covers 8 cells of the
+// copy (256 positions, base border[p] at position p) and walks tiles of 32
+// missions: warp w computes cell 8 g + w of the tile, lane = mission, writes
+// each base's 32 costs of the tile to the table (128 bytes per base row),
+// transposes them through its own shared tile and writes each mission's 32
+// costs of the cell to the copy (128 bytes), the lane of position p adding
+// its base's costs to the row sum and the warp taking each mission's minimum
+// over the cell.  Pads (m >= M) and positions past B hold INT32_MAX and add
+// nothing to a row sum.
+constexpr int kFusedCells = 8;
+
+template <int Metric>
+__global__ void __launch_bounds__(256) k_build_table_fused(int B, int M, int M_pad, int ldT,
+                                                           const int2 *__restrict__ base,
+                                                           const int2 *__restrict__ pick,
+                                                           const int2 *__restrict__ drop,
+                                                           const int32_t *__restrict__ pd,
+                                                           const int32_t *__restrict__ border,
+                                                           int32_t *__restrict__ cost, int32_t *__restrict__ costT,
+                                                           int32_t *__restrict__ cellmin,
+                                                           unsigned long long *__restrict__ S)
+{
+    __shared__ int32_t tile[kFusedCells][32][33];
+    __shared__ int32_t smin[2][32][kFusedCells];
+    __shared__ int2 sxy[kFusedCells * 32];
+    __shared__ double scos[kFusedCells * 32];
+    __shared__ int32_t sid[kFusedCells * 32];
+    const int nCell = ldT >> 5, ldC = cell_ld(ldT);
+    const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5;
+    const int cell = blockIdx.y * kFusedCells + wq;
+    const int p0 = blockIdx.y * kFusedCells * 32;
+    {
+        const int p = p0 + threadIdx.x;
+        const int b = p < ldT ? border[p] : -1;
+        sid[threadIdx.x] = b;
+        sxy[threadIdx.x] = b >= 0 ? base[b] : make_int2(0, 0);
+        scos[threadIdx.x] = b >= 0 ? point_cos<Metric>(base[b]) : 0.0;
+    }
+    __syncthreads();
+    const bool live = cell < nCell;   // the same on the warp
+    const int mb = sid[wq * 32 + lane];   // the base of this lane's position (transposed phase)
+    long long rs = 0;
+    const int nTiles = M_pad >> 5;
+    int buf = 0;
+    for (int t = blockIdx.x; t < nTiles; t += gridDim.x) {   // the same on the block
+        const int m = t * 32 + lane;
+        if (live) {
+            int2 pm = make_int2(0, 0), dm = make_int2(0, 0);
+            int l = -1;
+            if (m < M) { pm = pick[m]; dm = drop[m]; l = pd[m]; }
+            const double cpm = point_cos<Metric>(pm), cdm = point_cos<Metric>(dm);
+#pragma unroll 4
+            for (int k = 0; k < 32; k++) {
+                const int q = wq * 32 + k;
+                const int b = sid[q];
+                int32_t v = kInf;
+                if (b >= 0 && l >= 0) {
+                    const int2 o = sxy[q];
+                    const double co = scos[q];
+                    v = leg_of<Metric>(o, co, pm, cpm) + l + leg_of<Metric>(dm, cdm, o, co);
+                }
+                if (b >= 0) cost[(size_t)b * M_pad + m] = v;
+                tile[wq][k][lane] = v;
+            }
+            __syncwarp();
+            int32_t mymin = kInf;
+#pragma unroll 4
+            for (int mm = 0; mm < 32; mm++) {
+                const int32_t v = tile[wq][lane][mm];   // position lane, mission mm
+                costT[(size_t)(t * 32 + mm) * ldT + cell * 32 + lane] = v;
+                if (mb >= 0 && v != kInf) rs += v;
+                const int32_t mn = __reduce_min_sync(0xffffffffu, v);
+                if (lane == mm) mymin = mn;
+            }
+            smin[buf][lane][wq] = mymin;
+            __syncwarp();
+        }
+        __syncthreads();
+        {   // the tile's cell minima: 32 missions x 8 cells, 32 bytes per mission
+            const int mm = threadIdx.x >> 3, c = threadIdx.x & 7;
+            if (blockIdx.y * kFusedCells + c < nCell)
+                cellmin[(size_t)(t * 32 + mm) * ldC + blockIdx.y * kFusedCells + c] = smin[buf][mm][c];
+        }
+        buf ^= 1;
+    }
+    if (live && mb >= 0 && rs) atomicAdd(&S[mb], (unsigned long long)rs);
+}
+
+cudaError_t launch_table_fused(int B, int M, int M_pad, int ldT, const int2 *base, const int2 *pick,
+                               const int2 *drop, int32_t *pd, const int32_t *border, int32_t *cost, int32_t *costT,
+                               int32_t *cellmin, unsigned long long *S, int metric, cudaStream_t s)
+{
+    const int sms = sm_count();
+    int g1 = (M + 255) / 256;
+    if (g1 > 4096) g1 = 4096;
+    const int gy = (ldT / 32 + kFusedCells - 1) / kFusedCells;
+    int gx = (sms * 4 + gy - 1) / gy;   // about four blocks per SM
+    if (gx > M_pad / 32) gx = M_pad / 32;
+    if (gx < 1) gx = 1;
+    if (metric == 1) {
+        k_pickup_drop_leg<1><<<g1, 256, 0, s>>>(M, pick, drop, pd);
+        k_build_table_fused<1><<<dim3(gx, gy), 256, 0, s>>>(B, M, M_pad, ldT, base, pick, drop, pd, border, cost,
+                                                             costT, cellmin, S);
+    } else {
+        k_pickup_drop_leg<0><<<g1, 256, 0, s>>>(M, pick, drop, pd);
+        k_build_table_fused<0><<<dim3(gx, gy), 256, 0, s>>>(B, M, M_pad, ldT, base, pick, drop, pd, border, cost,
+                                                             costT, cellmin, S);
     }
     return cudaGetLastError();
 }
@@ -1543,7 +1657,7 @@ int table_ldT(int B) { return (B + 31) / 32 * 32; }
 // Tiled transpose through shared memory: reads and writes both coalesced;
 // position p of a mission's row holds base border[p] (INT32_MAX past B).  Each
 // tile also gives, per mission, the least cost of its 32 positions (the cell
-// minimum, cellmin[m * (ldT / 32) + cell]): exact, and enough to skip a cell
+// minimum, cellmin[m * cell_ld(ldT) + cell]): exact, and enough to skip a cell
 // with no cost below a threshold.
 __global__ void __launch_bounds__(256) k_transpose_table(const int32_t *__restrict__ cost, int M_pad, int ldT,
                                                          const int32_t *__restrict__ border,
@@ -1562,7 +1676,7 @@ __global__ void __launch_bounds__(256) k_transpose_table(const int32_t *__restri
         const int32_t v = tile[tx][k];
         if (m < M_pad && b < ldT) costT[(size_t)m * ldT + b] = v;
         const int32_t mn = __reduce_min_sync(0xffffffffu, v);
-        if (tx == 0 && m < M_pad) cellmin[(size_t)m * (ldT / 32) + blockIdx.y] = mn;
+        if (tx == 0 && m < M_pad) cellmin[(size_t)m * cell_ld(ldT) + blockIdx.y] = mn;
     }
 }
 

@@ -691,7 +691,7 @@ __global__ void __launch_bounds__(kPerThreads, 1) k_tabu_persist(PersistArgs A)
                     const int lane = tid & 31;
 #pragma unroll 4
                     for (int r = tid >> 5; r < n; r += kPerWarps) {   // a warp per record
-                        const size_t row = (size_t)srec[8 * r] * nCell;
+                        const size_t row = (size_t)srec[8 * r] * cell_ld(ldT);
                         for (int c = lane; c < nCell; c += 32) s_cells[r * nCell + c] = __ldcg(&w.cellmin[row + c]);
                     }
                 }

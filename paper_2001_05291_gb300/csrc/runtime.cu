@@ -162,6 +162,7 @@ void free_instance(stage_ctx *c, Instance *in)
     dev_free(c, in->mem_chg);
     dev_free(c, in->mem_costT);
     dev_free(c, in->mem_persist);
+    dev_free(c, in->mem_rowsum);
     delete in;
 }
 
@@ -281,8 +282,12 @@ stage_status do_rank(stage_ctx *c, Instance *in, int K, int32_t *out_open, int64
     auto *S = static_cast<unsigned long long *>(in->mem_scratch.p);
     auto *d_open = reinterpret_cast<int32_t *>(static_cast<char *>(in->mem_scratch.p) +
                                                round_up((size_t)in->B * 8, 256));
-    CK(cudaMemsetAsync(S, 0, (size_t)in->B * 8, c->stream));
-    CK(timed(c, "rowsum", 1, [&] { return launch_rowsum(in->cost, in->B, in->M, in->M_pad, S, c->stream); }));
+    if (in->rowsum_ok) {
+        S = static_cast<unsigned long long *>(in->mem_rowsum.p);   // built with the table
+    } else {
+        CK(cudaMemsetAsync(S, 0, (size_t)in->B * 8, c->stream));
+        CK(timed(c, "rowsum", 1, [&] { return launch_rowsum(in->cost, in->B, in->M, in->M_pad, S, c->stream); }));
+    }
     CK(timed(c, "topk", 1, [&] { return launch_topk(S, in->avail, in->B, K, d_open, c->stream); }));
     CK(cudaMemcpyAsync(out_open, d_open, (size_t)K * 4, cudaMemcpyDeviceToHost, c->stream));
     if (out_rowsum)
@@ -500,9 +505,7 @@ stage_status run_tabu(stage_ctx *c, Instance *in, const stage_tabu_params *p,
         // room for them (the context's HBM budget) the search takes the full pass
         const int ldT = table_ldT(in->B);
         const size_t need = (size_t)in->M_pad * 2 * sizeof(int4);
-        // the copy, its position order, its cell minima
-        const size_t needT = (size_t)in->M_pad * ldT * sizeof(int32_t) + (size_t)ldT * sizeof(int32_t) +
-                             (size_t)in->M_pad * (ldT / 32) * sizeof(int32_t);
+        const size_t needT = costT_bytes(in->M_pad, ldT);
         if (!in->mem_chg.p || in->mem_chg.bytes < need) {
             dev_free(c, in->mem_chg);
             if (dev_alloc(c, need, in->mem_chg) != STAGE_OK) {
@@ -1297,10 +1300,52 @@ stage_status stage_load_instance(stage_ctx *c, const stage_instance_desc *d, sta
             return launch_order(M, in->pick_in, in->drop_in, order_tmp.p, in->perm, in->inv, in->pick,
                                 in->drop, c->stream);
         });
-    if (e == cudaSuccess)
+    // where the search will take the incremental form, the table, its row
+    // sums, its mission-major copy and the copy's cell minima in one pass
+    // (with no room for the copy, the table alone; the copy follows when a
+    // search needs it)
+    const int ldT = table_ldT(B);
+    const bool want_copy = !(c->flags & STAGE_FULL_PASS) &&
+                           ((c->flags & STAGE_INCREMENTAL) || (size_t)B * M_pad * 4 >= kIncrementalMinTableBytes);
+    bool fused = false;
+    if (e == cudaSuccess && want_copy) {
+        fused = dev_alloc(c, costT_bytes(M_pad, ldT), in->mem_costT) == STAGE_OK &&
+                dev_alloc(c, (size_t)B * 8, in->mem_rowsum) == STAGE_OK;
+        if (!fused) {
+            dev_free(c, in->mem_costT);
+            dev_free(c, in->mem_rowsum);
+            set_err(c, STAGE_OK, "");   // a refused allocation here is not an error of the load
+        }
+    }
+    if (e == cudaSuccess && fused) {
+        std::vector<int2> bxy(B);
+        if (on_dev) e = cudaMemcpy(bxy.data(), d->base_xy, (size_t)B * sizeof(int2), cudaMemcpyDeviceToHost);
+        else std::memcpy(bxy.data(), d->base_xy, (size_t)B * sizeof(int2));
+        const std::vector<int32_t> border = spatial_order(bxy, ldT);
+        int32_t *costT = static_cast<int32_t *>(in->mem_costT.p);
+        int32_t *d_border = costT + (size_t)M_pad * ldT;
+        int32_t *d_cellmin = d_border + ldT;
+        auto *S = static_cast<unsigned long long *>(in->mem_rowsum.p);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(d_border, border.data(), (size_t)ldT * sizeof(int32_t), cudaMemcpyHostToDevice,
+                                c->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(S, 0, (size_t)B * 8, c->stream);
+        if (e == cudaSuccess)
+            e = timed(c, "table", 2, [&] {
+                return launch_table_fused(B, M, M_pad, ldT, in->base, in->pick, in->drop, in->pd, d_border,
+                                          in->cost, costT, d_cellmin, S, metric, c->stream);
+            });
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);   // the host order goes out of scope
+        if (e == cudaSuccess) {
+            in->ldT = ldT;
+            in->costT_ok = true;
+            in->rowsum_ok = true;
+        }
+    } else if (e == cudaSuccess) {
         e = timed(c, "table", 2, [&] {
             return launch_table(B, M, M_pad, in->base, in->pick, in->drop, in->pd, in->cost, metric, c->stream);
         });
+    }
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     dev_free(c, order_tmp);
     if (e != cudaSuccess) {
@@ -1459,6 +1504,7 @@ stage_status stage_update_instance(stage_ctx *c, stage_inst h, const stage_updat
     dev_free(c, in->mem_ws);
     in->ws_K = 0;
     in->costT_ok = false;
+    in->rowsum_ok = false;
     return STAGE_OK;
 }
 

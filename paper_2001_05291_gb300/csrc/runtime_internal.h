@@ -52,8 +52,10 @@ struct Instance {
     DevBuf mem_chg;      // change records of the incremental neighbourhood ([2 * M_pad] int4)
     DevBuf mem_costT;    // the table mission-major for the incremental neighbourhood (M_pad x ldT)
     DevBuf mem_persist;  // accumulators, counters and barrier of the persistent search
+    DevBuf mem_rowsum;   // [B] uint64 row sums of the table, built with it (the ranking's key)
     int ldT = 0;
     bool costT_ok = false;   // mem_costT holds the current table
+    bool rowsum_ok = false;  // mem_rowsum holds the current table's row sums
     size_t scratch_bytes = 0;
     int busy = 0;        // batch requests referring to this instance
 };

@@ -90,8 +90,8 @@ struct TabuBuffers {
     // in a spatial order, costT[m * ldT + p] = cost of base border[p] for m
     const int32_t *costT;
     const int32_t *border;   // [ldT] position -> base id (-1 past B)
-    // [M_pad][ldT / 32]: each mission's least cost over each 32 consecutive
-    // positions of its costT row
+    // [M_pad][cell_ld(ldT)]: each mission's least cost over each 32
+    // consecutive positions of its costT row
     const int32_t *cellmin;
     int ldT;
 };
@@ -131,6 +131,21 @@ cudaError_t launch_swap_delta(const TabuBuffers &w, cudaStream_t s);
 // The B x M_pad table copied mission-major (M_pad x ldT, ldT = B rounded up to
 // 32), the bases in the order border (position -> base id, -1 past B).
 int table_ldT(int B);
+// row stride of the cell minima (cells of 32 positions of a mission-major row),
+// a multiple of 8 cells (32 bytes)
+__host__ __device__ inline int cell_ld(int ldT) { return ((ldT >> 5) + 7) & ~7; }
+// bytes of the mission-major copy with its position order and cell minima:
+// [M_pad][ldT] costs, [ldT] positions, [M_pad][cell_ld(ldT)] minima
+inline size_t costT_bytes(int M_pad, int ldT)
+{
+    return ((size_t)M_pad * ldT + (size_t)ldT + (size_t)M_pad * cell_ld(ldT)) * sizeof(int32_t);
+}
+// the table, its row sums (added to S, zeroed by the caller), the mission-major
+// copy (bases in the order border, row length ldT) and its cell minima, in one
+// pass; pd receives the pickup-to-drop-off legs
+cudaError_t launch_table_fused(int B, int M, int M_pad, int ldT, const int2 *base, const int2 *pick,
+                               const int2 *drop, int32_t *pd, const int32_t *border, int32_t *cost, int32_t *costT,
+                               int32_t *cellmin, unsigned long long *S, int metric, cudaStream_t s);
 cudaError_t launch_transpose_table(const int32_t *cost, int B, int M_pad, const int32_t *border, int32_t *costT,
                                    int32_t *cellmin,
                                    cudaStream_t s);
