@@ -263,9 +263,18 @@ KERNELS = ("table", "order", "rowsum", "topk", "init", "begin", "transpose", "sw
 # per iteration of the persistent search: the refresh reads each mission's
 # state (a, b: 8 B; best and second-best slot: 4 B) and its costs to the
 # opened and the closed base (8 B); the selection reads each candidate's gain
-# (4 + 8 B) and each (slot, candidate) extra term (4 + 8 B)
+# (4 + 8 B) and each (slot, candidate) extra term (4 + 8 B); the update reads
+# each record (32 B), its row of cell minima (4 B per cell, the row padded to
+# 8 cells) and the 128-byte piece of each cell whose minimum is below the
+# record's threshold (the cells that can hold a term; counted on the device)
 REFRESH_BYTES_PER_MISSION = 20
 SELECT_BYTES_PER_ENTRY = 12
+CELL_PIECE_BYTES = 128
+
+
+def cell_row_bytes(B):
+    ldT = (B + 31) // 32 * 32
+    return 4 * (((ldT // 32) + 7) // 8 * 8)
 
 
 def stored_traffic(fname, inst, args):
@@ -364,13 +373,14 @@ def run_ours(args):
                  "records_fraction": rec_per_launch / inst.M}
     # the persistent search (the incremental form's whole loop in one launch):
     # algorithmic bytes per launch = its iterations' refresh and selection
-    # reads plus the delta step's records (each record's row of the
-    # mission-major copy and the record itself)
+    # reads plus the update's records, their cell-minimum rows and the cell
+    # pieces that can hold a term
     n_pe, ms_pe = stats["persist"]
     persist = None
     if n_pe and ms_pe > 0:
         iters_run = ctx.kernel_stats("persist_refresh")[0]
-        rec_bytes = records * (TABLE_BYTES_PER_ELEM * (inst.B - 1) + DELTA_BYTES_PER_RECORD)
+        cells = ctx.kernel_stats("swap_delta_cells_read")[0]
+        rec_bytes = (records * (DELTA_BYTES_PER_RECORD + cell_row_bytes(inst.B)) + cells * CELL_PIECE_BYTES)
         ref_bytes = iters_run * REFRESH_BYTES_PER_MISSION * inst.M
         sel_bytes = iters_run * SELECT_BYTES_PER_ENTRY * (inst.K + 1) * nC
         p_bytes = (rec_bytes + ref_bytes + sel_bytes) / n_pe
@@ -396,6 +406,7 @@ def run_ours(args):
                                                 / max(1, ctx.kernel_stats("swap_delta_warp_passes")[0])),
                    "warp_passes_per_record": ctx.kernel_stats("swap_delta_warp_passes")[0] / max(1, records),
                    "column_run_writes_per_record": ctx.kernel_stats("swap_delta_run_writes")[0] / max(1, records),
+                   "cells_read_per_record": cells / max(1, records),
                    "bytes_per_iteration": {"update": rec_bytes / max(1, iters_run),
                                            "refresh": ref_bytes / max(1, iters_run),
                                            "select": sel_bytes / max(1, iters_run)},
@@ -560,13 +571,18 @@ def kernel_code(text: str) -> str:
     return "\n".join(" ".join(line.split()) for line in text.splitlines() if line.strip())
 
 
+KERNEL_SOURCES = ("kernels.cu", "persist.cu", "device_common.cuh")
+
+
 def kernel_digest() -> str:
-    """Hash of the kernel code (comments and spacing aside): stored ncu traffic
+    """Hash of the device code (comments and spacing aside): stored ncu traffic
     applies only to the same code."""
     import hashlib
-    src = os.path.join(ROOT, "paper_2001_05291_gb300", "csrc", "kernels.cu")
-    with open(src, encoding="utf-8") as fh:
-        return hashlib.sha256(kernel_code(fh.read()).encode()).hexdigest()[:16]
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2001_05291_gb300", "csrc", name), encoding="utf-8") as fh:
+            h.update(kernel_code(fh.read()).encode())
+    return h.hexdigest()[:16]
 
 
 def _ctx_for(args, stage, torch, local=0):

@@ -307,8 +307,8 @@ __global__ void __launch_bounds__(kPerThreads, 1) k_tabu_persist(PersistArgs A)
     // the update's (record, base) pairs with a term, and the (record, warp
     // cell) passes with at least one: the update's work and how densely it
     // fills the warps
-    __shared__ unsigned long long s_terms[3];
-    if (tid < 3) s_terms[tid] = 0;
+    __shared__ unsigned long long s_terms[4];
+    if (tid < 4) s_terms[tid] = 0;
 
     if (tid == 0) {
         S.t = st->t;
@@ -711,7 +711,10 @@ __global__ void __launch_bounds__(kPerThreads, 1) k_tabu_persist(PersistArgs A)
                         if (need) cl[cnt + __popc(bm & ((1u << lane) - 1u))] = (uint16_t)r;
                         cnt += __popc(bm);
                     }
-                    if (lane == 0) s_ccnt[cell] = cnt;
+                    if (lane == 0) {
+                        s_ccnt[cell] = cnt;
+                        atomicAdd(&s_terms[3], (unsigned long long)cnt);   // cells read (128 bytes each)
+                    }
                 }
                 __syncthreads();
                 // work items: each cell's list in pieces of at most kUpdItem
@@ -847,7 +850,7 @@ __global__ void __launch_bounds__(kPerThreads, 1) k_tabu_persist(PersistArgs A)
 
     // ------------------------------------------------ hand the state back (CTA 0)
     __syncthreads();
-    if (tid < 3) atomicAdd(reinterpret_cast<unsigned long long *>(&A.info[2 + tid]), s_terms[tid]);
+    if (tid < 4) atomicAdd(reinterpret_cast<unsigned long long *>(&A.info[2 + tid]), s_terms[tid]);
     if (tid == 0) {
         for (int k = 0; k < kClocks; k++) A.cta_ns[(size_t)blockIdx.x * kClocks + k] = s_clk[k];
         if (lead_cta) A.info[1] = rec_total;

@@ -591,7 +591,7 @@ stage_status run_tabu(stage_ctx *c, Instance *in, const stage_tabu_params *p,
         }));
         // the records over the search (the traffic accounting), the
         // (record, base) pairs with a term and the warps' passes over them
-        long long info[5] = {0, 0, 0, 0, 0};
+        long long info[6] = {0, 0, 0, 0, 0, 0};
         CK(cudaMemcpyAsync(info, static_cast<const char *>(in->mem_persist.p) + persist_info_offset(K), sizeof info,
                            cudaMemcpyDeviceToHost, c->stream));
         CK(cudaStreamSynchronize(c->stream));
@@ -602,6 +602,7 @@ stage_status run_tabu(stage_ctx *c, Instance *in, const stage_tabu_params *p,
             c->stats["swap_delta_term_pairs"].launches += info[2];
             c->stats["swap_delta_warp_passes"].launches += info[3];
             c->stats["swap_delta_run_writes"].launches += info[4];
+            c->stats["swap_delta_cells_read"].launches += info[5];
         }
         if (profiling) {
             // the kernel's own clocks: per step the mean over the CTAs and the

@@ -164,10 +164,10 @@ cudaError_t launch_swap_table(const TabuBuffers &w, int nC, long long *out_c, lo
 // takes on the current device (0 when the shape is not supported: K > 256,
 // more than 2048 bases, or the per-CTA arrays do not fit in shared memory).
 // The scratch (persist_scratch_bytes) holds the sums, barrier, error word,
-// per-CTA keys and record regions; at byte offset persist_info_offset(K) four
+// per-CTA keys and record regions; at byte offset persist_info_offset(K) six
 // int64 -- the CTAs, the records over the search, the update's (record, base)
-// pairs with a term, and the warps' passes (a record with a term in the warp)
-// -- and at persist_clock_offset(K, grid, M_pad) [grid][kPersistClocks] int64:
+// pairs with a term, its (record, cell) passes with a term, the extra-column
+// runs it wrote, and the (record, cell) pieces it read -- and at persist_clock_offset(K, grid, M_pad) [grid][kPersistClocks] int64:
 // each CTA's time in ns of each step (choose and apply the move, refresh, wait
 // at the barrier after it, update the columns, wait at the barrier after it,
 // select, wait at the barrier before the next move; then parts of the refresh
