@@ -400,17 +400,33 @@ typedef struct {
     stage_inst inst;                  /* resident instance, or 0 to use desc */
     const stage_instance_desc *desc;  /* host descriptor, copied at submit (inst == 0) */
     const stage_update *update;       /* applied to inst before the search, or NULL (copied at submit) */
-    stage_tabu_params params;         /* K <= 256; resume is not supported; start_open copied at submit */
+    stage_tabu_params params;         /* K <= 256; params.resume is not used (see resume_resident);
+                                         start_open copied at submit */
     stage_move *traj;                 /* [params.iters] host buffer or NULL; written before completion */
     int32_t *best_open;               /* [K] host buffer or NULL; sorted ascending */
     int32_t *final_open;              /* [K] host buffer or NULL; sorted ascending */
+    /* 1 (resident instances only): continue from the instance's resident
+     * state -- the end state (placement, tabu expiries, iteration number, best
+     * so far) of the last request on it that set this flag with the same K --
+     * and keep this search's end state as the new one.  With no resident state
+     * the search starts as usual (start_open, else the ranking).  After an
+     * update of the instance the best so far restarts from the resumed
+     * placement (its objective changed), and every open base the update made
+     * unavailable is first closed by a forced move (reading A15): it opens the
+     * available closed base with the best swap objective (covered desc,
+     * distance asc, base id asc), tabu ignored, the unavailable bases taken in
+     * ascending id; a forced move takes no iteration, and both of its bases
+     * are tabu for the next tenure iterations.  0: the resident state is
+     * neither used nor changed. */
+    int32_t resume_resident;
+    int32_t reserved1;
 } stage_request;
 
 typedef struct {
     stage_status status;
     int32_t n_moves;
     int32_t best_iter;
-    int32_t reserved0;
+    int32_t n_forced;      /* forced moves before the search (resume_resident after an update) */
     int64_t best_cov;
     int64_t best_dist;
     int64_t final_cov;

@@ -226,6 +226,43 @@ def tabu(cost, K, R, iters, tenure, start_open=None, avail=None, accept_worsenin
                       np.sort(final_open), io.final_cov, io.final_dist, expiry)
 
 
+def forced_moves(cost, open_, R, avail, t, tenure, expiry):
+    """Reading A15 (an open base that became unavailable, serving): each
+    unavailable open base i, in ascending id, is closed by opening the
+    available closed base j with the best objective F(O - i + j) -- more
+    covered, then less distance, then the lower j -- tabu ignored.  A forced
+    move takes no iteration; both bases get expiry t + tenure (tabu for the
+    next `tenure` iterations from t).  Returns (placement in slot order,
+    expiry, [(i, j, cov, dist)])."""
+    cost = _i32(cost)
+    B = cost.shape[0]
+    av = np.asarray(avail).astype(bool)
+    O = [int(x) for x in open_]
+    exp = np.array(expiry, dtype=np.int64).copy()
+    done = []
+    while True:
+        out = sorted(b for b in O if not av[b])
+        if not out:
+            return O, exp, done
+        i = out[0]
+        k = O.index(i)
+        best = None
+        for j in range(B):
+            if not av[j] or j in O:
+                continue
+            trial = O[:k] + [j] + O[k + 1:]
+            cov, dist = evaluate(cost, trial, R)
+            key = (-cov, dist, j)
+            if best is None or key < best[0]:
+                best = (key, j, cov, dist)
+        if best is None:
+            raise ValueError("no available closed base for a forced move")
+        _, j, cov, dist = best
+        O[k] = j
+        exp[i] = exp[j] = t + tenure
+        done.append((i, j, cov, dist))
+
+
 @dataclass
 class LocalSearchResult:
     moves: list             # list of (move number, i, j, MOVE_NEW_BEST, cov, dist)

@@ -227,7 +227,20 @@ bool Engine::admit(Ticket *tk, bool &transient, stage_inst &busy_on)
         return fail(STAGE_ERR_INVALID_ARG);
     }
     std::vector<int32_t> start(K);
-    if (!tk->start.empty()) {
+    // the instance's resident state (A15 forced moves after an update)
+    const ResidentState &rsd = in->resident;
+    const bool from_resident = tk->req.resume_resident && !tk->inline_inst && rsd.valid && rsd.K == K &&
+                               (int)rsd.expiry.size() == in->B && (int)rsd.open.size() == K;
+    std::vector<int32_t> expiry0(in->B, 0);
+    int t0 = 0, n_forced = 0;
+    const bool keep_best = from_resident && rsd.version == in->version;
+    if (from_resident) {
+        start = rsd.open;
+        expiry0 = rsd.expiry;
+        t0 = rsd.t;
+        s = forced_moves(c, in, start.data(), K, p.R, t0, p.tenure, expiry0.data(), &n_forced);
+        if (s != STAGE_OK) return fail(s);
+    } else if (!tk->start.empty()) {
         s = check_placement(c, in, tk->start.data(), K);
         if (s != STAGE_OK) return fail(s);
         start = tk->start;
@@ -269,20 +282,27 @@ bool Engine::admit(Ticket *tk, bool &transient, stage_inst &busy_on)
         if (in->h_avail[b] && !is_open[b]) cand.push_back(b);
     sl.nC = (int)cand.size();
     TabuDevState st{};
+    st.t = t0;
     st.tenure = p.tenure;
     st.accept_worsening = p.accept_worsening ? 1 : 0;
     st.nC = sl.nC;
     st.traj_cap = p.iters;
     st.best_iter = -1;
-    st.t_end = p.iters;
-    std::vector<int32_t> zeros(in->B, 0);
+    st.t_end = t0 + p.iters;
+    if (keep_best) {   // resumed with no update since: the best so far carries over
+        st.best_iter = rsd.best_iter;
+        st.best_cov = rsd.best_cov;
+        st.best_dist = rsd.best_dist;
+    }
     // set-up runs on the context's stream: the engine's stream may be busy
     // with the current step, which this slot is not part of
     cudaStream_t stream = c->stream;
     cudaError_t e = cudaMemcpyAsync(tb.open, start.data(), (size_t)K * 4, cudaMemcpyHostToDevice, stream);
     if (e == cudaSuccess && sl.nC)
         e = cudaMemcpyAsync(tb.cand, cand.data(), (size_t)sl.nC * 4, cudaMemcpyHostToDevice, stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(tb.expiry, zeros.data(), (size_t)in->B * 4, cudaMemcpyHostToDevice, stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(tb.expiry, expiry0.data(), (size_t)in->B * 4, cudaMemcpyHostToDevice, stream);
+    if (e == cudaSuccess && keep_best)
+        e = cudaMemcpyAsync(tb.best_open, rsd.best_open.data(), (size_t)K * 4, cudaMemcpyHostToDevice, stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(tb.st, &st, sizeof st, cudaMemcpyHostToDevice, stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(tb.v0, 0, 16, stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(tb.loss_c, 0, (size_t)K * 8, stream);
@@ -292,7 +312,8 @@ bool Engine::admit(Ticket *tk, bool &transient, stage_inst &busy_on)
     if (e == cudaSuccess) e = cudaMemsetAsync(tb.extra_c, 0, (size_t)K * in->B * 4, stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(tb.extra_d, 0, (size_t)K * in->B * 8, stream);
     if (e == cudaSuccess) e = timed_on(c, stream, "init", 1, [&] { return launch_init(tb, in->cost, stream); });
-    if (e == cudaSuccess) e = timed_on(c, stream, "begin", 1, [&] { return launch_begin(tb, 0, stream); });
+    if (e == cudaSuccess)
+        e = timed_on(c, stream, "begin", 1, [&] { return launch_begin(tb, keep_best ? 1 : 0, stream); });
     if (e == cudaSuccess) e = cudaStreamSynchronize(stream);   // host vectors above go out of scope
     if (e != cudaSuccess) {
         dev_free(c, sl.ws);
@@ -301,6 +322,7 @@ bool Engine::admit(Ticket *tk, bool &transient, stage_inst &busy_on)
     }
     sl.tb = tb;
     in->busy += 1;
+    tk->res.n_forced = n_forced;
     {
         std::lock_guard<std::mutex> lk(mu);
         tk->state = 1;
@@ -470,7 +492,7 @@ struct Retiring {
     Slot sl;
     TabuDevState s;
     stage_status status;
-    std::vector<int32_t> fin, best;
+    std::vector<int32_t> fin, best, expiry;   // fin and best in slot order until published
 };
 
 void Engine::retire_copy(Retiring &r)
@@ -485,6 +507,10 @@ void Engine::retire_copy(Retiring &r)
     cudaError_t e = cudaMemcpyAsync(r.fin.data(), sl.tb.open, (size_t)K * 4, cudaMemcpyDeviceToHost, cs);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(r.best.data(), sl.tb.best_open, (size_t)K * 4, cudaMemcpyDeviceToHost, cs);
+    if (e == cudaSuccess && tk->req.resume_resident && !tk->inline_inst) {   // kept as the resident state
+        r.expiry.assign(sl.in->B, 0);
+        e = cudaMemcpyAsync(r.expiry.data(), sl.tb.expiry, (size_t)sl.in->B * 4, cudaMemcpyDeviceToHost, cs);
+    }
     const int n = std::min(r.s.n_moves, tk->req.params.iters);
     if (e == cudaSuccess && tk->req.traj && n > 0)
         e = cudaMemcpyAsync(tk->req.traj, sl.tb.traj, (size_t)n * sizeof(stage_move), cudaMemcpyDeviceToHost, cs);
@@ -498,6 +524,19 @@ void Engine::retire_finish(Retiring &r, bool copies_ok)
     stage_status status = r.status;
     if (!copies_ok && status == STAGE_OK) status = STAGE_ERR_CUDA;
     if (r.s.err && status == STAGE_OK) status = STAGE_ERR_INTERNAL;
+    if (tk->req.resume_resident && !tk->inline_inst) {
+        ResidentState &rs = sl.in->resident;
+        rs.valid = status == STAGE_OK && (int)r.expiry.size() == sl.in->B;
+        rs.K = sl.tb.K;
+        rs.t = r.s.t;
+        rs.best_iter = r.s.best_iter;
+        rs.best_cov = r.s.best_cov;
+        rs.best_dist = r.s.best_dist;
+        rs.version = sl.in->version;
+        rs.open = r.fin;
+        rs.best_open = r.best;
+        rs.expiry = r.expiry;
+    }
     std::sort(r.fin.begin(), r.fin.end());
     std::sort(r.best.begin(), r.best.end());
     if (tk->req.best_open) std::copy(r.best.begin(), r.best.end(), tk->req.best_open);

@@ -341,6 +341,54 @@ stage_status setup_search(stage_ctx *c, Instance *in, const int32_t *open, int K
     return STAGE_OK;
 }
 
+// A15 (reading): every open base of `open` that the instance no longer has
+// available is closed by a forced move, the unavailable ones in ascending id:
+// it opens the available closed base j with the best objective of the swap
+// (a4: F(O - i + j) by covered desc, distance asc, then j asc), tabu ignored.
+// A forced move takes no iteration; both bases become tabu for the next
+// `tenure` iterations from t (expiry = t + tenure).  Each move evaluates the
+// whole swap neighbourhood of the current placement once on the device.
+stage_status forced_moves(stage_ctx *c, Instance *in, int32_t *open, int K, int R, int t, int tenure,
+                          int32_t *expiry, int *n_forced)
+{
+    *n_forced = 0;
+    const int B = in->B;
+    const size_t n = (size_t)K * B;
+    std::vector<long long> cov, dist;
+    for (;;) {
+        int k_out = -1;
+        for (int k = 0; k < K; k++)
+            if (!in->h_avail[open[k]] && (k_out < 0 || open[k] < open[k_out])) k_out = k;
+        if (k_out < 0) return STAGE_OK;
+        int nC = 0;
+        stage_status s = setup_search(c, in, open, K, R, 0, 0, 1, 0, nullptr, &nC);
+        if (s != STAGE_OK) return s;
+        s = ensure_scratch(c, in, 2 * round_up(n * 8, 256));
+        if (s != STAGE_OK) return s;
+        auto *oc = static_cast<long long *>(in->mem_scratch.p);
+        auto *od = reinterpret_cast<long long *>(static_cast<char *>(in->mem_scratch.p) + round_up(n * 8, 256));
+        CK(cudaMemsetAsync(oc, 0xff, n * 8, c->stream));
+        CK(cudaMemsetAsync(od, 0xff, n * 8, c->stream));
+        CK(timed(c, "swap_eval", 1, [&] { return launch_swap_eval(in->tb, in->cost, nC, 1, c->stream); }));
+        CK(launch_swap_table(in->tb, nC, oc, od, c->stream));
+        cov.resize(B);
+        dist.resize(B);
+        CK(cudaMemcpyAsync(cov.data(), oc + (size_t)k_out * B, (size_t)B * 8, cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaMemcpyAsync(dist.data(), od + (size_t)k_out * B, (size_t)B * 8, cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        int jb = -1;
+        for (int j = 0; j < B; j++) {
+            if (cov[j] < 0) continue;   // open or unavailable
+            if (jb < 0 || cov[j] > cov[jb] || (cov[j] == cov[jb] && dist[j] < dist[jb])) jb = j;
+        }
+        if (jb < 0) return set_err(c, STAGE_ERR_INVALID_ARG, "no available closed base for a forced move");
+        const int i = open[k_out];
+        open[k_out] = jb;
+        expiry[i] = expiry[jb] = t + tenure;
+        *n_forced += 1;
+    }
+}
+
 // Time the swap pass for each candidate missions-per-block and record the
 // fastest for this shape bucket.  Runs on a scratch search state that is
 // discarded (every search sets its state up afresh).
@@ -1506,6 +1554,7 @@ stage_status stage_update_instance(stage_ctx *c, stage_inst h, const stage_updat
     in->ws_K = 0;
     in->costT_ok = false;
     in->rowsum_ok = false;
+    in->version += 1;
     return STAGE_OK;
 }
 

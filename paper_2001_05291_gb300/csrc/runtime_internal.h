@@ -30,6 +30,17 @@ struct KernelStat {
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending;
 };
 
+// The end state of the last batch search on a resident instance that asked
+// to keep it (stage_request.resume_resident): the next such request resumes
+// from it.  `version` is the instance's update count when it was saved.
+struct ResidentState {
+    bool valid = false;
+    int K = 0, t = 0, best_iter = -1;
+    int64_t best_cov = 0, best_dist = 0;
+    uint64_t version = 0;
+    std::vector<int32_t> open, best_open, expiry;
+};
+
 struct Instance {
     int B = 0, M = 0, M_pad = 0;   // M: table columns in use (live + removed); M_pad: allocated columns
     int metric = 0;                // 0: Euclidean legs on metres, 1: Haversine legs on microdegrees (Eq. 1)
@@ -58,6 +69,8 @@ struct Instance {
     bool rowsum_ok = false;  // mem_rowsum holds the current table's row sums
     size_t scratch_bytes = 0;
     int busy = 0;        // batch requests referring to this instance
+    uint64_t version = 0;      // stage_update_instance calls so far
+    ResidentState resident;    // kept between batch requests (resume_resident)
 };
 
 struct Engine;   // batch engine (engine.cu)
@@ -101,6 +114,10 @@ stage_status check_placement(stage_ctx *c, Instance *in, const int32_t *open, in
 stage_status do_rank(stage_ctx *c, Instance *in, int K, int32_t *out_open, int64_t *out_rowsum);
 void engine_destroy(stage_ctx *c);
 stage_status autotune_shape(stage_ctx *c, Instance *in, const int32_t *open, int K, int R, int *out_seg);
+stage_status setup_search(stage_ctx *c, Instance *in, const int32_t *open, int K, int R, int traj_cap, int tenure,
+                          int accept_worsening, int t0, const int32_t *expiry_in, int *out_nC);
+stage_status forced_moves(stage_ctx *c, Instance *in, int32_t *open, int K, int R, int t, int tenure,
+                          int32_t *expiry, int *n_forced);
 
 // Launch through `f`, counting launches and (with STAGE_PROFILE) timing them
 // on `stream`.

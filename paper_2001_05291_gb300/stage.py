@@ -96,12 +96,13 @@ class StageUpdate(C.Structure):
 class StageRequest(C.Structure):
     _fields_ = [("inst", C.c_uint64), ("desc", C.POINTER(StageInstanceDesc)),
                 ("update", C.POINTER(StageUpdate)), ("params", StageTabuParams),
-                ("traj", C.c_void_p), ("best_open", C.c_void_p), ("final_open", C.c_void_p)]
+                ("traj", C.c_void_p), ("best_open", C.c_void_p), ("final_open", C.c_void_p),
+                ("resume_resident", C.c_int32), ("reserved1", C.c_int32)]
 
 
 class StageResult(C.Structure):
     _fields_ = [("status", C.c_int32), ("n_moves", C.c_int32), ("best_iter", C.c_int32),
-                ("reserved0", C.c_int32), ("best_cov", C.c_int64), ("best_dist", C.c_int64),
+                ("n_forced", C.c_int32), ("best_cov", C.c_int64), ("best_dist", C.c_int64),
                 ("final_cov", C.c_int64), ("final_dist", C.c_int64), ("t_submit_ns", C.c_int64),
                 ("t_start_ns", C.c_int64), ("t_end_ns", C.c_int64)]
 
@@ -506,7 +507,9 @@ class Context:
     def batch_submit(self, requests):
         """stage_batch_submit.  Each request is a dict: inst (handle) or base_xy/pick_xy/drop_xy
         (+ base_available) for an instance given by value; K, R, iters, tenure;
-        optional start_open, accept_worsening, update (dict of update_instance's arguments).
+        optional start_open, accept_worsening, update (dict of update_instance's arguments),
+        resume_resident (continue from the resident instance's kept end state, A15 forced moves
+        after an update; the result's n_forced counts them).
         Returns a list of BatchTicket; call .wait() (or Context.poll) for results."""
         n = len(requests)
         arr = (StageRequest * max(1, n))()
@@ -536,6 +539,7 @@ class Context:
             K, iters = rq["K"], rq["iters"]
             r.params.K, r.params.R, r.params.iters, r.params.tenure = K, rq["R"], iters, rq["tenure"]
             r.params.accept_worsening = 1 if rq.get("accept_worsening", True) else 0
+            r.resume_resident = 1 if rq.get("resume_resident") else 0
             if rq.get("start_open") is not None:
                 so = _host_i32(rq["start_open"], K)
                 keep.append(so)
@@ -563,6 +567,7 @@ class Context:
         out = TabuResult(res.n_moves, ticket.best, res.best_cov, res.best_dist, res.best_iter, ticket.final,
                          res.final_cov, res.final_dist, moves)
         out.timing = dict(submit_ns=res.t_submit_ns, start_ns=res.t_start_ns, end_ns=res.t_end_ns)
+        out.n_forced = res.n_forced
         return out
 
     def autotune(self, inst: int, K: int, R: int, open_=None) -> int:

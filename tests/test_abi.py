@@ -61,7 +61,8 @@ int main(void) {
   P(stage_tabu_result); O(stage_tabu_result, best_open); O(stage_tabu_result, end_state);
   P(stage_update); O(stage_update, add_pick_xy); O(stage_update, avail_ids);
   P(stage_request); O(stage_request, params); O(stage_request, traj); O(stage_request, final_open);
-  P(stage_result); O(stage_result, best_cov); O(stage_result, t_end_ns);
+  O(stage_request, resume_resident);
+  P(stage_result); O(stage_result, n_forced); O(stage_result, best_cov); O(stage_result, t_end_ns);
   P(stage_ls_params); O(stage_ls_params, perm_slots); O(stage_ls_params, start_open);
   P(stage_ls_result); O(stage_ls_result, final_cov); O(stage_ls_result, final_open);
   P(stage_fleet_params); O(stage_fleet_params, base_helipad); O(stage_fleet_params, start_fixed);

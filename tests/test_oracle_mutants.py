@@ -1,7 +1,8 @@
 """Planted mistakes in a copy of the oracle, on the CPU: each plausible slip
 (a dropped term, a flipped sign or comparison, an off-by-one) must make at least
 one pin fail -- of tests/test_oracle_pins.py for the C part (oracle.c), of
-tests/test_oracle_fleet.py for the heterogeneous-fleet part (Python)."""
+tests/test_oracle_fleet.py and tests/test_oracle_resume.py for the Python parts
+(the heterogeneous fleet, the forced moves of reading A15)."""
 import os
 import subprocess
 import sys
@@ -62,7 +63,12 @@ PY_MUTANTS = {
     "fleet_tenure_off_by_one": ("expiry[i] = expiry[j] = t + tenure + 1", "expiry[i] = expiry[j] = t + tenure"),
     "fleet_no_aspiration": ("adm = [k for k in keys if not k[6] or better(k[1], best)]",
                             "adm = [k for k in keys if not k[6]]"),
+    # forced moves (reading A15)
+    "forced_move_tie_high_j": ("key = (-cov, dist, j)", "key = (-cov, dist, -j)"),
+    "forced_move_expiry_off_by_one": ("exp[i] = exp[j] = t + tenure", "exp[i] = exp[j] = t + tenure + 1"),
+    "forced_moves_descending_ids": ("        i = out[0]\n", "        i = out[-1]\n"),
 }
+PY_PIN_FILES = ("test_oracle_fleet.py", "test_oracle_resume.py")
 
 
 @pytest.mark.parametrize("name", sorted(PY_MUTANTS))
@@ -74,8 +80,8 @@ def test_fleet_pins_catch_mutant(name, tmp_path, orc):
     pkg.mkdir()
     (pkg / "__init__.py").write_text(src.replace(old, new))
     env = dict(os.environ, ORACLE_PY_OVERRIDE=str(tmp_path), ORACLE_LIB_OVERRIDE=orc.build())
-    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
-                        os.path.join(ROOT, "tests", "test_oracle_fleet.py")],
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider"] +
+                       [os.path.join(ROOT, "tests", f) for f in PY_PIN_FILES],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     assert r.returncode != 0, f"mutant {name} survived the pins:\n{r.stdout[-2000:]}"
 
@@ -89,7 +95,7 @@ def test_fleet_mutant_harness_runs_the_copy(tmp_path, orc):
     r = subprocess.run([sys.executable, "-c", "import sys; sys.path.insert(0, 'tests'); import conftest, oracle; "
                         "print(oracle.COPY_MARK)"], cwd=ROOT, env=env, capture_output=True, text=True, timeout=120)
     assert r.stdout.strip() == "1", r.stderr
-    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
-                        os.path.join(ROOT, "tests", "test_oracle_fleet.py")],
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider"] +
+                       [os.path.join(ROOT, "tests", f) for f in PY_PIN_FILES],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     assert r.returncode == 0, r.stdout[-2000:]
