@@ -726,7 +726,10 @@ def run_serving(args):
                 upd, added = make_update(r, inst, n_ids[p], closed[p])
                 n_ids[p] += added
                 closed[p].update(upd.get("unavailable", []))
-                rq = dict(inst=hs[p], K=inst.K, R=inst.R, iters=300, tenure=11, update=upd)
+                # the engine resumes each resident instance's search from its
+                # kept state (forced moves off closed open bases, reading A15)
+                rq = dict(inst=hs[p], K=inst.K, R=inst.R, iters=300, tenure=11, update=upd,
+                          resume_resident=True)
             if engine:
                 pending.append((arrive, ctx.batch_submit([rq])[0]))
             else:
@@ -772,7 +775,10 @@ def run_serving(args):
             "data": "synthetic",
             "config": {"workload": f"serving: seed 4, Poisson {args.rate:g} req/s for {args.duration:g} s, 30 % "
                                    f"updates to 32 resident instances, 70 % fresh instances of the batched size "
-                                   f"distribution, 300 Tabu iterations, tenure 11", "slots": args.slots},
+                                   f"distribution, 300 Tabu iterations, tenure 11; the engine resumes updated "
+                                   f"resident instances from their kept Tabu state, the serial plain path "
+                                   f"restarts them from the ranking (same iteration counts)",
+                       "slots": args.slots},
             "engine": eng, "serial_plain": ser}
     print(json.dumps(line))
     return 0

@@ -96,6 +96,15 @@ struct Engine {
 
     // requests waiting for their instance's current search to finish, per instance, in order
     std::unordered_map<stage_inst, std::deque<Ticket *>> parked;
+    // instances whose next request was released from `parked` and waits in
+    // `pending`: until it is admitted (or fails for good) later requests on the
+    // instance park behind it, so requests on one instance keep their order
+    std::unordered_map<stage_inst, int> releasing;
+    void unrelease(stage_inst h)
+    {
+        auto it = releasing.find(h);
+        if (it != releasing.end() && --it->second <= 0) releasing.erase(it);
+    }
     std::vector<struct Retiring> retiring;   // finished in the last round, released during the next
     void retire_pending();
 
@@ -169,7 +178,9 @@ bool Engine::admit(Ticket *tk, bool &transient, stage_inst &busy_on)
             d.base_available = tk->d_avail.empty() ? nullptr : tk->d_avail.data();
             d.flags = tk->d_flags;
             stage_inst h = 0;
+            c->load_without_copy = true;   // (the context lock is held)
             s = stage_load_instance(c, &d, &h);
+            c->load_without_copy = false;
             if (s == STAGE_ERR_ADMISSION || s == STAGE_ERR_NO_MEMORY) {
                 transient = !active.empty();
                 if (!transient) complete(tk, s);
@@ -188,7 +199,7 @@ bool Engine::admit(Ticket *tk, bool &transient, stage_inst &busy_on)
         complete(tk, STAGE_ERR_NOT_FOUND);
         return false;
     }
-    if (in->busy || (parked.count(tk->inst) && !tk->released)) {
+    if (in->busy || (!tk->released && (parked.count(tk->inst) || releasing.count(tk->inst)))) {
         busy_on = tk->inst;   // one request per instance at a time: updates and searches stay ordered
         return false;
     }
@@ -561,6 +572,7 @@ void Engine::retire_finish(Retiring &r, bool copies_ok)
         it->second.pop_front();
         if (it->second.empty()) parked.erase(it);
         nx->released = true;
+        releasing[inst] += 1;
         std::lock_guard<std::mutex> lk(mu);
         pending.push_front(nx);
     }
@@ -667,12 +679,25 @@ void Engine::run()
             PhaseClock pc(c, "engine_admit");
             bool transient = false;
             stage_inst busy_on = 0;
-            if (admit(tk, transient, busy_on)) continue;
+            const bool was_released = tk->released;
+            const stage_inst h0 = tk->inst;
+            if (admit(tk, transient, busy_on)) {
+                if (was_released) unrelease(h0);
+                continue;
+            }
             if (busy_on) {
-                parked[busy_on].push_back(tk);
+                if (was_released) {   // back to the head of its instance's queue
+                    unrelease(h0);
+                    tk->released = false;
+                    parked[busy_on].push_front(tk);
+                } else {
+                    parked[busy_on].push_back(tk);
+                }
             } else if (transient) {
-                retry.push_back(tk);
+                retry.push_back(tk);   // a released request stays released (and counted)
                 if (tk->inst && !tk->inline_inst) held.insert(tk->inst);
+            } else if (was_released) {
+                unrelease(h0);         // failed for good
             }
         }
         if (!retry.empty()) {

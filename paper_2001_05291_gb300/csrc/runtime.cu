@@ -1354,7 +1354,7 @@ stage_status stage_load_instance(stage_ctx *c, const stage_instance_desc *d, sta
     // (with no room for the copy, the table alone; the copy follows when a
     // search needs it)
     const int ldT = table_ldT(B);
-    const bool want_copy = !(c->flags & STAGE_FULL_PASS) &&
+    const bool want_copy = !c->load_without_copy && !(c->flags & STAGE_FULL_PASS) &&
                            ((c->flags & STAGE_INCREMENTAL) || (size_t)B * M_pad * 4 >= kIncrementalMinTableBytes);
     bool fused = false;
     if (e == cudaSuccess && want_copy) {

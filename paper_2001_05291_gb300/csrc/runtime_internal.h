@@ -83,6 +83,9 @@ struct stage_ctx {
     uint64_t budget = 0;
     int max_slots = 8;
     int64_t spin_limit = 1ll << 26;
+    // set by the batch engine around its loads of instances given by value:
+    // its grouped searches never read a mission-major copy, so none is built
+    bool load_without_copy = false;
     stage_alloc_fn alloc = nullptr;
     stage_free_fn free = nullptr;
     void *alloc_user = nullptr;

@@ -561,7 +561,10 @@ class Context:
             return None
         ticket.done = True
         if rc < 0:
-            raise StageError(rc, f"batch request failed (ticket {ticket.id})")
+            buf = C.create_string_buffer(512)
+            lib().stage_last_error(self._h, buf, 512)
+            raise StageError(rc, f"batch request failed (ticket {ticket.id}); the context's last error: "
+                                 f"{buf.value.decode(errors='replace')}")
         moves = [(ticket.traj[k].iter, ticket.traj[k].i, ticket.traj[k].j, ticket.traj[k].flags,
                   ticket.traj[k].cov, ticket.traj[k].dist) for k in range(res.n_moves)]
         out = TabuResult(res.n_moves, ticket.best, res.best_cov, res.best_dist, res.best_iter, ticket.final,

@@ -157,3 +157,29 @@ def test_batch_admission_and_errors(stage_mod):
             ctx.batch_submit([dict(base_xy=tiny.base_xy, pick_xy=tiny.pick_xy, drop_xy=tiny.drop_xy, K=300,
                                    R=tiny.R, iters=5, tenure=2)])[0].wait()
         assert e.value.status == -1
+
+
+def test_requests_on_one_instance_keep_their_order(stage_mod):
+    """Each removal names a mission the request just before it added: out of
+    order, the removal would be refused (an unknown id).  Requests arrive one
+    by one with other traffic between them, so releases of waiting requests
+    and admissions of new ones interleave."""
+    stage = stage_mod
+    inst = small(51, 40, 2000, 4)
+    with stage.Context(device=0, max_slots=6) as ctx:
+        h = ctx.load_instance(inst.base_xy, inst.pick_xy, inst.drop_xy)
+        n_ids, tickets = inst.M, []
+        for k in range(48):
+            if k % 2 == 0:
+                add = small(60 + k, 40, 30, 4)
+                upd = dict(add_pick=add.pick_xy, add_drop=add.drop_xy)
+                n_ids += 30
+            else:
+                upd = dict(remove=[n_ids - 1 - (k % 30)])
+            tickets += ctx.batch_submit([dict(inst=h, K=4, R=inst.R, iters=3, tenure=2, update=upd,
+                                              resume_resident=(k % 3 == 0))])
+            other = small(200 + k, 30, 1500, 3)
+            tickets += ctx.batch_submit([dict(base_xy=other.base_xy, pick_xy=other.pick_xy, drop_xy=other.drop_xy,
+                                              K=3, R=other.R, iters=3, tenure=2)])
+        for t in tickets:
+            t.wait()   # raises on a refused request
