@@ -55,9 +55,18 @@ struct Slot {
     Ticket *tk = nullptr;
     Instance *in = nullptr;
     DevBuf ws;
+    DevBuf chg;               // incremental slots: the refresh's change records
     TabuBuffers tb{};
     int nC = 0;
+    bool first_done = false;  // incremental slots: the first full pass has run
 };
+
+// Slots whose candidate rows x missions reach this many table bytes keep the
+// swap terms across steps (the incremental neighbourhood of a single search:
+// one full pass, then per step the records of the missions a move touched);
+// smaller ones stream their table every step.  Lower than the single search's
+// threshold: a batch's tables share L2 and are streamed from HBM anyway.
+constexpr size_t kEngineIncrementalMinBytes = 8ull << 20;
 
 }  // namespace
 
@@ -85,7 +94,7 @@ struct Engine {
     // latency-bound selection and refresh overlap another's streaming swap
     // pass instead of leaving SMs idle between kernels.
     struct Lane {
-        int n_swap = 0, n_sel = 0, n_ref = 0, maxK = 1;
+        int n_swap = 0, n_sel = 0, n_ref = 0, n_delta = 0, maxK = 1;
         size_t swap_smem = 0;
         size_t map_off = 0;   // first entry of this lane's block maps in d_map
     };
@@ -286,6 +295,27 @@ bool Engine::admit(Ticket *tk, bool &transient, stage_inst &busy_on)
     tb.M = in->M;
     tb.M_pad = in->M_pad;
     tb.R = p.R;
+    // the incremental form where the table is large enough and there is room
+    // for the mission-major copy and the records (else a full pass per step)
+    {
+        int nc_est = 0;
+        for (int b = 0; b < in->B; b++) nc_est += in->h_avail[b];
+        nc_est -= K;
+        const bool want = !(c->flags & STAGE_FULL_PASS) && swap_delta_fits(K) && nc_est > 0 &&
+                          ((c->flags & STAGE_INCREMENTAL) ||
+                           (size_t)nc_est * in->M_pad * sizeof(int32_t) >= kEngineIncrementalMinBytes);
+        if (want && ensure_costT(c, in) == STAGE_OK &&
+            dev_alloc(c, (size_t)in->M_pad * 2 * sizeof(int4), sl.chg) == STAGE_OK) {
+            tb.chg = static_cast<int4 *>(sl.chg.p);
+            tb.costT = static_cast<const int32_t *>(in->mem_costT.p);
+            tb.border = tb.costT + (size_t)in->M_pad * in->ldT;
+            tb.cellmin = tb.border + in->ldT;
+            tb.ldT = in->ldT;
+        } else {
+            dev_free(c, sl.chg);
+            set_err(c, STAGE_OK, "");   // a refused buffer only means the full pass
+        }
+    }
     std::vector<uint8_t> is_open(in->B, 0);
     for (int k = 0; k < K; k++) is_open[start[k]] = 1;
     std::vector<int32_t> cand;
@@ -328,6 +358,7 @@ bool Engine::admit(Ticket *tk, bool &transient, stage_inst &busy_on)
     if (e == cudaSuccess) e = cudaStreamSynchronize(stream);   // host vectors above go out of scope
     if (e != cudaSuccess) {
         dev_free(c, sl.ws);
+        dev_free(c, sl.chg);
         set_err(c, STAGE_ERR_CUDA, "batch slot set-up failed: %s", cudaGetErrorString(e));
         return fail(STAGE_ERR_CUDA);
     }
@@ -403,6 +434,11 @@ stage_status Engine::rebuild()
         gs[k].cost = sl.in->cost;
         gs[k].swap_blocks =
             group_swap_blocks(sl.tb.M_pad, sl.nC, sl.tb.K, common, &gs[k].swap_bx, &gs[k].swap_seg);
+        gs[k].delta_bx = gs[k].delta_by = 0;
+        if (sl.tb.chg) {
+            group_delta_blocks(sl.tb.ldT, sl.tb.M, &gs[k].delta_bx, &gs[k].delta_by);
+            if (sl.first_done) gs[k].swap_blocks = 0;   // its terms are kept by the delta step
+        }
         gs[k].sel_blocks = select_blocks(sl.tb.K, sl.nC);
         gs[k].ref_blocks = group_ref_blocks(sl.tb.M_pad);
     }
@@ -424,6 +460,9 @@ stage_status Engine::rebuild()
         for (int k = k0; k < k1; k++)
             for (int b = 0; b < gs[k].ref_blocks; b++) map.push_back(make_int2(k, b));
         ln.n_ref = (int)(map.size() - ln.map_off) - ln.n_swap - ln.n_sel;
+        for (int k = k0; k < k1; k++)
+            for (int b = 0; b < gs[k].delta_bx * gs[k].delta_by; b++) map.push_back(make_int2(k, b));
+        ln.n_delta = (int)(map.size() - ln.map_off) - ln.n_swap - ln.n_sel - ln.n_ref;
     }
     if (map.size() > map_cap) {
         std::lock_guard<std::recursive_mutex> g(c->mu);
@@ -455,15 +494,17 @@ cudaError_t Engine::launch_steps(int steps)
         const int2 *map_swap = static_cast<const int2 *>(d_map.p) + ln.map_off;
         const int2 *map_sel = map_swap + ln.n_swap;
         const int2 *map_ref = map_sel + ln.n_sel;
+        const int2 *map_delta = map_ref + ln.n_ref;
         cudaError_t e = cudaSuccess;
         for (int k = 0; e == cudaSuccess && k < steps; k++) {
             e = launch_group_swap(ds, map_swap, ln.n_swap, ln.swap_smem, s);
             if (e == cudaSuccess) e = launch_group_select(ds, map_sel, ln.n_sel, s);
             if (e == cudaSuccess) e = launch_group_refresh(ds, map_ref, ln.n_ref, ln.maxK, s);
+            if (e == cudaSuccess) e = launch_group_delta(ds, map_delta, ln.n_delta, s);
         }
         return e;
     };
-    auto used = [&](int l) { return lane[l].n_swap + lane[l].n_sel + lane[l].n_ref > 0; };
+    auto used = [&](int l) { return lane[l].n_swap + lane[l].n_sel + lane[l].n_ref + lane[l].n_delta > 0; };
     auto enqueue = [&]() {
         cudaError_t e = cudaEventRecord(ev_fork, stream);
         for (int l = 1; e == cudaSuccess && l < kLanes; l++)
@@ -562,6 +603,7 @@ void Engine::retire_finish(Retiring &r, bool copies_ok)
     {
         std::lock_guard<std::recursive_mutex> g(c->mu);
         dev_free(c, sl.ws);
+        dev_free(c, sl.chg);
         sl.in->busy -= 1;
         if (tk->inline_inst) stage_unload_instance(c, tk->inst);
     }
@@ -645,6 +687,9 @@ void Engine::run()
                     std::lock_guard<std::recursive_mutex> g(c->mu);
                     for (const char *nm : {"group_swap", "group_select", "group_refresh"})
                         c->stats[nm].launches += kStepsPerGraph;
+                    int n_delta = 0;
+                    for (int l = 0; l < kLanes; l++) n_delta += lane[l].n_delta;
+                    if (n_delta > 0) c->stats["group_delta"].launches += kStepsPerGraph;
                     c->stats["group_steps"].launches += kStepsPerGraph;
                 }
                 if (!ev_round[0]) {
@@ -717,6 +762,7 @@ void Engine::run()
                 k.launches += 1;
                 k.ms += gpu_ms;
             }
+            int erased = 0;
             for (size_t k = n; k-- > 0;) {   // descending: erasing keeps the lower indices
                 TabuDevState z{};
                 const TabuDevState &s = e == cudaSuccess ? h_states[k] : z;
@@ -724,8 +770,17 @@ void Engine::run()
                 if (!fin) continue;
                 retiring.push_back(Retiring{active[k], s, e != cudaSuccess ? STAGE_ERR_CUDA : STAGE_OK, {}, {}});
                 active.erase(active.begin() + k);
+                erased += 1;
                 dirty = true;
             }
+            // incremental slots that took part ran their first full pass: the
+            // next map leaves out their swap blocks (the round's remaining
+            // slots are the first n - erased; slots admitted meanwhile follow)
+            for (int k = 0; k < n - erased; k++)
+                if (active[k].tb.chg && !active[k].first_done) {
+                    active[k].first_done = true;
+                    dirty = true;
+                }
             // nothing left to run: release now rather than after a next round
             if (active.empty() && !retiring.empty()) {
                 PhaseClock pc(c, "engine_retire");

@@ -1576,7 +1576,9 @@ bool swap_delta_fits(int K) { return K <= kPipeMaxK; }
 // the others pass the mission together.  The gain terms of the base add up
 // in registers; the extra terms go out in runs of one slot (the records come
 // in runs of neighbouring missions, which share slots).
-__global__ void __launch_bounds__(kDeltaRows) k_swap_delta(TabuBuffers w)
+// Block (bx, by) of a gx x gy grid: positions bx * kDeltaRows .. +255, record
+// chunks by, by + gy, ...
+__device__ __forceinline__ void swap_delta_body(const TabuBuffers &w, int bx, int by, int gy)
 {
     TabuDevState *st = w.st;
     if (st->done || st->ls_hold) return;
@@ -1584,16 +1586,23 @@ __global__ void __launch_bounds__(kDeltaRows) k_swap_delta(TabuBuffers w)
     __shared__ int4 s_new[kDeltaChunk];   // clamped a, clamped b, best slot: after
     __shared__ long long s_off[kDeltaChunk];   // the mission's row in the mission-major copy
     __shared__ int s_hi[kDeltaChunk];          // the larger clamped second best: no term from x >= it
+    // the minima of the block's cells (a warp's 32 positions each) in each
+    // staged mission's row: a warp whose cell minimum is at or above the
+    // threshold has no term there and loads nothing (rows of 16 cells or more)
+    __shared__ int s_cm[kDeltaChunk][kDeltaRows / 32];
     const int ic = st->mv_i, R = w.R;
     const int nrec = min(st->chg_n, w.M);
-    const int p = blockIdx.x * kDeltaRows + (int)threadIdx.x;
+    const int p = bx * kDeltaRows + (int)threadIdx.x;
     const int j = p < w.ldT ? w.border[p] : -1;
     const bool row = j >= 0 && j != ic;   // the closed base's column: the refresh
     const int32_t *colp = w.costT + (row ? p : 0);
     const size_t ld = (size_t)w.ldT;
+    // skipping cells pays only on long rows: the staging of the minima costs a
+    // barrier and a scattered load per (record, cell) of each chunk
+    const bool use_cm = (ld >> 5) >= 16;
     long long gc = 0, gd = 0;
     DeltaRun rn{-1, 0, 0}, ro{-1, 0, 0};   // the new state's terms, the old state's (taken out)
-    for (int e0 = blockIdx.y * kDeltaChunk; e0 < nrec; e0 += gridDim.y * kDeltaChunk) {   // the same on every thread
+    for (int e0 = by * kDeltaChunk; e0 < nrec; e0 += gy * kDeltaChunk) {   // the same on every thread
         const int n = min(kDeltaChunk, nrec - e0);
         __syncthreads();   // the previous chunk is consumed
         if ((int)threadIdx.x < n) {
@@ -1605,11 +1614,22 @@ __global__ void __launch_bounds__(kDeltaRows) k_swap_delta(TabuBuffers w)
             s_hi[threadIdx.x] = max(bo1, bn1);
         }
         __syncthreads();
+        if (use_cm) {   // the same on the block
+            static_assert(kDeltaChunk * (kDeltaRows / 32) == kDeltaRows, "one cell minimum per thread");
+            const int r = threadIdx.x / (kDeltaRows / 32), cw = threadIdx.x % (kDeltaRows / 32);
+            const int cell = bx * (kDeltaRows / 32) + cw, nCell = (int)(ld >> 5);
+            s_cm[r][cw] = (r < n && cell < nCell) ? __ldg(&w.cellmin[(size_t)s_old[r].x * cell_ld((int)ld) + cell])
+                                                  : INT_MAX;
+            __syncthreads();
+        }
         if (!row) continue;
+        const int cw = (int)threadIdx.x >> 5;   // this warp's cell of the block
         for (int k0 = 0; k0 < n; k0 += kDeltaBatch) {
             int xv[kDeltaBatch];
 #pragma unroll
-            for (int u = 0; u < kDeltaBatch; u++) xv[u] = k0 + u < n ? __ldg(colp + s_off[k0 + u]) : INT_MAX;
+            for (int u = 0; u < kDeltaBatch; u++)
+                xv[u] = (k0 + u < n && (!use_cm || s_cm[k0 + u][cw] < s_hi[k0 + u])) ? __ldg(colp + s_off[k0 + u])
+                                                                                     : INT_MAX;
 #pragma unroll
             for (int u = 0; u < kDeltaBatch; u++) {
                 const int x = xv[u];
@@ -1636,6 +1656,11 @@ __global__ void __launch_bounds__(kDeltaRows) k_swap_delta(TabuBuffers w)
     delta_run_add(ro, -1, 0, 0, w, j);
     if (gc) atomicAdd(&w.gain_c[j], (int)gc);
     if (gd) atomicAdd(&w.gain_d[j], (unsigned long long)gd);
+}
+
+__global__ void __launch_bounds__(kDeltaRows) k_swap_delta(TabuBuffers w)
+{
+    swap_delta_body(w, blockIdx.x, blockIdx.y, gridDim.y);
 }
 
 cudaError_t launch_swap_delta(const TabuBuffers &w, cudaStream_t s)
@@ -2540,6 +2565,7 @@ k_group_swap(const GroupSlot *__restrict__ slots, const int2 *__restrict__ map)
     load_slot(slots, e.x, g);
     const TabuDevState *st = g.w.st;
     if (st->done || st->t >= st->t_end) return;
+    if (g.w.chg && st->n_moves > 0) return;   // incremental slot: its terms are kept by the delta step
     swap_direct_body<kDirJ>(g.w, g.cost, e.y % g.swap_bx, e.y / g.swap_bx, g.swap_seg);
 }
 
@@ -2584,6 +2610,36 @@ cudaError_t launch_group_refresh(const GroupSlot *slots, const int2 *map, int to
     if (total_blocks <= 0) return cudaSuccess;
     k_group_refresh<<<total_blocks, 256, refresh_smem(maxK), s>>>(slots, map);
     return cudaGetLastError();
+}
+
+// The incremental slots' update of their kept terms from the missions the
+// refresh recorded (the per-search k_swap_delta, one slot's grid per slot).
+__global__ void __launch_bounds__(kDeltaRows) k_group_delta(const GroupSlot *__restrict__ slots,
+                                                            const int2 *__restrict__ map)
+{
+    __shared__ GroupSlot g;
+    const int2 e = map[blockIdx.x];
+    load_slot(slots, e.x, g);
+    if (!g.w.chg) return;
+    swap_delta_body(g.w, e.y % g.delta_bx, e.y / g.delta_bx, g.delta_by);
+}
+
+cudaError_t launch_group_delta(const GroupSlot *slots, const int2 *map, int total_blocks, cudaStream_t s)
+{
+    if (total_blocks <= 0) return cudaSuccess;
+    k_group_delta<<<total_blocks, kDeltaRows, 0, s>>>(slots, map);
+    return cudaGetLastError();
+}
+
+// Delta grid of one incremental slot in a grouped launch: the copy's
+// positions in blocks of kDeltaRows, and a share of the record chunks sized
+// for the slot's missions (the record count is known only on the device).
+void group_delta_blocks(int ldT, int M, int *bx, int *by)
+{
+    *bx = (ldT + kDeltaRows - 1) / kDeltaRows;
+    int y = (M + 2047) / 2048;   // about one block per 64 record chunks of the whole table
+    if (y > 16) y = 16;
+    *by = y < 1 ? 1 : y;
 }
 
 __global__ void k_gather_states(const GroupSlot *__restrict__ slots, int n, TabuDevState *__restrict__ out)

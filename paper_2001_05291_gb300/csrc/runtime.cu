@@ -341,6 +341,41 @@ stage_status setup_search(stage_ctx *c, Instance *in, const int32_t *open, int K
     return STAGE_OK;
 }
 
+std::vector<int32_t> spatial_order(const std::vector<int2> &xy, int ld);
+
+// The instance's mission-major copy with its position order and cell minima
+// (built once per table by a tiled transpose when the load did not build it).
+// STAGE_ERR_NO_MEMORY / STAGE_ERR_ADMISSION when there is no room for it.
+stage_status ensure_costT(stage_ctx *c, Instance *in)
+{
+    if (in->costT_ok) return STAGE_OK;
+    const int ldT = table_ldT(in->B);
+    const size_t needT = costT_bytes(in->M_pad, ldT);
+    if (!in->mem_costT.p || in->mem_costT.bytes < needT) {
+        dev_free(c, in->mem_costT);
+        stage_status s = dev_alloc(c, needT, in->mem_costT);
+        if (s != STAGE_OK) return s;
+    }
+    // bases in Morton order of their coordinates (either metric: planar
+    // metres or latitude / longitude), so that bases near one another take
+    // neighbouring positions
+    std::vector<int2> bxy(in->B);
+    CK(cudaMemcpyAsync(bxy.data(), in->base, (size_t)in->B * sizeof(int2), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    std::vector<int32_t> border = spatial_order(bxy, ldT);
+    int32_t *costT = static_cast<int32_t *>(in->mem_costT.p);
+    int32_t *d_border = costT + (size_t)in->M_pad * ldT;
+    int32_t *d_cellmin = d_border + ldT;
+    CK(cudaMemcpyAsync(d_border, border.data(), (size_t)ldT * sizeof(int32_t), cudaMemcpyHostToDevice, c->stream));
+    CK(timed(c, "transpose", 1, [&] {
+        return launch_transpose_table(in->cost, in->B, in->M_pad, d_border, costT, d_cellmin, c->stream);
+    }));
+    CK(cudaStreamSynchronize(c->stream));   // the host order vector goes out of scope
+    in->ldT = ldT;
+    in->costT_ok = true;
+    return STAGE_OK;
+}
+
 // A15 (reading): every open base of `open` that the instance no longer has
 // available is closed by a forced move, the unavailable ones in ascending id:
 // it opens the available closed base j with the best objective of the swap
@@ -551,9 +586,7 @@ stage_status run_tabu(stage_ctx *c, Instance *in, const stage_tabu_params *p,
     if (inc) {
         // the change records and the mission-major copy of the table; with no
         // room for them (the context's HBM budget) the search takes the full pass
-        const int ldT = table_ldT(in->B);
         const size_t need = (size_t)in->M_pad * 2 * sizeof(int4);
-        const size_t needT = costT_bytes(in->M_pad, ldT);
         if (!in->mem_chg.p || in->mem_chg.bytes < need) {
             dev_free(c, in->mem_chg);
             if (dev_alloc(c, need, in->mem_chg) != STAGE_OK) {
@@ -561,36 +594,9 @@ stage_status run_tabu(stage_ctx *c, Instance *in, const stage_tabu_params *p,
                 set_err(c, STAGE_OK, "");   // a refused allocation here is not an error of the search
             }
         }
-        if (inc && !in->costT_ok) {
-            if (!in->mem_costT.p || in->mem_costT.bytes < needT) {
-                dev_free(c, in->mem_costT);
-                if (dev_alloc(c, needT, in->mem_costT) != STAGE_OK) {
-                    inc = false;
-                    set_err(c, STAGE_OK, "");
-                }
-            }
-            if (inc) {
-                // bases in Morton order of their coordinates (either metric:
-                // planar metres or latitude / longitude), so that bases near
-                // one another take neighbouring positions
-                std::vector<int2> bxy(in->B);
-                CK(cudaMemcpyAsync(bxy.data(), in->base, (size_t)in->B * sizeof(int2), cudaMemcpyDeviceToHost,
-                                   c->stream));
-                CK(cudaStreamSynchronize(c->stream));
-                std::vector<int32_t> border = spatial_order(bxy, ldT);
-                int32_t *costT = static_cast<int32_t *>(in->mem_costT.p);
-                int32_t *d_border = costT + (size_t)in->M_pad * ldT;
-                int32_t *d_cellmin = d_border + ldT;
-                CK(cudaMemcpyAsync(d_border, border.data(), (size_t)ldT * sizeof(int32_t), cudaMemcpyHostToDevice,
-                                   c->stream));
-                CK(timed(c, "transpose", 1, [&] {
-                    return launch_transpose_table(in->cost, in->B, in->M_pad, d_border, costT, d_cellmin,
-                                                  c->stream);
-                }));
-                CK(cudaStreamSynchronize(c->stream));   // the host order vector goes out of scope
-                in->ldT = ldT;
-                in->costT_ok = true;
-            }
+        if (inc && ensure_costT(c, in) != STAGE_OK) {
+            inc = false;
+            set_err(c, STAGE_OK, "");
         }
         if (inc) {
             tw.chg = static_cast<int4 *>(in->mem_chg.p);

@@ -119,6 +119,7 @@ void engine_destroy(stage_ctx *c);
 stage_status autotune_shape(stage_ctx *c, Instance *in, const int32_t *open, int K, int R, int *out_seg);
 stage_status setup_search(stage_ctx *c, Instance *in, const int32_t *open, int K, int R, int traj_cap, int tenure,
                           int accept_worsening, int t0, const int32_t *expiry_in, int *out_nC);
+stage_status ensure_costT(stage_ctx *c, Instance *in);
 stage_status forced_moves(stage_ctx *c, Instance *in, int32_t *open, int K, int R, int t, int tenure,
                           int32_t *expiry, int *n_forced);
 

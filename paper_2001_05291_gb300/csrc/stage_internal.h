@@ -198,10 +198,13 @@ struct GroupSlot {
     int ref_blocks;   // refresh blocks of this slot
     int swap_seg;     // missions per swap block
     int sel_blocks;   // select blocks of this slot
-    int pad;
+    int delta_bx;     // incremental slots (w.chg set): delta blocks along the copy's positions
+    int delta_by;     // ... and along the record chunks (0: a full pass every step)
 };
 constexpr int kGroupMaxK = 256;
 int group_swap_blocks(int M_pad, int nC, int K, int seg_override, int *bx, int *seg);
+void group_delta_blocks(int ldT, int M, int *bx, int *by);
+cudaError_t launch_group_delta(const GroupSlot *slots, const int2 *map, int total_blocks, cudaStream_t s);
 int group_common_segment(const int *M_pad, const int *nC, int n);
 size_t swap_direct_smem(int K);   // dynamic shared memory of the direct swap pass
 bool tabu_small_fits(int nC, int M_pad, int K);

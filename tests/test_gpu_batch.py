@@ -41,13 +41,16 @@ def same(got, want):
     assert np.array_equal(np.sort(got.final_open), np.sort(want.final_open))
 
 
-def test_batch_equals_alone_and_oracle(stage_mod):
+@pytest.mark.parametrize("incremental", [False, True])
+def test_batch_equals_alone_and_oracle(stage_mod, incremental):
+    """incremental: every slot keeps its swap terms across steps (one full
+    pass, then the records of the missions each move touched)."""
     stage = stage_mod
     insts = [small(s, B, M, K, R=R, iters=it) for s, (B, M, K, R, it) in enumerate(
         [(30, 2000, 4, 300_000, 30), (55, 17000, 9, 350_000, 25), (12, 300, 11, 250_000, 20),
          (80, 33000, 16, 400_000, 15), (40, 5000, 6, 200_000, 40), (9, 64, 3, 500_000, 12),
          (70, 20000, 32, 350_000, 18), (25, 9000, 5, 150_000, 35)])]
-    with stage.Context(device=0, max_slots=3) as ctx:        # fewer slots than requests: queueing
+    with stage.Context(device=0, max_slots=3, incremental=incremental, profile=True) as ctx:   # queueing
         hs = [ctx.load_instance(i.base_xy, i.pick_xy, i.drop_xy) for i in insts]
         reqs = [dict(inst=h, K=i.K, R=i.R, iters=i.iters, tenure=i.tenure) for h, i in zip(hs, insts)]
         # an instance given by value, an explicit start, an improving-only search
@@ -73,6 +76,8 @@ def test_batch_equals_alone_and_oracle(stage_mod):
                                nthreads=8)
             same(g, want)
             assert g.timing["submit_ns"] <= g.timing["start_ns"] <= g.timing["end_ns"]
+        if incremental:
+            assert ctx.kernel_stats("group_delta")[0] > 0
         assert got[-1].n_moves < 60   # the improving-only search stopped early inside the batch
 
 
