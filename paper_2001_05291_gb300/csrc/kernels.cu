@@ -574,7 +574,15 @@ cudaError_t launch_table_fused(int B, int M, int M_pad, int ldT, const int2 *bas
     int g1 = (M + 255) / 256;
     if (g1 > 4096) g1 = 4096;
     const int gy = (ldT / 32 + kFusedCells - 1) / kFusedCells;
-    int gx = (sms * 4 + gy - 1) / gy;   // about four blocks per SM
+    // one wave of as many resident blocks as the SMs hold (each block walks an
+    // equal share of the mission tiles)
+    int per_sm = 0;
+    if ((metric == 1 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_build_table_fused<1>, 256, 0)
+                     : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_build_table_fused<0>, 256, 0)) !=
+            cudaSuccess ||
+        per_sm < 1)
+        per_sm = 4;
+    int gx = (sms * per_sm + gy - 1) / gy;
     if (gx > M_pad / 32) gx = M_pad / 32;
     if (gx < 1) gx = 1;
     if (metric == 1) {
