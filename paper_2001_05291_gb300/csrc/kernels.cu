@@ -1852,6 +1852,14 @@ __global__ void __launch_bounds__(kSelectThreads) k_ls_select(TabuBuffers w, con
             st->ls_pos = best.u + 1;
             st->ls_moved = 1;
             st->ls_hold = 0;
+            st->chg_total += st->chg_n;          // the records the last incremental pass took
+            st->chg_n = 0;
+            if (w.chg) {
+                // the closed base is a candidate again: its column of the terms
+                // is rebuilt from zero by the refresh
+                w.gain_c[best.i] = 0;
+                w.gain_d[best.i] = 0;
+            }
             w.v0[0] = 0;
             w.v0[1] = 0;
             s_moved = 1;
@@ -1867,10 +1875,15 @@ __global__ void __launch_bounds__(kSelectThreads) k_ls_select(TabuBuffers w, con
     }
     __syncthreads();
     if (!s_moved) return;
+    const int ic = st->mv_i;
     for (int k = threadIdx.x; k < K; k += blockDim.x) {
         w.loss_c[k] = 0;
         w.loss_d[k] = 0;
         w.best_open[k] = w.open[k];
+        if (w.chg) {
+            w.extra_c[(size_t)k * w.B + ic] = 0;
+            w.extra_d[(size_t)k * w.B + ic] = 0;
+        }
     }
 }
 

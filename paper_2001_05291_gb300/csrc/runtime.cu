@@ -343,6 +343,33 @@ stage_status setup_search(stage_ctx *c, Instance *in, const int32_t *open, int K
 
 std::vector<int32_t> spatial_order(const std::vector<int2> &xy, int ld);
 
+stage_status ensure_costT(stage_ctx *c, Instance *in);
+
+// The change records and the mission-major copy for a search on `in`, set in
+// tw; false (and tw unchanged) when there is no room for them (the context's
+// HBM budget): the search then takes the full pass.
+bool use_incremental(stage_ctx *c, Instance *in, TabuBuffers &tw)
+{
+    const size_t need = (size_t)in->M_pad * 2 * sizeof(int4);
+    if (!in->mem_chg.p || in->mem_chg.bytes < need) {
+        dev_free(c, in->mem_chg);
+        if (dev_alloc(c, need, in->mem_chg) != STAGE_OK) {
+            set_err(c, STAGE_OK, "");   // a refused allocation here is not an error of the search
+            return false;
+        }
+    }
+    if (ensure_costT(c, in) != STAGE_OK) {
+        set_err(c, STAGE_OK, "");
+        return false;
+    }
+    tw.chg = static_cast<int4 *>(in->mem_chg.p);
+    tw.costT = static_cast<const int32_t *>(in->mem_costT.p);
+    tw.border = tw.costT + (size_t)in->M_pad * in->ldT;
+    tw.cellmin = tw.border + in->ldT;
+    tw.ldT = in->ldT;
+    return true;
+}
+
 // The instance's mission-major copy with its position order and cell minima
 // (built once per table by a tiled transpose when the load did not build it).
 // STAGE_ERR_NO_MEMORY / STAGE_ERR_ADMISSION when there is no room for it.
@@ -583,29 +610,7 @@ stage_status run_tabu(stage_ctx *c, Instance *in, const stage_tabu_params *p,
     bool persist = inc && multi && !(c->flags & STAGE_NO_PERSIST) && tw.mask == nullptr && exp_a == nullptr;
     const int pgrid = persist ? persist_grid(K, in->B, table_ldT(in->B), in->M_pad) : 0;
     if (pgrid < 1) persist = false;
-    if (inc) {
-        // the change records and the mission-major copy of the table; with no
-        // room for them (the context's HBM budget) the search takes the full pass
-        const size_t need = (size_t)in->M_pad * 2 * sizeof(int4);
-        if (!in->mem_chg.p || in->mem_chg.bytes < need) {
-            dev_free(c, in->mem_chg);
-            if (dev_alloc(c, need, in->mem_chg) != STAGE_OK) {
-                inc = false;
-                set_err(c, STAGE_OK, "");   // a refused allocation here is not an error of the search
-            }
-        }
-        if (inc && ensure_costT(c, in) != STAGE_OK) {
-            inc = false;
-            set_err(c, STAGE_OK, "");
-        }
-        if (inc) {
-            tw.chg = static_cast<int4 *>(in->mem_chg.p);
-            tw.costT = static_cast<const int32_t *>(in->mem_costT.p);
-            tw.border = tw.costT + (size_t)in->M_pad * in->ldT;
-            tw.cellmin = tw.border + in->ldT;
-            tw.ldT = in->ldT;
-        }
-    }
+    if (inc) inc = use_incremental(c, in, tw);
     // one Tabu iteration of the multi-kernel path
     auto step = [&](bool time_each) -> cudaError_t {
         cudaError_t e = cudaSuccess;
@@ -1083,7 +1088,14 @@ stage_status run_local_search(stage_ctx *c, Instance *in, const stage_ls_params 
     stage_status s = setup_search(c, in, start.data(), K, p->R, p->max_moves, 0, 1, 0, nullptr, &nC);
     if (s != STAGE_OK) return s;
     if (nC != nC0) return set_err(c, STAGE_ERR_INTERNAL, "candidate count %d, expected %d", nC, nC0);
-    TabuBuffers &tb = in->tb;
+    // beyond L2 (or with STAGE_INCREMENTAL) the terms are kept across moves:
+    // one full pass, then per step the records of the missions a move touched
+    // (a pass change holds the terms, as in the full-pass form)
+    TabuBuffers tb = in->tb;
+    bool inc = !(c->flags & STAGE_FULL_PASS) && swap_delta_fits(K) && nC > 0 &&
+               ((c->flags & STAGE_INCREMENTAL) ||
+                (size_t)nC * in->M_pad * sizeof(int32_t) >= kIncrementalMinTableBytes);
+    if (inc) inc = use_incremental(c, in, tb);
     DevBuf dr;
     s = dev_alloc(c, rank.size() * 4 + 4, dr);
     if (s != STAGE_OK) return s;
@@ -1100,10 +1112,13 @@ stage_status run_local_search(stage_ctx *c, Instance *in, const stage_ls_params 
     volatile int *done_flag = static_cast<volatile int *>(c->pinned);
     *done_flag = 0;
     const bool profiling = (c->flags & STAGE_PROFILE) != 0;
+    if (e == cudaSuccess && inc)
+        e = timed(c, "swap_eval", 1, [&] { return launch_swap_eval(tb, in->cost, nC, 0, c->stream); });
     auto step = [&]() {
-        cudaError_t r = launch_swap_eval(tb, in->cost, nC, 0, c->stream);
+        cudaError_t r = inc ? cudaSuccess : launch_swap_eval(tb, in->cost, nC, 0, c->stream);
         if (r == cudaSuccess) r = launch_ls_select(tb, nC, d_rank_slot, d_rank_cand, c->stream);
         if (r == cudaSuccess) r = launch_refresh(tb, in->cost, c->stream);
+        if (r == cudaSuccess && inc) r = launch_swap_delta(tb, c->stream);
         return r;
     };
     auto poll = [&]() {
@@ -1124,17 +1139,21 @@ stage_status run_local_search(stage_ctx *c, Instance *in, const stage_ls_params 
     long long it = 0;
     while (e == cudaSuccess && nC > 0 && it < max_steps) {
         if (ge) {
-            for (const char *nm : {"swap_eval", "ls_select", "refresh"}) c->stats[nm].launches += kGraphIters;
+            for (const char *nm : {"ls_select", "refresh"}) c->stats[nm].launches += kGraphIters;
+            c->stats[inc ? "swap_delta" : "swap_eval"].launches += kGraphIters;
             e = cudaGraphLaunch(ge, c->stream);
             it += kGraphIters;
         } else {
             for (int k = 0; e == cudaSuccess && k < kGraphIters && it < max_steps; k++, it++) {
-                e = timed(c, "swap_eval", 1, [&] { return launch_swap_eval(tb, in->cost, nC, 0, c->stream); });
+                if (!inc)
+                    e = timed(c, "swap_eval", 1, [&] { return launch_swap_eval(tb, in->cost, nC, 0, c->stream); });
                 if (e == cudaSuccess)
                     e = timed(c, "ls_select", 1,
                               [&] { return launch_ls_select(tb, nC, d_rank_slot, d_rank_cand, c->stream); });
                 if (e == cudaSuccess)
                     e = timed(c, "refresh", 1, [&] { return launch_refresh(tb, in->cost, c->stream); });
+                if (e == cudaSuccess && inc)
+                    e = timed(c, "swap_delta", 1, [&] { return launch_swap_delta(tb, c->stream); });
             }
         }
         if (e == cudaSuccess) e = poll();

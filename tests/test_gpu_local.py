@@ -106,3 +106,38 @@ def test_wide_range_and_bad_permutation(ctx):
     with pytest.raises(stage.StageError):
         ctx.local_search(h, 5, inst.R, ps, pc)
     ctx.unload_instance(h)
+
+
+@pytest.fixture(scope="module")
+def ictx():
+    """A context whose local searches keep the swap terms across moves (the
+    incremental neighbourhood: one full pass, then the records of the
+    missions each move touched; a pass change holds the terms)."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2001_05291_gb300 import build, stage
+    build.build()
+    with stage.Context(device=0, incremental=True, profile=True) as c:
+        yield c
+
+
+@pytest.mark.parametrize("B,M,K,seed", [(30, 900, 4, 1), (60, 17000, 12, 3), (80, 2500, 20, 5), (120, 12000, 9, 6)])
+def test_incremental_local_search(ictx, B, M, K, seed):
+    inst = small(100 + seed, B, M, K)
+    got = check(ictx, inst, K, inst.R, 8, seed)
+    assert got.passes >= 2
+
+
+def test_incremental_local_search_edges(ictx):
+    inst = small(300, 40, 4000, 5)
+    avail = np.ones(inst.B, dtype=np.uint8)
+    avail[[0, 5, 17, 33]] = 0
+    check(ictx, inst, 5, inst.R, 6, 10, avail=avail)
+    check(ictx, inst, 1, inst.R, 6, 11)
+    full = small(200, 50, 6000, 6)
+    cut = check(ictx, full, 6, full.R, 8, 8, max_moves=2)
+    assert cut.n_moves == 2 and not cut.local_optimum
+    check(ictx, full, 6, full.R, 8, 9, start_open=np.arange(6) * 3)
+    check(ictx, full, 6, 2**31 - 2, 5, 13)
+    assert ictx.kernel_stats("swap_delta")[0] > 0
