@@ -2000,6 +2000,12 @@ __global__ void __launch_bounds__(kSelectThreads) k_fleet_select(TabuBuffers A, 
                 st->n_moves += 1;
                 st->t = t + 1;
                 st->mv_s = P.s; st->mv_i = P.i; st->mv_j = P.j;
+                st->chg_total += st->chg_n;     // the records the last incremental pass took
+                st->chg_n = 0;
+                if (A.chg) {   // the closed base's column is rebuilt from zero by the refresh
+                    A.gain_c[P.i] = 0;
+                    A.gain_d[P.i] = 0;
+                }
                 A.v0[0] = 0;
                 A.v0[1] = 0;
                 s_moved = 1;
@@ -2014,6 +2020,12 @@ __global__ void __launch_bounds__(kSelectThreads) k_fleet_select(TabuBuffers A, 
                         b_pos[P.j] = -1;
                         sb->mv_s = P.s; sb->mv_i = P.i; sb->mv_j = P.j;
                         sb->ls_hold = 0;
+                        sb->chg_total += sb->chg_n;
+                        sb->chg_n = 0;
+                        if (B.chg) {
+                            B.gain_c[P.i] = 0;
+                            B.gain_d[P.i] = 0;
+                        }
                         B.v0[0] = 0;
                         B.v0[1] = 0;
                         s_rot = 1;
@@ -2027,15 +2039,24 @@ __global__ void __launch_bounds__(kSelectThreads) k_fleet_select(TabuBuffers A, 
     }
     __syncthreads();
     if (!s_moved) return;
+    const int ic = st->mv_i;
     for (int k = threadIdx.x; k < K; k += blockDim.x) {
         A.loss_c[k] = 0;
         A.loss_d[k] = 0;
         if (s_newbest) A.best_open[k] = A.open[k];
+        if (A.chg) {
+            A.extra_c[(size_t)k * A.B + ic] = 0;
+            A.extra_d[(size_t)k * A.B + ic] = 0;
+        }
     }
     if (s_rot)
         for (int k = threadIdx.x; k < B.K; k += blockDim.x) {
             B.loss_c[k] = 0;
             B.loss_d[k] = 0;
+            if (B.chg) {
+                B.extra_c[(size_t)k * B.B + ic] = 0;
+                B.extra_d[(size_t)k * B.B + ic] = 0;
+            }
         }
 }
 

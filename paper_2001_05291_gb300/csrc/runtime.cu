@@ -934,7 +934,7 @@ stage_status run_fleet(stage_ctx *c, Instance *in, const stage_fleet_params *p, 
     }
     std::copy(heli.begin(), heli.end(), host.data() + 2 * (size_t)in->M_pad);
     const int hasB = (Kr >= 1 && anyB) ? 1 : 0;
-    DevBuf dm, dpos;
+    DevBuf dm, dpos, chgB;
     stage_status s = dev_alloc(c, host.size(), dm);
     if (s != STAGE_OK) return s;
     s = dev_alloc(c, (size_t)B * 4, dpos);
@@ -950,6 +950,7 @@ stage_status run_fleet(stage_ctx *c, Instance *in, const stage_fleet_params *p, 
         dev_free(c, Bs.ws);
         dev_free(c, dm);
         dev_free(c, dpos);
+        dev_free(c, chgB);
     };
     cudaError_t e = cudaMemcpyAsync(d_m, host.data(), host.size(), cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
@@ -962,6 +963,29 @@ stage_status run_fleet(stage_ctx *c, Instance *in, const stage_fleet_params *p, 
     if (s != STAGE_OK) {
         cleanup();
         return s;
+    }
+    // beyond L2 (or with STAGE_INCREMENTAL) both searches keep their terms
+    // across moves: one full pass each, then per iteration the records of the
+    // missions a move touched (B, held after a fixed-wing move, skips its
+    // refresh and update as it skips its pass); B's candidates are every base
+    // outside its placement, so its columns stay whole while fixed-wing
+    // vehicles come and go
+    bool inc = !(c->flags & STAGE_FULL_PASS) && swap_delta_fits(K) && A.nC > 0 &&
+               ((c->flags & STAGE_INCREMENTAL) ||
+                (size_t)A.nC * in->M_pad * sizeof(int32_t) >= kIncrementalMinTableBytes);
+    if (inc) inc = use_incremental(c, in, A.tb);
+    if (inc && hasB) {
+        if (dev_alloc(c, (size_t)in->M_pad * 2 * sizeof(int4), chgB) == STAGE_OK) {
+            Bs.tb.chg = static_cast<int4 *>(chgB.p);
+            Bs.tb.costT = A.tb.costT;
+            Bs.tb.border = A.tb.border;
+            Bs.tb.cellmin = A.tb.cellmin;
+            Bs.tb.ldT = A.tb.ldT;
+        } else {
+            set_err(c, STAGE_OK, "");   // no room: both searches take the full pass
+            inc = false;
+            A.tb.chg = nullptr;
+        }
     }
     // state: A carries the search; B only its hold / done flags and last move
     unsigned long long v0a[2] = {0, 0}, v0b[2] = {0, 0};
@@ -988,8 +1012,10 @@ stage_status run_fleet(stage_ctx *c, Instance *in, const stage_fleet_params *p, 
     *done_flag = 0;
     const uint8_t *d_heli = d_m + 2 * (size_t)in->M_pad;
     for (int it = 0; e == cudaSuccess && it < p->iters && A.nC > 0; it++) {
-        e = timed(c, "swap_eval", 1, [&] { return launch_swap_eval(A.tb, in->cost, A.nC, 0, c->stream); });
-        if (e == cudaSuccess && hasB && Bs.nC > 0)
+        const bool full = !inc || it == 0;
+        if (full)
+            e = timed(c, "swap_eval", 1, [&] { return launch_swap_eval(A.tb, in->cost, A.nC, 0, c->stream); });
+        if (e == cudaSuccess && full && hasB && Bs.nC > 0)
             e = timed(c, "swap_eval", 1, [&] { return launch_swap_eval(Bs.tb, in->cost, Bs.nC, 0, c->stream); });
         if (e == cudaSuccess)
             e = timed(c, "fleet_select", 1,
@@ -997,6 +1023,10 @@ stage_status run_fleet(stage_ctx *c, Instance *in, const stage_fleet_params *p, 
         if (e == cudaSuccess) e = timed(c, "refresh", 1, [&] { return launch_refresh(A.tb, in->cost, c->stream); });
         if (e == cudaSuccess && hasB)
             e = timed(c, "refresh", 1, [&] { return launch_refresh(Bs.tb, in->cost, c->stream); });
+        if (e == cudaSuccess && inc)
+            e = timed(c, "swap_delta", 1, [&] { return launch_swap_delta(A.tb, c->stream); });
+        if (e == cudaSuccess && inc && hasB)
+            e = timed(c, "swap_delta", 1, [&] { return launch_swap_delta(Bs.tb, c->stream); });
         if (e == cudaSuccess && (it & 31) == 31) {
             e = cudaMemcpyAsync(c->pinned, &A.tb.st->done, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
             if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);

@@ -100,3 +100,38 @@ def test_paper_fleet_on_eq1_legs(ctx):
     ctx.unload_instance(h)
     got = check(ctx, inst, cost, heli, rot, Kr, Kf, 100, 7, haversine=True)
     assert not any(heli[b] for b in got.final_fixed)
+
+
+@pytest.fixture(scope="module")
+def ictx():
+    """Both searches of the fleet keep their swap terms across moves (the
+    incremental neighbourhood: one full pass each, then the records of the
+    missions each move touched; B, held after a fixed-wing move, skips its
+    refresh and update)."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2001_05291_gb300 import build, stage
+    build.build()
+    with stage.Context(device=0, incremental=True, profile=True) as c:
+        yield c
+
+
+@pytest.mark.parametrize("B,M,Kr,Kf,nh,frac,seed", [(30, 2000, 3, 2, 8, 0.3, 2), (50, 9000, 5, 3, 15, 0.2, 3),
+                                                    (60, 17000, 8, 4, 20, 0.3, 5), (20, 800, 1, 1, 5, 0.9, 6)])
+def test_incremental_fleets(ictx, B, M, Kr, Kf, nh, frac, seed):
+    inst = small(10 + seed, B, M, Kr + Kf)
+    cost = oracle.cost_table(inst.base_xy, inst.pick_xy, inst.drop_xy, 8)
+    heli, rot = synth.fleet_types(seed, B, M, nh, frac)
+    check(ictx, inst, cost, heli, rot, Kr, Kf, 60, 4)
+
+
+def test_incremental_fleet_edges(ictx):
+    inst = small(30, 35, 4000, 5)
+    cost = oracle.cost_table(inst.base_xy, inst.pick_xy, inst.drop_xy, 8)
+    heli, rot = synth.fleet_types(7, inst.B, inst.M, 9, 0.3)
+    check(ictx, inst, cost, heli, rot, 0, 4, 25, 3)                       # no rotary-wing vehicle
+    check(ictx, inst, cost, heli, np.zeros(inst.M, np.uint8), 2, 3, 25, 3)  # no rotary-only mission
+    check(ictx, inst, cost, heli, rot, 3, 2, 60, 2, accept_worsening=False)
+    check(ictx, inst, cost, heli, rot, 5, 0, 30, 3)                       # rotary-wing only
+    assert ictx.kernel_stats("swap_delta")[0] > 0
