@@ -436,7 +436,7 @@ stage_status Engine::rebuild()
             group_swap_blocks(sl.tb.M_pad, sl.nC, sl.tb.K, common, &gs[k].swap_bx, &gs[k].swap_seg);
         gs[k].delta_bx = gs[k].delta_by = 0;
         if (sl.tb.chg) {
-            group_delta_blocks(sl.tb.ldT, sl.tb.M, &gs[k].delta_bx, &gs[k].delta_by);
+            group_delta_blocks(sl.tb.ldT, sl.tb.M, sl.tb.K, &gs[k].delta_bx, &gs[k].delta_by);
             if (sl.first_done) gs[k].swap_blocks = 0;   // its terms are kept by the delta step
         }
         gs[k].sel_blocks = select_blocks(sl.tb.K, sl.nC);

@@ -2674,14 +2674,17 @@ cudaError_t launch_group_delta(const GroupSlot *slots, const int2 *map, int tota
 }
 
 // Delta grid of one incremental slot in a grouped launch: the copy's
-// positions in blocks of kDeltaRows, and a share of the record chunks sized
-// for the slot's missions (the record count is known only on the device).
-void group_delta_blocks(int ldT, int M, int *bx, int *by)
+// positions in blocks of kDeltaRows, and the record chunks over blocks sized
+// for the records a move can make (known only on the device): a move changes
+// the state of about 2 M / K missions (those near the two bases, K bases
+// sharing the missions), so about one block per eight chunks of 4 M / K.
+void group_delta_blocks(int ldT, int M, int K, int *bx, int *by)
 {
     *bx = (ldT + kDeltaRows - 1) / kDeltaRows;
-    int y = (M + 2047) / 2048;   // about one block per 64 record chunks of the whole table
-    if (y > 16) y = 16;
-    *by = y < 1 ? 1 : y;
+    const long long rec = 4ll * M / (K > 0 ? K : 1);
+    long long y = (rec + 8 * kDeltaChunk - 1) / (8 * kDeltaChunk);
+    if (y > 256) y = 256;
+    *by = y < 1 ? 1 : (int)y;
 }
 
 __global__ void k_gather_states(const GroupSlot *__restrict__ slots, int n, TabuDevState *__restrict__ out)

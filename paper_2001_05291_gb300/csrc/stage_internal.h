@@ -203,7 +203,7 @@ struct GroupSlot {
 };
 constexpr int kGroupMaxK = 256;
 int group_swap_blocks(int M_pad, int nC, int K, int seg_override, int *bx, int *seg);
-void group_delta_blocks(int ldT, int M, int *bx, int *by);
+void group_delta_blocks(int ldT, int M, int K, int *bx, int *by);
 cudaError_t launch_group_delta(const GroupSlot *slots, const int2 *map, int total_blocks, cudaStream_t s);
 int group_common_segment(const int *M_pad, const int *nC, int n);
 size_t swap_direct_smem(int K);   // dynamic shared memory of the direct swap pass
