@@ -277,7 +277,7 @@ def cell_row_bytes(B):
     return 4 * (((ldT // 32) + 7) // 8 * 8)
 
 
-def stored_traffic(fname, inst, args):
+def stored_traffic(fname, inst, args, kernel):
     """DRAM bytes per launch from a committed ncu summary under profiles/, only
     while the kernel source is the one measured and the workload the full one."""
     prof = os.path.join(ROOT, "profiles", fname)
@@ -289,7 +289,7 @@ def stored_traffic(fname, inst, args):
             if ":" in line and not line.startswith((" ", "#")):
                 k, v = line.split(":", 1)
                 fields[k.strip()] = v.strip()
-    if fields.get("workload") == inst.name and fields.get("kernel_source_digest") == kernel_digest():
+    if fields.get("workload") == inst.name and fields.get("kernel_source_digest") == kernel_digest(kernel):
         return float(fields["traffic_bytes_per_launch"])
     return None
 
@@ -413,11 +413,11 @@ def run_ours(args):
                    "steps_us_per_iteration": steps}
     # DRAM traffic per launch from the committed ncu summary, only while the
     # kernel source is the one that was measured and the workload is the full one
-    traffic = stored_traffic("swap_eval_traffic.md", inst, args)
+    traffic = stored_traffic("swap_eval_traffic.md", inst, args, "swap_eval")
     if delta:
-        delta["traffic"] = stored_traffic("swap_delta_traffic.md", inst, args)
+        delta["traffic"] = None   # no capture of the per-launch pass's current code
     if persist:
-        persist["traffic"] = stored_traffic("persist_traffic.md", inst, args)
+        persist["traffic"] = stored_traffic("persist_traffic.md", inst, args, "persist")
     # work performed on the device (the logical metric counts every swap of
     # every iteration): (candidate row, mission) pairs the full passes visit
     # plus (base, recorded mission) pairs of the incremental updates
@@ -571,15 +571,17 @@ def kernel_code(text: str) -> str:
     return "\n".join(" ".join(line.split()) for line in text.splitlines() if line.strip())
 
 
-KERNEL_SOURCES = ("kernels.cu", "persist.cu", "device_common.cuh")
+# the sources each stored traffic figure depends on
+KERNEL_SOURCES = {"persist": ("persist.cu", "device_common.cuh"),
+                  "swap_eval": ("kernels.cu", "device_common.cuh")}
 
 
-def kernel_digest() -> str:
-    """Hash of the device code (comments and spacing aside): stored ncu traffic
-    applies only to the same code."""
+def kernel_digest(kernel: str) -> str:
+    """Hash of a kernel's sources (comments and spacing aside): stored ncu
+    traffic applies only to the same code."""
     import hashlib
     h = hashlib.sha256()
-    for name in KERNEL_SOURCES:
+    for name in KERNEL_SOURCES[kernel]:
         with open(os.path.join(ROOT, "paper_2001_05291_gb300", "csrc", name), encoding="utf-8") as fh:
             h.update(kernel_code(fh.read()).encode())
     return h.hexdigest()[:16]
