@@ -61,12 +61,14 @@ namespace stg {
 
 constexpr int kPerThreads = 1024;
 constexpr int kPerWarps = kPerThreads / 32;
-constexpr int kBlockMissions = 256;    // missions per ownership block (8 warp chunks)
+constexpr int kBlockMissions = 32;     // missions per ownership block (one warp chunk)
 constexpr int kRecCap = 256;           // records staged in shared memory per round of the update
 constexpr int kUpdBatch = 8;           // listed records whose costs a warp loads at once
 constexpr int kUpdItem = 24;           // listed records of one cell per work item of a warp
 constexpr int kMaxLd = 2048;           // longest table-copy row (its 64 cells fit the item scan)
 constexpr size_t kPerSmemLimit = 220 * 1024;
+constexpr int kMaxGrid = 256;          // CTAs of a search (the update's count prefix and sums: 8 per lane)
+static_assert(kMaxGrid + 1 <= kRefQ, "the count prefix fits in the refresh's queue");
 
 // Per-CTA clocks (ns, summed over the search): choosing and applying the move,
 // the refresh, the wait at the barrier after it, the update, the wait at the
@@ -95,7 +97,7 @@ __device__ __forceinline__ long long gtimer()
 
 // Shared-memory layout (byte offsets).
 struct PerLayout {
-    size_t recs, raw, cnt, cells, wlist, cand, expiry, cidx, open, lc, ic, ld, id, lossc, lossd, q, total;
+    size_t recs, raw, cnt, cells, wlist, cand, expiry, cidx, open, lc, ic, ld, id, q, total;
 };
 
 __host__ __device__ inline size_t per_align(size_t x, size_t a) { return (x + a - 1) / a * a; }
@@ -117,8 +119,6 @@ __host__ __device__ inline PerLayout per_layout(int K, int B, int ldT)
     L.ic = o;     o = per_align(o + (size_t)K * 4, 16);
     L.ld = o;     o = per_align(o + (size_t)K * 8, 16);
     L.id = o;     o = per_align(o + (size_t)K * 8, 16);
-    L.lossc = o;  o = per_align(o + (size_t)K * 8, 16);
-    L.lossd = o;  o = per_align(o + (size_t)K * 8, 16);
     L.q = o;      o = per_align(o + (size_t)kRefQ * 4, 16);
     L.total = o;
     return L;
@@ -217,7 +217,8 @@ struct PersistArgs {
     unsigned *bar;                  // arrivals at the grid barriers
     int *err;                       // error word (kErr*)
     long long *info;                // [2] CTAs, records over the search
-    int *recn;                      // [2] length of the move's record list (w.chg)
+    int *nrec;                      // [gridDim.x] records in each CTA's region for the move
+    long long *psum;                // [2 * (2 + 2K)][gridDim.x] each CTA's parts of the move's sums
     long long *cta_ns;              // [gridDim.x][kClocks] per-CTA time of each step, ns
     int4 *region;                   // [gridDim.x * region_cap * 2] each CTA's records of a move
     long long spin_limit;
@@ -227,19 +228,22 @@ struct PersistArgs {
 // Search scalars, the same in every CTA (each applies the same moves).
 struct PerState {
     long long cur_c, cur_d, best_c, best_d, v0c, v0d;
-    int t, n_moves, best_iter, done, mv_s, mv_i, mv_j, recn, rbase, qn, prev_i;
+    int t, n_moves, best_iter, done, mv_s, mv_i, mv_j, recn, qn, prev_i;
 };
 
 // The best admissible and best overall key over this CTA's share of the
-// K x nC swaps, for the placement of iteration st.t.  The base closed by the
-// previous move (st.prev_i, -1 at the start) takes its column from the
-// refresh's sums `cl`.
+// K x nC swaps, for the placement of iteration st.t, whose V0 and loss are
+// `acc` (V0 returned in v0c, v0d).  The base closed by the previous move
+// (st.prev_i, -1 at the start) takes its column from the move's sums `cl`.
+// Every load of a swap's terms (V0, loss, gain, extra) is issued together.
 __device__ __forceinline__ void persist_select(const TabuBuffers &w, const PerState &st, int nC, const int *s_open,
-                                               const int *s_cand, const int *s_exp, const long long *lossc,
-                                               const long long *lossd, const unsigned long long *cl, MoveKey &adm,
-                                               MoveKey &all)
+                                               const int *s_cand, const int *s_exp, const unsigned long long *acc,
+                                               const unsigned long long *cl, MoveKey &adm, MoveKey &all,
+                                               long long &v0c, long long &v0d)
 {
     const int K = w.K, t = st.t;
+    v0c = (long long)__ldcg(&acc[0]);
+    v0d = (long long)__ldcg(&acc[1]);
     const int total = K * nC;   // K <= 256, nC <= 2048
     const int q0 = (int)((long long)total * blockIdx.x / gridDim.x);
     const int q1 = (int)((long long)total * (blockIdx.x + 1) / gridDim.x);
@@ -259,13 +263,34 @@ __device__ __forceinline__ void persist_select(const TabuBuffers &w, const PerSt
             ec = __ldcg(&w.extra_c[sj]);
             ed = (long long)__ldcg(&w.extra_d[sj]);
         }
+        const long long lc = (long long)__ldcg(&acc[2 + s]), ld = (long long)__ldcg(&acc[2 + K + s]);
         MoveKey k;
-        k.cov = st.v0c + gc + lossc[s] + ec;
-        k.dist = st.v0d + gd + lossd[s] + ed;
+        k.cov = v0c + gc + lc + ec;
+        k.dist = v0d + gd + ld + ed;
         k.i = i; k.j = j; k.s = s; k.c = c; k.valid = 1;
         k.tabu = (t < s_exp[i]) || (t < s_exp[j]);
         if (key_better(k, all)) all = k;
         if ((!k.tabu || obj_better(k.cov, k.dist, st.best_c, st.best_d)) && key_better(k, adm)) adm = k;
+    }
+}
+
+// Best admissible and best overall key of the CTA, valid in warp 0 only
+// (block_best2 without handing the result to every thread).
+__device__ __forceinline__ void block_best2_warp0(MoveKey &adm, MoveKey &all, MoveKey *s_adm, MoveKey *s_all)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    warp_best_key(adm);
+    warp_best_key(all);
+    if (lane == 0) {
+        s_adm[wid] = adm;
+        s_all[wid] = all;
+    }
+    __syncthreads();
+    if (wid == 0) {
+        adm = s_adm[lane];
+        all = s_all[lane];
+        warp_best_key(adm);
+        warp_best_key(all);
     }
 }
 
@@ -289,8 +314,6 @@ __global__ void __launch_bounds__(kPerThreads, 1) k_tabu_persist(PersistArgs A)
     int *s_ic = reinterpret_cast<int *>(smem + L.ic);
     unsigned long long *s_ld = reinterpret_cast<unsigned long long *>(smem + L.ld);
     unsigned long long *s_id = reinterpret_cast<unsigned long long *>(smem + L.id);
-    long long *s_lossc = reinterpret_cast<long long *>(smem + L.lossc);
-    long long *s_lossd = reinterpret_cast<long long *>(smem + L.lossd);
     int *s_q = reinterpret_cast<int *>(smem + L.q);
     __shared__ MoveKey s_adm[kPerWarps], s_all[kPerWarps];
     __shared__ PerState S;
@@ -325,12 +348,7 @@ __global__ void __launch_bounds__(kPerThreads, 1) k_tabu_persist(PersistArgs A)
         for (int k = 0; k < kClocks; k++) s_clk[k] = 0;
         s_clk[kClocks] = gtimer();
     }
-    for (int k = tid; k < K; k += kPerThreads) {
-        s_open[k] = w.open[k];
-        const unsigned long long *acc = A.acc + (size_t)(st->t & 1) * nA;
-        s_lossc[k] = (long long)acc[2 + k];
-        s_lossd[k] = (long long)acc[2 + K + k];
-    }
+    for (int k = tid; k < K; k += kPerThreads) s_open[k] = w.open[k];
     for (int b = tid; b < B; b += kPerThreads) {
         s_exp[b] = w.expiry[b];
         s_cidx[b] = -1;
@@ -361,27 +379,20 @@ __global__ void __launch_bounds__(kPerThreads, 1) k_tabu_persist(PersistArgs A)
         }
     };
     // the scores of this CTA's share of the swaps for the move of iteration
-    // S.t; CTA 0 also prepares the sums that move's refresh fills, and writes
-    // the previous move's closed column back
+    // S.t; CTA 0 also writes the previous move's closed column back
     auto select = [&]() {
         const int u = S.t;
         const unsigned long long *clp = A.col + (size_t)((u + 1) & 1) * nA;   // the previous move's sums
-        if (lead_cta) {
-            unsigned long long *nx = A.acc + (size_t)((u + 1) & 1) * nA;
-            const unsigned long long *cu = A.acc + (size_t)(u & 1) * nA;
-            unsigned long long *cl = A.col + (size_t)(u & 1) * nA;
-            for (int k = tid; k < nA; k += kPerThreads) {
-                nx[k] = __ldcg(&cu[k]);   // V0 and loss go on from this placement's
-                cl[k] = 0;
-            }
-            if (tid == 0) A.recn[u & 1] = 0;
-        }
+        const unsigned long long *acc = A.acc + (size_t)(u & 1) * nA;         // V0 and loss of this placement
         MoveKey adm = invalid_key(), all = invalid_key();
-        persist_select(w, S, nC, s_open, s_cand, s_exp, s_lossc, s_lossd, clp, adm, all);
-        block_best2<kPerThreads>(adm, all, s_adm, s_all);
+        long long v0c, v0d;
+        persist_select(w, S, nC, s_open, s_cand, s_exp, acc, clp, adm, all, v0c, v0d);
+        block_best2_warp0(adm, all, s_adm, s_all);
         if (tid == 0) {
             A.part[2 * blockIdx.x] = adm;
             A.part[2 * blockIdx.x + 1] = all;
+            S.v0c = v0c;   // for the check of the chosen move's objective
+            S.v0d = v0d;
         }
         if (lead_cta && S.prev_i >= 0) {
             // the closed column, now in the sums, into the global columns
@@ -589,32 +600,33 @@ __global__ void __launch_bounds__(kPerThreads, 1) k_tabu_persist(PersistArgs A)
                                 record);
             __syncthreads();
             sub(kClkRefRescan);
-            // the sums: the changes of V0 and loss (into a copy of the last
-            // move's values), the closed base's column
-            unsigned long long *cl = A.col + (size_t)(u & 1) * nA;
-            unsigned long long *nxt = A.acc + (size_t)((u + 1) & 1) * nA;
-            block_sum2<kPerThreads>(gic, gid);
-            if (tid == 0) {
-                if (gic) atomicAdd(&cl[0], (unsigned long long)gic);
-                if (gid) atomicAdd(&cl[1], (unsigned long long)gid);
+            // this CTA's parts of the move's sums -- the closed base's column
+            // (gain, extra per slot) and the changes of V0 and loss per slot --
+            // and its record count, stored in entries of its own (value v of
+            // CTA g at psum[v][g]); the update adds each value's parts up, so
+            // no address takes an atomic from every CTA
+            {
+                __shared__ long long s_p4[4][kPerWarps];
+                const long long p4[4] = {warp_sum_ll(gic), warp_sum_ll(gid), warp_sum_ll(rv0c), warp_sum_ll(rv0d)};
+                if (lane == 0)
+                    for (int e = 0; e < 4; e++) s_p4[e][warp] = p4[e];
+                __syncthreads();
+                const int g = blockIdx.x;
+                long long *P = A.psum;
+                if (tid < 4) {
+                    long long v = 0;
+                    for (int k = 0; k < kPerWarps; k++) v += s_p4[tid][k];
+                    const int at = tid < 2 ? tid : nA + tid - 2;   // gain (c, d); V0 (c, d)
+                    P[(size_t)at * G + g] = v;
+                }
+                if (tid == 0) A.nrec[g] = S.recn;
+                for (int k = tid; k < K; k += kPerThreads) {
+                    P[(size_t)(2 + k) * G + g] = (long long)s_ic[k];
+                    P[(size_t)(2 + K + k) * G + g] = (long long)s_id[k];
+                    P[(size_t)(nA + 2 + k) * G + g] = (long long)s_lc[k];
+                    P[(size_t)(nA + 2 + K + k) * G + g] = (long long)s_ld[k];
+                }
             }
-            __syncthreads();
-            block_sum2<kPerThreads>(rv0c, rv0d);
-            if (tid == 0) {
-                if (rv0c) atomicAdd(&nxt[0], (unsigned long long)rv0c);
-                if (rv0d) atomicAdd(&nxt[1], (unsigned long long)rv0d);
-            }
-            if (tid == 0) S.rbase = atomicAdd(&A.recn[u & 1], S.recn);   // this CTA's place in the list
-            for (int k = tid; k < K; k += kPerThreads) {
-                if (s_ic[k]) atomicAdd(&cl[2 + k], (unsigned long long)(long long)s_ic[k]);
-                if (s_id[k]) atomicAdd(&cl[2 + K + k], s_id[k]);
-                if (s_lc[k]) atomicAdd(&nxt[2 + k], (unsigned long long)(long long)s_lc[k]);
-                if (s_ld[k]) atomicAdd(&nxt[2 + K + k], s_ld[k]);
-            }
-            __syncthreads();   // the records, their count and their place are known
-            const int nr = S.recn, rb = S.rbase;
-            for (int q = tid; q < 2 * nr; q += kPerThreads) w.chg[2 * (size_t)rb + q] = region[q];
-            __syncthreads();
             sub(kClkRefSums);
         }
         lap(kClkRefresh);
@@ -636,7 +648,62 @@ __global__ void __launch_bounds__(kPerThreads, 1) k_tabu_persist(PersistArgs A)
             // (32 costs, 128 bytes per record) kUpdBatch records at a time and
             // compares each lane's cost with the threshold.  Each item adds
             // its sums to the columns by itself.
-            const int ntot = min(__ldcg(&A.recn[u & 1]), w.M);
+            const int G = gridDim.x;
+            // Every CTA's record count and their exclusive prefix s_pre (in
+            // the refresh's queue, unused until the next refresh): record r of
+            // the move's list is record r - s_pre[g] of CTA g's region, for
+            // the last g with s_pre[g] <= r.  Meanwhile warp k of CTA g adds up
+            // the parts of value v = g + k * G of the move's sums: the closed
+            // base's column (into the column sums), and V0 and loss of the new
+            // placement (this placement's plus the changes).
+            int *s_pre = s_q;
+            if (tid < G) s_pre[tid] = __ldcg(&A.nrec[tid]);
+            {
+                const unsigned long long *cu = A.acc + (size_t)(u & 1) * nA;
+                unsigned long long *nx = A.acc + (size_t)((u + 1) & 1) * nA;
+                unsigned long long *cl = A.col + (size_t)(u & 1) * nA;
+                for (int v = (int)blockIdx.x + warp * G; v < 2 * nA; v += kPerWarps * G) {   // the same on the warp
+                    const unsigned long long was = (v >= nA && lane == 0) ? __ldcg(&cu[v - nA]) : 0ull;
+                    long long sum = 0;
+#pragma unroll
+                    for (int e = 0; e < kMaxGrid / 32; e++) {
+                        const int g = lane + 32 * e;
+                        if (g < G) sum += __ldcg(&A.psum[(size_t)v * G + g]);
+                    }
+                    sum = warp_sum_ll(sum);
+                    if (lane == 0) {
+                        if (v < nA) cl[v] = (unsigned long long)sum;
+                        else nx[v - nA] = was + (unsigned long long)sum;
+                    }
+                }
+            }
+            __syncthreads();
+            if (warp == 0) {   // the prefix in place (G <= kMaxGrid: 8 counts per lane); s_pre[G] = the total
+                constexpr int PL = kMaxGrid / 32;
+                int v[PL], sum = 0;
+#pragma unroll
+                for (int e = 0; e < PL; e++) {
+                    const int g = lane * PL + e;
+                    v[e] = g < G ? s_pre[g] : 0;
+                    sum += v[e];
+                }
+                int incl = sum;
+#pragma unroll
+                for (int d = 1; d < 32; d <<= 1) {
+                    const int y = __shfl_up_sync(0xffffffffu, incl, d);
+                    if (lane >= d) incl += y;
+                }
+                int run = incl - sum;
+#pragma unroll
+                for (int e = 0; e < PL; e++) {
+                    const int g = lane * PL + e;
+                    if (g < G) s_pre[g] = run;
+                    run += v[e];
+                }
+                if (lane == 31) s_pre[G] = incl;
+            }
+            __syncthreads();
+            const int ntot = min(s_pre[G], w.M);
             const int r0 = (int)((long long)ntot * blockIdx.x / gridDim.x);
             const int nshare = (int)((long long)ntot * (blockIdx.x + 1) / gridDim.x) - r0;
             if (lead_cta) rec_total += ntot;
@@ -646,9 +713,17 @@ __global__ void __launch_bounds__(kPerThreads, 1) k_tabu_persist(PersistArgs A)
             unsigned flushes = 0;             // this thread's runs written to the columns
             for (int base = 0; base < nshare; base += kRecCap) {   // the same on every thread
                 const int n = min(kRecCap, nshare - base);
-                const int4 *list = w.chg + 2 * (size_t)(r0 + base);
                 __syncthreads();   // the previous round's records are used
-                for (int q = tid; q < 2 * n; q += kPerThreads) s_raw[q] = __ldcg(&list[q]);
+                for (int q = tid; q < 2 * n; q += kPerThreads) {
+                    const int r = r0 + base + (q >> 1);   // < ntot
+                    int lo = 0, hi = G - 1;               // the region holding record r
+                    while (lo < hi) {
+                        const int mid = (lo + hi + 1) >> 1;
+                        if (s_pre[mid] <= r) lo = mid;
+                        else hi = mid - 1;
+                    }
+                    s_raw[q] = __ldcg(&A.region[((size_t)lo * A.region_cap + (r - s_pre[lo])) * 2 + (q & 1)]);
+                }
                 for (int k = tid; k < K; k += kPerThreads) s_cnt[k] = 0;
                 __syncthreads();
                 // counting sort by new slot (the order within a slot is free:
@@ -832,19 +907,6 @@ __global__ void __launch_bounds__(kPerThreads, 1) k_tabu_persist(PersistArgs A)
         }
         if (!grid_sync(A.bar, gen, A.spin_limit, A.err)) break;
         lap(kClkWaitC);
-        // V0 and loss of the new placement (every CTA's refresh is in)
-        {
-            const unsigned long long *acc = A.acc + (size_t)((u + 1) & 1) * nA;
-            for (int k = tid; k < K; k += kPerThreads) {
-                s_lossc[k] = (long long)__ldcg(&acc[2 + k]);
-                s_lossd[k] = (long long)__ldcg(&acc[2 + K + k]);
-            }
-            if (tid == 0) {
-                S.v0c = (long long)__ldcg(&acc[0]);
-                S.v0d = (long long)__ldcg(&acc[1]);
-            }
-            __syncthreads();
-        }
         select();   // the next move's keys (and the closed column written back)
     }
 
@@ -916,6 +978,7 @@ int persist_grid(int K, int B, int ldT, int M_pad)
     const int blocks = (M_pad + kBlockMissions - 1) / kBlockMissions;
     int g = nb * sms;
     if (g > blocks) g = blocks;
+    if (g > kMaxGrid) g = kMaxGrid;
     return g > 0 ? g : 0;
 }
 
@@ -929,6 +992,7 @@ size_t persist_scratch_bytes(int K, int grid, int M_pad)
 {
     const size_t nA = 2 + 2 * (size_t)K;
     return per_align(2 * nA * 8, 256) * 2 + 256 + per_align((size_t)2 * grid * sizeof(MoveKey), 256) +
+           per_align((size_t)grid * 4, 256) + per_align(2 * nA * grid * 8, 256) +
            per_align(region_cap(M_pad, grid) * grid * 32, 256) + per_align((size_t)grid * kClocks * 8, 256);
 }
 
@@ -952,7 +1016,7 @@ cudaError_t launch_tabu_persist(const TabuBuffers &w, const int32_t *cost, void 
                                 long long spin_limit, cudaStream_t s)
 {
     const size_t nA = 2 + 2 * (size_t)w.K;
-    if (grid < 1 || w.ldT > kMaxLd || (w.ldT & 31)) return cudaErrorInvalidValue;
+    if (grid < 1 || grid > kMaxGrid || w.ldT > kMaxLd || (w.ldT & 31)) return cudaErrorInvalidValue;
     char *p = static_cast<char *>(scratch);
     PersistArgs A{};
     A.w = w;
@@ -963,12 +1027,15 @@ cudaError_t launch_tabu_persist(const TabuBuffers &w, const int32_t *cost, void 
     p += per_align(2 * nA * 8, 256);
     A.bar = reinterpret_cast<unsigned *>(p + 16);
     A.err = reinterpret_cast<int *>(p + 32);
-    A.recn = reinterpret_cast<int *>(p + 40);
     A.info = reinterpret_cast<long long *>(p + 64);
     p += 256;
     const size_t cleared = (size_t)(p - static_cast<char *>(scratch));
     A.part = reinterpret_cast<MoveKey *>(p);
     p += per_align((size_t)2 * grid * sizeof(MoveKey), 256);
+    A.nrec = reinterpret_cast<int *>(p);   // each written by its CTA before it is read
+    p += per_align((size_t)grid * 4, 256);
+    A.psum = reinterpret_cast<long long *>(p);
+    p += per_align(2 * nA * grid * 8, 256);
     A.region_cap = (int)region_cap(w.M_pad, grid);
     A.region = reinterpret_cast<int4 *>(p);
     p += per_align((size_t)A.region_cap * grid * 32, 256);
@@ -976,7 +1043,7 @@ cudaError_t launch_tabu_persist(const TabuBuffers &w, const int32_t *cost, void 
     A.spin_limit = spin_limit > 0 ? spin_limit : (1ll << 26);
     // clear the sums, counters and barrier, then put the start placement's
     // V0 and loss (the per-mission initialisation's) in both buffers (the
-    // first selection copies one into the other again)
+    // first move's update writes the other one again)
     cudaError_t e = cudaMemsetAsync(scratch, 0, cleared, s);
     for (int b = 0; b < 2 && e == cudaSuccess; b++) {
         unsigned long long *a0 = A.acc + (size_t)b * nA;
