@@ -260,6 +260,32 @@ STAGE_API stage_status stage_evaluate_swaps(stage_ctx *ctx, stage_inst inst, con
 STAGE_API stage_status stage_tabu_run(stage_ctx *ctx, stage_inst inst, const stage_tabu_params *params,
                             stage_tabu_result *result, stage_move *traj);
 
+/* Many Tabu searches (Alg. 3, each exactly as stage_tabu_run computes it)
+ * evaluated together: search k runs on the resident instance insts[k] with
+ * params[k]; results[k] and trajs[k] (trajs nullable, and each entry nullable;
+ * [params[k].iters] moves) receive what stage_tabu_run would return.  Every
+ * search whose shape the persistent search takes (K <= 256, at most 2048
+ * bases) and that has a move to make runs inside ONE cooperative launch:
+ * each on a gang of CTAs sized by its estimated work, the gangs placed on the
+ * GPU's CTAs largest first and run in one global order, so that their waits
+ * on one another are bounded.  Those searches use the incremental
+ * neighbourhood (one full pass, then the update of the swap terms from the
+ * missions each move touched), so each instance gets its mission-major table
+ * copy on first use, kept with it.  The other searches run one after another
+ * afterwards.  An instance may appear once per call; the call returns when all
+ * are done.
+ * Errors: STAGE_ERR_NOT_FOUND (unknown instance), STAGE_ERR_INVALID_ARG (n < 0,
+ * NULL arrays, an instance named twice, or a malformed params entry, checked
+ * as stage_tabu_run checks it), STAGE_ERR_NO_MEMORY / STAGE_ERR_ADMISSION (no
+ * room for the copies or scratch), STAGE_ERR_TIMEOUT (a wait between a
+ * search's CTAs gave up after the context's spin limit), STAGE_ERR_INTERNAL
+ * (a device self-check failed).  An error in checking or setting up a search
+ * returns at once; errors of the searches themselves are reported once every
+ * search has finished (the first of them). */
+STAGE_API stage_status stage_tabu_batch(stage_ctx *ctx, int32_t n, const stage_inst *insts,
+                              const stage_tabu_params *params, stage_tabu_result *results,
+                              stage_move *const *trajs);
+
 /* Local search (Alg. 2, read for identical vehicles): a first-improvement
  * scan of the swap neighbourhood in a randomised order.
  *   - the moves are the swaps (close the base in slot s, open the closed

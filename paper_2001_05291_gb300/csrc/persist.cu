@@ -59,10 +59,16 @@
 
 namespace stg {
 
+// CTA shapes (NT threads per CTA, REC records staged per round of the
+// update): 1024 threads and 256 records, one CTA per SM, for a single search
+// and for a batch.  (A batch of 256-thread CTAs, four per SM staging 128
+// records, took as much SM time for the batched workload's update, on 608
+// CTAs less evenly loaded: 612 ms against 517 ms per batch.)
 constexpr int kPerThreads = 1024;
-constexpr int kPerWarps = kPerThreads / 32;
+constexpr int kBatchThreads = 1024;
+constexpr int kBatchRec = 256;
 constexpr int kBlockMissions = 32;     // missions per ownership block (one warp chunk)
-constexpr int kRecCap = 256;           // records staged in shared memory per round of the update
+constexpr int kRecCap = 256;           // records staged in shared memory per round of a single search's update
 constexpr int kUpdBatch = 8;           // listed records whose costs a warp loads at once
 constexpr int kUpdItem = 24;           // listed records of one cell per work item of a warp
 constexpr int kMaxLd = 2048;           // longest table-copy row (its 64 cells fit the item scan)
@@ -102,15 +108,15 @@ struct PerLayout {
 
 __host__ __device__ inline size_t per_align(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
-__host__ __device__ inline PerLayout per_layout(int K, int B, int ldT)
+__host__ __device__ inline PerLayout per_layout(int K, int B, int ldT, int rec)
 {
     PerLayout L{};
     size_t o = 0;
-    L.recs = o;   o = per_align(o + (size_t)kRecCap * 32, 16);
-    L.raw = o;    o = per_align(o + (size_t)kRecCap * 32, 16);
+    L.recs = o;   o = per_align(o + (size_t)rec * 32, 16);
+    L.raw = o;    o = per_align(o + (size_t)rec * 32, 16);
     L.cnt = o;    o = per_align(o + (size_t)kPipeMaxK * 4, 16);
-    L.cells = o;  o = per_align(o + (size_t)kRecCap * (ldT / 32) * 4, 16);
-    L.wlist = o;  o = per_align(o + (size_t)(ldT / 32) * kRecCap * 2, 16);
+    L.cells = o;  o = per_align(o + (size_t)rec * (ldT / 32) * 4, 16);
+    L.wlist = o;  o = per_align(o + (size_t)(ldT / 32) * rec * 2, 16);
     L.cand = o;   o = per_align(o + (size_t)B * 4, 16);
     L.expiry = o; o = per_align(o + (size_t)B * 4, 16);
     L.cidx = o;   o = per_align(o + (size_t)B * 4, 16);
@@ -143,22 +149,22 @@ __device__ __forceinline__ bool wait_change(const unsigned *flag, unsigned seen,
     return false;
 }
 
-// Grid-wide barrier (the launch is cooperative, so every CTA is resident).
-// Arrivals count up without reset: barrier number g (from 0) is passed once
-// the count reaches gridDim.x * (g + 1).  Thread 0 of each CTA adds its
+// Barrier of the G CTAs that run one search (the launch is cooperative, so
+// every CTA is resident).  Arrivals count up without reset: barrier number g
+// (from 0) is passed once the count reaches G * (g + 1).  Thread 0 of each CTA adds its
 // arrival with release semantics (the CTA's writes, ordered before it by the
 // CTA barrier, become visible first) and polls the count with acquire loads,
 // at most `limit` times, then sets the timeout bit in *err and gives up.
 // Returns false when this CTA gave up or another CTA has reported an error:
 // the caller then leaves the loop.  (The count wraps after 2^32 arrivals:
 // 9 million iterations of three barriers on 152 CTAs.)
-__device__ __forceinline__ bool grid_sync(unsigned *bar, unsigned &gen, long long limit, int *err)
+__device__ __forceinline__ bool grid_sync(unsigned *bar, unsigned &gen, int G, long long limit, int *err)
 {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
         int ok = 1;
-        const unsigned target = gridDim.x * (gen + 1u);
+        const unsigned target = (unsigned)G * (gen + 1u);
         unsigned old;
         asm volatile("atom.add.release.gpu.global.u32 %0, [%1], 1;" : "=r"(old) : "l"(bar) : "memory");
         if (old + 1u != target) {
@@ -213,16 +219,18 @@ struct PersistArgs {
     const int32_t *cost;            // the table, row-major
     unsigned long long *acc;        // [2][2 + 2K]: V0 (covered, distance), loss_c[K], loss_d[K]
     unsigned long long *col;        // [2][2 + 2K]: closed column: gain (c, d), extra_c[K], extra_d[K]
-    MoveKey *part;                  // [2 * gridDim.x] best admissible, best overall per CTA
+    // per-CTA arrays are indexed by the CTA's rank g in the G CTAs of the search
+    MoveKey *part;                  // [2 * G] best admissible, best overall per CTA
     unsigned *bar;                  // arrivals at the grid barriers
     int *err;                       // error word (kErr*)
     long long *info;                // [2] CTAs, records over the search
-    int *nrec;                      // [gridDim.x] records in each CTA's region for the move
-    long long *psum;                // [2 * (2 + 2K)][gridDim.x] each CTA's parts of the move's sums
-    long long *cta_ns;              // [gridDim.x][kClocks] per-CTA time of each step, ns
-    int4 *region;                   // [gridDim.x * region_cap * 2] each CTA's records of a move
+    int *nrec;                      // [G] records in each CTA's region for the move
+    long long *psum;                // [2 * (2 + 2K)][G] each CTA's parts of the move's sums
+    long long *cta_ns;              // [G][kClocks] per-CTA time of each step, ns
+    int4 *region;                   // [G * region_cap * 2] each CTA's records of a move
     long long spin_limit;
     int region_cap;                 // records per CTA region
+    int G;                          // CTAs of the search
 };
 
 // Search scalars, the same in every CTA (each applies the same moves).
@@ -236,18 +244,19 @@ struct PerState {
 // `acc` (V0 returned in v0c, v0d).  The base closed by the previous move
 // (st.prev_i, -1 at the start) takes its column from the move's sums `cl`.
 // Every load of a swap's terms (V0, loss, gain, extra) is issued together.
+template <int NT>
 __device__ __forceinline__ void persist_select(const TabuBuffers &w, const PerState &st, int nC, const int *s_open,
                                                const int *s_cand, const int *s_exp, const unsigned long long *acc,
                                                const unsigned long long *cl, MoveKey &adm, MoveKey &all,
-                                               long long &v0c, long long &v0d)
+                                               long long &v0c, long long &v0d, int gr, int G)
 {
     const int K = w.K, t = st.t;
     v0c = (long long)__ldcg(&acc[0]);
     v0d = (long long)__ldcg(&acc[1]);
     const int total = K * nC;   // K <= 256, nC <= 2048
-    const int q0 = (int)((long long)total * blockIdx.x / gridDim.x);
-    const int q1 = (int)((long long)total * (blockIdx.x + 1) / gridDim.x);
-    for (int q = q0 + (int)threadIdx.x; q < q1; q += kPerThreads) {
+    const int q0 = (int)((long long)total * gr / G);
+    const int q1 = (int)((long long)total * (gr + 1) / G);
+    for (int q = q0 + (int)threadIdx.x; q < q1; q += NT) {
         const int s = q / nC, c = q - s * nC;
         const int i = s_open[s], j = s_cand[c];
         long long gc, gd, ec, ed;
@@ -276,6 +285,7 @@ __device__ __forceinline__ void persist_select(const TabuBuffers &w, const PerSt
 
 // Best admissible and best overall key of the CTA, valid in warp 0 only
 // (block_best2 without handing the result to every thread).
+template <int NT>
 __device__ __forceinline__ void block_best2_warp0(MoveKey &adm, MoveKey &all, MoveKey *s_adm, MoveKey *s_all)
 {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -287,24 +297,30 @@ __device__ __forceinline__ void block_best2_warp0(MoveKey &adm, MoveKey &all, Mo
     }
     __syncthreads();
     if (wid == 0) {
-        adm = s_adm[lane];
-        all = s_all[lane];
+        adm = lane < NT / 32 ? s_adm[lane] : invalid_key();
+        all = lane < NT / 32 ? s_all[lane] : invalid_key();
         warp_best_key(adm);
         warp_best_key(all);
     }
 }
 
-__global__ void __launch_bounds__(kPerThreads, 1) k_tabu_persist(PersistArgs A)
+// One whole search, run by the G CTAs of ranks gr = 0 .. G-1 (all resident,
+// each calling this with the same arguments); the lead CTA (rank 0) hands the
+// state back.
+template <int NT, int REC>
+__device__ __forceinline__ void persist_search(const PersistArgs &A, const int gr, const int G)
 {
+    constexpr int kPerWarps = NT / 32;
+    static_assert(REC <= NT && REC % 32 == 0, "one staged record per thread");
     const TabuBuffers &w = A.w;
     extern __shared__ __align__(128) unsigned char smem[];
     const int K = w.K, B = w.B, R = w.R, ldT = w.ldT;
-    const PerLayout L = per_layout(K, B, ldT);
+    const PerLayout L = per_layout(K, B, ldT, REC);
     int4 *s_recs = reinterpret_cast<int4 *>(smem + L.recs);
     int32_t *s_cells = reinterpret_cast<int32_t *>(smem + L.cells);
     int4 *s_raw = reinterpret_cast<int4 *>(smem + L.raw);
     int *s_cnt = reinterpret_cast<int *>(smem + L.cnt);
-    uint16_t *s_clist = reinterpret_cast<uint16_t *>(smem + L.wlist);   // [cell][kRecCap]
+    uint16_t *s_clist = reinterpret_cast<uint16_t *>(smem + L.wlist);   // [cell][REC]
     __shared__ int s_ccnt[kMaxLd / 32], s_ipre[kMaxLd / 32 + 1];
     int *s_cand = reinterpret_cast<int *>(smem + L.cand);
     int *s_exp = reinterpret_cast<int *>(smem + L.expiry);
@@ -320,12 +336,12 @@ __global__ void __launch_bounds__(kPerThreads, 1) k_tabu_persist(PersistArgs A)
     __shared__ long long s_clk[kClocks + 1];
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const bool lead_cta = blockIdx.x == 0;
+    const bool lead_cta = gr == 0;
     const int nA = 2 + 2 * K;
     TabuDevState *st = w.st;
     const int t_end = st->t_end, tenure = st->tenure, aw = st->accept_worsening, nC = st->nC;
     const int traj_cap = st->traj_cap;
-    int4 *region = A.region + (size_t)blockIdx.x * A.region_cap * 2;
+    int4 *region = A.region + (size_t)gr * A.region_cap * 2;
     long long rec_total = 0;   // records of this CTA over the search
     // the update's (record, base) pairs with a term, and the (record, warp
     // cell) passes with at least one: the update's work and how densely it
@@ -348,13 +364,13 @@ __global__ void __launch_bounds__(kPerThreads, 1) k_tabu_persist(PersistArgs A)
         for (int k = 0; k < kClocks; k++) s_clk[k] = 0;
         s_clk[kClocks] = gtimer();
     }
-    for (int k = tid; k < K; k += kPerThreads) s_open[k] = w.open[k];
-    for (int b = tid; b < B; b += kPerThreads) {
+    for (int k = tid; k < K; k += NT) s_open[k] = w.open[k];
+    for (int b = tid; b < B; b += NT) {
         s_exp[b] = w.expiry[b];
         s_cidx[b] = -1;
     }
     __syncthreads();
-    for (int c = tid; c < nC; c += kPerThreads) {
+    for (int c = tid; c < nC; c += NT) {
         const int b = w.cand[c];
         s_cand[c] = b;
         s_cidx[b] = c;
@@ -386,11 +402,11 @@ __global__ void __launch_bounds__(kPerThreads, 1) k_tabu_persist(PersistArgs A)
         const unsigned long long *acc = A.acc + (size_t)(u & 1) * nA;         // V0 and loss of this placement
         MoveKey adm = invalid_key(), all = invalid_key();
         long long v0c, v0d;
-        persist_select(w, S, nC, s_open, s_cand, s_exp, acc, clp, adm, all, v0c, v0d);
-        block_best2_warp0(adm, all, s_adm, s_all);
+        persist_select<NT>(w, S, nC, s_open, s_cand, s_exp, acc, clp, adm, all, v0c, v0d, gr, G);
+        block_best2_warp0<NT>(adm, all, s_adm, s_all);
         if (tid == 0) {
-            A.part[2 * blockIdx.x] = adm;
-            A.part[2 * blockIdx.x + 1] = all;
+            A.part[2 * gr] = adm;
+            A.part[2 * gr + 1] = all;
             S.v0c = v0c;   // for the check of the chosen move's objective
             S.v0d = v0d;
         }
@@ -402,7 +418,7 @@ __global__ void __launch_bounds__(kPerThreads, 1) k_tabu_persist(PersistArgs A)
                 w.gain_c[ip] = (int)(long long)__ldcg(&clp[0]);
                 w.gain_d[ip] = __ldcg(&clp[1]);
             }
-            for (int k = tid; k < K; k += kPerThreads) {
+            for (int k = tid; k < K; k += NT) {
                 w.extra_c[(size_t)k * B + ip] = (int)(long long)__ldcg(&clp[2 + k]);
                 w.extra_d[(size_t)k * B + ip] = __ldcg(&clp[2 + K + k]);
             }
@@ -413,17 +429,17 @@ __global__ void __launch_bounds__(kPerThreads, 1) k_tabu_persist(PersistArgs A)
     select();   // the first move's keys
 
     while (S.t < t_end) {   // S.t is read after a CTA barrier on every path: the same on every thread
-        if (!grid_sync(A.bar, gen, A.spin_limit, A.err)) break;
+        if (!grid_sync(A.bar, gen, G, A.spin_limit, A.err)) break;
         lap(kClkWaitA);
         const int u = S.t;   // the move of this iteration
         // ------------------------------------------------ choose and apply the move (a5, a6)
         MoveKey adm = invalid_key(), all = invalid_key();
-        for (int b = tid; b < (int)gridDim.x; b += kPerThreads) {
+        for (int b = tid; b < G; b += NT) {
             const MoveKey pa = load_key_cg(&A.part[2 * b]), px = load_key_cg(&A.part[2 * b + 1]);
             if (key_better(pa, adm)) adm = pa;
             if (key_better(px, all)) all = px;
         }
-        block_best2<kPerThreads>(adm, all, s_adm, s_all);
+        block_best2<NT>(adm, all, s_adm, s_all);
         if (!all.valid) {
             if (tid == 0) S.done = 1;   // no closed available base
             break;
@@ -471,7 +487,7 @@ __global__ void __launch_bounds__(kPerThreads, 1) k_tabu_persist(PersistArgs A)
             S.recn = 0;
             S.qn = 0;
         }
-        for (int k = tid; k < K; k += kPerThreads) {
+        for (int k = tid; k < K; k += NT) {
             s_lc[k] = 0;
             s_ld[k] = 0;
             s_ic[k] = 0;
@@ -562,16 +578,15 @@ __global__ void __launch_bounds__(kPerThreads, 1) k_tabu_persist(PersistArgs A)
                 record(term && terms_changed(ao, bo, so, a, b, k1, R), m, ao, bo, so, a, b, k1);
             };
             // this CTA's chunks: chunk r of block b is missions (b * CPB + r)
-            // * 32 .. +31, blocks blockIdx.x, + G, + 2G, ...; warp w takes the
+            // * 32 .. +31, blocks gr, gr + G, gr + 2G, ...; warp w takes the
             // CTA's chunks w, w + 32, ..., kStep per step (their loads in
             // flight together)
             constexpr int CPB = kBlockMissions / 32;   // chunks per block
             const int nch = (w.M + 31) >> 5;
-            const int G = gridDim.x;
             const int nblk = (nch + CPB - 1) / CPB;
-            const int mine_blocks = nblk > (int)blockIdx.x ? (nblk - (int)blockIdx.x + G - 1) / G : 0;
+            const int mine_blocks = nblk > gr ? (nblk - gr + G - 1) / G : 0;
             const int mine_chunks = mine_blocks * CPB;
-            auto chunk_of = [&](int k) { return ((int)blockIdx.x + (k / CPB) * G) * CPB + (k % CPB); };
+            auto chunk_of = [&](int k) { return (gr + (k / CPB) * G) * CPB + (k % CPB); };
             constexpr int kStep = 2;
             for (int k = warp; k < mine_chunks; k += kStep * kPerWarps) {   // the same on every lane
                 int ch[kStep], mm[kStep], va[kStep], vb[kStep], v1[kStep], v2[kStep], vx[kStep], vxi[kStep];
@@ -611,7 +626,7 @@ __global__ void __launch_bounds__(kPerThreads, 1) k_tabu_persist(PersistArgs A)
                 if (lane == 0)
                     for (int e = 0; e < 4; e++) s_p4[e][warp] = p4[e];
                 __syncthreads();
-                const int g = blockIdx.x;
+                const int g = gr;
                 long long *P = A.psum;
                 if (tid < 4) {
                     long long v = 0;
@@ -620,7 +635,7 @@ __global__ void __launch_bounds__(kPerThreads, 1) k_tabu_persist(PersistArgs A)
                     P[(size_t)at * G + g] = v;
                 }
                 if (tid == 0) A.nrec[g] = S.recn;
-                for (int k = tid; k < K; k += kPerThreads) {
+                for (int k = tid; k < K; k += NT) {
                     P[(size_t)(2 + k) * G + g] = (long long)s_ic[k];
                     P[(size_t)(2 + K + k) * G + g] = (long long)s_id[k];
                     P[(size_t)(nA + 2 + k) * G + g] = (long long)s_lc[k];
@@ -630,14 +645,14 @@ __global__ void __launch_bounds__(kPerThreads, 1) k_tabu_persist(PersistArgs A)
             sub(kClkRefSums);
         }
         lap(kClkRefresh);
-        if (!grid_sync(A.bar, gen, A.spin_limit, A.err)) break;
+        if (!grid_sync(A.bar, gen, G, A.spin_limit, A.err)) break;
         lap(kClkWaitB);
 
         // ------------------------------------------------ update every column with this CTA's records (a4)
         {
             // This CTA's share of the list: records r0 .. r0+nshare-1 (the
             // list is in spatial order, so a share is spatially compact),
-            // staged in shared memory in rounds of at most kRecCap, ordered by
+            // staged in shared memory in rounds of at most REC, ordered by
             // their new slot (a base's terms in a row then mostly go to one
             // slot's column and add up in one run), with the cell minima of
             // each record's row.  Per cell of the row (32 positions, one per
@@ -648,7 +663,6 @@ __global__ void __launch_bounds__(kPerThreads, 1) k_tabu_persist(PersistArgs A)
             // (32 costs, 128 bytes per record) kUpdBatch records at a time and
             // compares each lane's cost with the threshold.  Each item adds
             // its sums to the columns by itself.
-            const int G = gridDim.x;
             // Every CTA's record count and their exclusive prefix s_pre (in
             // the refresh's queue, unused until the next refresh): record r of
             // the move's list is record r - s_pre[g] of CTA g's region, for
@@ -662,7 +676,7 @@ __global__ void __launch_bounds__(kPerThreads, 1) k_tabu_persist(PersistArgs A)
                 const unsigned long long *cu = A.acc + (size_t)(u & 1) * nA;
                 unsigned long long *nx = A.acc + (size_t)((u + 1) & 1) * nA;
                 unsigned long long *cl = A.col + (size_t)(u & 1) * nA;
-                for (int v = (int)blockIdx.x + warp * G; v < 2 * nA; v += kPerWarps * G) {   // the same on the warp
+                for (int v = gr + warp * G; v < 2 * nA; v += kPerWarps * G) {   // the same on the warp
                     const unsigned long long was = (v >= nA && lane == 0) ? __ldcg(&cu[v - nA]) : 0ull;
                     long long sum = 0;
 #pragma unroll
@@ -704,17 +718,17 @@ __global__ void __launch_bounds__(kPerThreads, 1) k_tabu_persist(PersistArgs A)
             }
             __syncthreads();
             const int ntot = min(s_pre[G], w.M);
-            const int r0 = (int)((long long)ntot * blockIdx.x / gridDim.x);
-            const int nshare = (int)((long long)ntot * (blockIdx.x + 1) / gridDim.x) - r0;
+            const int r0 = (int)((long long)ntot * gr / G);
+            const int nshare = (int)((long long)ntot * (gr + 1) / G) - r0;
             if (lead_cta) rec_total += ntot;
             const int nCell = ldT >> 5;
             const int *srec = reinterpret_cast<const int *>(s_recs);
             unsigned lanes = 0, passes = 0;   // this warp's pairs with a term, (record, cell) passes
             unsigned flushes = 0;             // this thread's runs written to the columns
-            for (int base = 0; base < nshare; base += kRecCap) {   // the same on every thread
-                const int n = min(kRecCap, nshare - base);
+            for (int base = 0; base < nshare; base += REC) {   // the same on every thread
+                const int n = min(REC, nshare - base);
                 __syncthreads();   // the previous round's records are used
-                for (int q = tid; q < 2 * n; q += kPerThreads) {
+                for (int q = tid; q < 2 * n; q += NT) {
                     const int r = r0 + base + (q >> 1);   // < ntot
                     int lo = 0, hi = G - 1;               // the region holding record r
                     while (lo < hi) {
@@ -724,11 +738,10 @@ __global__ void __launch_bounds__(kPerThreads, 1) k_tabu_persist(PersistArgs A)
                     }
                     s_raw[q] = __ldcg(&A.region[((size_t)lo * A.region_cap + (r - s_pre[lo])) * 2 + (q & 1)]);
                 }
-                for (int k = tid; k < K; k += kPerThreads) s_cnt[k] = 0;
+                for (int k = tid; k < K; k += NT) s_cnt[k] = 0;
                 __syncthreads();
                 // counting sort by new slot (the order within a slot is free:
                 // the sums are integers)
-                static_assert(kRecCap <= kPerThreads, "one record per thread");
                 int key = tid < n ? s_raw[2 * tid + 1].w : 0;
                 key = (unsigned)key < (unsigned)K ? key : 0;   // an index; only the order depends on it
                 const int pos = tid < n ? atomicAdd(&s_cnt[key], 1) : 0;
@@ -777,7 +790,7 @@ __global__ void __launch_bounds__(kPerThreads, 1) k_tabu_persist(PersistArgs A)
                 // or above it has no term)
                 const int lane = tid & 31, warp = tid >> 5;
                 for (int cell = warp; cell < nCell; cell += kPerWarps) {   // the same on the warp
-                    uint16_t *cl = s_clist + cell * kRecCap;
+                    uint16_t *cl = s_clist + cell * REC;
                     int cnt = 0;
                     for (int rb = 0; rb < n; rb += 32) {   // the same on the warp
                         const int r = rb + lane;
@@ -822,7 +835,7 @@ __global__ void __launch_bounds__(kPerThreads, 1) k_tabu_persist(PersistArgs A)
                     }
                     const int cell = lo;
                     const int e0 = (it - s_ipre[cell]) * kUpdItem, e1 = min(e0 + kUpdItem, s_ccnt[cell]);
-                    const uint16_t *cl = s_clist + cell * kRecCap;
+                    const uint16_t *cl = s_clist + cell * REC;
                     const int pos = cell * 32 + lane;   // < ldT
                     const int j = w.border[pos];
                     const bool mine = j >= 0 && j != ic;
@@ -905,7 +918,7 @@ __global__ void __launch_bounds__(kPerThreads, 1) k_tabu_persist(PersistArgs A)
             S.t = u + 1;
             S.prev_i = ic;
         }
-        if (!grid_sync(A.bar, gen, A.spin_limit, A.err)) break;
+        if (!grid_sync(A.bar, gen, G, A.spin_limit, A.err)) break;
         lap(kClkWaitC);
         select();   // the next move's keys (and the closed column written back)
     }
@@ -914,19 +927,19 @@ __global__ void __launch_bounds__(kPerThreads, 1) k_tabu_persist(PersistArgs A)
     __syncthreads();
     if (tid < 4) atomicAdd(reinterpret_cast<unsigned long long *>(&A.info[2 + tid]), s_terms[tid]);
     if (tid == 0) {
-        for (int k = 0; k < kClocks; k++) A.cta_ns[(size_t)blockIdx.x * kClocks + k] = s_clk[k];
+        for (int k = 0; k < kClocks; k++) A.cta_ns[(size_t)gr * kClocks + k] = s_clk[k];
         if (lead_cta) A.info[1] = rec_total;
     }
     if (!lead_cta) return;
     const int t = S.t;
     const unsigned long long *acc = A.acc + (size_t)(t & 1) * nA;
-    for (int k = tid; k < K; k += kPerThreads) {
+    for (int k = tid; k < K; k += NT) {
         w.open[k] = s_open[k];
         w.loss_c[k] = __ldcg(&acc[2 + k]);
         w.loss_d[k] = __ldcg(&acc[2 + K + k]);
     }
-    for (int c = tid; c < nC; c += kPerThreads) w.cand[c] = s_cand[c];
-    for (int b = tid; b < B; b += kPerThreads) w.expiry[b] = s_exp[b];
+    for (int c = tid; c < nC; c += NT) w.cand[c] = s_cand[c];
+    for (int b = tid; b < B; b += NT) w.expiry[b] = s_exp[b];
     if (tid == 0) {
         w.v0[0] = __ldcg(&acc[0]);
         w.v0[1] = __ldcg(&acc[1]);
@@ -943,7 +956,37 @@ __global__ void __launch_bounds__(kPerThreads, 1) k_tabu_persist(PersistArgs A)
         st->mv_j = S.mv_j;
         st->chg_n = 0;
         st->err |= *reinterpret_cast<volatile int *>(A.err);
-        A.info[0] = gridDim.x;
+        A.info[0] = G;
+    }
+}
+
+__global__ void __launch_bounds__(kPerThreads, 1) k_tabu_persist(PersistArgs A)
+{
+    persist_search<kPerThreads, kRecCap>(A, (int)blockIdx.x, (int)gridDim.x);
+}
+
+// Many searches in one cooperative launch: CTA b runs the entries
+// sched[off[b]] .. sched[off[b+1]-1], each (search, its rank among the
+// search's G CTAs), in order.  The host gives every CTA its entries in one
+// global order of the searches, so the lowest-numbered unfinished search has
+// every one of its CTAs at it or done with it, and each barrier wait ends
+// (bounded by the spin limit in any case).  A search's arguments are staged
+// in shared memory.
+__global__ void __launch_bounds__(kBatchThreads, 1024 / kBatchThreads) k_tabu_batch(const PersistArgs *__restrict__ args,
+                                                               const int2 *__restrict__ sched,
+                                                               const int *__restrict__ off)
+{
+    __shared__ __align__(16) PersistArgs sA;
+    static_assert(sizeof(PersistArgs) % 4 == 0, "copied as 32-bit words");
+    const int e0 = off[blockIdx.x], e1 = off[blockIdx.x + 1];
+    for (int e = e0; e < e1; e++) {
+        const int2 it = sched[e];
+        const int *src = reinterpret_cast<const int *>(args + it.x);
+        int *dst = reinterpret_cast<int *>(&sA);
+        for (int q = threadIdx.x; q < (int)(sizeof(PersistArgs) / 4); q += kBatchThreads) dst[q] = __ldg(src + q);
+        __syncthreads();
+        persist_search<kBatchThreads, kBatchRec>(sA, it.y, sA.G);
+        __syncthreads();   // every thread is done with this search's arguments
     }
 }
 
@@ -956,7 +999,8 @@ __global__ void k_wait_unset_flag(const unsigned *flag, long long limit, int *er
 
 // ---------------------------------------------------------------- host side
 
-static size_t persist_smem(int K, int B, int ldT) { return per_layout(K, B, ldT).total; }
+static size_t persist_smem(int K, int B, int ldT) { return per_layout(K, B, ldT, kRecCap).total; }
+static size_t batch_smem(int K, int B, int ldT) { return per_layout(K, B, ldT, kBatchRec).total; }
 
 // CTAs of a persistent search: up to one per SM (the cooperative launch needs
 // them all resident), no more than the mission blocks; 0 when the shape is
@@ -1009,16 +1053,24 @@ size_t persist_info_offset(int K)
 
 cudaError_t persist_init()
 {
-    return cudaFuncSetAttribute(k_tabu_persist, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPerSmemLimit);
+    cudaError_t e = cudaFuncSetAttribute(k_tabu_persist, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPerSmemLimit);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_tabu_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPerSmemLimit);
+    return e;
 }
 
-cudaError_t launch_tabu_persist(const TabuBuffers &w, const int32_t *cost, void *scratch, int grid,
-                                long long spin_limit, cudaStream_t s)
+// The arguments of one search on `grid` CTAs over its scratch (laid out as
+// persist_scratch_bytes counts it), with the scratch's sums, counters and
+// barrier cleared and the start placement's V0 and loss put in both buffers
+// (asynchronously, on s).
+static cudaError_t persist_args(const TabuBuffers &w, const int32_t *cost, void *scratch, int grid,
+                                long long spin_limit, cudaStream_t s, PersistArgs &A)
 {
     const size_t nA = 2 + 2 * (size_t)w.K;
     if (grid < 1 || grid > kMaxGrid || w.ldT > kMaxLd || (w.ldT & 31)) return cudaErrorInvalidValue;
     char *p = static_cast<char *>(scratch);
-    PersistArgs A{};
+    A = PersistArgs{};
+    A.G = grid;
     A.w = w;
     A.cost = cost;
     A.acc = reinterpret_cast<unsigned long long *>(p);
@@ -1052,10 +1104,65 @@ cudaError_t launch_tabu_persist(const TabuBuffers &w, const int32_t *cost, void 
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(a0 + 2 + w.K, w.loss_d, (size_t)w.K * 8, cudaMemcpyDeviceToDevice, s);
     }
+    return e;
+}
+
+cudaError_t launch_tabu_persist(const TabuBuffers &w, const int32_t *cost, void *scratch, int grid,
+                                long long spin_limit, cudaStream_t s)
+{
+    PersistArgs A;
+    cudaError_t e = persist_args(w, cost, scratch, grid, spin_limit, s, A);
     if (e != cudaSuccess) return e;
     void *args[] = {&A};
     return cudaLaunchCooperativeKernel((const void *)k_tabu_persist, dim3(grid), dim3(kPerThreads), args,
                                        persist_smem(w.K, w.B, w.ldT), s);
+}
+
+size_t persist_args_bytes() { return sizeof(PersistArgs); }
+
+cudaError_t persist_args_host(const TabuBuffers &w, const int32_t *cost, void *scratch, int gang,
+                              long long spin_limit, cudaStream_t s, void *out)
+{
+    PersistArgs A;
+    cudaError_t e = persist_args(w, cost, scratch, gang, spin_limit, s, A);
+    if (e == cudaSuccess) *static_cast<PersistArgs *>(out) = A;
+    return e;
+}
+
+size_t persist_search_smem(int K, int B, int ldT) { return batch_smem(K, B, ldT); }
+
+// CTAs of a batch launch with `smem` bytes of dynamic shared memory: as many
+// as the device holds at once (one per SM for 1024-thread CTAs); 0 when none
+// fits.  (Each search of the batch takes at most kMaxGrid of them.)
+int persist_batch_grid(size_t smem)
+{
+    if (smem > kPerSmemLimit) return 0;
+    int nb = 0, dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, (const void *)k_tabu_batch, kBatchThreads, smem) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return nb * sms;
+}
+
+// Searches whose shape the persistent body takes (K <= 256, at most 2048
+// bases, its per-CTA arrays within the shared-memory limit).
+bool persist_shape_ok(int K, int B, int ldT)
+{
+    return K <= kPipeMaxK && !(ldT & 31) && ldT <= kMaxLd && batch_smem(K, B, ldT) <= kPerSmemLimit;
+}
+
+int persist_max_gang() { return kMaxGrid; }
+
+cudaError_t launch_tabu_batch(const void *d_args, const int2 *d_sched, const int *d_off, int grid, size_t smem,
+                              cudaStream_t s)
+{
+    const PersistArgs *a = static_cast<const PersistArgs *>(d_args);
+    void *args[] = {(void *)&a, (void *)&d_sched, (void *)&d_off};
+    return cudaLaunchCooperativeKernel((const void *)k_tabu_batch, dim3(grid), dim3(kBatchThreads), args, smem, s);
 }
 
 cudaError_t launch_wait_unset_flag(unsigned *flag, long long limit, int *err, cudaStream_t s)

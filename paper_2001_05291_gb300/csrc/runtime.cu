@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
 #include <climits>
 #include <cstdarg>
 #include <cstdio>
@@ -528,9 +529,10 @@ std::vector<int32_t> spatial_order(const std::vector<int2> &xy, int ld)
     return order;
 }
 
-stage_status run_tabu(stage_ctx *c, Instance *in, const stage_tabu_params *p,
-                      stage_tabu_result *res, stage_move *traj, int32_t *exp_a, int32_t *exp_b,
-                      int32_t *exp_b1, int32_t *exp_b2)
+// The start of one Tabu search: the parameters checked, the start placement
+// (given, resumed or ranked), the workspace set up and initialised for it,
+// the resumed best so far restored (t0 and nC out).
+stage_status tabu_prepare(stage_ctx *c, Instance *in, const stage_tabu_params *p, int *out_t0, int *out_nC)
 {
     if (!p) return set_err(c, STAGE_ERR_INVALID_ARG, "params is NULL");
     const int K = p->K;
@@ -587,6 +589,90 @@ stage_status run_tabu(stage_ctx *c, Instance *in, const stage_tabu_params *p,
         CK(cudaStreamSynchronize(c->stream));
     }
     CK(timed(c, "begin", 1, [&] { return launch_begin(tb, rs ? 1 : 0, c->stream); }));
+    *out_t0 = t0;
+    *out_nC = nC;
+    return STAGE_OK;
+}
+
+// The end of one Tabu search: the device's error word checked, the
+// trajectory and the result (best and final placements, end state) read back;
+// exp_* (nullable) receive the per-mission best / second-best state.
+stage_status tabu_finish(stage_ctx *c, Instance *in, const stage_tabu_params *p, bool count_records,
+                         stage_tabu_result *res, stage_move *traj, int32_t *exp_a, int32_t *exp_b,
+                         int32_t *exp_b1, int32_t *exp_b2)
+{
+    const int K = p->K, iters = p->iters;
+    TabuBuffers &tb = in->tb;
+    stage_status s = STAGE_OK;
+    if (exp_a) {
+        size_t per = round_up((size_t)in->M * 4, 256);
+        s = ensure_scratch(c, in, 4 * per);
+        if (s != STAGE_OK) return s;
+        char *sc = static_cast<char *>(in->mem_scratch.p);
+        auto *da = reinterpret_cast<int32_t *>(sc);
+        auto *db = reinterpret_cast<int32_t *>(sc + per);
+        auto *db1 = reinterpret_cast<int32_t *>(sc + 2 * per);
+        auto *db2 = reinterpret_cast<int32_t *>(sc + 3 * per);
+        CK(launch_export_best_two(tb, in->perm, da, db, db1, db2, c->stream));
+        CK(cudaMemcpyAsync(exp_a, da, (size_t)in->M * 4, cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaMemcpyAsync(exp_b, db, (size_t)in->M * 4, cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaMemcpyAsync(exp_b1, db1, (size_t)in->M * 4, cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaMemcpyAsync(exp_b2, db2, (size_t)in->M * 4, cudaMemcpyDeviceToHost, c->stream));
+    }
+    TabuDevState st{};
+    std::vector<int32_t> fin(K), best(K), expiry(in->B);
+    CK(cudaMemcpyAsync(&st, tb.st, sizeof st, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(fin.data(), tb.open, (size_t)K * 4, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(best.data(), tb.best_open, (size_t)K * 4, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(expiry.data(), tb.expiry, (size_t)in->B * 4, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (st.err & kErrPipelineTimeout)
+        return set_err(c, STAGE_ERR_TIMEOUT, "a device-side wait gave up after %lld polls at iteration %d",
+                       (long long)c->spin_limit, st.t);
+    if (st.err)
+        return set_err(c, STAGE_ERR_INTERNAL, "device self-check failed (code %d) at iteration %d", st.err, st.t);
+    if (count_records) {
+        // missions the incremental passes took (traffic accounting)
+        std::lock_guard<std::recursive_mutex> g(c->mu);
+        c->stats["swap_delta_records"].launches += st.chg_total + st.chg_n;
+    }
+    const int n = std::min(st.n_moves, iters);
+    if (traj && n > 0)
+        CK(cudaMemcpy(traj, tb.traj, (size_t)n * sizeof(stage_move), cudaMemcpyDeviceToHost));
+    if (res) {
+        res->n_moves = st.n_moves;
+        res->best_iter = st.best_iter;
+        res->best_cov = st.best_cov;
+        res->best_dist = st.best_dist;
+        res->final_cov = st.cur_cov;
+        res->final_dist = st.cur_dist;
+        if (res->end_state) {
+            stage_tabu_state *es = res->end_state;
+            es->t = st.t;
+            es->best_iter = st.best_iter;
+            es->best_cov = st.best_cov;
+            es->best_dist = st.best_dist;
+            if (es->open) std::copy(fin.begin(), fin.end(), es->open);
+            if (es->best_open) std::copy(best.begin(), best.end(), es->best_open);
+            if (es->tabu_expiry) std::copy(expiry.begin(), expiry.end(), es->tabu_expiry);
+        }
+        std::sort(fin.begin(), fin.end());
+        std::sort(best.begin(), best.end());
+        if (res->best_open) std::copy(best.begin(), best.end(), res->best_open);
+        if (res->final_open) std::copy(fin.begin(), fin.end(), res->final_open);
+    }
+    return STAGE_OK;
+}
+
+stage_status run_tabu(stage_ctx *c, Instance *in, const stage_tabu_params *p,
+                      stage_tabu_result *res, stage_move *traj, int32_t *exp_a, int32_t *exp_b,
+                      int32_t *exp_b1, int32_t *exp_b2)
+{
+    int t0 = 0, nC = 0;
+    stage_status s = tabu_prepare(c, in, p, &t0, &nC);
+    if (s != STAGE_OK) return s;
+    const int K = p->K, iters = p->iters;
+    TabuBuffers &tb = in->tb;
     volatile int *done_flag = static_cast<volatile int *>(c->pinned);
     const bool profiling = (c->flags & STAGE_PROFILE) != 0;
     // Incremental neighbourhood (multi-kernel path): one full pass, then each
@@ -741,64 +827,324 @@ stage_status run_tabu(stage_ctx *c, Instance *in, const stage_tabu_params *p,
             }
         }
     }
-    if (exp_a) {
-        size_t per = round_up((size_t)in->M * 4, 256);
-        s = ensure_scratch(c, in, 4 * per);
+    return tabu_finish(c, in, p, inc && multi && !persist, res, traj, exp_a, exp_b, exp_b1, exp_b2);
+}
+
+// ----------------------------------------------------------- many searches, one launch
+// Every search of a batch whose shape the persistent body takes runs inside
+// one cooperative launch (k_tabu_batch), on a gang of CTAs sized by its
+// estimated work; the others (no move to make, or a shape the body does not
+// take) run alone afterwards.  Each search computes what stage_tabu_run
+// computes for it.
+namespace {
+
+struct BatchItem {
+    Instance *in = nullptr;
+    int t0 = 0, nC = 0;
+    bool fused = false;   // runs inside the batch launch
+    int gang = 1;
+    double us_per_iter = 0.0;   // estimated on one CTA (without the fixed part)
+    TabuBuffers tw{};
+};
+
+// Estimated device time of one iteration of the persistent body on one CTA,
+// beyond its fixed part, in us, before any measurement of the instance: 2.2 ns
+// per mission (the refresh), 2 cov M / K records per move (the covered
+// missions whose best or second-best base is the closed one; cov = the start
+// placement's covered fraction) at 20 ns each plus 28 ns per cell of the row
+// read (0.386 of the row's 32-position cells on average), 2.05 ns per swap
+// (the selection).  The costs are the batched workload's measured per-CTA
+// totals (512 searches on a GB300) over these counts.  Once an instance has
+// run in a batch launch, its measured time replaces the estimate.
+double batch_iter_us(const Instance *in, int K, int R, int nC, double cov)
+{
+    if (in->batch_K == K && in->batch_R == R && in->batch_version == in->version && in->batch_work_us > 0.0)
+        return in->batch_work_us;
+    const double M = in->M_pad, cells = 0.386 * table_ldT(in->B) / 32.0;
+    const double records = 2.0 * cov * M / K;
+    return (2.2 * M + records * (20.0 + 28.0 * cells) + 2.05 * K * nC) * 1e-3;
+}
+
+constexpr double kBatchFixedUs = 5.0;    // an iteration's move, barriers and reductions on one CTA
+constexpr double kBatchGangUs = 4.0;     // more per iteration once the search spans several CTAs
+
+double batch_search_us(const BatchItem &it, int iters, int g)
+{
+    return iters * (kBatchFixedUs + (g > 1 ? kBatchGangUs : 0.0) + it.us_per_iter / g);
+}
+
+}  // namespace
+
+stage_status run_tabu_batch(stage_ctx *c, int n, const stage_inst *hs, const stage_tabu_params *ps,
+                            stage_tabu_result *res, stage_move *const *trajs)
+{
+    // host time of the call's phases (set-up, launch and read-back, results)
+    auto host_ms = [t = std::chrono::steady_clock::now()]() mutable {
+        const auto now = std::chrono::steady_clock::now();
+        const double ms = std::chrono::duration<double, std::milli>(now - t).count();
+        t = now;
+        return ms;
+    };
+    std::vector<BatchItem> items(n);
+    for (int i = 0; i < n; i++) {
+        items[i].in = find_inst(c, hs[i]);
+        if (!items[i].in) return set_err(c, STAGE_ERR_NOT_FOUND, "request %d: unknown instance %llu", i,
+                                         (unsigned long long)hs[i]);
+        for (int k = 0; k < i; k++)
+            if (items[k].in == items[i].in)
+                return set_err(c, STAGE_ERR_INVALID_ARG, "requests %d and %d name the same instance", k, i);
+    }
+    // the start of every search; the full pass that starts the incremental form
+    size_t smem = 0;
+    double total_us = 0.0;
+    for (int i = 0; i < n; i++) {
+        BatchItem &it = items[i];
+        Instance *in = it.in;
+        const stage_tabu_params *p = &ps[i];
+        stage_status s = tabu_prepare(c, in, p, &it.t0, &it.nC);
         if (s != STAGE_OK) return s;
-        char *sc = static_cast<char *>(in->mem_scratch.p);
-        auto *da = reinterpret_cast<int32_t *>(sc);
-        auto *db = reinterpret_cast<int32_t *>(sc + per);
-        auto *db1 = reinterpret_cast<int32_t *>(sc + 2 * per);
-        auto *db2 = reinterpret_cast<int32_t *>(sc + 3 * per);
-        CK(launch_export_best_two(tb, in->perm, da, db, db1, db2, c->stream));
-        CK(cudaMemcpyAsync(exp_a, da, (size_t)in->M * 4, cudaMemcpyDeviceToHost, c->stream));
-        CK(cudaMemcpyAsync(exp_b, db, (size_t)in->M * 4, cudaMemcpyDeviceToHost, c->stream));
-        CK(cudaMemcpyAsync(exp_b1, db1, (size_t)in->M * 4, cudaMemcpyDeviceToHost, c->stream));
-        CK(cudaMemcpyAsync(exp_b2, db2, (size_t)in->M * 4, cudaMemcpyDeviceToHost, c->stream));
-    }
-    TabuDevState st{};
-    std::vector<int32_t> fin(K), best(K), expiry(in->B);
-    CK(cudaMemcpyAsync(&st, tb.st, sizeof st, cudaMemcpyDeviceToHost, c->stream));
-    CK(cudaMemcpyAsync(fin.data(), tb.open, (size_t)K * 4, cudaMemcpyDeviceToHost, c->stream));
-    CK(cudaMemcpyAsync(best.data(), tb.best_open, (size_t)K * 4, cudaMemcpyDeviceToHost, c->stream));
-    CK(cudaMemcpyAsync(expiry.data(), tb.expiry, (size_t)in->B * 4, cudaMemcpyDeviceToHost, c->stream));
-    CK(cudaStreamSynchronize(c->stream));
-    if (st.err & kErrPipelineTimeout)
-        return set_err(c, STAGE_ERR_TIMEOUT, "a device-side wait gave up after %lld polls at iteration %d",
-                       (long long)c->spin_limit, st.t);
-    if (st.err)
-        return set_err(c, STAGE_ERR_INTERNAL, "device self-check failed (code %d) at iteration %d", st.err, st.t);
-    if (inc && multi && !persist) {
-        // missions the incremental passes took (traffic accounting)
-        std::lock_guard<std::recursive_mutex> g(c->mu);
-        c->stats["swap_delta_records"].launches += st.chg_total + st.chg_n;
-    }
-    const int n = std::min(st.n_moves, iters);
-    if (traj && n > 0)
-        CK(cudaMemcpy(traj, tb.traj, (size_t)n * sizeof(stage_move), cudaMemcpyDeviceToHost));
-    if (res) {
-        res->n_moves = st.n_moves;
-        res->best_iter = st.best_iter;
-        res->best_cov = st.best_cov;
-        res->best_dist = st.best_dist;
-        res->final_cov = st.cur_cov;
-        res->final_dist = st.cur_dist;
-        if (res->end_state) {
-            stage_tabu_state *es = res->end_state;
-            es->t = st.t;
-            es->best_iter = st.best_iter;
-            es->best_cov = st.best_cov;
-            es->best_dist = st.best_dist;
-            if (es->open) std::copy(fin.begin(), fin.end(), es->open);
-            if (es->best_open) std::copy(best.begin(), best.end(), es->best_open);
-            if (es->tabu_expiry) std::copy(expiry.begin(), expiry.end(), es->tabu_expiry);
+        const int K = p->K, ldT = table_ldT(in->B);
+        it.fused = it.nC > 0 && p->iters > 0 && persist_shape_ok(K, in->B, ldT) &&
+                   !(c->flags & (STAGE_FULL_PASS | STAGE_NO_PERSIST));
+        if (!it.fused) continue;
+        it.tw = in->tb;
+        if (!use_incremental(c, in, it.tw)) {
+            it.fused = false;
+            continue;
         }
-        std::sort(fin.begin(), fin.end());
-        std::sort(best.begin(), best.end());
-        if (res->best_open) std::copy(best.begin(), best.end(), res->best_open);
-        if (res->final_open) std::copy(fin.begin(), fin.end(), res->final_open);
+        CK(timed(c, "swap_eval", 1, [&] { return launch_swap_eval(it.tw, in->cost, it.nC, 0, c->stream); }));
+        smem = std::max(smem, persist_search_smem(K, in->B, ldT));
     }
-    return STAGE_OK;
+    // the start placements' covered counts (the estimate of an unmeasured search)
+    std::vector<unsigned long long> v0(2 * (size_t)n, 0ull);
+    for (int i = 0; i < n; i++)
+        if (items[i].fused)
+            CK(cudaMemcpyAsync(&v0[2 * (size_t)i], items[i].tw.v0, 16, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    for (int i = 0; i < n; i++) {
+        BatchItem &it = items[i];
+        if (!it.fused) continue;
+        const double cov = it.in->M > 0 ? std::min(1.0, (double)v0[2 * (size_t)i] / it.in->M) : 0.0;
+        it.us_per_iter = batch_iter_us(it.in, ps[i].K, ps[i].R, it.nC, cov);
+        total_us += batch_search_us(it, ps[i].iters, 1);
+    }
+    const int P = smem ? persist_batch_grid(smem) : 0;
+    c->stats["batch_host_setup"].ms += host_ms();
+    std::vector<int> order;
+    for (int i = 0; i < n; i++)
+        if (items[i].fused) {
+            if (P < 1) items[i].fused = false;
+            else order.push_back(i);
+        }
+    if (!order.empty()) {
+        // gang sizes: the smallest power of two that brings a search under half
+        // of the ideal per-CTA time (at most the search's 32-mission chunks)
+        const double ideal = total_us / P;
+        for (int i : order) {
+            BatchItem &it = items[i];
+            const int gmax = std::min({persist_max_gang(), P, (int)((it.in->M_pad + 31) / 32)});
+            int g = 1;
+            while (g * 2 <= gmax && batch_search_us(it, ps[i].iters, g) > 0.5 * ideal) g *= 2;
+            it.gang = g;
+        }
+        // placement, largest first: each search on the gang of CTAs that are
+        // free first, from the latest of their finish times; every CTA's
+        // entries are in placement order (one global order)
+        std::sort(order.begin(), order.end(), [&](int a, int b) {
+            const double wa = batch_search_us(items[a], ps[a].iters, items[a].gang) * items[a].gang;
+            const double wb = batch_search_us(items[b], ps[b].iters, items[b].gang) * items[b].gang;
+            return wa != wb ? wa > wb : a < b;
+        });
+        std::vector<double> fin(P, 0.0);
+        std::vector<std::vector<int2>> lists(P);
+        std::vector<int> idx(P);
+        for (int k = 0; k < (int)order.size(); k++) {
+            const int i = order[k];
+            const int g = items[i].gang;
+            for (int q = 0; q < P; q++) idx[q] = q;
+            std::partial_sort(idx.begin(), idx.begin() + g, idx.end(), [&](int a, int b) {
+                return fin[a] != fin[b] ? fin[a] < fin[b] : a < b;
+            });
+            double start = 0.0;
+            for (int r = 0; r < g; r++) start = std::max(start, fin[idx[r]]);
+            const double end = start + batch_search_us(items[i], ps[i].iters, g);
+            for (int r = 0; r < g; r++) {
+                fin[idx[r]] = end;
+                lists[idx[r]].push_back(make_int2(k, r));   // k: the search's place in the args array
+            }
+        }
+        // per search its scratch and arguments; the schedule
+        const size_t ab = persist_args_bytes();
+        std::vector<unsigned char> h_args(ab * order.size());
+        for (int k = 0; k < (int)order.size(); k++) {
+            BatchItem &it = items[order[k]];
+            Instance *in = it.in;
+            const size_t need = persist_scratch_bytes(ps[order[k]].K, it.gang, in->M_pad);
+            if (!in->mem_persist.p || in->mem_persist.bytes < need) {
+                dev_free(c, in->mem_persist);
+                stage_status s = dev_alloc(c, need, in->mem_persist);
+                if (s != STAGE_OK) return s;
+            }
+            CK(persist_args_host(it.tw, in->cost, in->mem_persist.p, it.gang, c->spin_limit, c->stream,
+                                 h_args.data() + ab * k));
+        }
+        std::vector<int2> h_sched;
+        std::vector<int> h_off(P + 1, 0);
+        for (int q = 0; q < P; q++) {
+            h_off[q] = (int)h_sched.size();
+            h_sched.insert(h_sched.end(), lists[q].begin(), lists[q].end());
+        }
+        h_off[P] = (int)h_sched.size();
+        const size_t off_args = 0, off_sched = round_up(h_args.size(), 256),
+                     off_off = off_sched + round_up(h_sched.size() * sizeof(int2), 256),
+                     bytes = off_off + round_up(h_off.size() * sizeof(int), 256);
+        DevBuf buf;
+        stage_status s = dev_alloc(c, bytes, buf);
+        if (s != STAGE_OK) return s;
+        char *d = static_cast<char *>(buf.p);
+        cudaError_t e = cudaMemcpyAsync(d + off_args, h_args.data(), h_args.size(), cudaMemcpyHostToDevice, c->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(d + off_sched, h_sched.data(), h_sched.size() * sizeof(int2), cudaMemcpyHostToDevice,
+                                c->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(d + off_off, h_off.data(), h_off.size() * sizeof(int), cudaMemcpyHostToDevice,
+                                c->stream);
+        if (e == cudaSuccess)
+            e = timed(c, "tabu_batch", 1, [&] {
+                return launch_tabu_batch(d + off_args, reinterpret_cast<const int2 *>(d + off_sched),
+                                         reinterpret_cast<const int *>(d + off_off), P, smem, c->stream);
+            });
+        // the host arrays are read by the copies: wait for them
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        dev_free(c, buf);
+        CK(e);
+        // each search's measured work (its CTAs' time outside the waits, per
+        // iteration) for the next batch's gang sizes
+        {
+            std::vector<std::vector<long long>> clk(order.size());
+            std::vector<TabuDevState> sd(order.size());
+            for (int k = 0; k < (int)order.size(); k++) {
+                const BatchItem &it = items[order[k]];
+                clk[k].resize((size_t)it.gang * kPersistClocks);
+                CK(cudaMemcpyAsync(clk[k].data(),
+                                   static_cast<const char *>(it.in->mem_persist.p) +
+                                       persist_clock_offset(ps[order[k]].K, it.gang, it.in->M_pad),
+                                   clk[k].size() * sizeof(long long), cudaMemcpyDeviceToHost, c->stream));
+                CK(cudaMemcpyAsync(&sd[k], it.tw.st, sizeof(TabuDevState), cudaMemcpyDeviceToHost, c->stream));
+            }
+            CK(cudaStreamSynchronize(c->stream));
+            for (int k = 0; k < (int)order.size(); k++) {
+                BatchItem &it = items[order[k]];
+                const int done = sd[k].t - it.t0;
+                if (done < 1 || sd[k].err) continue;
+                double ns = 0.0;
+                for (int r = 0; r < it.gang; r++) {
+                    const long long *q = &clk[k][(size_t)r * kPersistClocks];
+                    ns += (double)(q[0] + q[1] + q[3] + q[5]);   // move, refresh, update, select
+                }
+                const double fixed = kBatchFixedUs * it.gang;   // counted in the move and select
+                it.in->batch_work_us = std::max(0.0, ns * 1e-3 / done - fixed);
+                it.in->batch_K = ps[order[k]].K;
+                it.in->batch_R = ps[order[k]].R;
+                it.in->batch_version = it.in->version;
+            }
+        }
+        // records over each search (the batch's traffic accounting)
+        std::vector<long long> info(6 * order.size(), 0);
+        for (int k = 0; k < (int)order.size(); k++)
+            CK(cudaMemcpyAsync(&info[6 * k],
+                               static_cast<const char *>(items[order[k]].in->mem_persist.p) +
+                                   persist_info_offset(ps[order[k]].K),
+                               6 * sizeof(long long), cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        {
+            std::lock_guard<std::recursive_mutex> g(c->mu);
+            for (int k = 0; k < (int)order.size(); k++) {
+                c->stats["batch_records"].launches += info[6 * k + 1];
+                c->stats["batch_cells_read"].launches += info[6 * k + 5];
+            }
+            c->stats["batch_searches"].launches += (long long)order.size();
+            c->stats["batch_ctas"].launches = P;
+            int gmax = 1;
+            for (int i : order) gmax = std::max(gmax, items[i].gang);
+            c->stats["batch_gang_max"].launches = gmax;
+        }
+        if (c->flags & STAGE_PROFILE) {
+            // the searches' own clocks: each CTA's busy time (the sum of its
+            // searches' steps) and each step's total over the batch
+            std::vector<double> busy(P, 0.0), step(kPersistClocks, 0.0);
+            double est = 0.0, longest = 0.0;
+            int longest_i = -1;
+            for (int k = 0; k < (int)order.size(); k++) {
+                const BatchItem &it = items[order[k]];
+                const int K = ps[order[k]].K;
+                std::vector<long long> clk((size_t)it.gang * kPersistClocks);
+                CK(cudaMemcpy(clk.data(),
+                              static_cast<const char *>(it.in->mem_persist.p) +
+                                  persist_clock_offset(K, it.gang, it.in->M_pad),
+                              clk.size() * sizeof(long long), cudaMemcpyDeviceToHost));
+                double dur = 0.0;   // the search's time: its slowest CTA's
+                for (int r = 0; r < it.gang; r++) {
+                    double d = 0.0;
+                    for (int q = 0; q < kPersistClocks; q++) {
+                        step[q] += clk[(size_t)r * kPersistClocks + q] * 1e-6;
+                        if (q < 7) d += clk[(size_t)r * kPersistClocks + q] * 1e-6;
+                    }
+                    dur = std::max(dur, d);
+                }
+                if (dur > longest) {
+                    longest = dur;
+                    longest_i = order[k];
+                }
+                est += batch_search_us(it, ps[order[k]].iters, it.gang) * 1e-3 * it.gang;
+            }
+            for (int q = 0; q < P; q++)
+                for (int e = h_off[q]; e < h_off[q + 1]; e++) {
+                    const int k = h_sched[e].x, r = h_sched[e].y;
+                    const BatchItem &it = items[order[k]];
+                    std::vector<long long> clk(7);
+                    CK(cudaMemcpy(clk.data(),
+                                  static_cast<const char *>(it.in->mem_persist.p) +
+                                      persist_clock_offset(ps[order[k]].K, it.gang, it.in->M_pad) +
+                                      (size_t)r * kPersistClocks * sizeof(long long),
+                                  7 * sizeof(long long), cudaMemcpyDeviceToHost));
+                    for (int q2 = 0; q2 < 7; q2++) busy[q] += clk[q2] * 1e-6;
+                }
+            std::lock_guard<std::recursive_mutex> g(c->mu);
+            double mx = 0.0, sum = 0.0;
+            for (double b : busy) { mx = std::max(mx, b); sum += b; }
+            c->stats["batch_cta_busy_max"].ms += mx;
+            c->stats["batch_cta_busy_mean"].ms += sum / P;
+            c->stats["batch_cta_estimate"].ms += est / P;
+            if (longest_i >= 0) {
+                // the longest search: its time, request index and gang; its estimate
+                KernelStat &ls = c->stats["batch_longest"];
+                ls.ms = longest;
+                ls.launches = longest_i;
+                KernelStat &le = c->stats["batch_longest_estimate"];
+                le.ms = batch_search_us(items[longest_i], ps[longest_i].iters, items[longest_i].gang) * 1e-3;
+                le.launches = items[longest_i].gang;
+            }
+            const char *nm[7] = {"batch_move", "batch_refresh", "batch_wait_refresh", "batch_update",
+                                 "batch_wait_update", "batch_select", "batch_wait_select"};
+            for (int q = 0; q < 7; q++) c->stats[nm[q]].ms += step[q];
+        }
+    }
+    // the results; the searches the launch did not take, alone
+    c->stats["batch_host_launch"].ms += host_ms();
+    stage_status first = STAGE_OK;
+    for (int i = 0; i < n; i++) {
+        stage_status s;
+        if (items[i].fused || items[i].nC == 0 || ps[i].iters == 0)
+            s = tabu_finish(c, items[i].in, &ps[i], false, &res[i], trajs ? trajs[i] : nullptr, nullptr, nullptr,
+                            nullptr, nullptr);
+        else
+            s = run_tabu(c, items[i].in, &ps[i], &res[i], trajs ? trajs[i] : nullptr, nullptr, nullptr, nullptr,
+                         nullptr);
+        if (s != STAGE_OK && first == STAGE_OK) first = s;
+    }
+    c->stats["batch_host_results"].ms += host_ms();
+    return first;
 }
 
 // ----------------------------------------------------------- heterogeneous fleet
@@ -1712,6 +2058,18 @@ stage_status stage_tabu_run(stage_ctx *c, stage_inst h, const stage_tabu_params 
     if (!in) return set_err(c, STAGE_ERR_NOT_FOUND, "unknown instance %llu", (unsigned long long)h);
     CK(cudaSetDevice(c->device));
     return run_tabu(c, in, p, res, traj, nullptr, nullptr, nullptr, nullptr);
+}
+
+stage_status stage_tabu_batch(stage_ctx *c, int32_t n, const stage_inst *insts, const stage_tabu_params *params,
+                              stage_tabu_result *results, stage_move *const *trajs)
+{
+    if (!c) return STAGE_ERR_INVALID_ARG;
+    Guard g(c);
+    if (n < 0) return set_err(c, STAGE_ERR_INVALID_ARG, "n=%d < 0", n);
+    if (n == 0) return STAGE_OK;
+    if (!insts || !params || !results) return set_err(c, STAGE_ERR_INVALID_ARG, "insts, params or results is NULL");
+    CK(cudaSetDevice(c->device));
+    return run_tabu_batch(c, n, insts, params, results, trajs);
 }
 
 stage_status stage_autotune(stage_ctx *c, stage_inst h, const int32_t *open, int32_t K, int32_t R, int32_t *out)

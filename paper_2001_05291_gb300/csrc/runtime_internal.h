@@ -71,6 +71,12 @@ struct Instance {
     int busy = 0;        // batch requests referring to this instance
     uint64_t version = 0;      // stage_update_instance calls so far
     ResidentState resident;    // kept between batch requests (resume_resident)
+    // the measured device work of this instance's last search in a batch
+    // launch (CTA time per iteration outside the waits, us), for that K, R and
+    // version: the next batch sizes its gang from it
+    double batch_work_us = 0.0;
+    int batch_K = 0, batch_R = -1;
+    uint64_t batch_version = 0;
 };
 
 struct Engine;   // batch engine (engine.cu)

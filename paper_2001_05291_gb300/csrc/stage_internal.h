@@ -181,6 +181,22 @@ size_t persist_info_offset(int K);
 size_t persist_clock_offset(int K, int grid, int M_pad);
 cudaError_t launch_tabu_persist(const TabuBuffers &w, const int32_t *cost, void *scratch, int grid,
                                 long long spin_limit, cudaStream_t s);
+// Many searches in one cooperative launch (k_tabu_batch): search k runs on
+// `gang` CTAs with the arguments persist_args_host wrote (persist_args_bytes
+// each, copied to the device as one array d_args), its scratch laid out for
+// that gang; d_sched / d_off give each CTA its (search, rank) entries in one
+// global order of the searches.  persist_search_smem: the dynamic shared
+// memory a search of this shape needs (the launch takes the largest);
+// persist_batch_grid: the CTAs the device holds at once with that much.
+size_t persist_args_bytes();
+cudaError_t persist_args_host(const TabuBuffers &w, const int32_t *cost, void *scratch, int gang,
+                              long long spin_limit, cudaStream_t s, void *out);
+size_t persist_search_smem(int K, int B, int ldT);
+int persist_batch_grid(size_t smem);
+bool persist_shape_ok(int K, int B, int ldT);
+int persist_max_gang();
+cudaError_t launch_tabu_batch(const void *d_args, const int2 *d_sched, const int *d_off, int grid, size_t smem,
+                              cudaStream_t s);
 cudaError_t persist_init();
 // Test support: a wait on a flag that nothing sets, bounded by `limit` polls;
 // it sets kErrPipelineTimeout in *err when it gives up.

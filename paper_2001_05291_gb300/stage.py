@@ -51,6 +51,19 @@ class StageMove(C.Structure):
                 ("cov", C.c_int64), ("dist", C.c_int64)]
 
 
+_MOVE_DTYPE = np.dtype([("iter", np.int32), ("i", np.int32), ("j", np.int32), ("flags", np.int32),
+                        ("cov", np.int64), ("dist", np.int64)])
+assert _MOVE_DTYPE.itemsize == C.sizeof(StageMove)
+
+
+def _moves(traj, n: int) -> list:
+    """The first n stage_move records of a ctypes array, as (iter, i, j,
+    flags, cov, dist) tuples of Python ints."""
+    if traj is None or n <= 0:
+        return []
+    return np.frombuffer(traj, dtype=_MOVE_DTYPE, count=n).tolist()
+
+
 class StageTabuState(C.Structure):
     _fields_ = [("t", C.c_int32), ("best_iter", C.c_int32), ("best_cov", C.c_int64),
                 ("best_dist", C.c_int64), ("open", C.c_void_p), ("best_open", C.c_void_p),
@@ -138,6 +151,8 @@ def lib():
             "stage_evaluate_placement": ([p, C.c_uint64, p, i32, i32, C.POINTER(i64), C.POINTER(i64)], st),
             "stage_evaluate_swaps": ([p, C.c_uint64, p, i32, i32, p, p], st),
             "stage_tabu_run": ([p, C.c_uint64, C.POINTER(StageTabuParams), C.POINTER(StageTabuResult), p], st),
+            "stage_tabu_batch": ([p, i32, C.POINTER(C.c_uint64), C.POINTER(StageTabuParams),
+                                  C.POINTER(StageTabuResult), C.POINTER(p)], st),
             "stage_local_search": ([p, C.c_uint64, C.POINTER(StageLsParams), C.POINTER(StageLsResult), p], st),
             "stage_fleet_tabu": ([p, C.c_uint64, C.POINTER(StageFleetParams), C.POINTER(StageFleetResult), p], st),
             "stage_kernel_stats": ([p, C.c_char_p, C.POINTER(i64), C.POINTER(C.c_double)], st),
@@ -401,10 +416,7 @@ class Context:
         traj = (StageMove * max(1, iters))() if trajectory else None
         self._check(lib().stage_fleet_tabu(self._h, inst, C.byref(p), C.byref(r),
                                            C.cast(traj, C.c_void_p) if traj is not None else None))
-        moves = []
-        if traj is not None:
-            moves = [(traj[k].iter, traj[k].i, traj[k].j, traj[k].flags, traj[k].cov, traj[k].dist)
-                     for k in range(min(r.n_moves, iters))]
+        moves = _moves(traj, min(r.n_moves, iters))
         return FleetResult(r.n_moves, br, bf, r.best_cov, r.best_dist, r.best_iter, fr, ff, r.final_cov,
                            r.final_dist, moves)
 
@@ -430,10 +442,7 @@ class Context:
         traj = (StageMove * max(1, max_moves))() if trajectory else None
         self._check(lib().stage_local_search(self._h, inst, C.byref(p), C.byref(r),
                                              C.cast(traj, C.c_void_p) if traj is not None else None))
-        moves = []
-        if traj is not None:
-            moves = [(traj[k].iter, traj[k].i, traj[k].j, traj[k].flags, traj[k].cov, traj[k].dist)
-                     for k in range(min(r.n_moves, max_moves))]
+        moves = _moves(traj, min(r.n_moves, max_moves))
         return LocalSearchResult(r.n_moves, r.passes, bool(r.local_optimum), fin, r.final_cov, r.final_dist,
                                  moves)
 
@@ -475,8 +484,7 @@ class Context:
                                          C.cast(traj, C.c_void_p) if traj is not None else None))
         moves = []
         if traj is not None:
-            moves = [(traj[k].iter, traj[k].i, traj[k].j, traj[k].flags, traj[k].cov, traj[k].dist)
-                     for k in range(r.n_moves)]
+            moves = _moves(traj, r.n_moves)
         out = TabuResult(r.n_moves, best, r.best_cov, r.best_dist, r.best_iter, fin, r.final_cov,
                          r.final_dist, moves)
         if es is not None:
@@ -484,6 +492,40 @@ class Context:
                                  best_dist=es.best_dist, open=es_open, best_open=es_best,
                                  tabu_expiry=es_exp)
         return out
+
+    def tabu_batch(self, requests, trajectory: bool = True) -> list:
+        """stage_tabu_batch: many Tabu searches in one launch.  Each request is a
+        dict(inst, K, R, iters, tenure[, start_open][, accept_worsening]); returns
+        one TabuResult per request, in order."""
+        n = len(requests)
+        hs = (C.c_uint64 * max(1, n))()
+        ps = (StageTabuParams * max(1, n))()
+        rs = (StageTabuResult * max(1, n))()
+        tp = (C.c_void_p * max(1, n))()
+        keep, outs = [], []
+        for k, q in enumerate(requests):
+            hs[k] = q["inst"]
+            P = ps[k]
+            P.K, P.R, P.iters, P.tenure = q["K"], q["R"], q["iters"], q["tenure"]
+            P.accept_worsening = 1 if q.get("accept_worsening", True) else 0
+            if q.get("start_open") is not None:
+                so = _host_i32(q["start_open"], q["K"])
+                keep.append(so)
+                P.start_open = _ptr(so)
+            best = np.empty(q["K"], dtype=np.int32)
+            fin = np.empty(q["K"], dtype=np.int32)
+            rs[k].best_open, rs[k].final_open = _ptr(best), _ptr(fin)
+            traj = (StageMove * max(1, q["iters"]))() if trajectory else None
+            tp[k] = C.cast(traj, C.c_void_p) if traj is not None else None
+            outs.append((best, fin, traj))
+        self._check(lib().stage_tabu_batch(self._h, n, hs, ps, rs, tp))
+        results = []
+        for k, (best, fin, traj) in enumerate(outs):
+            r = rs[k]
+            moves = _moves(traj, r.n_moves)
+            results.append(TabuResult(r.n_moves, best, r.best_cov, r.best_dist, r.best_iter, fin, r.final_cov,
+                                      r.final_dist, moves))
+        return results
 
     def best_two(self, inst: int, open_, R: int, M: int, tabu_steps: int = 0, tenure: int = 0):
         o = _host_i32(open_)
@@ -565,8 +607,7 @@ class Context:
             lib().stage_last_error(self._h, buf, 512)
             raise StageError(rc, f"batch request failed (ticket {ticket.id}); the context's last error: "
                                  f"{buf.value.decode(errors='replace')}")
-        moves = [(ticket.traj[k].iter, ticket.traj[k].i, ticket.traj[k].j, ticket.traj[k].flags,
-                  ticket.traj[k].cov, ticket.traj[k].dist) for k in range(res.n_moves)]
+        moves = _moves(ticket.traj, res.n_moves)
         out = TabuResult(res.n_moves, ticket.best, res.best_cov, res.best_dist, res.best_iter, ticket.final,
                          res.final_cov, res.final_dist, moves)
         out.timing = dict(submit_ns=res.t_submit_ns, start_ns=res.t_start_ns, end_ns=res.t_end_ns)
@@ -678,6 +719,7 @@ stage_rank_bases = Context.rank_bases
 stage_evaluate_placement = Context.evaluate_placement
 stage_evaluate_swaps = Context.evaluate_swaps
 stage_tabu_run = Context.tabu_run
+stage_tabu_batch = Context.tabu_batch
 stage_local_search = Context.local_search
 stage_fleet_tabu = Context.fleet_tabu
 stage_best_two = Context.best_two
