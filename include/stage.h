@@ -75,11 +75,15 @@ typedef int32_t stage_status;
 #define STAGE_AUTOTUNE     4u   /* tune the swap pass's tile the first time a shape is met */
 #define STAGE_FULL_PASS    8u   /* Tabu searches (stage_tabu_run) re-evaluate the whole swap
                                    neighbourhood by a full pass over the cost table every
-                                   iteration.  By default, for tables well beyond the L2 cache
-                                   (candidate rows x missions x 4 B >= 256 MiB), the
-                                   neighbourhood's terms are kept across iterations and updated
-                                   for the missions whose best or second-best open base changed
-                                   (the same values exactly).  That form keeps a mission-major
+                                   iteration.  By default the neighbourhood's terms are kept
+                                   across iterations and updated for the missions whose best or
+                                   second-best open base changed (the same values exactly),
+                                   the whole search in one cooperative launch, whenever that
+                                   launch takes the shape (K <= 256, at most 2048 bases) and the
+                                   search is not one small enough for a single block; with
+                                   STAGE_NO_PERSIST, as per-iteration launches for tables well
+                                   beyond the L2 cache (candidate rows x missions x 4 B >=
+                                   256 MiB) and a full pass otherwise.  That form keeps a mission-major
                                    copy of the cost table with the instance (the table's size
                                    again, built on the first such search and again after
                                    stage_update_instance) and 32 bytes per mission; when the

@@ -675,27 +675,26 @@ stage_status run_tabu(stage_ctx *c, Instance *in, const stage_tabu_params *p,
     TabuBuffers &tb = in->tb;
     volatile int *done_flag = static_cast<volatile int *>(c->pinned);
     const bool profiling = (c->flags & STAGE_PROFILE) != 0;
-    // Incremental neighbourhood (multi-kernel path): one full pass, then each
-    // iteration selects and applies a move, refreshes the per-mission state
-    // (recording the missions whose terms changed, rebuilding the closed
-    // base's column) and updates the other columns from those records.
-    // STAGE_FULL_PASS: a full pass every iteration instead.
-    // Only for tables well beyond the L2 cache: an L2-resident table is
-    // streamed faster than the scattered columns of the changed missions.
-    bool inc = !(c->flags & STAGE_FULL_PASS) && swap_delta_fits(K) &&
-               ((c->flags & STAGE_INCREMENTAL) ||
-                (size_t)nC * in->M_pad * sizeof(int32_t) >= kIncrementalMinTableBytes);
+    // Incremental neighbourhood: one full pass, then each iteration selects
+    // and applies a move, refreshes the per-mission state (recording the
+    // missions whose terms changed, rebuilding the closed base's column) and
+    // updates the other columns from those records.  STAGE_FULL_PASS: a full
+    // pass every iteration instead.  The whole loop runs in one cooperative
+    // launch where the shape fits and the device can hold the grid (not with
+    // STAGE_NO_PERSIST, nor for the test-support export of the per-mission
+    // state, which the persistent search keeps exact only up to R); that form
+    // is taken whenever it can run.  The per-iteration launches of the
+    // incremental form are taken only for tables well beyond the L2 cache: an
+    // L2-resident table is streamed faster than their scattered columns.
     TabuBuffers tw = tb;   // the buffers of this run's multi-kernel launches
     const bool multi = nC > 0 && iters > 0 && !(tabu_resident_fits(K, in->B, in->M_pad, nC)) &&
                        !(tabu_small_fits(nC, in->M_pad, K));
-    // the incremental form's whole loop in one cooperative launch, where the
-    // shape fits and the device can hold the grid (STAGE_NO_PERSIST: the
-    // per-iteration launches instead)
-    // (not for the test-support export of the per-mission state: the
-    // persistent search keeps it exact only up to R)
-    bool persist = inc && multi && !(c->flags & STAGE_NO_PERSIST) && tw.mask == nullptr && exp_a == nullptr;
-    const int pgrid = persist ? persist_grid(K, in->B, table_ldT(in->B), in->M_pad) : 0;
-    if (pgrid < 1) persist = false;
+    const bool persist_ok = multi && !(c->flags & STAGE_NO_PERSIST) && tw.mask == nullptr && exp_a == nullptr;
+    const int pgrid = persist_ok ? persist_grid(K, in->B, table_ldT(in->B), in->M_pad) : 0;
+    bool inc = !(c->flags & STAGE_FULL_PASS) && swap_delta_fits(K) &&
+               ((c->flags & STAGE_INCREMENTAL) || pgrid > 0 ||
+                (size_t)nC * in->M_pad * sizeof(int32_t) >= kIncrementalMinTableBytes);
+    bool persist = inc && pgrid > 0;
     if (inc) inc = use_incremental(c, in, tw);
     // one Tabu iteration of the multi-kernel path
     auto step = [&](bool time_each) -> cudaError_t {
@@ -1009,86 +1008,65 @@ stage_status run_tabu_batch(stage_ctx *c, int n, const stage_inst *hs, const sta
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(d + off_off, h_off.data(), h_off.size() * sizeof(int), cudaMemcpyHostToDevice,
                                 c->stream);
+        // the launch, timed by CUDA events on its stream whether or not the
+        // context profiles (one launch per call)
+        cudaEvent_t ev0 = get_event(c), ev1 = get_event(c);
+        if (e == cudaSuccess) e = cudaEventRecord(ev0, c->stream);
         if (e == cudaSuccess)
-            e = timed(c, "tabu_batch", 1, [&] {
-                return launch_tabu_batch(d + off_args, reinterpret_cast<const int2 *>(d + off_sched),
-                                         reinterpret_cast<const int *>(d + off_off), P, smem, c->stream);
-            });
+            e = launch_tabu_batch(d + off_args, reinterpret_cast<const int2 *>(d + off_sched),
+                                  reinterpret_cast<const int *>(d + off_off), P, smem, c->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(ev1, c->stream);
         // the host arrays are read by the copies: wait for them
         if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        float kms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&kms, ev0, ev1);
+        c->event_pool.push_back(ev0);
+        c->event_pool.push_back(ev1);
         dev_free(c, buf);
         CK(e);
-        // each search's measured work (its CTAs' time outside the waits, per
-        // iteration) for the next batch's gang sizes
-        {
-            std::vector<std::vector<long long>> clk(order.size());
-            std::vector<TabuDevState> sd(order.size());
-            for (int k = 0; k < (int)order.size(); k++) {
-                const BatchItem &it = items[order[k]];
-                clk[k].resize((size_t)it.gang * kPersistClocks);
-                CK(cudaMemcpyAsync(clk[k].data(),
-                                   static_cast<const char *>(it.in->mem_persist.p) +
-                                       persist_clock_offset(ps[order[k]].K, it.gang, it.in->M_pad),
-                                   clk[k].size() * sizeof(long long), cudaMemcpyDeviceToHost, c->stream));
-                CK(cudaMemcpyAsync(&sd[k], it.tw.st, sizeof(TabuDevState), cudaMemcpyDeviceToHost, c->stream));
-            }
-            CK(cudaStreamSynchronize(c->stream));
-            for (int k = 0; k < (int)order.size(); k++) {
-                BatchItem &it = items[order[k]];
-                const int done = sd[k].t - it.t0;
-                if (done < 1 || sd[k].err) continue;
-                double ns = 0.0;
-                for (int r = 0; r < it.gang; r++) {
-                    const long long *q = &clk[k][(size_t)r * kPersistClocks];
-                    ns += (double)(q[0] + q[1] + q[3] + q[5]);   // move, refresh, update, select
-                }
-                const double fixed = kBatchFixedUs * it.gang;   // counted in the move and select
-                it.in->batch_work_us = std::max(0.0, ns * 1e-3 / done - fixed);
-                it.in->batch_K = ps[order[k]].K;
-                it.in->batch_R = ps[order[k]].R;
-                it.in->batch_version = it.in->version;
-            }
-        }
-        // records over each search (the batch's traffic accounting)
-        std::vector<long long> info(6 * order.size(), 0);
-        for (int k = 0; k < (int)order.size(); k++)
-            CK(cudaMemcpyAsync(&info[6 * k],
-                               static_cast<const char *>(items[order[k]].in->mem_persist.p) +
-                                   persist_info_offset(ps[order[k]].K),
-                               6 * sizeof(long long), cudaMemcpyDeviceToHost, c->stream));
-        CK(cudaStreamSynchronize(c->stream));
         {
             std::lock_guard<std::recursive_mutex> g(c->mu);
-            for (int k = 0; k < (int)order.size(); k++) {
-                c->stats["batch_records"].launches += info[6 * k + 1];
-                c->stats["batch_cells_read"].launches += info[6 * k + 5];
-            }
-            c->stats["batch_searches"].launches += (long long)order.size();
-            c->stats["batch_ctas"].launches = P;
-            int gmax = 1;
-            for (int i : order) gmax = std::max(gmax, items[i].gang);
-            c->stats["batch_gang_max"].launches = gmax;
+            KernelStat &ks = c->stats["tabu_batch"];
+            ks.launches += 1;
+            ks.ms += kms;
         }
-        if (c->flags & STAGE_PROFILE) {
-            // the searches' own clocks: each CTA's busy time (the sum of its
-            // searches' steps) and each step's total over the batch
-            std::vector<double> busy(P, 0.0), step(kPersistClocks, 0.0);
+        // Each search's own clocks, state and counters.  Its measured work (its
+        // CTAs' time outside the waits, per iteration) sizes its gang in the
+        // next batch; the batch's statistics: every CTA's busy time (the sum of
+        // its searches' steps), each step's total, the longest search, the
+        // records and cell pieces the updates read.
+        {
+            const int ns_ = (int)order.size();
+            std::vector<std::vector<long long>> clk(ns_);
+            std::vector<TabuDevState> sd(ns_);
+            std::vector<long long> info(6 * (size_t)ns_, 0);
+            for (int k = 0; k < ns_; k++) {
+                const BatchItem &it = items[order[k]];
+                const char *base = static_cast<const char *>(it.in->mem_persist.p);
+                clk[k].resize((size_t)it.gang * kPersistClocks);
+                CK(cudaMemcpyAsync(clk[k].data(), base + persist_clock_offset(ps[order[k]].K, it.gang, it.in->M_pad),
+                                   clk[k].size() * sizeof(long long), cudaMemcpyDeviceToHost, c->stream));
+                CK(cudaMemcpyAsync(&sd[k], it.tw.st, sizeof(TabuDevState), cudaMemcpyDeviceToHost, c->stream));
+                CK(cudaMemcpyAsync(&info[6 * (size_t)k], base + persist_info_offset(ps[order[k]].K),
+                                   6 * sizeof(long long), cudaMemcpyDeviceToHost, c->stream));
+            }
+            CK(cudaStreamSynchronize(c->stream));
+            std::vector<double> busy(P, 0.0), step(7, 0.0);
             double est = 0.0, longest = 0.0;
             int longest_i = -1;
-            for (int k = 0; k < (int)order.size(); k++) {
-                const BatchItem &it = items[order[k]];
-                const int K = ps[order[k]].K;
-                std::vector<long long> clk((size_t)it.gang * kPersistClocks);
-                CK(cudaMemcpy(clk.data(),
-                              static_cast<const char *>(it.in->mem_persist.p) +
-                                  persist_clock_offset(K, it.gang, it.in->M_pad),
-                              clk.size() * sizeof(long long), cudaMemcpyDeviceToHost));
-                double dur = 0.0;   // the search's time: its slowest CTA's
+            long long records = 0, cells = 0, cellmin_bytes = 0, moves = 0, refresh_bytes = 0, select_bytes = 0;
+            for (int k = 0; k < ns_; k++) {
+                BatchItem &it = items[order[k]];
+                const stage_tabu_params &pk = ps[order[k]];
+                const int done = sd[k].t - it.t0;
+                double work = 0.0, dur = 0.0;
                 for (int r = 0; r < it.gang; r++) {
+                    const long long *q = &clk[k][(size_t)r * kPersistClocks];
+                    work += (double)(q[0] + q[1] + q[3] + q[5]);   // move, refresh, update, select
                     double d = 0.0;
-                    for (int q = 0; q < kPersistClocks; q++) {
-                        step[q] += clk[(size_t)r * kPersistClocks + q] * 1e-6;
-                        if (q < 7) d += clk[(size_t)r * kPersistClocks + q] * 1e-6;
+                    for (int q2 = 0; q2 < 7; q2++) {
+                        step[q2] += q[q2] * 1e-6;
+                        d += q[q2] * 1e-6;
                     }
                     dur = std::max(dur, d);
                 }
@@ -1096,21 +1074,40 @@ stage_status run_tabu_batch(stage_ctx *c, int n, const stage_inst *hs, const sta
                     longest = dur;
                     longest_i = order[k];
                 }
-                est += batch_search_us(it, ps[order[k]].iters, it.gang) * 1e-3 * it.gang;
+                est += batch_search_us(it, pk.iters, it.gang) * 1e-3 * it.gang;
+                if (done >= 1 && !sd[k].err) {
+                    const double fixed = kBatchFixedUs * it.gang;   // counted in the move and select
+                    it.in->batch_work_us = std::max(0.0, work * 1e-3 / done - fixed);
+                    it.in->batch_K = pk.K;
+                    it.in->batch_R = pk.R;
+                    it.in->batch_version = it.in->version;
+                }
+                const long long nrec = info[6 * (size_t)k + 1];
+                records += nrec;
+                cells += info[6 * (size_t)k + 5];
+                cellmin_bytes += nrec * 4 * (table_ldT(it.in->B) / 32);
+                moves += std::max(0, done);
+                refresh_bytes += (long long)std::max(0, done) * 20 * it.in->M;
+                select_bytes += (long long)std::max(0, done) * 12 * pk.K * it.nC;
             }
             for (int q = 0; q < P; q++)
                 for (int e = h_off[q]; e < h_off[q + 1]; e++) {
-                    const int k = h_sched[e].x, r = h_sched[e].y;
-                    const BatchItem &it = items[order[k]];
-                    std::vector<long long> clk(7);
-                    CK(cudaMemcpy(clk.data(),
-                                  static_cast<const char *>(it.in->mem_persist.p) +
-                                      persist_clock_offset(ps[order[k]].K, it.gang, it.in->M_pad) +
-                                      (size_t)r * kPersistClocks * sizeof(long long),
-                                  7 * sizeof(long long), cudaMemcpyDeviceToHost));
-                    for (int q2 = 0; q2 < 7; q2++) busy[q] += clk[q2] * 1e-6;
+                    const long long *cq = &clk[h_sched[e].x][(size_t)h_sched[e].y * kPersistClocks];
+                    for (int q2 = 0; q2 < 7; q2++) busy[q] += cq[q2] * 1e-6;
                 }
             std::lock_guard<std::recursive_mutex> g(c->mu);
+            c->stats["batch_records"].launches += records;
+            c->stats["batch_cells_read"].launches += cells;
+            // the method's bytes: the refreshes' 20 per mission, the updates' 32
+            // per record, its row of cell minima and 128 per cell piece, the
+            // selections' 12 per swap
+            c->stats["batch_bytes"].launches += refresh_bytes + records * 32 + cellmin_bytes + cells * 128 + select_bytes;
+            c->stats["batch_moves"].launches += moves;
+            c->stats["batch_searches"].launches += ns_;
+            c->stats["batch_ctas"].launches = P;
+            int gmax = 1;
+            for (int i : order) gmax = std::max(gmax, items[i].gang);
+            c->stats["batch_gang_max"].launches = gmax;
             double mx = 0.0, sum = 0.0;
             for (double b : busy) { mx = std::max(mx, b); sum += b; }
             c->stats["batch_cta_busy_max"].ms += mx;
