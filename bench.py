@@ -60,6 +60,8 @@ def parse_args():
     ap.add_argument("--full-pass-iters", type=int, default=200,
                     help="large: Tabu iterations of the full-pass reference run (0: skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-other-configs", action="store_true",
+                    help="large: skip the tiny, province and batched figures added to the line")
     ap.add_argument("--cpu-sample-missions", type=int, default=100_000)
     return ap.parse_args()
 
@@ -526,6 +528,15 @@ def run_ours(args):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(inst, args.cpu_sample_missions)
 
+    # the other configurations' headline figures, compactly, in the same run
+    # (tiny and province: time per Tabu iteration; batched: instances/s of the
+    # 512 searches in one persistent launch)
+    others = None
+    if rank == 0 and world == 1 and args.workload == "large" and not args.missions and not args.no_other_configs:
+        ctx.close()
+        torch.cuda.empty_cache()
+        others = other_configs(stage, torch, local)
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -554,12 +565,66 @@ def run_ours(args):
             "search_only": search,
             "clocks": clk,
             "best": {"cov": res.best_cov, "dist": res.best_dist, "iter": res.best_iter},
+            "other_configs": others,
         }
         print(json.dumps(line))
     ctx.close()
     if dist:
         dist.destroy_process_group()
     return 0
+
+
+def other_configs(stage, torch, local):
+    """Tiny and province: CUDA-event time per Tabu iteration of the whole search
+    call on a loaded instance; batched: the 512 searches in one stage_tabu_batch
+    launch after one untimed call (wall time per call, the kernel's CUDA-event
+    time and method bytes).  Each part reports an error string instead of
+    failing the run."""
+    from paper_2001_05291_gb300 import synth
+    out = {}
+    for name, reps in (("tiny", 20), ("province", 5)):
+        try:
+            inst = synth.by_name(name)
+            with stage.Context(device=local) as c:
+                h = c.load_instance(inst.base_xy, inst.pick_xy, inst.drop_xy)
+                for _ in range(2):
+                    r = c.tabu_run(h, inst.K, inst.R, inst.iters, inst.tenure)
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(c.torch_stream)
+                for _ in range(reps):
+                    r = c.tabu_run(h, inst.K, inst.R, inst.iters, inst.tenure)
+                e1.record(c.torch_stream)
+                e1.synchronize()
+                ms = e0.elapsed_time(e1) / reps
+            out[name] = {"workload": f"{name}: B={inst.B}, M={inst.M}, K={inst.K}, R={inst.R} m, "
+                                     f"{inst.iters} iterations, tenure {inst.tenure}",
+                         "ms_per_search": ms, "us_per_iteration": 1000.0 * ms / max(1, r.n_moves),
+                         "best": {"cov": r.best_cov, "dist": r.best_dist}}
+        except Exception as e:   # reported, not fatal to the headline line
+            out[name] = {"error": f"{type(e).__name__}: {e}"}
+    try:
+        insts = synth.batched(n=512)
+        with stage.Context(device=local) as c:
+            hs = [c.load_instance(i.base_xy, i.pick_xy, i.drop_xy) for i in insts]
+            reqs = [dict(inst=h, K=i.K, R=i.R, iters=i.iters, tenure=i.tenure) for h, i in zip(hs, insts)]
+            c.tabu_batch(reqs)
+            torch.cuda.synchronize()
+            c.reset_stats()
+            t0 = time.perf_counter()
+            c.tabu_batch(reqs)
+            s = time.perf_counter() - t0
+            kms = c.kernel_stats("tabu_batch")[1]
+            nbytes = c.kernel_stats("batch_bytes")[0]
+        peak, _ = load_peaks()
+        out["batched"] = {"workload": "batched: seed 3, 512 instances, B log-uniform [50, 800], M log-uniform "
+                                      "[1e3, 2e5], K uniform [4, 32], R uniform [600, 1200] km, 300 Tabu "
+                                      "iterations, tenure 11; every search in one stage_tabu_batch launch",
+                          "inst_per_s": len(insts) / s, "s_per_call": s, "kernel_ms": kms,
+                          "hbm_frac": nbytes / (kms * 1e-3) / 1e9 / peak if kms > 0 else None}
+    except Exception as e:
+        out["batched"] = {"error": f"{type(e).__name__}: {e}"}
+    return out
 
 
 def kernel_code(text: str) -> str:
