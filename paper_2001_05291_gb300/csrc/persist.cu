@@ -70,7 +70,7 @@ constexpr int kBatchRec = 256;
 constexpr int kBlockMissions = 32;     // missions per ownership block (one warp chunk)
 constexpr int kRecCap = 256;           // records staged in shared memory per round of a single search's update
 constexpr int kUpdBatch = 8;           // listed records whose costs a warp loads at once
-constexpr int kUpdItem = 24;           // listed records of one cell per work item of a warp
+constexpr int kUpdItem = 16;           // listed records of one cell per work item of a warp
 constexpr int kMaxLd = 2048;           // longest table-copy row (its 64 cells fit the item scan)
 constexpr size_t kPerSmemLimit = 220 * 1024;
 constexpr int kMaxGrid = 256;          // CTAs of a search (the update's count prefix and sums: 8 per lane)
@@ -153,8 +153,10 @@ __device__ __forceinline__ bool wait_change(const unsigned *flag, unsigned seen,
 // every CTA is resident).  Arrivals count up without reset: barrier number g
 // (from 0) is passed once the count reaches G * (g + 1).  Thread 0 of each CTA adds its
 // arrival with release semantics (the CTA's writes, ordered before it by the
-// CTA barrier, become visible first) and polls the count with acquire loads,
-// at most `limit` times, then sets the timeout bit in *err and gives up.
+// CTA barrier, become visible first), a reduction that returns nothing, and
+// polls the count with acquire loads (the first poll sees its own arrival:
+// same thread, same address), at most `limit` times, then sets the timeout
+// bit in *err and gives up.
 // Returns false when this CTA gave up or another CTA has reported an error:
 // the caller then leaves the loop.  (The count wraps after 2^32 arrivals:
 // 9 million iterations of three barriers on 152 CTAs.)
@@ -163,21 +165,17 @@ __device__ __forceinline__ bool grid_sync(unsigned *bar, unsigned &gen, int G, l
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
-        int ok = 1;
+        int ok = 0;
         const unsigned target = (unsigned)G * (gen + 1u);
-        unsigned old;
-        asm volatile("atom.add.release.gpu.global.u32 %0, [%1], 1;" : "=r"(old) : "l"(bar) : "memory");
-        if (old + 1u != target) {
-            ok = 0;
-            for (long long k = 0; k < limit; k++) {
-                if ((int)(ld_acquire_u32(bar) - target) >= 0) {
-                    ok = 1;
-                    break;
-                }
-                if (k > 256) __nanosleep(32);
+        asm volatile("red.release.gpu.global.add.u32 [%0], 1;" : : "l"(bar) : "memory");
+        for (long long k = 0; k < limit; k++) {
+            if ((int)(ld_acquire_u32(bar) - target) >= 0) {
+                ok = 1;
+                break;
             }
-            if (!ok) atomicOr(err, kErrPipelineTimeout);
+            if (k > 256) __nanosleep(32);
         }
+        if (!ok) atomicOr(err, kErrPipelineTimeout);
         if (ok && *reinterpret_cast<volatile int *>(err) != 0) ok = 0;
         s_ok = ok;
     }
