@@ -1058,11 +1058,11 @@ cudaError_t persist_init()
 }
 
 // The arguments of one search on `grid` CTAs over its scratch (laid out as
-// persist_scratch_bytes counts it), with the scratch's sums, counters and
-// barrier cleared and the start placement's V0 and loss put in both buffers
-// (asynchronously, on s).
+// persist_scratch_bytes counts it); with `clear`, the scratch's sums, counters
+// and barrier are cleared and the start placement's V0 and loss put in both
+// buffers (asynchronously, on s; a batch does this with k_batch_prep).
 static cudaError_t persist_args(const TabuBuffers &w, const int32_t *cost, void *scratch, int grid,
-                                long long spin_limit, cudaStream_t s, PersistArgs &A)
+                                long long spin_limit, cudaStream_t s, PersistArgs &A, bool clear = true)
 {
     const size_t nA = 2 + 2 * (size_t)w.K;
     if (grid < 1 || grid > kMaxGrid || w.ldT > kMaxLd || (w.ldT & 31)) return cudaErrorInvalidValue;
@@ -1091,6 +1091,7 @@ static cudaError_t persist_args(const TabuBuffers &w, const int32_t *cost, void 
     p += per_align((size_t)A.region_cap * grid * 32, 256);
     A.cta_ns = reinterpret_cast<long long *>(p);
     A.spin_limit = spin_limit > 0 ? spin_limit : (1ll << 26);
+    if (!clear) return cudaSuccess;
     // clear the sums, counters and barrier, then put the start placement's
     // V0 and loss (the per-mission initialisation's) in both buffers (the
     // first move's update writes the other one again)
@@ -1122,9 +1123,33 @@ cudaError_t persist_args_host(const TabuBuffers &w, const int32_t *cost, void *s
                               long long spin_limit, cudaStream_t s, void *out)
 {
     PersistArgs A;
-    cudaError_t e = persist_args(w, cost, scratch, gang, spin_limit, s, A);
+    cudaError_t e = persist_args(w, cost, scratch, gang, spin_limit, s, A, false);
     if (e == cudaSuccess) *static_cast<PersistArgs *>(out) = A;
     return e;
+}
+
+// Block k readies search k of a batch: clears its sums, counters and barrier
+// (the scratch's head, as persist_args clears it) and puts its start
+// placement's V0 and loss in both buffers.
+__global__ void k_batch_prep(const PersistArgs *__restrict__ args)
+{
+    const PersistArgs &A = args[blockIdx.x];
+    const int K = A.w.K;
+    const size_t nA = 2 + 2 * (size_t)K;
+    const size_t words = (2 * per_align(2 * nA * 8, 256) + 256) / 8;
+    for (size_t q = threadIdx.x; q < words; q += blockDim.x) A.acc[q] = 0ull;
+    __syncthreads();
+    for (size_t q = threadIdx.x; q < 2 * nA; q += blockDim.x) {
+        const size_t k = q % nA;
+        A.acc[q] = k < 2 ? A.w.v0[k] : k < 2 + (size_t)K ? A.w.loss_c[k - 2] : A.w.loss_d[k - 2 - K];
+    }
+}
+
+cudaError_t launch_batch_prep(const void *d_args, int n, cudaStream_t s)
+{
+    if (n < 1) return cudaSuccess;
+    k_batch_prep<<<n, 256, 0, s>>>(static_cast<const PersistArgs *>(d_args));
+    return cudaGetLastError();
 }
 
 size_t persist_search_smem(int K, int B, int ldT) { return batch_smem(K, B, ldT); }

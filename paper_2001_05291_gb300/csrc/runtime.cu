@@ -271,37 +271,55 @@ stage_status check_placement(stage_ctx *c, Instance *in, const int32_t *open, in
     return STAGE_OK;
 }
 
-stage_status do_rank(stage_ctx *c, Instance *in, int K, int32_t *out_open, int64_t *out_rowsum)
+// The ranking (Alg. 1) queued on the context's stream: the row sums (kept
+// with the instance once computed, until an update), the K smallest, their
+// ids copied to out_open (host memory; pinned memory is filled when the stream
+// gets there, pageable memory before this returns) and, if asked, the sums.
+stage_status rank_queue(stage_ctx *c, Instance *in, int K, int32_t *out_open, int64_t *out_rowsum)
 {
     if (K < 1 || K > in->B || K > STAGE_MAX_K)
         return set_err(c, STAGE_ERR_INVALID_ARG, "K=%d outside [1, min(B=%d, %d)]", K, in->B, STAGE_MAX_K);
     if (K > in->n_avail)
         return set_err(c, STAGE_ERR_INVALID_ARG, "K=%d exceeds the %d available bases", K, in->n_avail);
-    size_t need = round_up((size_t)in->B * 8, 256) + round_up((size_t)K * 4, 256);
+    size_t need = round_up((size_t)K * 4, 256);
     stage_status s = ensure_scratch(c, in, need);
     if (s != STAGE_OK) return s;
-    auto *S = static_cast<unsigned long long *>(in->mem_scratch.p);
-    auto *d_open = reinterpret_cast<int32_t *>(static_cast<char *>(in->mem_scratch.p) +
-                                               round_up((size_t)in->B * 8, 256));
-    if (in->rowsum_ok) {
-        S = static_cast<unsigned long long *>(in->mem_rowsum.p);   // built with the table
-    } else {
+    auto *d_open = static_cast<int32_t *>(in->mem_scratch.p);
+    if (!in->rowsum_ok) {
+        if (!in->mem_rowsum.p || in->mem_rowsum.bytes < (size_t)in->B * 8) {
+            dev_free(c, in->mem_rowsum);
+            s = dev_alloc(c, (size_t)in->B * 8, in->mem_rowsum);
+            if (s != STAGE_OK) return s;
+        }
+        auto *S = static_cast<unsigned long long *>(in->mem_rowsum.p);
         CK(cudaMemsetAsync(S, 0, (size_t)in->B * 8, c->stream));
         CK(timed(c, "rowsum", 1, [&] { return launch_rowsum(in->cost, in->B, in->M, in->M_pad, S, c->stream); }));
+        in->rowsum_ok = true;
     }
+    const auto *S = static_cast<const unsigned long long *>(in->mem_rowsum.p);
     CK(timed(c, "topk", 1, [&] { return launch_topk(S, in->avail, in->B, K, d_open, c->stream); }));
     CK(cudaMemcpyAsync(out_open, d_open, (size_t)K * 4, cudaMemcpyDeviceToHost, c->stream));
     if (out_rowsum)
         CK(cudaMemcpyAsync(out_rowsum, S, (size_t)in->B * 8, cudaMemcpyDeviceToHost, c->stream));
+    return STAGE_OK;
+}
+
+stage_status do_rank(stage_ctx *c, Instance *in, int K, int32_t *out_open, int64_t *out_rowsum)
+{
+    stage_status s = rank_queue(c, in, K, out_open, out_rowsum);
+    if (s != STAGE_OK) return s;
     CK(cudaStreamSynchronize(c->stream));
     return STAGE_OK;
 }
 
 // Set up the workspace for placement `open` (host ids), zero the accumulators,
 // and run the per-mission initialisation.  Returns the number of candidates.
+// sync = false: return without waiting for the copies and kernels it queued
+// (its host arrays are pageable, and a copy from pageable host memory is
+// staged before cudaMemcpyAsync returns, so they may go out of scope).
 stage_status setup_search(stage_ctx *c, Instance *in, const int32_t *open, int K, int R,
                           int traj_cap, int tenure, int accept_worsening, int t0,
-                          const int32_t *expiry_in, int *out_nC)
+                          const int32_t *expiry_in, int *out_nC, bool sync)
 {
     stage_status s = ensure_ws(c, in, K, traj_cap);
     if (s != STAGE_OK) return s;
@@ -336,8 +354,7 @@ stage_status setup_search(stage_ctx *c, Instance *in, const int32_t *open, int K
     CK(cudaMemsetAsync(tb.extra_c, 0, (size_t)K * in->B * 4, c->stream));
     CK(cudaMemsetAsync(tb.extra_d, 0, (size_t)K * in->B * 8, c->stream));
     CK(timed(c, "init", 1, [&] { return launch_init(tb, in->cost, c->stream); }));
-    // the host copies above read stack vectors: finish them before returning
-    CK(cudaStreamSynchronize(c->stream));
+    if (sync) CK(cudaStreamSynchronize(c->stream));
     *out_nC = nC;
     return STAGE_OK;
 }
@@ -531,8 +548,11 @@ std::vector<int32_t> spatial_order(const std::vector<int2> &xy, int ld)
 
 // The start of one Tabu search: the parameters checked, the start placement
 // (given, resumed or ranked), the workspace set up and initialised for it,
-// the resumed best so far restored (t0 and nC out).
-stage_status tabu_prepare(stage_ctx *c, Instance *in, const stage_tabu_params *p, int *out_t0, int *out_nC)
+// the resumed best so far restored (t0 and nC out).  ranked (nullable): the
+// ranking's start placement, already computed; sync = false: return with the
+// set-up still queued on the stream (setup_search).
+stage_status tabu_prepare(stage_ctx *c, Instance *in, const stage_tabu_params *p, int *out_t0, int *out_nC,
+                          const int32_t *ranked = nullptr, bool sync = true)
 {
     if (!p) return set_err(c, STAGE_ERR_INVALID_ARG, "params is NULL");
     const int K = p->K;
@@ -558,6 +578,8 @@ stage_status tabu_prepare(stage_ctx *c, Instance *in, const stage_tabu_params *p
         stage_status s = check_placement(c, in, p->start_open, K);
         if (s != STAGE_OK) return s;
         std::copy(p->start_open, p->start_open + K, start.begin());
+    } else if (ranked) {
+        std::copy(ranked, ranked + K, start.begin());
     } else {
         stage_status s = do_rank(c, in, K, start.data(), nullptr);
         if (s != STAGE_OK) return s;
@@ -575,7 +597,8 @@ stage_status tabu_prepare(stage_ctx *c, Instance *in, const stage_tabu_params *p
     }
     int nC = 0;
     stage_status s = setup_search(c, in, start.data(), K, p->R, iters, p->tenure,
-                                  p->accept_worsening ? 1 : 0, t0, rs ? rs->tabu_expiry : nullptr, &nC);
+                                  p->accept_worsening ? 1 : 0, t0, rs ? rs->tabu_expiry : nullptr, &nC,
+                                  sync || rs);
     if (s != STAGE_OK) return s;
     TabuBuffers &tb = in->tb;
     if (rs) {
@@ -593,6 +616,10 @@ stage_status tabu_prepare(stage_ctx *c, Instance *in, const stage_tabu_params *p
     *out_nC = nC;
     return STAGE_OK;
 }
+
+stage_status tabu_result(stage_ctx *c, const stage_tabu_params *p, bool count_records, const TabuDevState &st,
+                         const int32_t *fin_in, const int32_t *best_in, const int32_t *expiry_in, int B,
+                         stage_tabu_result *res);
 
 // The end of one Tabu search: the device's error word checked, the
 // trajectory and the result (best and final placements, end state) read back;
@@ -626,6 +653,20 @@ stage_status tabu_finish(stage_ctx *c, Instance *in, const stage_tabu_params *p,
     CK(cudaMemcpyAsync(best.data(), tb.best_open, (size_t)K * 4, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaMemcpyAsync(expiry.data(), tb.expiry, (size_t)in->B * 4, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
+    const int n = std::min(st.n_moves, iters);
+    if (traj && n > 0 && !st.err)
+        CK(cudaMemcpy(traj, tb.traj, (size_t)n * sizeof(stage_move), cudaMemcpyDeviceToHost));
+    return tabu_result(c, p, count_records, st, fin.data(), best.data(), expiry.data(), in->B, res);
+}
+
+// A search's result from host copies of its end state, placement, best
+// placement and expiries (the trajectory already copied): the device's error
+// word checked, the result and end state filled in.
+stage_status tabu_result(stage_ctx *c, const stage_tabu_params *p, bool count_records, const TabuDevState &st,
+                         const int32_t *fin_in, const int32_t *best_in, const int32_t *expiry_in, int B,
+                         stage_tabu_result *res)
+{
+    const int K = p->K;
     if (st.err & kErrPipelineTimeout)
         return set_err(c, STAGE_ERR_TIMEOUT, "a device-side wait gave up after %lld polls at iteration %d",
                        (long long)c->spin_limit, st.t);
@@ -636,10 +677,8 @@ stage_status tabu_finish(stage_ctx *c, Instance *in, const stage_tabu_params *p,
         std::lock_guard<std::recursive_mutex> g(c->mu);
         c->stats["swap_delta_records"].launches += st.chg_total + st.chg_n;
     }
-    const int n = std::min(st.n_moves, iters);
-    if (traj && n > 0)
-        CK(cudaMemcpy(traj, tb.traj, (size_t)n * sizeof(stage_move), cudaMemcpyDeviceToHost));
     if (res) {
+        std::vector<int32_t> fin(fin_in, fin_in + K), best(best_in, best_in + K);
         res->n_moves = st.n_moves;
         res->best_iter = st.best_iter;
         res->best_cov = st.best_cov;
@@ -654,7 +693,7 @@ stage_status tabu_finish(stage_ctx *c, Instance *in, const stage_tabu_params *p,
             es->best_dist = st.best_dist;
             if (es->open) std::copy(fin.begin(), fin.end(), es->open);
             if (es->best_open) std::copy(best.begin(), best.end(), es->best_open);
-            if (es->tabu_expiry) std::copy(expiry.begin(), expiry.end(), es->tabu_expiry);
+            if (es->tabu_expiry) std::copy(expiry_in, expiry_in + B, es->tabu_expiry);
         }
         std::sort(fin.begin(), fin.end());
         std::sort(best.begin(), best.end());
@@ -874,6 +913,23 @@ double batch_search_us(const BatchItem &it, int iters, int g)
 
 }  // namespace
 
+// Pinned host staging of a batch call's copies, at least `bytes` (kept with
+// the context; every copy into it has completed when a call returns).
+static char *batch_staging(stage_ctx *c, size_t bytes)
+{
+    if (c->batch_pinned_bytes < bytes) {
+        if (c->batch_pinned) cudaFreeHost(c->batch_pinned);
+        c->batch_pinned = nullptr;
+        c->batch_pinned_bytes = 0;
+        if (cudaMallocHost(&c->batch_pinned, bytes) != cudaSuccess) {
+            c->batch_pinned = nullptr;
+            return nullptr;
+        }
+        c->batch_pinned_bytes = bytes;
+    }
+    return static_cast<char *>(c->batch_pinned);
+}
+
 stage_status run_tabu_batch(stage_ctx *c, int n, const stage_inst *hs, const stage_tabu_params *ps,
                             stage_tabu_result *res, stage_move *const *trajs)
 {
@@ -893,14 +949,36 @@ stage_status run_tabu_batch(stage_ctx *c, int n, const stage_inst *hs, const sta
             if (items[k].in == items[i].in)
                 return set_err(c, STAGE_ERR_INVALID_ARG, "requests %d and %d name the same instance", k, i);
     }
-    // the start of every search; the full pass that starts the incremental form
+    // 1. the ranking of every search that starts from it, queued together
+    //    (its start placement to pinned staging), one wait
+    std::vector<size_t> at_rank(n), at_v0(n);
+    size_t bytes = 0;
+    for (int i = 0; i < n; i++) {
+        at_rank[i] = bytes;
+        bytes += round_up((size_t)std::max(1, ps[i].K) * 4, 16);
+        at_v0[i] = bytes;
+        bytes += 16;
+    }
+    char *stage = batch_staging(c, bytes);
+    if (!stage) return set_err(c, STAGE_ERR_NO_MEMORY, "no pinned host memory for the batch (%zu bytes)", bytes);
+    for (int i = 0; i < n; i++)
+        if (!ps[i].resume && !ps[i].start_open) {
+            stage_status s = rank_queue(c, items[i].in, ps[i].K, reinterpret_cast<int32_t *>(stage + at_rank[i]),
+                                        nullptr);
+            if (s != STAGE_OK) return s;
+        }
+    CK(cudaStreamSynchronize(c->stream));
+    // 2. the start of every search, queued (no wait per search); the full pass
+    //    that starts the incremental form; the start placements' covered counts
+    //    (the estimate of an unmeasured search), one wait
     size_t smem = 0;
-    double total_us = 0.0;
     for (int i = 0; i < n; i++) {
         BatchItem &it = items[i];
         Instance *in = it.in;
         const stage_tabu_params *p = &ps[i];
-        stage_status s = tabu_prepare(c, in, p, &it.t0, &it.nC);
+        const bool ranked = !p->resume && !p->start_open;
+        stage_status s = tabu_prepare(c, in, p, &it.t0, &it.nC,
+                                      ranked ? reinterpret_cast<const int32_t *>(stage + at_rank[i]) : nullptr, false);
         if (s != STAGE_OK) return s;
         const int K = p->K, ldT = table_ldT(in->B);
         it.fused = it.nC > 0 && p->iters > 0 && persist_shape_ok(K, in->B, ldT) &&
@@ -912,18 +990,16 @@ stage_status run_tabu_batch(stage_ctx *c, int n, const stage_inst *hs, const sta
             continue;
         }
         CK(timed(c, "swap_eval", 1, [&] { return launch_swap_eval(it.tw, in->cost, it.nC, 0, c->stream); }));
+        CK(cudaMemcpyAsync(stage + at_v0[i], it.tw.v0, 16, cudaMemcpyDeviceToHost, c->stream));
         smem = std::max(smem, persist_search_smem(K, in->B, ldT));
     }
-    // the start placements' covered counts (the estimate of an unmeasured search)
-    std::vector<unsigned long long> v0(2 * (size_t)n, 0ull);
-    for (int i = 0; i < n; i++)
-        if (items[i].fused)
-            CK(cudaMemcpyAsync(&v0[2 * (size_t)i], items[i].tw.v0, 16, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
+    double total_us = 0.0;
     for (int i = 0; i < n; i++) {
         BatchItem &it = items[i];
         if (!it.fused) continue;
-        const double cov = it.in->M > 0 ? std::min(1.0, (double)v0[2 * (size_t)i] / it.in->M) : 0.0;
+        const unsigned long long covered = *reinterpret_cast<const unsigned long long *>(stage + at_v0[i]);
+        const double cov = it.in->M > 0 ? std::min(1.0, (double)covered / it.in->M) : 0.0;
         it.us_per_iter = batch_iter_us(it.in, ps[i].K, ps[i].R, it.nC, cov);
         total_us += batch_search_us(it, ps[i].iters, 1);
     }
@@ -935,9 +1011,11 @@ stage_status run_tabu_batch(stage_ctx *c, int n, const stage_inst *hs, const sta
             if (P < 1) items[i].fused = false;
             else order.push_back(i);
         }
+    stage_status first = STAGE_OK;
     if (!order.empty()) {
-        // gang sizes: the smallest power of two that brings a search under half
-        // of the ideal per-CTA time (at most the search's 32-mission chunks)
+        // 3. gang sizes: the smallest power of two that brings a search under
+        //    half of the ideal per-CTA time (at most the search's 32-mission
+        //    chunks)
         const double ideal = total_us / P;
         for (int i : order) {
             BatchItem &it = items[i];
@@ -954,10 +1032,11 @@ stage_status run_tabu_batch(stage_ctx *c, int n, const stage_inst *hs, const sta
             const double wb = batch_search_us(items[b], ps[b].iters, items[b].gang) * items[b].gang;
             return wa != wb ? wa > wb : a < b;
         });
+        const int ns = (int)order.size();
         std::vector<double> fin(P, 0.0);
         std::vector<std::vector<int2>> lists(P);
         std::vector<int> idx(P);
-        for (int k = 0; k < (int)order.size(); k++) {
+        for (int k = 0; k < ns; k++) {
             const int i = order[k];
             const int g = items[i].gang;
             for (int q = 0; q < P; q++) idx[q] = q;
@@ -974,8 +1053,8 @@ stage_status run_tabu_batch(stage_ctx *c, int n, const stage_inst *hs, const sta
         }
         // per search its scratch and arguments; the schedule
         const size_t ab = persist_args_bytes();
-        std::vector<unsigned char> h_args(ab * order.size());
-        for (int k = 0; k < (int)order.size(); k++) {
+        std::vector<unsigned char> h_args(ab * ns);
+        for (int k = 0; k < ns; k++) {
             BatchItem &it = items[order[k]];
             Instance *in = it.in;
             const size_t need = persist_scratch_bytes(ps[order[k]].K, it.gang, in->M_pad);
@@ -996,11 +1075,12 @@ stage_status run_tabu_batch(stage_ctx *c, int n, const stage_inst *hs, const sta
         h_off[P] = (int)h_sched.size();
         const size_t off_args = 0, off_sched = round_up(h_args.size(), 256),
                      off_off = off_sched + round_up(h_sched.size() * sizeof(int2), 256),
-                     bytes = off_off + round_up(h_off.size() * sizeof(int), 256);
+                     dbytes = off_off + round_up(h_off.size() * sizeof(int), 256);
         DevBuf buf;
-        stage_status s = dev_alloc(c, bytes, buf);
+        stage_status s = dev_alloc(c, dbytes, buf);
         if (s != STAGE_OK) return s;
         char *d = static_cast<char *>(buf.p);
+        // (copies from pageable host memory are staged before they return)
         cudaError_t e = cudaMemcpyAsync(d + off_args, h_args.data(), h_args.size(), cudaMemcpyHostToDevice, c->stream);
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(d + off_sched, h_sched.data(), h_sched.size() * sizeof(int2), cudaMemcpyHostToDevice,
@@ -1008,131 +1088,160 @@ stage_status run_tabu_batch(stage_ctx *c, int n, const stage_inst *hs, const sta
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(d + off_off, h_off.data(), h_off.size() * sizeof(int), cudaMemcpyHostToDevice,
                                 c->stream);
-        // the launch, timed by CUDA events on its stream whether or not the
-        // context profiles (one launch per call)
+        // every search's scratch readied, then the launch, timed by CUDA events
+        // on its stream whether or not the context profiles (one launch per call)
+        if (e == cudaSuccess) e = launch_batch_prep(d + off_args, ns, c->stream);
         cudaEvent_t ev0 = get_event(c), ev1 = get_event(c);
         if (e == cudaSuccess) e = cudaEventRecord(ev0, c->stream);
         if (e == cudaSuccess)
             e = launch_tabu_batch(d + off_args, reinterpret_cast<const int2 *>(d + off_sched),
                                   reinterpret_cast<const int *>(d + off_off), P, smem, c->stream);
         if (e == cudaSuccess) e = cudaEventRecord(ev1, c->stream);
-        // the host arrays are read by the copies: wait for them
+        // 4. every search's clocks, end state, counters, placements, expiries
+        //    and trajectory to pinned staging, one wait
+        std::vector<size_t> at_clk(ns), at_st(ns), at_info(ns), at_open(ns), at_best(ns), at_exp(ns), at_traj(ns);
+        size_t rb = 0;
+        for (int k = 0; k < ns; k++) {
+            const BatchItem &it = items[order[k]];
+            const int K = ps[order[k]].K;
+            at_clk[k] = rb; rb += round_up((size_t)it.gang * kPersistClocks * 8, 16);
+            at_st[k] = rb; rb += round_up(sizeof(TabuDevState), 16);
+            at_info[k] = rb; rb += 48;
+            at_open[k] = rb; rb += round_up((size_t)K * 4, 16);
+            at_best[k] = rb; rb += round_up((size_t)K * 4, 16);
+            at_exp[k] = rb; rb += round_up((size_t)it.in->B * 4, 16);
+            at_traj[k] = rb; rb += round_up((size_t)ps[order[k]].iters * sizeof(stage_move), 16);
+        }
+        if (e == cudaSuccess) {
+            stage = batch_staging(c, rb);   // the earlier staging is consumed
+            if (!stage) e = cudaErrorMemoryAllocation;
+        }
+        for (int k = 0; k < ns && e == cudaSuccess; k++) {
+            const BatchItem &it = items[order[k]];
+            const int K = ps[order[k]].K;
+            const char *base = static_cast<const char *>(it.in->mem_persist.p);
+            const TabuBuffers &tb = it.in->tb;
+            auto cp = [&](size_t at, const void *src, size_t nb) {
+                if (e == cudaSuccess) e = cudaMemcpyAsync(stage + at, src, nb, cudaMemcpyDeviceToHost, c->stream);
+            };
+            cp(at_clk[k], base + persist_clock_offset(K, it.gang, it.in->M_pad),
+               (size_t)it.gang * kPersistClocks * 8);
+            cp(at_st[k], tb.st, sizeof(TabuDevState));
+            cp(at_info[k], base + persist_info_offset(K), 48);
+            cp(at_open[k], tb.open, (size_t)K * 4);
+            cp(at_best[k], tb.best_open, (size_t)K * 4);
+            cp(at_exp[k], tb.expiry, (size_t)it.in->B * 4);
+            if (trajs && trajs[order[k]] && ps[order[k]].iters > 0)
+                cp(at_traj[k], tb.traj, (size_t)ps[order[k]].iters * sizeof(stage_move));
+        }
         if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
         float kms = 0.f;
         if (e == cudaSuccess) e = cudaEventElapsedTime(&kms, ev0, ev1);
         c->event_pool.push_back(ev0);
         c->event_pool.push_back(ev1);
+        if (e != cudaSuccess) cudaStreamSynchronize(c->stream);   // nothing of this call left in flight
         dev_free(c, buf);
         CK(e);
-        {
-            std::lock_guard<std::recursive_mutex> g(c->mu);
-            KernelStat &ks = c->stats["tabu_batch"];
-            ks.launches += 1;
-            ks.ms += kms;
+        c->stats["batch_host_launch"].ms += host_ms();
+        // Each search's measured work (its CTAs' time outside the waits, per
+        // iteration) sizes its gang in the next batch; the batch's statistics:
+        // every CTA's busy time (the sum of its searches' steps), each step's
+        // total, the longest search, the records and cell pieces the updates
+        // read; then each search's result.
+        auto clk_of = [&](int k) { return reinterpret_cast<const long long *>(stage + at_clk[k]); };
+        std::vector<double> busy(P, 0.0), step(7, 0.0);
+        double est = 0.0, longest = 0.0;
+        int longest_i = -1;
+        long long records = 0, cells = 0, cellmin_bytes = 0, moves = 0, refresh_bytes = 0, select_bytes = 0;
+        for (int k = 0; k < ns; k++) {
+            BatchItem &it = items[order[k]];
+            const stage_tabu_params &pk = ps[order[k]];
+            const TabuDevState &sd = *reinterpret_cast<const TabuDevState *>(stage + at_st[k]);
+            const long long *info = reinterpret_cast<const long long *>(stage + at_info[k]);
+            const int done = sd.t - it.t0;
+            double work = 0.0, dur = 0.0;
+            for (int r = 0; r < it.gang; r++) {
+                const long long *q = clk_of(k) + (size_t)r * kPersistClocks;
+                work += (double)(q[0] + q[1] + q[3] + q[5]);   // move, refresh, update, select
+                double dd = 0.0;
+                for (int q2 = 0; q2 < 7; q2++) {
+                    step[q2] += q[q2] * 1e-6;
+                    dd += q[q2] * 1e-6;
+                }
+                dur = std::max(dur, dd);
+            }
+            if (dur > longest) {
+                longest = dur;
+                longest_i = order[k];
+            }
+            est += batch_search_us(it, pk.iters, it.gang) * 1e-3 * it.gang;
+            if (done >= 1 && !sd.err) {
+                const double fixed = kBatchFixedUs * it.gang;   // counted in the move and select
+                it.in->batch_work_us = std::max(0.0, work * 1e-3 / done - fixed);
+                it.in->batch_K = pk.K;
+                it.in->batch_R = pk.R;
+                it.in->batch_version = it.in->version;
+            }
+            records += info[1];
+            cells += info[5];
+            cellmin_bytes += info[1] * 4 * (table_ldT(it.in->B) / 32);
+            moves += std::max(0, done);
+            refresh_bytes += (long long)std::max(0, done) * 20 * it.in->M;
+            select_bytes += (long long)std::max(0, done) * 12 * pk.K * it.nC;
+            // the result
+            const int i = order[k];
+            stage_move *tr = trajs ? trajs[i] : nullptr;
+            const int nm = std::min(sd.n_moves, pk.iters);
+            if (tr && nm > 0 && !sd.err) std::memcpy(tr, stage + at_traj[k], (size_t)nm * sizeof(stage_move));
+            s = tabu_result(c, &pk, false, sd, reinterpret_cast<const int32_t *>(stage + at_open[k]),
+                            reinterpret_cast<const int32_t *>(stage + at_best[k]),
+                            reinterpret_cast<const int32_t *>(stage + at_exp[k]), it.in->B, &res[i]);
+            if (s != STAGE_OK && first == STAGE_OK) first = s;
         }
-        // Each search's own clocks, state and counters.  Its measured work (its
-        // CTAs' time outside the waits, per iteration) sizes its gang in the
-        // next batch; the batch's statistics: every CTA's busy time (the sum of
-        // its searches' steps), each step's total, the longest search, the
-        // records and cell pieces the updates read.
-        {
-            const int ns_ = (int)order.size();
-            std::vector<std::vector<long long>> clk(ns_);
-            std::vector<TabuDevState> sd(ns_);
-            std::vector<long long> info(6 * (size_t)ns_, 0);
-            for (int k = 0; k < ns_; k++) {
-                const BatchItem &it = items[order[k]];
-                const char *base = static_cast<const char *>(it.in->mem_persist.p);
-                clk[k].resize((size_t)it.gang * kPersistClocks);
-                CK(cudaMemcpyAsync(clk[k].data(), base + persist_clock_offset(ps[order[k]].K, it.gang, it.in->M_pad),
-                                   clk[k].size() * sizeof(long long), cudaMemcpyDeviceToHost, c->stream));
-                CK(cudaMemcpyAsync(&sd[k], it.tw.st, sizeof(TabuDevState), cudaMemcpyDeviceToHost, c->stream));
-                CK(cudaMemcpyAsync(&info[6 * (size_t)k], base + persist_info_offset(ps[order[k]].K),
-                                   6 * sizeof(long long), cudaMemcpyDeviceToHost, c->stream));
+        for (int q = 0; q < P; q++)
+            for (int ee = h_off[q]; ee < h_off[q + 1]; ee++) {
+                const long long *cq = clk_of(h_sched[ee].x) + (size_t)h_sched[ee].y * kPersistClocks;
+                for (int q2 = 0; q2 < 7; q2++) busy[q] += cq[q2] * 1e-6;
             }
-            CK(cudaStreamSynchronize(c->stream));
-            std::vector<double> busy(P, 0.0), step(7, 0.0);
-            double est = 0.0, longest = 0.0;
-            int longest_i = -1;
-            long long records = 0, cells = 0, cellmin_bytes = 0, moves = 0, refresh_bytes = 0, select_bytes = 0;
-            for (int k = 0; k < ns_; k++) {
-                BatchItem &it = items[order[k]];
-                const stage_tabu_params &pk = ps[order[k]];
-                const int done = sd[k].t - it.t0;
-                double work = 0.0, dur = 0.0;
-                for (int r = 0; r < it.gang; r++) {
-                    const long long *q = &clk[k][(size_t)r * kPersistClocks];
-                    work += (double)(q[0] + q[1] + q[3] + q[5]);   // move, refresh, update, select
-                    double d = 0.0;
-                    for (int q2 = 0; q2 < 7; q2++) {
-                        step[q2] += q[q2] * 1e-6;
-                        d += q[q2] * 1e-6;
-                    }
-                    dur = std::max(dur, d);
-                }
-                if (dur > longest) {
-                    longest = dur;
-                    longest_i = order[k];
-                }
-                est += batch_search_us(it, pk.iters, it.gang) * 1e-3 * it.gang;
-                if (done >= 1 && !sd[k].err) {
-                    const double fixed = kBatchFixedUs * it.gang;   // counted in the move and select
-                    it.in->batch_work_us = std::max(0.0, work * 1e-3 / done - fixed);
-                    it.in->batch_K = pk.K;
-                    it.in->batch_R = pk.R;
-                    it.in->batch_version = it.in->version;
-                }
-                const long long nrec = info[6 * (size_t)k + 1];
-                records += nrec;
-                cells += info[6 * (size_t)k + 5];
-                cellmin_bytes += nrec * 4 * (table_ldT(it.in->B) / 32);
-                moves += std::max(0, done);
-                refresh_bytes += (long long)std::max(0, done) * 20 * it.in->M;
-                select_bytes += (long long)std::max(0, done) * 12 * pk.K * it.nC;
-            }
-            for (int q = 0; q < P; q++)
-                for (int e = h_off[q]; e < h_off[q + 1]; e++) {
-                    const long long *cq = &clk[h_sched[e].x][(size_t)h_sched[e].y * kPersistClocks];
-                    for (int q2 = 0; q2 < 7; q2++) busy[q] += cq[q2] * 1e-6;
-                }
-            std::lock_guard<std::recursive_mutex> g(c->mu);
-            c->stats["batch_records"].launches += records;
-            c->stats["batch_cells_read"].launches += cells;
-            // the method's bytes: the refreshes' 20 per mission, the updates' 32
-            // per record, its row of cell minima and 128 per cell piece, the
-            // selections' 12 per swap
-            c->stats["batch_bytes"].launches += refresh_bytes + records * 32 + cellmin_bytes + cells * 128 + select_bytes;
-            c->stats["batch_moves"].launches += moves;
-            c->stats["batch_searches"].launches += ns_;
-            c->stats["batch_ctas"].launches = P;
-            int gmax = 1;
-            for (int i : order) gmax = std::max(gmax, items[i].gang);
-            c->stats["batch_gang_max"].launches = gmax;
-            double mx = 0.0, sum = 0.0;
-            for (double b : busy) { mx = std::max(mx, b); sum += b; }
-            c->stats["batch_cta_busy_max"].ms += mx;
-            c->stats["batch_cta_busy_mean"].ms += sum / P;
-            c->stats["batch_cta_estimate"].ms += est / P;
-            if (longest_i >= 0) {
-                // the longest search: its time, request index and gang; its estimate
-                KernelStat &ls = c->stats["batch_longest"];
-                ls.ms = longest;
-                ls.launches = longest_i;
-                KernelStat &le = c->stats["batch_longest_estimate"];
-                le.ms = batch_search_us(items[longest_i], ps[longest_i].iters, items[longest_i].gang) * 1e-3;
-                le.launches = items[longest_i].gang;
-            }
-            const char *nm[7] = {"batch_move", "batch_refresh", "batch_wait_refresh", "batch_update",
-                                 "batch_wait_update", "batch_select", "batch_wait_select"};
-            for (int q = 0; q < 7; q++) c->stats[nm[q]].ms += step[q];
+        std::lock_guard<std::recursive_mutex> g(c->mu);
+        KernelStat &ks = c->stats["tabu_batch"];
+        ks.launches += 1;
+        ks.ms += kms;
+        c->stats["batch_records"].launches += records;
+        c->stats["batch_cells_read"].launches += cells;
+        // the method's bytes: the refreshes' 20 per mission, the updates' 32
+        // per record, its row of cell minima and 128 per cell piece, the
+        // selections' 12 per swap
+        c->stats["batch_bytes"].launches += refresh_bytes + records * 32 + cellmin_bytes + cells * 128 + select_bytes;
+        c->stats["batch_moves"].launches += moves;
+        c->stats["batch_searches"].launches += ns;
+        c->stats["batch_ctas"].launches = P;
+        int gmax = 1;
+        for (int i : order) gmax = std::max(gmax, items[i].gang);
+        c->stats["batch_gang_max"].launches = gmax;
+        double mx = 0.0, sum = 0.0;
+        for (double b : busy) { mx = std::max(mx, b); sum += b; }
+        c->stats["batch_cta_busy_max"].ms += mx;
+        c->stats["batch_cta_busy_mean"].ms += sum / P;
+        c->stats["batch_cta_estimate"].ms += est / P;
+        if (longest_i >= 0) {
+            // the longest search: its time, request index and gang; its estimate
+            KernelStat &ls = c->stats["batch_longest"];
+            ls.ms = longest;
+            ls.launches = longest_i;
+            KernelStat &le = c->stats["batch_longest_estimate"];
+            le.ms = batch_search_us(items[longest_i], ps[longest_i].iters, items[longest_i].gang) * 1e-3;
+            le.launches = items[longest_i].gang;
         }
+        const char *nm[7] = {"batch_move", "batch_refresh", "batch_wait_refresh", "batch_update",
+                             "batch_wait_update", "batch_select", "batch_wait_select"};
+        for (int q = 0; q < 7; q++) c->stats[nm[q]].ms += step[q];
     }
-    // the results; the searches the launch did not take, alone
-    c->stats["batch_host_launch"].ms += host_ms();
-    stage_status first = STAGE_OK;
+    // the searches the launch did not take, alone
     for (int i = 0; i < n; i++) {
+        if (items[i].fused) continue;
         stage_status s;
-        if (items[i].fused || items[i].nC == 0 || ps[i].iters == 0)
+        if (items[i].nC == 0 || ps[i].iters == 0)
             s = tabu_finish(c, items[i].in, &ps[i], false, &res[i], trajs ? trajs[i] : nullptr, nullptr, nullptr,
                             nullptr, nullptr);
         else
@@ -1646,6 +1755,7 @@ stage_status stage_destroy(stage_ctx *c)
     }
     for (cudaEvent_t e : c->event_pool) cudaEventDestroy(e);
     if (c->pinned) cudaFreeHost(c->pinned);
+    if (c->batch_pinned) cudaFreeHost(c->batch_pinned);
     if (c->own_stream) cudaStreamDestroy(c->stream);
     delete c;
     return STAGE_OK;

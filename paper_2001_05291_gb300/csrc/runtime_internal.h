@@ -106,6 +106,8 @@ struct stage_ctx {
     std::unordered_map<std::string, stg_rt::KernelStat> stats;
     std::vector<cudaEvent_t> event_pool;
     void *pinned = nullptr;       // small pinned host buffer for early-stop polls
+    void *batch_pinned = nullptr; // pinned staging of stage_tabu_batch's copies, grown as needed
+    size_t batch_pinned_bytes = 0;
     std::atomic<stg_rt::Engine *> engine{nullptr};
 };
 
@@ -124,7 +126,8 @@ stage_status do_rank(stage_ctx *c, Instance *in, int K, int32_t *out_open, int64
 void engine_destroy(stage_ctx *c);
 stage_status autotune_shape(stage_ctx *c, Instance *in, const int32_t *open, int K, int R, int *out_seg);
 stage_status setup_search(stage_ctx *c, Instance *in, const int32_t *open, int K, int R, int traj_cap, int tenure,
-                          int accept_worsening, int t0, const int32_t *expiry_in, int *out_nC);
+                          int accept_worsening, int t0, const int32_t *expiry_in, int *out_nC, bool sync = true);
+stage_status rank_queue(stage_ctx *c, Instance *in, int K, int32_t *out_open, int64_t *out_rowsum);
 stage_status ensure_costT(stage_ctx *c, Instance *in);
 stage_status forced_moves(stage_ctx *c, Instance *in, int32_t *open, int K, int R, int t, int tenure,
                           int32_t *expiry, int *n_forced);

@@ -191,6 +191,9 @@ cudaError_t launch_tabu_persist(const TabuBuffers &w, const int32_t *cost, void 
 size_t persist_args_bytes();
 cudaError_t persist_args_host(const TabuBuffers &w, const int32_t *cost, void *scratch, int gang,
                               long long spin_limit, cudaStream_t s, void *out);
+// readies every search's scratch of a batch (clears, start V0 and loss):
+// one block per search, before the batch launch
+cudaError_t launch_batch_prep(const void *d_args, int n, cudaStream_t s);
 size_t persist_search_smem(int K, int B, int ldT);
 int persist_batch_grid(size_t smem);
 bool persist_shape_ok(int K, int B, int ldT);

@@ -131,6 +131,41 @@ def test_batched_workload_instances_in_one_batch(stage_mod):
         check_sampled_moves(cost, inst.K, inst.R, inst.tenure, start, r.moves, (50, 150, inst.iters - 1))
 
 
+def test_batched_workload_in_one_launch(stage_mod):
+    """All 512 searches of the batched workload in one stage_tabu_batch launch,
+    as bench.py times it (the second call, its gangs sized from the first's
+    measured costs): every result equals the batch engine's (itself equal to
+    each search alone), and six instances across the size range are checked
+    against the oracle as above."""
+    stage = stage_mod
+    insts = synth.batched()
+    sizes = synth.batched_sizes()
+    order = np.argsort([(B - K) * M for B, M, K, R in sizes])
+    pick = [int(order[-1]), int(order[0]), int(order[128]), int(order[256]), int(order[384]), int(order[500])]
+    with stage.Context(device=0, max_slots=512) as ctx:
+        hs = [ctx.load_instance(i.base_xy, i.pick_xy, i.drop_xy) for i in insts]
+        reqs = [dict(inst=h, K=i.K, R=i.R, iters=i.iters, tenure=i.tenure) for h, i in zip(hs, insts)]
+        first = ctx.tabu_batch(reqs)
+        res = ctx.tabu_batch(reqs)
+        assert ctx.kernel_stats("batch_gang_max")[0] > 1
+        eng = [t.wait() for t in ctx.batch_submit(reqs)]
+        starts = {k: ctx.rank_bases(hs[k], insts[k].K)[0] for k in pick}
+    for a, b, c in zip(res, first, eng):
+        assert a.moves == b.moves == c.moves
+        assert (a.best_cov, a.best_dist, a.best_iter) == (c.best_cov, c.best_dist, c.best_iter)
+        assert np.array_equal(np.sort(a.best_open), np.sort(c.best_open))
+    for k in pick:
+        inst, r, start = insts[k], res[k], starts[k]
+        assert r.n_moves == inst.iters
+        cost = oracle.cost_table(inst.base_xy, inst.pick_xy, inst.drop_xy, THREADS)
+        ref = oracle.tabu(cost, inst.K, inst.R, 12, inst.tenure, nthreads=THREADS)
+        assert [tuple(m) for m in r.moves[:12]] == [tuple(m) for m in ref.moves]
+        placements = replay(start, r.moves)
+        assert oracle.evaluate(cost, placements[inst.iters - 1], inst.R) == (r.moves[-1][4], r.moves[-1][5])
+        assert oracle.evaluate(cost, r.best_open, inst.R) == (r.best_cov, r.best_dist)
+        check_sampled_moves(cost, inst.K, inst.R, inst.tenure, start, r.moves, (100, inst.iters - 1))
+
+
 def test_local_search_large_workload(stage_mod):
     """Local search (Alg. 2) on the large workload: the first moves equal the
     oracle's on the full table; the complete run's sampled placements, final
