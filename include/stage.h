@@ -527,6 +527,18 @@ STAGE_API stage_status stage_best_two(stage_ctx *ctx, stage_inst inst, const int
  * expected outcome -- with no trap and no hang; the context stays usable. */
 STAGE_API stage_status stage_test_wait_timeout(stage_ctx *ctx);
 
+/* The placement stage_tabu_batch uses (host logic only; no device, no context):
+ * n searches, search k estimated at us[k] microseconds on gang[k] CTAs (1 <=
+ * gang[k] <= P), placed largest first (by gang x time) on the gang[k] CTAs
+ * that are free first, from the latest of their finish times.  out_off [P+1]
+ * receives each CTA's first entry in out_entries [2 * sum(gang)], entries
+ * (search k, its rank among the search's CTAs) in the order the CTA runs them
+ * -- one global order of the searches for every CTA.  *out_makespan_us
+ * receives the latest estimated finish.  Errors: STAGE_ERR_INVALID_ARG (NULL
+ * arrays, n < 0, P < 1, a gang outside [1, P]). */
+STAGE_API stage_status stage_test_batch_schedule(int32_t n, const double *us, const int32_t *gang, int32_t P,
+                                       int32_t *out_off, int32_t *out_entries, double *out_makespan_us);
+
 /* ------------------------------------------------------- allocation-free call */
 
 /* Every GPU that loads this library keeps a STAGE_NOALLOC_SCRATCH_MB MiB device

@@ -913,6 +913,42 @@ double batch_search_us(const BatchItem &it, int iters, int g)
 
 }  // namespace
 
+// Placement of a batch's searches on P CTAs: search k takes gang[k] CTAs for
+// work[k] (its estimated time on them); largest first by gang x time, each on
+// the gang of CTAs that are free first, starting at the latest of their finish
+// times.  lists[q]: CTA q's (search, rank) entries in placement order, so
+// every CTA runs the searches in one global order; returns the latest finish.
+static double batch_place(int n, const double *work, const int *gang, int P, std::vector<std::vector<int2>> &lists,
+                          std::vector<int> &order)
+{
+    order.resize(n);
+    for (int k = 0; k < n; k++) order[k] = k;
+    std::sort(order.begin(), order.end(), [&](int a, int b) {
+        const double wa = work[a] * gang[a], wb = work[b] * gang[b];
+        return wa != wb ? wa > wb : a < b;
+    });
+    std::vector<double> fin(P, 0.0);
+    lists.assign(P, {});
+    std::vector<int> idx(P);
+    double makespan = 0.0;
+    for (int pos = 0; pos < n; pos++) {
+        const int k = order[pos], g = gang[k];
+        for (int q = 0; q < P; q++) idx[q] = q;
+        std::partial_sort(idx.begin(), idx.begin() + g, idx.end(), [&](int a, int b) {
+            return fin[a] != fin[b] ? fin[a] < fin[b] : a < b;
+        });
+        double start = 0.0;
+        for (int r = 0; r < g; r++) start = std::max(start, fin[idx[r]]);
+        const double end = start + work[k];
+        makespan = std::max(makespan, end);
+        for (int r = 0; r < g; r++) {
+            fin[idx[r]] = end;
+            lists[idx[r]].push_back(make_int2(pos, r));   // pos: the search's place in the placement order
+        }
+    }
+    return makespan;
+}
+
 // Pinned host staging of a batch call's copies, at least `bytes` (kept with
 // the context; every copy into it has completed when a call returns).
 static char *batch_staging(stage_ctx *c, size_t bytes)
@@ -1024,32 +1060,21 @@ stage_status run_tabu_batch(stage_ctx *c, int n, const stage_inst *hs, const sta
             while (g * 2 <= gmax && batch_search_us(it, ps[i].iters, g) > 0.5 * ideal) g *= 2;
             it.gang = g;
         }
-        // placement, largest first: each search on the gang of CTAs that are
-        // free first, from the latest of their finish times; every CTA's
-        // entries are in placement order (one global order)
-        std::sort(order.begin(), order.end(), [&](int a, int b) {
-            const double wa = batch_search_us(items[a], ps[a].iters, items[a].gang) * items[a].gang;
-            const double wb = batch_search_us(items[b], ps[b].iters, items[b].gang) * items[b].gang;
-            return wa != wb ? wa > wb : a < b;
-        });
+        // placement (batch_place); `order` becomes the placement order, which
+        // is also the order of the searches' arguments on the device
         const int ns = (int)order.size();
-        std::vector<double> fin(P, 0.0);
-        std::vector<std::vector<int2>> lists(P);
-        std::vector<int> idx(P);
+        std::vector<double> work(ns);
+        std::vector<int> gangs(ns), place;
         for (int k = 0; k < ns; k++) {
-            const int i = order[k];
-            const int g = items[i].gang;
-            for (int q = 0; q < P; q++) idx[q] = q;
-            std::partial_sort(idx.begin(), idx.begin() + g, idx.end(), [&](int a, int b) {
-                return fin[a] != fin[b] ? fin[a] < fin[b] : a < b;
-            });
-            double start = 0.0;
-            for (int r = 0; r < g; r++) start = std::max(start, fin[idx[r]]);
-            const double end = start + batch_search_us(items[i], ps[i].iters, g);
-            for (int r = 0; r < g; r++) {
-                fin[idx[r]] = end;
-                lists[idx[r]].push_back(make_int2(k, r));   // k: the search's place in the args array
-            }
+            work[k] = batch_search_us(items[order[k]], ps[order[k]].iters, items[order[k]].gang);
+            gangs[k] = items[order[k]].gang;
+        }
+        std::vector<std::vector<int2>> lists;
+        batch_place(ns, work.data(), gangs.data(), P, lists, place);
+        {
+            std::vector<int> placed(ns);
+            for (int pos = 0; pos < ns; pos++) placed[pos] = order[place[pos]];
+            order = placed;
         }
         // per search its scratch and arguments; the schedule
         const size_t ab = persist_args_bytes();
@@ -2237,6 +2262,33 @@ stage_status stage_read_table(stage_ctx *c, stage_inst h, int32_t b0, int32_t nb
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     dev_free(c, win);
     if (e != cudaSuccess) return set_err(c, STAGE_ERR_CUDA, "reading the table failed: %s", cudaGetErrorString(e));
+    return STAGE_OK;
+}
+
+stage_status stage_test_batch_schedule(int32_t n, const double *us, const int32_t *gang, int32_t P,
+                                       int32_t *out_off, int32_t *out_entries, double *out_makespan_us)
+{
+    if (n < 0 || P < 1 || (n > 0 && (!us || !gang || !out_entries)) || !out_off) return STAGE_ERR_INVALID_ARG;
+    std::vector<int> g(n);
+    for (int k = 0; k < n; k++) {
+        if (gang[k] < 1 || gang[k] > P) return STAGE_ERR_INVALID_ARG;
+        g[k] = gang[k];
+    }
+    std::vector<std::vector<int2>> lists;
+    std::vector<int> order;
+    const double mk = n > 0 ? batch_place(n, us, g.data(), P, lists, order) : 0.0;
+    if (n == 0) lists.assign(P, {});
+    int at = 0;
+    for (int q = 0; q < P; q++) {
+        out_off[q] = at;
+        for (const int2 &e : lists[q]) {
+            out_entries[2 * at] = order[e.x];   // the caller's search index
+            out_entries[2 * at + 1] = e.y;
+            at++;
+        }
+    }
+    out_off[P] = at;
+    if (out_makespan_us) *out_makespan_us = mk;
     return STAGE_OK;
 }
 

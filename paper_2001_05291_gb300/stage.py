@@ -164,6 +164,7 @@ def lib():
             "stage_batch_submit": ([p, C.POINTER(StageRequest), i32, C.POINTER(C.c_uint64)], st),
             "stage_poll": ([p, C.c_uint64, C.POINTER(StageResult), i32], st),
             "stage_test_wait_timeout": ([p], st),
+            "stage_test_batch_schedule": ([i32, p, p, i32, p, p, C.POINTER(C.c_double)], st),
             "stage_evaluate_swaps_noalloc": ([p, i32, i32, i32, p, p, i32, i32, p, p, p, C.c_char_p,
                                               C.c_size_t], st),
         }
@@ -698,6 +699,27 @@ def evaluate_swaps_noalloc(cost, M: int, open_, R: int, out_cov, out_dist, base_
 
 
 stage_evaluate_swaps_noalloc = evaluate_swaps_noalloc
+
+
+def batch_schedule(us, gang, P: int):
+    """stage_test_batch_schedule (host logic, no device): the placement a
+    stage_tabu_batch call uses for searches of estimated times `us` on gangs of
+    `gang` CTAs over P CTAs.  Returns (lists, makespan_us): lists[q] = CTA q's
+    (search, rank) entries in the order it runs them."""
+    us = np.ascontiguousarray(us, dtype=np.float64)
+    g = np.ascontiguousarray(gang, dtype=np.int32)
+    n = int(us.size)
+    if g.size != n:
+        raise ValueError("us and gang differ in length")
+    off = np.empty(P + 1, dtype=np.int32)
+    ent = np.empty(max(1, 2 * int(g.sum()) if n else 1), dtype=np.int32)
+    mk = C.c_double()
+    rc = lib().stage_test_batch_schedule(n, _ptr(us) if n else None, _ptr(g) if n else None, P, _ptr(off),
+                                         _ptr(ent), C.byref(mk))
+    if rc != STAGE_OK:
+        raise StageError(rc, "stage_test_batch_schedule refused its arguments")
+    lists = [[(int(ent[2 * e]), int(ent[2 * e + 1])) for e in range(off[q], off[q + 1])] for q in range(P)]
+    return lists, mk.value
 
 
 def _is_cuda_tensor(x) -> bool:
