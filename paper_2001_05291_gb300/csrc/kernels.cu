@@ -36,19 +36,28 @@ int swap_segment_for(int M_pad, int nC, int K);
 // root of the exact squared distance n.  |coord| <= 2^24 keeps n below 2^52,
 // where the ceiling of the correctly rounded float64 root is exactly the
 // integer ceiling square root; that integer is computed here without float64
-// (GB300's float64 rate is low): a float32 estimate from the 32-bit
-// differences, then integer steps (one 32 x 32 -> 64-bit product each) to the
-// exact floor root s (s^2 <= n < (s+1)^2), then s + [s^2 != n].
+// (GB300's float64 rate is low): a float32 estimate s from the 32-bit
+// differences, the exact remainder r = n - s^2 (one 32 x 32 -> 64-bit
+// product), then steps of s by one that keep r exact by additions alone
+// ((s - 1)^2 = s^2 - (2s - 1), (s + 1)^2 = s^2 + (2s + 1)) to the floor root
+// (0 <= r <= 2s), then s + [r != 0].  Exact whatever the estimate's error.
 __device__ __forceinline__ int32_t leg_ceil(int x1, int y1, int x2, int y2)
 {
     const int dx = x1 - x2, dy = y1 - y2;   // |.| <= 2^25
     const long long n = (long long)dx * dx + (long long)dy * dy;
     const float fx = (float)dx, fy = (float)dy;
     const float fn = __fmaf_rn(fx, fx, __fmul_rn(fy, fy));   // n to a few parts in 2^24
-    int s = fn > 0.0f ? (int)__fmul_rn(fn, rsqrtf(fn)) : 0;   // within a few units of sqrt(n)
-    while ((long long)s * s > n) --s;
-    while ((long long)(s + 1) * (s + 1) <= n) ++s;
-    return s + ((long long)s * s != n ? 1 : 0);
+    int s = fn > 0.0f ? (int)__fmul_rn(fn, rsqrtf(fn)) : 0;   // within a few tens of units of sqrt(n)
+    long long r = n - (long long)s * s;
+    while (r < 0) {
+        r += 2 * s - 1;
+        --s;
+    }
+    while (r > 2 * (long long)s) {
+        ++s;
+        r -= 2 * s - 1;
+    }
+    return s + (r != 0 ? 1 : 0);
 }
 
 // Leg cost of Eq. 1 (Haversine) for points given as (latitude, longitude) in
