@@ -51,7 +51,7 @@ def parse_args():
     ap.add_argument("--passes", type=int, default=16, help="local: permutation pairs (scan orders) supplied")
     ap.add_argument("--instances", type=int, default=512, help="batched / serving: instances")
     ap.add_argument("--slots", type=int, default=512, help="batched / serving: engine slots")
-    ap.add_argument("--duration", type=float, default=20.0, help="serving: seconds of arrivals")
+    ap.add_argument("--duration", type=float, default=60.0, help="serving: seconds of arrivals")
     ap.add_argument("--rate", type=float, default=200.0, help="serving: arrivals per second")
     ap.add_argument("--no-plain", action="store_true", help="batched / serving: skip the plain-path pass")
     ap.add_argument("--missions", type=int, default=0,
