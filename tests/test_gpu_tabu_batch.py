@@ -102,6 +102,24 @@ def test_gangs_and_repeated_calls(stage_mod):
     same(first[0], oracle.tabu(cost, big.K, big.R, big.iters, big.tenure, nthreads=16))
 
 
+def test_searches_the_launch_does_not_take(stage_mod):
+    """More than 2048 bases, or K above 256: those searches run alone after
+    the launch, the others inside it; all equal their solo runs."""
+    stage = stage_mod
+    wide = small(60, 2100, 700, 6, iters=8)        # 2100 bases: longer rows than the body takes
+    many = small(61, 400, 3000, 300, iters=6)      # K = 300 open bases
+    mid = small(62, 60, 9000, 7, iters=20)
+    with stage.Context(device=0, profile=True) as ctx:
+        hs = [ctx.load_instance(i.base_xy, i.pick_xy, i.drop_xy) for i in (wide, many, mid)]
+        reqs = [dict(inst=h, K=i.K, R=i.R, iters=i.iters, tenure=i.tenure) for h, i in zip(hs, (wide, many, mid))]
+        got = ctx.tabu_batch(reqs)
+        assert ctx.kernel_stats("batch_searches")[0] == 1
+        for rq, g in zip(reqs, got):
+            same(g, ctx.tabu_run(rq["inst"], rq["K"], rq["R"], rq["iters"], rq["tenure"]))
+    cost = oracle.cost_table(mid.base_xy, mid.pick_xy, mid.drop_xy, 8)
+    same(got[2], oracle.tabu(cost, mid.K, mid.R, mid.iters, mid.tenure, nthreads=8))
+
+
 def test_malformed_batches_are_refused(stage_mod):
     stage = stage_mod
     a, b = small(80, 30, 2000, 4), small(81, 25, 1000, 3)
