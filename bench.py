@@ -925,7 +925,7 @@ def run_local(args):
     clk = clocks.stop()
     ms = e0.elapsed_time(e1)
     stats = {k: ctx.kernel_stats(k) for k in ("table", "order", "rowsum", "topk", "init", "begin", "transpose",
-                                              "swap_eval", "ls_select", "refresh", "swap_delta")}
+                                              "swap_eval", "local_persist", "ls_select", "refresh", "swap_delta")}
     n_sw, ms_sw = stats["swap_eval"]
     nC = inst.B - inst.K
     alg_bytes = TABLE_BYTES_PER_ELEM * nC * inst.M + AUX_BYTES_PER_MISSION * inst.M
@@ -941,11 +941,14 @@ def run_local(args):
             "moves_per_search": res.n_moves, "passes_used": res.passes, "local_optimum": res.local_optimum,
             "final": {"cov": res.final_cov, "dist": res.final_dist},
             "moves_per_s": moves / (ms / 1000.0),
-            # with the incremental neighbourhood (tables beyond L2) a search runs
-            # one full pass and then, per move, the selection, the refresh and the
-            # update from the changed missions: device time per applied move
-            "per_move_us": {k: 1000.0 * stats[k][1] / max(1, moves) for k in ("ls_select", "refresh",
-                                                                                "swap_delta", "swap_eval")},
+            # with the incremental neighbourhood a search runs one full pass and
+            # then, per move, the selection, the refresh and the update from the
+            # changed missions -- here all of them inside one cooperative launch
+            # (local_persist; the per-launch form's kernels otherwise): device
+            # time per applied move
+            "per_move_us": {k: 1000.0 * stats[k][1] / max(1, moves) for k in ("local_persist", "ls_select",
+                                                                                "refresh", "swap_delta",
+                                                                                "swap_eval")},
             "first_pass_roofline": {"bound": "hbm", "kernel": "swap_eval", "achieved": achieved, "peak": peak,
                          "peak_source": peak_src, "unit": "GB/s",
                          "frac": achieved / peak if achieved and peak else None,

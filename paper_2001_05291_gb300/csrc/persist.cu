@@ -229,13 +229,98 @@ struct PersistArgs {
     long long spin_limit;
     int region_cap;                 // records per CTA region
     int G;                          // CTAs of the search
+    const int *rank_slot;           // local search: [passes][K] each slot's place in a pass's scan order
+    const int *rank_cand;           // local search: [passes][nC] each candidate position's place
 };
 
 // Search scalars, the same in every CTA (each applies the same moves).
 struct PerState {
     long long cur_c, cur_d, best_c, best_d, v0c, v0d;
     int t, n_moves, best_iter, done, mv_s, mv_i, mv_j, recn, qn, prev_i;
+    int ls_pass, ls_pos, ls_moved, ls_optimum, ls_passes;   // local search (Alg. 2)
 };
+
+// The local search's pick (Alg. 2 as read: the first strictly improving swap
+// of a scan order): the swap's objective, its place u in the order.
+struct LsPick {
+    long long cov, dist;
+    int u, i, j, s, c, valid;
+};
+static_assert(sizeof(LsPick) <= sizeof(MoveKey), "picks use the per-CTA key slots");
+
+__device__ __forceinline__ LsPick no_pick()
+{
+    LsPick k;
+    k.cov = 0; k.dist = 0; k.u = INT_MAX; k.i = 0; k.j = 0; k.s = 0; k.c = 0; k.valid = 0;
+    return k;
+}
+
+// The warp's pick with the smallest place (places are distinct), in every lane.
+__device__ __forceinline__ void warp_first_pick(LsPick &k)
+{
+    const unsigned full = 0xffffffffu;
+    const unsigned v = k.valid ? (unsigned)k.u : 0xffffffffu;
+    const unsigned m = __reduce_min_sync(full, v);
+    if (m == 0xffffffffu) {   // the same on the warp
+        k = no_pick();
+        return;
+    }
+    const int src = __ffs(__ballot_sync(full, v == m)) - 1;
+    LsPick o;
+    o.cov = __shfl_sync(full, k.cov, src);
+    o.dist = __shfl_sync(full, k.dist, src);
+    o.u = (int)m;
+    o.i = __shfl_sync(full, k.i, src);
+    o.j = __shfl_sync(full, k.j, src);
+    o.s = __shfl_sync(full, k.s, src);
+    o.c = __shfl_sync(full, k.c, src);
+    o.valid = 1;
+    k = o;
+}
+
+// The CTA's first picks a and b: in warp 0 (to_all false) or in every thread.
+template <int NT>
+__device__ __forceinline__ void block_first_picks(LsPick &a, LsPick &b, LsPick *sa, LsPick *sb, bool to_all)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    warp_first_pick(a);
+    warp_first_pick(b);
+    if (lane == 0) {
+        sa[wid] = a;
+        sb[wid] = b;
+    }
+    __syncthreads();
+    if (wid == 0) {
+        a = lane < NT / 32 ? sa[lane] : no_pick();
+        b = lane < NT / 32 ? sb[lane] : no_pick();
+        warp_first_pick(a);
+        warp_first_pick(b);
+        if (to_all && lane == 0) {
+            sa[0] = a;
+            sb[0] = b;
+        }
+    }
+    if (to_all) {
+        __syncthreads();
+        a = sa[0];
+        b = sb[0];
+        __syncthreads();
+    }
+}
+
+__device__ __forceinline__ LsPick load_pick_cg(const LsPick *p)
+{
+    LsPick k;
+    k.cov = __ldcg(&p->cov);
+    k.dist = __ldcg(&p->dist);
+    k.u = __ldcg(&p->u);
+    k.i = __ldcg(&p->i);
+    k.j = __ldcg(&p->j);
+    k.s = __ldcg(&p->s);
+    k.c = __ldcg(&p->c);
+    k.valid = __ldcg(&p->valid);
+    return k;
+}
 
 // The best admissible and best overall key over this CTA's share of the
 // K x nC swaps, for the placement of iteration st.t, whose V0 and loss are
@@ -281,6 +366,59 @@ __device__ __forceinline__ void persist_select(const TabuBuffers &w, const PerSt
     }
 }
 
+// The local search's picks over this CTA's share of the K x nC swaps, for
+// the placement of move st.t (V0 and loss in `acc`, returned in v0c, v0d):
+// the first strictly improving swap at or after place st.ls_pos of pass
+// st.ls_pass's scan order (p1), and the first of the next pass's order (p2,
+// taken when the current pass has none left after a move).  A swap's place
+// is rank_slot[s] * nC + rank_cand[c] for its slot s and candidate position c.
+template <int NT>
+__device__ __forceinline__ void persist_local_select(const TabuBuffers &w, const PerState &st, int nC,
+                                                     const int *s_open, const int *s_cand, const int *rank_slot,
+                                                     const int *rank_cand, const unsigned long long *acc,
+                                                     const unsigned long long *cl, LsPick &p1, LsPick &p2,
+                                                     long long &v0c, long long &v0d, int gr, int G)
+{
+    const int K = w.K;
+    v0c = (long long)__ldcg(&acc[0]);
+    v0d = (long long)__ldcg(&acc[1]);
+    const int pass = st.ls_pass, pos0 = st.ls_pos;
+    const bool next = pass + 1 < st.ls_passes;
+    const int *ra = rank_slot + (size_t)pass * K, *rb = rank_cand + (size_t)pass * nC;
+    const int *ra2 = next ? ra + K : ra, *rb2 = next ? rb + nC : rb;
+    const int total = K * nC;
+    const int q0 = (int)((long long)total * gr / G);
+    const int q1 = (int)((long long)total * (gr + 1) / G);
+    for (int q = q0 + (int)threadIdx.x; q < q1; q += NT) {
+        const int s = q / nC, c = q - s * nC;
+        const int i = s_open[s], j = s_cand[c];
+        long long gc, gd, ec, ed;
+        if (j == st.prev_i) {
+            gc = (long long)__ldcg(&cl[0]);
+            gd = (long long)__ldcg(&cl[1]);
+            ec = (long long)__ldcg(&cl[2 + s]);
+            ed = (long long)__ldcg(&cl[2 + K + s]);
+        } else {
+            const size_t sj = (size_t)s * w.B + j;
+            gc = __ldcg(&w.gain_c[j]);
+            gd = (long long)__ldcg(&w.gain_d[j]);
+            ec = __ldcg(&w.extra_c[sj]);
+            ed = (long long)__ldcg(&w.extra_d[sj]);
+        }
+        const int u1 = __ldg(&ra[s]) * nC + __ldg(&rb[c]);
+        const int u2 = __ldg(&ra2[s]) * nC + __ldg(&rb2[c]);
+        const long long lc = (long long)__ldcg(&acc[2 + s]), ld = (long long)__ldcg(&acc[2 + K + s]);
+        const long long cov = v0c + gc + lc + ec, dist = v0d + gd + ld + ed;
+        if (!obj_better(cov, dist, st.cur_c, st.cur_d)) continue;
+        if (u1 >= pos0 && u1 < p1.u) {
+            p1.cov = cov; p1.dist = dist; p1.u = u1; p1.i = i; p1.j = j; p1.s = s; p1.c = c; p1.valid = 1;
+        }
+        if (next && u2 < p2.u) {
+            p2.cov = cov; p2.dist = dist; p2.u = u2; p2.i = i; p2.j = j; p2.s = s; p2.c = c; p2.valid = 1;
+        }
+    }
+}
+
 // Best admissible and best overall key of the CTA, valid in warp 0 only
 // (block_best2 without handing the result to every thread).
 template <int NT>
@@ -304,8 +442,10 @@ __device__ __forceinline__ void block_best2_warp0(MoveKey &adm, MoveKey &all, Mo
 
 // One whole search, run by the G CTAs of ranks gr = 0 .. G-1 (all resident,
 // each calling this with the same arguments); the lead CTA (rank 0) hands the
-// state back.
-template <int NT, int REC>
+// state back.  LOCAL: Alg. 2's local search (first improvement over the scan
+// orders of A.rank_slot / A.rank_cand) instead of the Tabu search; the
+// refresh and the update are the same.
+template <int NT, int REC, bool LOCAL = false>
 __device__ __forceinline__ void persist_search(const PersistArgs &A, const int gr, const int G)
 {
     constexpr int kPerWarps = NT / 32;
@@ -356,6 +496,8 @@ __device__ __forceinline__ void persist_search(const PersistArgs &A, const int g
         S.prev_i = -1;
         S.cur_c = st->cur_cov; S.cur_d = st->cur_dist;
         S.best_c = st->best_cov; S.best_d = st->best_dist;
+        S.ls_pass = st->ls_pass; S.ls_pos = st->ls_pos; S.ls_moved = st->ls_moved;
+        S.ls_optimum = st->ls_optimum; S.ls_passes = st->ls_passes;
         const unsigned long long *acc = A.acc + (size_t)(S.t & 1) * nA;
         S.v0c = (long long)acc[0];
         S.v0d = (long long)acc[1];
@@ -398,13 +540,27 @@ __device__ __forceinline__ void persist_search(const PersistArgs &A, const int g
         const int u = S.t;
         const unsigned long long *clp = A.col + (size_t)((u + 1) & 1) * nA;   // the previous move's sums
         const unsigned long long *acc = A.acc + (size_t)(u & 1) * nA;         // V0 and loss of this placement
-        MoveKey adm = invalid_key(), all = invalid_key();
         long long v0c, v0d;
-        persist_select<NT>(w, S, nC, s_open, s_cand, s_exp, acc, clp, adm, all, v0c, v0d, gr, G);
-        block_best2_warp0<NT>(adm, all, s_adm, s_all);
+        if constexpr (LOCAL) {
+            LsPick p1 = no_pick(), p2 = no_pick();
+            persist_local_select<NT>(w, S, nC, s_open, s_cand, A.rank_slot, A.rank_cand, acc, clp, p1, p2, v0c,
+                                     v0d, gr, G);
+            block_first_picks<NT>(p1, p2, reinterpret_cast<LsPick *>(s_adm), reinterpret_cast<LsPick *>(s_all),
+                                  false);
+            if (tid == 0) {
+                reinterpret_cast<LsPick *>(A.part)[2 * gr] = p1;
+                reinterpret_cast<LsPick *>(A.part)[2 * gr + 1] = p2;
+            }
+        } else {
+            MoveKey adm = invalid_key(), all = invalid_key();
+            persist_select<NT>(w, S, nC, s_open, s_cand, s_exp, acc, clp, adm, all, v0c, v0d, gr, G);
+            block_best2_warp0<NT>(adm, all, s_adm, s_all);
+            if (tid == 0) {
+                A.part[2 * gr] = adm;
+                A.part[2 * gr + 1] = all;
+            }
+        }
         if (tid == 0) {
-            A.part[2 * gr] = adm;
-            A.part[2 * gr + 1] = all;
             S.v0c = v0c;   // for the check of the chosen move's objective
             S.v0d = v0d;
         }
@@ -431,6 +587,65 @@ __device__ __forceinline__ void persist_search(const PersistArgs &A, const int g
         lap(kClkWaitA);
         const int u = S.t;   // the move of this iteration
         // ------------------------------------------------ choose and apply the move (a5, a6)
+        if constexpr (LOCAL) {
+            // Alg. 2 (readings L3, L4): the first improving swap of the pass
+            // at or after the scan position; none left after a move in this
+            // pass: the next pass's first from its start; none: stop (a local
+            // optimum unless the pass had moved and no pass is left)
+            LsPick p1 = no_pick(), p2 = no_pick();
+            for (int b = tid; b < G; b += NT) {
+                const LsPick a1 = load_pick_cg(reinterpret_cast<const LsPick *>(A.part) + 2 * b);
+                const LsPick a2 = load_pick_cg(reinterpret_cast<const LsPick *>(A.part) + 2 * b + 1);
+                if (a1.valid && a1.u < p1.u) p1 = a1;
+                if (a2.valid && a2.u < p2.u) p2 = a2;
+            }
+            block_first_picks<NT>(p1, p2, reinterpret_cast<LsPick *>(s_adm), reinterpret_cast<LsPick *>(s_all),
+                                  true);
+            if (S.cur_c != S.v0c || S.cur_d != S.v0d) {
+                if (lead_cta && tid == 0) atomicOr(A.err, kErrObjectiveMismatch);
+                if (tid == 0) S.done = 1;
+                break;
+            }
+            const int lpass = S.ls_pass, lmoved = S.ls_moved, lpasses = S.ls_passes;
+            const bool take2 = !p1.valid && lmoved && lpass + 1 < lpasses;
+            const LsPick Pm = p1.valid ? p1 : p2;
+            __syncthreads();   // every thread has read S before thread 0 changes it
+            if (!p1.valid && !(take2 && p2.valid)) {
+                if (tid == 0) {
+                    if (take2) S.ls_pass = lpass + 1;   // the new pass has no improving swap
+                    S.ls_optimum = (take2 || !lmoved) ? 1 : 0;
+                    S.done = 1;
+                }
+                break;
+            }
+            if (tid == 0) {
+                S.best_c = Pm.cov;   // every applied move is strictly better
+                S.best_d = Pm.dist;
+                S.best_iter = u;
+                S.cur_c = Pm.cov;
+                S.cur_d = Pm.dist;
+                S.mv_s = Pm.s; S.mv_i = Pm.i; S.mv_j = Pm.j;
+                s_open[Pm.s] = Pm.j;
+                s_cand[Pm.c] = Pm.i;
+                s_cidx[Pm.i] = Pm.c;
+                s_cidx[Pm.j] = -1;
+                if (lead_cta) {
+                    if (S.n_moves < traj_cap) {
+                        stage_move mv;
+                        mv.iter = u; mv.i = Pm.i; mv.j = Pm.j; mv.flags = STAGE_MOVE_NEW_BEST;
+                        mv.cov = Pm.cov; mv.dist = Pm.dist;
+                        w.traj[S.n_moves] = mv;
+                    }
+                    for (int k = 0; k < K; k++) w.best_open[k] = s_open[k];
+                }
+                if (take2) S.ls_pass = lpass + 1;
+                S.ls_pos = Pm.u + 1;
+                S.ls_moved = 1;
+                S.n_moves += 1;
+                S.recn = 0;
+                S.qn = 0;
+            }
+        } else {
         MoveKey adm = invalid_key(), all = invalid_key();
         for (int b = tid; b < G; b += NT) {
             const MoveKey pa = load_key_cg(&A.part[2 * b]), px = load_key_cg(&A.part[2 * b + 1]);
@@ -485,6 +700,7 @@ __device__ __forceinline__ void persist_search(const PersistArgs &A, const int g
             S.recn = 0;
             S.qn = 0;
         }
+        }   // the Tabu move
         for (int k = tid; k < K; k += NT) {
             s_lc[k] = 0;
             s_ld[k] = 0;
@@ -954,6 +1170,12 @@ __device__ __forceinline__ void persist_search(const PersistArgs &A, const int g
         st->mv_j = S.mv_j;
         st->chg_n = 0;
         st->err |= *reinterpret_cast<volatile int *>(A.err);
+        if constexpr (LOCAL) {
+            st->ls_pass = S.ls_pass;
+            st->ls_pos = S.ls_pos;
+            st->ls_moved = S.ls_moved;
+            st->ls_optimum = S.ls_optimum;
+        }
         A.info[0] = G;
     }
 }
@@ -961,6 +1183,12 @@ __device__ __forceinline__ void persist_search(const PersistArgs &A, const int g
 __global__ void __launch_bounds__(kPerThreads, 1) k_tabu_persist(PersistArgs A)
 {
     persist_search<kPerThreads, kRecCap>(A, (int)blockIdx.x, (int)gridDim.x);
+}
+
+// Alg. 2's local search in one cooperative launch (the same body, LOCAL).
+__global__ void __launch_bounds__(kPerThreads, 1) k_local_persist(PersistArgs A)
+{
+    persist_search<kPerThreads, kRecCap, true>(A, (int)blockIdx.x, (int)gridDim.x);
 }
 
 // Many searches in one cooperative launch: CTA b runs the entries
@@ -1054,8 +1282,11 @@ cudaError_t persist_init()
     cudaError_t e = cudaFuncSetAttribute(k_tabu_persist, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPerSmemLimit);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_tabu_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPerSmemLimit);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_local_persist, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPerSmemLimit);
     return e;
 }
+
 
 // The arguments of one search on `grid` CTAs over its scratch (laid out as
 // persist_scratch_bytes counts it); with `clear`, the scratch's sums, counters
@@ -1114,6 +1345,19 @@ cudaError_t launch_tabu_persist(const TabuBuffers &w, const int32_t *cost, void 
     if (e != cudaSuccess) return e;
     void *args[] = {&A};
     return cudaLaunchCooperativeKernel((const void *)k_tabu_persist, dim3(grid), dim3(kPerThreads), args,
+                                       persist_smem(w.K, w.B, w.ldT), s);
+}
+
+cudaError_t launch_local_persist(const TabuBuffers &w, const int32_t *cost, void *scratch, int grid,
+                                 long long spin_limit, const int *rank_slot, const int *rank_cand, cudaStream_t s)
+{
+    PersistArgs A;
+    cudaError_t e = persist_args(w, cost, scratch, grid, spin_limit, s, A);
+    if (e != cudaSuccess) return e;
+    A.rank_slot = rank_slot;
+    A.rank_cand = rank_cand;
+    void *args[] = {&A};
+    return cudaLaunchCooperativeKernel((const void *)k_local_persist, dim3(grid), dim3(kPerThreads), args,
                                        persist_smem(w.K, w.B, w.ldT), s);
 }
 

@@ -1595,14 +1595,33 @@ stage_status run_local_search(stage_ctx *c, Instance *in, const stage_ls_params 
     stage_status s = setup_search(c, in, start.data(), K, p->R, p->max_moves, 0, 1, 0, nullptr, &nC);
     if (s != STAGE_OK) return s;
     if (nC != nC0) return set_err(c, STAGE_ERR_INTERNAL, "candidate count %d, expected %d", nC, nC0);
-    // beyond L2 (or with STAGE_INCREMENTAL) the terms are kept across moves:
-    // one full pass, then per step the records of the missions a move touched
-    // (a pass change holds the terms, as in the full-pass form)
+    // The terms are kept across moves (one full pass, then per step the
+    // records of the missions a move touched; a pass change holds the terms,
+    // as in the full-pass form): the whole search in one cooperative launch
+    // for tables of 2^18 entries or more (or with STAGE_INCREMENTAL) where
+    // that launch takes the shape (not with STAGE_NO_PERSIST; smaller tables
+    // stream faster than its fixed cost per move), else per-step launches for
+    // tables beyond L2 (or with STAGE_INCREMENTAL), else a full pass per step.
     TabuBuffers tb = in->tb;
+    const bool big = (size_t)nC * in->M_pad >= (1u << 18) || (c->flags & STAGE_INCREMENTAL);
+    const int pgrid = nC > 0 && p->max_moves > 0 && big && !(c->flags & STAGE_NO_PERSIST) && tb.mask == nullptr
+                          ? persist_grid(K, in->B, table_ldT(in->B), in->M_pad)
+                          : 0;
     bool inc = !(c->flags & STAGE_FULL_PASS) && swap_delta_fits(K) && nC > 0 &&
-               ((c->flags & STAGE_INCREMENTAL) ||
+               ((c->flags & STAGE_INCREMENTAL) || pgrid > 0 ||
                 (size_t)nC * in->M_pad * sizeof(int32_t) >= kIncrementalMinTableBytes);
     if (inc) inc = use_incremental(c, in, tb);
+    bool persist = inc && pgrid > 0;
+    if (persist) {
+        const size_t need = persist_scratch_bytes(K, pgrid, in->M_pad);
+        if (!in->mem_persist.p || in->mem_persist.bytes < need) {
+            dev_free(c, in->mem_persist);
+            if (dev_alloc(c, need, in->mem_persist) != STAGE_OK) {
+                persist = false;
+                set_err(c, STAGE_OK, "");   // a refused allocation here is not an error of the search
+            }
+        }
+    }
     DevBuf dr;
     s = dev_alloc(c, rank.size() * 4 + 4, dr);
     if (s != STAGE_OK) return s;
@@ -1633,8 +1652,13 @@ stage_status run_local_search(stage_ctx *c, Instance *in, const stage_ls_params 
         if (r == cudaSuccess) r = cudaStreamSynchronize(c->stream);
         return r;
     };
+    if (e == cudaSuccess && persist)
+        e = timed(c, "local_persist", 1, [&] {
+            return launch_local_persist(tb, in->cost, in->mem_persist.p, pgrid, c->spin_limit, d_rank_slot,
+                                        d_rank_cand, c->stream);
+        });
     cudaGraphExec_t ge = nullptr;
-    if (e == cudaSuccess && nC > 0 && !profiling && max_steps >= kGraphIters) {
+    if (e == cudaSuccess && nC > 0 && !persist && !profiling && max_steps >= kGraphIters) {
         cudaGraph_t gr = nullptr;
         e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
         for (int k = 0; e == cudaSuccess && k < kGraphIters; k++) e = step();
@@ -1644,7 +1668,7 @@ stage_status run_local_search(stage_ctx *c, Instance *in, const stage_ls_params 
         if (gr) cudaGraphDestroy(gr);
     }
     long long it = 0;
-    while (e == cudaSuccess && nC > 0 && it < max_steps) {
+    while (e == cudaSuccess && nC > 0 && !persist && it < max_steps) {
         if (ge) {
             for (const char *nm : {"ls_select", "refresh"}) c->stats[nm].launches += kGraphIters;
             c->stats[inc ? "swap_delta" : "swap_eval"].launches += kGraphIters;
@@ -1677,6 +1701,9 @@ stage_status run_local_search(stage_ctx *c, Instance *in, const stage_ls_params 
         e = cudaMemcpy(traj, tb.traj, (size_t)n * sizeof(stage_move), cudaMemcpyDeviceToHost);
     dev_free(c, dr);
     if (e != cudaSuccess) return set_err(c, STAGE_ERR_CUDA, "local search failed: %s", cudaGetErrorString(e));
+    if (st.err & kErrPipelineTimeout)
+        return set_err(c, STAGE_ERR_TIMEOUT, "a device-side wait gave up after %lld polls after %d moves",
+                       (long long)c->spin_limit, st.n_moves);
     if (st.err)
         return set_err(c, STAGE_ERR_INTERNAL, "device self-check failed (code %d) after %d moves", st.err, st.n_moves);
     if (nC > 0 && !st.done && st.n_moves < p->max_moves)

@@ -200,6 +200,12 @@ bool persist_shape_ok(int K, int B, int ldT);
 int persist_max_gang();
 cudaError_t launch_tabu_batch(const void *d_args, const int2 *d_sched, const int *d_off, int grid, size_t smem,
                               cudaStream_t s);
+// Alg. 2's local search with the incremental neighbourhood in one cooperative
+// launch (the persistent body with its first-improvement selection): the
+// scan orders' ranks rank_slot [passes][K], rank_cand [passes][nC] on the
+// device, passes in w.st->ls_passes; grid and scratch as for the Tabu search.
+cudaError_t launch_local_persist(const TabuBuffers &w, const int32_t *cost, void *scratch, int grid,
+                                 long long spin_limit, const int *rank_slot, const int *rank_cand, cudaStream_t s);
 cudaError_t persist_init();
 // Test support: a wait on a flag that nothing sets, bounded by `limit` polls;
 // it sets kErrPipelineTimeout in *err when it gives up.

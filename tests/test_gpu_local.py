@@ -3,9 +3,10 @@
 The whole trajectory (every applied move with its objective), the final
 placement, the number of passes and the local-optimum flag must be identical:
 integers, zero tolerance.  The cases span single-block and graph-replayed
-driver paths, pass changes (the step that keeps the accumulators and skips the
-swap pass), budgets, unavailable bases, K = 1 and an instance with no
-candidate base.
+driver paths, the persistent search (the whole local search in one
+cooperative launch) and its per-launch form, pass changes (the step that keeps
+the accumulators and skips the swap pass), budgets, unavailable bases, K = 1
+and an instance with no candidate base.
 """
 import numpy as np
 import pytest
@@ -108,17 +109,19 @@ def test_wide_range_and_bad_permutation(ctx):
     ctx.unload_instance(h)
 
 
-@pytest.fixture(scope="module")
-def ictx():
+@pytest.fixture(scope="module", params=[True, False], ids=["persistent", "per-launch"])
+def ictx(request):
     """A context whose local searches keep the swap terms across moves (the
     incremental neighbourhood: one full pass, then the records of the
-    missions each move touched; a pass change holds the terms)."""
+    missions each move touched; a pass change holds the terms): the whole
+    search in one cooperative launch, or per-step launches."""
     torch = pytest.importorskip("torch")
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     from paper_2001_05291_gb300 import build, stage
     build.build()
-    with stage.Context(device=0, incremental=True, profile=True) as c:
+    with stage.Context(device=0, incremental=True, persist=request.param, profile=True) as c:
+        c.persistent = request.param
         yield c
 
 
@@ -140,4 +143,7 @@ def test_incremental_local_search_edges(ictx):
     assert cut.n_moves == 2 and not cut.local_optimum
     check(ictx, full, 6, full.R, 8, 9, start_open=np.arange(6) * 3)
     check(ictx, full, 6, 2**31 - 2, 5, 13)
-    assert ictx.kernel_stats("swap_delta")[0] > 0
+    if ictx.persistent:
+        assert ictx.kernel_stats("local_persist")[0] > 0
+    else:
+        assert ictx.kernel_stats("swap_delta")[0] > 0
