@@ -997,11 +997,17 @@ stage_status run_tabu_batch(stage_ctx *c, int n, const stage_inst *hs, const sta
     }
     char *stage = batch_staging(c, bytes);
     if (!stage) return set_err(c, STAGE_ERR_NO_MEMORY, "no pinned host memory for the batch (%zu bytes)", bytes);
+    // (an early return first waits for the copies already queued into the
+    // staging, which a later call may reallocate)
+    auto fail = [&](stage_status s) {
+        cudaStreamSynchronize(c->stream);
+        return s;
+    };
     for (int i = 0; i < n; i++)
         if (!ps[i].resume && !ps[i].start_open) {
             stage_status s = rank_queue(c, items[i].in, ps[i].K, reinterpret_cast<int32_t *>(stage + at_rank[i]),
                                         nullptr);
-            if (s != STAGE_OK) return s;
+            if (s != STAGE_OK) return fail(s);
         }
     CK(cudaStreamSynchronize(c->stream));
     // 2. the start of every search, queued (no wait per search); the full pass
@@ -1015,7 +1021,7 @@ stage_status run_tabu_batch(stage_ctx *c, int n, const stage_inst *hs, const sta
         const bool ranked = !p->resume && !p->start_open;
         stage_status s = tabu_prepare(c, in, p, &it.t0, &it.nC,
                                       ranked ? reinterpret_cast<const int32_t *>(stage + at_rank[i]) : nullptr, false);
-        if (s != STAGE_OK) return s;
+        if (s != STAGE_OK) return fail(s);
         const int K = p->K, ldT = table_ldT(in->B);
         it.fused = it.nC > 0 && p->iters > 0 && persist_shape_ok(K, in->B, ldT) &&
                    !(c->flags & (STAGE_FULL_PASS | STAGE_NO_PERSIST));
@@ -1025,8 +1031,9 @@ stage_status run_tabu_batch(stage_ctx *c, int n, const stage_inst *hs, const sta
             it.fused = false;
             continue;
         }
-        CK(timed(c, "swap_eval", 1, [&] { return launch_swap_eval(it.tw, in->cost, it.nC, 0, c->stream); }));
-        CK(cudaMemcpyAsync(stage + at_v0[i], it.tw.v0, 16, cudaMemcpyDeviceToHost, c->stream));
+        cudaError_t e = timed(c, "swap_eval", 1, [&] { return launch_swap_eval(it.tw, in->cost, it.nC, 0, c->stream); });
+        if (e == cudaSuccess) e = cudaMemcpyAsync(stage + at_v0[i], it.tw.v0, 16, cudaMemcpyDeviceToHost, c->stream);
+        if (e != cudaSuccess) return fail(set_err(c, STAGE_ERR_CUDA, "batch set-up failed: %s", cudaGetErrorString(e)));
         smem = std::max(smem, persist_search_smem(K, in->B, ldT));
     }
     CK(cudaStreamSynchronize(c->stream));
