@@ -64,6 +64,14 @@ def _moves(traj, n: int) -> list:
     return np.frombuffer(traj, dtype=_MOVE_DTYPE, count=n).tolist()
 
 
+def _moves_array(traj, n: int) -> np.ndarray:
+    """The first n stage_move records of a ctypes array as a structured numpy
+    view (it keeps the array alive)."""
+    if traj is None or n <= 0:
+        return np.empty(0, dtype=_MOVE_DTYPE)
+    return np.frombuffer(traj, dtype=_MOVE_DTYPE, count=n)
+
+
 class StageTabuState(C.Structure):
     _fields_ = [("t", C.c_int32), ("best_iter", C.c_int32), ("best_cov", C.c_int64),
                 ("best_dist", C.c_int64), ("open", C.c_void_p), ("best_open", C.c_void_p),
@@ -194,18 +202,31 @@ def _host_i32(a, n=None) -> np.ndarray:
     return out
 
 
-@dataclass
 class TabuResult:
-    n_moves: int
-    best_open: np.ndarray
-    best_cov: int
-    best_dist: int
-    best_iter: int
-    final_open: np.ndarray
-    final_cov: int
-    final_dist: int
-    moves: list = field(default_factory=list)   # (iter, i, j, flags, cov, dist)
-    end_state: dict | None = None
+    """A Tabu search's result.  moves_array: the applied moves as a numpy
+    structured array (iter, i, j, flags, cov, dist), a view of the returned
+    trajectory; moves: the same as a list of tuples of Python ints, built from
+    it on first use."""
+
+    def __init__(self, n_moves, best_open, best_cov, best_dist, best_iter, final_open, final_cov, final_dist,
+                 moves=None, end_state=None):
+        self.n_moves, self.best_open, self.best_cov, self.best_dist = n_moves, best_open, best_cov, best_dist
+        self.best_iter, self.final_open, self.final_cov, self.final_dist = best_iter, final_open, final_cov, final_dist
+        self.end_state = end_state
+        if isinstance(moves, np.ndarray):
+            self.moves_array, self._moves = moves, None
+        else:
+            self.moves_array, self._moves = None, list(moves) if moves is not None else []
+
+    @property
+    def moves(self) -> list:
+        if self._moves is None:
+            self._moves = self.moves_array.tolist()
+        return self._moves
+
+    def __repr__(self):
+        return (f"TabuResult(n_moves={self.n_moves}, best_cov={self.best_cov}, best_dist={self.best_dist}, "
+                f"best_iter={self.best_iter}, final_cov={self.final_cov}, final_dist={self.final_dist})")
 
 
 @dataclass
@@ -483,9 +504,7 @@ class Context:
         traj = (StageMove * max(1, iters))() if trajectory else None
         self._check(lib().stage_tabu_run(self._h, inst, C.byref(p), C.byref(r),
                                          C.cast(traj, C.c_void_p) if traj is not None else None))
-        moves = []
-        if traj is not None:
-            moves = _moves(traj, r.n_moves)
+        moves = _moves_array(traj, min(r.n_moves, iters))
         out = TabuResult(r.n_moves, best, r.best_cov, r.best_dist, r.best_iter, fin, r.final_cov,
                          r.final_dist, moves)
         if es is not None:
@@ -523,7 +542,7 @@ class Context:
         results = []
         for k, (best, fin, traj) in enumerate(outs):
             r = rs[k]
-            moves = _moves(traj, r.n_moves)
+            moves = _moves_array(traj, min(r.n_moves, requests[k]["iters"]))
             results.append(TabuResult(r.n_moves, best, r.best_cov, r.best_dist, r.best_iter, fin, r.final_cov,
                                       r.final_dist, moves))
         return results
@@ -608,7 +627,7 @@ class Context:
             lib().stage_last_error(self._h, buf, 512)
             raise StageError(rc, f"batch request failed (ticket {ticket.id}); the context's last error: "
                                  f"{buf.value.decode(errors='replace')}")
-        moves = _moves(ticket.traj, res.n_moves)
+        moves = _moves_array(ticket.traj, res.n_moves)
         out = TabuResult(res.n_moves, ticket.best, res.best_cov, res.best_dist, res.best_iter, ticket.final,
                          res.final_cov, res.final_dist, moves)
         out.timing = dict(submit_ns=res.t_submit_ns, start_ns=res.t_start_ns, end_ns=res.t_end_ns)
