@@ -1010,6 +1010,8 @@ stage_status run_tabu_batch(stage_ctx *c, int n, const stage_inst *hs, const sta
             if (s != STAGE_OK) return fail(s);
         }
     CK(cudaStreamSynchronize(c->stream));
+    const double rank_ms = host_ms();
+    double prep_ms = 0.0;   // host time in the searches' set-up (the rest of phase 2: their full passes)
     // 2. the start of every search, queued (no wait per search); the full pass
     //    that starts the incremental form; the start placements' covered counts
     //    (the estimate of an unmeasured search), one wait
@@ -1019,8 +1021,10 @@ stage_status run_tabu_batch(stage_ctx *c, int n, const stage_inst *hs, const sta
         Instance *in = it.in;
         const stage_tabu_params *p = &ps[i];
         const bool ranked = !p->resume && !p->start_open;
+        const auto tp0 = std::chrono::steady_clock::now();
         stage_status s = tabu_prepare(c, in, p, &it.t0, &it.nC,
                                       ranked ? reinterpret_cast<const int32_t *>(stage + at_rank[i]) : nullptr, false);
+        prep_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - tp0).count();
         if (s != STAGE_OK) return fail(s);
         const int K = p->K, ldT = table_ldT(in->B);
         it.fused = it.nC > 0 && p->iters > 0 && persist_shape_ok(K, in->B, ldT) &&
@@ -1047,7 +1051,14 @@ stage_status run_tabu_batch(stage_ctx *c, int n, const stage_inst *hs, const sta
         total_us += batch_search_us(it, ps[i].iters, 1);
     }
     const int P = smem ? persist_batch_grid(smem) : 0;
-    c->stats["batch_host_setup"].ms += host_ms();
+    {
+        // set-up: the rankings, the searches' set-up, their full passes and covered counts
+        const double ms = host_ms();
+        c->stats["batch_host_setup"].ms += rank_ms + ms;
+        c->stats["batch_host_setup_rank"].ms += rank_ms;
+        c->stats["batch_host_setup_prepare"].ms += prep_ms;
+        c->stats["batch_host_setup_pass"].ms += ms - prep_ms;
+    }
     std::vector<int> order;
     for (int i = 0; i < n; i++)
         if (items[i].fused) {
