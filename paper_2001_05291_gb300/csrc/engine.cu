@@ -8,6 +8,12 @@
 // kStepsPerGraph steps and replayed while the set of slots is unchanged.
 // Between replays finished slots retire (results copied to the caller's
 // buffers, memory released) and waiting requests join: continuous batching.
+// Slots whose shape the persistent search takes (K <= 256, at most 2048 bases;
+// not with STAGE_NO_PERSIST or STAGE_FULL_PASS) run their first full pass at
+// admission and are then advanced, every round, by one cooperative launch of
+// the persistent batch body (each on a gang of CTAs placed when the slot set
+// changes), kStepsPerGraph iterations per launch; the others by the grouped
+// launches.
 // Every slot runs exactly the search stage_tabu_run would run alone, so each
 // result is independent of what else is in the batch.
 #include <cuda_runtime.h>
@@ -59,6 +65,9 @@ struct Slot {
     TabuBuffers tb{};
     int nC = 0;
     bool first_done = false;  // incremental slots: the first full pass has run
+    bool persist = false;     // advanced by the persistent batch launch
+    DevBuf pscratch;          // its scratch for that launch (sized for its gang)
+    double cov = 0.5;         // covered fraction of the start placement (its gang's estimate)
 };
 
 // Slots whose candidate rows x missions reach this many table bytes keep the
@@ -99,6 +108,15 @@ struct Engine {
         size_t map_off = 0;   // first entry of this lane's block maps in d_map
     };
     Lane lane[kLanes];
+    // the persistent slots' launch: their arguments, the schedule and the
+    // per-CTA offsets (device), the grid and its dynamic shared memory
+    DevBuf d_pbuf;
+    const void *p_args = nullptr;
+    const int2 *p_sched = nullptr;
+    const int *p_off = nullptr;
+    int p_n = 0, p_grid = 0;
+    size_t p_smem = 0;
+    cudaEvent_t ev_p[2] = {nullptr, nullptr};
     cudaStream_t lane_stream[kLanes] = {};   // lane_stream[0] is `stream`
     cudaEvent_t ev_fork = nullptr, ev_join[kLanes] = {};
     int lane_begin[kLanes + 1] = {};         // active[lane_begin[l], lane_begin[l + 1]) is lane l
@@ -297,12 +315,15 @@ bool Engine::admit(Ticket *tk, bool &transient, stage_inst &busy_on)
     tb.R = p.R;
     // the incremental form where the table is large enough and there is room
     // for the mission-major copy and the records (else a full pass per step)
+    bool pmode = false;
     {
         int nc_est = 0;
         for (int b = 0; b < in->B; b++) nc_est += in->h_avail[b];
         nc_est -= K;
+        pmode = !(c->flags & (STAGE_FULL_PASS | STAGE_NO_PERSIST)) && swap_delta_fits(K) && nc_est > 0 &&
+                p.iters > 0 && persist_shape_ok(K, in->B, table_ldT(in->B));
         const bool want = !(c->flags & STAGE_FULL_PASS) && swap_delta_fits(K) && nc_est > 0 &&
-                          ((c->flags & STAGE_INCREMENTAL) ||
+                          (pmode || (c->flags & STAGE_INCREMENTAL) ||
                            (size_t)nc_est * in->M_pad * sizeof(int32_t) >= kEngineIncrementalMinBytes);
         if (want && ensure_costT(c, in) == STAGE_OK &&
             dev_alloc(c, (size_t)in->M_pad * 2 * sizeof(int4), sl.chg) == STAGE_OK) {
@@ -313,6 +334,7 @@ bool Engine::admit(Ticket *tk, bool &transient, stage_inst &busy_on)
             tb.ldT = in->ldT;
         } else {
             dev_free(c, sl.chg);
+            pmode = false;
             set_err(c, STAGE_OK, "");   // a refused buffer only means the full pass
         }
     }
@@ -355,7 +377,15 @@ bool Engine::admit(Ticket *tk, bool &transient, stage_inst &busy_on)
     if (e == cudaSuccess) e = timed_on(c, stream, "init", 1, [&] { return launch_init(tb, in->cost, stream); });
     if (e == cudaSuccess)
         e = timed_on(c, stream, "begin", 1, [&] { return launch_begin(tb, keep_best ? 1 : 0, stream); });
+    // a persistent slot's first full pass (its swap terms, then kept move by move)
+    // and its start placement's covered count
+    unsigned long long v0h[2] = {0, 0};
+    if (e == cudaSuccess && pmode && sl.nC > 0) {
+        e = timed_on(c, stream, "swap_eval", 1, [&] { return launch_swap_eval(tb, in->cost, sl.nC, 0, stream); });
+        if (e == cudaSuccess) e = cudaMemcpyAsync(v0h, tb.v0, 16, cudaMemcpyDeviceToHost, stream);
+    }
     if (e == cudaSuccess) e = cudaStreamSynchronize(stream);   // host vectors above go out of scope
+    if (in->M > 0) sl.cov = std::min(1.0, (double)v0h[0] / in->M);
     if (e != cudaSuccess) {
         dev_free(c, sl.ws);
         dev_free(c, sl.chg);
@@ -363,6 +393,8 @@ bool Engine::admit(Ticket *tk, bool &transient, stage_inst &busy_on)
         return fail(STAGE_ERR_CUDA);
     }
     sl.tb = tb;
+    sl.persist = pmode && sl.nC > 0;
+    sl.first_done = sl.first_done || sl.persist;
     in->busy += 1;
     tk->res.n_forced = n_forced;
     {
@@ -441,6 +473,10 @@ stage_status Engine::rebuild()
         }
         gs[k].sel_blocks = select_blocks(sl.tb.K, sl.nC);
         gs[k].ref_blocks = group_ref_blocks(sl.tb.M_pad);
+        if (sl.persist) {   // advanced by the persistent launch only
+            gs[k].swap_blocks = gs[k].sel_blocks = gs[k].ref_blocks = 0;
+            gs[k].delta_bx = gs[k].delta_by = 0;
+        }
     }
     std::vector<int2> map;   // per lane: swap blocks, then select blocks, then refresh blocks
     for (int l = 0; l < kLanes; l++) {
@@ -479,6 +515,96 @@ stage_status Engine::rebuild()
         e = cudaMemcpyAsync(d_map.p, map.data(), sizeof(int2) * map.size(), cudaMemcpyHostToDevice, stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
     if (e != cudaSuccess) return STAGE_ERR_CUDA;
+    // the persistent slots: gang sizes (the smallest power of two that brings
+    // a slot's round under half of the ideal per-CTA time, from the estimate of
+    // the one-launch batch), placement, scratch and arguments
+    p_n = 0;
+    std::vector<int> pk;
+    for (int k = 0; k < n; k++)
+        if (active[k].persist) pk.push_back(k);
+    if (!pk.empty()) {
+        const int np = (int)pk.size();
+        size_t smem = 0;
+        std::vector<double> us(np);
+        double total = 0.0;
+        for (int i = 0; i < np; i++) {
+            const Slot &sl = active[pk[i]];
+            smem = std::max(smem, persist_search_smem(sl.tb.K, sl.in->B, sl.tb.ldT));
+            // the instance's measured work in a batch launch for this K and R,
+            // else the estimate from the start placement's covered fraction
+            const Instance *in = sl.in;
+            us[i] = in->batch_K == sl.tb.K && in->batch_R == sl.tb.R && in->batch_version == in->version &&
+                            in->batch_work_us > 0.0
+                        ? in->batch_work_us
+                        : persist_iter_us_estimate(in, sl.tb.K, sl.nC, sl.cov);
+            total += kStepsPerGraph * (5.0 + us[i]);
+        }
+        const int P = persist_batch_grid(smem);
+        if (P < 1) return STAGE_ERR_INTERNAL;
+        const double ideal = total / P;
+        std::vector<int> gang(np, 1);
+        std::vector<double> work(np);
+        auto round_us = [&](int i, int g) { return kStepsPerGraph * (5.0 + (g > 1 ? 4.0 : 0.0) + us[i] / g); };
+        for (int i = 0; i < np; i++) {
+            const Slot &sl = active[pk[i]];
+            const int gmax = std::min({persist_max_gang(), P, (sl.tb.M_pad + 31) / 32});
+            while (gang[i] * 2 <= gmax && round_us(i, gang[i]) > 0.5 * ideal) gang[i] *= 2;
+            work[i] = round_us(i, gang[i]);
+        }
+        std::vector<std::vector<int2>> lists;
+        std::vector<int> order;
+        batch_place(np, work.data(), gang.data(), P, lists, order);
+        const size_t ab = persist_args_bytes();
+        std::vector<unsigned char> h_args(ab * np);
+        for (int pos = 0; pos < np; pos++) {
+            const int i = order[pos];
+            Slot &sl = active[pk[i]];
+            const size_t need = persist_scratch_bytes(sl.tb.K, gang[i], sl.tb.M_pad);
+            if (!sl.pscratch.p || sl.pscratch.bytes < need) {
+                std::lock_guard<std::recursive_mutex> g(c->mu);
+                dev_free(c, sl.pscratch);
+                stage_status st = dev_alloc(c, need, sl.pscratch);
+                if (st != STAGE_OK) return st;
+            }
+            if (persist_args_host(sl.tb, sl.in->cost, sl.pscratch.p, gang[i], c->spin_limit, stream,
+                                  h_args.data() + ab * pos) != cudaSuccess)
+                return STAGE_ERR_CUDA;
+        }
+        std::vector<int2> h_sched;
+        std::vector<int> h_off(P + 1, 0);
+        for (int q = 0; q < P; q++) {
+            h_off[q] = (int)h_sched.size();
+            h_sched.insert(h_sched.end(), lists[q].begin(), lists[q].end());
+        }
+        h_off[P] = (int)h_sched.size();
+        const size_t off_sched = round_up(h_args.size(), 256),
+                     off_off = off_sched + round_up(h_sched.size() * sizeof(int2), 256),
+                     bytes = off_off + round_up(h_off.size() * sizeof(int), 256);
+        if (!d_pbuf.p || d_pbuf.bytes < bytes) {
+            std::lock_guard<std::recursive_mutex> g(c->mu);
+            dev_free(c, d_pbuf);
+            stage_status st = dev_alloc(c, bytes, d_pbuf);
+            if (st != STAGE_OK) return st;
+        }
+        // new buffers are allocated in order on the context stream: finish it
+        // before the engine's stream uses them
+        if (cudaStreamSynchronize(c->stream) != cudaSuccess) return STAGE_ERR_CUDA;
+        char *d = static_cast<char *>(d_pbuf.p);
+        e = cudaMemcpyAsync(d, h_args.data(), h_args.size(), cudaMemcpyHostToDevice, stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(d + off_sched, h_sched.data(), h_sched.size() * sizeof(int2), cudaMemcpyHostToDevice,
+                                stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(d + off_off, h_off.data(), h_off.size() * sizeof(int), cudaMemcpyHostToDevice, stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(stream);   // the host arrays above
+        if (e != cudaSuccess) return STAGE_ERR_CUDA;
+        p_args = d;
+        p_sched = reinterpret_cast<const int2 *>(d + off_sched);
+        p_off = reinterpret_cast<const int *>(d + off_off);
+        p_n = np;
+        p_grid = P;
+        p_smem = smem;
+    }
     dirty = false;
     stable = 0;
     return STAGE_OK;
@@ -505,6 +631,11 @@ cudaError_t Engine::launch_steps(int steps)
         return e;
     };
     auto used = [&](int l) { return lane[l].n_swap + lane[l].n_sel + lane[l].n_ref + lane[l].n_delta > 0; };
+    {
+        bool any = false;
+        for (int l = 0; l < kLanes; l++) any = any || used(l);
+        if (!any) return cudaSuccess;   // every slot is advanced by the persistent launch
+    }
     auto enqueue = [&]() {
         cudaError_t e = cudaEventRecord(ev_fork, stream);
         for (int l = 1; e == cudaSuccess && l < kLanes; l++)
@@ -604,6 +735,7 @@ void Engine::retire_finish(Retiring &r, bool copies_ok)
         std::lock_guard<std::recursive_mutex> g(c->mu);
         dev_free(c, sl.ws);
         dev_free(c, sl.chg);
+        dev_free(c, sl.pscratch);
         sl.in->busy -= 1;
         if (tk->inline_inst) stage_unload_instance(c, tk->inst);
     }
@@ -698,6 +830,18 @@ void Engine::run()
                 }
                 cudaEventRecord(ev_round[0], stream);
                 e = launch_steps(kStepsPerGraph);
+                if (e == cudaSuccess && p_n > 0) {
+                    // the persistent slots: kStepsPerGraph iterations each, in one launch
+                    if (!ev_p[0]) {
+                        cudaEventCreate(&ev_p[0]);
+                        cudaEventCreate(&ev_p[1]);
+                    }
+                    e = launch_batch_prep(p_args, p_n, stream);
+                    if (e == cudaSuccess) e = cudaEventRecord(ev_p[0], stream);
+                    if (e == cudaSuccess)
+                        e = launch_tabu_batch(p_args, p_sched, p_off, p_grid, p_smem, stream, kStepsPerGraph);
+                    if (e == cudaSuccess) e = cudaEventRecord(ev_p[1], stream);
+                }
                 if (e == cudaSuccess)
                     e = launch_gather_states(static_cast<const GroupSlot *>(d_slots.p), n,
                                              static_cast<TabuDevState *>(d_states.p), stream);
@@ -761,6 +905,12 @@ void Engine::run()
                 KernelStat &k = c->stats["engine_gpu_round"];   // device time of the round's launches
                 k.launches += 1;
                 k.ms += gpu_ms;
+                float pms = 0.f;
+                if (p_n > 0 && cudaEventElapsedTime(&pms, ev_p[0], ev_p[1]) == cudaSuccess) {
+                    KernelStat &kp = c->stats["engine_persist"];   // the persistent launch's device time
+                    kp.launches += 1;
+                    kp.ms += pms;
+                }
             }
             int erased = 0;
             for (size_t k = n; k-- > 0;) {   // descending: erasing keeps the lower indices
@@ -831,6 +981,9 @@ void engine_destroy(stage_ctx *c)
     if (E->graph) cudaGraphExecDestroy(E->graph);
     for (cudaEvent_t ev : E->ev_round)
         if (ev) cudaEventDestroy(ev);
+    for (cudaEvent_t ev : E->ev_p)
+        if (ev) cudaEventDestroy(ev);
+    dev_free(c, E->d_pbuf);
     dev_free(c, E->d_slots);
     dev_free(c, E->d_map);
     dev_free(c, E->d_states);

@@ -444,9 +444,11 @@ __device__ __forceinline__ void block_best2_warp0(MoveKey &adm, MoveKey &all, Mo
 // each calling this with the same arguments); the lead CTA (rank 0) hands the
 // state back.  LOCAL: Alg. 2's local search (first improvement over the scan
 // orders of A.rank_slot / A.rank_cand) instead of the Tabu search; the
-// refresh and the update are the same.
+// refresh and the update are the same.  max_steps > 0: at most that many
+// iterations this launch (the search goes on in a later launch from the state
+// handed back); a search already done makes none.
 template <int NT, int REC, bool LOCAL = false>
-__device__ __forceinline__ void persist_search(const PersistArgs &A, const int gr, const int G)
+__device__ __forceinline__ void persist_search(const PersistArgs &A, const int gr, const int G, int max_steps = 0)
 {
     constexpr int kPerWarps = NT / 32;
     static_assert(REC <= NT && REC % 32 == 0, "one staged record per thread");
@@ -477,7 +479,8 @@ __device__ __forceinline__ void persist_search(const PersistArgs &A, const int g
     const bool lead_cta = gr == 0;
     const int nA = 2 + 2 * K;
     TabuDevState *st = w.st;
-    const int t_end = st->t_end, tenure = st->tenure, aw = st->accept_worsening, nC = st->nC;
+    const int t_end0 = st->t_end, tenure = st->tenure, aw = st->accept_worsening, nC = st->nC;
+    const int t_end = st->done ? st->t : max_steps > 0 ? min(t_end0, st->t + max_steps) : t_end0;
     const int traj_cap = st->traj_cap;
     int4 *region = A.region + (size_t)gr * A.region_cap * 2;
     long long rec_total = 0;   // records of this CTA over the search
@@ -491,7 +494,7 @@ __device__ __forceinline__ void persist_search(const PersistArgs &A, const int g
         S.t = st->t;
         S.n_moves = st->n_moves;
         S.best_iter = st->best_iter;
-        S.done = 0;
+        S.done = st->done;
         S.mv_s = st->mv_s; S.mv_i = st->mv_i; S.mv_j = st->mv_j;
         S.prev_i = -1;
         S.cur_c = st->cur_cov; S.cur_d = st->cur_dist;
@@ -1198,7 +1201,8 @@ __global__ void __launch_bounds__(kPerThreads, 1) k_local_persist(PersistArgs A)
 // every one of its CTAs at it or done with it, and each barrier wait ends
 // (bounded by the spin limit in any case).  A search's arguments are staged
 // in shared memory.
-__global__ void __launch_bounds__(kBatchThreads, 1024 / kBatchThreads) k_tabu_batch(const PersistArgs *__restrict__ args,
+__global__ void __launch_bounds__(kBatchThreads, 1024 / kBatchThreads) k_tabu_batch(int max_steps,
+                                                                                       const PersistArgs *__restrict__ args,
                                                                const int2 *__restrict__ sched,
                                                                const int *__restrict__ off)
 {
@@ -1211,7 +1215,7 @@ __global__ void __launch_bounds__(kBatchThreads, 1024 / kBatchThreads) k_tabu_ba
         int *dst = reinterpret_cast<int *>(&sA);
         for (int q = threadIdx.x; q < (int)(sizeof(PersistArgs) / 4); q += kBatchThreads) dst[q] = __ldg(src + q);
         __syncthreads();
-        persist_search<kBatchThreads, kBatchRec>(sA, it.y, sA.G);
+        persist_search<kBatchThreads, kBatchRec>(sA, it.y, sA.G, max_steps);
         __syncthreads();   // every thread is done with this search's arguments
     }
 }
@@ -1425,10 +1429,10 @@ bool persist_shape_ok(int K, int B, int ldT)
 int persist_max_gang() { return kMaxGrid; }
 
 cudaError_t launch_tabu_batch(const void *d_args, const int2 *d_sched, const int *d_off, int grid, size_t smem,
-                              cudaStream_t s)
+                              cudaStream_t s, int max_steps)
 {
     const PersistArgs *a = static_cast<const PersistArgs *>(d_args);
-    void *args[] = {(void *)&a, (void *)&d_sched, (void *)&d_off};
+    void *args[] = {(void *)&max_steps, (void *)&a, (void *)&d_sched, (void *)&d_off};
     return cudaLaunchCooperativeKernel((const void *)k_tabu_batch, dim3(grid), dim3(kBatchThreads), args, smem, s);
 }
 

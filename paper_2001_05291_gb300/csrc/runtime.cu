@@ -885,6 +885,17 @@ struct BatchItem {
     TabuBuffers tw{};
 };
 
+}  // namespace
+
+double persist_iter_us_estimate(const Instance *in, int K, int nC, double cov)
+{
+    const double M = in->M_pad, cells = 0.386 * table_ldT(in->B) / 32.0;
+    const double records = 2.0 * cov * M / K;
+    return (2.2 * M + records * (20.0 + 28.0 * cells) + 2.05 * K * nC) * 1e-3;
+}
+
+namespace {
+
 // Estimated device time of one iteration of the persistent body on one CTA,
 // beyond its fixed part, in us, before any measurement of the instance: 2.2 ns
 // per mission (the refresh), 2 cov M / K records per move (the covered
@@ -898,9 +909,7 @@ double batch_iter_us(const Instance *in, int K, int R, int nC, double cov)
 {
     if (in->batch_K == K && in->batch_R == R && in->batch_version == in->version && in->batch_work_us > 0.0)
         return in->batch_work_us;
-    const double M = in->M_pad, cells = 0.386 * table_ldT(in->B) / 32.0;
-    const double records = 2.0 * cov * M / K;
-    return (2.2 * M + records * (20.0 + 28.0 * cells) + 2.05 * K * nC) * 1e-3;
+    return persist_iter_us_estimate(in, K, nC, cov);
 }
 
 constexpr double kBatchFixedUs = 5.0;    // an iteration's move, barriers and reductions on one CTA
@@ -918,8 +927,8 @@ double batch_search_us(const BatchItem &it, int iters, int g)
 // the gang of CTAs that are free first, starting at the latest of their finish
 // times.  lists[q]: CTA q's (search, rank) entries in placement order, so
 // every CTA runs the searches in one global order; returns the latest finish.
-static double batch_place(int n, const double *work, const int *gang, int P, std::vector<std::vector<int2>> &lists,
-                          std::vector<int> &order)
+double batch_place(int n, const double *work, const int *gang, int P, std::vector<std::vector<int2>> &lists,
+                   std::vector<int> &order)
 {
     order.resize(n);
     for (int k = 0; k < n; k++) order[k] = k;

@@ -128,6 +128,14 @@ stage_status autotune_shape(stage_ctx *c, Instance *in, const int32_t *open, int
 stage_status setup_search(stage_ctx *c, Instance *in, const int32_t *open, int K, int R, int traj_cap, int tenure,
                           int accept_worsening, int t0, const int32_t *expiry_in, int *out_nC, bool sync = true);
 stage_status rank_queue(stage_ctx *c, Instance *in, int K, int32_t *out_open, int64_t *out_rowsum);
+// The persistent batch launch's host logic (runtime.cu): the estimated work of
+// one iteration of a search on one CTA (us; cov = covered fraction), and the
+// placement of n searches (work[k] on gang[k] CTAs) on P CTAs -- lists[q] =
+// CTA q's (placement position, rank) entries, order[pos] = the search placed
+// at pos; returns the latest estimated finish.
+double persist_iter_us_estimate(const Instance *in, int K, int nC, double cov);
+double batch_place(int n, const double *work, const int *gang, int P, std::vector<std::vector<int2>> &lists,
+                   std::vector<int> &order);
 stage_status ensure_costT(stage_ctx *c, Instance *in);
 stage_status forced_moves(stage_ctx *c, Instance *in, int32_t *open, int K, int R, int t, int tenure,
                           int32_t *expiry, int *n_forced);

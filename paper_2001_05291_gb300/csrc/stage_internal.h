@@ -198,8 +198,10 @@ size_t persist_search_smem(int K, int B, int ldT);
 int persist_batch_grid(size_t smem);
 bool persist_shape_ok(int K, int B, int ldT);
 int persist_max_gang();
+// max_steps > 0: each search makes at most that many iterations in this launch
+// and goes on from its handed-back state in a later one (engine rounds).
 cudaError_t launch_tabu_batch(const void *d_args, const int2 *d_sched, const int *d_off, int grid, size_t smem,
-                              cudaStream_t s);
+                              cudaStream_t s, int max_steps = 0);
 // Alg. 2's local search with the incremental neighbourhood in one cooperative
 // launch (the persistent body with its first-improvement selection): the
 // scan orders' ranks rank_slot [passes][K], rank_cand [passes][nC] on the

@@ -41,16 +41,26 @@ def same(got, want):
     assert np.array_equal(np.sort(got.final_open), np.sort(want.final_open))
 
 
-@pytest.mark.parametrize("incremental", [False, True])
-def test_batch_equals_alone_and_oracle(stage_mod, incremental):
-    """incremental: every slot keeps its swap terms across steps (one full
-    pass, then the records of the missions each move touched)."""
+MODES = {   # engine modes: Context keyword arguments
+    "persistent": dict(),                                    # slots advanced by the persistent batch launch
+    "grouped": dict(persist=False),                          # grouped launches, a full pass per step below 8 MB
+    "grouped-incremental": dict(persist=False, incremental=True),   # grouped launches, terms kept across steps
+}
+
+
+@pytest.mark.parametrize("mode", list(MODES))
+def test_batch_equals_alone_and_oracle(stage_mod, mode):
+    """Every slot's search equals its solo run and the oracle, whichever way
+    the engine advances it: the persistent batch launch (the slot's terms kept
+    across steps inside it), grouped launches with a full pass per step, or
+    grouped launches keeping the terms (one full pass, then the records of the
+    missions each move touched)."""
     stage = stage_mod
     insts = [small(s, B, M, K, R=R, iters=it) for s, (B, M, K, R, it) in enumerate(
         [(30, 2000, 4, 300_000, 30), (55, 17000, 9, 350_000, 25), (12, 300, 11, 250_000, 20),
          (80, 33000, 16, 400_000, 15), (40, 5000, 6, 200_000, 40), (9, 64, 3, 500_000, 12),
          (70, 20000, 32, 350_000, 18), (25, 9000, 5, 150_000, 35)])]
-    with stage.Context(device=0, max_slots=3, incremental=incremental, profile=True) as ctx:   # queueing
+    with stage.Context(device=0, max_slots=3, profile=True, **MODES[mode]) as ctx:   # queueing
         hs = [ctx.load_instance(i.base_xy, i.pick_xy, i.drop_xy) for i in insts]
         reqs = [dict(inst=h, K=i.K, R=i.R, iters=i.iters, tenure=i.tenure) for h, i in zip(hs, insts)]
         # an instance given by value, an explicit start, an improving-only search
@@ -76,8 +86,10 @@ def test_batch_equals_alone_and_oracle(stage_mod, incremental):
                                nthreads=8)
             same(g, want)
             assert g.timing["submit_ns"] <= g.timing["start_ns"] <= g.timing["end_ns"]
-        if incremental:
+        if mode == "grouped-incremental":
             assert ctx.kernel_stats("group_delta")[0] > 0
+        if mode == "persistent":
+            assert ctx.kernel_stats("engine_persist")[0] > 0
         assert got[-1].n_moves < 60   # the improving-only search stopped early inside the batch
 
 

@@ -38,7 +38,7 @@ def moves(res):
     return [tuple(int(x) for x in m) for m in res.moves]
 
 
-def run_scenario(stage, mix, incremental=False):
+def run_scenario(stage, mix, **ctx_kwargs):
     inst = small(31, 90, 5000, 6)
     extra = small(32, 90, 400, 6)
     K, R, tenure = inst.K, inst.R, 4
@@ -62,7 +62,7 @@ def run_scenario(stage, mix, incremental=False):
     o3 = oracle.tabu(cost3, K, R, 25, tenure, start_open=O3, avail=avail, t0=35, expiry_in=exp3, best_in=O3,
                      best_cov_in=cov3, best_dist_in=dist3, best_iter_in=-1, nthreads=8)
     assert len(done) == 2
-    with stage.Context(device=0, max_slots=8, incremental=incremental) as ctx:
+    with stage.Context(device=0, max_slots=8, **ctx_kwargs) as ctx:
         h = ctx.load_instance(inst.base_xy, inst.pick_xy, inst.drop_xy)
         base = dict(inst=h, K=K, R=R, tenure=tenure, resume_resident=True)
         r1 = ctx.batch_submit([dict(base, iters=20)])[0].wait()
@@ -99,8 +99,12 @@ def test_resumed_requests_in_a_mix(stage_mod):
     run_scenario(stage_mod, mix=True)
 
 
-def test_resumed_requests_incremental_slots(stage_mod):
-    run_scenario(stage_mod, mix=True, incremental=True)
+def test_resumed_requests_grouped_incremental_slots(stage_mod):
+    run_scenario(stage_mod, mix=True, incremental=True, persist=False)
+
+
+def test_resumed_requests_grouped_full_pass_slots(stage_mod):
+    run_scenario(stage_mod, mix=True, persist=False)
 
 
 def test_resume_without_resident_state_starts_from_the_ranking(stage_mod):
