@@ -12,7 +12,7 @@
 // not with STAGE_NO_PERSIST or STAGE_FULL_PASS) run their first full pass at
 // admission and are then advanced, every round, by one cooperative launch of
 // the persistent batch body (each on a gang of CTAs placed when the slot set
-// changes), kStepsPerGraph iterations per launch; the others by the grouped
+// changes), kPersistRoundSteps iterations per launch; the others by the grouped
 // launches.
 // Every slot runs exactly the search stage_tabu_run would run alone, so each
 // result is independent of what else is in the batch.
@@ -32,6 +32,7 @@ namespace stg_rt {
 namespace {
 
 constexpr int kStepsPerGraph = 8;
+constexpr int kPersistRoundSteps = 16;  // iterations of the persistent slots per round (8: the same latency, 543 inst/s batched; 32: p99 223 ms)
 constexpr int kLanes = 2;   // lanes of slots advanced on their own streams (see Engine::Lane)
 
 int64_t now_ns()
@@ -537,14 +538,14 @@ stage_status Engine::rebuild()
                             in->batch_work_us > 0.0
                         ? in->batch_work_us
                         : persist_iter_us_estimate(in, sl.tb.K, sl.nC, sl.cov);
-            total += kStepsPerGraph * (5.0 + us[i]);
+            total += kPersistRoundSteps * (5.0 + us[i]);
         }
         const int P = persist_batch_grid(smem);
         if (P < 1) return STAGE_ERR_INTERNAL;
         const double ideal = total / P;
         std::vector<int> gang(np, 1);
         std::vector<double> work(np);
-        auto round_us = [&](int i, int g) { return kStepsPerGraph * (5.0 + (g > 1 ? 4.0 : 0.0) + us[i] / g); };
+        auto round_us = [&](int i, int g) { return kPersistRoundSteps * (5.0 + (g > 1 ? 4.0 : 0.0) + us[i] / g); };
         for (int i = 0; i < np; i++) {
             const Slot &sl = active[pk[i]];
             const int gmax = std::min({persist_max_gang(), P, (sl.tb.M_pad + 31) / 32});
@@ -831,7 +832,7 @@ void Engine::run()
                 cudaEventRecord(ev_round[0], stream);
                 e = launch_steps(kStepsPerGraph);
                 if (e == cudaSuccess && p_n > 0) {
-                    // the persistent slots: kStepsPerGraph iterations each, in one launch
+                    // the persistent slots: kPersistRoundSteps iterations each, in one launch
                     if (!ev_p[0]) {
                         cudaEventCreate(&ev_p[0]);
                         cudaEventCreate(&ev_p[1]);
@@ -839,7 +840,7 @@ void Engine::run()
                     e = launch_batch_prep(p_args, p_n, stream);
                     if (e == cudaSuccess) e = cudaEventRecord(ev_p[0], stream);
                     if (e == cudaSuccess)
-                        e = launch_tabu_batch(p_args, p_sched, p_off, p_grid, p_smem, stream, kStepsPerGraph);
+                        e = launch_tabu_batch(p_args, p_sched, p_off, p_grid, p_smem, stream, kPersistRoundSteps);
                     if (e == cudaSuccess) e = cudaEventRecord(ev_p[1], stream);
                 }
                 if (e == cudaSuccess)
