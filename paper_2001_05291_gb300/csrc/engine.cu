@@ -326,6 +326,20 @@ bool Engine::admit(Ticket *tk, bool &transient, stage_inst &busy_on)
         const bool want = !(c->flags & STAGE_FULL_PASS) && swap_delta_fits(K) && nc_est > 0 &&
                           (pmode || (c->flags & STAGE_INCREMENTAL) ||
                            (size_t)nc_est * in->M_pad * sizeof(int32_t) >= kEngineIncrementalMinBytes);
+        // a persistent slot's scratch, for the largest gang it can be given (so
+        // that placing it later allocates nothing)
+        if (pmode) {
+            const int ldT = table_ldT(in->B);
+            const int gcap = std::min({persist_max_gang(), persist_batch_grid(persist_search_smem(K, in->B, ldT)),
+                                       (in->M_pad + 31) / 32});
+            size_t need = 0;   // over the gangs it can be given: powers of two up to gcap
+            for (int g = 1; g <= gcap; g *= 2) need = std::max(need, persist_scratch_bytes(K, g, in->M_pad));
+            if (gcap < 1 || dev_alloc(c, need, sl.pscratch) != STAGE_OK) {
+                pmode = false;
+                dev_free(c, sl.pscratch);
+                set_err(c, STAGE_OK, "");   // a refused buffer only means the grouped launches
+            }
+        }
         if (want && ensure_costT(c, in) == STAGE_OK &&
             dev_alloc(c, (size_t)in->M_pad * 2 * sizeof(int4), sl.chg) == STAGE_OK) {
             tb.chg = static_cast<int4 *>(sl.chg.p);
@@ -335,9 +349,11 @@ bool Engine::admit(Ticket *tk, bool &transient, stage_inst &busy_on)
             tb.ldT = in->ldT;
         } else {
             dev_free(c, sl.chg);
+            dev_free(c, sl.pscratch);
             pmode = false;
             set_err(c, STAGE_OK, "");   // a refused buffer only means the full pass
         }
+        if (!pmode) dev_free(c, sl.pscratch);
     }
     std::vector<uint8_t> is_open(in->B, 0);
     for (int k = 0; k < K; k++) is_open[start[k]] = 1;
@@ -390,11 +406,13 @@ bool Engine::admit(Ticket *tk, bool &transient, stage_inst &busy_on)
     if (e != cudaSuccess) {
         dev_free(c, sl.ws);
         dev_free(c, sl.chg);
+        dev_free(c, sl.pscratch);
         set_err(c, STAGE_ERR_CUDA, "batch slot set-up failed: %s", cudaGetErrorString(e));
         return fail(STAGE_ERR_CUDA);
     }
     sl.tb = tb;
     sl.persist = pmode && sl.nC > 0;
+    if (!sl.persist) dev_free(c, sl.pscratch);
     sl.first_done = sl.first_done || sl.persist;
     in->busy += 1;
     tk->res.n_forced = n_forced;
