@@ -61,7 +61,7 @@ def parse_args():
                     help="large: Tabu iterations of the full-pass reference run (0: skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-other-configs", action="store_true",
-                    help="large: skip the tiny, province and batched figures added to the line")
+                    help="large: skip the tiny, province, batched and serving figures added to the line")
     ap.add_argument("--cpu-sample-missions", type=int, default=100_000)
     return ap.parse_args()
 
@@ -535,7 +535,7 @@ def run_ours(args):
     if rank == 0 and world == 1 and args.workload == "large" and not args.missions and not args.no_other_configs:
         ctx.close()
         torch.cuda.empty_cache()
-        others = other_configs(stage, torch, local)
+        others = other_configs(args, stage, torch, local)
 
     if rank == 0:
         line = {
@@ -574,12 +574,13 @@ def run_ours(args):
     return 0
 
 
-def other_configs(stage, torch, local):
+def other_configs(args, stage, torch, local):
     """Tiny and province: CUDA-event time per Tabu iteration of the whole search
     call on a loaded instance; batched: the 512 searches in one stage_tabu_batch
     launch after one untimed call (wall time per call, the kernel's CUDA-event
-    time and method bytes).  Each part reports an error string instead of
-    failing the run."""
+    time and method bytes); serving: the 60 s trace at 200 req/s through the
+    batch engine (latency percentiles, throughput; no serial comparison).  Each
+    part reports an error string instead of failing the run."""
     from paper_2001_05291_gb300 import synth
     out = {}
     for name, reps in (("tiny", 20), ("province", 5)):
@@ -624,6 +625,14 @@ def other_configs(stage, torch, local):
                           "hbm_frac": nbytes / (kms * 1e-3) / 1e9 / peak if kms > 0 else None}
     except Exception as e:
         out["batched"] = {"error": f"{type(e).__name__}: {e}"}
+    try:
+        eng, _ = serving_results(args, plain=False)
+        out["serving"] = {"workload": f"serving: seed 4, Poisson {args.rate:g} req/s for {args.duration:g} s, "
+                                      "30 % updates to 32 resident instances, 70 % fresh instances of the "
+                                      "batched size distribution, 300 Tabu iterations, tenure 11",
+                          **{k: eng[k] for k in ("p50_ms", "p99_ms", "mean_ms", "throughput_req_s", "requests")}}
+    except Exception as e:
+        out["serving"] = {"error": f"{type(e).__name__}: {e}"}
     return out
 
 
@@ -774,7 +783,9 @@ def serving_trace(args):
     return trace
 
 
-def run_serving(args):
+def serving_results(args, plain: bool):
+    """The serving trace through the engine, and (plain) the same trace served
+    serially on the plain path: latency percentiles and throughput of each."""
     import numpy as np
     import torch
     from paper_2001_05291_gb300 import build, stage, synth
@@ -867,8 +878,12 @@ def run_serving(args):
             out["host_phases"] = phases
         return out
 
-    eng = serve(True)
-    ser = None if args.no_plain else serve(False)
+    return serve(True), (serve(False) if plain else None)
+
+
+def run_serving(args):
+    rank, world, local = env_rank()
+    eng, ser = serving_results(args, not args.no_plain)
     line = {"metric": "serving p50/p99 latency", "value": eng["p99_ms"], "unit": "ms (p99)", "n_gpus": world,
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
             "data": "synthetic",
