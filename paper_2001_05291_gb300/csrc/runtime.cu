@@ -1025,6 +1025,7 @@ stage_status run_tabu_batch(stage_ctx *c, int n, const stage_inst *hs, const sta
     //    that starts the incremental form; the start placements' covered counts
     //    (the estimate of an unmeasured search), one wait
     size_t smem = 0;
+    std::vector<int> full;   // the searches the launch takes, each with its full pass
     for (int i = 0; i < n; i++) {
         BatchItem &it = items[i];
         Instance *in = it.in;
@@ -1044,12 +1045,57 @@ stage_status run_tabu_batch(stage_ctx *c, int n, const stage_inst *hs, const sta
             it.fused = false;
             continue;
         }
-        cudaError_t e = timed(c, "swap_eval", 1, [&] { return launch_swap_eval(it.tw, in->cost, it.nC, 0, c->stream); });
-        if (e == cudaSuccess) e = cudaMemcpyAsync(stage + at_v0[i], it.tw.v0, 16, cudaMemcpyDeviceToHost, c->stream);
-        if (e != cudaSuccess) return fail(set_err(c, STAGE_ERR_CUDA, "batch set-up failed: %s", cudaGetErrorString(e)));
+        full.push_back(i);
         smem = std::max(smem, persist_search_smem(K, in->B, ldT));
     }
-    CK(cudaStreamSynchronize(c->stream));
+    {
+        // every full pass in one grouped launch (the searches' descriptors and
+        // its block map uploaded first), then each start's covered count
+        const int nf = (int)full.size();
+        std::vector<int> mp(nf), nc(nf);
+        for (int k = 0; k < nf; k++) {
+            mp[k] = items[full[k]].in->M_pad;
+            nc[k] = items[full[k]].nC;
+        }
+        const int common = group_common_segment(mp.data(), nc.data(), nf);
+        std::vector<GroupSlot> gs(nf);
+        std::vector<int2> map;
+        size_t pass_smem = 0;
+        for (int k = 0; k < nf; k++) {
+            const BatchItem &it = items[full[k]];
+            gs[k] = GroupSlot{};
+            gs[k].w = it.tw;
+            gs[k].cost = it.in->cost;
+            gs[k].swap_blocks = group_swap_blocks(mp[k], nc[k], it.tw.K, common, &gs[k].swap_bx, &gs[k].swap_seg);
+            for (int b = 0; b < gs[k].swap_blocks; b++) map.push_back(make_int2(k, b));
+            pass_smem = std::max(pass_smem, swap_direct_smem(it.tw.K));
+        }
+        const size_t off_map = round_up(gs.size() * sizeof(GroupSlot), 256);
+        DevBuf gbuf;
+        cudaError_t e = cudaSuccess;
+        if (nf > 0) {
+            stage_status s = dev_alloc(c, off_map + map.size() * sizeof(int2), gbuf);
+            if (s != STAGE_OK) return fail(s);
+            char *d = static_cast<char *>(gbuf.p);
+            // (copies from pageable host memory are staged before they return)
+            e = cudaMemcpyAsync(d, gs.data(), gs.size() * sizeof(GroupSlot), cudaMemcpyHostToDevice, c->stream);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(d + off_map, map.data(), map.size() * sizeof(int2), cudaMemcpyHostToDevice,
+                                    c->stream);
+            if (e == cudaSuccess)
+                e = timed(c, "group_swap", 1, [&] {
+                    return launch_group_swap(reinterpret_cast<const GroupSlot *>(d),
+                                             reinterpret_cast<const int2 *>(d + off_map), (int)map.size(), pass_smem,
+                                             c->stream);
+                });
+        }
+        for (int k = 0; k < nf && e == cudaSuccess; k++)
+            e = cudaMemcpyAsync(stage + at_v0[full[k]], items[full[k]].tw.v0, 16, cudaMemcpyDeviceToHost, c->stream);
+        const cudaError_t se = cudaStreamSynchronize(c->stream);
+        dev_free(c, gbuf);   // after the wait: the launch has read it
+        if (e == cudaSuccess) e = se;
+        if (e != cudaSuccess) return set_err(c, STAGE_ERR_CUDA, "batch set-up failed: %s", cudaGetErrorString(e));
+    }
     double total_us = 0.0;
     for (int i = 0; i < n; i++) {
         BatchItem &it = items[i];
