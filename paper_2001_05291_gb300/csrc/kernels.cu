@@ -639,14 +639,14 @@ cudaError_t launch_rowsum(const int32_t *cost, int B, int M, int M_pad, unsigned
 }
 
 // rank(b) = number of available b' with (S[b'], b') < (S[b], b); the K with
-// rank < K are written in rank order.
-__global__ void __launch_bounds__(256) k_topk(const unsigned long long *__restrict__ S,
-                                              const uint8_t *__restrict__ avail, int B, int K,
-                                              int32_t *__restrict__ open)
+// rank < K are written in rank order.  Block `blk` ranks bases blk*256 ...
+__device__ __forceinline__ void topk_body(const unsigned long long *__restrict__ S,
+                                          const uint8_t *__restrict__ avail, int B, int K,
+                                          int32_t *__restrict__ open, int blk)
 {
     __shared__ long long sS[1024];
     __shared__ uint8_t sA[1024];
-    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    const int b = blk * blockDim.x + threadIdx.x;
     const bool mine = b < B && avail[b];
     const long long s = mine ? (long long)S[b] : 0;
     int rank = 0;
@@ -669,10 +669,38 @@ __global__ void __launch_bounds__(256) k_topk(const unsigned long long *__restri
     if (mine && rank < K) open[rank] = b;
 }
 
+__global__ void __launch_bounds__(256) k_topk(const unsigned long long *__restrict__ S,
+                                              const uint8_t *__restrict__ avail, int B, int K,
+                                              int32_t *__restrict__ open)
+{
+    topk_body(S, avail, B, K, open, blockIdx.x);
+}
+
+// Many rankings in one launch: map[b] = (ranking, block within it).
+__global__ void __launch_bounds__(256) k_topk_group(const TopkSlot *__restrict__ slots,
+                                                    const int2 *__restrict__ map)
+{
+    const int2 e = map[blockIdx.x];
+    const TopkSlot g = slots[e.x];
+    topk_body(g.S, g.avail, g.B, g.K, g.open, e.y);
+}
+
+int topk_blocks(int B)
+{
+    return (B + 255) / 256;
+}
+
+cudaError_t launch_topk_group(const TopkSlot *slots, const int2 *map, int total_blocks, cudaStream_t s)
+{
+    if (total_blocks <= 0) return cudaSuccess;
+    k_topk_group<<<total_blocks, 256, 0, s>>>(slots, map);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_topk(const unsigned long long *S, const uint8_t *avail, int B, int K,
                         int32_t *open, cudaStream_t s)
 {
-    k_topk<<<(B + 255) / 256, 256, 0, s>>>(S, avail, B, K, open);
+    k_topk<<<topk_blocks(B), 256, 0, s>>>(S, avail, B, K, open);
     return cudaGetLastError();
 }
 
@@ -2625,6 +2653,24 @@ cudaError_t launch_group_swap(const GroupSlot *slots, const int2 *map, int total
 {
     if (total_blocks <= 0) return cudaSuccess;
     k_group_swap<<<total_blocks, kDirThreads, smem, s>>>(slots, map);
+    return cudaGetLastError();
+}
+
+// out[2k], out[2k + 1] = slot k's V0 (covered, distance): every slot's start
+// objective gathered for one read-back.
+__global__ void k_group_v0(const GroupSlot *__restrict__ slots, int n, unsigned long long *__restrict__ out)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const unsigned long long *v0 = slots[k].w.v0;
+    out[2 * k] = v0[0];
+    out[2 * k + 1] = v0[1];
+}
+
+cudaError_t launch_group_v0(const GroupSlot *slots, int n, unsigned long long *out, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    k_group_v0<<<(n + 127) / 128, 128, 0, s>>>(slots, n, out);
     return cudaGetLastError();
 }
 

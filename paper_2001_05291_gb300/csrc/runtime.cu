@@ -271,21 +271,16 @@ stage_status check_placement(stage_ctx *c, Instance *in, const int32_t *open, in
     return STAGE_OK;
 }
 
-// The ranking (Alg. 1) queued on the context's stream: the row sums (kept
-// with the instance once computed, until an update), the K smallest, their
-// ids copied to out_open (host memory; pinned memory is filled when the stream
-// gets there, pageable memory before this returns) and, if asked, the sums.
-stage_status rank_queue(stage_ctx *c, Instance *in, int K, int32_t *out_open, int64_t *out_rowsum)
+// The ranking's checks of K and its row sums (Alg. 1), queued on the
+// context's stream (kept with the instance once computed, until an update).
+stage_status rank_sums(stage_ctx *c, Instance *in, int K)
 {
     if (K < 1 || K > in->B || K > STAGE_MAX_K)
         return set_err(c, STAGE_ERR_INVALID_ARG, "K=%d outside [1, min(B=%d, %d)]", K, in->B, STAGE_MAX_K);
     if (K > in->n_avail)
         return set_err(c, STAGE_ERR_INVALID_ARG, "K=%d exceeds the %d available bases", K, in->n_avail);
-    size_t need = round_up((size_t)K * 4, 256);
-    stage_status s = ensure_scratch(c, in, need);
-    if (s != STAGE_OK) return s;
-    auto *d_open = static_cast<int32_t *>(in->mem_scratch.p);
     if (!in->rowsum_ok) {
+        stage_status s;
         if (!in->mem_rowsum.p || in->mem_rowsum.bytes < (size_t)in->B * 8) {
             dev_free(c, in->mem_rowsum);
             s = dev_alloc(c, (size_t)in->B * 8, in->mem_rowsum);
@@ -296,6 +291,20 @@ stage_status rank_queue(stage_ctx *c, Instance *in, int K, int32_t *out_open, in
         CK(timed(c, "rowsum", 1, [&] { return launch_rowsum(in->cost, in->B, in->M, in->M_pad, S, c->stream); }));
         in->rowsum_ok = true;
     }
+    return STAGE_OK;
+}
+
+// The ranking (Alg. 1) queued on the context's stream: the row sums, the K
+// smallest, their ids copied to out_open (host memory; pinned memory is
+// filled when the stream gets there, pageable memory before this returns)
+// and, if asked, the sums.
+stage_status rank_queue(stage_ctx *c, Instance *in, int K, int32_t *out_open, int64_t *out_rowsum)
+{
+    stage_status s = rank_sums(c, in, K);
+    if (s != STAGE_OK) return s;
+    s = ensure_scratch(c, in, round_up((size_t)K * 4, 256));
+    if (s != STAGE_OK) return s;
+    auto *d_open = static_cast<int32_t *>(in->mem_scratch.p);
     const auto *S = static_cast<const unsigned long long *>(in->mem_rowsum.p);
     CK(timed(c, "topk", 1, [&] { return launch_topk(S, in->avail, in->B, K, d_open, c->stream); }));
     CK(cudaMemcpyAsync(out_open, d_open, (size_t)K * 4, cudaMemcpyDeviceToHost, c->stream));
@@ -994,31 +1003,67 @@ stage_status run_tabu_batch(stage_ctx *c, int n, const stage_inst *hs, const sta
             if (items[k].in == items[i].in)
                 return set_err(c, STAGE_ERR_INVALID_ARG, "requests %d and %d name the same instance", k, i);
     }
-    // 1. the ranking of every search that starts from it, queued together
-    //    (its start placement to pinned staging), one wait
-    std::vector<size_t> at_rank(n), at_v0(n);
-    size_t bytes = 0;
-    for (int i = 0; i < n; i++) {
-        at_rank[i] = bytes;
-        bytes += round_up((size_t)std::max(1, ps[i].K) * 4, 16);
-        at_v0[i] = bytes;
-        bytes += 16;
-    }
-    char *stage = batch_staging(c, bytes);
-    if (!stage) return set_err(c, STAGE_ERR_NO_MEMORY, "no pinned host memory for the batch (%zu bytes)", bytes);
-    // (an early return first waits for the copies already queued into the
-    // staging, which a later call may reallocate)
+    // 1. the ranking of every search that starts from it: the row sums an
+    //    instance lacks, then every search's K smallest in one grouped launch
+    //    and one read-back of the start placements to pinned staging, one wait
+    // (an early return first waits for the work already queued, whose
+    // buffers a later call may reallocate)
     auto fail = [&](stage_status s) {
         cudaStreamSynchronize(c->stream);
         return s;
     };
-    for (int i = 0; i < n; i++)
-        if (!ps[i].resume && !ps[i].start_open) {
-            stage_status s = rank_queue(c, items[i].in, ps[i].K, reinterpret_cast<int32_t *>(stage + at_rank[i]),
-                                        nullptr);
-            if (s != STAGE_OK) return fail(s);
+    std::vector<size_t> at_rank(n, 0);
+    std::vector<int> ranked;   // the searches that start from the ranking
+    size_t rank_bytes = 0, rank_blocks = 0;
+    for (int i = 0; i < n; i++) {
+        if (ps[i].resume || ps[i].start_open) continue;
+        stage_status s = rank_sums(c, items[i].in, ps[i].K);
+        if (s != STAGE_OK) return fail(s);
+        ranked.push_back(i);
+        at_rank[i] = rank_bytes;
+        rank_bytes += round_up((size_t)ps[i].K * 4, 16);
+        rank_blocks += topk_blocks(items[i].in->B);
+    }
+    // the staging: the start placements, then every search's V0 (phase 2)
+    const size_t v0_at = round_up(rank_bytes, 16);
+    const size_t bytes = v0_at + 16 * (size_t)n;
+    char *stage = batch_staging(c, bytes);
+    if (!stage)
+        return fail(set_err(c, STAGE_ERR_NO_MEMORY, "no pinned host memory for the batch (%zu bytes)", bytes));
+    if (!ranked.empty()) {
+        const size_t off_map = round_up(ranked.size() * sizeof(TopkSlot), 256),
+                     off_open = off_map + round_up(rank_blocks * sizeof(int2), 256);
+        DevBuf rbuf;
+        stage_status s = dev_alloc(c, off_open + rank_bytes, rbuf);
+        if (s != STAGE_OK) return fail(s);
+        char *d = static_cast<char *>(rbuf.p);
+        std::vector<TopkSlot> ts(ranked.size());
+        std::vector<int2> tmap;
+        tmap.reserve(rank_blocks);
+        for (size_t k = 0; k < ranked.size(); k++) {
+            const int i = ranked[k];
+            const Instance *in = items[i].in;
+            ts[k] = TopkSlot{static_cast<const unsigned long long *>(in->mem_rowsum.p), in->avail,
+                             reinterpret_cast<int32_t *>(d + off_open + at_rank[i]), in->B, ps[i].K};
+            for (int b = 0; b < topk_blocks(in->B); b++) tmap.push_back(make_int2((int)k, b));
         }
-    CK(cudaStreamSynchronize(c->stream));
+        // (copies from pageable host memory are staged before they return)
+        cudaError_t e = cudaMemcpyAsync(d, ts.data(), ts.size() * sizeof(TopkSlot), cudaMemcpyHostToDevice,
+                                        c->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(d + off_map, tmap.data(), tmap.size() * sizeof(int2), cudaMemcpyHostToDevice,
+                                c->stream);
+        if (e == cudaSuccess)
+            e = timed(c, "topk", 1, [&] {
+                return launch_topk_group(reinterpret_cast<const TopkSlot *>(d),
+                                         reinterpret_cast<const int2 *>(d + off_map), (int)tmap.size(), c->stream);
+            });
+        if (e == cudaSuccess) e = cudaMemcpyAsync(stage, d + off_open, rank_bytes, cudaMemcpyDeviceToHost, c->stream);
+        const cudaError_t se = cudaStreamSynchronize(c->stream);
+        dev_free(c, rbuf);   // after the wait: the launch and the copy have read it
+        if (e == cudaSuccess) e = se;
+        if (e != cudaSuccess) return set_err(c, STAGE_ERR_CUDA, "batch ranking failed: %s", cudaGetErrorString(e));
+    }
     const double rank_ms = host_ms();
     double prep_ms = 0.0;   // host time in the searches' set-up (the rest of phase 2: their full passes)
     // 2. the start of every search, queued (no wait per search); the full pass
@@ -1050,7 +1095,8 @@ stage_status run_tabu_batch(stage_ctx *c, int n, const stage_inst *hs, const sta
     }
     {
         // every full pass in one grouped launch (the searches' descriptors and
-        // its block map uploaded first), then each start's covered count
+        // its block map uploaded first), then every start's V0 gathered into
+        // one read-back
         const int nf = (int)full.size();
         std::vector<int> mp(nf), nc(nf);
         for (int k = 0; k < nf; k++) {
@@ -1070,11 +1116,12 @@ stage_status run_tabu_batch(stage_ctx *c, int n, const stage_inst *hs, const sta
             for (int b = 0; b < gs[k].swap_blocks; b++) map.push_back(make_int2(k, b));
             pass_smem = std::max(pass_smem, swap_direct_smem(it.tw.K));
         }
-        const size_t off_map = round_up(gs.size() * sizeof(GroupSlot), 256);
+        const size_t off_map = round_up(gs.size() * sizeof(GroupSlot), 256),
+                     off_v0 = off_map + round_up(map.size() * sizeof(int2), 256);
         DevBuf gbuf;
         cudaError_t e = cudaSuccess;
         if (nf > 0) {
-            stage_status s = dev_alloc(c, off_map + map.size() * sizeof(int2), gbuf);
+            stage_status s = dev_alloc(c, off_v0 + 16 * (size_t)nf, gbuf);
             if (s != STAGE_OK) return fail(s);
             char *d = static_cast<char *>(gbuf.p);
             // (copies from pageable host memory are staged before they return)
@@ -1088,19 +1135,22 @@ stage_status run_tabu_batch(stage_ctx *c, int n, const stage_inst *hs, const sta
                                              reinterpret_cast<const int2 *>(d + off_map), (int)map.size(), pass_smem,
                                              c->stream);
                 });
+            if (e == cudaSuccess)
+                e = launch_group_v0(reinterpret_cast<const GroupSlot *>(d), nf,
+                                    reinterpret_cast<unsigned long long *>(d + off_v0), c->stream);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(stage + v0_at, d + off_v0, 16 * (size_t)nf, cudaMemcpyDeviceToHost, c->stream);
         }
-        for (int k = 0; k < nf && e == cudaSuccess; k++)
-            e = cudaMemcpyAsync(stage + at_v0[full[k]], items[full[k]].tw.v0, 16, cudaMemcpyDeviceToHost, c->stream);
         const cudaError_t se = cudaStreamSynchronize(c->stream);
         dev_free(c, gbuf);   // after the wait: the launch has read it
         if (e == cudaSuccess) e = se;
         if (e != cudaSuccess) return set_err(c, STAGE_ERR_CUDA, "batch set-up failed: %s", cudaGetErrorString(e));
     }
     double total_us = 0.0;
-    for (int i = 0; i < n; i++) {
+    for (size_t k = 0; k < full.size(); k++) {
+        const int i = full[k];
         BatchItem &it = items[i];
-        if (!it.fused) continue;
-        const unsigned long long covered = *reinterpret_cast<const unsigned long long *>(stage + at_v0[i]);
+        const unsigned long long covered = *reinterpret_cast<const unsigned long long *>(stage + v0_at + 16 * k);
         const double cov = it.in->M > 0 ? std::min(1.0, (double)covered / it.in->M) : 0.0;
         it.us_per_iter = batch_iter_us(it.in, ps[i].K, ps[i].R, it.nC, cov);
         total_us += batch_search_us(it, ps[i].iters, 1);

@@ -128,6 +128,7 @@ stage_status autotune_shape(stage_ctx *c, Instance *in, const int32_t *open, int
 stage_status setup_search(stage_ctx *c, Instance *in, const int32_t *open, int K, int R, int traj_cap, int tenure,
                           int accept_worsening, int t0, const int32_t *expiry_in, int *out_nC, bool sync = true);
 stage_status rank_queue(stage_ctx *c, Instance *in, int K, int32_t *out_open, int64_t *out_rowsum);
+stage_status rank_sums(stage_ctx *c, Instance *in, int K);   // its checks and row sums only
 // The persistent batch launch's host logic (runtime.cu): the estimated work of
 // one iteration of a search on one CTA (us; cov = covered fraction), and the
 // placement of n searches (work[k] on gang[k] CTAs) on P CTAs -- lists[q] =

@@ -114,6 +114,15 @@ cudaError_t launch_rowsum(const int32_t *cost, int B, int M, int M_pad, unsigned
                           cudaStream_t s);
 cudaError_t launch_topk(const unsigned long long *S, const uint8_t *avail, int B, int K,
                         int32_t *open, cudaStream_t s);
+// many rankings in one launch (one descriptor each; map[b] = (ranking, block))
+struct TopkSlot {
+    const unsigned long long *S;   // row sums [B]
+    const uint8_t *avail;          // [B]
+    int32_t *open;                 // out: [K] base ids in rank order
+    int B, K;
+};
+int topk_blocks(int B);
+cudaError_t launch_topk_group(const TopkSlot *slots, const int2 *map, int total_blocks, cudaStream_t s);
 cudaError_t launch_evaluate(const int32_t *cost, int M, int M_pad, const int32_t *open, int K,
                             int R, unsigned long long *out2, cudaStream_t s);
 cudaError_t launch_init(const TabuBuffers &w, const int32_t *cost, cudaStream_t s);
@@ -258,6 +267,8 @@ cudaError_t launch_swap_direct_seg(const TabuBuffers &w, const int32_t *cost, in
 int group_ref_blocks(int M_pad);
 cudaError_t launch_group_swap(const GroupSlot *slots, const int2 *map, int total_blocks, size_t smem,
                               cudaStream_t s);
+// out[2k .. 2k + 1] = slots[k].w.v0[0 .. 1] for k < n
+cudaError_t launch_group_v0(const GroupSlot *slots, int n, unsigned long long *out, cudaStream_t s);
 cudaError_t launch_group_select(const GroupSlot *slots, const int2 *map, int total_blocks, cudaStream_t s);
 cudaError_t launch_group_refresh(const GroupSlot *slots, const int2 *map, int total_blocks, int maxK,
                                  cudaStream_t s);
