@@ -275,7 +275,9 @@ STAGE_API stage_status stage_tabu_run(stage_ctx *ctx, stage_inst inst, const sta
  * on one another are bounded.  Those searches use the incremental
  * neighbourhood (one full pass, then the update of the swap terms from the
  * missions each move touched), so each instance gets its mission-major table
- * copy on first use, kept with it.  The other searches run one after another
+ * copy on first use, kept with it.  Before that launch, the rankings of the
+ * searches that start from Alg. 1 run as one grouped launch, and so do the
+ * searches' first full passes.  The other searches run one after another
  * afterwards.  An instance may appear once per call; the call returns when all
  * are done.
  * Errors: STAGE_ERR_NOT_FOUND (unknown instance), STAGE_ERR_INVALID_ARG (n < 0,
