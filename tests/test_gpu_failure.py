@@ -12,7 +12,6 @@
   documented fallback with the exact result, and nothing leaks (the context's
   accounting returns to zero, every hook allocation is freed).
 """
-import numpy as np
 import pytest
 
 import oracle

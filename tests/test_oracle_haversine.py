@@ -11,7 +11,6 @@
 import math
 
 import numpy as np
-import pytest
 
 from paper_2001_05291_gb300 import synth
 

@@ -8,7 +8,6 @@
   better than the optimum, every recorded objective equal to a recomputation);
 * an independent brute-force replay of the Tabu rules in Python.
 """
-import itertools
 import json
 import math
 import os
