@@ -1066,9 +1066,10 @@ stage_status run_tabu_batch(stage_ctx *c, int n, const stage_inst *hs, const sta
     }
     const double rank_ms = host_ms();
     double prep_ms = 0.0;   // host time in the searches' set-up (the rest of phase 2: their full passes)
-    // 2. the start of every search, queued (no wait per search); the full pass
-    //    that starts the incremental form; the start placements' covered counts
-    //    (the estimate of an unmeasured search), one wait
+    // 2. the start of every search, queued (no wait per search); the full
+    //    passes that start the incremental form, all in one grouped launch; the
+    //    start placements' covered counts (the estimate of an unmeasured
+    //    search), one read-back and one wait
     size_t smem = 0;
     std::vector<int> full;   // the searches the launch takes, each with its full pass
     for (int i = 0; i < n; i++) {
