@@ -664,10 +664,14 @@ class BatchTicket:
 def _make_update(add_pick=None, add_drop=None, remove=None, unavailable=None, available=None):
     u = StageUpdate()
     keep = []
+    if (add_pick is None) != (add_drop is None):
+        raise ValueError("add_pick and add_drop go together")
     if add_pick is not None:
         ap, ad = _host_i32(add_pick), _host_i32(add_drop)
         if ap.size != ad.size:
             raise ValueError("add_pick and add_drop differ in size")
+        if ap.size % 2:
+            raise ValueError("add_pick and add_drop hold (x, y) pairs")
         u.n_add, u.add_pick_xy, u.add_drop_xy = ap.size // 2, _ptr(ap), _ptr(ad)
         keep += [ap, ad]
     for name, cnt, ptr in ((remove, "n_remove", "remove_ids"), (unavailable, "n_unavail", "unavail_ids"),
