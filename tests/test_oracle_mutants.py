@@ -1,8 +1,10 @@
 """Planted mistakes in a copy of the oracle, on the CPU: each plausible slip
 (a dropped term, a flipped sign or comparison, an off-by-one) must make at least
 one pin fail -- of tests/test_oracle_pins.py for the C part (oracle.c), of
+tests/test_oracle_haversine.py for its Haversine leg (Eq. 1), of
 tests/test_oracle_fleet.py and tests/test_oracle_resume.py for the Python parts
-(the heterogeneous fleet, the forced moves of reading A15)."""
+(the heterogeneous fleet, the forced moves of reading A15), of
+tests/test_oracle_local.py for the local search (Alg. 2)."""
 import os
 import subprocess
 import sys
@@ -31,10 +33,23 @@ MUTANTS = {
 }
 
 
-@pytest.mark.parametrize("name", sorted(MUTANTS))
-def test_pins_catch_mutant(name, tmp_path):
-    old, new = MUTANTS[name]
+# the Haversine leg of Eq. 1 and the table built from it
+GEO_MUTANTS = {
+    "haversine_no_latitude_factor": ("(cos(phi1) * cos(phi2)) * (sl * sl)", "(sl * sl)"),
+    "haversine_full_angles": ("double sp = sin(0.5 * dphi), sl = sin(0.5 * dpsi);",
+                              "double sp = sin(dphi), sl = sin(dpsi);"),
+    "haversine_radius_not_doubled": ("(2.0 * ORACLE_EARTH_RADIUS_M) * asin", "ORACLE_EARTH_RADIUS_M * asin"),
+    "haversine_longitude_from_latitudes": ("double dpsi = (double)(lon2 - lon1)", "double dpsi = (double)(lat2 - lat1)"),
+    "haversine_rounded_down": ("asin(sqrt(h));\n    return (int32_t)ceil(d);",
+                               "asin(sqrt(h));\n    return (int32_t)floor(d);"),
+    "geo_dropped_return_leg": (" +\n               oracle_leg_haversine(qx, qy, bx, by)", ""),
+}
+
+
+def _c_mutant_survives(name, old, new, pin_files, tmp_path, exact_once=False):
     src = open(SRC).read()
+    if exact_once:
+        assert src.count(old) == 1, f"mutation site of {name} not found once"
     assert src.count(old) >= 1, f"mutation site of {name} not found"
     mutant = tmp_path / "oracle_mutant.c"
     mutant.write_text(src.replace(old, new))
@@ -42,10 +57,24 @@ def test_pins_catch_mutant(name, tmp_path):
     subprocess.run(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-pthread", str(mutant),
                     "-o", str(so), "-lm"], check=True)
     env = dict(os.environ, ORACLE_LIB_OVERRIDE=str(so))
-    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
-                        os.path.join(ROOT, "tests", "test_oracle_pins.py")],
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider"] +
+                       [os.path.join(ROOT, "tests", f) for f in pin_files],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
-    assert r.returncode != 0, f"mutant {name} survived the pins:\n{r.stdout[-2000:]}"
+    return r.returncode == 0, r.stdout[-2000:]
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_pins_catch_mutant(name, tmp_path):
+    old, new = MUTANTS[name]
+    survived, out = _c_mutant_survives(name, old, new, ("test_oracle_pins.py",), tmp_path)
+    assert not survived, f"mutant {name} survived the pins:\n{out}"
+
+
+@pytest.mark.parametrize("name", sorted(GEO_MUTANTS))
+def test_haversine_pins_catch_mutant(name, tmp_path):
+    old, new = GEO_MUTANTS[name]
+    survived, out = _c_mutant_survives(name, old, new, ("test_oracle_haversine.py",), tmp_path, exact_once=True)
+    assert not survived, f"mutant {name} survived the pins:\n{out}"
 
 
 # the fleet ranking (Alg. 1, lines 14-16 and 20-21) and the fleet move rule (Sec. 3)
@@ -70,10 +99,21 @@ PY_MUTANTS = {
 }
 PY_PIN_FILES = ("test_oracle_fleet.py", "test_oracle_resume.py")
 
+# the local search (Alg. 2 as read for identical vehicles): scan order,
+# candidate bookkeeping, the table of the current placement, strictness, the
+# local-optimum report
+LS_MUTANTS = {
+    "ls_closed_base_not_repositioned": ("O[s], cand[c] = j, i", "O[s] = j"),
+    "ls_scan_slots_inside": ("s, c = int(pa[u // nC]), int(pb[u % nC])", "s, c = int(pa[u % K]), int(pb[u // K])"),
+    "ls_table_kept_after_a_move": ("                moved = True\n                table = None\n",
+                                   "                moved = True\n"),
+    "ls_accepts_equal_objective": ("            if better(F, cur):\n", "            if not better(cur, F):\n"),
+    "ls_optimum_never_reported": ("        if not moved:\n            optimum = True\n",
+                                  "        if not moved:\n            optimum = False\n"),
+}
 
-@pytest.mark.parametrize("name", sorted(PY_MUTANTS))
-def test_fleet_pins_catch_mutant(name, tmp_path, orc):
-    old, new = PY_MUTANTS[name]
+
+def _py_mutant_survives(name, old, new, pin_files, tmp_path, orc):
     src = open(PY_SRC).read()
     assert src.count(old) == 1, f"mutation site of {name} not found once"
     pkg = tmp_path / "oracle"
@@ -81,9 +121,23 @@ def test_fleet_pins_catch_mutant(name, tmp_path, orc):
     (pkg / "__init__.py").write_text(src.replace(old, new))
     env = dict(os.environ, ORACLE_PY_OVERRIDE=str(tmp_path), ORACLE_LIB_OVERRIDE=orc.build())
     r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider"] +
-                       [os.path.join(ROOT, "tests", f) for f in PY_PIN_FILES],
+                       [os.path.join(ROOT, "tests", f) for f in pin_files],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
-    assert r.returncode != 0, f"mutant {name} survived the pins:\n{r.stdout[-2000:]}"
+    return r.returncode == 0, r.stdout[-2000:]
+
+
+@pytest.mark.parametrize("name", sorted(PY_MUTANTS))
+def test_fleet_pins_catch_mutant(name, tmp_path, orc):
+    old, new = PY_MUTANTS[name]
+    survived, out = _py_mutant_survives(name, old, new, PY_PIN_FILES, tmp_path, orc)
+    assert not survived, f"mutant {name} survived the pins:\n{out}"
+
+
+@pytest.mark.parametrize("name", sorted(LS_MUTANTS))
+def test_local_search_pins_catch_mutant(name, tmp_path, orc):
+    old, new = LS_MUTANTS[name]
+    survived, out = _py_mutant_survives(name, old, new, ("test_oracle_local.py",), tmp_path, orc)
+    assert not survived, f"mutant {name} survived the pins:\n{out}"
 
 
 def test_fleet_mutant_harness_runs_the_copy(tmp_path, orc):
