@@ -1014,7 +1014,8 @@ def run_fleet(args):
     e1.synchronize()
     clk = clocks.stop()
     ms = e0.elapsed_time(e1)
-    stats = {k: ctx.kernel_stats(k) for k in ("swap_eval", "fleet_select", "refresh", "swap_delta", "transpose", "init", "rowsum", "topk")}
+    stats = {k: ctx.kernel_stats(k) for k in ("swap_eval", "fleet_select", "refresh", "swap_delta", "transpose",
+                                              "init", "rowsum", "topk")}
     ctx.unload_instance(h)
     line = {"metric": "heterogeneous-fleet Tabu iters/s", "value": n / (ms / 1000.0), "unit": "iters/s",
             "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,

@@ -39,7 +39,8 @@ GEO_MUTANTS = {
     "haversine_full_angles": ("double sp = sin(0.5 * dphi), sl = sin(0.5 * dpsi);",
                               "double sp = sin(dphi), sl = sin(dpsi);"),
     "haversine_radius_not_doubled": ("(2.0 * ORACLE_EARTH_RADIUS_M) * asin", "ORACLE_EARTH_RADIUS_M * asin"),
-    "haversine_longitude_from_latitudes": ("double dpsi = (double)(lon2 - lon1)", "double dpsi = (double)(lat2 - lat1)"),
+    "haversine_longitude_from_latitudes": ("double dpsi = (double)(lon2 - lon1)",
+                                           "double dpsi = (double)(lat2 - lat1)"),
     "haversine_rounded_down": ("asin(sqrt(h));\n    return (int32_t)ceil(d);",
                                "asin(sqrt(h));\n    return (int32_t)floor(d);"),
     "geo_dropped_return_leg": (" +\n               oracle_leg_haversine(qx, qy, bx, by)", ""),
